@@ -1,0 +1,153 @@
+/*
+ * hps.h -- C ABI of the GB300 HPS direct solver for the 2-D variable
+ * coefficient Helmholtz impedance problem
+ *
+ *     -Lap u(x) - kappa^2 c(x) u(x) = s(x)    x in Omega = [x0,x1] x [y0,y1]
+ *     du/dnu + i eta u = t(x)                 x on the boundary of Omega
+ *
+ * (arXiv:1812.07167, Eq. (1); Re(eta) != 0).  The method is the
+ * Hierarchical Poincare-Steklov (HPS) scheme of that paper: per-leaf
+ * corner-free Chebyshev collocation (Sec. 2.1), level-by-level merges of
+ * impedance-to-impedance (ItI) operators (Sec. 2.2, Algorithm 1), and a
+ * solve made of an upward and a downward sweep (Algorithm 2), with the
+ * operators stored as in Sec. 2.4.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Complex numbers are interleaved (re, im) pairs of doubles (C99
+ * double complex / CUDA double2 layout).  Arrays are dense and C-ordered as
+ * written ([a][b] means index b runs fastest).
+ *
+ * Leaves: the domain is cut into mx x my equal rectangles (mx == my, a power
+ * of two).  Leaves are numbered in Morton order: bit 2i of the leaf index is
+ * bit i of the leaf's column (x), bit 2i+1 is bit i of its row (y).
+ *
+ * Nodes: each leaf carries the p x p Chebyshev tensor grid with its four
+ * corners dropped (p^2 - 4 nodes, Sec. 2.1), ordered
+ *     [south edge, east edge, north edge, west edge, interior]
+ * where each edge holds the p-2 non-corner nodes in increasing coordinate and
+ * the (p-2)^2 interior nodes run row by row, x fastest.  Nodes on an edge
+ * shared by two leaves appear once per leaf.
+ *
+ * Outer boundary: 4 m (p-2) nodes ordered [south, east, north, west], each side
+ * in increasing coordinate (the concatenation of the leaves' edges).
+ *
+ * Memory: every array argument may be host or device memory; the library
+ * asks the CUDA runtime which.  Device arrays are used in place; host arrays
+ * are staged through device buffers owned by the handle.  The caller keeps
+ * ownership of every array it passes; the handle owns all operators.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Work is enqueued on it in stream order.  Calls whose outputs are host
+ * memory return after the outputs are written; calls with device outputs
+ * return once the work is enqueued.  A handle must not be used from two
+ * host threads at the same time.
+ *
+ * Errors: every call returns one of the HPS_* codes below; nothing aborts
+ * and no kernel traps.  Numerical failures found on the device (an exactly
+ * zero pivot) are recorded in the handle and reported by hps_status().
+ */
+#ifndef HPS_H
+#define HPS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HPS_OK = 0,
+  HPS_EINVAL = 1,    /* an argument is out of range (see each call) */
+  HPS_ENOMEM = 2,    /* a device allocation failed or the handle's memory cap was hit */
+  HPS_ESINGULAR = 3, /* a leaf matrix B or an interface matrix W had a zero pivot */
+  HPS_ETIMEOUT = 4,  /* a bounded device wait gave up */
+  HPS_ECUDA = 5,     /* a CUDA runtime call failed (no device, launch error, ...) */
+  HPS_ENOTSUP = 6    /* a valid request this build does not implement */
+};
+
+enum { HPS_FP64 = 0 };
+
+typedef struct {
+  double x0, x1, y0, y1; /* the rectangle Omega, x1 > x0, y1 > y0 */
+  int mx, my;            /* leaves per side: equal powers of two, 1 .. 1024 */
+  int p;                 /* Chebyshev nodes per leaf side (the paper's n_c), 4 .. 32 */
+  int q;                 /* points per leaf edge for boundary data: 0 or p-2 (the
+                            corner-free Chebyshev edge nodes; other values are
+                            HPS_EINVAL) */
+  double kappa;          /* wave number, > 0 */
+  double eta_re, eta_im; /* impedance parameter eta, Re(eta) != 0 */
+  int precision;         /* HPS_FP64 (complex128 throughout) */
+} hps_desc;
+
+typedef struct hps_handle hps_handle;
+
+typedef struct {
+  int leaves;               /* mx * my */
+  int levels;               /* merge levels (2 log2 m) */
+  int n_leaf;               /* p^2 - 4 nodes per leaf */
+  int n_bdry;               /* 4 m (p-2) outer boundary nodes */
+  long long dof;            /* leaves * (p^2 - 4) */
+  long long operator_bytes; /* device bytes of stored operators (Sec. 2.4) */
+  long long build_flops;    /* real floating-point operations of one build */
+  long long solve_flops;    /* real floating-point operations of one solve, per RHS */
+  long long solve_bytes;    /* operator bytes one solve reads */
+} hps_info_t;
+
+/* Node coordinates (host helper, no device work; Sec. 2.1 grid).
+ *   leaf_xy: [leaves][p^2-4][2] (x, y) of every leaf node, or NULL
+ *   bdry_xy: [4 m (p-2)][2] outer boundary nodes, or NULL
+ * Both are host memory.  Returns HPS_EINVAL for an invalid descriptor. */
+int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy);
+
+/* Build the direct solver (Algorithm 1 with the leaf step of Sec. 2.1 and the
+ * merge of Sec. 2.2): leaf operators Psi, Y, Gamma for every leaf, then per
+ * merge level W^{-1}, R33a, R33b, R13a, R23b, Phi_a, Phi_b, up to the root
+ * ItI operator.
+ *   c:    [leaves][(p-2)^2] real c(x) at each leaf's interior nodes (the
+ *         boundary rows of the leaf system do not involve c)
+ *   out:  receives the new handle; unchanged on failure
+ * Device memory for all operators is allocated here and owned by the handle.
+ * Returns HPS_EINVAL (bad descriptor, NULL c/out), HPS_ENOMEM, HPS_ECUDA. */
+int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **out);
+
+/* Solve for nrhs right-hand sides (Algorithm 2: upward then downward pass).
+ *   s: [nrhs][leaves][(p-2)^2] complex body load at the interior nodes
+ *   t: [nrhs][4 m (p-2)] complex impedance data du/dnu + i eta u on the
+ *      outer boundary
+ *   u: [nrhs][leaves][p^2-4] complex solution at every leaf node (written)
+ * nrhs == 0 does nothing and returns HPS_OK.  Returns HPS_EINVAL (NULL
+ * handle or array, nrhs < 0), HPS_ENOMEM (workspace), HPS_ECUDA. */
+int hps_solve(hps_handle *h, const double *s, const double *t, double *u, int nrhs, void *stream);
+
+/* The root ItI operator R (Definition of the ItI map; R f = g on the outer
+ * boundary) in the outer-boundary order above.
+ *   R: [4 m (p-2)][4 m (p-2)] complex, row-major (R[i][j] maps incoming data
+ *      at node j to outgoing data at node i)
+ * The root R is the last merge's product; the build keeps it.  Returns
+ * HPS_EINVAL or HPS_ECUDA. */
+int hps_root_R(hps_handle *h, double *R, void *stream);
+
+/* Stored operators of one leaf (Sec. 2.1.1, 2.1.2, 2.4), for inspection.
+ *   Psi: [p^2-4][4(p-2)], Y: [p^2-4][(p-2)^2], Gam: [4(p-2)][(p-2)^2], each
+ *   complex row-major; any may be NULL.
+ * Returns HPS_EINVAL for a leaf index out of range. */
+int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, void *stream);
+
+/* Sizes and operation counts of a built handle (host only, no device work). */
+int hps_info(const hps_handle *h, hps_info_t *info);
+
+/* Wait for the handle's work on `stream` and report device-side failures:
+ * HPS_ESINGULAR with *level / *box (may be NULL) set to the tree level
+ * (leaf level = levels) and box index of the first zero pivot, or HPS_OK. */
+int hps_status(hps_handle *h, void *stream, int *level, int *box);
+
+/* Release the handle and all its device memory.  NULL is allowed. */
+int hps_free(hps_handle *h);
+
+/* Static description of an error code. */
+const char *hps_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPS_H */

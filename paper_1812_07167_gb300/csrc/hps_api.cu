@@ -1,0 +1,902 @@
+// C ABI of the HPS solver (include/hps.h): argument checks, the host-side
+// tree planner (index maps per merge level), device memory ownership, and the
+// per-level launch sequences of the build (Algorithm 1 / Sec. 2.2) and the
+// solve (Algorithm 2).
+//
+// Tree: m x m leaves in Morton order (x bit lowest); level L = 2 log2 m holds
+// the leaves, level 0 the root; the parent of box j on level l+1 is box j/2 on
+// level l, alpha = child 2j, beta = child 2j+1.  The merge into level l is
+// horizontal (alpha west, beta east, shared vertical edge) when L-1-l is
+// even and vertical (alpha south, beta north) otherwise, so the first merge
+// above the leaves is horizontal as in Fig. 3 of the paper.
+//
+// Every box keeps its boundary nodes in the order [I1, I2] that the merge of
+// Sec. 2.2 produces (leaves: [S, E, N, W]).  The planner tracks, for every
+// position of that order, the side and the offset along the side, and
+// derives I1, I2, I3 from it; no reordering pass runs on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/hps.h"
+#include "hps_internal.h"
+
+using hps::CopyBatch;
+using hps::CopyDesc;
+using hps::GemmDesc;
+using hps::Mat;
+
+namespace {
+
+struct Canon {
+  int side;  // 0 S, 1 E, 2 N, 3 W
+  int off;   // offset along the side, in nodes
+};
+
+struct Level {
+  int lev;         // tree level of the parents
+  int P;           // parents on this level
+  int horizontal;  // 1: alpha west / beta east
+  int nc;          // boundary length of each child
+  int n1, n2, n3, nt;
+  std::vector<int> I1, I2, I3a, I3b;  // positions in the children's orders
+  int *d_I1 = nullptr, *d_I2 = nullptr, *d_I3a = nullptr, *d_I3b = nullptr;
+  // stored operators, per parent contiguous (Sec. 2.4)
+  double2 *Winv = nullptr, *R33a = nullptr, *R33b = nullptr, *R13a = nullptr, *R23b = nullptr;
+  double2 *Phia = nullptr, *Phib = nullptr;
+  int gj_cs = 1;
+};
+
+struct Plan {
+  int m, p, e, n, nb, ni, L, leaves, nbdry;
+  std::vector<Level> lv;        // lv[j]: merge j from the leaves up (parents on level L-1-j)
+  std::vector<int> root_src;    // root position -> public boundary index
+  std::vector<int> ints;        // all index maps, concatenated for one upload
+};
+
+long long cplx_bytes(long long count) { return 16LL * count; }
+
+}  // namespace
+
+struct hps_handle {
+  hps_desc desc;
+  Plan plan;
+  hps_info_t info;
+  void *arena = nullptr;  // operators + tables + index maps (one allocation)
+  size_t arena_bytes = 0;
+  double2 *X = nullptr, *GX = nullptr, *Rroot = nullptr;
+  void *tables = nullptr;
+  int *d_ints = nullptr;
+  int *d_root_src = nullptr;
+  unsigned int *d_status = nullptr;
+  int leaf_cs = 8;
+  // solve workspace (grown on demand)
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  // staging for host arrays
+  void *stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+namespace {
+
+int check_desc(const hps_desc *d) {
+  if (!d) return HPS_EINVAL;
+  if (!(d->x1 > d->x0) || !(d->y1 > d->y0)) return HPS_EINVAL;
+  if (!std::isfinite(d->x0) || !std::isfinite(d->x1) || !std::isfinite(d->y0) ||
+      !std::isfinite(d->y1))
+    return HPS_EINVAL;
+  if (d->mx != d->my || d->mx < 1 || d->mx > 1024 || (d->mx & (d->mx - 1))) return HPS_EINVAL;
+  if (d->p < 4 || d->p > 32) return HPS_EINVAL;
+  if (d->q != 0 && d->q != d->p - 2) return HPS_EINVAL;
+  if (!(d->kappa > 0.0) || !std::isfinite(d->kappa)) return HPS_EINVAL;
+  if (d->eta_re == 0.0 || !std::isfinite(d->eta_re) || !std::isfinite(d->eta_im)) return HPS_EINVAL;
+  if (d->precision != HPS_FP64) return HPS_EINVAL;
+  return HPS_OK;
+}
+
+// Chebyshev points (increasing) on [a, b] and the differentiation matrix
+// (row-major), Sec. 2.1: off-diagonal (c_i/c_j)(-1)^(i+j)/(x_i - x_j) with
+// c_0 = c_N = 2, diagonal from the zero row sum of the exact derivative of a
+// constant.
+void cheb(int p, double a, double b, std::vector<double> &x, std::vector<double> &D) {
+  const int N = p - 1;
+  std::vector<double> t(p);
+  x.assign(p, 0.0);
+  D.assign((size_t)p * p, 0.0);
+  for (int j = 0; j < p; j++) {
+    t[j] = std::sin(M_PI * (2.0 * j - N) / (2.0 * N));
+    x[j] = a + 0.5 * (b - a) * (t[j] + 1.0);
+  }
+  for (int i = 0; i < p; i++) {
+    double ci = (i == 0 || i == N) ? 2.0 : 1.0, sum = 0.0;
+    for (int j = 0; j < p; j++) {
+      if (j == i) continue;
+      double cj = (j == 0 || j == N) ? 2.0 : 1.0;
+      double v = (ci / cj) * (((i + j) & 1) ? -1.0 : 1.0) / (t[i] - t[j]);
+      D[(size_t)i * p + j] = v;
+      sum += v;
+    }
+    D[(size_t)i * p + i] = -sum;
+  }
+  for (auto &v : D) v *= 2.0 / (b - a);
+}
+
+// Grid coordinates (ix, iy) of local node k in the order [S, E, N, W, interior].
+void local_grid(int p, int k, int &ix, int &iy) {
+  const int e = p - 2;
+  if (k < e) { ix = 1 + k; iy = 0; return; }
+  k -= e;
+  if (k < e) { ix = p - 1; iy = 1 + k; return; }
+  k -= e;
+  if (k < e) { ix = 1 + k; iy = p - 1; return; }
+  k -= e;
+  if (k < e) { ix = 0; iy = 1 + k; return; }
+  k -= e;
+  ix = 1 + k % e;
+  iy = 1 + k / e;
+}
+
+int log2i(int m) {
+  int k = 0;
+  while ((1 << k) < m) k++;
+  return k;
+}
+
+void morton_decode(int idx, int bits, int &col, int &row) {
+  col = row = 0;
+  for (int i = 0; i < bits; i++) {
+    col |= ((idx >> (2 * i)) & 1) << i;
+    row |= ((idx >> (2 * i + 1)) & 1) << i;
+  }
+}
+
+// Index maps of every merge level (Sec. 2.2, Fig. 3).
+void make_plan(const hps_desc &d, Plan &pl) {
+  pl.m = d.mx;
+  pl.p = d.p;
+  pl.e = d.p - 2;
+  pl.n = d.p * d.p - 4;
+  pl.nb = 4 * pl.e;
+  pl.ni = pl.e * pl.e;
+  pl.L = 2 * log2i(pl.m);
+  pl.leaves = pl.m * pl.m;
+  pl.nbdry = 4 * pl.m * pl.e;
+  const int e = pl.e;
+  std::vector<Canon> cur(pl.nb);
+  for (int k = 0; k < pl.nb; k++) cur[k] = {k / e, k % e};
+  int a = 1, b = 1;  // child box size in leaves (width, height)
+  pl.lv.clear();
+  for (int j = 0; j < pl.L; j++) {
+    Level L;
+    L.lev = pl.L - 1 - j;
+    L.P = 1 << L.lev;
+    L.horizontal = (j % 2 == 0);
+    L.nc = (int)cur.size();
+    const int n3 = L.horizontal ? b * e : a * e;
+    L.n3 = n3;
+    L.I3a.assign(n3, -1);
+    L.I3b.assign(n3, -1);
+    std::vector<Canon> parent;
+    std::vector<Canon> from_b;
+    for (int child = 0; child < 2; child++) {
+      for (int pos = 0; pos < L.nc; pos++) {
+        Canon c = cur[pos];
+        bool shared;
+        Canon pc = c;
+        if (L.horizontal) {
+          if (child == 0) {
+            shared = (c.side == 1);
+          } else {
+            shared = (c.side == 3);
+            if (c.side == 0 || c.side == 2) pc.off += a * e;
+          }
+        } else {
+          if (child == 0) {
+            shared = (c.side == 2);
+          } else {
+            shared = (c.side == 0);
+            if (c.side == 1 || c.side == 3) pc.off += b * e;
+          }
+        }
+        if (shared) {
+          (child == 0 ? L.I3a : L.I3b)[c.off] = pos;
+        } else if (child == 0) {
+          L.I1.push_back(pos);
+          parent.push_back(pc);
+        } else {
+          L.I2.push_back(pos);
+          from_b.push_back(pc);
+        }
+      }
+    }
+    L.n1 = (int)L.I1.size();
+    L.n2 = (int)L.I2.size();
+    L.nt = L.n1 + L.n2;
+    parent.insert(parent.end(), from_b.begin(), from_b.end());
+    cur.swap(parent);
+    if (L.horizontal) a *= 2; else b *= 2;
+    pl.lv.push_back(std::move(L));
+  }
+  // root position -> public boundary index ([S, E, N, W], m e nodes per side)
+  pl.root_src.resize(cur.size());
+  for (size_t pos = 0; pos < cur.size(); pos++)
+    pl.root_src[pos] = cur[pos].side * pl.m * e + cur[pos].off;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int cuda_fail(cudaError_t err) {
+  if (err == cudaSuccess) return HPS_OK;
+  if (err == cudaErrorMemoryAllocation) return HPS_ENOMEM;
+  return HPS_ECUDA;
+}
+
+#define CK(call)                                 \
+  do {                                           \
+    cudaError_t err_ = (call);                   \
+    if (err_ != cudaSuccess) return cuda_fail(err_); \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+Mat mat(const double2 *ptr, long long ld, long long stride, const int *rmap = nullptr,
+        const int *cmap = nullptr) {
+  Mat m;
+  m.ptr = ptr;
+  m.ld = ld;
+  m.stride = stride;
+  m.rmap = rmap;
+  m.cmap = cmap;
+  return m;
+}
+
+GemmDesc gemm(int M, int N, int K, int batch, Mat A, Mat B, Mat C) {
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.batch = batch;
+  g.A = A;
+  g.B = B;
+  g.ksplit = K;
+  g.C = C;
+  g.alpha = make_double2(1.0, 0.0);
+  g.beta = make_double2(0.0, 0.0);
+  return g;
+}
+
+CopyDesc copy(int M, int N, int batch, Mat src, Mat dst, double alpha = 1.0) {
+  CopyDesc c;
+  memset(&c, 0, sizeof(c));
+  c.M = M;
+  c.N = N;
+  c.batch = batch;
+  c.src = src;
+  c.dst = dst;
+  c.alpha = make_double2(alpha, 0.0);
+  return c;
+}
+
+long long env_cap() {
+  const char *s = getenv("HPS_MEM_CAP_BYTES");
+  if (!s || !*s) return -1;
+  return atoll(s);
+}
+
+// Operation counts (real flops; one complex multiply-add = 8).
+void fill_info(const Plan &pl, hps_info_t &in) {
+  in.leaves = pl.leaves;
+  in.levels = pl.L;
+  in.n_leaf = pl.n;
+  in.n_bdry = pl.nbdry;
+  in.dof = (long long)pl.leaves * pl.n;
+  long long n = pl.n, nb = pl.nb, ni = pl.ni;
+  long long bf = (long long)pl.leaves * 8 * (n * n * n + nb * n * pl.p);
+  long long sf = (long long)pl.leaves * 8 * (nb * ni + n * n);
+  long long ob = (long long)pl.leaves * cplx_bytes(n * n + nb * n);
+  long long sb = (long long)pl.leaves * cplx_bytes(n * n + nb * ni);
+  for (const Level &L : pl.lv) {
+    long long n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, P = L.P;
+    bf += P * 8 * (2 * n3 * n3 * n3 + n3 * n3 * n1 + 2 * n3 * n3 * nt + (n1 + n2) * n3 * nt);
+    sf += P * 8 * (3 * n3 * n3 + (n1 + n2) * n3 + 2 * n3 * nt);
+    long long ops = 3 * n3 * n3 + n1 * n3 + n2 * n3 + 2 * n3 * nt;
+    ob += P * cplx_bytes(ops);
+    sb += P * cplx_bytes(ops);
+  }
+  in.build_flops = bf;
+  in.solve_flops = sf;
+  in.operator_bytes = ob;
+  in.solve_bytes = sb;
+}
+
+int choose_gj_cs(int n, int batch) {
+  // smallest cluster whose shared memory fits, then wider while the level
+  // has too few matrices to fill the chip
+  int cs = 1;
+  while (cs < hps::gj_max_cluster() && hps::gj_smem_bytes(n, cs, false, 0) > 200 * 1024) cs *= 2;
+  while (cs < hps::gj_max_cluster() && (long long)batch * cs < 152 && n / (2 * cs) >= 8) cs *= 2;
+  return cs;
+}
+
+int grow(void **buf, size_t *have, size_t need) {
+  if (*have >= need) return HPS_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  CK(cudaMalloc(buf, need));
+  *have = need;
+  return HPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hps_strerror(int code) {
+  switch (code) {
+    case HPS_OK: return "success";
+    case HPS_EINVAL: return "invalid argument";
+    case HPS_ENOMEM: return "out of device memory (or over HPS_MEM_CAP_BYTES)";
+    case HPS_ESINGULAR: return "zero pivot in a leaf or interface matrix";
+    case HPS_ETIMEOUT: return "bounded device wait timed out";
+    case HPS_ECUDA: return "CUDA runtime error";
+    case HPS_ENOTSUP: return "not supported by this build";
+    default: return "unknown error";
+  }
+}
+
+int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy) {
+  int st = check_desc(desc);
+  if (st) return st;
+  const int m = desc->mx, p = desc->p, e = p - 2, n = p * p - 4, bits = log2i(m);
+  const double hx = (desc->x1 - desc->x0) / m, hy = (desc->y1 - desc->y0) / m;
+  std::vector<double> xs, ys, D;
+  if (leaf_xy) {
+    for (int l = 0; l < m * m; l++) {
+      int col, row;
+      morton_decode(l, bits, col, row);
+      cheb(p, desc->x0 + col * hx, desc->x0 + (col + 1) * hx, xs, D);
+      cheb(p, desc->y0 + row * hy, desc->y0 + (row + 1) * hy, ys, D);
+      for (int k = 0; k < n; k++) {
+        int ix, iy;
+        local_grid(p, k, ix, iy);
+        leaf_xy[((size_t)l * n + k) * 2] = xs[ix];
+        leaf_xy[((size_t)l * n + k) * 2 + 1] = ys[iy];
+      }
+    }
+  }
+  if (bdry_xy) {
+    size_t q = 0;
+    for (int side = 0; side < 4; side++)
+      for (int c = 0; c < m; c++) {
+        bool horiz = (side == 0 || side == 2);
+        if (horiz)
+          cheb(p, desc->x0 + c * hx, desc->x0 + (c + 1) * hx, xs, D);
+        else
+          cheb(p, desc->y0 + c * hy, desc->y0 + (c + 1) * hy, ys, D);
+        for (int k = 1; k <= e; k++, q++) {
+          double x = horiz ? xs[k] : (side == 1 ? desc->x1 : desc->x0);
+          double y = horiz ? (side == 0 ? desc->y0 : desc->y1) : ys[k];
+          bdry_xy[2 * q] = x;
+          bdry_xy[2 * q + 1] = y;
+        }
+      }
+  }
+  return HPS_OK;
+}
+
+int hps_free(hps_handle *h) {
+  if (!h) return HPS_OK;
+  if (h->arena) cudaFree(h->arena);
+  if (h->ws) cudaFree(h->ws);
+  if (h->stage) cudaFree(h->stage);
+  delete h;
+  return HPS_OK;
+}
+
+int hps_info(const hps_handle *h, hps_info_t *info) {
+  if (!h || !info) return HPS_EINVAL;
+  *info = h->info;
+  return HPS_OK;
+}
+
+static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
+  Plan &pl = h->plan;
+  const int n = pl.n, nb = pl.nb, ni = pl.ni, p = pl.p, nl = pl.leaves;
+
+  // ---- one arena: leaf operators, merge operators, root R, tables, maps ----
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  size_t oX = take(cplx_bytes((long long)nl * n * n));
+  size_t oGX = take(cplx_bytes((long long)nl * n * nb));
+  std::vector<size_t> oops(pl.lv.size() * 7);
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    const Level &L = pl.lv[j];
+    long long P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt;
+    oops[7 * j + 0] = take(cplx_bytes(P * n3 * n3));  // Winv
+    oops[7 * j + 1] = take(cplx_bytes(P * n3 * n3));  // R33a
+    oops[7 * j + 2] = take(cplx_bytes(P * n3 * n3));  // R33b
+    oops[7 * j + 3] = take(cplx_bytes(P * n1 * n3));  // R13a
+    oops[7 * j + 4] = take(cplx_bytes(P * n2 * n3));  // R23b
+    oops[7 * j + 5] = take(cplx_bytes(P * n3 * nt));  // Phia
+    oops[7 * j + 6] = take(cplx_bytes(P * n3 * nt));  // Phib
+  }
+  const int nroot = pl.lv.empty() ? nb : pl.lv.back().nt;
+  size_t oRroot = take(cplx_bytes((long long)nroot * nroot));
+  size_t tab_bytes = sizeof(double) * 4 * p * p + sizeof(int) * n;
+  size_t oTab = take(tab_bytes);
+  // index maps: per level I1, I2, I3a, I3b, then the root map
+  std::vector<int> ints;
+  std::vector<size_t> imap(pl.lv.size() * 4);
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    const Level &L = pl.lv[j];
+    const std::vector<int> *v[4] = {&L.I1, &L.I2, &L.I3a, &L.I3b};
+    for (int q = 0; q < 4; q++) {
+      imap[4 * j + q] = ints.size();
+      ints.insert(ints.end(), v[q]->begin(), v[q]->end());
+    }
+  }
+  size_t root_at = ints.size();
+  ints.insert(ints.end(), pl.root_src.begin(), pl.root_src.end());
+  size_t oInts = take(sizeof(int) * (ints.size() + 1));
+  size_t oStatus = take(sizeof(unsigned int));
+  h->arena_bytes = off;
+
+  long long cap = env_cap();
+  if (cap >= 0 && (long long)h->arena_bytes > cap) return HPS_ENOMEM;
+  CK(cudaMalloc(&h->arena, h->arena_bytes));
+  char *base = (char *)h->arena;
+  h->X = (double2 *)(base + oX);
+  h->GX = (double2 *)(base + oGX);
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    Level &L = pl.lv[j];
+    L.Winv = (double2 *)(base + oops[7 * j + 0]);
+    L.R33a = (double2 *)(base + oops[7 * j + 1]);
+    L.R33b = (double2 *)(base + oops[7 * j + 2]);
+    L.R13a = (double2 *)(base + oops[7 * j + 3]);
+    L.R23b = (double2 *)(base + oops[7 * j + 4]);
+    L.Phia = (double2 *)(base + oops[7 * j + 5]);
+    L.Phib = (double2 *)(base + oops[7 * j + 6]);
+  }
+  h->Rroot = (double2 *)(base + oRroot);
+  h->tables = base + oTab;
+  h->d_ints = (int *)(base + oInts);
+  h->d_status = (unsigned int *)(base + oStatus);
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    Level &L = pl.lv[j];
+    L.d_I1 = h->d_ints + imap[4 * j + 0];
+    L.d_I2 = h->d_ints + imap[4 * j + 1];
+    L.d_I3a = h->d_ints + imap[4 * j + 2];
+    L.d_I3b = h->d_ints + imap[4 * j + 3];
+  }
+  h->d_root_src = h->d_ints + root_at;
+
+  // ---- host tables: 1-D differentiation on the leaf, squared, node grid ----
+  const double hx = (h->desc.x1 - h->desc.x0) / pl.m, hy = (h->desc.y1 - h->desc.y0) / pl.m;
+  std::vector<double> x, D1x, D1y;
+  cheb(p, 0.0, hx, x, D1x);
+  cheb(p, 0.0, hy, x, D1y);
+  std::vector<unsigned char> tab(tab_bytes);
+  double *T = (double *)tab.data();
+  for (int i = 0; i < p * p; i++) {
+    T[i] = D1x[i];
+    T[p * p + i] = D1y[i];
+  }
+  for (int i = 0; i < p; i++)
+    for (int j = 0; j < p; j++) {
+      double sx = 0.0, sy = 0.0;
+      for (int k = 0; k < p; k++) {
+        sx += D1x[i * p + k] * D1x[k * p + j];
+        sy += D1y[i * p + k] * D1y[k * p + j];
+      }
+      T[2 * p * p + i * p + j] = sx;
+      T[3 * p * p + i * p + j] = sy;
+    }
+  int *G = (int *)(T + 4 * p * p);
+  for (int k = 0; k < n; k++) {
+    int ix, iy;
+    local_grid(p, k, ix, iy);
+    G[k] = ix | (iy << 8);
+  }
+  CK(cudaMemcpyAsync(h->tables, tab.data(), tab_bytes, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned int), st));
+
+  // ---- c on the device ----
+  const double *c_dev = c;
+  void *c_stage = nullptr;
+  size_t cbytes = sizeof(double) * (size_t)nl * ni;
+  if (!is_device_ptr(c)) {
+    CK(cudaMallocAsync(&c_stage, cbytes, st));
+    CK(cudaMemcpyAsync(c_stage, c, cbytes, cudaMemcpyHostToDevice, st));
+    c_dev = (const double *)c_stage;
+  }
+
+  // ---- leaves (Sec. 2.1): one cluster launch over all leaves ----
+  hps::LeafTables lt;
+  lt.p = p;
+  lt.e = pl.e;
+  lt.n = n;
+  lt.nb = nb;
+  lt.ni = ni;
+  lt.eta = make_double2(h->desc.eta_re, h->desc.eta_im);
+  lt.kappa2 = h->desc.kappa * h->desc.kappa;
+  CK(hps::launch_leaf(lt, h->tables, c_dev, nl, h->X, h->GX, h->d_status, pl.L, h->leaf_cs, st));
+  if (c_stage) CK(cudaFreeAsync(c_stage, st));
+
+  if (pl.lv.empty()) {
+    // a single leaf: the root R is the leaf's R = GX[:, :nb]
+    CopyBatch cb;
+    cb.count = 1;
+    cb.d[0] = copy(nb, nb, 1, mat(h->GX, nb, 0), mat(h->Rroot, nb, 0));
+    CK(hps::launch_copy(cb, st));
+    return HPS_OK;
+  }
+
+  // ---- merges (Sec. 2.2), one level at a time (Algorithm 3's level loop) ----
+  size_t rbuf = 0, qbuf = 0;
+  for (const Level &L : pl.lv) {
+    rbuf = std::max(rbuf, (size_t)L.P * L.nt * L.nt);
+    qbuf = std::max(qbuf, (size_t)L.P * L.n3 * L.nt);
+  }
+  double2 *scratch = nullptr;
+  CK(cudaMallocAsync((void **)&scratch, sizeof(double2) * (2 * rbuf + qbuf), st));
+  double2 *Rbuf[2] = {scratch, scratch + rbuf};
+  double2 *Q = scratch + 2 * rbuf;
+
+  // child R of the first merge: the leaves' R = GX[:, :nb] (ld nb, stride n nb)
+  const double2 *Rc = h->GX;
+  long long ldc = nb, strc = (long long)n * nb;
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    Level &L = pl.lv[j];
+    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt;
+    const bool last = (j + 1 == pl.lv.size());
+    double2 *Rp = last ? h->Rroot : Rbuf[j & 1];
+    const long long s2 = 2 * strc;
+    Mat Ra = mat(Rc, ldc, s2), Rb = mat(Rc + strc, ldc, s2);
+    auto sub = [&](Mat m, const int *r, const int *c) {
+      m.rmap = r;
+      m.cmap = c;
+      return m;
+    };
+    // stored blocks and the parts of Phi_b and R^tau that are copies
+    CopyBatch cb;
+    cb.count = 0;
+    cb.d[cb.count++] = copy(n3, n3, P, sub(Ra, L.d_I3a, L.d_I3a), mat(L.R33a, n3, (long long)n3 * n3));
+    cb.d[cb.count++] = copy(n3, n3, P, sub(Rb, L.d_I3b, L.d_I3b), mat(L.R33b, n3, (long long)n3 * n3));
+    cb.d[cb.count++] = copy(n1, n3, P, sub(Ra, L.d_I1, L.d_I3a), mat(L.R13a, n1, (long long)n1 * n3));
+    cb.d[cb.count++] = copy(n2, n3, P, sub(Rb, L.d_I2, L.d_I3b), mat(L.R23b, n2, (long long)n2 * n3));
+    // Q = [R33b R31a | -R32b]: the right block here, the left one by GEMM below
+    cb.d[cb.count++] = copy(n3, n2, P, sub(Rb, L.d_I3b, L.d_I2),
+                            mat(Q + (size_t)n1 * n3, n3, (long long)n3 * nt), -1.0);
+    // Phi_b starts as -[R31a | 0]
+    cb.d[cb.count++] = copy(n3, n1, P, sub(Ra, L.d_I3a, L.d_I1), mat(L.Phib, n3, (long long)n3 * nt), -1.0);
+    cb.d[cb.count++] = copy(n3, n2, P, mat(nullptr, 0, 0), mat(L.Phib + (size_t)n1 * n3, n3, (long long)n3 * nt));
+    // R^tau starts as diag(R11a, R22b)
+    const long long sp = (long long)nt * nt;
+    cb.d[cb.count++] = copy(n1, n1, P, sub(Ra, L.d_I1, L.d_I1), mat(Rp, nt, sp));
+    cb.d[cb.count++] = copy(n2, n2, P, sub(Rb, L.d_I2, L.d_I2), mat(Rp + (size_t)n1 * nt + n1, nt, sp));
+    cb.d[cb.count++] = copy(n2, n1, P, mat(nullptr, 0, 0), mat(Rp + n1, nt, sp));
+    cb.d[cb.count++] = copy(n1, n2, P, mat(nullptr, 0, 0), mat(Rp + (size_t)n1 * nt, nt, sp));
+    CK(hps::launch_copy(cb, st));
+
+    const long long s33 = (long long)n3 * n3, s3t = (long long)n3 * nt;
+    // W = I - R33b R33a (into the W^{-1} slot), then invert in place
+    GemmDesc g = gemm(n3, n3, n3, P, mat(L.R33b, n3, s33), mat(L.R33a, n3, s33), mat(L.Winv, n3, s33));
+    g.alpha = make_double2(-1.0, 0.0);
+    g.addI = 1;
+    CK(hps::launch_gemm(&g, 1, st));
+    CK(hps::launch_gj_inverse(L.Winv, n3, P, h->d_status, L.lev, L.gj_cs, st));
+    // Q(:, :n1) = R33b R31a
+    g = gemm(n3, n1, n3, P, mat(L.R33b, n3, s33), sub(Ra, L.d_I3a, L.d_I1), mat(Q, n3, s3t));
+    CK(hps::launch_gemm(&g, 1, st));
+    // Phi_a = W^{-1} Q
+    g = gemm(n3, nt, n3, P, mat(L.Winv, n3, s33), mat(Q, n3, s3t), mat(L.Phia, n3, s3t));
+    CK(hps::launch_gemm(&g, 1, st));
+    // Phi_b = -[R31a | 0] - R33a Phi_a
+    g = gemm(n3, nt, n3, P, mat(L.R33a, n3, s33), mat(L.Phia, n3, s3t), mat(L.Phib, n3, s3t));
+    g.alpha = make_double2(-1.0, 0.0);
+    g.D = g.C;
+    g.beta = make_double2(1.0, 0.0);
+    CK(hps::launch_gemm(&g, 1, st));
+    // R^tau = diag(R11a, R22b) + diag(R13a, R23b) [Phi_a; Phi_b]
+    GemmDesc g2[2];
+    g2[0] = gemm(n1, nt, n3, P, mat(L.R13a, n1, (long long)n1 * n3), mat(L.Phia, n3, s3t), mat(Rp, nt, sp));
+    g2[0].D = g2[0].C;
+    g2[0].beta = make_double2(1.0, 0.0);
+    g2[1] = gemm(n2, nt, n3, P, mat(L.R23b, n2, (long long)n2 * n3), mat(L.Phib, n3, s3t),
+                 mat(Rp + n1, nt, sp));
+    g2[1].D = g2[1].C;
+    g2[1].beta = make_double2(1.0, 0.0);
+    CK(hps::launch_gemm(g2, 2, st));
+    Rc = Rp;
+    ldc = nt;
+    strc = sp;
+  }
+  CK(cudaFreeAsync(scratch, st));
+  return HPS_OK;
+}
+
+int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **out) {
+  int st0 = check_desc(desc);
+  if (st0) return st0;
+  if (!c || !out) return HPS_EINVAL;
+  hps_handle *h = new (std::nothrow) hps_handle();
+  if (!h) return HPS_ENOMEM;
+  h->desc = *desc;
+  if (h->desc.q == 0) h->desc.q = desc->p - 2;
+  make_plan(h->desc, h->plan);
+  fill_info(h->plan, h->info);
+  // leaf cluster: the smallest power of two whose shared memory fits
+  int cs = 1;
+  while (cs < hps::gj_max_cluster() && hps::gj_smem_bytes(h->plan.n, cs, true, h->plan.p) > 200 * 1024)
+    cs *= 2;
+  if (const char *e = getenv("HPS_LEAF_CLUSTER")) {
+    int v = atoi(e);
+    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) cs = std::max(cs, v);
+  }
+  h->leaf_cs = cs;
+  for (Level &L : h->plan.lv) L.gj_cs = choose_gj_cs(L.n3, L.P);
+  long long cap = env_cap();
+  if (cap >= 0 && h->info.operator_bytes > cap) {
+    delete h;
+    return HPS_ENOMEM;
+  }
+  int st = build_impl(h, c, (cudaStream_t)stream);
+  if (st != HPS_OK) {
+    hps_free(h);
+    return st;
+  }
+  *out = h;
+  return HPS_OK;
+}
+
+int hps_status(hps_handle *h, void *stream, int *level, int *box) {
+  if (!h) return HPS_EINVAL;
+  unsigned int w = 0;
+  CK(cudaMemcpyAsync(&w, h->d_status, sizeof(w), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  if (level) *level = w ? (int)((w >> 20) & 0xff) : -1;
+  if (box) *box = w ? (int)(w & 0xfffff) : -1;
+  return w ? HPS_ESINGULAR : HPS_OK;
+}
+
+int hps_solve(hps_handle *h, const double *s_, const double *t_, double *u_, int nrhs, void *stream) {
+  if (!h || nrhs < 0) return HPS_EINVAL;
+  if (nrhs == 0) return HPS_OK;
+  if (!s_ || !t_ || !u_) return HPS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Plan &pl = h->plan;
+  const int n = pl.n, nb = pl.nb, ni = pl.ni, nl = pl.leaves, R = nrhs;
+
+  // workspace: h per level, t~3a / t~3b per merge, t per level, one temp
+  std::vector<size_t> oh(pl.lv.size() + 1), ot(pl.lv.size() + 1), ota(pl.lv.size()), otb(pl.lv.size());
+  size_t off = 0;
+  auto take = [&](long long count) {
+    size_t o = off;
+    off = align256(off + sizeof(double2) * (size_t)count);
+    return o;
+  };
+  oh[0] = take((long long)R * nl * nb);
+  ot[0] = take((long long)R * nl * nb);
+  long long vmax = 1;
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    const Level &L = pl.lv[j];
+    oh[j + 1] = take((long long)R * L.P * L.nt);
+    ot[j + 1] = take((long long)R * L.P * L.nt);
+    ota[j] = take((long long)R * L.P * L.n3);
+    otb[j] = take((long long)R * L.P * L.n3);
+    vmax = std::max(vmax, (long long)R * L.P * L.n3);
+  }
+  size_t ov = take(vmax);
+  size_t ws_need = off;
+  int gst = grow(&h->ws, &h->ws_bytes, ws_need);
+  if (gst) return gst;
+  char *wb = (char *)h->ws;
+  auto W = [&](size_t o) { return (double2 *)(wb + o); };
+
+  // stage host arrays
+  const bool sdev = is_device_ptr(s_), tdev = is_device_ptr(t_), udev = is_device_ptr(u_);
+  size_t sbytes = sizeof(double2) * (size_t)R * nl * ni, tbytes = sizeof(double2) * (size_t)R * pl.nbdry;
+  size_t ubytes = sizeof(double2) * (size_t)R * nl * n;
+  size_t need = (sdev ? 0 : align256(sbytes)) + (tdev ? 0 : align256(tbytes)) + (udev ? 0 : align256(ubytes));
+  if (need) {
+    gst = grow(&h->stage, &h->stage_bytes, need);
+    if (gst) return gst;
+  }
+  char *sb = (char *)h->stage;
+  const double2 *s = (const double2 *)s_;
+  const double2 *t = (const double2 *)t_;
+  double2 *u = (double2 *)u_;
+  if (!sdev) {
+    CK(cudaMemcpyAsync(sb, s_, sbytes, cudaMemcpyHostToDevice, st));
+    s = (const double2 *)sb;
+    sb += align256(sbytes);
+  }
+  if (!tdev) {
+    CK(cudaMemcpyAsync(sb, t_, tbytes, cudaMemcpyHostToDevice, st));
+    t = (const double2 *)sb;
+    sb += align256(tbytes);
+  }
+  if (!udev) u = (double2 *)sb;
+
+  // ---- upward pass ----
+  // leaves: h = Gamma s  (Gamma = GX[:, nb:])
+  GemmDesc g = gemm(nb, R, ni, nl, mat(h->GX + (size_t)nb * nb, nb, (long long)n * nb),
+                    mat(s, (long long)nl * ni, ni), mat(W(oh[0]), (long long)nl * nb, nb));
+  CK(hps::launch_gemm(&g, 1, st));
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    const Level &L = pl.lv[j];
+    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc;
+    const double2 *hc = W(oh[j]);
+    const long long ldh = (long long)2 * P * nc;
+    Mat hA = mat(hc, ldh, 2LL * nc), hB = mat(hc + nc, ldh, 2LL * nc);
+    Mat h3a = hA, h3b = hB, h1a = hA, h2b = hB;
+    h3a.rmap = L.d_I3a;
+    h3b.rmap = L.d_I3b;
+    h1a.rmap = L.d_I1;
+    h2b.rmap = L.d_I2;
+    const long long s33 = (long long)n3 * n3, ldv = (long long)P * n3;
+    double2 *v = W(ov), *ta = W(ota[j]), *tb = W(otb[j]);
+    // v = R33b h3a - h3b ;  t~3a = W^{-1} v  (Upsilon_a [h3a; h3b])
+    g = gemm(n3, R, n3, P, mat(L.R33b, n3, s33), h3a, mat(v, ldv, n3));
+    g.D = h3b;
+    g.beta = make_double2(-1.0, 0.0);
+    CK(hps::launch_gemm(&g, 1, st));
+    g = gemm(n3, R, n3, P, mat(L.Winv, n3, s33), mat(v, ldv, n3), mat(ta, ldv, n3));
+    CK(hps::launch_gemm(&g, 1, st));
+    // t~3b = -h3a - R33a t~3a  (Upsilon_b [h3a; h3b])
+    g = gemm(n3, R, n3, P, mat(L.R33a, n3, s33), mat(ta, ldv, n3), mat(tb, ldv, n3));
+    g.alpha = make_double2(-1.0, 0.0);
+    g.D = h3a;
+    g.beta = make_double2(-1.0, 0.0);
+    CK(hps::launch_gemm(&g, 1, st));
+    // h^tau = [h1a + R13a t~3a ; h2b + R23b t~3b]  (Eq. flux_part)
+    const long long ldp = (long long)P * nt;
+    GemmDesc g2[2];
+    g2[0] = gemm(n1, R, n3, P, mat(L.R13a, n1, (long long)n1 * n3), mat(ta, ldv, n3), mat(W(oh[j + 1]), ldp, nt));
+    g2[0].D = h1a;
+    g2[0].beta = make_double2(1.0, 0.0);
+    g2[1] = gemm(n2, R, n3, P, mat(L.R23b, n2, (long long)n2 * n3), mat(tb, ldv, n3),
+                 mat(W(oh[j + 1]) + n1, ldp, nt));
+    g2[1].D = h2b;
+    g2[1].beta = make_double2(1.0, 0.0);
+    CK(hps::launch_gemm(g2, 2, st));
+  }
+
+  // ---- downward pass ----
+  const size_t top = pl.lv.size();
+  const int ntop = top ? pl.lv.back().nt : nb;
+  {
+    // root incoming data: public [S, E, N, W] order -> the root's [I1, I2] order
+    CopyBatch cb;
+    cb.count = 1;
+    cb.d[0] = copy(ntop, R, 1, mat(t, pl.nbdry, 0, h->d_root_src), mat(W(ot[top]), ntop, 0));
+    CK(hps::launch_copy(cb, st));
+  }
+  for (size_t jj = top; jj-- > 0;) {
+    const Level &L = pl.lv[jj];
+    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc;
+    const double2 *tp = W(ot[jj + 1]);
+    double2 *tc = W(ot[jj]);
+    const long long ldp = (long long)P * nt, ldc2 = (long long)2 * P * nc, ldv = (long long)P * n3;
+    const long long s3t = (long long)n3 * nt;
+    // t3a = Phi_a t^tau + t~3a -> alpha rows I3 ; t3b = Phi_b t^tau + t~3b -> beta rows I3
+    GemmDesc g2[2];
+    g2[0] = gemm(n3, R, nt, P, mat(L.Phia, n3, s3t), mat(tp, ldp, nt), mat(tc, ldc2, 2LL * nc, L.d_I3a));
+    g2[0].D = mat(W(ota[jj]), ldv, n3);
+    g2[0].beta = make_double2(1.0, 0.0);
+    g2[1] = gemm(n3, R, nt, P, mat(L.Phib, n3, s3t), mat(tp, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I3b));
+    g2[1].D = mat(W(otb[jj]), ldv, n3);
+    g2[1].beta = make_double2(1.0, 0.0);
+    CK(hps::launch_gemm(g2, 2, st));
+    // the rest of the children's incoming data is the parent's: I1 and I2
+    CopyBatch cb;
+    cb.count = 2;
+    cb.d[0] = copy(n1, R, P, mat(tp, ldp, nt), mat(tc, ldc2, 2LL * nc, L.d_I1));
+    cb.d[1] = copy(n2, R, P, mat(tp + n1, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I2));
+    CK(hps::launch_copy(cb, st));
+  }
+  // leaves: u = Psi t + Y s = X [t; s]
+  g = gemm(n, R, n, nl, mat(h->X, n, (long long)n * n), mat(W(ot[0]), (long long)nl * nb, nb),
+           mat(u, (long long)nl * n, n));
+  g.B2 = mat(s, (long long)nl * ni, ni);
+  g.ksplit = nb;
+  CK(hps::launch_gemm(&g, 1, st));
+
+  if (!udev) {
+    CK(cudaMemcpyAsync(u_, u, ubytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  } else if (!sdev || !tdev) {
+    // host inputs were staged: make the call's staging reusable on return
+    CK(cudaStreamSynchronize(st));
+  }
+  return HPS_OK;
+}
+
+int hps_root_R(hps_handle *h, double *R, void *stream) {
+  if (!h || !R) return HPS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nbr = h->plan.nbdry;
+  const bool dev = is_device_ptr(R);
+  double2 *dst = (double2 *)R;
+  size_t bytes = sizeof(double2) * (size_t)nbr * nbr;
+  if (!dev) {
+    int gst = grow(&h->stage, &h->stage_bytes, bytes);
+    if (gst) return gst;
+    dst = (double2 *)h->stage;
+  }
+  const int nr = h->plan.lv.empty() ? h->plan.nb : h->plan.lv.back().nt;
+  // public row-major R[a][b] = root(src^-1 ...): with the root order map
+  // root position -> public index, R_pub[pub(i)][pub(j)] = R_root(i, j).
+  // As a column-major matrix R_pub^T: element (pub(j), pub(i)) = R_root(i, j),
+  // i.e. dst(a=pub(j), b=pub(i)) = src(i, j): a transposed copy with the
+  // destination rows and columns mapped by the root map.
+  CopyBatch cb;
+  cb.count = 1;
+  cb.d[0] = copy(nr, nr, 1, mat(h->Rroot, nr, 0), mat(dst, nbr, 0, h->d_root_src, h->d_root_src));
+  cb.d[0].trans = 1;
+  CK(hps::launch_copy(cb, st));
+  if (!dev) {
+    CK(cudaMemcpyAsync(R, dst, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return HPS_OK;
+}
+
+int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, void *stream) {
+  if (!h || leaf < 0 || leaf >= h->plan.leaves) return HPS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = h->plan.n, nb = h->plan.nb, ni = h->plan.ni;
+  const double2 *X = h->X + (size_t)leaf * n * n;
+  const double2 *GX = h->GX + (size_t)leaf * n * nb;
+  struct Part {
+    double *out;
+    int rows, cols;
+    const double2 *src;
+    long long ld;
+  } parts[3] = {{Psi, n, nb, X, n}, {Y, n, ni, X + (size_t)nb * n, n}, {Gam, nb, ni, GX + (size_t)nb * nb, nb}};
+  for (const Part &pt : parts) {
+    if (!pt.out) continue;
+    size_t bytes = sizeof(double2) * (size_t)pt.rows * pt.cols;
+    const bool dev = is_device_ptr(pt.out);
+    double2 *dst = (double2 *)pt.out;
+    if (!dev) {
+      int gst = grow(&h->stage, &h->stage_bytes, bytes);
+      if (gst) return gst;
+      dst = (double2 *)h->stage;
+    }
+    // row-major out[i][j] = src(i, j): column-major (j, i) of dst = src(i, j)
+    CopyBatch cb;
+    cb.count = 1;
+    cb.d[0] = copy(pt.cols, pt.rows, 1, mat(pt.src, pt.ld, 0), mat(dst, pt.cols, 0));
+    cb.d[0].trans = 1;
+    CK(hps::launch_copy(cb, st));
+    if (!dev) {
+      CK(cudaMemcpyAsync(pt.out, dst, bytes, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+  }
+  return HPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,223 @@
+"""Thin Python binding of the C ABI in ``include/hps.h`` (ctypes).
+
+The functions carry the C names (``hps_nodes``, ``hps_build``, ``hps_solve``,
+``hps_root_R``, ``hps_leaf_ops``, ``hps_info``, ``hps_status``, ``hps_free``)
+and only marshal arguments: arrays are passed as raw pointers (numpy arrays
+as host pointers, torch tensors as their data pointers), streams as
+``cudaStream_t`` handles.  Every step of the method runs in the library's
+CUDA kernels; there is no fallback.  Loading fails loudly if
+``_lib/libhps.so`` has not been built (``python -m paper_1812_07167_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libhps.so")
+
+HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ETIMEOUT, HPS_ECUDA, HPS_ENOTSUP = range(7)
+HPS_FP64 = 0
+
+# every entry point include/hps.h declares
+EXPORTS = ("hps_nodes", "hps_build", "hps_solve", "hps_root_R", "hps_leaf_ops", "hps_info",
+           "hps_status", "hps_free", "hps_strerror")
+
+
+class hps_desc(ctypes.Structure):
+    _fields_ = [
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("mx", ctypes.c_int), ("my", ctypes.c_int),
+        ("p", ctypes.c_int), ("q", ctypes.c_int),
+        ("kappa", ctypes.c_double),
+        ("eta_re", ctypes.c_double), ("eta_im", ctypes.c_double),
+        ("precision", ctypes.c_int),
+    ]
+
+
+class hps_info_t(ctypes.Structure):
+    _fields_ = [
+        ("leaves", ctypes.c_int), ("levels", ctypes.c_int),
+        ("n_leaf", ctypes.c_int), ("n_bdry", ctypes.c_int),
+        ("dof", ctypes.c_longlong), ("operator_bytes", ctypes.c_longlong),
+        ("build_flops", ctypes.c_longlong), ("solve_flops", ctypes.c_longlong),
+        ("solve_bytes", ctypes.c_longlong),
+    ]
+
+
+class HPSError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {hps_strerror(code)} (code {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libhps (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhps is not built ({LIB_PATH} missing); run "
+                               "python -m paper_1812_07167_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        D = ctypes.POINTER(hps_desc)
+        L.hps_nodes.argtypes = [D, P, P]
+        L.hps_build.argtypes = [D, P, P, ctypes.POINTER(ctypes.c_void_p)]
+        L.hps_solve.argtypes = [P, P, P, P, ctypes.c_int, P]
+        L.hps_root_R.argtypes = [P, P, P]
+        L.hps_leaf_ops.argtypes = [P, ctypes.c_int, P, P, P, P]
+        L.hps_info.argtypes = [P, ctypes.POINTER(hps_info_t)]
+        L.hps_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.hps_free.argtypes = [P]
+        L.hps_strerror.argtypes = [ctypes.c_int]
+        L.hps_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def hps_strerror(code: int) -> str:
+    return lib().hps_strerror(int(code)).decode()
+
+
+@dataclass
+class Problem:
+    """Parameters of one problem (the fields of hps_desc)."""
+    m: int
+    p: int
+    kappa: float
+    eta: complex
+    x0: float = 0.0
+    x1: float = 1.0
+    y0: float = 0.0
+    y1: float = 1.0
+
+    def desc(self) -> hps_desc:
+        eta = complex(self.eta)
+        return hps_desc(self.x0, self.x1, self.y0, self.y1, self.m, self.m, self.p, self.p - 2,
+                        float(self.kappa), eta.real, eta.imag, HPS_FP64)
+
+    @property
+    def n(self) -> int:
+        return self.p * self.p - 4
+
+    @property
+    def nb(self) -> int:
+        return 4 * (self.p - 2)
+
+    @property
+    def ni(self) -> int:
+        return (self.p - 2) ** 2
+
+    @property
+    def leaves(self) -> int:
+        return self.m * self.m
+
+    @property
+    def nbdry(self) -> int:
+        return 4 * self.m * (self.p - 2)
+
+
+def _ptr(a) -> int:
+    """Raw pointer of a numpy array (host) or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to libhps must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors passed to libhps must be contiguous")
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(code: int, what: str):
+    if code != HPS_OK:
+        raise HPSError(code, what)
+
+
+def hps_nodes(pr: Problem):
+    """(leaf_xy [leaves, p^2-4, 2], bdry_xy [4 m (p-2), 2]) as numpy arrays."""
+    lxy = np.zeros((pr.leaves, pr.n, 2))
+    bxy = np.zeros((pr.nbdry, 2))
+    d = pr.desc()
+    _check(lib().hps_nodes(ctypes.byref(d), _ptr(lxy), _ptr(bxy)), "hps_nodes")
+    return lxy, bxy
+
+
+class Handle:
+    """A built solver (owns device memory until free())."""
+
+    def __init__(self, ptr: int, pr: Problem):
+        self.ptr = ptr
+        self.pr = pr
+
+    def info(self) -> hps_info_t:
+        out = hps_info_t()
+        _check(lib().hps_info(self.ptr, ctypes.byref(out)), "hps_info")
+        return out
+
+    def free(self):
+        if self.ptr:
+            lib().hps_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hps_build(pr: Problem, c, stream=None) -> Handle:
+    """Build the solver; c is [leaves, (p-2)^2] float64 (numpy or torch)."""
+    d = pr.desc()
+    h = ctypes.c_void_p()
+    _check(lib().hps_build(ctypes.byref(d), _ptr(c), _stream(stream), ctypes.byref(h)), "hps_build")
+    return Handle(h.value, pr)
+
+
+def hps_solve(h: Handle, s, t, u, nrhs: int, stream=None):
+    """u[nrhs, leaves, p^2-4] (complex128) from s and t (numpy or torch)."""
+    _check(lib().hps_solve(h.ptr, _ptr(s), _ptr(t), _ptr(u), int(nrhs), _stream(stream)), "hps_solve")
+    return u
+
+
+def hps_root_R(h: Handle, R, stream=None):
+    _check(lib().hps_root_R(h.ptr, _ptr(R), _stream(stream)), "hps_root_R")
+    return R
+
+
+def hps_leaf_ops(h: Handle, leaf: int, Psi=None, Y=None, Gam=None, stream=None):
+    _check(lib().hps_leaf_ops(h.ptr, int(leaf), _ptr(Psi), _ptr(Y), _ptr(Gam), _stream(stream)),
+           "hps_leaf_ops")
+    return Psi, Y, Gam
+
+
+def hps_status(h: Handle, stream=None):
+    """(code, level, box) after waiting for the handle's work on the stream."""
+    lev = ctypes.c_int(-1)
+    box = ctypes.c_int(-1)
+    code = lib().hps_status(h.ptr, _stream(stream), ctypes.byref(lev), ctypes.byref(box))
+    return code, lev.value, box.value
+
+
+def hps_free(h: Handle):
+    h.free()

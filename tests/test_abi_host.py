@@ -1,0 +1,99 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads and
+exports every entry point include/hps.h declares, argument checks fail with
+the documented codes before any device work, and the node layout agrees
+with the oracle's."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1812_07167_gb300 import build as B
+from paper_1812_07167_gb300 import hps
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hps.h")).read()
+    return sorted(set(re.findall(r"\b(hps_[a-zA-Z_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert _declared() == sorted(hps.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(hps.LIB_PATH)
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_strerror_codes():
+    for code in range(7):
+        assert hps.hps_strerror(code)
+    assert hps.hps_strerror(99) == "unknown error"
+
+
+@pytest.mark.parametrize("m,p", [(1, 4), (2, 8), (4, 16), (8, 6)])
+def test_nodes_match_oracle(m, p):
+    pr = hps.Problem(m, p, 10.0, 10.0, -1.0, 2.0, 0.5, 1.0)
+    lxy, bxy = hps.hps_nodes(pr)
+    olxy, obxy = O.nodes(O.Problem(m, p, 10.0, 10.0, -1.0, 2.0, 0.5, 1.0))
+    np.testing.assert_allclose(lxy, olxy, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(bxy, obxy, rtol=0, atol=1e-15)
+
+
+def _desc(**kw):
+    base = dict(x0=0.0, x1=1.0, y0=0.0, y1=1.0, mx=4, my=4, p=8, q=6, kappa=5.0, eta_re=5.0,
+                eta_im=0.0, precision=0)
+    base.update(kw)
+    return hps.hps_desc(**base)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(mx=3, my=3), dict(mx=4, my=2), dict(mx=0, my=0), dict(p=3), dict(p=33), dict(q=5),
+    dict(kappa=0.0), dict(kappa=-1.0), dict(eta_re=0.0, eta_im=1.0), dict(x1=0.0),
+    dict(y1=-1.0), dict(precision=7), dict(kappa=float("nan")),
+])
+def test_invalid_descriptor_is_rejected_before_device_work(bad):
+    d = _desc(**bad)
+    c = np.ones(4 * 4 * 36)
+    h = ctypes.c_void_p()
+    assert hps.lib().hps_build(ctypes.byref(d), c.ctypes.data, None, ctypes.byref(h)) == hps.HPS_EINVAL
+    assert hps.lib().hps_nodes(ctypes.byref(d), None, None) == hps.HPS_EINVAL
+    assert h.value is None
+
+
+def test_null_arguments():
+    d = _desc()
+    h = ctypes.c_void_p()
+    assert hps.lib().hps_build(ctypes.byref(d), None, None, ctypes.byref(h)) == hps.HPS_EINVAL
+    assert hps.lib().hps_build(None, None, None, ctypes.byref(h)) == hps.HPS_EINVAL
+    assert hps.lib().hps_solve(None, None, None, None, 1, None) == hps.HPS_EINVAL
+    assert hps.lib().hps_root_R(None, None, None) == hps.HPS_EINVAL
+    assert hps.lib().hps_leaf_ops(None, 0, None, None, None, None) == hps.HPS_EINVAL
+    assert hps.lib().hps_status(None, None, None, None) == hps.HPS_EINVAL
+    assert hps.lib().hps_info(None, None) == hps.HPS_EINVAL
+    assert hps.lib().hps_free(None) == hps.HPS_OK
+
+
+def test_memory_cap_refuses_before_allocating(monkeypatch):
+    monkeypatch.setenv("HPS_MEM_CAP_BYTES", "1000")
+    d = _desc()
+    c = np.ones(16 * 36)
+    h = ctypes.c_void_p()
+    assert hps.lib().hps_build(ctypes.byref(d), c.ctypes.data, None, ctypes.byref(h)) == hps.HPS_ENOMEM
+
+
+def test_q_zero_means_p_minus_2():
+    d = _desc(q=0)
+    lxy = np.zeros((16, 60, 2))
+    assert hps.lib().hps_nodes(ctypes.byref(d), lxy.ctypes.data, None) == hps.HPS_OK

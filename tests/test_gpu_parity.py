@@ -1,0 +1,188 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Bar (FP64 path): max |x_gpu - x_oracle| / max |x_oracle| <= 1e-10 for the
+leaf operators (Psi, Y, Gamma), the root ItI operator and the solution u.
+Sizes span several GEMM tiles and cluster column slabs with ragged tails
+(n = p^2 - 4 = 252 over 8 CTAs of 32 columns, merge sizes 14 ... 224).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1812_07167_gb300 import hps
+from paper_1812_07167_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def device():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    hps.lib()  # loud failure if libhps was not built
+    yield
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _pair(m, p, kappa, eta, domain=(0.0, 1.0, 0.0, 1.0)):
+    x0, x1, y0, y1 = domain
+    return (hps.Problem(m, p, kappa, eta, x0, x1, y0, y1), O.Problem(m, p, kappa, eta, x0, x1, y0, y1))
+
+
+def gpu_build(pr, c):
+    cd = torch.from_numpy(np.ascontiguousarray(c, dtype=np.float64)).cuda()
+    h = hps.hps_build(pr, cd, torch.cuda.current_stream())
+    code, lev, box = hps.hps_status(h, torch.cuda.current_stream())
+    assert code == hps.HPS_OK, (code, lev, box)
+    return h
+
+
+def gpu_solve(h, s, t):
+    pr = h.pr
+    s = np.ascontiguousarray(s, dtype=np.complex128).reshape(-1, pr.leaves, pr.ni)
+    nrhs = s.shape[0]
+    t = np.ascontiguousarray(t, dtype=np.complex128).reshape(nrhs, pr.nbdry)
+    sd = torch.from_numpy(s).cuda()
+    td = torch.from_numpy(t).cuda()
+    ud = torch.empty((nrhs, pr.leaves, pr.n), dtype=torch.complex128, device="cuda")
+    hps.hps_solve(h, sd, td, ud, nrhs, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return ud.cpu().numpy()
+
+
+def gpu_root_R(h):
+    R = np.zeros((h.pr.nbdry, h.pr.nbdry), complex)
+    hps.hps_root_R(h, R, torch.cuda.current_stream())
+    return R
+
+
+@pytest.mark.parametrize("m,p,kappa,eta", [(1, 8, 7.0, 3.0 + 1.0j), (2, 16, 30.0, 30.0), (4, 12, 20.0, 20.0)])
+def test_leaf_operators(m, p, kappa, eta):
+    pr, opr = _pair(m, p, kappa, eta, (0.0, 1.0, 0.0, 0.5))
+    c, _, _ = W.random_data(m, p, kappa, eta, seed=31)
+    h = gpu_build(pr, c)
+    for leaf in range(pr.leaves):
+        Psi = np.zeros((pr.n, pr.nb), complex)
+        Y = np.zeros((pr.n, pr.ni), complex)
+        Gam = np.zeros((pr.nb, pr.ni), complex)
+        hps.hps_leaf_ops(h, leaf, Psi, Y, Gam, torch.cuda.current_stream())
+        oPsi, oY, oR, oGam = O.leaf(opr, c[leaf])
+        assert _rel(Psi, oPsi) < TOL
+        assert _rel(Y, oY) < TOL
+        assert _rel(Gam, oGam) < TOL
+    h.free()
+
+
+@pytest.mark.parametrize(
+    "m,p,kappa,eta,domain,nrhs",
+    [
+        (1, 6, 4.0, 2.0, (0.0, 1.0, 0.0, 1.0), 1),
+        (2, 8, 9.0, 9.0 - 2.0j, (0.0, 1.0, 0.0, 1.0), 3),
+        (4, 10, 15.0, 6.0, (-1.0, 1.0, 0.0, 0.5), 2),
+        (4, 16, 25.0, 25.0, (0.0, 1.0, 0.0, 1.0), 40),
+        (8, 8, 30.0, 30.0, (0.0, 1.0, 0.0, 1.0), 1),
+        (8, 16, 40.0, 40.0, (0.0, 1.0, 0.0, 1.0), 5),
+    ],
+)
+def test_solution_and_root_operator(m, p, kappa, eta, domain, nrhs):
+    pr, opr = _pair(m, p, kappa, eta, domain)
+    c, s, t = W.random_data(m, p, kappa, eta, seed=m * 100 + p, nrhs=nrhs)
+    h = gpu_build(pr, c)
+    u = gpu_solve(h, s, t)
+    R = gpu_root_R(h)
+    with O.Tree(opr, c, nthreads=os.cpu_count() or 1) as T:
+        uo = T.solve(s, t, nthreads=os.cpu_count() or 1)
+        Ro = T.root_R()
+    assert _rel(u, uo) < TOL
+    assert _rel(R, Ro) < TOL
+    h.free()
+
+
+def test_polynomial_solution_reproduced():
+    wl = W.polynomial_solution(4, 10, 12.0, 5.0 + 1.0j, domain=(0.0, 2.0, 0.0, 1.0))
+    pr = hps.Problem(4, 10, wl.kappa, wl.eta, 0.0, 2.0, 0.0, 1.0)
+    lxy, bxy = hps.hps_nodes(pr)
+    c, s, t = wl.sample(lxy, bxy)
+    h = gpu_build(pr, c)
+    u = gpu_solve(h, s[None], t[None])[0]
+    assert _rel(u, wl.u_exact(lxy[..., 0], lxy[..., 1])) < 1e-10
+
+
+def test_plane_wave_bump_config():
+    """4 x 4 leaves, p = 16, kappa = eta = 20 (the paper-shaped manufactured
+    plane wave): GPU vs oracle and vs the exact solution."""
+    wl = W.plane_wave_bump()
+    pr, opr = _pair(wl.m, wl.p, wl.kappa, wl.eta)
+    lxy, bxy = hps.hps_nodes(pr)
+    c, s, t = wl.sample(lxy, bxy)
+    h = gpu_build(pr, c)
+    u = gpu_solve(h, s[None], t[None])[0]
+    with O.Tree(opr, c) as T:
+        uo = T.solve(s[None], t[None])[0]
+    assert _rel(u, uo) < TOL
+    assert np.abs(u - wl.u_exact(lxy[..., 0], lxy[..., 1])).max() < 1e-9
+
+
+def test_point_sources_full_size():
+    """16 x 16 leaves, p = 16, kappa = eta = 80, eight Gaussian sources: the
+    full benchmark configuration, compared on every node."""
+    wl = W.point_sources()
+    pr, opr = _pair(wl.m, wl.p, wl.kappa, wl.eta)
+    lxy, bxy = hps.hps_nodes(pr)
+    c, s, t = wl.sample(lxy, bxy)
+    h = gpu_build(pr, c)
+    u = gpu_solve(h, s[None], t[None])[0]
+    R = gpu_root_R(h)
+    nt = os.cpu_count() or 1
+    with O.Tree(opr, c, nthreads=nt) as T:
+        uo = T.solve(s[None], t[None], nthreads=nt)[0]
+        Ro = T.root_R()
+    assert _rel(u, uo) < TOL
+    assert _rel(R, Ro) < TOL
+    h.free()
+
+
+def test_host_and_device_arrays_agree():
+    pr, _ = _pair(4, 8, 10.0, 10.0)
+    c, s, t = W.random_data(4, 8, 10.0, 10.0, seed=77, nrhs=2)
+    h1 = gpu_build(pr, c)                      # device c
+    h2 = hps.hps_build(pr, np.ascontiguousarray(c))  # host c, default stream
+    u_dev = gpu_solve(h1, s, t)
+    u_host = np.zeros((2, pr.leaves, pr.n), complex)
+    hps.hps_solve(h2, np.ascontiguousarray(s), np.ascontiguousarray(t), u_host, 2)
+    assert np.array_equal(u_dev, u_host)
+
+
+def test_repeat_solve_is_bitwise_stable():
+    pr, _ = _pair(4, 8, 10.0, 10.0)
+    c, s, t = W.random_data(4, 8, 10.0, 10.0, seed=5, nrhs=3)
+    h = gpu_build(pr, c)
+    assert np.array_equal(gpu_solve(h, s, t), gpu_solve(h, s, t))
+
+
+def test_empty_and_invalid_solves():
+    pr, _ = _pair(2, 6, 5.0, 5.0)
+    c, s, t = W.random_data(2, 6, 5.0, 5.0, seed=1)
+    h = gpu_build(pr, c)
+    u = np.zeros((1, pr.leaves, pr.n), complex)
+    assert hps.lib().hps_solve(h.ptr, s.ctypes.data, t.ctypes.data, u.ctypes.data, 0, None) == hps.HPS_OK
+    assert np.all(u == 0)
+    assert hps.lib().hps_solve(h.ptr, s.ctypes.data, t.ctypes.data, u.ctypes.data, -1, None) == hps.HPS_EINVAL
+    assert hps.lib().hps_leaf_ops(h.ptr, pr.leaves, None, None, None, None) == hps.HPS_EINVAL
+
+
+def test_solve_is_linear():
+    pr, _ = _pair(4, 10, 12.0, 12.0)
+    c, s, t = W.random_data(4, 10, 12.0, 12.0, seed=8, nrhs=2)
+    h = gpu_build(pr, c)
+    u = gpu_solve(h, s, t)
+    a, b = 0.7 - 0.2j, -1.5 + 0.4j
+    ul = gpu_solve(h, a * s[:1] + b * s[1:], a * t[:1] + b * t[1:])[0]
+    assert _rel(ul, a * u[0] + b * u[1]) < 1e-12
