@@ -1,0 +1,375 @@
+"""Benchmark of the HPS direct solver on one GB300 (or N, as independent replicas).
+
+A step is one pass of the whole hot path: the build (leaf operators, then
+every merge level up to the root) followed by one solve (upward and downward
+sweeps) for one right-hand side, on the 16 x 16-leaf workload (p = 16, q = 14,
+kappa = eta = 80, periodic medium, eight Gaussian point sources, t = 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` = DOF built and solved per second over
+the K timed steps (inputs resident in HBM, L2 flushed between steps), plus
+separate build DOF/s, solve RHS/s and p50/p99 single-RHS solve latency.  The
+`reference` implementation is the plain CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1812_07167_gb300 import workloads as W  # noqa: E402
+
+METRIC = "HPS build DOF/s and solve RHS/s at stated rel. error; p50/p99 solve latency"
+M, P_ORDER, KAPPA = 16, 16, 80.0
+# FP64 peak from unit counts: 152 SMs x 2 FP64 FMA/clk/SM (4 flop) x 2.07 GHz
+# (the 1.25 TFLOP/s nominal of the part)
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+
+def workload():
+    return W.point_sources(m=M, p=P_ORDER, kappa=KAPPA)
+
+
+def config_dict(nrhs=1, l2="flushed between steps (256 MiB write)"):
+    wl = workload()
+    return {
+        "workload": "helmholtz_impedance_point_sources",
+        "leaves": f"{M}x{M}", "p": P_ORDER, "q": P_ORDER - 2, "kappa": KAPPA, "eta": KAPPA,
+        "c": "1+0.3 sin(4 pi x) cos(6 pi y)", "s": "8 Gaussian sources, width 0.01, seed 1", "t": 0,
+        "dof": M * M * (P_ORDER * P_ORDER - 4), "tensor_nodes": M * M * P_ORDER * P_ORDER,
+        "nrhs_per_step": nrhs, "l2": l2, "precision": "complex128",
+        "domain": list(wl.domain),
+    }
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_oracle_step(c, s, t, threads):
+    import oracle as O
+
+    wl = workload()
+    pr = O.Problem(wl.m, wl.p, wl.kappa, wl.eta)
+    t0 = time.perf_counter()
+    T = O.Tree(pr, c, nthreads=threads)
+    u = T.solve(s[None], t[None], nthreads=threads)[0]
+    dt = time.perf_counter() - t0
+    R = T.root_R()
+    T.close()
+    return dt, u, R
+
+
+def reference_arm(args, rank, world):
+    """The plain CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle as O
+
+    wl = workload()
+    pr = O.Problem(wl.m, wl.p, wl.kappa, wl.eta)
+    lxy, bxy = O.nodes(pr)
+    c, s, t = wl.sample(lxy, bxy)
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        run_oracle_step(c, s, t, threads)
+    times = [run_oracle_step(c, s, t, threads)[0] for _ in range(args.steps)]
+    dof = pr.leaves * pr.n
+    total = sum(times)
+    value = dof * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(l2="n/a (CPU)"),
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": threads, "kind": "oracle",
+                         "sample": "full 16x16-leaf build + 1-RHS solve per step"},
+        "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1812_07167_gb300 import hps
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+    st = torch.cuda.current_stream()
+    wl = workload()
+    pr = hps.Problem(wl.m, wl.p, wl.kappa, wl.eta)
+    lxy, bxy = hps.hps_nodes(pr)
+    c, s, t = wl.sample(lxy, bxy)
+    cd = torch.from_numpy(c).to(dev)
+    sd = torch.from_numpy(np.ascontiguousarray(s[None])).to(dev)
+    td = torch.from_numpy(np.ascontiguousarray(t[None])).to(dev)
+    ud = torch.empty((1, pr.leaves, pr.n), dtype=torch.complex128, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def step():
+        h = hps.hps_build(pr, cd, st)
+        hps.hps_solve(h, sd, td, ud, 1, st)
+        return h
+
+    for _ in range(max(args.warmup, 3)):
+        h = step()
+        torch.cuda.synchronize()
+        code, lev, box = hps.hps_status(h, st)
+        if code != hps.HPS_OK:
+            raise RuntimeError(f"build reported {hps.hps_strerror(code)} at level {lev} box {box}")
+        h.free()
+    info = h.info() if h.ptr else None
+    h0 = step()
+    torch.cuda.synchronize()
+    info = h0.info()
+    h0.free()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    leaf_ms = []
+    handles = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(st)
+            h = step()
+            ev[k][1].record(st)
+            handles.append(h)
+            if len(handles) > 1:  # free the previous step's operators outside the timed pair
+                torch.cuda.synchronize()
+                leaf_ms.append(hps.hps_build_times(handles[0])[0])
+                handles.pop(0).free()
+        torch.cuda.synchronize()
+        t_wall1 = time.perf_counter()
+    for hh in handles:
+        leaf_ms.append(hps.hps_build_times(hh)[0])
+        hh.free()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    dof = pr.leaves * pr.n
+    value = world * dof * args.steps / (total_ms / 1e3)
+
+    # ---- separate build / solve figures (device-resident inputs) ----
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    build_ms = []
+    for _ in range(5):
+        flush.zero_()
+        e0.record(st)
+        h = hps.hps_build(pr, cd, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        build_ms.append(e0.elapsed_time(e1))
+        h.free()
+    h = hps.hps_build(pr, cd, st)
+    lat = []
+    for k in range(220):
+        e0.record(st)
+        hps.hps_solve(h, sd, td, ud, 1, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if k >= 20:
+            lat.append(e0.elapsed_time(e1))
+    nb = 64
+    S = sd.repeat(nb, 1, 1).contiguous()
+    T = td.repeat(nb, 1).contiguous()
+    U = torch.empty((nb, pr.leaves, pr.n), dtype=torch.complex128, device=dev)
+    for _ in range(2):
+        hps.hps_solve(h, S, T, U, nb, st)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(5):
+        hps.hps_solve(h, S, T, U, nb, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / 5
+    u_gpu = ud.cpu().numpy()[0]
+    R_gpu = np.zeros((pr.nbdry, pr.nbdry), complex)
+    hps.hps_root_R(h, R_gpu, st)
+    h.free()
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    cp = torch.from_numpy(c).pin_memory()
+    sp = torch.from_numpy(np.ascontiguousarray(s[None])).pin_memory()
+    tp = torch.from_numpy(np.ascontiguousarray(t[None])).pin_memory()
+    upin = torch.empty((1, pr.leaves, pr.n), dtype=torch.complex128).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hh = hps.hps_build(pr, cp.numpy(), st)
+        hps.hps_solve(hh, sp.numpy(), tp.numpy(), upin.numpy(), 1, st)  # returns once u is on the host
+        t1 = time.perf_counter()
+        hh.free()
+        if k >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e_total = sum(e2e_ms)
+    if dist:
+        tt = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+    e2e_value = world * dof * len(e2e_ms) / (e2e_total / 1e3)
+
+    if rank != 0:
+        return
+    leaf_flops = pr.leaves * 8 * (pr.n ** 3 + pr.nb * pr.n * pr.p)
+    leaf_avg = statistics.mean(leaf_ms)
+    achieved = leaf_flops / (leaf_avg / 1e3) / 1e12
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "leaf_kernel_traffic.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as f:
+            tr = json.load(f)
+        if tr.get("kernel_hash") == kernel_hash():
+            traffic = tr.get("bytes_per_launch")
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded point sources; no dataset)", "config": config_dict(),
+        "build_dof_per_s": dof / (statistics.median(build_ms) / 1e3),
+        "build_ms_median": statistics.median(build_ms),
+        "solve_rhs_per_s": nb / (batch_ms / 1e3), "solve_nrhs_batch": nb,
+        "solve_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                             "nrhs": 1, "samples": len(lat)},
+        "operator_bytes": info.operator_bytes, "build_flops": info.build_flops,
+        "roofline": {"kernel": "leaf_kernel", "bound": "alu", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": traffic, "leaf_ms": leaf_avg,
+                     "peak_source": "FP64 unit count x max SM clock (152 SM x 4 flop/clk x 2.07 GHz)"},
+        "e2e": {"value": e2e_value, "unit": "DOF/s",
+                "h2d_bytes_per_step": int(c.nbytes + s.nbytes + t.nbytes),
+                "d2h_bytes_per_step": int(u_gpu.nbytes)},
+        "gpu_launches": args.steps * (info.build_launches + info.solve_launches),
+        "clocks": clk.summary(),
+        "wall_s_timed_region": t_wall1 - t_wall0,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        dt, u_ora, R_ora = run_oracle_step(c, s, t, threads)
+        line["cpu_baseline"] = {"value": dof / dt, "unit": "DOF/s", "cores": threads, "kind": "oracle",
+                                "sample": "one full 16x16-leaf build + 1-RHS solve"}
+        line["rel_err_vs_oracle"] = {
+            "u": float(np.abs(u_gpu - u_ora).max() / np.abs(u_ora).max()),
+            "root_R": float(np.linalg.norm(R_gpu - R_ora) / np.linalg.norm(R_ora)),
+        }
+    print(json.dumps(line), flush=True)
+
+
+def kernel_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1812_07167_gb300", "csrc", "gj.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    try:
+        ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

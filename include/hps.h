@@ -90,6 +90,8 @@ typedef struct {
   long long build_flops;    /* real floating-point operations of one build */
   long long solve_flops;    /* real floating-point operations of one solve, per RHS */
   long long solve_bytes;    /* operator bytes one solve reads */
+  int build_launches;       /* kernels one hps_build launches */
+  int solve_launches;       /* kernels one hps_solve launches */
 } hps_info_t;
 
 /* Node coordinates (host helper, no device work; Sec. 2.1 grid).
@@ -134,6 +136,13 @@ int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, v
 
 /* Sizes and operation counts of a built handle (host only, no device work). */
 int hps_info(const hps_handle *h, hps_info_t *info);
+
+/* Device time of the phases of the handle's build, from CUDA events the
+ * build recorded on its stream: ms[0] = the leaf kernel (Sec. 2.1), ms[1+j] =
+ * merge level j counted from the leaves up (Sec. 2.2).  Writes at most cap
+ * values and returns how many phases there are (1 + levels), or a negative
+ * HPS_* code.  Waits for the build to finish. */
+int hps_build_times(hps_handle *h, double *ms, int cap);
 
 /* Wait for the handle's work on `stream` and report device-side failures:
  * HPS_ESINGULAR with *level / *box (may be NULL) set to the tree level

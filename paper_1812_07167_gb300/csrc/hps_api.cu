@@ -82,6 +82,8 @@ struct hps_handle {
   // staging for host arrays
   void *stage = nullptr;
   size_t stage_bytes = 0;
+  // phase events of the build: [before leaf, after leaf, after merge 0, ...]
+  std::vector<cudaEvent_t> ev;
 };
 
 namespace {
@@ -322,6 +324,8 @@ void fill_info(const Plan &pl, hps_info_t &in) {
   in.solve_flops = sf;
   in.operator_bytes = ob;
   in.solve_bytes = sb;
+  in.build_launches = pl.lv.empty() ? 2 : 1 + 7 * (int)pl.lv.size();
+  in.solve_launches = 3 + 6 * (int)pl.lv.size();
 }
 
 int choose_gj_cs(int n, int batch) {
@@ -402,6 +406,7 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy) {
 
 int hps_free(hps_handle *h) {
   if (!h) return HPS_OK;
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->arena) cudaFree(h->arena);
   if (h->ws) cudaFree(h->ws);
   if (h->stage) cudaFree(h->stage);
@@ -540,7 +545,11 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
   lt.ni = ni;
   lt.eta = make_double2(h->desc.eta_re, h->desc.eta_im);
   lt.kappa2 = h->desc.kappa * h->desc.kappa;
+  h->ev.assign(pl.lv.size() + 2, nullptr);
+  for (cudaEvent_t &e : h->ev) CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(h->ev[0], st));
   CK(hps::launch_leaf(lt, h->tables, c_dev, nl, h->X, h->GX, h->d_status, pl.L, h->leaf_cs, st));
+  CK(cudaEventRecord(h->ev[1], st));
   if (c_stage) CK(cudaFreeAsync(c_stage, st));
 
   if (pl.lv.empty()) {
@@ -628,6 +637,7 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
     g2[1].D = g2[1].C;
     g2[1].beta = make_double2(1.0, 0.0);
     CK(hps::launch_gemm(g2, 2, st));
+    CK(cudaEventRecord(h->ev[2 + j], st));
     Rc = Rp;
     ldc = nt;
     strc = sp;
@@ -668,6 +678,20 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
   }
   *out = h;
   return HPS_OK;
+}
+
+int hps_build_times(hps_handle *h, double *ms, int cap) {
+  if (!h || (!ms && cap > 0) || cap < 0) return -HPS_EINVAL;
+  const int nph = (int)h->plan.lv.size() + 1;
+  if (h->ev.size() < 2) return -HPS_EINVAL;
+  if (cudaEventSynchronize(h->ev.back()) != cudaSuccess) return -HPS_ECUDA;
+  for (int q = 0; q < nph && q < cap; q++) {
+    float t = 0.0f;
+    if (q + 1 >= (int)h->ev.size() || cudaEventElapsedTime(&t, h->ev[q], h->ev[q + 1]) != cudaSuccess)
+      return -HPS_ECUDA;
+    ms[q] = t;
+  }
+  return nph;
 }
 
 int hps_status(hps_handle *h, void *stream, int *level, int *box) {

@@ -25,7 +25,7 @@ HPS_FP64 = 0
 
 # every entry point include/hps.h declares
 EXPORTS = ("hps_nodes", "hps_build", "hps_solve", "hps_root_R", "hps_leaf_ops", "hps_info",
-           "hps_status", "hps_free", "hps_strerror")
+           "hps_build_times", "hps_status", "hps_free", "hps_strerror")
 
 
 class hps_desc(ctypes.Structure):
@@ -47,6 +47,7 @@ class hps_info_t(ctypes.Structure):
         ("dof", ctypes.c_longlong), ("operator_bytes", ctypes.c_longlong),
         ("build_flops", ctypes.c_longlong), ("solve_flops", ctypes.c_longlong),
         ("solve_bytes", ctypes.c_longlong),
+        ("build_launches", ctypes.c_int), ("solve_launches", ctypes.c_int),
     ]
 
 
@@ -75,6 +76,7 @@ def lib():
         L.hps_root_R.argtypes = [P, P, P]
         L.hps_leaf_ops.argtypes = [P, ctypes.c_int, P, P, P, P]
         L.hps_info.argtypes = [P, ctypes.POINTER(hps_info_t)]
+        L.hps_build_times.argtypes = [P, P, ctypes.c_int]
         L.hps_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.hps_free.argtypes = [P]
         L.hps_strerror.argtypes = [ctypes.c_int]
@@ -209,6 +211,15 @@ def hps_leaf_ops(h: Handle, leaf: int, Psi=None, Y=None, Gam=None, stream=None):
     _check(lib().hps_leaf_ops(h.ptr, int(leaf), _ptr(Psi), _ptr(Y), _ptr(Gam), _stream(stream)),
            "hps_leaf_ops")
     return Psi, Y, Gam
+
+
+def hps_build_times(h: Handle):
+    """Device milliseconds of [leaf kernel, merge level 0, 1, ...] of the build."""
+    out = np.zeros(64)
+    n = lib().hps_build_times(h.ptr, _ptr(out), len(out))
+    if n < 0:
+        raise HPSError(-n, "hps_build_times")
+    return out[:n].copy()
 
 
 def hps_status(h: Handle, stream=None):
