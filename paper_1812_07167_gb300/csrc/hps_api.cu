@@ -24,7 +24,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/hps.h"
+#include "hps.h"
 #include "hps_internal.h"
 
 using hps::CopyBatch;
@@ -329,11 +329,13 @@ void fill_info(const Plan &pl, hps_info_t &in) {
 }
 
 int choose_gj_cs(int n, int batch) {
-  // smallest cluster whose shared memory fits, then wider while the level
-  // has too few matrices to fill the chip
+  // smallest cluster whose shared memory fits two CTAs per SM, then wider
+  // while the level has too few matrices to fill the chip and every CTA
+  // keeps at least two panels
   int cs = 1;
-  while (cs < hps::gj_max_cluster() && hps::gj_smem_bytes(n, cs, false, 0) > 200 * 1024) cs *= 2;
-  while (cs < hps::gj_max_cluster() && (long long)batch * cs < 152 && n / (2 * cs) >= 8) cs *= 2;
+  while (cs < hps::gj_max_cluster() && hps::gj_smem_bytes(n, cs, false, 0) > 110 * 1024) cs *= 2;
+  while (cs < hps::gj_max_cluster() && (long long)batch * cs < 304 && hps::gj_slab(n, 2 * cs) >= 16)
+    cs *= 2;
   return cs;
 }
 
@@ -545,11 +547,23 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
   lt.ni = ni;
   lt.eta = make_double2(h->desc.eta_re, h->desc.eta_im);
   lt.kappa2 = h->desc.kappa * h->desc.kappa;
+  // scratch for the in-place elimination: leaves go in chunks of at most
+  // ~1 GiB of matrices
+  const int chunk = (int)std::max<long long>(
+      1, std::min<long long>(nl, (1LL << 30) / (16LL * n * n)));
+  double2 *lscr = nullptr;
+  int *lmeta = nullptr;
+  CK(cudaMallocAsync((void **)&lscr, sizeof(double2) * (size_t)chunk * n * n, st));
+  CK(cudaMallocAsync((void **)&lmeta, sizeof(int) * (size_t)chunk * hps::gj_meta_ints(n), st));
   h->ev.assign(pl.lv.size() + 2, nullptr);
   for (cudaEvent_t &e : h->ev) CK(cudaEventCreate(&e));
   CK(cudaEventRecord(h->ev[0], st));
-  CK(hps::launch_leaf(lt, h->tables, c_dev, nl, h->X, h->GX, h->d_status, pl.L, h->leaf_cs, st));
+  for (int l0 = 0; l0 < nl; l0 += chunk)
+    CK(hps::launch_leaf(lt, h->tables, c_dev, l0, std::min(chunk, nl - l0), h->X, h->GX, lscr, lmeta,
+                        h->d_status, pl.L, h->leaf_cs, st));
   CK(cudaEventRecord(h->ev[1], st));
+  CK(cudaFreeAsync(lscr, st));
+  CK(cudaFreeAsync(lmeta, st));
   if (c_stage) CK(cudaFreeAsync(c_stage, st));
 
   if (pl.lv.empty()) {
@@ -562,15 +576,20 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
   }
 
   // ---- merges (Sec. 2.2), one level at a time (Algorithm 3's level loop) ----
-  size_t rbuf = 0, qbuf = 0;
+  size_t rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0;
   for (const Level &L : pl.lv) {
     rbuf = std::max(rbuf, (size_t)L.P * L.nt * L.nt);
     qbuf = std::max(qbuf, (size_t)L.P * L.n3 * L.nt);
+    wbuf = std::max(wbuf, (size_t)L.P * L.n3 * L.n3);
+    mbuf = std::max(mbuf, (size_t)L.P * hps::gj_meta_ints(L.n3));
   }
   double2 *scratch = nullptr;
-  CK(cudaMallocAsync((void **)&scratch, sizeof(double2) * (2 * rbuf + qbuf), st));
+  int *wmeta = nullptr;
+  CK(cudaMallocAsync((void **)&scratch, sizeof(double2) * (2 * rbuf + qbuf + wbuf), st));
+  CK(cudaMallocAsync((void **)&wmeta, sizeof(int) * mbuf, st));
   double2 *Rbuf[2] = {scratch, scratch + rbuf};
   double2 *Q = scratch + 2 * rbuf;
+  double2 *Wscr = Q + qbuf;
 
   // child R of the first merge: the leaves' R = GX[:, :nb] (ld nb, stride n nb)
   const double2 *Rc = h->GX;
@@ -609,12 +628,12 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
     CK(hps::launch_copy(cb, st));
 
     const long long s33 = (long long)n3 * n3, s3t = (long long)n3 * nt;
-    // W = I - R33b R33a (into the W^{-1} slot), then invert in place
-    GemmDesc g = gemm(n3, n3, n3, P, mat(L.R33b, n3, s33), mat(L.R33a, n3, s33), mat(L.Winv, n3, s33));
+    // W = I - R33b R33a (in scratch), then W^{-1} into its stored slot
+    GemmDesc g = gemm(n3, n3, n3, P, mat(L.R33b, n3, s33), mat(L.R33a, n3, s33), mat(Wscr, n3, s33));
     g.alpha = make_double2(-1.0, 0.0);
     g.addI = 1;
     CK(hps::launch_gemm(&g, 1, st));
-    CK(hps::launch_gj_inverse(L.Winv, n3, P, h->d_status, L.lev, L.gj_cs, st));
+    CK(hps::launch_gj_inverse(Wscr, L.Winv, n3, P, wmeta, h->d_status, L.lev, L.gj_cs, st));
     // Q(:, :n1) = R33b R31a
     g = gemm(n3, n1, n3, P, mat(L.R33b, n3, s33), sub(Ra, L.d_I3a, L.d_I1), mat(Q, n3, s3t));
     CK(hps::launch_gemm(&g, 1, st));
@@ -643,6 +662,7 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
     strc = sp;
   }
   CK(cudaFreeAsync(scratch, st));
+  CK(cudaFreeAsync(wmeta, st));
   return HPS_OK;
 }
 
@@ -656,13 +676,14 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
   if (h->desc.q == 0) h->desc.q = desc->p - 2;
   make_plan(h->desc, h->plan);
   fill_info(h->plan, h->info);
-  // leaf cluster: the smallest power of two whose shared memory fits
+  // leaf cluster: wider clusters split each leaf finer, which balances the
+  // chip when there are few leaves (measured best: 8 CTAs a leaf for 16
+  // leaves, 4 for 256, 1 from 1024 leaves on)
   int cs = 1;
-  while (cs < hps::gj_max_cluster() && hps::gj_smem_bytes(h->plan.n, cs, true, h->plan.p) > 200 * 1024)
-    cs *= 2;
+  while (cs < 8 && (long long)h->plan.leaves * cs < 1024) cs *= 2;
   if (const char *e = getenv("HPS_LEAF_CLUSTER")) {
     int v = atoi(e);
-    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) cs = std::max(cs, v);
+    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) cs = v;
   }
   h->leaf_cs = cs;
   for (Level &L : h->plan.lv) L.gj_cs = choose_gj_cs(L.n3, L.P);

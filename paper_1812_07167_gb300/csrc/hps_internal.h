@@ -62,24 +62,28 @@ struct DevStatus {
 cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st);
 cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st);
 
-// Leaf step (Sec. 2.1): assemble B for every leaf, invert it in place by
-// Gauss-Jordan with partial pivoting across a cluster of `cs` CTAs, write
-// X = B^{-1} = [Psi | Y] ([leaf][n][n] column-major) and GX = G X
-// ([leaf][n][nb] column-major: R = GX[:, :nb], Gamma = GX[:, nb:]).
+// Leaf step (Sec. 2.1) for leaves [leaf0, leaf0 + count): assemble B, invert
+// it by blocked Gauss-Jordan with partial pivoting across a cluster of `cs`
+// CTAs, write X = B^{-1} = [Psi | Y] ([leaf][n][n] column-major) and
+// GX = G X ([leaf][n][nb] column-major: R = GX[:, :nb], Gamma = GX[:, nb:]).
 //   tab_dev: device tables: double D1x[p*p], D1y[p*p], D2x[p*p], D2y[p*p]
-//            (row-major, scaled to the leaf), int2 grid[n] (ix, iy per node)
-cudaError_t launch_leaf(const LeafTables &lt, const void *tab_dev, const double *c, int leaves,
-                        double2 *X, double2 *GX, unsigned int *status, int level, int cs,
-                        cudaStream_t st);
+//            (row-major, scaled to the leaf), then int grid[n] (ix | iy << 8)
+//   S, meta: scratch for `count` matrices: count * n * n complex and
+//            count * gj_meta_ints(n) ints
+cudaError_t launch_leaf(const LeafTables &lt, const void *tab_dev, const double *c, int leaf0,
+                        int count, double2 *X, double2 *GX, double2 *S, int *meta,
+                        unsigned int *status, int level, int cs, cudaStream_t st);
 
-// In-place inverse of `batch` n x n column-major matrices (leading dim n,
-// batch stride n*n) by Gauss-Jordan with partial pivoting across clusters of
-// `cs` CTAs.
-cudaError_t launch_gj_inverse(double2 *A, int n, int batch, unsigned int *status, int level,
-                              int cs, cudaStream_t st);
+// Inverse of `batch` n x n column-major matrices (leading dim n, batch stride
+// n*n) by blocked Gauss-Jordan with partial pivoting across clusters of `cs`
+// CTAs.  S holds the matrices and is destroyed; the inverses go to out.
+cudaError_t launch_gj_inverse(double2 *S, double2 *out, int n, int batch, int *meta,
+                              unsigned int *status, int level, int cs, cudaStream_t st);
 
-// Largest cluster size the GJ kernels accept and shared memory they need.
+// Cluster limits and scratch / shared-memory sizes of the Gauss-Jordan kernels.
 int gj_max_cluster();
+int gj_slab(int n, int cs);
 size_t gj_smem_bytes(int n, int cs, bool leaf, int p);
+size_t gj_meta_ints(int n);
 
 }  // namespace hps
