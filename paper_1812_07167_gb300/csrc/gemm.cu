@@ -9,6 +9,8 @@
 //
 // The path is complex FP64 (DFMA-bound on this part: the tile sizes only
 // need enough reuse to keep shared-memory traffic well below the DFMA rate).
+#include <algorithm>
+
 #include "hps_internal.h"
 
 namespace hps {
@@ -137,6 +139,82 @@ __global__ void __launch_bounds__(256) copy_kernel(const __grid_constant__ CopyB
   }
 }
 
+// Skinny products (N <= NN: the solve's right-hand sides).  A CTA computes 32
+// rows of one batch entry; its 8 warps split K (warp w takes k = w, w+8, ...),
+// each lane one row, so the 32 loads of A a warp issues are one coalesced
+// column segment and B(k, :) is a broadcast.  The 8 partial sums meet in
+// shared memory.  Enough CTAs exist even for one large matrix.
+template <int NN>
+__global__ void __launch_bounds__(256) gemv_kernel(const __grid_constant__ GemmPack pack) {
+  __shared__ double2 red[8][NN][33];
+  const GemmDesc &g = pack.d[blockIdx.z];
+  const int rblocks = (g.M + 31) / 32;
+  if ((long long)blockIdx.x >= (long long)rblocks * g.batch) return;
+  const int b = blockIdx.x / rblocks;
+  const int i = (blockIdx.x % rblocks) * 32 + (threadIdx.x & 31);
+  const int w = threadIdx.x >> 5;
+  const bool live = i < g.M;
+  double2 acc[NN];
+#pragma unroll
+  for (int j = 0; j < NN; j++) acc[j] = make_double2(0.0, 0.0);
+  if (live) {
+    const long long arow = (long long)b * g.A.stride + (g.A.rmap ? (long long)__ldg(g.A.rmap + i) : i);
+#pragma unroll 4
+    for (int k = w; k < g.K; k += 8) {
+      const long long c = g.A.cmap ? (long long)__ldg(g.A.cmap + k) : k;
+      const double2 a = ld2(g.A.ptr + arow + c * g.A.ld);
+      const bool second = (g.B2.ptr != nullptr && k >= g.ksplit);
+      const double2 *bp = second ? g.B2.ptr : g.B.ptr;
+      const int *brm = second ? g.B2.rmap : g.B.rmap;
+      const int *bcm = second ? g.B2.cmap : g.B.cmap;
+      const long long bld = second ? g.B2.ld : g.B.ld;
+      const long long bst = second ? g.B2.stride : g.B.stride;
+      const int kk = second ? k - g.ksplit : k;
+      const long long brow = (long long)b * bst + (brm ? (long long)__ldg(brm + kk) : kk);
+#pragma unroll
+      for (int j = 0; j < NN; j++)
+        if (j < g.N) {
+          const long long cj = bcm ? (long long)__ldg(bcm + j) : j;
+          cmac(acc[j], a, ld2(bp + brow + cj * bld));
+        }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NN; j++) red[w][j][threadIdx.x & 31] = acc[j];
+  __syncthreads();
+  if (w == 0 && live) {
+    const int l = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < NN; j++) {
+      if (j >= g.N) continue;
+      double2 v = red[0][j][l];
+#pragma unroll
+      for (int q = 1; q < 8; q++) {
+        v.x += red[q][j][l].x;
+        v.y += red[q][j][l].y;
+      }
+      v = cmul(g.alpha, v);
+      if (g.D.ptr) {
+        double2 t = cmul(g.beta, g.D.ptr[mat_off(g.D, b, i, j)]);
+        v.x += t.x;
+        v.y += t.y;
+      }
+      if (g.addI && i == j) v.x += 1.0;
+      const_cast<double2 *>(g.C.ptr)[mat_off(g.C, b, i, j)] = v;
+    }
+  }
+}
+
+template <int BM, int BN, int BK, int TM, int TN>
+long long cfg_ctas(const GemmPack &pk) {
+  long long ctas = 0;
+  for (int q = 0; q < pk.n; q++) {
+    const GemmDesc &g = pk.d[q];
+    ctas += (long long)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * g.batch;
+  }
+  return ctas;
+}
+
 template <int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_cfg(const GemmPack &pk, cudaStream_t st) {
   int maxtiles = 0, maxbatch = 0;
@@ -149,6 +227,17 @@ cudaError_t launch_cfg(const GemmPack &pk, cudaStream_t st) {
   if (maxtiles == 0 || maxbatch == 0) return cudaSuccess;
   dim3 grid(maxtiles, maxbatch < 65535 ? maxbatch : 65535, pk.n);
   gemm_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(pk);
+  return cudaGetLastError();
+}
+
+template <int NN>
+cudaError_t launch_gemv(const GemmPack &pk, cudaStream_t st) {
+  long long blocks = 0;
+  for (int q = 0; q < pk.n; q++)
+    blocks = std::max(blocks, (long long)((pk.d[q].M + 31) / 32) * pk.d[q].batch);
+  if (blocks == 0) return cudaSuccess;
+  dim3 grid((unsigned)blocks, 1, pk.n);
+  gemv_kernel<NN><<<grid, 256, 0, st>>>(pk);
   return cudaGetLastError();
 }
 
@@ -167,9 +256,16 @@ cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st) {
   }
   if (pk.n == 0) return cudaSuccess;
   // K == 0 is legal (C = beta D); the k-loop simply does not run.
-  if (maxN >= 32) return launch_cfg<64, 64, 16, 4, 4>(pk, st);
-  if (maxN >= 2) return launch_cfg<128, 16, 16, 4, 2>(pk, st);
-  return launch_cfg<128, 1, 16, 1, 1>(pk, st);
+  if (maxN <= 1) return launch_gemv<1>(pk, st);
+  if (maxN <= 2) return launch_gemv<2>(pk, st);
+  if (maxN <= 4) return launch_gemv<4>(pk, st);
+  if (maxN <= 8) return launch_gemv<8>(pk, st);
+  if (maxN < 32) return launch_cfg<64, 16, 16, 2, 2>(pk, st);
+  // FP64-bound tiles: the largest tile that still gives every SM two CTAs
+  const long long want = 2 * 152;
+  if (cfg_ctas<64, 64, 16, 4, 4>(pk) >= want) return launch_cfg<64, 64, 16, 4, 4>(pk, st);
+  if (cfg_ctas<32, 32, 16, 2, 2>(pk) >= want) return launch_cfg<32, 32, 16, 2, 2>(pk, st);
+  return launch_cfg<16, 16, 16, 1, 1>(pk, st);
 }
 
 cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st) {
