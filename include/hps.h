@@ -61,7 +61,8 @@ enum {
   HPS_ESINGULAR = 3, /* a leaf matrix B or an interface matrix W had a zero pivot */
   HPS_ETIMEOUT = 4,  /* a bounded device wait gave up */
   HPS_ECUDA = 5,     /* a CUDA runtime call failed (no device, launch error, ...) */
-  HPS_ENOTSUP = 6    /* a valid request this build does not implement */
+  HPS_ENOTSUP = 6,   /* a valid request this build does not implement */
+  HPS_ETOOBIG = 7    /* the request needs more than the fixed no-allocation workspace */
 };
 
 enum { HPS_FP64 = 0 };
@@ -119,6 +120,33 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
  * nrhs == 0 does nothing and returns HPS_OK.  Returns HPS_EINVAL (NULL
  * handle or array, nrhs < 0), HPS_ENOMEM (workspace), HPS_ECUDA. */
 int hps_solve(hps_handle *h, const double *s, const double *t, double *u, int nrhs, void *stream);
+
+/* Size of the fixed device workspace behind hps_solve_noalloc (16 MiB).  It
+ * is part of the library's device image, so every GPU that loads the library
+ * holds it until the process exits. */
+#define HPS_NOALLOC_WORKSPACE_BYTES (16u << 20)
+
+/* The same solve as hps_solve, for callers that cannot allocate device
+ * memory at solve time: code whose device memory is already handed out to a
+ * pool or framework allocator up front, and latency-bound request loops where
+ * a cudaMalloc (which may synchronize the device, and may fail at run time)
+ * is not acceptable.  It allocates nothing: the solve's scratch vectors live
+ * in a fixed file-scope device array of HPS_NOALLOC_WORKSPACE_BYTES.
+ * The paper has no counterpart; this is a deployment variant of Algorithm 2.
+ *   s, t, u: as for hps_solve, but all three must be device memory (host
+ *            arrays would need staging buffers): HPS_EINVAL otherwise.
+ * Returns HPS_ETOOBIG when nrhs right-hand sides of this handle's tree need
+ * more workspace than the array holds (about 1.8 MB per right-hand side for
+ * 16 x 16 leaves with p = 16), HPS_EINVAL for bad arguments, HPS_ECUDA if the
+ * workspace address cannot be obtained.  nrhs == 0 returns HPS_OK.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (different streams, or different handles, without ordering between
+ * them) race on it and must be serialized by the caller.  Nothing in the
+ * array needs to start at zero; each call overwrites what it reads. */
+int hps_solve_noalloc(hps_handle *h, const double *s, const double *t, double *u, int nrhs,
+                      void *stream);
 
 /* The root ItI operator R (Definition of the ItI map; R f = g on the outer
  * boundary) in the outer-boundary order above.

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -351,6 +352,158 @@ int grow(void **buf, size_t *have, size_t need) {
 
 }  // namespace
 
+// Solve workspace layout: h per level, t per level, t~3a / t~3b per merge,
+// one temporary.  Returns the bytes needed for nrhs right-hand sides.
+struct SolveWs {
+  static constexpr int kMax = 24;  // merge levels: 2 log2(1024) = 20 at most
+  size_t oh[kMax + 1], ot[kMax + 1], ota[kMax], otb[kMax];
+  size_t ov = 0, bytes = 0;
+};
+
+static void solve_ws_layout(const Plan &pl, int R, SolveWs &w) {
+  size_t off = 0;
+  auto take = [&](long long count) {
+    size_t o = off;
+    off = align256(off + sizeof(double2) * (size_t)count);
+    return o;
+  };
+  w.oh[0] = take((long long)R * pl.leaves * pl.nb);
+  w.ot[0] = take((long long)R * pl.leaves * pl.nb);
+  long long vmax = 1;
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    const Level &L = pl.lv[j];
+    w.oh[j + 1] = take((long long)R * L.P * L.nt);
+    w.ot[j + 1] = take((long long)R * L.P * L.nt);
+    w.ota[j] = take((long long)R * L.P * L.n3);
+    w.otb[j] = take((long long)R * L.P * L.n3);
+    vmax = std::max(vmax, (long long)R * L.P * L.n3);
+  }
+  w.ov = take(vmax);
+  w.bytes = off;
+}
+
+// Algorithm 2 for R right-hand sides on device arrays s, t, u, with the
+// workspace at wb (laid out by solve_ws_layout).  Launches kernels only.
+static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, double2 *u, int R,
+                        char *wb, const SolveWs &ws, cudaStream_t st) {
+  const Plan &pl = h->plan;
+  const int n = pl.n, nb = pl.nb, ni = pl.ni, nl = pl.leaves;
+  const size_t *oh = ws.oh, *ot = ws.ot, *ota = ws.ota, *otb = ws.otb;
+  const size_t ov = ws.ov;
+  auto W = [&](size_t o) { return (double2 *)(wb + o); };
+
+  // ---- upward pass ----
+  // leaves: h = Gamma s  (Gamma = GX[:, nb:])
+  GemmDesc g = gemm(nb, R, ni, nl, mat(h->GX + (size_t)nb * nb, nb, (long long)n * nb),
+                    mat(s, (long long)nl * ni, ni), mat(W(oh[0]), (long long)nl * nb, nb));
+  CK(hps::launch_gemm(&g, 1, st));
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    const Level &L = pl.lv[j];
+    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc;
+    const double2 *hc = W(oh[j]);
+    const long long ldh = (long long)2 * P * nc;
+    Mat hA = mat(hc, ldh, 2LL * nc), hB = mat(hc + nc, ldh, 2LL * nc);
+    Mat h3a = hA, h3b = hB, h1a = hA, h2b = hB;
+    h3a.rmap = L.d_I3a;
+    h3b.rmap = L.d_I3b;
+    h1a.rmap = L.d_I1;
+    h2b.rmap = L.d_I2;
+    const long long s33 = (long long)n3 * n3, ldv = (long long)P * n3;
+    double2 *v = W(ov), *ta = W(ota[j]), *tb = W(otb[j]);
+    // v = R33b h3a - h3b ;  t~3a = W^{-1} v  (Upsilon_a [h3a; h3b])
+    g = gemm(n3, R, n3, P, mat(L.R33b, n3, s33), h3a, mat(v, ldv, n3));
+    g.D = h3b;
+    g.beta = make_double2(-1.0, 0.0);
+    CK(hps::launch_gemm(&g, 1, st));
+    g = gemm(n3, R, n3, P, mat(L.Winv, n3, s33), mat(v, ldv, n3), mat(ta, ldv, n3));
+    CK(hps::launch_gemm(&g, 1, st));
+    // t~3b = -h3a - R33a t~3a  (Upsilon_b [h3a; h3b])
+    g = gemm(n3, R, n3, P, mat(L.R33a, n3, s33), mat(ta, ldv, n3), mat(tb, ldv, n3));
+    g.alpha = make_double2(-1.0, 0.0);
+    g.D = h3a;
+    g.beta = make_double2(-1.0, 0.0);
+    CK(hps::launch_gemm(&g, 1, st));
+    // h^tau = [h1a + R13a t~3a ; h2b + R23b t~3b]  (Eq. flux_part)
+    const long long ldp = (long long)P * nt;
+    GemmDesc g2[2];
+    g2[0] = gemm(n1, R, n3, P, mat(L.R13a, n1, (long long)n1 * n3), mat(ta, ldv, n3), mat(W(oh[j + 1]), ldp, nt));
+    g2[0].D = h1a;
+    g2[0].beta = make_double2(1.0, 0.0);
+    g2[1] = gemm(n2, R, n3, P, mat(L.R23b, n2, (long long)n2 * n3), mat(tb, ldv, n3),
+                 mat(W(oh[j + 1]) + n1, ldp, nt));
+    g2[1].D = h2b;
+    g2[1].beta = make_double2(1.0, 0.0);
+    CK(hps::launch_gemm(g2, 2, st));
+  }
+
+  // ---- downward pass ----
+  const size_t top = pl.lv.size();
+  const int ntop = top ? pl.lv.back().nt : nb;
+  {
+    // root incoming data: public [S, E, N, W] order -> the root's [I1, I2] order
+    CopyBatch cb;
+    cb.count = 1;
+    cb.d[0] = copy(ntop, R, 1, mat(t, pl.nbdry, 0, h->d_root_src), mat(W(ot[top]), ntop, 0));
+    CK(hps::launch_copy(cb, st));
+  }
+  for (size_t jj = top; jj-- > 0;) {
+    const Level &L = pl.lv[jj];
+    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc;
+    const double2 *tp = W(ot[jj + 1]);
+    double2 *tc = W(ot[jj]);
+    const long long ldp = (long long)P * nt, ldc2 = (long long)2 * P * nc, ldv = (long long)P * n3;
+    const long long s3t = (long long)n3 * nt;
+    // t3a = Phi_a t^tau + t~3a -> alpha rows I3 ; t3b = Phi_b t^tau + t~3b -> beta rows I3
+    GemmDesc g2[2];
+    g2[0] = gemm(n3, R, nt, P, mat(L.Phia, n3, s3t), mat(tp, ldp, nt), mat(tc, ldc2, 2LL * nc, L.d_I3a));
+    g2[0].D = mat(W(ota[jj]), ldv, n3);
+    g2[0].beta = make_double2(1.0, 0.0);
+    g2[1] = gemm(n3, R, nt, P, mat(L.Phib, n3, s3t), mat(tp, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I3b));
+    g2[1].D = mat(W(otb[jj]), ldv, n3);
+    g2[1].beta = make_double2(1.0, 0.0);
+    CK(hps::launch_gemm(g2, 2, st));
+    // the rest of the children's incoming data is the parent's: I1 and I2
+    CopyBatch cb;
+    cb.count = 2;
+    cb.d[0] = copy(n1, R, P, mat(tp, ldp, nt), mat(tc, ldc2, 2LL * nc, L.d_I1));
+    cb.d[1] = copy(n2, R, P, mat(tp + n1, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I2));
+    CK(hps::launch_copy(cb, st));
+  }
+  // leaves: u = Psi t + Y s = X [t; s]
+  g = gemm(n, R, n, nl, mat(h->X, n, (long long)n * n), mat(W(ot[0]), (long long)nl * nb, nb),
+           mat(u, (long long)nl * n, n));
+  g.B2 = mat(s, (long long)nl * ni, ni);
+  g.ksplit = nb;
+  CK(hps::launch_gemm(&g, 1, st));
+
+  return HPS_OK;
+}
+
+// ---- fixed workspace of hps_solve_noalloc ----------------------------------
+// The array lives in the library's device image: every GPU that loads the
+// library holds HPS_NOALLOC_WORKSPACE_BYTES of it until the process exits.
+// Host code may not use its name as a device address; the address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_ws[HPS_NOALLOC_WORKSPACE_BYTES];
+
+static int noalloc_ws_ptr(char **out) {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static void *ptrs[kMaxDev] = {nullptr};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) return HPS_ECUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptrs[dev]) {
+    void *p = nullptr;
+    cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_ws);
+    if (err != cudaSuccess || !p) return HPS_ECUDA;
+    ptrs[dev] = p;
+  }
+  *out = (char *)ptrs[dev];
+  return HPS_OK;
+}
+
 extern "C" {
 
 const char *hps_strerror(int code) {
@@ -362,6 +515,7 @@ const char *hps_strerror(int code) {
     case HPS_ETIMEOUT: return "bounded device wait timed out";
     case HPS_ECUDA: return "CUDA runtime error";
     case HPS_ENOTSUP: return "not supported by this build";
+    case HPS_ETOOBIG: return "request needs more than the fixed no-allocation workspace";
     default: return "unknown error";
   }
 }
@@ -731,33 +885,12 @@ int hps_solve(hps_handle *h, const double *s_, const double *t_, double *u_, int
   if (!s_ || !t_ || !u_) return HPS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const Plan &pl = h->plan;
-  const int n = pl.n, nb = pl.nb, ni = pl.ni, nl = pl.leaves, R = nrhs;
+  const int n = pl.n, ni = pl.ni, nl = pl.leaves, R = nrhs;
 
-  // workspace: h per level, t~3a / t~3b per merge, t per level, one temp
-  std::vector<size_t> oh(pl.lv.size() + 1), ot(pl.lv.size() + 1), ota(pl.lv.size()), otb(pl.lv.size());
-  size_t off = 0;
-  auto take = [&](long long count) {
-    size_t o = off;
-    off = align256(off + sizeof(double2) * (size_t)count);
-    return o;
-  };
-  oh[0] = take((long long)R * nl * nb);
-  ot[0] = take((long long)R * nl * nb);
-  long long vmax = 1;
-  for (size_t j = 0; j < pl.lv.size(); j++) {
-    const Level &L = pl.lv[j];
-    oh[j + 1] = take((long long)R * L.P * L.nt);
-    ot[j + 1] = take((long long)R * L.P * L.nt);
-    ota[j] = take((long long)R * L.P * L.n3);
-    otb[j] = take((long long)R * L.P * L.n3);
-    vmax = std::max(vmax, (long long)R * L.P * L.n3);
-  }
-  size_t ov = take(vmax);
-  size_t ws_need = off;
-  int gst = grow(&h->ws, &h->ws_bytes, ws_need);
+  SolveWs ws;
+  solve_ws_layout(pl, R, ws);
+  int gst = grow(&h->ws, &h->ws_bytes, ws.bytes);
   if (gst) return gst;
-  char *wb = (char *)h->ws;
-  auto W = [&](size_t o) { return (double2 *)(wb + o); };
 
   // stage host arrays
   const bool sdev = is_device_ptr(s_), tdev = is_device_ptr(t_), udev = is_device_ptr(u_);
@@ -784,89 +917,8 @@ int hps_solve(hps_handle *h, const double *s_, const double *t_, double *u_, int
   }
   if (!udev) u = (double2 *)sb;
 
-  // ---- upward pass ----
-  // leaves: h = Gamma s  (Gamma = GX[:, nb:])
-  GemmDesc g = gemm(nb, R, ni, nl, mat(h->GX + (size_t)nb * nb, nb, (long long)n * nb),
-                    mat(s, (long long)nl * ni, ni), mat(W(oh[0]), (long long)nl * nb, nb));
-  CK(hps::launch_gemm(&g, 1, st));
-  for (size_t j = 0; j < pl.lv.size(); j++) {
-    const Level &L = pl.lv[j];
-    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc;
-    const double2 *hc = W(oh[j]);
-    const long long ldh = (long long)2 * P * nc;
-    Mat hA = mat(hc, ldh, 2LL * nc), hB = mat(hc + nc, ldh, 2LL * nc);
-    Mat h3a = hA, h3b = hB, h1a = hA, h2b = hB;
-    h3a.rmap = L.d_I3a;
-    h3b.rmap = L.d_I3b;
-    h1a.rmap = L.d_I1;
-    h2b.rmap = L.d_I2;
-    const long long s33 = (long long)n3 * n3, ldv = (long long)P * n3;
-    double2 *v = W(ov), *ta = W(ota[j]), *tb = W(otb[j]);
-    // v = R33b h3a - h3b ;  t~3a = W^{-1} v  (Upsilon_a [h3a; h3b])
-    g = gemm(n3, R, n3, P, mat(L.R33b, n3, s33), h3a, mat(v, ldv, n3));
-    g.D = h3b;
-    g.beta = make_double2(-1.0, 0.0);
-    CK(hps::launch_gemm(&g, 1, st));
-    g = gemm(n3, R, n3, P, mat(L.Winv, n3, s33), mat(v, ldv, n3), mat(ta, ldv, n3));
-    CK(hps::launch_gemm(&g, 1, st));
-    // t~3b = -h3a - R33a t~3a  (Upsilon_b [h3a; h3b])
-    g = gemm(n3, R, n3, P, mat(L.R33a, n3, s33), mat(ta, ldv, n3), mat(tb, ldv, n3));
-    g.alpha = make_double2(-1.0, 0.0);
-    g.D = h3a;
-    g.beta = make_double2(-1.0, 0.0);
-    CK(hps::launch_gemm(&g, 1, st));
-    // h^tau = [h1a + R13a t~3a ; h2b + R23b t~3b]  (Eq. flux_part)
-    const long long ldp = (long long)P * nt;
-    GemmDesc g2[2];
-    g2[0] = gemm(n1, R, n3, P, mat(L.R13a, n1, (long long)n1 * n3), mat(ta, ldv, n3), mat(W(oh[j + 1]), ldp, nt));
-    g2[0].D = h1a;
-    g2[0].beta = make_double2(1.0, 0.0);
-    g2[1] = gemm(n2, R, n3, P, mat(L.R23b, n2, (long long)n2 * n3), mat(tb, ldv, n3),
-                 mat(W(oh[j + 1]) + n1, ldp, nt));
-    g2[1].D = h2b;
-    g2[1].beta = make_double2(1.0, 0.0);
-    CK(hps::launch_gemm(g2, 2, st));
-  }
-
-  // ---- downward pass ----
-  const size_t top = pl.lv.size();
-  const int ntop = top ? pl.lv.back().nt : nb;
-  {
-    // root incoming data: public [S, E, N, W] order -> the root's [I1, I2] order
-    CopyBatch cb;
-    cb.count = 1;
-    cb.d[0] = copy(ntop, R, 1, mat(t, pl.nbdry, 0, h->d_root_src), mat(W(ot[top]), ntop, 0));
-    CK(hps::launch_copy(cb, st));
-  }
-  for (size_t jj = top; jj-- > 0;) {
-    const Level &L = pl.lv[jj];
-    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc;
-    const double2 *tp = W(ot[jj + 1]);
-    double2 *tc = W(ot[jj]);
-    const long long ldp = (long long)P * nt, ldc2 = (long long)2 * P * nc, ldv = (long long)P * n3;
-    const long long s3t = (long long)n3 * nt;
-    // t3a = Phi_a t^tau + t~3a -> alpha rows I3 ; t3b = Phi_b t^tau + t~3b -> beta rows I3
-    GemmDesc g2[2];
-    g2[0] = gemm(n3, R, nt, P, mat(L.Phia, n3, s3t), mat(tp, ldp, nt), mat(tc, ldc2, 2LL * nc, L.d_I3a));
-    g2[0].D = mat(W(ota[jj]), ldv, n3);
-    g2[0].beta = make_double2(1.0, 0.0);
-    g2[1] = gemm(n3, R, nt, P, mat(L.Phib, n3, s3t), mat(tp, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I3b));
-    g2[1].D = mat(W(otb[jj]), ldv, n3);
-    g2[1].beta = make_double2(1.0, 0.0);
-    CK(hps::launch_gemm(g2, 2, st));
-    // the rest of the children's incoming data is the parent's: I1 and I2
-    CopyBatch cb;
-    cb.count = 2;
-    cb.d[0] = copy(n1, R, P, mat(tp, ldp, nt), mat(tc, ldc2, 2LL * nc, L.d_I1));
-    cb.d[1] = copy(n2, R, P, mat(tp + n1, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I2));
-    CK(hps::launch_copy(cb, st));
-  }
-  // leaves: u = Psi t + Y s = X [t; s]
-  g = gemm(n, R, n, nl, mat(h->X, n, (long long)n * n), mat(W(ot[0]), (long long)nl * nb, nb),
-           mat(u, (long long)nl * n, n));
-  g.B2 = mat(s, (long long)nl * ni, ni);
-  g.ksplit = nb;
-  CK(hps::launch_gemm(&g, 1, st));
+  gst = solve_launch(h, s, t, u, R, (char *)h->ws, ws, st);
+  if (gst) return gst;
 
   if (!udev) {
     CK(cudaMemcpyAsync(u_, u, ubytes, cudaMemcpyDeviceToHost, st));
@@ -876,6 +928,24 @@ int hps_solve(hps_handle *h, const double *s_, const double *t_, double *u_, int
     CK(cudaStreamSynchronize(st));
   }
   return HPS_OK;
+}
+
+int hps_solve_noalloc(hps_handle *h, const double *s_, const double *t_, double *u_, int nrhs,
+                      void *stream) {
+  if (!h || nrhs < 0) return HPS_EINVAL;
+  if (nrhs == 0) return HPS_OK;
+  if (!s_ || !t_ || !u_) return HPS_EINVAL;
+  if (!is_device_ptr(s_) || !is_device_ptr(t_) || !is_device_ptr(u_)) return HPS_EINVAL;
+  SolveWs ws;
+  solve_ws_layout(h->plan, nrhs, ws);
+  if (ws.bytes > (size_t)HPS_NOALLOC_WORKSPACE_BYTES) return HPS_ETOOBIG;
+  char *wb = nullptr;
+  int st = noalloc_ws_ptr(&wb);
+  if (st) return st;
+  // every buffer of the workspace is written before it is read, so nothing
+  // left there by an earlier call needs clearing
+  return solve_launch(h, (const double2 *)s_, (const double2 *)t_, (double2 *)u_, nrhs, wb, ws,
+                      (cudaStream_t)stream);
 }
 
 int hps_root_R(hps_handle *h, double *R, void *stream) {

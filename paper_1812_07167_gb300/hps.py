@@ -20,11 +20,12 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libhps.so")
 
-HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ETIMEOUT, HPS_ECUDA, HPS_ENOTSUP = range(7)
+HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ETIMEOUT, HPS_ECUDA, HPS_ENOTSUP, HPS_ETOOBIG = range(8)
+HPS_NOALLOC_WORKSPACE_BYTES = 16 << 20
 HPS_FP64 = 0
 
 # every entry point include/hps.h declares
-EXPORTS = ("hps_nodes", "hps_build", "hps_solve", "hps_root_R", "hps_leaf_ops", "hps_info",
+EXPORTS = ("hps_nodes", "hps_build", "hps_solve", "hps_solve_noalloc", "hps_root_R", "hps_leaf_ops", "hps_info",
            "hps_build_times", "hps_status", "hps_free", "hps_strerror")
 
 
@@ -73,6 +74,7 @@ def lib():
         L.hps_nodes.argtypes = [D, P, P]
         L.hps_build.argtypes = [D, P, P, ctypes.POINTER(ctypes.c_void_p)]
         L.hps_solve.argtypes = [P, P, P, P, ctypes.c_int, P]
+        L.hps_solve_noalloc.argtypes = [P, P, P, P, ctypes.c_int, P]
         L.hps_root_R.argtypes = [P, P, P]
         L.hps_leaf_ops.argtypes = [P, ctypes.c_int, P, P, P, P]
         L.hps_info.argtypes = [P, ctypes.POINTER(hps_info_t)]
@@ -199,6 +201,14 @@ def hps_build(pr: Problem, c, stream=None) -> Handle:
 def hps_solve(h: Handle, s, t, u, nrhs: int, stream=None):
     """u[nrhs, leaves, p^2-4] (complex128) from s and t (numpy or torch)."""
     _check(lib().hps_solve(h.ptr, _ptr(s), _ptr(t), _ptr(u), int(nrhs), _stream(stream)), "hps_solve")
+    return u
+
+
+def hps_solve_noalloc(h: Handle, s, t, u, nrhs: int, stream=None):
+    """hps_solve without allocation: s, t, u must be device tensors; the scratch
+    is the library's fixed workspace (see include/hps.h)."""
+    _check(lib().hps_solve_noalloc(h.ptr, _ptr(s), _ptr(t), _ptr(u), int(nrhs), _stream(stream)),
+           "hps_solve_noalloc")
     return u
 
 

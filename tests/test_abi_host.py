@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_strerror_codes():
-    for code in range(7):
+    for code in range(8):
         assert hps.hps_strerror(code)
     assert hps.hps_strerror(99) == "unknown error"
 
