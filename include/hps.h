@@ -109,7 +109,10 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy);
  *         boundary rows of the leaf system do not involve c)
  *   out:  receives the new handle; unchanged on failure
  * Device memory for all operators is allocated here and owned by the handle.
- * Returns HPS_EINVAL (bad descriptor, NULL c/out), HPS_ENOMEM, HPS_ECUDA. */
+ * Returns HPS_EINVAL (bad descriptor, NULL c/out), HPS_ENOMEM, HPS_ECUDA, or
+ * HPS_ENOTSUP when an interface of the tree is too large for this build's
+ * interface-inverse kernel (p = 16: 64 x 64 leaves and more), before any
+ * device work. */
 int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **out);
 
 /* Solve for nrhs right-hand sides (Algorithm 2: upward then downward pass).

@@ -840,7 +840,18 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
     if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) cs = v;
   }
   h->leaf_cs = cs;
-  for (Level &L : h->plan.lv) L.gj_cs = choose_gj_cs(L.n3, L.P);
+  for (Level &L : h->plan.lv) {
+    L.gj_cs = choose_gj_cs(L.n3, L.P);
+    // the interface inverse keeps two panels of the matrix in shared memory
+    if (hps::gj_smem_bytes(L.n3, L.gj_cs, false, 0) > 227 * 1024) {
+      delete h;
+      return HPS_ENOTSUP;
+    }
+  }
+  if (hps::gj_smem_bytes(h->plan.n, h->leaf_cs, true, h->plan.p) > 227 * 1024) {
+    delete h;
+    return HPS_ENOTSUP;
+  }
   long long cap = env_cap();
   if (cap >= 0 && h->info.operator_bytes > cap) {
     delete h;

@@ -97,3 +97,10 @@ def test_q_zero_means_p_minus_2():
     d = _desc(q=0)
     lxy = np.zeros((16, 60, 2))
     assert hps.lib().hps_nodes(ctypes.byref(d), lxy.ctypes.data, None) == hps.HPS_OK
+
+
+def test_too_large_interfaces_are_refused_before_device_work():
+    d = _desc(mx=64, my=64, p=16, q=14)
+    c = np.ones(64 * 64 * 196)
+    h = ctypes.c_void_p()
+    assert hps.lib().hps_build(ctypes.byref(d), c.ctypes.data, None, ctypes.byref(h)) == hps.HPS_ENOTSUP
