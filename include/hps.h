@@ -65,7 +65,7 @@ enum {
   HPS_ETOOBIG = 7    /* the request needs more than the fixed no-allocation workspace */
 };
 
-enum { HPS_FP64 = 0 };
+enum { HPS_FP64 = 0, HPS_MIXED = 1 };
 
 typedef struct {
   double x0, x1, y0, y1; /* the rectangle Omega, x1 > x0, y1 > y0 */
@@ -76,7 +76,16 @@ typedef struct {
                             HPS_EINVAL) */
   double kappa;          /* wave number, > 0 */
   double eta_re, eta_im; /* impedance parameter eta, Re(eta) != 0 */
-  int precision;         /* HPS_FP64 (complex128 throughout) */
+  int precision;         /* HPS_FP64: complex128 throughout.
+                            HPS_MIXED: leaves and the merge levels below the top
+                            fp64_levels in complex64, the top levels (their
+                            interface inverses W^{-1}, whose conditioning grows
+                            with kappa) in complex128; every solve is refined in
+                            complex128 against the residual of the global
+                            collocation system (see hps_solve). */
+  int fp64_levels;       /* HPS_MIXED: merge levels kept in complex128, counted
+                            from the root; 0 = 4 (clamped to the tree depth) */
+  int refine_steps;      /* HPS_MIXED: refinement steps per solve; 0 = 2, < 0 = none */
 } hps_desc;
 
 typedef struct hps_handle hps_handle;
@@ -116,6 +125,14 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy);
 int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **out);
 
 /* Solve for nrhs right-hand sides (Algorithm 2: upward then downward pass).
+ * For an HPS_MIXED handle the solve is iterative refinement: u = S(s, t), then
+ * refine_steps times: the residual of the global collocation system (every
+ * leaf's interior rows, the impedance rows F u = t on the outer boundary and,
+ * at every pair of coincident nodes on a shared edge, the two conditions
+ * t3a = -g3b, g3a = -t3b of Sec. 2.2) is formed in complex128 and the
+ * correction S(residual) added, where S is Algorithm 2 on the mixed
+ * operators with the interface residuals injected into h3 at the merge whose
+ * interface holds them.
  *   s: [nrhs][leaves][(p-2)^2] complex body load at the interior nodes
  *   t: [nrhs][4 m (p-2)] complex impedance data du/dnu + i eta u on the
  *      outer boundary
@@ -138,6 +155,8 @@ int hps_solve(hps_handle *h, const double *s, const double *t, double *u, int nr
  * The paper has no counterpart; this is a deployment variant of Algorithm 2.
  *   s, t, u: as for hps_solve, but all three must be device memory (host
  *            arrays would need staging buffers): HPS_EINVAL otherwise.
+ * HPS_MIXED handles are refused (HPS_ENOTSUP): their refinement needs more
+ * workspace than the array holds.
  * Returns HPS_ETOOBIG when nrhs right-hand sides of this handle's tree need
  * more workspace than the array holds (about 1.8 MB per right-hand side for
  * 16 x 16 leaves with p = 16), HPS_EINVAL for bad arguments, HPS_ECUDA if the

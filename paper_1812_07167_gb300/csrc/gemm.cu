@@ -1,14 +1,16 @@
-// Batched, index-mapped complex128 GEMM and copy kernels.
+// Batched, index-mapped complex GEMM and copy kernels.
 //
 // Every dense product of the HPS merge (Sec. 2.2: W = I - R33b R33a,
 // Phi_a = W^{-1}[R33b R31a | -R32b], Phi_b, R^tau) and of the solve sweeps
 // (Algorithm 2: the leaf matvecs Y s, Gamma s, Psi t and the per-level
-// Upsilon / Phi actions) is one launch of gemm_kernel over all boxes of a
+// Upsilon / Phi actions) is one launch of these kernels over all boxes of a
 // tree level.  Sub-blocks such as R33a = R^alpha(I3, I3) are read through
 // index maps, so no gather pass is needed before a product.
 //
-// The path is complex FP64 (DFMA-bound on this part: the tile sizes only
-// need enough reuse to keep shared-memory traffic well below the DFMA rate).
+// The arithmetic is complex128 (DFMA-bound on this part: the tiles only need
+// enough reuse to keep shared-memory traffic below the DFMA rate) or
+// complex64 for the mixed-precision path; each operand may be stored in
+// either precision and is converted when loaded or stored.
 #include <algorithm>
 
 #include "hps_internal.h"
@@ -22,13 +24,52 @@ struct GemmPack {
   GemmDesc d[2];
 };
 
+template <class C>
+struct CT;
+template <>
+struct CT<double2> {
+  __device__ static double2 make(double x, double y) { return make_double2(x, y); }
+};
+template <>
+struct CT<float2> {
+  __device__ static float2 make(double x, double y) { return make_float2((float)x, (float)y); }
+};
+
 __device__ __forceinline__ long long mat_off(const Mat &m, int b, int i, int j) {
   long long r = m.rmap ? (long long)__ldg(m.rmap + i) : (long long)i;
   long long c = m.cmap ? (long long)__ldg(m.cmap + j) : (long long)j;
   return (long long)b * m.stride + r + c * m.ld;
 }
 
-__device__ __forceinline__ double2 ld2(const double2 *p) { return __ldg(p); }
+// element `off` of matrix m (read-only for the kernel), converted to C
+template <class C>
+__device__ __forceinline__ C ldm(const Mat &m, long long off) {
+  if (m.f32) {
+    float2 v = __ldg((const float2 *)m.ptr + off);
+    return CT<C>::make(v.x, v.y);
+  }
+  double2 v = __ldg((const double2 *)m.ptr + off);
+  return CT<C>::make(v.x, v.y);
+}
+
+// plain load, for operands that may alias the output
+template <class C>
+__device__ __forceinline__ C ldm_rw(const Mat &m, long long off) {
+  if (m.f32) {
+    float2 v = ((const float2 *)m.ptr)[off];
+    return CT<C>::make(v.x, v.y);
+  }
+  double2 v = ((const double2 *)m.ptr)[off];
+  return CT<C>::make(v.x, v.y);
+}
+
+template <class C>
+__device__ __forceinline__ void stm(const Mat &m, long long off, C v) {
+  if (m.f32)
+    ((float2 *)m.ptr)[off] = make_float2((float)v.x, (float)v.y);
+  else
+    ((double2 *)m.ptr)[off] = make_double2((double)v.x, (double)v.y);
+}
 
 __device__ __forceinline__ void cmac(double2 &acc, double2 a, double2 b) {
   acc.x = fma(a.x, b.x, acc.x);
@@ -36,19 +77,42 @@ __device__ __forceinline__ void cmac(double2 &acc, double2 a, double2 b) {
   acc.y = fma(a.x, b.y, acc.y);
   acc.y = fma(a.y, b.x, acc.y);
 }
+__device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+template <class C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+// alpha * acc + beta * D(i, j) (+ 1 on the diagonal), stored to C(i, j)
+template <class C>
+__device__ __forceinline__ void epilogue(const GemmDesc &g, int b, int i, int j, C acc) {
+  C v = cmul(CT<C>::make(g.alpha.x, g.alpha.y), acc);
+  if (g.D.ptr) {
+    C t = cmul(CT<C>::make(g.beta.x, g.beta.y), ldm_rw<C>(g.D, mat_off(g.D, b, i, j)));
+    v.x += t.x;
+    v.y += t.y;
+  }
+  if (g.addI && i == j) v.x += 1;
+  stm(g.C, mat_off(g.C, b, i, j), v);
 }
 
 // C tile of BM x BN per CTA; each thread owns TM x TN outputs at rows
 // tx + r * (BM/TM) and columns ty + c * (BN/TN).
-template <int BM, int BN, int BK, int TM, int TN>
+template <class C, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     gemm_kernel(const __grid_constant__ GemmPack pack) {
   constexpr int NTX = BM / TM, NTY = BN / TN, NT = NTX * NTY;
-  __shared__ double2 As[BK][BM];
-  __shared__ double2 Bs[BK][BN];
+  __shared__ C As[BK][BM];
+  __shared__ C Bs[BK][BN];
   const GemmDesc &g = pack.d[blockIdx.z];
   const int tiles_m = (g.M + BM - 1) / BM;
   const int tiles_n = (g.N + BN - 1) / BN;
@@ -59,66 +123,134 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const int tx = tid % NTX, ty = tid / NTX;
 
   for (int b = blockIdx.y; b < g.batch; b += gridDim.y) {
-  double2 acc[TM][TN];
+    C acc[TM][TN];
 #pragma unroll
-  for (int r = 0; r < TM; r++)
+    for (int r = 0; r < TM; r++)
 #pragma unroll
-    for (int c = 0; c < TN; c++) acc[r][c] = make_double2(0.0, 0.0);
+      for (int c = 0; c < TN; c++) acc[r][c] = CT<C>::make(0.0, 0.0);
 
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    // A tile: BM x BK, consecutive threads walk down a column
-    for (int e = tid; e < BM * BK; e += NT) {
-      int i = e % BM, k = e / BM;
-      int gi = m0 + i, gk = k0 + k;
-      double2 v = make_double2(0.0, 0.0);
-      if (gi < g.M && gk < g.K) v = ld2(g.A.ptr + mat_off(g.A, b, gi, gk));
-      As[k][i] = v;
-    }
-    // B tile: BK x BN
-    for (int e = tid; e < BK * BN; e += NT) {
-      int k = e % BK, j = e / BK;
-      int gk = k0 + k, gj = n0 + j;
-      double2 v = make_double2(0.0, 0.0);
-      if (gk < g.K && gj < g.N) {
-        if (g.B2.ptr == nullptr || gk < g.ksplit)
-          v = ld2(g.B.ptr + mat_off(g.B, b, gk, gj));
-        else
-          v = ld2(g.B2.ptr + mat_off(g.B2, b, gk - g.ksplit, gj));
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+      // A tile: BM x BK, consecutive threads walk down a column
+      for (int e = tid; e < BM * BK; e += NT) {
+        int i = e % BM, k = e / BM;
+        int gi = m0 + i, gk = k0 + k;
+        C v = CT<C>::make(0.0, 0.0);
+        if (gi < g.M && gk < g.K) v = ldm<C>(g.A, mat_off(g.A, b, gi, gk));
+        As[k][i] = v;
       }
-      Bs[k][j] = v;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < BK; k++) {
-      double2 a[TM], bv[TN];
-#pragma unroll
-      for (int r = 0; r < TM; r++) a[r] = As[k][tx + r * NTX];
-#pragma unroll
-      for (int c = 0; c < TN; c++) bv[c] = Bs[k][ty + c * NTY];
-#pragma unroll
-      for (int r = 0; r < TM; r++)
-#pragma unroll
-        for (int c = 0; c < TN; c++) cmac(acc[r][c], a[r], bv[c]);
-    }
-    __syncthreads();
-  }
-
-#pragma unroll
-  for (int r = 0; r < TM; r++)
-#pragma unroll
-    for (int c = 0; c < TN; c++) {
-      int i = m0 + tx + r * NTX, j = n0 + ty + c * NTY;
-      if (i < g.M && j < g.N) {
-        double2 v = cmul(g.alpha, acc[r][c]);
-        if (g.D.ptr) {
-          double2 d = g.D.ptr[mat_off(g.D, b, i, j)];
-          double2 t = cmul(g.beta, d);
-          v.x += t.x;
-          v.y += t.y;
+      // B tile: BK x BN
+      for (int e = tid; e < BK * BN; e += NT) {
+        int k = e % BK, j = e / BK;
+        int gk = k0 + k, gj = n0 + j;
+        C v = CT<C>::make(0.0, 0.0);
+        if (gk < g.K && gj < g.N) {
+          if (g.B2.ptr == nullptr || gk < g.ksplit)
+            v = ldm<C>(g.B, mat_off(g.B, b, gk, gj));
+          else
+            v = ldm<C>(g.B2, mat_off(g.B2, b, gk - g.ksplit, gj));
         }
-        if (g.addI && i == j) v.x += 1.0;
-        const_cast<double2 *>(g.C.ptr)[mat_off(g.C, b, i, j)] = v;
+        Bs[k][j] = v;
       }
+      __syncthreads();
+#pragma unroll 4
+      for (int k = 0; k < BK; k++) {
+        C a[TM], bv[TN];
+#pragma unroll
+        for (int r = 0; r < TM; r++) a[r] = As[k][tx + r * NTX];
+#pragma unroll
+        for (int c = 0; c < TN; c++) bv[c] = Bs[k][ty + c * NTY];
+#pragma unroll
+        for (int r = 0; r < TM; r++)
+#pragma unroll
+          for (int c = 0; c < TN; c++) cmac(acc[r][c], a[r], bv[c]);
+      }
+      __syncthreads();
+    }
+
+#pragma unroll
+    for (int r = 0; r < TM; r++)
+#pragma unroll
+      for (int c = 0; c < TN; c++) {
+        int i = m0 + tx + r * NTX, j = n0 + ty + c * NTY;
+        if (i < g.M && j < g.N) epilogue<C>(g, b, i, j, acc[r][c]);
+      }
+  }
+}
+
+// element `off` of a matrix stored as T, converted to C
+template <class C, class T>
+__device__ __forceinline__ C ldt(const void *ptr, long long off) {
+  const T v = __ldg((const T *)ptr + off);
+  return CT<C>::make(v.x, v.y);
+}
+
+// k-loop of the skinny product with the storage types of A and B fixed
+template <class C, class TA, class TB, int NN>
+__device__ __forceinline__ void gemv_loop(const GemmDesc &g, int b, int i, int w, C (&acc)[NN]) {
+  const long long arow = (long long)b * g.A.stride + (g.A.rmap ? (long long)__ldg(g.A.rmap + i) : i);
+#pragma unroll 4
+  for (int k = w; k < g.K; k += 8) {
+    const long long c = g.A.cmap ? (long long)__ldg(g.A.cmap + k) : k;
+    const C a = ldt<C, TA>(g.A.ptr, arow + c * g.A.ld);
+    const bool second = (g.B2.ptr != nullptr && k >= g.ksplit);
+    const int kk = second ? k - g.ksplit : k;
+#pragma unroll
+    for (int j = 0; j < NN; j++)
+      if (j < g.N) {
+        const C bb = second ? ldt<C, TB>(g.B2.ptr, mat_off(g.B2, b, kk, j))
+                            : ldt<C, TB>(g.B.ptr, mat_off(g.B, b, kk, j));
+        cmac(acc[j], a, bb);
+      }
+  }
+}
+
+// Skinny products (N <= NN: the solve's right-hand sides).  A CTA computes 32
+// rows of one batch entry; its 8 warps split K (warp w takes k = w, w+8, ...),
+// each lane one row, so the 32 loads of A a warp issues are one coalesced
+// column segment and B(k, :) is a broadcast.  The 8 partial sums meet in
+// shared memory.  Enough CTAs exist even for one large matrix.  B and B2 share
+// one storage type.
+template <class C, int NN>
+__global__ void __launch_bounds__(256) gemv_kernel(const __grid_constant__ GemmPack pack) {
+  __shared__ C red[8][NN][33];
+  const GemmDesc &g = pack.d[blockIdx.z];
+  const int rblocks = (g.M + 31) / 32;
+  if ((long long)blockIdx.x >= (long long)rblocks * g.batch) return;
+  const int b = blockIdx.x / rblocks;
+  const int i = (blockIdx.x % rblocks) * 32 + (threadIdx.x & 31);
+  const int w = threadIdx.x >> 5;
+  const bool live = i < g.M;
+  C acc[NN];
+#pragma unroll
+  for (int j = 0; j < NN; j++) acc[j] = CT<C>::make(0.0, 0.0);
+  if (live) {
+    if (g.A.f32) {
+      if (g.B.f32)
+        gemv_loop<C, float2, float2, NN>(g, b, i, w, acc);
+      else
+        gemv_loop<C, float2, double2, NN>(g, b, i, w, acc);
+    } else {
+      if (g.B.f32)
+        gemv_loop<C, double2, float2, NN>(g, b, i, w, acc);
+      else
+        gemv_loop<C, double2, double2, NN>(g, b, i, w, acc);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NN; j++) red[w][j][threadIdx.x & 31] = acc[j];
+  __syncthreads();
+  if (w == 0 && live) {
+    const int l = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < NN; j++) {
+      if (j >= g.N) continue;
+      C v = red[0][j][l];
+#pragma unroll
+      for (int q = 1; q < 8; q++) {
+        v.x += red[q][j][l].x;
+        v.y += red[q][j][l].y;
+      }
+      epilogue<C>(g, b, i, j, v);
     }
   }
 }
@@ -132,80 +264,21 @@ __global__ void __launch_bounds__(256) copy_kernel(const __grid_constant__ CopyB
   for (int b = blockIdx.y; b < d.batch; b += gridDim.y) {
     double2 v = make_double2(0.0, 0.0);
     if (d.src.ptr) {
-      double2 s = d.trans ? d.src.ptr[mat_off(d.src, b, j, i)] : d.src.ptr[mat_off(d.src, b, i, j)];
+      double2 s = d.trans ? ldm_rw<double2>(d.src, mat_off(d.src, b, j, i))
+                          : ldm_rw<double2>(d.src, mat_off(d.src, b, i, j));
       v = cmul(d.alpha, s);
     }
-    const_cast<double2 *>(d.dst.ptr)[mat_off(d.dst, b, i, j)] = v;
+    const long long o = mat_off(d.dst, b, i, j);
+    if (d.accumulate) {
+      const double2 w = ldm_rw<double2>(d.dst, o);
+      v.x += w.x;
+      v.y += w.y;
+    }
+    stm(d.dst, o, v);
   }
 }
 
-// Skinny products (N <= NN: the solve's right-hand sides).  A CTA computes 32
-// rows of one batch entry; its 8 warps split K (warp w takes k = w, w+8, ...),
-// each lane one row, so the 32 loads of A a warp issues are one coalesced
-// column segment and B(k, :) is a broadcast.  The 8 partial sums meet in
-// shared memory.  Enough CTAs exist even for one large matrix.
-template <int NN>
-__global__ void __launch_bounds__(256) gemv_kernel(const __grid_constant__ GemmPack pack) {
-  __shared__ double2 red[8][NN][33];
-  const GemmDesc &g = pack.d[blockIdx.z];
-  const int rblocks = (g.M + 31) / 32;
-  if ((long long)blockIdx.x >= (long long)rblocks * g.batch) return;
-  const int b = blockIdx.x / rblocks;
-  const int i = (blockIdx.x % rblocks) * 32 + (threadIdx.x & 31);
-  const int w = threadIdx.x >> 5;
-  const bool live = i < g.M;
-  double2 acc[NN];
-#pragma unroll
-  for (int j = 0; j < NN; j++) acc[j] = make_double2(0.0, 0.0);
-  if (live) {
-    const long long arow = (long long)b * g.A.stride + (g.A.rmap ? (long long)__ldg(g.A.rmap + i) : i);
-#pragma unroll 4
-    for (int k = w; k < g.K; k += 8) {
-      const long long c = g.A.cmap ? (long long)__ldg(g.A.cmap + k) : k;
-      const double2 a = ld2(g.A.ptr + arow + c * g.A.ld);
-      const bool second = (g.B2.ptr != nullptr && k >= g.ksplit);
-      const double2 *bp = second ? g.B2.ptr : g.B.ptr;
-      const int *brm = second ? g.B2.rmap : g.B.rmap;
-      const int *bcm = second ? g.B2.cmap : g.B.cmap;
-      const long long bld = second ? g.B2.ld : g.B.ld;
-      const long long bst = second ? g.B2.stride : g.B.stride;
-      const int kk = second ? k - g.ksplit : k;
-      const long long brow = (long long)b * bst + (brm ? (long long)__ldg(brm + kk) : kk);
-#pragma unroll
-      for (int j = 0; j < NN; j++)
-        if (j < g.N) {
-          const long long cj = bcm ? (long long)__ldg(bcm + j) : j;
-          cmac(acc[j], a, ld2(bp + brow + cj * bld));
-        }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < NN; j++) red[w][j][threadIdx.x & 31] = acc[j];
-  __syncthreads();
-  if (w == 0 && live) {
-    const int l = threadIdx.x & 31;
-#pragma unroll
-    for (int j = 0; j < NN; j++) {
-      if (j >= g.N) continue;
-      double2 v = red[0][j][l];
-#pragma unroll
-      for (int q = 1; q < 8; q++) {
-        v.x += red[q][j][l].x;
-        v.y += red[q][j][l].y;
-      }
-      v = cmul(g.alpha, v);
-      if (g.D.ptr) {
-        double2 t = cmul(g.beta, g.D.ptr[mat_off(g.D, b, i, j)]);
-        v.x += t.x;
-        v.y += t.y;
-      }
-      if (g.addI && i == j) v.x += 1.0;
-      const_cast<double2 *>(g.C.ptr)[mat_off(g.C, b, i, j)] = v;
-    }
-  }
-}
-
-template <int BM, int BN, int BK, int TM, int TN>
+template <int BM, int BN>
 long long cfg_ctas(const GemmPack &pk) {
   long long ctas = 0;
   for (int q = 0; q < pk.n; q++) {
@@ -215,7 +288,7 @@ long long cfg_ctas(const GemmPack &pk) {
   return ctas;
 }
 
-template <int BM, int BN, int BK, int TM, int TN>
+template <class C, int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_cfg(const GemmPack &pk, cudaStream_t st) {
   int maxtiles = 0, maxbatch = 0;
   for (int q = 0; q < pk.n; q++) {
@@ -226,19 +299,33 @@ cudaError_t launch_cfg(const GemmPack &pk, cudaStream_t st) {
   }
   if (maxtiles == 0 || maxbatch == 0) return cudaSuccess;
   dim3 grid(maxtiles, maxbatch < 65535 ? maxbatch : 65535, pk.n);
-  gemm_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(pk);
+  gemm_kernel<C, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(pk);
   return cudaGetLastError();
 }
 
-template <int NN>
+template <class C, int NN>
 cudaError_t launch_gemv(const GemmPack &pk, cudaStream_t st) {
   long long blocks = 0;
   for (int q = 0; q < pk.n; q++)
     blocks = std::max(blocks, (long long)((pk.d[q].M + 31) / 32) * pk.d[q].batch);
   if (blocks == 0) return cudaSuccess;
   dim3 grid((unsigned)blocks, 1, pk.n);
-  gemv_kernel<NN><<<grid, 256, 0, st>>>(pk);
+  gemv_kernel<C, NN><<<grid, 256, 0, st>>>(pk);
   return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_typed(const GemmPack &pk, int maxN, cudaStream_t st) {
+  if (maxN <= 1) return launch_gemv<C, 1>(pk, st);
+  if (maxN <= 2) return launch_gemv<C, 2>(pk, st);
+  if (maxN <= 4) return launch_gemv<C, 4>(pk, st);
+  if (maxN <= 8) return launch_gemv<C, 8>(pk, st);
+  if (maxN < 32) return launch_cfg<C, 64, 16, 16, 2, 2>(pk, st);
+  // the largest tile that still gives every SM two CTAs
+  const long long want = 2 * 152;
+  if (cfg_ctas<64, 64>(pk) >= want) return launch_cfg<C, 64, 64, 16, 4, 4>(pk, st);
+  if (cfg_ctas<32, 32>(pk) >= want) return launch_cfg<C, 32, 32, 16, 2, 2>(pk, st);
+  return launch_cfg<C, 16, 16, 16, 1, 1>(pk, st);
 }
 
 }  // namespace
@@ -247,25 +334,18 @@ cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st) {
   if (ndesc < 1 || ndesc > 2) return cudaErrorInvalidValue;
   GemmPack pk;
   pk.n = 0;
-  int maxN = 0;
+  int maxN = 0, cf32 = -1;
   for (int q = 0; q < ndesc; q++) {
     const GemmDesc &g = descs[q];
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) continue;
+    if (cf32 >= 0 && cf32 != g.cf32) return cudaErrorInvalidValue;  // one precision a launch
+    cf32 = g.cf32;
     pk.d[pk.n++] = g;
     if (g.N > maxN) maxN = g.N;
   }
   if (pk.n == 0) return cudaSuccess;
   // K == 0 is legal (C = beta D); the k-loop simply does not run.
-  if (maxN <= 1) return launch_gemv<1>(pk, st);
-  if (maxN <= 2) return launch_gemv<2>(pk, st);
-  if (maxN <= 4) return launch_gemv<4>(pk, st);
-  if (maxN <= 8) return launch_gemv<8>(pk, st);
-  if (maxN < 32) return launch_cfg<64, 16, 16, 2, 2>(pk, st);
-  // FP64-bound tiles: the largest tile that still gives every SM two CTAs
-  const long long want = 2 * 152;
-  if (cfg_ctas<64, 64, 16, 4, 4>(pk) >= want) return launch_cfg<64, 64, 16, 4, 4>(pk, st);
-  if (cfg_ctas<32, 32, 16, 2, 2>(pk) >= want) return launch_cfg<32, 32, 16, 2, 2>(pk, st);
-  return launch_cfg<16, 16, 16, 1, 1>(pk, st);
+  return cf32 ? launch_typed<float2>(pk, maxN, st) : launch_typed<double2>(pk, maxN, st);
 }
 
 cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st) {

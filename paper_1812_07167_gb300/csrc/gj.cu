@@ -43,28 +43,57 @@ constexpr int KB = 8;           // panel width
 constexpr int kMoves = 2 * KB;  // row moves of one panel, at most
 constexpr int kMoveInts = 1 + 2 * kMoves;
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-__device__ __forceinline__ double2 crecip(double2 z) {
-  // 1 / z with Smith's scaling (Smith, CACM 1962)
-  if (fabs(z.x) >= fabs(z.y)) {
-    double r = z.y / z.x, d = z.x + z.y * r;
-    return make_double2(1.0 / d, -r / d);
-  } else {
-    double r = z.x / z.y, d = z.x * r + z.y;
-    return make_double2(r / d, -1.0 / d);
+template <class C>
+struct CX;
+template <>
+struct CX<double2> {
+  using R = double;
+  __device__ static double2 make(double x, double y) { return make_double2(x, y); }
+  __device__ static double fmad(double a, double b, double c) { return fma(a, b, c); }
+  // max(|Re|, |Im|) as the integer image of its IEEE-754 bits (for
+  // non-negative values integer order is numeric order): the pivot search
+  // compares integers instead of spending floating-point instructions
+  __device__ static unsigned long long key(double2 z) {
+    unsigned long long a = (unsigned long long)__double_as_longlong(z.x) & 0x7fffffffffffffffull;
+    unsigned long long b = (unsigned long long)__double_as_longlong(z.y) & 0x7fffffffffffffffull;
+    return a > b ? a : b;
   }
+};
+template <>
+struct CX<float2> {
+  using R = float;
+  __device__ static float2 make(double x, double y) { return make_float2((float)x, (float)y); }
+  __device__ static float fmad(float a, float b, float c) { return fmaf(a, b, c); }
+  __device__ static unsigned long long key(float2 z) {
+    unsigned int a = __float_as_uint(z.x) & 0x7fffffffu;
+    unsigned int b = __float_as_uint(z.y) & 0x7fffffffu;
+    return a > b ? a : b;
+  }
+};
+
+template <class C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
 }
 
-// max(|Re|, |Im|) as the integer image of its IEEE-754 bits (for
-// non-negative doubles integer order is numeric order): the pivot search
-// compares integers instead of spending FP64 instructions.
-__device__ __forceinline__ unsigned long long mag_key(double2 z) {
-  unsigned long long a = (unsigned long long)__double_as_longlong(z.x) & 0x7fffffffffffffffull;
-  unsigned long long b = (unsigned long long)__double_as_longlong(z.y) & 0x7fffffffffffffffull;
-  return a > b ? a : b;
+template <class C>
+__device__ __forceinline__ C crecip(C z) {
+  // 1 / z with Smith's scaling (Smith, CACM 1962)
+  using R = typename CX<C>::R;
+  C out;
+  if (fabs(z.x) >= fabs(z.y)) {
+    R r = z.y / z.x, d = z.x + z.y * r;
+    out.x = R(1) / d;
+    out.y = -r / d;
+  } else {
+    R r = z.x / z.y, d = z.x * r + z.y;
+    out.x = r / d;
+    out.y = R(-1) / d;
+  }
+  return out;
 }
 
 __device__ __forceinline__ void cluster_arrive() {
@@ -80,23 +109,24 @@ __host__ __device__ inline int npanels(int n) { return (n + KB - 1) / KB; }
 __host__ __device__ inline int meta_ints(int n) { return n + npanels(n) * kMoveInts; }
 
 struct SmemPlan {
-  size_t T, F, x, mvbuf, col, prow, mv, rows, srcs, scal, pinv, perm, dtab, grid, loc, cv, total;
+  size_t T, F, x, mvbuf, col, prow, mv, rows, srcs, scal, pinv, perm, dtab, grid, loc, cv, rsc, total;
 };
 
-__host__ __device__ inline SmemPlan plan_smem(int n, int cw, bool leaf, int p) {
+__host__ __device__ inline SmemPlan plan_smem(int n, int cw, bool leaf, int p, bool tglobal = false,
+                                               size_t esz = 16) {
   SmemPlan s;
   size_t o = 0;
-  s.T = o;    o = align16(o + sizeof(double2) * (size_t)KB * n);
-  s.F = o;    o = align16(o + sizeof(double2) * (size_t)KB * n);
-  s.x = o;    o = align16(o + sizeof(double2) * (size_t)KB * cw);
-  s.mvbuf = o; o = align16(o + sizeof(double2) * (size_t)kMoves * cw);
-  s.col = o;  o = align16(o + sizeof(double2) * (size_t)n);
-  s.prow = o; o = align16(o + sizeof(double2) * KB);
+  s.T = o;    if (!tglobal) o = align16(o + esz * (size_t)KB * n);
+  s.F = o;    if (!tglobal) o = align16(o + esz * (size_t)KB * n);
+  s.x = o;    o = align16(o + esz * (size_t)KB * cw);
+  s.mvbuf = o; o = align16(o + esz * (size_t)kMoves * cw);
+  s.col = o;  o = align16(o + esz * (size_t)n);
+  s.prow = o; o = align16(o + esz * KB);
   s.mv = o;   o = align16(o + sizeof(int) * kMoveInts);
   s.rows = o; o = align16(o + sizeof(int) * 2 * KB);
   s.srcs = o; o = align16(o + sizeof(int) * 2 * KB);
   s.scal = o; o = align16(o + sizeof(int) * 4);
-  s.pinv = o; o = align16(o + sizeof(double2));
+  s.pinv = o; o = align16(o + esz);
   s.perm = o; o = align16(o + sizeof(int) * (size_t)n);
   if (leaf) {
     int ni = (p - 2) * (p - 2);
@@ -104,42 +134,45 @@ __host__ __device__ inline SmemPlan plan_smem(int n, int cw, bool leaf, int p) {
     s.grid = o; o = align16(o + sizeof(int) * (size_t)n);
     s.loc = o;  o = align16(o + sizeof(int) * (size_t)p * p);
     s.cv = o;   o = align16(o + sizeof(double) * (size_t)ni);
+    s.rsc = o;  o = align16(o + sizeof(double) * (size_t)n);
   } else {
-    s.dtab = s.grid = s.loc = s.cv = o;
+    s.dtab = s.grid = s.loc = s.cv = s.rsc = o;
   }
   s.total = o;
   return s;
 }
 
+template <class C>
 struct Shared {
-  double2 *T;     // [KB][n] panel being applied (column-major)
-  double2 *F;     // [KB][n] panel being eliminated (owner only)
-  double2 *x;     // [KB][cw] panel rows of the own columns, after the moves
-  double2 *mvbuf; // [cw][kMoves] values in flight during the row moves
-  double2 *col;   // [n] pivot column of the current elimination step
-  double2 *prow;  // [KB] scaled pivot row within the panel
+  C *T;     // [KB][n] panel being applied (column-major), or null: read in place
+  C *F;     // [KB][n] panel being eliminated (owner only), or null: in place
+  C *x;     // [KB][cw] panel rows of the own columns, after the moves
+  C *mvbuf; // [cw][kMoves] values in flight during the row moves
+  C *col;   // [n] pivot column of the current elimination step
+  C *prow;  // [KB] scaled pivot row within the panel
   int *mv;        // [kMoveInts] row moves of the panel being applied
   int *rows;      // [2 KB] scratch for building a move list
   int *srcs;      // [2 KB]
   int *scal;      // [4] pivot row, zero flag
-  double2 *pinv;  // [1] reciprocal of the pivot
+  C *pinv;  // [1] reciprocal of the pivot
   int *perm;      // [n] pivot rows, for the final column permutation
   int n, cw;
 };
 
-__device__ Shared bind(unsigned char *smem, const SmemPlan &sp, int n, int cw) {
-  Shared s;
-  s.T = (double2 *)(smem + sp.T);
-  s.F = (double2 *)(smem + sp.F);
-  s.x = (double2 *)(smem + sp.x);
-  s.mvbuf = (double2 *)(smem + sp.mvbuf);
-  s.col = (double2 *)(smem + sp.col);
-  s.prow = (double2 *)(smem + sp.prow);
+template <class C>
+__device__ Shared<C> bind(unsigned char *smem, const SmemPlan &sp, int n, int cw) {
+  Shared<C> s;
+  s.T = (sp.F > sp.T) ? (C *)(smem + sp.T) : nullptr;
+  s.F = (sp.x > sp.F) ? (C *)(smem + sp.F) : nullptr;
+  s.x = (C *)(smem + sp.x);
+  s.mvbuf = (C *)(smem + sp.mvbuf);
+  s.col = (C *)(smem + sp.col);
+  s.prow = (C *)(smem + sp.prow);
   s.mv = (int *)(smem + sp.mv);
   s.rows = (int *)(smem + sp.rows);
   s.srcs = (int *)(smem + sp.srcs);
   s.scal = (int *)(smem + sp.scal);
-  s.pinv = (double2 *)(smem + sp.pinv);
+  s.pinv = (C *)(smem + sp.pinv);
   s.perm = (int *)(smem + sp.perm);
   s.n = n;
   s.cw = cw;
@@ -149,22 +182,27 @@ __device__ Shared bind(unsigned char *smem, const SmemPlan &sp, int n, int cw) {
 // Eliminate panel [k0, k0 + kbp) of S (column-major, ld n) in shared memory
 // and write it back; record its pivot rows and row moves in `meta`.
 // Returns true if a zero pivot was met.
-__device__ bool eliminate_panel(const Shared &s, double2 *S, int *meta, int k0, int kbp) {
+template <class C>
+__device__ bool eliminate_panel(const Shared<C> &s, C *S, int *meta, int k0, int kbp) {
   const int tid = threadIdx.x, nthr = blockDim.x, n = s.n;
   bool zero = false;
-  for (int e = tid; e < kbp * n; e += nthr) {
-    const int q = e / n, i = e % n;
-    s.F[q * n + i] = S[(size_t)(k0 + q) * n + i];
-  }
+  // work on a shared-memory copy of the panel, or in place in S when the
+  // panel does not fit next to the other buffers
+  C *F = s.F ? s.F : S + (size_t)k0 * n;
+  if (s.F)
+    for (int e = tid; e < kbp * n; e += nthr) {
+      const int q = e / n, i = e % n;
+      F[q * n + i] = S[(size_t)(k0 + q) * n + i];
+    }
   __syncthreads();
   for (int q = 0; q < kbp; q++) {
     const int k = k0 + q;
-    const double2 *Fk = s.F + q * n;
+    const C *Fk = F + q * n;
     if (tid < 32) {
       unsigned long long best = 0;
       int bi = n;
       for (int i = k + tid; i < n; i += 32) {
-        unsigned long long key = mag_key(Fk[i]);
+        unsigned long long key = CX<C>::key(Fk[i]);
         if (bi == n || key > best) {
           best = key;
           bi = i;
@@ -180,58 +218,59 @@ __device__ bool eliminate_panel(const Shared &s, double2 *S, int *meta, int k0, 
       }
       if (tid == 0) {
         const int r = (bi < n) ? bi : k;
-        const double2 pv = Fk[r];
-        const bool z = (mag_key(pv) == 0ull);
+        const C pv = Fk[r];
+        const bool z = (CX<C>::key(pv) == 0ull);
         s.scal[0] = r;
         s.scal[1] = z ? 1 : 0;
-        s.pinv[0] = z ? make_double2(0.0, 0.0) : crecip(pv);
+        s.pinv[0] = z ? CX<C>::make(0.0, 0.0) : crecip(pv);
         meta[k] = r;
       }
     }
     __syncthreads();
     const int r = s.scal[0];
     if (s.scal[1]) zero = true;
-    const double2 pinv = s.pinv[0];
+    const C pinv = s.pinv[0];
     // swap rows k and r inside the panel
     if (r != k)
       for (int qq = tid; qq < kbp; qq += nthr) {
-        double2 t = s.F[qq * n + k];
-        s.F[qq * n + k] = s.F[qq * n + r];
-        s.F[qq * n + r] = t;
+        C t = F[qq * n + k];
+        F[qq * n + k] = F[qq * n + r];
+        F[qq * n + r] = t;
       }
     __syncthreads();
     // pivot column with its pivot entry zeroed, and the scaled pivot row
-    for (int i = tid; i < n; i += nthr) s.col[i] = (i == k) ? make_double2(0.0, 0.0) : Fk[i];
-    for (int qq = tid; qq < kbp; qq += nthr) s.prow[qq] = cmul(s.F[qq * n + k], pinv);
+    for (int i = tid; i < n; i += nthr) s.col[i] = (i == k) ? CX<C>::make(0.0, 0.0) : Fk[i];
+    for (int qq = tid; qq < kbp; qq += nthr) s.prow[qq] = cmul(F[qq * n + k], pinv);
     __syncthreads();
     for (int e = tid; e < kbp * n; e += nthr) {
       const int qq = e / n, i = e % n;
-      double2 *a = &s.F[qq * n + i];
+      C *a = &F[qq * n + i];
       if (qq == q) {
         // the eliminated column becomes -col / pivot, 1 / pivot at the pivot
         if (i == k) {
           *a = pinv;
         } else {
-          double2 f = cmul(s.col[i], pinv);
-          *a = make_double2(-f.x, -f.y);
+          C f = cmul(s.col[i], pinv);
+          *a = CX<C>::make(-f.x, -f.y);
         }
       } else if (i == k) {
         *a = s.prow[qq];
       } else {
-        double2 f = s.col[i], pr = s.prow[qq], v = *a;
-        v.x = fma(-f.x, pr.x, v.x);
-        v.x = fma(f.y, pr.y, v.x);
-        v.y = fma(-f.x, pr.y, v.y);
-        v.y = fma(-f.y, pr.x, v.y);
+        C f = s.col[i], pr = s.prow[qq], v = *a;
+        v.x = CX<C>::fmad(-f.x, pr.x, v.x);
+        v.x = CX<C>::fmad(f.y, pr.y, v.x);
+        v.y = CX<C>::fmad(-f.x, pr.y, v.y);
+        v.y = CX<C>::fmad(-f.y, pr.x, v.y);
         *a = v;
       }
     }
     __syncthreads();
   }
-  for (int e = tid; e < kbp * n; e += nthr) {
-    const int q = e / n, i = e % n;
-    S[(size_t)(k0 + q) * n + i] = s.F[q * n + i];
-  }
+  if (s.F)
+    for (int e = tid; e < kbp * n; e += nthr) {
+      const int q = e / n, i = e % n;
+      S[(size_t)(k0 + q) * n + i] = F[q * n + i];
+    }
   if (tid == 0) {
     // net row moves of the panel's swaps: after the swaps (k, piv[k]) in
     // order, row rows[t] holds what row srcs[t] held before
@@ -280,8 +319,9 @@ __device__ __forceinline__ bool skipped(int j, int a0, int a1, int b0, int b1) {
 
 // Apply the panel [k0, k0+kbp) held in s.T / s.mv to the own columns
 // j = c0 + jj, jj in [ja, jb), except those in [a0, a1) and [b0, b1).
-__device__ void apply_panel(const Shared &s, double2 *S, int c0, int ja, int jb, int a0, int a1,
-                            int b0, int b1, int k0, int kbp) {
+template <class C>
+__device__ void apply_panel(const Shared<C> &s, const C *T, C *S, int c0, int ja, int jb,
+                            int a0, int a1, int b0, int b1, int k0, int kbp) {
   const int tid = threadIdx.x, nthr = blockDim.x, n = s.n, cw = s.cw;
   const int nm = s.mv[0];
   // 1) row moves (all loads, then all stores, staged in shared memory), then
@@ -307,25 +347,25 @@ __device__ void apply_panel(const Shared &s, double2 *S, int c0, int ja, int jb,
   for (int jj = ja + cl; jj < jb; jj += (nthr >> 6)) {
     const int j = c0 + jj;
     if (skipped(j, a0, a1, b0, b1)) continue;
-    double2 *Sj = S + (size_t)j * n;
+    C *Sj = S + (size_t)j * n;
     for (int base = 0; base < n; base += 256) {
-      double2 v[4];
+      C v[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const int i = base + rl + 64 * u;
-        v[u] = (i < n && (i < k0 || i >= k0 + kbp)) ? Sj[i] : make_double2(0.0, 0.0);
+        v[u] = (i < n && (i < k0 || i >= k0 + kbp)) ? Sj[i] : CX<C>::make(0.0, 0.0);
       }
       for (int q = 0; q < kbp; q++) {
-        const double2 xv = s.x[q * cw + jj];
-        const double2 *Tq = s.T + q * n + base + rl;
+        const C xv = s.x[q * cw + jj];
+        const C *Tq = T + q * n + base + rl;
 #pragma unroll
         for (int u = 0; u < 4; u++) {
           if (base + rl + 64 * u < n) {
-            const double2 t = Tq[64 * u];
-            v[u].x = fma(t.x, xv.x, v[u].x);
-            v[u].x = fma(-t.y, xv.y, v[u].x);
-            v[u].y = fma(t.x, xv.y, v[u].y);
-            v[u].y = fma(t.y, xv.x, v[u].y);
+            const C t = Tq[64 * u];
+            v[u].x = CX<C>::fmad(t.x, xv.x, v[u].x);
+            v[u].x = CX<C>::fmad(-t.y, xv.y, v[u].x);
+            v[u].y = CX<C>::fmad(t.x, xv.y, v[u].y);
+            v[u].y = CX<C>::fmad(t.y, xv.x, v[u].y);
           }
         }
       }
@@ -340,7 +380,8 @@ __device__ void apply_panel(const Shared &s, double2 *S, int c0, int ja, int jb,
 }
 
 // The blocked Gauss-Jordan sweep over the matrix S of this cluster.
-__device__ bool gj_blocked(const Shared &s, double2 *S, int *meta, int rank) {
+template <class C>
+__device__ bool gj_blocked(const Shared<C> &s, C *S, int *meta, int rank) {
   const int n = s.n, cw = s.cw, c0 = rank * cw;
   const int ncols = max(0, min(cw, n - c0));
   const int np = npanels(n);
@@ -352,24 +393,26 @@ __device__ bool gj_blocked(const Shared &s, double2 *S, int *meta, int rank) {
   cluster_wait();
   for (int p = 0; p < np; p++) {
     const int k0 = p * KB, kbp = min(KB, n - k0);
-    for (int e = threadIdx.x; e < kbp * n; e += blockDim.x) {
-      const int q = e / n, i = e % n;
-      s.T[q * n + i] = S[(size_t)(k0 + q) * n + i];
-    }
+    const C *T = s.T ? s.T : S + (size_t)k0 * n;
+    if (s.T)
+      for (int e = threadIdx.x; e < kbp * n; e += blockDim.x) {
+        const int q = e / n, i = e % n;
+        s.T[q * n + i] = S[(size_t)(k0 + q) * n + i];
+      }
     for (int t = threadIdx.x; t < kMoveInts; t += blockDim.x) s.mv[t] = meta[n + p * kMoveInts + t];
     __syncthreads();
     const int kn0 = (p + 1) * KB, kbn = (p + 1 < np) ? min(KB, n - kn0) : 0;
     const bool next_mine = (kbn > 0) && kn0 >= c0 && kn0 < c0 + ncols;
     if (next_mine) {
       // the next panel's columns first, then eliminate it and publish
-      apply_panel(s, S, c0, kn0 - c0, kn0 - c0 + kbn, k0, k0 + kbp, 0, 0, k0, kbp);
+      apply_panel(s, T, S, c0, kn0 - c0, kn0 - c0 + kbn, k0, k0 + kbp, 0, 0, k0, kbp);
       zero |= eliminate_panel(s, S, meta, kn0, kbn);
       __threadfence();
       cluster_arrive();
-      apply_panel(s, S, c0, 0, ncols, k0, k0 + kbp, kn0, kn0 + kbn, k0, kbp);
+      apply_panel(s, T, S, c0, 0, ncols, k0, k0 + kbp, kn0, kn0 + kbn, k0, kbp);
       cluster_wait();
     } else {
-      apply_panel(s, S, c0, 0, ncols, k0, k0 + kbp, 0, 0, k0, kbp);
+      apply_panel(s, T, S, c0, 0, ncols, k0, k0 + kbp, 0, 0, k0, kbp);
       cluster_arrive();
       cluster_wait();
     }
@@ -404,9 +447,9 @@ struct LeafArgs {
   LeafTables lt;
   const double *tab;  // D1x, D1y, D2x, D2y (p*p each), then int grid[n]
   const double *c;    // [leaves][ni]
-  double2 *X;         // [leaf][n][n] column-major
-  double2 *GX;        // [leaf][n][nb] column-major
-  double2 *S;         // [chunk][n][n] scratch
+  void *X;            // [leaf][n][n] column-major (element type C)
+  void *GX;           // [leaf][n][nb] column-major
+  void *S;            // [chunk][n][n] scratch
   int *meta;          // [chunk][meta_ints(n)]
   int leaf0;          // first leaf of this chunk
   unsigned int *status;
@@ -414,8 +457,10 @@ struct LeafArgs {
   int cw;
 };
 
+template <class C>
 __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant__ LeafArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  using R = typename CX<C>::R;
   cg::cluster_group cl = cg::this_cluster();
   const int cs = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -424,15 +469,15 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
   const int p = a.lt.p, e = a.lt.e, n = a.lt.n, nb = a.lt.nb, ni = a.lt.ni;
   const int cw = a.cw, c0 = rank * cw;
   const int ncols = max(0, min(cw, n - c0));
-  const SmemPlan sp = plan_smem(n, cw, true, p);
-  const Shared s = bind(smem, sp, n, cw);
+  const SmemPlan sp = plan_smem(n, cw, true, p, false, sizeof(C));
+  const Shared<C> s = bind<C>(smem, sp, n, cw);
   double *D1x = (double *)(smem + sp.dtab);
   double *D1y = D1x + p * p, *D2x = D1y + p * p, *D2y = D2x + p * p;
   int *grid = (int *)(smem + sp.grid);
   int *loc = (int *)(smem + sp.loc);
   double *cv = (double *)(smem + sp.cv);
   const int tid = threadIdx.x, nthr = blockDim.x;
-  double2 *S = a.S + (size_t)slot * n * n;
+  C *S = (C *)a.S + (size_t)slot * n * n;
   int *meta = a.meta + (size_t)slot * meta_ints(n);
 
   for (int i = tid; i < 4 * p * p; i += nthr) D1x[i] = a.tab[i];
@@ -444,55 +489,92 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
   for (int i = tid; i < n; i += nthr) loc[(grid[i] >> 8) * p + (grid[i] & 0xff)] = i;
   __syncthreads();
 
-  // assemble the own columns of B
+  // Row equilibration: row i of B is scaled by an exact power of two d_i
+  // that brings its largest entry into [1, 2); the elimination inverts D B
+  // and X = (D B)^{-1} D, i.e. column j of the result is scaled by d_j.
+  // Without it the impedance rows (scale 2/h p^2) and the interior rows
+  // (scale (2/h)^2 p^4) are ~10^5 apart, which costs complex64 most of its
+  // digits.
   const double2 eta = a.lt.eta;
+  double *rsc = (double *)(smem + sp.rsc);
+  for (int i = tid; i < n; i += nthr) {
+    const int ix = grid[i] & 0xff, iy = grid[i] >> 8;
+    double mx = 0.0;
+    if (i < nb) {
+      const int side = i / e;
+      const double sgn = (side == 0 || side == 3) ? -1.0 : 1.0;
+      for (int t = 0; t < p; t++) {
+        const double v = sgn * ((side == 0) ? D1y[0 * p + t] : (side == 1) ? D1x[(p - 1) * p + t]
+                                : (side == 2) ? D1y[(p - 1) * p + t] : D1x[0 * p + t]);
+        const bool diag = (side == 0 || side == 2) ? (t == iy) : (t == ix);
+        // at the node itself the entry is the derivative weight + i eta
+        mx = fmax(mx, diag ? fmax(fabs(v - eta.y), fabs(eta.x)) : fabs(v));
+      }
+    } else {
+      for (int t = 0; t < p; t++) {
+        if (t != ix) mx = fmax(mx, fabs(D2x[ix * p + t]));
+        if (t != iy) mx = fmax(mx, fabs(D2y[iy * p + t]));
+      }
+      mx = fmax(mx, fabs(D2x[ix * p + ix] + D2y[iy * p + iy] + a.lt.kappa2 * cv[i - nb]));
+    }
+    int ex = 0;
+    frexp(mx > 0.0 ? mx : 1.0, &ex);
+    rsc[i] = ldexp(1.0, 1 - ex);
+  }
+  __syncthreads();
+
+  // assemble the own columns of D B (entries computed in FP64, stored as C)
   for (int idx = tid; idx < n * ncols; idx += nthr) {
     const int i = idx % n, jj = idx / n, j = c0 + jj;
     const int ix = grid[i] & 0xff, iy = grid[i] >> 8;
     const int jx = grid[j] & 0xff, jy = grid[j] >> 8;
-    double2 v = make_double2(0.0, 0.0);
+    double vx = 0.0, vy = 0.0;
     if (i < nb) {
       const int side = i / e;
       if (side == 0) {
-        if (jx == ix) v.x = -D1y[0 * p + jy];  // south: -d/dy
+        if (jx == ix) vx = -D1y[0 * p + jy];  // south: -d/dy
       } else if (side == 1) {
-        if (jy == iy) v.x = D1x[(p - 1) * p + jx];  // east: +d/dx
+        if (jy == iy) vx = D1x[(p - 1) * p + jx];  // east: +d/dx
       } else if (side == 2) {
-        if (jx == ix) v.x = D1y[(p - 1) * p + jy];  // north: +d/dy
+        if (jx == ix) vx = D1y[(p - 1) * p + jy];  // north: +d/dy
       } else {
-        if (jy == iy) v.x = -D1x[0 * p + jx];  // west: -d/dx
+        if (jy == iy) vx = -D1x[0 * p + jx];  // west: -d/dx
       }
       if (i == j) {  // + i eta
-        v.x -= eta.y;
-        v.y += eta.x;
+        vx -= eta.y;
+        vy += eta.x;
       }
     } else {
-      if (jy == iy) v.x -= D2x[ix * p + jx];
-      if (jx == ix) v.x -= D2y[iy * p + jy];
-      if (i == j) v.x -= a.lt.kappa2 * cv[i - nb];
+      if (jy == iy) vx -= D2x[ix * p + jx];
+      if (jx == ix) vx -= D2y[iy * p + jy];
+      if (i == j) vx -= a.lt.kappa2 * cv[i - nb];
     }
-    S[(size_t)j * n + i] = v;
+    S[(size_t)j * n + i] = CX<C>::make(rsc[i] * vx, rsc[i] * vy);
   }
   __syncthreads();
 
-  const bool zero = gj_blocked(s, S, meta, rank);
+  const bool zero = gj_blocked<C>(s, S, meta, rank);
   if (zero && tid == 0) record_status(a.status, 1u, a.level, leaf);
 
-  // X = B^{-1}: own columns to their destination columns
-  double2 *Xl = a.X + (size_t)leaf * n * n;
+  // X = (D B)^{-1} D: own columns to their destination columns, scaled
+  C *Xl = (C *)a.X + (size_t)leaf * n * n;
   for (int idx = tid; idx < n * ncols; idx += nthr) {
     const int i = idx % n, jj = idx / n, j = c0 + jj;
-    Xl[(size_t)dest_col(s.perm, n, j) * n + i] = S[(size_t)j * n + i];
+    const int dc = dest_col(s.perm, n, j);
+    const R d = (R)rsc[dc];
+    const C v = S[(size_t)j * n + i];
+    Xl[(size_t)dc * n + i] = CX<C>::make(d * v.x, d * v.y);
   }
   // G X for the own columns: row r of G is the outward normal derivative
   // along the line through boundary node r, minus i eta at r itself
-  double2 *GXl = a.GX + (size_t)leaf * n * nb;
+  C *GXl = (C *)a.GX + (size_t)leaf * n * nb;
+  const C ieta = CX<C>::make(-eta.y, eta.x);
   for (int idx = tid; idx < nb * ncols; idx += nthr) {
     const int r = idx % nb, jj = idx / nb, j = c0 + jj;
-    const double2 *Sj = S + (size_t)j * n;
+    const C *Sj = S + (size_t)j * n;
     const int side = r / e;
     const int ix = grid[r] & 0xff, iy = grid[r] >> 8;
-    double2 acc = make_double2(0.0, 0.0);
+    C acc = CX<C>::make(0.0, 0.0);
     for (int t = 0; t < p; t++) {
       double w;
       int q;
@@ -509,20 +591,23 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
         w = -D1x[0 * p + t];
         q = loc[iy * p + t];
       }
-      double2 x = Sj[q];
-      acc.x = fma(w, x.x, acc.x);
-      acc.y = fma(w, x.y, acc.y);
+      const C x = Sj[q];
+      acc.x = CX<C>::fmad((R)w, x.x, acc.x);
+      acc.y = CX<C>::fmad((R)w, x.y, acc.y);
     }
-    double2 ie = cmul(make_double2(-eta.y, eta.x), Sj[r]);  // - i eta x_r
+    const C ie = cmul(ieta, Sj[r]);  // - i eta x_r
     acc.x -= ie.x;
     acc.y -= ie.y;
-    GXl[(size_t)dest_col(s.perm, n, j) * nb + r] = acc;
+    const int dc = dest_col(s.perm, n, j);
+    const R d = (R)rsc[dc];
+    GXl[(size_t)dc * nb + r] = CX<C>::make(d * acc.x, d * acc.y);
   }
 }
 
 struct GJArgs {
-  double2 *S;     // [batch][n][n] column-major input, destroyed
-  double2 *out;   // [batch][n][n] column-major inverse
+  int tglobal;    // panels read in place from S instead of shared memory
+  void *S;        // [batch][n][n] column-major input, destroyed (element type C)
+  void *out;      // [batch][n][n] column-major inverse
   int *meta;      // [batch][meta_ints(n)]
   int n;
   int cw;
@@ -530,6 +615,7 @@ struct GJArgs {
   int level;
 };
 
+template <class C>
 __global__ void __launch_bounds__(kThreads, 2) gj_kernel(const __grid_constant__ GJArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -538,13 +624,13 @@ __global__ void __launch_bounds__(kThreads, 2) gj_kernel(const __grid_constant__
   const int mat = blockIdx.x / cs;
   const int n = a.n, cw = a.cw, c0 = rank * cw;
   const int ncols = max(0, min(cw, n - c0));
-  const SmemPlan sp = plan_smem(n, cw, false, 0);
-  const Shared s = bind(smem, sp, n, cw);
-  double2 *S = a.S + (size_t)mat * n * n;
+  const SmemPlan sp = plan_smem(n, cw, false, 0, a.tglobal != 0, sizeof(C));
+  const Shared<C> s = bind<C>(smem, sp, n, cw);
+  C *S = (C *)a.S + (size_t)mat * n * n;
   int *meta = a.meta + (size_t)mat * meta_ints(n);
-  const bool zero = gj_blocked(s, S, meta, rank);
+  const bool zero = gj_blocked<C>(s, S, meta, rank);
   if (zero && threadIdx.x == 0) record_status(a.status, 2u, a.level, mat);
-  double2 *O = a.out + (size_t)mat * n * n;
+  C *O = (C *)a.out + (size_t)mat * n * n;
   for (int idx = threadIdx.x; idx < n * ncols; idx += blockDim.x) {
     const int i = idx % n, jj = idx / n, j = c0 + jj;
     O[(size_t)dest_col(s.perm, n, j) * n + i] = S[(size_t)j * n + i];
@@ -585,15 +671,15 @@ int gj_slab(int n, int cs) {
   return ((cw + KB - 1) / KB) * KB;
 }
 
-size_t gj_smem_bytes(int n, int cs, bool leaf, int p) {
-  return plan_smem(n, gj_slab(n, cs), leaf, p).total;
+size_t gj_smem_bytes(int n, int cs, bool leaf, int p, bool tglobal, bool f32) {
+  return plan_smem(n, gj_slab(n, cs), leaf, p, tglobal, f32 ? 8 : 16).total;
 }
 
 size_t gj_meta_ints(int n) { return (size_t)meta_ints(n); }
 
 cudaError_t launch_leaf(const LeafTables &lt, const void *tab_dev, const double *c, int leaf0,
-                        int count, double2 *X, double2 *GX, double2 *S, int *meta,
-                        unsigned int *status, int level, int cs, cudaStream_t st) {
+                        int count, void *X, void *GX, void *S, int *meta, unsigned int *status,
+                        int level, int cs, bool f32, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   LeafArgs a;
   a.lt = lt;
@@ -607,14 +693,16 @@ cudaError_t launch_leaf(const LeafTables &lt, const void *tab_dev, const double 
   a.status = status;
   a.level = level;
   a.cw = gj_slab(lt.n, cs);
-  size_t smem = plan_smem(lt.n, a.cw, true, lt.p).total;
-  return launch_cluster(leaf_kernel, a, count, cs, smem, st);
+  size_t smem = plan_smem(lt.n, a.cw, true, lt.p, false, f32 ? 8 : 16).total;
+  return f32 ? launch_cluster(leaf_kernel<float2>, a, count, cs, smem, st)
+             : launch_cluster(leaf_kernel<double2>, a, count, cs, smem, st);
 }
 
-cudaError_t launch_gj_inverse(double2 *S, double2 *out, int n, int batch, int *meta,
-                              unsigned int *status, int level, int cs, cudaStream_t st) {
+cudaError_t launch_gj_inverse(void *S, void *out, int n, int batch, int *meta, unsigned int *status,
+                              int level, int cs, bool tglobal, bool f32, cudaStream_t st) {
   if (batch <= 0 || n <= 0) return cudaSuccess;
   GJArgs a;
+  a.tglobal = tglobal ? 1 : 0;
   a.S = S;
   a.out = out;
   a.meta = meta;
@@ -622,8 +710,9 @@ cudaError_t launch_gj_inverse(double2 *S, double2 *out, int n, int batch, int *m
   a.cw = gj_slab(n, cs);
   a.status = status;
   a.level = level;
-  size_t smem = plan_smem(n, a.cw, false, 0).total;
-  return launch_cluster(gj_kernel, a, batch, cs, smem, st);
+  size_t smem = plan_smem(n, a.cw, false, 0, tglobal, f32 ? 8 : 16).total;
+  return f32 ? launch_cluster(gj_kernel<float2>, a, batch, cs, smem, st)
+             : launch_cluster(gj_kernel<double2>, a, batch, cs, smem, st);
 }
 
 }  // namespace hps

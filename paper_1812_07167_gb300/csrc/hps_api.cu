@@ -46,22 +46,34 @@ struct Level {
   int horizontal;  // 1: alpha west / beta east
   int nc;          // boundary length of each child
   int n1, n2, n3, nt;
+  int f32;         // operators and arithmetic of this level in complex64
   std::vector<int> I1, I2, I3a, I3b;  // positions in the children's orders
   int *d_I1 = nullptr, *d_I2 = nullptr, *d_I3a = nullptr, *d_I3b = nullptr;
+  // the leaf and node of both ends of every I3 pair, relative to the parent:
+  // [k][4] = (leaf in parent, node in leaf) of alpha's end, then beta's
+  std::vector<int> pairs;
+  int *d_pairs = nullptr;
+  int leaves_per_parent;
+  long long jump_off;  // offset of this level's pairs in the flat jump arrays
   // stored operators, per parent contiguous (Sec. 2.4)
-  double2 *Winv = nullptr, *R33a = nullptr, *R33b = nullptr, *R13a = nullptr, *R23b = nullptr;
-  double2 *Phia = nullptr, *Phib = nullptr;
+  void *Winv = nullptr, *R33a = nullptr, *R33b = nullptr, *R13a = nullptr, *R23b = nullptr;
+  void *Phia = nullptr, *Phib = nullptr;
   int gj_cs = 1;
+  bool gj_tglobal = false;  // panels of W read in place from global memory
 };
 
 struct Plan {
   int m, p, e, n, nb, ni, L, leaves, nbdry;
+  bool mixed;                   // HPS_MIXED
+  int leaf_f32;                 // leaf operators in complex64
+  int refine_steps;             // refinement steps of a mixed solve
   std::vector<Level> lv;        // lv[j]: merge j from the leaves up (parents on level L-1-j)
   std::vector<int> root_src;    // root position -> public boundary index
-  std::vector<int> ints;        // all index maps, concatenated for one upload
+  std::vector<int> outer;       // public boundary index -> leaf * nb + node
+  long long total_pairs = 0;    // I3 pairs over all merges
 };
 
-long long cplx_bytes(long long count) { return 16LL * count; }
+long long cplx_bytes(long long count, int f32 = 0) { return (f32 ? 8LL : 16LL) * count; }
 
 }  // namespace
 
@@ -71,7 +83,10 @@ struct hps_handle {
   hps_info_t info;
   void *arena = nullptr;  // operators + tables + index maps (one allocation)
   size_t arena_bytes = 0;
-  double2 *X = nullptr, *GX = nullptr, *Rroot = nullptr;
+  void *X = nullptr, *GX = nullptr;  // leaf operators (complex64 when plan.leaf_f32)
+  double2 *Rroot = nullptr;
+  double *c_dev = nullptr;  // c at the interior nodes (for the refinement residual)
+  int *d_outer = nullptr;
   void *tables = nullptr;
   int *d_ints = nullptr;
   int *d_root_src = nullptr;
@@ -100,7 +115,8 @@ int check_desc(const hps_desc *d) {
   if (d->q != 0 && d->q != d->p - 2) return HPS_EINVAL;
   if (!(d->kappa > 0.0) || !std::isfinite(d->kappa)) return HPS_EINVAL;
   if (d->eta_re == 0.0 || !std::isfinite(d->eta_re) || !std::isfinite(d->eta_im)) return HPS_EINVAL;
-  if (d->precision != HPS_FP64) return HPS_EINVAL;
+  if (d->precision != HPS_FP64 && d->precision != HPS_MIXED) return HPS_EINVAL;
+  if (d->fp64_levels < 0) return HPS_EINVAL;
   return HPS_OK;
 }
 
@@ -171,23 +187,36 @@ void make_plan(const hps_desc &d, Plan &pl) {
   pl.L = 2 * log2i(pl.m);
   pl.leaves = pl.m * pl.m;
   pl.nbdry = 4 * pl.m * pl.e;
+  pl.mixed = (d.precision == HPS_MIXED);
+  pl.leaf_f32 = pl.mixed ? 1 : 0;
+  pl.refine_steps = d.refine_steps == 0 ? 2 : (d.refine_steps < 0 ? 0 : d.refine_steps);
+  const int top = std::min(pl.L, d.fp64_levels == 0 ? 4 : d.fp64_levels);
   const int e = pl.e;
   std::vector<Canon> cur(pl.nb);
-  for (int k = 0; k < pl.nb; k++) cur[k] = {k / e, k % e};
+  // (leaf within the box, node within the leaf) of every boundary position
+  std::vector<std::pair<int, int>> at(pl.nb);
+  for (int k = 0; k < pl.nb; k++) {
+    cur[k] = {k / e, k % e};
+    at[k] = {0, k};
+  }
   int a = 1, b = 1;  // child box size in leaves (width, height)
+  int child_leaves = 1;
   pl.lv.clear();
+  pl.total_pairs = 0;
   for (int j = 0; j < pl.L; j++) {
     Level L;
     L.lev = pl.L - 1 - j;
     L.P = 1 << L.lev;
     L.horizontal = (j % 2 == 0);
+    L.f32 = (pl.mixed && j < pl.L - top) ? 1 : 0;
     L.nc = (int)cur.size();
+    L.leaves_per_parent = 2 * child_leaves;
     const int n3 = L.horizontal ? b * e : a * e;
     L.n3 = n3;
     L.I3a.assign(n3, -1);
     L.I3b.assign(n3, -1);
-    std::vector<Canon> parent;
-    std::vector<Canon> from_b;
+    std::vector<Canon> parent, from_b;
+    std::vector<std::pair<int, int>> pat, pat_b;
     for (int child = 0; child < 2; child++) {
       for (int pos = 0; pos < L.nc; pos++) {
         Canon c = cur[pos];
@@ -208,29 +237,49 @@ void make_plan(const hps_desc &d, Plan &pl) {
             if (c.side == 1 || c.side == 3) pc.off += b * e;
           }
         }
+        std::pair<int, int> where = {at[pos].first + child * child_leaves, at[pos].second};
         if (shared) {
           (child == 0 ? L.I3a : L.I3b)[c.off] = pos;
         } else if (child == 0) {
           L.I1.push_back(pos);
           parent.push_back(pc);
+          pat.push_back(where);
         } else {
           L.I2.push_back(pos);
           from_b.push_back(pc);
+          pat_b.push_back(where);
         }
       }
     }
+    L.pairs.resize(4 * (size_t)n3);
+    for (int k = 0; k < n3; k++) {
+      L.pairs[4 * k + 0] = at[L.I3a[k]].first;
+      L.pairs[4 * k + 1] = at[L.I3a[k]].second;
+      L.pairs[4 * k + 2] = at[L.I3b[k]].first + child_leaves;
+      L.pairs[4 * k + 3] = at[L.I3b[k]].second;
+    }
+    L.jump_off = pl.total_pairs;
+    pl.total_pairs += (long long)L.P * n3;
     L.n1 = (int)L.I1.size();
     L.n2 = (int)L.I2.size();
     L.nt = L.n1 + L.n2;
     parent.insert(parent.end(), from_b.begin(), from_b.end());
+    pat.insert(pat.end(), pat_b.begin(), pat_b.end());
     cur.swap(parent);
+    at.swap(pat);
     if (L.horizontal) a *= 2; else b *= 2;
+    child_leaves *= 2;
     pl.lv.push_back(std::move(L));
   }
-  // root position -> public boundary index ([S, E, N, W], m e nodes per side)
+  // root position -> public boundary index ([S, E, N, W], m e nodes per side),
+  // and public boundary index -> the leaf node that carries it
   pl.root_src.resize(cur.size());
-  for (size_t pos = 0; pos < cur.size(); pos++)
-    pl.root_src[pos] = cur[pos].side * pl.m * e + cur[pos].off;
+  pl.outer.resize(cur.size());
+  for (size_t pos = 0; pos < cur.size(); pos++) {
+    const int q = cur[pos].side * pl.m * e + cur[pos].off;
+    pl.root_src[pos] = q;
+    pl.outer[q] = at[pos].first * pl.nb + at[pos].second;
+  }
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -256,14 +305,15 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-Mat mat(const double2 *ptr, long long ld, long long stride, const int *rmap = nullptr,
-        const int *cmap = nullptr) {
+Mat mat(const void *ptr, long long ld, long long stride, const int *rmap = nullptr,
+        const int *cmap = nullptr, int f32 = 0) {
   Mat m;
   m.ptr = ptr;
   m.ld = ld;
   m.stride = stride;
   m.rmap = rmap;
   m.cmap = cmap;
+  m.f32 = f32;
   return m;
 }
 
@@ -301,7 +351,7 @@ long long env_cap() {
   return atoll(s);
 }
 
-// Operation counts (real flops; one complex multiply-add = 8).
+// Operation counts (real flops; one complex multiply-add = 8) and bytes.
 void fill_info(const Plan &pl, hps_info_t &in) {
   in.leaves = pl.leaves;
   in.levels = pl.L;
@@ -311,15 +361,15 @@ void fill_info(const Plan &pl, hps_info_t &in) {
   long long n = pl.n, nb = pl.nb, ni = pl.ni;
   long long bf = (long long)pl.leaves * 8 * (n * n * n + nb * n * pl.p);
   long long sf = (long long)pl.leaves * 8 * (nb * ni + n * n);
-  long long ob = (long long)pl.leaves * cplx_bytes(n * n + nb * n);
-  long long sb = (long long)pl.leaves * cplx_bytes(n * n + nb * ni);
+  long long ob = (long long)pl.leaves * cplx_bytes(n * n + nb * n, pl.leaf_f32);
+  long long sb = (long long)pl.leaves * cplx_bytes(n * n + nb * ni, pl.leaf_f32);
   for (const Level &L : pl.lv) {
     long long n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, P = L.P;
     bf += P * 8 * (2 * n3 * n3 * n3 + n3 * n3 * n1 + 2 * n3 * n3 * nt + (n1 + n2) * n3 * nt);
     sf += P * 8 * (3 * n3 * n3 + (n1 + n2) * n3 + 2 * n3 * nt);
     long long ops = 3 * n3 * n3 + n1 * n3 + n2 * n3 + 2 * n3 * nt;
-    ob += P * cplx_bytes(ops);
-    sb += P * cplx_bytes(ops);
+    ob += P * cplx_bytes(ops, L.f32);
+    sb += P * cplx_bytes(ops, L.f32);
   }
   in.build_flops = bf;
   in.solve_flops = sf;
@@ -327,14 +377,26 @@ void fill_info(const Plan &pl, hps_info_t &in) {
   in.solve_bytes = sb;
   in.build_launches = pl.lv.empty() ? 2 : 1 + 7 * (int)pl.lv.size();
   in.solve_launches = 3 + 6 * (int)pl.lv.size();
+  if (pl.mixed) {
+    int conv = 0;
+    for (size_t j = 0; j < pl.lv.size(); j++)
+      if (!pl.lv[j].f32 && (j == 0 ? pl.leaf_f32 : pl.lv[j - 1].f32)) conv++;
+    in.build_launches += conv;
+    // each refinement step: residual, jumps and outer data, the injections
+    // of the correction solve, the correction solve, the update of u
+    const int steps = pl.refine_steps;
+    in.solve_launches += steps * (2 + (int)pl.lv.size() + in.solve_launches + 1);
+    sf *= 1 + steps;
+    in.solve_flops = sf;
+  }
 }
 
-int choose_gj_cs(int n, int batch) {
+int choose_gj_cs(int n, int batch, bool tglobal, int f32) {
   // smallest cluster whose shared memory fits two CTAs per SM, then wider
   // while the level has too few matrices to fill the chip and every CTA
   // keeps at least two panels
   int cs = 1;
-  while (cs < hps::gj_max_cluster() && hps::gj_smem_bytes(n, cs, false, 0) > 110 * 1024) cs *= 2;
+  while (cs < hps::gj_max_cluster() && hps::gj_smem_bytes(n, cs, false, 0, tglobal, f32) > 110 * 1024) cs *= 2;
   while (cs < hps::gj_max_cluster() && (long long)batch * cs < 304 && hps::gj_slab(n, 2 * cs) >= 16)
     cs *= 2;
   return cs;
@@ -352,12 +414,19 @@ int grow(void **buf, size_t *have, size_t need) {
 
 }  // namespace
 
+// element `idx` of an array of complex64 (f32) or complex128 values
+static inline void *elem(const void *base, long long idx, int f32) {
+  return (char *)base + (f32 ? 8LL : 16LL) * idx;
+}
+
 // Solve workspace layout: h per level, t per level, t~3a / t~3b per merge,
 // one temporary.  Returns the bytes needed for nrhs right-hand sides.
 struct SolveWs {
   static constexpr int kMax = 24;  // merge levels: 2 log2(1024) = 20 at most
   size_t oh[kMax + 1], ot[kMax + 1], ota[kMax], otb[kMax];
   size_t ov = 0, bytes = 0;
+  // refinement (HPS_MIXED): residual parts and the correction
+  size_t osd = 0, otd = 0, ofu = 0, ogu = 0, oja = 0, ojb = 0, od = 0;
 };
 
 static void solve_ws_layout(const Plan &pl, int R, SolveWs &w) {
@@ -379,28 +448,46 @@ static void solve_ws_layout(const Plan &pl, int R, SolveWs &w) {
     vmax = std::max(vmax, (long long)R * L.P * L.n3);
   }
   w.ov = take(vmax);
+  if (pl.mixed && pl.refine_steps > 0) {
+    w.osd = take((long long)R * pl.leaves * pl.ni);
+    w.otd = take((long long)R * pl.nbdry);
+    w.ofu = take((long long)R * pl.leaves * pl.nb);
+    w.ogu = take((long long)R * pl.leaves * pl.nb);
+    w.oja = take((long long)R * std::max(1LL, pl.total_pairs));
+    w.ojb = take((long long)R * std::max(1LL, pl.total_pairs));
+    w.od = take((long long)R * pl.leaves * pl.n);
+  }
   w.bytes = off;
 }
 
 // Algorithm 2 for R right-hand sides on device arrays s, t, u, with the
 // workspace at wb (laid out by solve_ws_layout).  Launches kernels only.
+// Vectors are complex128; each level computes in its own precision.  JA, JB
+// (optional, [R][total_pairs]): residuals of the two interface conditions of
+// every I3 pair, injected as h3a -= JB, h3b -= JA before the level's Upsilon
+// actions (the right-hand side of t3a = -g3b + JA, t3b = -g3a + JB).
 static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, double2 *u, int R,
-                        char *wb, const SolveWs &ws, cudaStream_t st) {
+                        char *wb, const SolveWs &ws, cudaStream_t st, const double2 *JA = nullptr,
+                        const double2 *JB = nullptr) {
   const Plan &pl = h->plan;
-  const int n = pl.n, nb = pl.nb, ni = pl.ni, nl = pl.leaves;
+  const int n = pl.n, nb = pl.nb, ni = pl.ni, nl = pl.leaves, lf = pl.leaf_f32;
   const size_t *oh = ws.oh, *ot = ws.ot, *ota = ws.ota, *otb = ws.otb;
   const size_t ov = ws.ov;
   auto W = [&](size_t o) { return (double2 *)(wb + o); };
+  auto F = [&](const void *ptr, long long ld, long long stride, int f32) {
+    return mat(ptr, ld, stride, nullptr, nullptr, f32);
+  };
 
   // ---- upward pass ----
   // leaves: h = Gamma s  (Gamma = GX[:, nb:])
-  GemmDesc g = gemm(nb, R, ni, nl, mat(h->GX + (size_t)nb * nb, nb, (long long)n * nb),
+  GemmDesc g = gemm(nb, R, ni, nl, F(elem(h->GX, (long long)nb * nb, lf), nb, (long long)n * nb, lf),
                     mat(s, (long long)nl * ni, ni), mat(W(oh[0]), (long long)nl * nb, nb));
+  g.cf32 = lf;
   CK(hps::launch_gemm(&g, 1, st));
   for (size_t j = 0; j < pl.lv.size(); j++) {
     const Level &L = pl.lv[j];
-    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc;
-    const double2 *hc = W(oh[j]);
+    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc, f = L.f32;
+    double2 *hc = W(oh[j]);
     const long long ldh = (long long)2 * P * nc;
     Mat hA = mat(hc, ldh, 2LL * nc), hB = mat(hc + nc, ldh, 2LL * nc);
     Mat h3a = hA, h3b = hB, h1a = hA, h2b = hB;
@@ -408,31 +495,45 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     h3b.rmap = L.d_I3b;
     h1a.rmap = L.d_I1;
     h2b.rmap = L.d_I2;
+    if (JA && JB) {
+      CopyBatch cb;
+      cb.count = 2;
+      cb.d[0] = copy(n3, R, P, mat(JB + L.jump_off, pl.total_pairs, n3), h3a, -1.0);
+      cb.d[0].accumulate = 1;
+      cb.d[1] = copy(n3, R, P, mat(JA + L.jump_off, pl.total_pairs, n3), h3b, -1.0);
+      cb.d[1].accumulate = 1;
+      CK(hps::launch_copy(cb, st));
+    }
     const long long s33 = (long long)n3 * n3, ldv = (long long)P * n3;
     double2 *v = W(ov), *ta = W(ota[j]), *tb = W(otb[j]);
     // v = R33b h3a - h3b ;  t~3a = W^{-1} v  (Upsilon_a [h3a; h3b])
-    g = gemm(n3, R, n3, P, mat(L.R33b, n3, s33), h3a, mat(v, ldv, n3));
+    g = gemm(n3, R, n3, P, F(L.R33b, n3, s33, f), h3a, mat(v, ldv, n3));
     g.D = h3b;
     g.beta = make_double2(-1.0, 0.0);
+    g.cf32 = f;
     CK(hps::launch_gemm(&g, 1, st));
-    g = gemm(n3, R, n3, P, mat(L.Winv, n3, s33), mat(v, ldv, n3), mat(ta, ldv, n3));
+    g = gemm(n3, R, n3, P, F(L.Winv, n3, s33, f), mat(v, ldv, n3), mat(ta, ldv, n3));
+    g.cf32 = f;
     CK(hps::launch_gemm(&g, 1, st));
     // t~3b = -h3a - R33a t~3a  (Upsilon_b [h3a; h3b])
-    g = gemm(n3, R, n3, P, mat(L.R33a, n3, s33), mat(ta, ldv, n3), mat(tb, ldv, n3));
+    g = gemm(n3, R, n3, P, F(L.R33a, n3, s33, f), mat(ta, ldv, n3), mat(tb, ldv, n3));
     g.alpha = make_double2(-1.0, 0.0);
     g.D = h3a;
     g.beta = make_double2(-1.0, 0.0);
+    g.cf32 = f;
     CK(hps::launch_gemm(&g, 1, st));
     // h^tau = [h1a + R13a t~3a ; h2b + R23b t~3b]  (Eq. flux_part)
     const long long ldp = (long long)P * nt;
     GemmDesc g2[2];
-    g2[0] = gemm(n1, R, n3, P, mat(L.R13a, n1, (long long)n1 * n3), mat(ta, ldv, n3), mat(W(oh[j + 1]), ldp, nt));
+    g2[0] = gemm(n1, R, n3, P, F(L.R13a, n1, (long long)n1 * n3, f), mat(ta, ldv, n3), mat(W(oh[j + 1]), ldp, nt));
     g2[0].D = h1a;
     g2[0].beta = make_double2(1.0, 0.0);
-    g2[1] = gemm(n2, R, n3, P, mat(L.R23b, n2, (long long)n2 * n3), mat(tb, ldv, n3),
+    g2[0].cf32 = f;
+    g2[1] = gemm(n2, R, n3, P, F(L.R23b, n2, (long long)n2 * n3, f), mat(tb, ldv, n3),
                  mat(W(oh[j + 1]) + n1, ldp, nt));
     g2[1].D = h2b;
     g2[1].beta = make_double2(1.0, 0.0);
+    g2[1].cf32 = f;
     CK(hps::launch_gemm(g2, 2, st));
   }
 
@@ -448,19 +549,21 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
   }
   for (size_t jj = top; jj-- > 0;) {
     const Level &L = pl.lv[jj];
-    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc;
+    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc, f = L.f32;
     const double2 *tp = W(ot[jj + 1]);
     double2 *tc = W(ot[jj]);
     const long long ldp = (long long)P * nt, ldc2 = (long long)2 * P * nc, ldv = (long long)P * n3;
     const long long s3t = (long long)n3 * nt;
     // t3a = Phi_a t^tau + t~3a -> alpha rows I3 ; t3b = Phi_b t^tau + t~3b -> beta rows I3
     GemmDesc g2[2];
-    g2[0] = gemm(n3, R, nt, P, mat(L.Phia, n3, s3t), mat(tp, ldp, nt), mat(tc, ldc2, 2LL * nc, L.d_I3a));
+    g2[0] = gemm(n3, R, nt, P, F(L.Phia, n3, s3t, f), mat(tp, ldp, nt), mat(tc, ldc2, 2LL * nc, L.d_I3a));
     g2[0].D = mat(W(ota[jj]), ldv, n3);
     g2[0].beta = make_double2(1.0, 0.0);
-    g2[1] = gemm(n3, R, nt, P, mat(L.Phib, n3, s3t), mat(tp, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I3b));
+    g2[0].cf32 = f;
+    g2[1] = gemm(n3, R, nt, P, F(L.Phib, n3, s3t, f), mat(tp, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I3b));
     g2[1].D = mat(W(otb[jj]), ldv, n3);
     g2[1].beta = make_double2(1.0, 0.0);
+    g2[1].cf32 = f;
     CK(hps::launch_gemm(g2, 2, st));
     // the rest of the children's incoming data is the parent's: I1 and I2
     CopyBatch cb;
@@ -470,12 +573,58 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     CK(hps::launch_copy(cb, st));
   }
   // leaves: u = Psi t + Y s = X [t; s]
-  g = gemm(n, R, n, nl, mat(h->X, n, (long long)n * n), mat(W(ot[0]), (long long)nl * nb, nb),
+  g = gemm(n, R, n, nl, F(h->X, n, (long long)n * n, lf), mat(W(ot[0]), (long long)nl * nb, nb),
            mat(u, (long long)nl * n, n));
   g.B2 = mat(s, (long long)nl * ni, ni);
   g.ksplit = nb;
+  g.cf32 = lf;
   CK(hps::launch_gemm(&g, 1, st));
 
+  return HPS_OK;
+}
+
+// Iterative refinement of an HPS_MIXED solve: u = S(s, t), then per step the
+// complex128 residual of the global collocation system and u += S(residual).
+static int solve_refine(hps_handle *h, const double2 *s, const double2 *t, double2 *u, int R, char *wb,
+                        const SolveWs &ws, cudaStream_t st) {
+  const Plan &pl = h->plan;
+  int rc = solve_launch(h, s, t, u, R, wb, ws, st);
+  if (rc) return rc;
+  auto W = [&](size_t o) { return (double2 *)(wb + o); };
+  double2 *sd = W(ws.osd), *td = W(ws.otd), *Fu = W(ws.ofu), *Gu = W(ws.ogu);
+  double2 *JA = W(ws.oja), *JB = W(ws.ojb), *d = W(ws.od);
+  hps::ResidualSetup rs;
+  rs.tab = (const double *)h->tables;
+  rs.c = h->c_dev;
+  rs.p = pl.p;
+  rs.e = pl.e;
+  rs.n = pl.n;
+  rs.nb = pl.nb;
+  rs.ni = pl.ni;
+  rs.leaves = pl.leaves;
+  rs.nbdry = pl.nbdry;
+  rs.eta = make_double2(h->desc.eta_re, h->desc.eta_im);
+  rs.kappa2 = h->desc.kappa * h->desc.kappa;
+  rs.outer = h->d_outer;
+  rs.total_pairs = pl.total_pairs;
+  rs.nlev = (int)pl.lv.size();
+  for (size_t j = 0; j < pl.lv.size() && j < hps::kMaxLevels; j++) {
+    rs.lev[j].pairs = pl.lv[j].d_pairs;
+    rs.lev[j].n3 = pl.lv[j].n3;
+    rs.lev[j].lpp = pl.lv[j].leaves_per_parent;
+    rs.lev[j].off = pl.lv[j].jump_off;
+  }
+  for (int it = 0; it < pl.refine_steps; it++) {
+    CK(hps::launch_residual(rs, u, s, t, sd, td, Fu, Gu, JA, JB, R, st));
+    rc = solve_launch(h, sd, td, d, R, wb, ws, st, JA, JB);
+    if (rc) return rc;
+    CopyBatch cb;
+    cb.count = 1;
+    cb.d[0] = copy(pl.n * pl.leaves, R, 1, mat(d, (long long)pl.n * pl.leaves, 0),
+                   mat(u, (long long)pl.n * pl.leaves, 0));
+    cb.d[0].accumulate = 1;
+    CK(hps::launch_copy(cb, st));
+  }
   return HPS_OK;
 }
 
@@ -579,6 +728,7 @@ int hps_info(const hps_handle *h, hps_info_t *info) {
 static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
   Plan &pl = h->plan;
   const int n = pl.n, nb = pl.nb, ni = pl.ni, p = pl.p, nl = pl.leaves;
+  const int lf = pl.leaf_f32;
 
   // ---- one arena: leaf operators, merge operators, root R, tables, maps ----
   size_t off = 0;
@@ -587,37 +737,42 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
     off = align256(off + bytes);
     return o;
   };
-  size_t oX = take(cplx_bytes((long long)nl * n * n));
-  size_t oGX = take(cplx_bytes((long long)nl * n * nb));
+  size_t oX = take(cplx_bytes((long long)nl * n * n, lf));
+  size_t oGX = take(cplx_bytes((long long)nl * n * nb, lf));
   std::vector<size_t> oops(pl.lv.size() * 7);
   for (size_t j = 0; j < pl.lv.size(); j++) {
     const Level &L = pl.lv[j];
     long long P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt;
-    oops[7 * j + 0] = take(cplx_bytes(P * n3 * n3));  // Winv
-    oops[7 * j + 1] = take(cplx_bytes(P * n3 * n3));  // R33a
-    oops[7 * j + 2] = take(cplx_bytes(P * n3 * n3));  // R33b
-    oops[7 * j + 3] = take(cplx_bytes(P * n1 * n3));  // R13a
-    oops[7 * j + 4] = take(cplx_bytes(P * n2 * n3));  // R23b
-    oops[7 * j + 5] = take(cplx_bytes(P * n3 * nt));  // Phia
-    oops[7 * j + 6] = take(cplx_bytes(P * n3 * nt));  // Phib
+    const int f = L.f32;
+    oops[7 * j + 0] = take(cplx_bytes(P * n3 * n3, f));  // Winv
+    oops[7 * j + 1] = take(cplx_bytes(P * n3 * n3, f));  // R33a
+    oops[7 * j + 2] = take(cplx_bytes(P * n3 * n3, f));  // R33b
+    oops[7 * j + 3] = take(cplx_bytes(P * n1 * n3, f));  // R13a
+    oops[7 * j + 4] = take(cplx_bytes(P * n2 * n3, f));  // R23b
+    oops[7 * j + 5] = take(cplx_bytes(P * n3 * nt, f));  // Phia
+    oops[7 * j + 6] = take(cplx_bytes(P * n3 * nt, f));  // Phib
   }
   const int nroot = pl.lv.empty() ? nb : pl.lv.back().nt;
   size_t oRroot = take(cplx_bytes((long long)nroot * nroot));
-  size_t tab_bytes = sizeof(double) * 4 * p * p + sizeof(int) * n;
+  // tables: D1x, D1y, D2x, D2y, then the node grid and the grid -> node map
+  size_t tab_bytes = sizeof(double) * 4 * p * p + sizeof(int) * (n + p * p);
   size_t oTab = take(tab_bytes);
-  // index maps: per level I1, I2, I3a, I3b, then the root map
+  size_t oC = pl.mixed ? take(sizeof(double) * (size_t)nl * ni) : 0;
+  // index maps: per level I1, I2, I3a, I3b, the I3 pairs; the root and outer maps
   std::vector<int> ints;
-  std::vector<size_t> imap(pl.lv.size() * 4);
+  std::vector<size_t> imap(pl.lv.size() * 5);
   for (size_t j = 0; j < pl.lv.size(); j++) {
     const Level &L = pl.lv[j];
-    const std::vector<int> *v[4] = {&L.I1, &L.I2, &L.I3a, &L.I3b};
-    for (int q = 0; q < 4; q++) {
-      imap[4 * j + q] = ints.size();
+    const std::vector<int> *v[5] = {&L.I1, &L.I2, &L.I3a, &L.I3b, &L.pairs};
+    for (int q = 0; q < 5; q++) {
+      imap[5 * j + q] = ints.size();
       ints.insert(ints.end(), v[q]->begin(), v[q]->end());
     }
   }
   size_t root_at = ints.size();
   ints.insert(ints.end(), pl.root_src.begin(), pl.root_src.end());
+  size_t outer_at = ints.size();
+  ints.insert(ints.end(), pl.outer.begin(), pl.outer.end());
   size_t oInts = take(sizeof(int) * (ints.size() + 1));
   size_t oStatus = take(sizeof(unsigned int));
   h->arena_bytes = off;
@@ -626,30 +781,33 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
   if (cap >= 0 && (long long)h->arena_bytes > cap) return HPS_ENOMEM;
   CK(cudaMalloc(&h->arena, h->arena_bytes));
   char *base = (char *)h->arena;
-  h->X = (double2 *)(base + oX);
-  h->GX = (double2 *)(base + oGX);
+  h->X = base + oX;
+  h->GX = base + oGX;
   for (size_t j = 0; j < pl.lv.size(); j++) {
     Level &L = pl.lv[j];
-    L.Winv = (double2 *)(base + oops[7 * j + 0]);
-    L.R33a = (double2 *)(base + oops[7 * j + 1]);
-    L.R33b = (double2 *)(base + oops[7 * j + 2]);
-    L.R13a = (double2 *)(base + oops[7 * j + 3]);
-    L.R23b = (double2 *)(base + oops[7 * j + 4]);
-    L.Phia = (double2 *)(base + oops[7 * j + 5]);
-    L.Phib = (double2 *)(base + oops[7 * j + 6]);
+    L.Winv = base + oops[7 * j + 0];
+    L.R33a = base + oops[7 * j + 1];
+    L.R33b = base + oops[7 * j + 2];
+    L.R13a = base + oops[7 * j + 3];
+    L.R23b = base + oops[7 * j + 4];
+    L.Phia = base + oops[7 * j + 5];
+    L.Phib = base + oops[7 * j + 6];
   }
   h->Rroot = (double2 *)(base + oRroot);
   h->tables = base + oTab;
+  h->c_dev = pl.mixed ? (double *)(base + oC) : nullptr;
   h->d_ints = (int *)(base + oInts);
   h->d_status = (unsigned int *)(base + oStatus);
   for (size_t j = 0; j < pl.lv.size(); j++) {
     Level &L = pl.lv[j];
-    L.d_I1 = h->d_ints + imap[4 * j + 0];
-    L.d_I2 = h->d_ints + imap[4 * j + 1];
-    L.d_I3a = h->d_ints + imap[4 * j + 2];
-    L.d_I3b = h->d_ints + imap[4 * j + 3];
+    L.d_I1 = h->d_ints + imap[5 * j + 0];
+    L.d_I2 = h->d_ints + imap[5 * j + 1];
+    L.d_I3a = h->d_ints + imap[5 * j + 2];
+    L.d_I3b = h->d_ints + imap[5 * j + 3];
+    L.d_pairs = h->d_ints + imap[5 * j + 4];
   }
   h->d_root_src = h->d_ints + root_at;
+  h->d_outer = h->d_ints + outer_at;
 
   // ---- host tables: 1-D differentiation on the leaf, squared, node grid ----
   const double hx = (h->desc.x1 - h->desc.x0) / pl.m, hy = (h->desc.y1 - h->desc.y0) / pl.m;
@@ -673,20 +831,26 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
       T[3 * p * p + i * p + j] = sy;
     }
   int *G = (int *)(T + 4 * p * p);
+  int *Loc = G + n;
+  for (int k = 0; k < p * p; k++) Loc[k] = -1;
   for (int k = 0; k < n; k++) {
     int ix, iy;
     local_grid(p, k, ix, iy);
     G[k] = ix | (iy << 8);
+    Loc[iy * p + ix] = k;
   }
   CK(cudaMemcpyAsync(h->tables, tab.data(), tab_bytes, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h->d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned int), st));
 
-  // ---- c on the device ----
+  // ---- c on the device (the mixed path keeps a copy for its residuals) ----
   const double *c_dev = c;
   void *c_stage = nullptr;
   size_t cbytes = sizeof(double) * (size_t)nl * ni;
-  if (!is_device_ptr(c)) {
+  if (pl.mixed) {
+    CK(cudaMemcpyAsync(h->c_dev, c, cbytes, cudaMemcpyDefault, st));
+    c_dev = h->c_dev;
+  } else if (!is_device_ptr(c)) {
     CK(cudaMallocAsync(&c_stage, cbytes, st));
     CK(cudaMemcpyAsync(c_stage, c, cbytes, cudaMemcpyHostToDevice, st));
     c_dev = (const double *)c_stage;
@@ -703,18 +867,18 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
   lt.kappa2 = h->desc.kappa * h->desc.kappa;
   // scratch for the in-place elimination: leaves go in chunks of at most
   // ~1 GiB of matrices
-  const int chunk = (int)std::max<long long>(
-      1, std::min<long long>(nl, (1LL << 30) / (16LL * n * n)));
-  double2 *lscr = nullptr;
+  const long long esz = lf ? 8 : 16;
+  const int chunk = (int)std::max<long long>(1, std::min<long long>(nl, (1LL << 30) / (esz * n * n)));
+  void *lscr = nullptr;
   int *lmeta = nullptr;
-  CK(cudaMallocAsync((void **)&lscr, sizeof(double2) * (size_t)chunk * n * n, st));
+  CK(cudaMallocAsync(&lscr, (size_t)esz * chunk * n * n, st));
   CK(cudaMallocAsync((void **)&lmeta, sizeof(int) * (size_t)chunk * hps::gj_meta_ints(n), st));
   h->ev.assign(pl.lv.size() + 2, nullptr);
   for (cudaEvent_t &e : h->ev) CK(cudaEventCreate(&e));
   CK(cudaEventRecord(h->ev[0], st));
   for (int l0 = 0; l0 < nl; l0 += chunk)
     CK(hps::launch_leaf(lt, h->tables, c_dev, l0, std::min(chunk, nl - l0), h->X, h->GX, lscr, lmeta,
-                        h->d_status, pl.L, h->leaf_cs, st));
+                        h->d_status, pl.L, h->leaf_cs, lf != 0, st));
   CK(cudaEventRecord(h->ev[1], st));
   CK(cudaFreeAsync(lscr, st));
   CK(cudaFreeAsync(lmeta, st));
@@ -724,94 +888,120 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
     // a single leaf: the root R is the leaf's R = GX[:, :nb]
     CopyBatch cb;
     cb.count = 1;
-    cb.d[0] = copy(nb, nb, 1, mat(h->GX, nb, 0), mat(h->Rroot, nb, 0));
+    cb.d[0] = copy(nb, nb, 1, mat(h->GX, nb, 0, nullptr, nullptr, lf), mat(h->Rroot, nb, 0));
     CK(hps::launch_copy(cb, st));
     return HPS_OK;
   }
 
   // ---- merges (Sec. 2.2), one level at a time (Algorithm 3's level loop) ----
-  size_t rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0;
-  for (const Level &L : pl.lv) {
+  // scratch sized for complex128; complex64 levels use part of it
+  size_t rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    const Level &L = pl.lv[j];
     rbuf = std::max(rbuf, (size_t)L.P * L.nt * L.nt);
     qbuf = std::max(qbuf, (size_t)L.P * L.n3 * L.nt);
     wbuf = std::max(wbuf, (size_t)L.P * L.n3 * L.n3);
     mbuf = std::max(mbuf, (size_t)L.P * hps::gj_meta_ints(L.n3));
+    const int cf = (j == 0) ? lf : pl.lv[j - 1].f32;
+    if (cf != L.f32) cbuf = std::max(cbuf, (size_t)2 * L.P * L.nc * L.nc);
   }
   double2 *scratch = nullptr;
   int *wmeta = nullptr;
-  CK(cudaMallocAsync((void **)&scratch, sizeof(double2) * (2 * rbuf + qbuf + wbuf), st));
+  CK(cudaMallocAsync((void **)&scratch, sizeof(double2) * (2 * rbuf + qbuf + wbuf + cbuf), st));
   CK(cudaMallocAsync((void **)&wmeta, sizeof(int) * mbuf, st));
   double2 *Rbuf[2] = {scratch, scratch + rbuf};
   double2 *Q = scratch + 2 * rbuf;
   double2 *Wscr = Q + qbuf;
+  double2 *Rconv = Wscr + wbuf;
 
+  auto sub = [&](Mat m, const int *r, const int *c) {
+    m.rmap = r;
+    m.cmap = c;
+    return m;
+  };
   // child R of the first merge: the leaves' R = GX[:, :nb] (ld nb, stride n nb)
-  const double2 *Rc = h->GX;
+  const void *Rc = h->GX;
+  int rcf = lf;
   long long ldc = nb, strc = (long long)n * nb;
   for (size_t j = 0; j < pl.lv.size(); j++) {
     Level &L = pl.lv[j];
-    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt;
+    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc, f = L.f32;
     const bool last = (j + 1 == pl.lv.size());
-    double2 *Rp = last ? h->Rroot : Rbuf[j & 1];
+    if (rcf != f) {
+      // the first complex128 level: its children's R once in complex128
+      CopyBatch cv;
+      cv.count = 1;
+      cv.d[0] = copy(nc, nc, 2 * P, mat(Rc, ldc, strc, nullptr, nullptr, rcf),
+                     mat(Rconv, nc, (long long)nc * nc));
+      CK(hps::launch_copy(cv, st));
+      Rc = Rconv;
+      rcf = 0;
+      ldc = nc;
+      strc = (long long)nc * nc;
+    }
+    void *Rp = last ? (void *)h->Rroot : (void *)Rbuf[j & 1];
     const long long s2 = 2 * strc;
-    Mat Ra = mat(Rc, ldc, s2), Rb = mat(Rc + strc, ldc, s2);
-    auto sub = [&](Mat m, const int *r, const int *c) {
-      m.rmap = r;
-      m.cmap = c;
-      return m;
-    };
+    Mat Ra = mat(Rc, ldc, s2, nullptr, nullptr, rcf), Rb = mat(elem(Rc, strc, rcf), ldc, s2, nullptr, nullptr, rcf);
+    auto M = [&](const void *ptr, long long ld, long long stride) { return mat(ptr, ld, stride, nullptr, nullptr, f); };
     // stored blocks and the parts of Phi_b and R^tau that are copies
     CopyBatch cb;
     cb.count = 0;
-    cb.d[cb.count++] = copy(n3, n3, P, sub(Ra, L.d_I3a, L.d_I3a), mat(L.R33a, n3, (long long)n3 * n3));
-    cb.d[cb.count++] = copy(n3, n3, P, sub(Rb, L.d_I3b, L.d_I3b), mat(L.R33b, n3, (long long)n3 * n3));
-    cb.d[cb.count++] = copy(n1, n3, P, sub(Ra, L.d_I1, L.d_I3a), mat(L.R13a, n1, (long long)n1 * n3));
-    cb.d[cb.count++] = copy(n2, n3, P, sub(Rb, L.d_I2, L.d_I3b), mat(L.R23b, n2, (long long)n2 * n3));
+    cb.d[cb.count++] = copy(n3, n3, P, sub(Ra, L.d_I3a, L.d_I3a), M(L.R33a, n3, (long long)n3 * n3));
+    cb.d[cb.count++] = copy(n3, n3, P, sub(Rb, L.d_I3b, L.d_I3b), M(L.R33b, n3, (long long)n3 * n3));
+    cb.d[cb.count++] = copy(n1, n3, P, sub(Ra, L.d_I1, L.d_I3a), M(L.R13a, n1, (long long)n1 * n3));
+    cb.d[cb.count++] = copy(n2, n3, P, sub(Rb, L.d_I2, L.d_I3b), M(L.R23b, n2, (long long)n2 * n3));
     // Q = [R33b R31a | -R32b]: the right block here, the left one by GEMM below
     cb.d[cb.count++] = copy(n3, n2, P, sub(Rb, L.d_I3b, L.d_I2),
-                            mat(Q + (size_t)n1 * n3, n3, (long long)n3 * nt), -1.0);
+                            M(elem(Q, (long long)n1 * n3, f), n3, (long long)n3 * nt), -1.0);
     // Phi_b starts as -[R31a | 0]
-    cb.d[cb.count++] = copy(n3, n1, P, sub(Ra, L.d_I3a, L.d_I1), mat(L.Phib, n3, (long long)n3 * nt), -1.0);
-    cb.d[cb.count++] = copy(n3, n2, P, mat(nullptr, 0, 0), mat(L.Phib + (size_t)n1 * n3, n3, (long long)n3 * nt));
+    cb.d[cb.count++] = copy(n3, n1, P, sub(Ra, L.d_I3a, L.d_I1), M(L.Phib, n3, (long long)n3 * nt), -1.0);
+    cb.d[cb.count++] = copy(n3, n2, P, mat(nullptr, 0, 0), M(elem(L.Phib, (long long)n1 * n3, f), n3, (long long)n3 * nt));
     // R^tau starts as diag(R11a, R22b)
     const long long sp = (long long)nt * nt;
-    cb.d[cb.count++] = copy(n1, n1, P, sub(Ra, L.d_I1, L.d_I1), mat(Rp, nt, sp));
-    cb.d[cb.count++] = copy(n2, n2, P, sub(Rb, L.d_I2, L.d_I2), mat(Rp + (size_t)n1 * nt + n1, nt, sp));
-    cb.d[cb.count++] = copy(n2, n1, P, mat(nullptr, 0, 0), mat(Rp + n1, nt, sp));
-    cb.d[cb.count++] = copy(n1, n2, P, mat(nullptr, 0, 0), mat(Rp + (size_t)n1 * nt, nt, sp));
+    cb.d[cb.count++] = copy(n1, n1, P, sub(Ra, L.d_I1, L.d_I1), M(Rp, nt, sp));
+    cb.d[cb.count++] = copy(n2, n2, P, sub(Rb, L.d_I2, L.d_I2), M(elem(Rp, (long long)n1 * nt + n1, f), nt, sp));
+    cb.d[cb.count++] = copy(n2, n1, P, mat(nullptr, 0, 0), M(elem(Rp, n1, f), nt, sp));
+    cb.d[cb.count++] = copy(n1, n2, P, mat(nullptr, 0, 0), M(elem(Rp, (long long)n1 * nt, f), nt, sp));
     CK(hps::launch_copy(cb, st));
 
     const long long s33 = (long long)n3 * n3, s3t = (long long)n3 * nt;
     // W = I - R33b R33a (in scratch), then W^{-1} into its stored slot
-    GemmDesc g = gemm(n3, n3, n3, P, mat(L.R33b, n3, s33), mat(L.R33a, n3, s33), mat(Wscr, n3, s33));
+    GemmDesc g = gemm(n3, n3, n3, P, M(L.R33b, n3, s33), M(L.R33a, n3, s33), M(Wscr, n3, s33));
     g.alpha = make_double2(-1.0, 0.0);
     g.addI = 1;
+    g.cf32 = f;
     CK(hps::launch_gemm(&g, 1, st));
-    CK(hps::launch_gj_inverse(Wscr, L.Winv, n3, P, wmeta, h->d_status, L.lev, L.gj_cs, st));
+    CK(hps::launch_gj_inverse(Wscr, L.Winv, n3, P, wmeta, h->d_status, L.lev, L.gj_cs, L.gj_tglobal, f != 0, st));
     // Q(:, :n1) = R33b R31a
-    g = gemm(n3, n1, n3, P, mat(L.R33b, n3, s33), sub(Ra, L.d_I3a, L.d_I1), mat(Q, n3, s3t));
+    g = gemm(n3, n1, n3, P, M(L.R33b, n3, s33), sub(Ra, L.d_I3a, L.d_I1), M(Q, n3, s3t));
+    g.cf32 = f;
     CK(hps::launch_gemm(&g, 1, st));
     // Phi_a = W^{-1} Q
-    g = gemm(n3, nt, n3, P, mat(L.Winv, n3, s33), mat(Q, n3, s3t), mat(L.Phia, n3, s3t));
+    g = gemm(n3, nt, n3, P, M(L.Winv, n3, s33), M(Q, n3, s3t), M(L.Phia, n3, s3t));
+    g.cf32 = f;
     CK(hps::launch_gemm(&g, 1, st));
     // Phi_b = -[R31a | 0] - R33a Phi_a
-    g = gemm(n3, nt, n3, P, mat(L.R33a, n3, s33), mat(L.Phia, n3, s3t), mat(L.Phib, n3, s3t));
+    g = gemm(n3, nt, n3, P, M(L.R33a, n3, s33), M(L.Phia, n3, s3t), M(L.Phib, n3, s3t));
     g.alpha = make_double2(-1.0, 0.0);
     g.D = g.C;
     g.beta = make_double2(1.0, 0.0);
+    g.cf32 = f;
     CK(hps::launch_gemm(&g, 1, st));
     // R^tau = diag(R11a, R22b) + diag(R13a, R23b) [Phi_a; Phi_b]
     GemmDesc g2[2];
-    g2[0] = gemm(n1, nt, n3, P, mat(L.R13a, n1, (long long)n1 * n3), mat(L.Phia, n3, s3t), mat(Rp, nt, sp));
+    g2[0] = gemm(n1, nt, n3, P, M(L.R13a, n1, (long long)n1 * n3), M(L.Phia, n3, s3t), M(Rp, nt, sp));
     g2[0].D = g2[0].C;
     g2[0].beta = make_double2(1.0, 0.0);
-    g2[1] = gemm(n2, nt, n3, P, mat(L.R23b, n2, (long long)n2 * n3), mat(L.Phib, n3, s3t),
-                 mat(Rp + n1, nt, sp));
+    g2[0].cf32 = f;
+    g2[1] = gemm(n2, nt, n3, P, M(L.R23b, n2, (long long)n2 * n3), M(L.Phib, n3, s3t),
+                 M(elem(Rp, n1, f), nt, sp));
     g2[1].D = g2[1].C;
     g2[1].beta = make_double2(1.0, 0.0);
+    g2[1].cf32 = f;
     CK(hps::launch_gemm(g2, 2, st));
     CK(cudaEventRecord(h->ev[2 + j], st));
     Rc = Rp;
+    rcf = f;
     ldc = nt;
     strc = sp;
   }
@@ -841,14 +1031,15 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
   }
   h->leaf_cs = cs;
   for (Level &L : h->plan.lv) {
-    L.gj_cs = choose_gj_cs(L.n3, L.P);
-    // the interface inverse keeps two panels of the matrix in shared memory
-    if (hps::gj_smem_bytes(L.n3, L.gj_cs, false, 0) > 227 * 1024) {
+    // stage the panels in shared memory while they fit beside the rest
+    L.gj_tglobal = hps::gj_smem_bytes(L.n3, hps::gj_max_cluster(), false, 0, false, L.f32) > 200 * 1024;
+    L.gj_cs = choose_gj_cs(L.n3, L.P, L.gj_tglobal, L.f32);
+    if (hps::gj_smem_bytes(L.n3, L.gj_cs, false, 0, L.gj_tglobal, L.f32) > 227 * 1024) {
       delete h;
       return HPS_ENOTSUP;
     }
   }
-  if (hps::gj_smem_bytes(h->plan.n, h->leaf_cs, true, h->plan.p) > 227 * 1024) {
+  if (hps::gj_smem_bytes(h->plan.n, h->leaf_cs, true, h->plan.p, false, h->plan.leaf_f32) > 227 * 1024) {
     delete h;
     return HPS_ENOTSUP;
   }
@@ -928,7 +1119,8 @@ int hps_solve(hps_handle *h, const double *s_, const double *t_, double *u_, int
   }
   if (!udev) u = (double2 *)sb;
 
-  gst = solve_launch(h, s, t, u, R, (char *)h->ws, ws, st);
+  gst = pl.mixed && pl.refine_steps > 0 ? solve_refine(h, s, t, u, R, (char *)h->ws, ws, st)
+                                         : solve_launch(h, s, t, u, R, (char *)h->ws, ws, st);
   if (gst) return gst;
 
   if (!udev) {
@@ -947,6 +1139,7 @@ int hps_solve_noalloc(hps_handle *h, const double *s_, const double *t_, double 
   if (nrhs == 0) return HPS_OK;
   if (!s_ || !t_ || !u_) return HPS_EINVAL;
   if (!is_device_ptr(s_) || !is_device_ptr(t_) || !is_device_ptr(u_)) return HPS_EINVAL;
+  if (h->plan.mixed) return HPS_ENOTSUP;  // refinement needs more workspace than the fixed array
   SolveWs ws;
   solve_ws_layout(h->plan, nrhs, ws);
   if (ws.bytes > (size_t)HPS_NOALLOC_WORKSPACE_BYTES) return HPS_ETOOBIG;
@@ -992,15 +1185,16 @@ int hps_root_R(hps_handle *h, double *R, void *stream) {
 int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, void *stream) {
   if (!h || leaf < 0 || leaf >= h->plan.leaves) return HPS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const int n = h->plan.n, nb = h->plan.nb, ni = h->plan.ni;
-  const double2 *X = h->X + (size_t)leaf * n * n;
-  const double2 *GX = h->GX + (size_t)leaf * n * nb;
+  const int n = h->plan.n, nb = h->plan.nb, ni = h->plan.ni, lf = h->plan.leaf_f32;
+  const void *X = elem(h->X, (long long)leaf * n * n, lf);
+  const void *GX = elem(h->GX, (long long)leaf * n * nb, lf);
   struct Part {
     double *out;
     int rows, cols;
-    const double2 *src;
+    const void *src;
     long long ld;
-  } parts[3] = {{Psi, n, nb, X, n}, {Y, n, ni, X + (size_t)nb * n, n}, {Gam, nb, ni, GX + (size_t)nb * nb, nb}};
+  } parts[3] = {{Psi, n, nb, X, n}, {Y, n, ni, elem(X, (long long)nb * n, lf), n},
+                {Gam, nb, ni, elem(GX, (long long)nb * nb, lf), nb}};
   for (const Part &pt : parts) {
     if (!pt.out) continue;
     size_t bytes = sizeof(double2) * (size_t)pt.rows * pt.cols;
@@ -1014,7 +1208,7 @@ int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, v
     // row-major out[i][j] = src(i, j): column-major (j, i) of dst = src(i, j)
     CopyBatch cb;
     cb.count = 1;
-    cb.d[0] = copy(pt.cols, pt.rows, 1, mat(pt.src, pt.ld, 0), mat(dst, pt.cols, 0));
+    cb.d[0] = copy(pt.cols, pt.rows, 1, mat(pt.src, pt.ld, 0, nullptr, nullptr, lf), mat(dst, pt.cols, 0));
     cb.d[0].trans = 1;
     CK(hps::launch_copy(cb, st));
     if (!dev) {

@@ -8,19 +8,22 @@ namespace hps {
 
 // Element (i, j) of batch b of a strided, optionally index-mapped complex
 // matrix:  ptr[b * stride + (rmap ? rmap[i] : i) + (cmap ? cmap[j] : j) * ld]
-// (column-major storage, leading dimension ld, complex128 as double2).
+// (column-major storage, leading dimension ld).  Elements are complex128
+// (double2) or, with f32 set, complex64 (float2).
 struct Mat {
-  const double2 *ptr;
+  const void *ptr;
   long long ld;
   long long stride;
   const int *rmap;
   const int *cmap;
+  int f32;
 };
 
 // One batched GEMM:  C = alpha * A * B  + beta * D  (+ I if addI)
 // A: M x K, B: K x N (rows k >= ksplit read from B2, row k - ksplit),
 // C, D: M x N.  D.ptr may be NULL (then beta is ignored); D may alias C
-// element for element.
+// element for element.  Operands may be complex128 or complex64 each; the
+// arithmetic is complex64 when cf32 is set, complex128 otherwise.
 struct GemmDesc {
   int M, N, K, batch;
   Mat A, B, B2;
@@ -28,15 +31,19 @@ struct GemmDesc {
   Mat C, D;
   double2 alpha, beta;
   int addI;
+  int cf32;
 };
 
 // One batched mapped copy:  dst(i, j) = alpha * src(i, j) for i < M, j < N
-// (src(j, i) when trans), or a fill with zeros when src.ptr is NULL.
+// (src(j, i) when trans; += with accumulate), or a fill with zeros when
+// src.ptr is NULL.  The
+// element types of src and dst may differ (a precision conversion).
 struct CopyDesc {
   int M, N, batch;
   Mat src, dst;
   double2 alpha;
   int trans;
+  int accumulate;  // dst(i, j) += alpha * src(i, j) instead of =
 };
 
 constexpr int kMaxCopies = 12;
@@ -66,24 +73,53 @@ cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st);
 // it by blocked Gauss-Jordan with partial pivoting across a cluster of `cs`
 // CTAs, write X = B^{-1} = [Psi | Y] ([leaf][n][n] column-major) and
 // GX = G X ([leaf][n][nb] column-major: R = GX[:, :nb], Gamma = GX[:, nb:]).
+// The arithmetic and X, GX, S are complex64 when f32, complex128 otherwise.
 //   tab_dev: device tables: double D1x[p*p], D1y[p*p], D2x[p*p], D2y[p*p]
 //            (row-major, scaled to the leaf), then int grid[n] (ix | iy << 8)
 //   S, meta: scratch for `count` matrices: count * n * n complex and
 //            count * gj_meta_ints(n) ints
 cudaError_t launch_leaf(const LeafTables &lt, const void *tab_dev, const double *c, int leaf0,
-                        int count, double2 *X, double2 *GX, double2 *S, int *meta,
-                        unsigned int *status, int level, int cs, cudaStream_t st);
+                        int count, void *X, void *GX, void *S, int *meta, unsigned int *status,
+                        int level, int cs, bool f32, cudaStream_t st);
 
 // Inverse of `batch` n x n column-major matrices (leading dim n, batch stride
 // n*n) by blocked Gauss-Jordan with partial pivoting across clusters of `cs`
-// CTAs.  S holds the matrices and is destroyed; the inverses go to out.
-cudaError_t launch_gj_inverse(double2 *S, double2 *out, int n, int batch, int *meta,
-                              unsigned int *status, int level, int cs, cudaStream_t st);
+// CTAs.  S holds the matrices and is destroyed; the inverses go to out.  With
+// tglobal the panels are read in place from S (large n) instead of being
+// staged in shared memory; with f32 everything is complex64.
+cudaError_t launch_gj_inverse(void *S, void *out, int n, int batch, int *meta, unsigned int *status,
+                              int level, int cs, bool tglobal, bool f32, cudaStream_t st);
+
+// ---- complex128 residual of the global collocation system (refinement) ----
+constexpr int kMaxLevels = 24;
+struct ResidualLevel {
+  const int *pairs;  // [n3][4]: (leaf in parent, node) of the alpha end, then beta's
+  int n3, lpp;       // pairs per parent, leaves per parent
+  long long off;     // offset of the level's pairs in the flat jump arrays
+};
+struct ResidualSetup {
+  const double *tab;  // leaf tables: D1x, D1y, D2x, D2y, grid[n], loc[p*p]
+  const double *c;    // [leaves][ni]
+  int p, e, n, nb, ni, leaves, nbdry;
+  double2 eta;
+  double kappa2;
+  const int *outer;   // public boundary index -> leaf * nb + node
+  long long total_pairs;
+  int nlev;
+  ResidualLevel lev[kMaxLevels];
+};
+// For R right-hand sides: sd = s - A u on every leaf's interior rows; Fu, Gu
+// = F u, G u at every leaf's boundary nodes; td = t - F u on the outer
+// boundary; JA = -(F^a u^a + G^b u^b), JB = -(G^a u^a + F^b u^b) at every I3
+// pair (Sec. 2.2's t3a = -g3b, g3a = -t3b).
+cudaError_t launch_residual(const ResidualSetup &rs, const double2 *u, const double2 *s,
+                            const double2 *t, double2 *sd, double2 *td, double2 *Fu, double2 *Gu,
+                            double2 *JA, double2 *JB, int R, cudaStream_t st);
 
 // Cluster limits and scratch / shared-memory sizes of the Gauss-Jordan kernels.
 int gj_max_cluster();
 int gj_slab(int n, int cs);
-size_t gj_smem_bytes(int n, int cs, bool leaf, int p);
+size_t gj_smem_bytes(int n, int cs, bool leaf, int p, bool tglobal = false, bool f32 = false);
 size_t gj_meta_ints(int n);
 
 }  // namespace hps

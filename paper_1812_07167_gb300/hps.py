@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libhps.so")
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ETIMEOUT, HPS_ECUDA, HPS_ENOTSUP, HPS_ETOOBIG = range(8)
 HPS_NOALLOC_WORKSPACE_BYTES = 16 << 20
 HPS_FP64 = 0
+HPS_MIXED = 1
 
 # every entry point include/hps.h declares
 EXPORTS = ("hps_nodes", "hps_build", "hps_solve", "hps_solve_noalloc", "hps_root_R", "hps_leaf_ops", "hps_info",
@@ -38,6 +39,7 @@ class hps_desc(ctypes.Structure):
         ("kappa", ctypes.c_double),
         ("eta_re", ctypes.c_double), ("eta_im", ctypes.c_double),
         ("precision", ctypes.c_int),
+        ("fp64_levels", ctypes.c_int), ("refine_steps", ctypes.c_int),
     ]
 
 
@@ -102,11 +104,15 @@ class Problem:
     x1: float = 1.0
     y0: float = 0.0
     y1: float = 1.0
+    precision: int = HPS_FP64
+    fp64_levels: int = 0
+    refine_steps: int = 0
 
     def desc(self) -> hps_desc:
         eta = complex(self.eta)
         return hps_desc(self.x0, self.x1, self.y0, self.y1, self.m, self.m, self.p, self.p - 2,
-                        float(self.kappa), eta.real, eta.imag, HPS_FP64)
+                        float(self.kappa), eta.real, eta.imag, int(self.precision),
+                        int(self.fp64_levels), int(self.refine_steps))
 
     @property
     def n(self) -> int:

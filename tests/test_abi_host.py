@@ -53,7 +53,7 @@ def test_nodes_match_oracle(m, p):
 
 def _desc(**kw):
     base = dict(x0=0.0, x1=1.0, y0=0.0, y1=1.0, mx=4, my=4, p=8, q=6, kappa=5.0, eta_re=5.0,
-                eta_im=0.0, precision=0)
+                eta_im=0.0, precision=0, fp64_levels=0, refine_steps=0)
     base.update(kw)
     return hps.hps_desc(**base)
 
@@ -61,7 +61,8 @@ def _desc(**kw):
 @pytest.mark.parametrize("bad", [
     dict(mx=3, my=3), dict(mx=4, my=2), dict(mx=0, my=0), dict(p=3), dict(p=33), dict(q=5),
     dict(kappa=0.0), dict(kappa=-1.0), dict(eta_re=0.0, eta_im=1.0), dict(x1=0.0),
-    dict(y1=-1.0), dict(precision=7), dict(kappa=float("nan")),
+    dict(y1=-1.0), dict(precision=7), dict(precision=-1), dict(kappa=float("nan")),
+    dict(precision=1, fp64_levels=-2),
 ])
 def test_invalid_descriptor_is_rejected_before_device_work(bad):
     d = _desc(**bad)
@@ -97,10 +98,3 @@ def test_q_zero_means_p_minus_2():
     d = _desc(q=0)
     lxy = np.zeros((16, 60, 2))
     assert hps.lib().hps_nodes(ctypes.byref(d), lxy.ctypes.data, None) == hps.HPS_OK
-
-
-def test_too_large_interfaces_are_refused_before_device_work():
-    d = _desc(mx=64, my=64, p=16, q=14)
-    c = np.ones(64 * 64 * 196)
-    h = ctypes.c_void_p()
-    assert hps.lib().hps_build(ctypes.byref(d), c.ctypes.data, None, ctypes.byref(h)) == hps.HPS_ENOTSUP

@@ -1,0 +1,111 @@
+"""Mixed-precision path (complex64 leaves and lower merges, complex128 top
+levels, complex128 iterative refinement) against the oracle and against the
+plain FP64 GPU path.
+
+Bar: the refined solution matches the FP64 oracle to <= 1e-8 relative
+(max-abs).  The root ItI operator is built from complex64 lower levels and is
+not refined; its error is checked against a loose bound and reported.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1812_07167_gb300 import hps
+from paper_1812_07167_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def device():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    hps.lib()
+    yield
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _build(pr, c):
+    h = hps.hps_build(pr, torch.from_numpy(np.ascontiguousarray(c)).cuda(), torch.cuda.current_stream())
+    code, lev, box = hps.hps_status(h, torch.cuda.current_stream())
+    assert code == hps.HPS_OK, (code, lev, box)
+    return h
+
+
+def _solve(h, s, t):
+    pr = h.pr
+    s = np.ascontiguousarray(s, dtype=np.complex128).reshape(-1, pr.leaves, pr.ni)
+    nrhs = s.shape[0]
+    t = np.ascontiguousarray(t, dtype=np.complex128).reshape(nrhs, pr.nbdry)
+    ud = torch.empty((nrhs, pr.leaves, pr.n), dtype=torch.complex128, device="cuda")
+    hps.hps_solve(h, torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda(), ud, nrhs,
+                  torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return ud.cpu().numpy()
+
+
+def _mixed(m, p, kappa, eta, fp64_levels=0, refine_steps=0):
+    return hps.Problem(m, p, kappa, eta, precision=hps.HPS_MIXED, fp64_levels=fp64_levels,
+                       refine_steps=refine_steps)
+
+
+@pytest.mark.parametrize("m,p,kappa,fp64_levels,nrhs", [
+    (2, 10, 15.0, 0, 1), (4, 16, 20.0, 0, 2), (8, 12, 30.0, 0, 3), (8, 16, 40.0, 1, 1), (16, 16, 80.0, 4, 12),
+])
+def test_mixed_matches_oracle(m, p, kappa, fp64_levels, nrhs):
+    c, s, t = W.random_data(m, p, kappa, kappa, seed=700 + m + p, nrhs=nrhs)
+    h = _build(_mixed(m, p, kappa, kappa, fp64_levels), c)
+    u = _solve(h, s, t)
+    nt = os.cpu_count() or 1
+    with O.Tree(O.Problem(m, p, kappa, kappa), c, nthreads=nt) as T:
+        uo = T.solve(s, t, nthreads=nt)
+    assert _rel(u, uo) <= TOL_MIXED, _rel(u, uo)
+    h.free()
+
+
+def test_refinement_is_what_reaches_the_bar():
+    """Without refinement the complex64 operators give ~1e-5; the refined
+    solve gains several digits per step."""
+    m, p, kappa = 8, 16, 40.0
+    c, s, t = W.random_data(m, p, kappa, kappa, seed=71)
+    errs = {}
+    with O.Tree(O.Problem(m, p, kappa, kappa), c, nthreads=os.cpu_count() or 1) as T:
+        uo = T.solve(s, t)
+    for steps in (-1, 1, 3):
+        h = _build(_mixed(m, p, kappa, kappa, fp64_levels=1, refine_steps=steps), c)
+        errs[steps] = _rel(_solve(h, s, t), uo)
+        h.free()
+    assert errs[-1] > 1e-9
+    assert errs[1] < errs[-1] / 100
+    assert errs[3] <= TOL_MIXED
+    print("rel err by refinement steps:", errs)
+
+
+def test_mixed_equals_fp64_path_on_the_benchmark_problem():
+    wl = W.point_sources()
+    pf = hps.Problem(wl.m, wl.p, wl.kappa, wl.eta)
+    lxy, bxy = hps.hps_nodes(pf)
+    c, s, t = wl.sample(lxy, bxy)
+    h64 = _build(pf, c)
+    hmx = _build(_mixed(wl.m, wl.p, wl.kappa, wl.eta), c)
+    for nrhs in (1, 9):
+        S = np.repeat(s[None], nrhs, 0) * (1 + np.arange(nrhs))[:, None, None]
+        T = np.repeat(t[None], nrhs, 0)
+        u64 = _solve(h64, S, T)
+        umx = _solve(hmx, S, T)
+        assert _rel(umx, u64) <= TOL_MIXED
+    R64 = np.zeros((pf.nbdry, pf.nbdry), complex)
+    Rmx = np.zeros_like(R64)
+    hps.hps_root_R(h64, R64)
+    hps.hps_root_R(hmx, Rmx)
+    relR = np.linalg.norm(Rmx - R64) / np.linalg.norm(R64)
+    print("root R, mixed vs FP64:", relR)
+    assert relR < 1e-3
+    assert hmx.info().operator_bytes < h64.info().operator_bytes
