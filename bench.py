@@ -294,6 +294,43 @@ def ours(args, rank, world, local_rank):
         e2e_total = float(tt.item())
     e2e_value = world * dof * len(e2e_ms) / (e2e_total / 1e3)
 
+    # ---- mixed-precision path on the same problem (complex64 leaves and lower
+    # merges, complex128 top levels and refinement) ----
+    pm = hps.Problem(wl.m, wl.p, wl.kappa, wl.eta, precision=hps.HPS_MIXED)
+    mb = []
+    for _ in range(4):
+        flush.zero_()
+        e0.record(st)
+        hm = hps.hps_build(pm, cd, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        mb.append(e0.elapsed_time(e1))
+        hm.free()
+    hm = hps.hps_build(pm, cd, st)
+    um = torch.empty_like(ud)
+    mlat = []
+    for k in range(60):
+        st.synchronize()
+        t0 = time.perf_counter()
+        hps.hps_solve(hm, sd, td, um, 1, st)
+        st.synchronize()
+        if k >= 10:
+            mlat.append((time.perf_counter() - t0) * 1e3)
+    Um = torch.empty_like(U)
+    hps.hps_solve(hm, S, T, Um, nb, st)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(5):
+        hps.hps_solve(hm, S, T, Um, nb, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    mbatch_ms = e0.elapsed_time(e1) / 5
+    u_mixed = um.cpu().numpy()[0]
+    R_mixed = np.zeros_like(R_gpu)
+    hps.hps_root_R(hm, R_mixed, st)
+    minfo = hm.info()
+    hm.free()
+
     if rank != 0:
         return
     leaf_flops = pr.leaves * 8 * (pr.n ** 3 + pr.nb * pr.n * pr.p)
@@ -330,6 +367,16 @@ def ours(args, rank, world, local_rank):
         "gpu_launches": args.steps * (info.build_launches + info.solve_launches),
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall1 - t_wall0,
+        "mixed": {
+            "what": "complex64 leaves and lower merges, complex128 top 4 levels, 2 complex128 refinement steps",
+            "build_dof_per_s": dof / (statistics.median(mb) / 1e3), "build_ms_median": statistics.median(mb),
+            "solve_rhs_per_s": nb / (mbatch_ms / 1e3),
+            "solve_latency_ms": {"p50": float(np.percentile(mlat, 50)), "p99": float(np.percentile(mlat, 99)),
+                                 "nrhs": 1, "samples": len(mlat)},
+            "rel_err_u_vs_fp64_gpu": float(np.abs(u_mixed - u_gpu).max() / np.abs(u_gpu).max()),
+            "rel_err_root_R_vs_fp64_gpu": float(np.linalg.norm(R_mixed - R_gpu) / np.linalg.norm(R_gpu)),
+            "operator_bytes": minfo.operator_bytes,
+        },
     }
     if world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -340,6 +387,8 @@ def ours(args, rank, world, local_rank):
             "u": float(np.abs(u_gpu - u_ora).max() / np.abs(u_ora).max()),
             "root_R": float(np.linalg.norm(R_gpu - R_ora) / np.linalg.norm(R_ora)),
         }
+        line["mixed"]["rel_err_u_vs_oracle"] = float(np.abs(u_mixed - u_ora).max() / np.abs(u_ora).max())
+        line["mixed"]["rel_err_root_R_vs_oracle"] = float(np.linalg.norm(R_mixed - R_ora) / np.linalg.norm(R_ora))
     print(json.dumps(line), flush=True)
 
 
