@@ -637,6 +637,74 @@ __global__ void __launch_bounds__(kThreads, 2) gj_kernel(const __grid_constant__
   }
 }
 
+// ---- wide variant: one launch per panel, a matrix spread over G CTAs ----
+// For levels with few matrices (the top of the tree) a cluster's 16 SMs at
+// most are too few.  Here every panel round is its own launch over the whole
+// chip: CTA 0 of each matrix applies panel p to the columns of panel p+1 and
+// eliminates that panel (the look-ahead of the cluster kernel); CTAs 1..G-1
+// apply panel p to their slabs of the remaining columns.  Launch order on the
+// stream is the barrier between rounds.  Phase -1 eliminates panel 0 only;
+// phase np writes the inverse out with the column permutation.
+struct WideArgs {
+  int tglobal;  // panels read in place from S instead of shared memory
+  void *S;      // [batch][n][n] column-major input, destroyed
+  void *out;    // [batch][n][n] column-major inverse
+  int *meta;    // [batch][meta_ints(n)]
+  int n, G, slab;
+  unsigned int *status;
+  int level;
+};
+
+template <class C>
+__global__ void __launch_bounds__(kThreads) gj_wide_kernel(const __grid_constant__ WideArgs a, int phase) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = a.n, G = a.G;
+  const int mat = blockIdx.x / G, g = blockIdx.x % G;
+  const int cwmax = a.slab > KB ? a.slab : KB;
+  const SmemPlan sp = plan_smem(n, cwmax, false, 0, a.tglobal != 0, sizeof(C));
+  const Shared<C> s = bind<C>(smem, sp, n, cwmax);
+  C *S = (C *)a.S + (size_t)mat * n * n;
+  int *meta = a.meta + (size_t)mat * meta_ints(n);
+  const int np = npanels(n);
+  // slab of CTA g >= 1: columns [c0, c0 + slab) of the matrix
+  const int c0 = (g - 1) * a.slab;
+  const int nc = (g >= 1) ? max(0, min(a.slab, n - c0)) : 0;
+  if (phase < 0) {
+    if (g == 0 && eliminate_panel<C>(s, S, meta, 0, min(KB, n)) && threadIdx.x == 0)
+      record_status(a.status, 2u, a.level, mat);
+    return;
+  }
+  if (phase >= np) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s.perm[t] = meta[t];
+    __syncthreads();
+    C *O = (C *)a.out + (size_t)mat * n * n;
+    for (int idx = threadIdx.x; idx < n * nc; idx += blockDim.x) {
+      const int i = idx % n, jj = idx / n, j = c0 + jj;
+      O[(size_t)dest_col(s.perm, n, j) * n + i] = S[(size_t)j * n + i];
+    }
+    return;
+  }
+  const int k0 = phase * KB, kbp = min(KB, n - k0);
+  const int kn0 = (phase + 1) * KB, kbn = (phase + 1 < np) ? min(KB, n - kn0) : 0;
+  const C *T = s.T ? s.T : S + (size_t)k0 * n;
+  if (s.T)
+    for (int e = threadIdx.x; e < kbp * n; e += blockDim.x) {
+      const int q = e / n, i = e % n;
+      s.T[q * n + i] = S[(size_t)(k0 + q) * n + i];
+    }
+  for (int t = threadIdx.x; t < kMoveInts; t += blockDim.x) s.mv[t] = meta[n + phase * kMoveInts + t];
+  __syncthreads();
+  if (g == 0) {
+    if (kbn > 0) {
+      apply_panel<C>(s, T, S, kn0, 0, kbn, k0, k0 + kbp, 0, 0, k0, kbp);
+      if (eliminate_panel<C>(s, S, meta, kn0, kbn) && threadIdx.x == 0)
+        record_status(a.status, 2u, a.level, mat);
+    }
+  } else if (nc > 0) {
+    apply_panel<C>(s, T, S, c0, 0, nc, k0, k0 + kbp, kn0, kn0 + kbn, k0, kbp);
+  }
+}
+
 template <typename Kern, typename Args>
 cudaError_t launch_cluster(Kern kern, const Args &args, int blocks, int cs, size_t smem,
                            cudaStream_t st) {
@@ -676,6 +744,40 @@ size_t gj_smem_bytes(int n, int cs, bool leaf, int p, bool tglobal, bool f32) {
 }
 
 size_t gj_meta_ints(int n) { return (size_t)meta_ints(n); }
+
+size_t gj_wide_smem_bytes(int n, int slab, bool f32, bool tglobal) {
+  return plan_smem(n, slab > KB ? slab : KB, false, 0, tglobal, f32 ? 8 : 16).total;
+}
+
+cudaError_t launch_gj_wide(void *S, void *out, int n, int batch, int G, int *meta,
+                           unsigned int *status, int level, bool f32, cudaStream_t st) {
+  if (batch <= 0 || n <= 0) return cudaSuccess;
+  if (G < 2) G = 2;
+  WideArgs a;
+  a.S = S;
+  a.out = out;
+  a.meta = meta;
+  a.n = n;
+  a.G = G;
+  a.slab = (n + G - 2) / (G - 1);
+  a.status = status;
+  a.level = level;
+  a.tglobal = gj_wide_smem_bytes(n, a.slab, f32, false) > 200 * 1024 ? 1 : 0;
+  const size_t smem = gj_wide_smem_bytes(n, a.slab, f32, a.tglobal != 0);
+  cudaError_t err = f32 ? cudaFuncSetAttribute(gj_wide_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                        : cudaFuncSetAttribute(gj_wide_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int np = npanels(n);
+  for (int phase = -1; phase <= np; phase++) {
+    if (f32)
+      gj_wide_kernel<float2><<<batch * G, kThreads, smem, st>>>(a, phase);
+    else
+      gj_wide_kernel<double2><<<batch * G, kThreads, smem, st>>>(a, phase);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t launch_leaf(const LeafTables &lt, const void *tab_dev, const double *c, int leaf0,
                         int count, void *X, void *GX, void *S, int *meta, unsigned int *status,

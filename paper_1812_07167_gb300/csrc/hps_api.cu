@@ -60,6 +60,7 @@ struct Level {
   void *Phia = nullptr, *Phib = nullptr;
   int gj_cs = 1;
   bool gj_tglobal = false;  // panels of W read in place from global memory
+  int gj_wide = 0;          // > 0: one launch per panel over P * gj_wide CTAs
 };
 
 struct Plan {
@@ -971,7 +972,10 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
     g.addI = 1;
     g.cf32 = f;
     CK(hps::launch_gemm(&g, 1, st));
-    CK(hps::launch_gj_inverse(Wscr, L.Winv, n3, P, wmeta, h->d_status, L.lev, L.gj_cs, L.gj_tglobal, f != 0, st));
+    if (L.gj_wide)
+      CK(hps::launch_gj_wide(Wscr, L.Winv, n3, P, L.gj_wide, wmeta, h->d_status, L.lev, f != 0, st));
+    else
+      CK(hps::launch_gj_inverse(Wscr, L.Winv, n3, P, wmeta, h->d_status, L.lev, L.gj_cs, L.gj_tglobal, f != 0, st));
     // Q(:, :n1) = R33b R31a
     g = gemm(n3, n1, n3, P, M(L.R33b, n3, s33), sub(Ra, L.d_I3a, L.d_I1), M(Q, n3, s3t));
     g.cf32 = f;
@@ -1019,7 +1023,6 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
   h->desc = *desc;
   if (h->desc.q == 0) h->desc.q = desc->p - 2;
   make_plan(h->desc, h->plan);
-  fill_info(h->plan, h->info);
   // leaf cluster: wider clusters split each leaf finer, which balances the
   // chip when there are few leaves (measured best: 8 CTAs a leaf for 16
   // leaves, 4 for 256, 1 from 1024 leaves on)
@@ -1034,7 +1037,13 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
     // stage the panels in shared memory while they fit beside the rest
     L.gj_tglobal = hps::gj_smem_bytes(L.n3, hps::gj_max_cluster(), false, 0, false, L.f32) > 200 * 1024;
     L.gj_cs = choose_gj_cs(L.n3, L.P, L.gj_tglobal, L.f32);
-    if (hps::gj_smem_bytes(L.n3, L.gj_cs, false, 0, L.gj_tglobal, L.f32) > 227 * 1024) {
+    // too few matrices to fill the chip with clusters: one launch per panel
+    // over about two CTAs per SM, each with a slab of at least 4 columns
+    if ((long long)L.P * L.gj_cs < 152 && L.n3 >= 64 && !getenv("HPS_NO_WIDE_GJ")) {
+      int G = (int)std::min<long long>((2 * 152 + L.P - 1) / L.P, L.n3 / 4 + 1);
+      L.gj_wide = std::max(2, G);
+    }
+    if (!L.gj_wide && hps::gj_smem_bytes(L.n3, L.gj_cs, false, 0, L.gj_tglobal, L.f32) > 227 * 1024) {
       delete h;
       return HPS_ENOTSUP;
     }
@@ -1043,6 +1052,9 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
     delete h;
     return HPS_ENOTSUP;
   }
+  fill_info(h->plan, h->info);
+  for (const Level &L : h->plan.lv)
+    if (L.gj_wide) h->info.build_launches += (L.n3 + 7) / 8 + 1;  // np + 2 launches instead of 1
   long long cap = env_cap();
   if (cap >= 0 && h->info.operator_bytes > cap) {
     delete h;

@@ -116,6 +116,13 @@ cudaError_t launch_residual(const ResidualSetup &rs, const double2 *u, const dou
                             const double2 *t, double2 *sd, double2 *td, double2 *Fu, double2 *Gu,
                             double2 *JA, double2 *JB, int R, cudaStream_t st);
 
+// The same inverse for few, larger matrices: one launch per 8-column panel
+// over batch * G CTAs (CTA 0 of a matrix eliminates the next panel, the
+// others update slabs of columns), so a single matrix uses the whole chip.
+cudaError_t launch_gj_wide(void *S, void *out, int n, int batch, int G, int *meta,
+                           unsigned int *status, int level, bool f32, cudaStream_t st);
+size_t gj_wide_smem_bytes(int n, int slab, bool f32, bool tglobal);
+
 // Cluster limits and scratch / shared-memory sizes of the Gauss-Jordan kernels.
 int gj_max_cluster();
 int gj_slab(int n, int cs);
