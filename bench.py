@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_1812_07167_gb300 import replicas  # noqa: E402
 from paper_1812_07167_gb300 import workloads as W  # noqa: E402
 
 METRIC = "HPS build DOF/s and solve RHS/s at stated rel. error; p50/p99 solve latency"
@@ -219,13 +220,9 @@ def ours(args, rank, world, local_rank):
         leaf_ms.append(hps.hps_build_times(hh)[0])
         hh.free()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
     dof = pr.leaves * pr.n
-    value = world * dof * args.steps / (total_ms / 1e3)
+    all_units, total_ms = replicas.aggregate(dof * args.steps, sum(step_ms), dev)
+    value = all_units / (total_ms / 1e3)
 
     # ---- separate build / solve figures (device-resident inputs) ----
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -287,12 +284,7 @@ def ours(args, rank, world, local_rank):
         hh.free()
         if k >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
-    e2e_total = sum(e2e_ms)
-    if dist:
-        tt = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_total = float(tt.item())
-    e2e_value = world * dof * len(e2e_ms) / (e2e_total / 1e3)
+    e2e_value = replicas.throughput(dof * len(e2e_ms), sum(e2e_ms), dev)
 
     # ---- mixed-precision path on the same problem (complex64 leaves and lower
     # merges, complex128 top levels and refinement) ----

@@ -102,6 +102,9 @@ typedef struct {
   long long solve_bytes;    /* operator bytes one solve reads */
   int build_launches;       /* kernels one hps_build launches */
   int solve_launches;       /* kernels one hps_solve launches */
+  long long build_scratch_bytes; /* transient device memory a build needs on top of
+                                    operator_bytes (released when it finishes) */
+  long long solve_ws_bytes_per_rhs; /* solve workspace per right-hand side */
 } hps_info_t;
 
 /* Node coordinates (host helper, no device work; Sec. 2.1 grid).
@@ -183,6 +186,11 @@ int hps_root_R(hps_handle *h, double *R, void *stream);
  *   complex row-major; any may be NULL.
  * Returns HPS_EINVAL for a leaf index out of range. */
 int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, void *stream);
+
+/* Sizes and operation counts of the solver hps_build would create for desc,
+ * without building it (host only, no device work): the admission check of a
+ * request loop.  Same HPS_EINVAL / HPS_ENOTSUP results as hps_build. */
+int hps_plan(const hps_desc *desc, hps_info_t *info);
 
 /* Sizes and operation counts of a built handle (host only, no device work). */
 int hps_info(const hps_handle *h, hps_info_t *info);

@@ -1014,12 +1014,11 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
   return HPS_OK;
 }
 
-int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **out) {
+// Planning shared by hps_build and hps_plan: tree, precisions, kernel
+// regimes, sizes.  Returns HPS_OK, HPS_EINVAL or HPS_ENOTSUP.
+static int plan_handle(hps_handle *h, const hps_desc *desc) {
   int st0 = check_desc(desc);
   if (st0) return st0;
-  if (!c || !out) return HPS_EINVAL;
-  hps_handle *h = new (std::nothrow) hps_handle();
-  if (!h) return HPS_ENOMEM;
   h->desc = *desc;
   if (h->desc.q == 0) h->desc.q = desc->p - 2;
   make_plan(h->desc, h->plan);
@@ -1043,24 +1042,64 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
       int G = (int)std::min<long long>((2 * 152 + L.P - 1) / L.P, L.n3 / 4 + 1);
       L.gj_wide = std::max(2, G);
     }
-    if (!L.gj_wide && hps::gj_smem_bytes(L.n3, L.gj_cs, false, 0, L.gj_tglobal, L.f32) > 227 * 1024) {
-      delete h;
+    if (!L.gj_wide && hps::gj_smem_bytes(L.n3, L.gj_cs, false, 0, L.gj_tglobal, L.f32) > 227 * 1024)
       return HPS_ENOTSUP;
-    }
   }
-  if (hps::gj_smem_bytes(h->plan.n, h->leaf_cs, true, h->plan.p, false, h->plan.leaf_f32) > 227 * 1024) {
-    delete h;
+  if (hps::gj_smem_bytes(h->plan.n, h->leaf_cs, true, h->plan.p, false, h->plan.leaf_f32) > 227 * 1024)
     return HPS_ENOTSUP;
-  }
   fill_info(h->plan, h->info);
   for (const Level &L : h->plan.lv)
     if (L.gj_wide) h->info.build_launches += (L.n3 + 7) / 8 + 1;  // np + 2 launches instead of 1
+  // transient build memory: the leaf elimination chunk, then the merge scratch
+  const Plan &pl = h->plan;
+  const long long esz = pl.leaf_f32 ? 8 : 16, n = pl.n;
+  const long long chunk = std::max<long long>(1, std::min<long long>(pl.leaves, (1LL << 30) / (esz * n * n)));
+  long long leaf_scr = esz * chunk * n * n + 4LL * chunk * (long long)hps::gj_meta_ints(pl.n);
+  long long rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
+  for (size_t j = 0; j < pl.lv.size(); j++) {
+    const Level &L = pl.lv[j];
+    rbuf = std::max(rbuf, (long long)L.P * L.nt * L.nt);
+    qbuf = std::max(qbuf, (long long)L.P * L.n3 * L.nt);
+    wbuf = std::max(wbuf, (long long)L.P * L.n3 * L.n3);
+    mbuf = std::max(mbuf, (long long)L.P * (long long)hps::gj_meta_ints(L.n3));
+    const int cf = (j == 0) ? pl.leaf_f32 : pl.lv[j - 1].f32;
+    if (cf != L.f32) cbuf = std::max(cbuf, 2LL * L.P * L.nc * L.nc);
+  }
+  const long long merge_scr = 16 * (2 * rbuf + qbuf + wbuf + cbuf) + 4 * mbuf;
+  h->info.build_scratch_bytes = std::max(leaf_scr, merge_scr) + (pl.mixed ? 0 : 8LL * pl.leaves * pl.ni);
+  SolveWs w1;
+  solve_ws_layout(pl, 1, w1);
+  h->info.solve_ws_bytes_per_rhs = (long long)w1.bytes;
+  return HPS_OK;
+}
+
+int hps_plan(const hps_desc *desc, hps_info_t *info) {
+  if (!info) return HPS_EINVAL;
+  hps_handle *h = new (std::nothrow) hps_handle();
+  if (!h) return HPS_ENOMEM;
+  int st = plan_handle(h, desc);
+  if (st == HPS_OK) *info = h->info;
+  delete h;
+  return st;
+}
+
+int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **out) {
+  int st0 = check_desc(desc);
+  if (st0) return st0;
+  if (!c || !out) return HPS_EINVAL;
+  hps_handle *h = new (std::nothrow) hps_handle();
+  if (!h) return HPS_ENOMEM;
+  int st = plan_handle(h, desc);
+  if (st != HPS_OK) {
+    delete h;
+    return st;
+  }
   long long cap = env_cap();
   if (cap >= 0 && h->info.operator_bytes > cap) {
     delete h;
     return HPS_ENOMEM;
   }
-  int st = build_impl(h, c, (cudaStream_t)stream);
+  st = build_impl(h, c, (cudaStream_t)stream);
   if (st != HPS_OK) {
     hps_free(h);
     return st;

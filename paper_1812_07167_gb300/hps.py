@@ -26,8 +26,8 @@ HPS_FP64 = 0
 HPS_MIXED = 1
 
 # every entry point include/hps.h declares
-EXPORTS = ("hps_nodes", "hps_build", "hps_solve", "hps_solve_noalloc", "hps_root_R", "hps_leaf_ops", "hps_info",
-           "hps_build_times", "hps_status", "hps_free", "hps_strerror")
+EXPORTS = ("hps_nodes", "hps_build", "hps_solve", "hps_solve_noalloc", "hps_root_R", "hps_leaf_ops",
+           "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
 
 
 class hps_desc(ctypes.Structure):
@@ -51,6 +51,7 @@ class hps_info_t(ctypes.Structure):
         ("build_flops", ctypes.c_longlong), ("solve_flops", ctypes.c_longlong),
         ("solve_bytes", ctypes.c_longlong),
         ("build_launches", ctypes.c_int), ("solve_launches", ctypes.c_int),
+        ("build_scratch_bytes", ctypes.c_longlong), ("solve_ws_bytes_per_rhs", ctypes.c_longlong),
     ]
 
 
@@ -80,6 +81,7 @@ def lib():
         L.hps_root_R.argtypes = [P, P, P]
         L.hps_leaf_ops.argtypes = [P, ctypes.c_int, P, P, P, P]
         L.hps_info.argtypes = [P, ctypes.POINTER(hps_info_t)]
+        L.hps_plan.argtypes = [D, ctypes.POINTER(hps_info_t)]
         L.hps_build_times.argtypes = [P, P, ctypes.c_int]
         L.hps_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.hps_free.argtypes = [P]
@@ -194,6 +196,14 @@ class Handle:
             self.free()
         except Exception:
             pass
+
+
+def hps_plan(pr: Problem) -> hps_info_t:
+    """Sizes of the solver hps_build would create, without building it."""
+    d = pr.desc()
+    out = hps_info_t()
+    _check(lib().hps_plan(ctypes.byref(d), ctypes.byref(out)), "hps_plan")
+    return out
 
 
 def hps_build(pr: Problem, c, stream=None) -> Handle:

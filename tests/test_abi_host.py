@@ -98,3 +98,19 @@ def test_q_zero_means_p_minus_2():
     d = _desc(q=0)
     lxy = np.zeros((16, 60, 2))
     assert hps.lib().hps_nodes(ctypes.byref(d), lxy.ctypes.data, None) == hps.HPS_OK
+
+
+def test_plan_reports_sizes_without_device_work():
+    d = _desc(mx=16, my=16, p=16, q=14, kappa=80.0, eta_re=80.0)
+    info = hps.hps_info_t()
+    assert hps.lib().hps_plan(ctypes.byref(d), ctypes.byref(info)) == hps.HPS_OK
+    assert info.leaves == 256 and info.levels == 8 and info.dof == 256 * 252
+    # Sec. 2.4 storage: X = [Psi | Y] and G X per leaf, 7 blocks per merge
+    assert 0.39e9 < info.operator_bytes < 0.41e9
+    assert info.build_scratch_bytes > 0 and info.solve_ws_bytes_per_rhs > 0
+    dm = _desc(mx=16, my=16, p=16, q=14, kappa=80.0, eta_re=80.0, precision=1)
+    im = hps.hps_info_t()
+    assert hps.lib().hps_plan(ctypes.byref(dm), ctypes.byref(im)) == hps.HPS_OK
+    assert im.operator_bytes < 0.6 * info.operator_bytes
+    bad = _desc(mx=3, my=3)
+    assert hps.lib().hps_plan(ctypes.byref(bad), ctypes.byref(info)) == hps.HPS_EINVAL
