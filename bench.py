@@ -384,6 +384,108 @@ def ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def serving_run(args, local_rank, precision):
+    """Config-5 serving workload: a 128 x 128-leaf solver (p = 16, kappa = eta
+    = 600, random medium, seed 3) resident in HBM, and a Poisson stream of
+    requests: 90% solves of 1..64 right-hand sides (8 seeded Gaussian sources
+    each, t = 0), 10% builds of 16 x 16 .. 64 x 64-leaf problems (kappa uniform
+    in [20, 200], random medium).  Capacity = requests per second with every
+    request queued at once; then the same requests arrive as a Poisson
+    process at 50% and 90% of that capacity."""
+    import torch
+
+    from paper_1812_07167_gb300 import hps, serve
+
+    dev = torch.device("cuda", local_rank)
+    m, p, kappa = args.serve_m, P_ORDER, 600.0
+    pr = hps.Problem(m, p, kappa, kappa, precision=precision)
+    lxy, _ = hps.hps_nodes(pr)
+    nb = pr.nb
+    xi, yi = lxy[:, nb:, 0], lxy[:, nb:, 1]
+    c = W.random_medium(3)(xi, yi)
+    st = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    h = hps.hps_build(pr, torch.from_numpy(c).to(dev), st)
+    code = hps.hps_status(h, st)[0]
+    build_s = time.perf_counter() - t0
+    if code != hps.HPS_OK:
+        raise RuntimeError(f"resident build: {hps.hps_strerror(code)}")
+    del c
+    pool_n, distinct = 64, 8
+    S = torch.empty((pool_n, pr.leaves, pr.ni), dtype=torch.complex128, device=dev)
+    for k in range(distinct):
+        src, _ = W.gaussian_sources(4000 + k)
+        S[k] = torch.from_numpy(src(xi, yi))
+    for k in range(distinct, pool_n):
+        S[k] = S[k % distinct]
+    T = torch.zeros((pool_n, pr.nbdry), dtype=torch.complex128, device=dev)
+    sched = W.request_stream(4, args.serve_requests, 1.0)
+    builds = {}
+    for k, d in enumerate(sched):
+        if d["kind"] == "build":
+            bp = hps.Problem(d["m"], p, d["kappa"], d["kappa"], precision=precision)
+            bx, _ = hps.hps_nodes(bp)
+            bc = W.random_medium(d["seed"])(bx[:, nb:, 0], bx[:, nb:, 1])
+            builds[k] = (bp, torch.from_numpy(bc).to(dev))
+    torch.cuda.synchronize()
+
+    def make(rate):
+        out = []
+        for k, d in enumerate(W.request_stream(4, args.serve_requests, rate)):
+            if d["kind"] == "solve":
+                r = d["nrhs"]
+                o = (7 * k) % (pool_n - r + 1)
+                out.append(serve.Request(k, d["arrival"], "solve", key="main", nrhs=r, s=S[o:o + r], t=T[:r]))
+            else:
+                bp, bc = builds[k]
+                out.append(serve.Request(k, d["arrival"], "build", problem=bp, c=bc))
+        return out
+
+    srv = serve.Server(max_batch_rhs=args.serve_max_rhs)
+    srv.add_solver("main", h)
+    # warm-up: one batch and one build of each size
+    warm = [serve.Request(0, 0.0, "solve", key="main", nrhs=4, s=S[:4], t=T[:4])]
+    for j, (bp, bc) in enumerate({bp.m: (bp, bc) for bp, bc in builds.values()}.values()):
+        warm.append(serve.Request(j + 1, 0.0, "build", problem=bp, c=bc))
+    drop = lambda r: setattr(r, "u", None)  # noqa: E731  (results are not kept)
+    srv.run(warm, on_done=drop)
+    srv.release_built()
+    torch.cuda.synchronize()
+    res = {"resident_build_s": build_s, "resident_operator_bytes": h.info().operator_bytes}
+    backlog = srv.run(make(0.0), on_done=drop)
+    srv.release_built()
+    cap = serve.summarize(backlog)
+    res["capacity"] = cap
+    for frac in (0.5, 0.9):
+        reqs = srv.run(make(frac * cap["req_per_s"]), on_done=drop)
+        srv.release_built()
+        res[f"load_{int(frac * 100)}"] = serve.summarize(reqs)
+    h.free()
+    return res
+
+
+def serving(args, local_rank):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    from paper_1812_07167_gb300 import hps
+
+    out = {"metric": "HPS serving: p50/p99 request latency and throughput under Poisson load",
+           "unit": "ms", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "helmholtz_serving_resident", "leaves": f"{args.serve_m}x{args.serve_m}",
+                      "p": P_ORDER, "q": P_ORDER - 2, "kappa": 600.0, "eta": 600.0,
+                      "c": "random medium, 32 Fourier modes, seed 3", "requests": args.serve_requests,
+                      "mix": "90% solves (nrhs U{1..64}, 8 Gaussian sources, t = 0), "
+                             "10% builds (m U{16,32,64}, kappa U[20,200])",
+                      "max_batch_rhs": args.serve_max_rhs, "arrivals": "Poisson, seed 4"}}
+    with ClockSampler(local_rank) as clk:
+        out["fp64"] = serving_run(args, local_rank, hps.HPS_FP64)
+        out["mixed"] = serving_run(args, local_rank, hps.HPS_MIXED)
+    out["value"] = out["fp64"]["load_90"]["solve_p99_ms"]
+    out["clocks"] = clk.summary()
+    print(json.dumps(out), flush=True)
+
+
 def kernel_hash():
     import hashlib
 
@@ -400,12 +502,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead of the step bench")
+    ap.add_argument("--serve-m", type=int, default=128)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-max-rhs", type=int, default=128)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.serve:
+        serving(args, local_rank)
         return
     if world > 1:
         import torch.distributed as dist

@@ -144,6 +144,32 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
  * handle or array, nrhs < 0), HPS_ENOMEM (workspace), HPS_ECUDA. */
 int hps_solve(hps_handle *h, const double *s, const double *t, double *u, int nrhs, void *stream);
 
+/* Several independent solve requests against one handle, done as ONE pass
+ * of Algorithm 2 whose right-hand sides are the requests' side by side
+ * (R = nrhs[0] + ... + nrhs[nreq-1] columns): the operators are read once for
+ * the whole batch.  This is the continuous-batching step of a request loop.
+ *   s[k], t[k], u[k]: request k's arrays in the layouts of hps_solve with
+ *     nrhs[k] right-hand sides; device or host memory, in any mix.  They are
+ *     gathered into the handle's staging buffer by copies on `stream`, and
+ *     each u[k] is written back from it.
+ *   nrhs[k] >= 0; requests with nrhs[k] == 0 are skipped.
+ * Column r of request k gives the same u as solving request k alone, up to
+ * the summation order of the kernels chosen for the batch width.  Every call
+ * on one handle must be ordered with the others (one stream per handle, or
+ * events): the staging and workspace belong to the handle.  When every
+ * pointer is device memory the call only enqueues; otherwise it waits for the
+ * stream before returning.  Returns HPS_EINVAL (NULL handle or array for a
+ * request with nrhs[k] > 0, nreq < 0, nrhs[k] < 0), HPS_ENOMEM, HPS_ECUDA. */
+int hps_solve_batch(hps_handle *h, int nreq, const double *const *s, const double *const *t,
+                    double *const *u, const int *nrhs, void *stream);
+
+/* Allocate now the handle's solve workspace and staging for calls of up to
+ * nrhs right-hand sides in total, so that such later hps_solve and
+ * hps_solve_batch calls allocate nothing (cudaMalloc/cudaFree synchronize the
+ * device, which stalls other streams' work).  Returns HPS_EINVAL for nrhs < 0,
+ * HPS_ENOMEM. */
+int hps_reserve(hps_handle *h, int nrhs);
+
 /* Size of the fixed device workspace behind hps_solve_noalloc (16 MiB).  It
  * is part of the library's device image, so every GPU that loads the library
  * holds it until the process exits. */

@@ -1184,6 +1184,67 @@ int hps_solve(hps_handle *h, const double *s_, const double *t_, double *u_, int
   return HPS_OK;
 }
 
+int hps_reserve(hps_handle *h, int nrhs) {
+  if (!h || nrhs < 0) return HPS_EINVAL;
+  const Plan &pl = h->plan;
+  SolveWs ws;
+  solve_ws_layout(pl, std::max(nrhs, 1), ws);
+  int gst = grow(&h->ws, &h->ws_bytes, ws.bytes);
+  if (gst) return gst;
+  const size_t R = (size_t)std::max(nrhs, 1);
+  return grow(&h->stage, &h->stage_bytes,
+              align256(sizeof(double2) * R * pl.leaves * pl.ni) + align256(sizeof(double2) * R * pl.nbdry) +
+                  align256(sizeof(double2) * R * pl.leaves * pl.n));
+}
+
+int hps_solve_batch(hps_handle *h, int nreq, const double *const *s_, const double *const *t_,
+                    double *const *u_, const int *nrhs, void *stream) {
+  if (!h || nreq < 0) return HPS_EINVAL;
+  if (nreq == 0) return HPS_OK;
+  if (!s_ || !t_ || !u_ || !nrhs) return HPS_EINVAL;
+  long long Rl = 0;
+  bool all_dev = true;
+  for (int k = 0; k < nreq; k++) {
+    if (nrhs[k] < 0) return HPS_EINVAL;
+    if (nrhs[k] == 0) continue;
+    if (!s_[k] || !t_[k] || !u_[k]) return HPS_EINVAL;
+    Rl += nrhs[k];
+    all_dev = all_dev && is_device_ptr(s_[k]) && is_device_ptr(t_[k]) && is_device_ptr(u_[k]);
+  }
+  if (Rl == 0) return HPS_OK;
+  if (Rl > (1LL << 30)) return HPS_EINVAL;
+  const int R = (int)Rl;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Plan &pl = h->plan;
+  int gst = hps_reserve(h, R);
+  if (gst) return gst;
+  SolveWs ws;
+  solve_ws_layout(pl, R, ws);
+  const size_t sc = (size_t)pl.leaves * pl.ni, tc = (size_t)pl.nbdry, uc = (size_t)pl.leaves * pl.n;
+  double2 *S = (double2 *)h->stage;
+  double2 *T = (double2 *)((char *)h->stage + align256(sizeof(double2) * R * sc));
+  double2 *U = (double2 *)((char *)T + align256(sizeof(double2) * R * tc));
+  // gather: request k's columns follow request k-1's
+  size_t col = 0;
+  for (int k = 0; k < nreq; k++) {
+    if (nrhs[k] == 0) continue;
+    CK(cudaMemcpyAsync(S + col * sc, s_[k], sizeof(double2) * nrhs[k] * sc, cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(T + col * tc, t_[k], sizeof(double2) * nrhs[k] * tc, cudaMemcpyDefault, st));
+    col += nrhs[k];
+  }
+  gst = pl.mixed && pl.refine_steps > 0 ? solve_refine(h, S, T, U, R, (char *)h->ws, ws, st)
+                                         : solve_launch(h, S, T, U, R, (char *)h->ws, ws, st);
+  if (gst) return gst;
+  col = 0;
+  for (int k = 0; k < nreq; k++) {
+    if (nrhs[k] == 0) continue;
+    CK(cudaMemcpyAsync(u_[k], U + col * uc, sizeof(double2) * nrhs[k] * uc, cudaMemcpyDefault, st));
+    col += nrhs[k];
+  }
+  if (!all_dev) CK(cudaStreamSynchronize(st));
+  return HPS_OK;
+}
+
 int hps_solve_noalloc(hps_handle *h, const double *s_, const double *t_, double *u_, int nrhs,
                       void *stream) {
   if (!h || nrhs < 0) return HPS_EINVAL;

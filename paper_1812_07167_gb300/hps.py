@@ -26,8 +26,8 @@ HPS_FP64 = 0
 HPS_MIXED = 1
 
 # every entry point include/hps.h declares
-EXPORTS = ("hps_nodes", "hps_build", "hps_solve", "hps_solve_noalloc", "hps_root_R", "hps_leaf_ops",
-           "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
+EXPORTS = ("hps_nodes", "hps_build", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
+           "hps_root_R", "hps_leaf_ops", "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
 
 
 class hps_desc(ctypes.Structure):
@@ -78,6 +78,8 @@ def lib():
         L.hps_build.argtypes = [D, P, P, ctypes.POINTER(ctypes.c_void_p)]
         L.hps_solve.argtypes = [P, P, P, P, ctypes.c_int, P]
         L.hps_solve_noalloc.argtypes = [P, P, P, P, ctypes.c_int, P]
+        L.hps_solve_batch.argtypes = [P, ctypes.c_int, P, P, P, P, P]
+        L.hps_reserve.argtypes = [P, ctypes.c_int]
         L.hps_root_R.argtypes = [P, P, P]
         L.hps_leaf_ops.argtypes = [P, ctypes.c_int, P, P, P, P]
         L.hps_info.argtypes = [P, ctypes.POINTER(hps_info_t)]
@@ -218,6 +220,26 @@ def hps_solve(h: Handle, s, t, u, nrhs: int, stream=None):
     """u[nrhs, leaves, p^2-4] (complex128) from s and t (numpy or torch)."""
     _check(lib().hps_solve(h.ptr, _ptr(s), _ptr(t), _ptr(u), int(nrhs), _stream(stream)), "hps_solve")
     return u
+
+
+def hps_solve_batch(h: Handle, s_list, t_list, u_list, nrhs_list, stream=None):
+    """One solve pass over several requests' right-hand sides side by side
+    (each request's arrays in the hps_solve layouts)."""
+    k = len(nrhs_list)
+    if not (len(s_list) == len(t_list) == len(u_list) == k):
+        raise ValueError("hps_solve_batch: one s, t, u and nrhs per request")
+    arr = ctypes.c_void_p * max(k, 1)
+    sp = arr(*[_ptr(x) for x in s_list])
+    tp = arr(*[_ptr(x) for x in t_list])
+    up = arr(*[_ptr(x) for x in u_list])
+    nr = (ctypes.c_int * max(k, 1))(*[int(x) for x in nrhs_list])
+    _check(lib().hps_solve_batch(h.ptr, k, sp, tp, up, nr, _stream(stream)), "hps_solve_batch")
+    return u_list
+
+
+def hps_reserve(h: Handle, nrhs: int):
+    """Allocate the handle's solve workspace for up to nrhs right-hand sides now."""
+    _check(lib().hps_reserve(h.ptr, int(nrhs)), "hps_reserve")
 
 
 def hps_solve_noalloc(h: Handle, s, t, u, nrhs: int, stream=None):

@@ -266,3 +266,32 @@ def random_data(m: int, p: int, kappa: float, eta: complex, seed: int, nrhs: int
     nt = nrhs * nb
     t = (r[k:k + nt] - 0.5 + 1j * (r[k + nt:k + 2 * nt] - 0.5)).reshape(nrhs, nb)
     return c, s, t
+
+
+def request_stream(seed: int, count: int, rate: float, solve_frac: float = 0.9, nrhs_max: int = 64,
+                   build_m=(16, 32, 64), kappa_range=(20.0, 200.0)):
+    """Arrival schedule of the serving workload (scheduling data only).
+
+    Arrivals form a Poisson process of ``rate`` requests per second
+    (exponential gaps of mean 1/rate; ``rate = 0`` puts every arrival at 0,
+    a backlog).  Each request is a solve with probability ``solve_frac``,
+    carrying nrhs uniform in 1..nrhs_max right-hand sides, else a build of
+    m x m leaves with m uniform in ``build_m`` and kappa uniform in
+    ``kappa_range``.  The draws other than the gaps do not depend on the
+    rate, so schedules at different loads hold the same requests.  Returns a
+    list of dicts with keys arrival, kind, nrhs, m, kappa, seed.
+    """
+    r = uniform(seed, 4 * count, offset=1 << 40)
+    gap = -np.log1p(-r[0::4])
+    arrival = np.cumsum(gap) / rate if rate > 0 else np.zeros(count)
+    out = []
+    for k in range(count):
+        if r[4 * k + 1] < solve_frac:
+            out.append(dict(arrival=float(arrival[k]), kind="solve",
+                            nrhs=1 + int(r[4 * k + 2] * nrhs_max), m=0, kappa=0.0, seed=seed * 1000 + k))
+        else:
+            lo, hi = kappa_range
+            out.append(dict(arrival=float(arrival[k]), kind="build", nrhs=0,
+                            m=int(build_m[int(r[4 * k + 2] * len(build_m))]),
+                            kappa=float(lo + (hi - lo) * r[4 * k + 3]), seed=seed * 1000 + k))
+    return out
