@@ -127,6 +127,26 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy);
  * device work. */
 int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **out);
 
+/* Build nprob independent solvers together (a ragged batch): Algorithm 1
+ * for every problem, with the leaves of all problems in one leaf launch and
+ * each merge level done once for every problem that has it.  The merge
+ * sizes of level j (counted from the leaves) depend on j and p only, so the
+ * problems' parents on that level form one batch of equal-size merges.
+ *   descs[k], c[k]: problem k as for hps_build.  Every desc must have the
+ *     same p, precision and fp64_levels (HPS_EINVAL otherwise); m, the
+ *     domain, kappa and eta may differ.
+ *   out[k] receives problem k's handle.  The handles share one device
+ *     allocation, released with the last of them; hps_free each one.
+ * A merge level runs as one launch per kernel over its problems, or as up
+ * to three where its problems differ in precision (HPS_MIXED) or some of
+ * them end at that level (their roots).  hps_status on any handle of the
+ * batch reports the batch's first failure; hps_build_times reports the
+ * batch's phases.  Results equal those of separate hps_build calls up to the
+ * summation order of the kernel shapes chosen for the batch.  Same errors as
+ * hps_build; on error no handle is returned. */
+int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, void *stream,
+                    hps_handle **out);
+
 /* Solve for nrhs right-hand sides (Algorithm 2: upward then downward pass).
  * For an HPS_MIXED handle the solve is iterative refinement: u = S(s, t), then
  * refine_steps times: the residual of the global collocation system (every

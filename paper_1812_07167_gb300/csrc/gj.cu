@@ -445,13 +445,13 @@ __device__ __forceinline__ void record_status(unsigned int *status, unsigned int
 
 struct LeafArgs {
   LeafTables lt;
-  const double *tab;  // D1x, D1y, D2x, D2y (p*p each), then int grid[n]
-  const double *c;    // [leaves][ni]
+  const LeafProb *probs;  // per-problem tables, c, kappa^2, eta (device)
+  int nprob;
   void *X;            // [leaf][n][n] column-major (element type C)
   void *GX;           // [leaf][n][nb] column-major
   void *S;            // [chunk][n][n] scratch
   int *meta;          // [chunk][meta_ints(n)]
-  int leaf0;          // first leaf of this chunk
+  long long leaf0;    // first leaf of this chunk
   unsigned int *status;
   int level;
   int cw;
@@ -465,7 +465,23 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
   const int cs = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int slot = blockIdx.x / cs;
-  const int leaf = a.leaf0 + slot;
+  const long long leaf = a.leaf0 + slot;
+  // the problem this leaf belongs to: the last one starting at or before it
+  int pk = 0;
+  for (int lo = 0, hi = a.nprob - 1; lo <= hi;) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(&a.probs[mid].leaf0) <= leaf) {
+      pk = mid;
+      lo = mid + 1;
+    } else {
+      hi = mid - 1;
+    }
+  }
+  const LeafProb &pb = a.probs[pk];
+  const double *tab = pb.tab;
+  const double kappa2 = pb.kappa2;
+  const double2 eta = pb.eta;
+  const double *cleaf = pb.c + (size_t)(leaf - pb.leaf0) * a.lt.ni;
   const int p = a.lt.p, e = a.lt.e, n = a.lt.n, nb = a.lt.nb, ni = a.lt.ni;
   const int cw = a.cw, c0 = rank * cw;
   const int ncols = max(0, min(cw, n - c0));
@@ -480,11 +496,11 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
   C *S = (C *)a.S + (size_t)slot * n * n;
   int *meta = a.meta + (size_t)slot * meta_ints(n);
 
-  for (int i = tid; i < 4 * p * p; i += nthr) D1x[i] = a.tab[i];
-  const int *gsrc = (const int *)(a.tab + 4 * p * p);
+  for (int i = tid; i < 4 * p * p; i += nthr) D1x[i] = tab[i];
+  const int *gsrc = (const int *)(tab + 4 * p * p);
   for (int i = tid; i < n; i += nthr) grid[i] = gsrc[i];
   for (int i = tid; i < p * p; i += nthr) loc[i] = -1;
-  for (int i = tid; i < ni; i += nthr) cv[i] = a.c[(size_t)leaf * ni + i];
+  for (int i = tid; i < ni; i += nthr) cv[i] = cleaf[i];
   __syncthreads();
   for (int i = tid; i < n; i += nthr) loc[(grid[i] >> 8) * p + (grid[i] & 0xff)] = i;
   __syncthreads();
@@ -495,7 +511,6 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
   // Without it the impedance rows (scale 2/h p^2) and the interior rows
   // (scale (2/h)^2 p^4) are ~10^5 apart, which costs complex64 most of its
   // digits.
-  const double2 eta = a.lt.eta;
   double *rsc = (double *)(smem + sp.rsc);
   for (int i = tid; i < n; i += nthr) {
     const int ix = grid[i] & 0xff, iy = grid[i] >> 8;
@@ -515,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
         if (t != ix) mx = fmax(mx, fabs(D2x[ix * p + t]));
         if (t != iy) mx = fmax(mx, fabs(D2y[iy * p + t]));
       }
-      mx = fmax(mx, fabs(D2x[ix * p + ix] + D2y[iy * p + iy] + a.lt.kappa2 * cv[i - nb]));
+      mx = fmax(mx, fabs(D2x[ix * p + ix] + D2y[iy * p + iy] + kappa2 * cv[i - nb]));
     }
     int ex = 0;
     frexp(mx > 0.0 ? mx : 1.0, &ex);
@@ -547,14 +562,14 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
     } else {
       if (jy == iy) vx -= D2x[ix * p + jx];
       if (jx == ix) vx -= D2y[iy * p + jy];
-      if (i == j) vx -= a.lt.kappa2 * cv[i - nb];
+      if (i == j) vx -= kappa2 * cv[i - nb];
     }
     S[(size_t)j * n + i] = CX<C>::make(rsc[i] * vx, rsc[i] * vy);
   }
   __syncthreads();
 
   const bool zero = gj_blocked<C>(s, S, meta, rank);
-  if (zero && tid == 0) record_status(a.status, 1u, a.level, leaf);
+  if (zero && tid == 0) record_status(a.status, 1u, a.level, (int)leaf);
 
   // X = (D B)^{-1} D: own columns to their destination columns, scaled
   C *Xl = (C *)a.X + (size_t)leaf * n * n;
@@ -779,14 +794,14 @@ cudaError_t launch_gj_wide(void *S, void *out, int n, int batch, int G, int *met
   return cudaSuccess;
 }
 
-cudaError_t launch_leaf(const LeafTables &lt, const void *tab_dev, const double *c, int leaf0,
+cudaError_t launch_leaf(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0,
                         int count, void *X, void *GX, void *S, int *meta, unsigned int *status,
                         int level, int cs, bool f32, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   LeafArgs a;
   a.lt = lt;
-  a.tab = (const double *)tab_dev;
-  a.c = c;
+  a.probs = probs;
+  a.nprob = nprob;
   a.X = X;
   a.GX = GX;
   a.S = S;

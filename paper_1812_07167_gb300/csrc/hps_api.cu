@@ -58,9 +58,6 @@ struct Level {
   // stored operators, per parent contiguous (Sec. 2.4)
   void *Winv = nullptr, *R33a = nullptr, *R33b = nullptr, *R13a = nullptr, *R23b = nullptr;
   void *Phia = nullptr, *Phib = nullptr;
-  int gj_cs = 1;
-  bool gj_tglobal = false;  // panels of W read in place from global memory
-  int gj_wide = 0;          // > 0: one launch per panel over P * gj_wide CTAs
 };
 
 struct Plan {
@@ -78,12 +75,23 @@ long long cplx_bytes(long long count, int f32 = 0) { return (f32 ? 8LL : 16LL) *
 
 }  // namespace
 
+// Device memory of one build: operators, tables and index maps of one
+// problem, or of every problem of a batch (hps_build_batch).  Released with
+// the last handle that refers to it.
+struct Shared {
+  void *arena = nullptr;
+  size_t bytes = 0;
+  int refs = 0;                 // handles referring to it (guarded by g_shared_mu)
+  std::vector<cudaEvent_t> ev;  // [before leaves, after leaves, after merge 0, ...]
+  int launches = 0;             // kernels the build launched
+};
+static std::mutex g_shared_mu;
+
 struct hps_handle {
   hps_desc desc;
   Plan plan;
   hps_info_t info;
-  void *arena = nullptr;  // operators + tables + index maps (one allocation)
-  size_t arena_bytes = 0;
+  Shared *sh = nullptr;
   void *X = nullptr, *GX = nullptr;  // leaf operators (complex64 when plan.leaf_f32)
   double2 *Rroot = nullptr;
   double *c_dev = nullptr;  // c at the interior nodes (for the refinement residual)
@@ -99,8 +107,6 @@ struct hps_handle {
   // staging for host arrays
   void *stage = nullptr;
   size_t stage_bytes = 0;
-  // phase events of the build: [before leaf, after leaf, after merge 0, ...]
-  std::vector<cudaEvent_t> ev;
 };
 
 namespace {
@@ -402,6 +408,35 @@ int choose_gj_cs(int n, int batch, bool tglobal, int f32) {
     cs *= 2;
   return cs;
 }
+
+// Kernel regime of the interface inverses of one launch: P matrices n3 x n3.
+struct GJChoice {
+  int cs = 1;            // cluster size of the cluster kernel
+  bool tglobal = false;  // cluster kernel: panels read in place from global memory
+  int wide = 0;          // > 0: one launch per panel over P * wide CTAs instead
+};
+
+// false when no regime fits this build's shared memory
+bool choose_gj(int n3, long long P, int f32, GJChoice &g) {
+  // stage the panels in shared memory while they fit beside the rest
+  g.tglobal = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, f32) > 200 * 1024;
+  g.cs = choose_gj_cs(n3, (int)std::min<long long>(P, 1 << 30), g.tglobal, f32);
+  const bool fits = hps::gj_smem_bytes(n3, g.cs, false, 0, g.tglobal, f32) <= 227 * 1024;
+  g.wide = 0;
+  // too few matrices to fill the chip with clusters (or a matrix too large
+  // for one cluster): one launch per panel over about two CTAs per SM, each
+  // with a slab of at least 4 columns
+  if (!fits || ((long long)P * g.cs < 152 && n3 >= 64 && !getenv("HPS_NO_WIDE_GJ"))) {
+    const long long G = std::min<long long>((2 * 152 + P - 1) / P, n3 / 4 + 1);
+    g.wide = (int)std::max<long long>(2, G);
+    const int slab = (n3 + g.wide - 2) / (g.wide - 1);
+    const bool tg = hps::gj_wide_smem_bytes(n3, slab, f32, false) > 200 * 1024;
+    return hps::gj_wide_smem_bytes(n3, slab, f32, tg) <= 227 * 1024;
+  }
+  return true;
+}
+
+int gj_launches(int n3, const GJChoice &g) { return g.wide ? (n3 + 7) / 8 + 2 : 1; }
 
 int grow(void **buf, size_t *have, size_t need) {
   if (*have >= need) return HPS_OK;
@@ -712,8 +747,18 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy) {
 
 int hps_free(hps_handle *h) {
   if (!h) return HPS_OK;
-  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
-  if (h->arena) cudaFree(h->arena);
+  if (Shared *sh = h->sh) {
+    bool last;
+    {
+      std::lock_guard<std::mutex> lock(g_shared_mu);
+      last = (--sh->refs == 0);
+    }
+    if (last) {
+      for (cudaEvent_t e : sh->ev) cudaEventDestroy(e);
+      if (sh->arena) cudaFree(sh->arena);
+      delete sh;
+    }
+  }
   if (h->ws) cudaFree(h->ws);
   if (h->stage) cudaFree(h->stage);
   delete h;
@@ -726,192 +771,347 @@ int hps_info(const hps_handle *h, hps_info_t *info) {
   return HPS_OK;
 }
 
-static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
-  Plan &pl = h->plan;
-  const int n = pl.n, nb = pl.nb, ni = pl.ni, p = pl.p, nl = pl.leaves;
-  const int lf = pl.leaf_f32;
+// Parents of one merge level that go through the level's kernels together:
+// the same precision and the same destination (the level's R buffer, or the
+// root block when these parents are roots).
+struct BuildRun {
+  long long p0;    // first parent of the run in the level's numbering
+  int P;           // parents
+  int f32;         // complex64 operators and arithmetic
+  bool finishing;  // the parents are the roots of their problems
+  int k0, nk;      // problems [k0, k0 + nk) in build order
+  size_t op[7];    // arena offsets: Winv, R33a, R33b, R13a, R23b, Phia, Phib
+  size_t rout;     // byte offset of the run's R^tau in the level's R buffer
+  size_t root;     // arena offset of the root block (finishing runs)
+  GJChoice gj;
+};
 
-  // ---- one arena: leaf operators, merge operators, root R, tables, maps ----
+// Children of a run: a contiguous range of the level below held by one run
+// there (or by the leaves), or several pieces that are gathered first.
+struct ChildPiece {
+  long long c0, count;  // children [c0, c0 + count) in the lower level's numbering
+  int run;              // run of the lower level holding them (-1: the leaves)
+};
+
+static std::vector<ChildPiece> child_pieces(const std::vector<std::vector<BuildRun>> &runs, int j,
+                                            const BuildRun &r) {
+  std::vector<ChildPiece> out;
+  const long long c0 = 2 * r.p0, c1 = 2 * (r.p0 + r.P);
+  if (j == 0) {
+    out.push_back({c0, c1 - c0, -1});
+    return out;
+  }
+  const std::vector<BuildRun> &lo = runs[j - 1];
+  for (size_t q = 0; q < lo.size(); q++) {
+    const long long a = std::max(c0, lo[q].p0), b = std::min(c1, lo[q].p0 + lo[q].P);
+    if (a < b) out.push_back({a, b - a, (int)q});
+  }
+  return out;
+}
+
+// Algorithm 1 for every handle of hs at once.  hs is in build order: tallest
+// tree first, all with the same p, precision and top-level count; each has
+// its plan.  Leaves of all problems are numbered problem after problem and
+// go through one leaf launch (chunked only to bound the scratch); merge
+// level j numbers the parents of every problem that has that level the same
+// way, so the parents of a problem's boxes on level j are boxes 2b, 2b+1 of
+// level j-1 in that numbering.  The index maps of level j depend on j only
+// (the box shape after j merges), so one copy of them serves every problem.
+// On success every handle refers to one Shared allocation.
+static int build_many(const std::vector<hps_handle *> &hs, const std::vector<const double *> &cin,
+                      cudaStream_t st) {
+  const int K = (int)hs.size();
+  const Plan &P0 = hs[0]->plan;
+  const int n = P0.n, nb = P0.nb, ni = P0.ni, p = P0.p, lf = P0.leaf_f32;
+  const int Lmax = P0.L;
+  const bool mixed = P0.mixed;
+  const long long esl = lf ? 8 : 16;
+  auto esz = [](int f32) { return f32 ? 8LL : 16LL; };
+
+  std::vector<long long> leaf0(K + 1, 0);
+  for (int k = 0; k < K; k++) leaf0[k + 1] = leaf0[k] + hs[k]->plan.leaves;
+  const long long NL = leaf0[K];
+
+  // ---- runs of every merge level, and each problem's first parent there ----
+  std::vector<std::vector<BuildRun>> runs(Lmax);
+  std::vector<std::vector<long long>> first(K);
+  for (int j = 0; j < Lmax; j++) {
+    long long pos = 0;
+    for (int k = 0; k < K && hs[k]->plan.L > j; k++) {
+      const Level &Lk = hs[k]->plan.lv[j];
+      const bool fin = (hs[k]->plan.L == j + 1);
+      std::vector<BuildRun> &R = runs[j];
+      if (!R.empty() && R.back().f32 == Lk.f32 && R.back().finishing == fin) {
+        R.back().P += Lk.P;
+        R.back().nk++;
+      } else {
+        BuildRun r{};
+        r.p0 = pos;
+        r.P = Lk.P;
+        r.f32 = Lk.f32;
+        r.finishing = fin;
+        r.k0 = k;
+        r.nk = 1;
+        R.push_back(r);
+      }
+      first[k].push_back(pos);
+      pos += Lk.P;
+    }
+    for (BuildRun &r : runs[j]) {
+      if (r.finishing && r.f32) return HPS_ENOTSUP;  // roots are complex128
+      if (!choose_gj(P0.lv[j].n3, r.P, r.f32, r.gj)) return HPS_ENOTSUP;
+    }
+  }
+
+  // ---- one arena: leaf operators, merge operators, roots, tables, maps ----
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
     off = align256(off + bytes);
     return o;
   };
-  size_t oX = take(cplx_bytes((long long)nl * n * n, lf));
-  size_t oGX = take(cplx_bytes((long long)nl * n * nb, lf));
-  std::vector<size_t> oops(pl.lv.size() * 7);
-  for (size_t j = 0; j < pl.lv.size(); j++) {
-    const Level &L = pl.lv[j];
-    long long P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt;
-    const int f = L.f32;
-    oops[7 * j + 0] = take(cplx_bytes(P * n3 * n3, f));  // Winv
-    oops[7 * j + 1] = take(cplx_bytes(P * n3 * n3, f));  // R33a
-    oops[7 * j + 2] = take(cplx_bytes(P * n3 * n3, f));  // R33b
-    oops[7 * j + 3] = take(cplx_bytes(P * n1 * n3, f));  // R13a
-    oops[7 * j + 4] = take(cplx_bytes(P * n2 * n3, f));  // R23b
-    oops[7 * j + 5] = take(cplx_bytes(P * n3 * nt, f));  // Phia
-    oops[7 * j + 6] = take(cplx_bytes(P * n3 * nt, f));  // Phib
+  const size_t oX = take((size_t)(esl * NL * n * n));
+  const size_t oGX = take((size_t)(esl * NL * n * nb));
+  for (int j = 0; j < Lmax; j++) {
+    const Level &S = P0.lv[j];
+    const long long n1 = S.n1, n2 = S.n2, n3 = S.n3, nt = S.nt;
+    const long long per[7] = {n3 * n3, n3 * n3, n3 * n3, n1 * n3, n2 * n3, n3 * nt, n3 * nt};
+    for (BuildRun &r : runs[j]) {
+      for (int q = 0; q < 7; q++) r.op[q] = take((size_t)(esz(r.f32) * r.P * per[q]));
+      if (r.finishing) r.root = take((size_t)(16LL * r.P * nt * nt));
+    }
   }
-  const int nroot = pl.lv.empty() ? nb : pl.lv.back().nt;
-  size_t oRroot = take(cplx_bytes((long long)nroot * nroot));
-  // tables: D1x, D1y, D2x, D2y, then the node grid and the grid -> node map
-  size_t tab_bytes = sizeof(double) * 4 * p * p + sizeof(int) * (n + p * p);
-  size_t oTab = take(tab_bytes);
-  size_t oC = pl.mixed ? take(sizeof(double) * (size_t)nl * ni) : 0;
-  // index maps: per level I1, I2, I3a, I3b, the I3 pairs; the root and outer maps
+  // problems with a single leaf: the root is the leaf's R
+  int k1 = K;
+  while (k1 > 0 && hs[k1 - 1]->plan.L == 0) k1--;
+  const size_t oRoot1 = take(16ULL * (K - k1) * nb * nb);
+  const size_t tab_bytes = sizeof(double) * 4 * p * p + sizeof(int) * (n + p * p);
+  std::vector<size_t> oTab(K), oC(K, 0);
+  for (int k = 0; k < K; k++) {
+    oTab[k] = take(tab_bytes);
+    if (mixed) oC[k] = take(sizeof(double) * (size_t)hs[k]->plan.leaves * ni);
+  }
+  // index maps: per level I1, I2, I3a, I3b, the I3 pairs; per problem the
+  // root and outer maps
   std::vector<int> ints;
-  std::vector<size_t> imap(pl.lv.size() * 5);
-  for (size_t j = 0; j < pl.lv.size(); j++) {
-    const Level &L = pl.lv[j];
+  std::vector<size_t> imap((size_t)Lmax * 5);
+  for (int j = 0; j < Lmax; j++) {
+    const Level &L = P0.lv[j];
     const std::vector<int> *v[5] = {&L.I1, &L.I2, &L.I3a, &L.I3b, &L.pairs};
     for (int q = 0; q < 5; q++) {
       imap[5 * j + q] = ints.size();
       ints.insert(ints.end(), v[q]->begin(), v[q]->end());
     }
   }
-  size_t root_at = ints.size();
-  ints.insert(ints.end(), pl.root_src.begin(), pl.root_src.end());
-  size_t outer_at = ints.size();
-  ints.insert(ints.end(), pl.outer.begin(), pl.outer.end());
-  size_t oInts = take(sizeof(int) * (ints.size() + 1));
-  size_t oStatus = take(sizeof(unsigned int));
-  h->arena_bytes = off;
+  std::vector<size_t> root_at(K), outer_at(K);
+  for (int k = 0; k < K; k++) {
+    const Plan &pk = hs[k]->plan;
+    root_at[k] = ints.size();
+    ints.insert(ints.end(), pk.root_src.begin(), pk.root_src.end());
+    outer_at[k] = ints.size();
+    ints.insert(ints.end(), pk.outer.begin(), pk.outer.end());
+  }
+  const size_t oInts = take(sizeof(int) * (ints.size() + 1));
+  const size_t oStatus = take(sizeof(unsigned int));
+  const size_t oProbs = take(sizeof(hps::LeafProb) * K);
 
   long long cap = env_cap();
-  if (cap >= 0 && (long long)h->arena_bytes > cap) return HPS_ENOMEM;
-  CK(cudaMalloc(&h->arena, h->arena_bytes));
-  char *base = (char *)h->arena;
-  h->X = base + oX;
-  h->GX = base + oGX;
-  for (size_t j = 0; j < pl.lv.size(); j++) {
-    Level &L = pl.lv[j];
-    L.Winv = base + oops[7 * j + 0];
-    L.R33a = base + oops[7 * j + 1];
-    L.R33b = base + oops[7 * j + 2];
-    L.R13a = base + oops[7 * j + 3];
-    L.R23b = base + oops[7 * j + 4];
-    L.Phia = base + oops[7 * j + 5];
-    L.Phib = base + oops[7 * j + 6];
+  if (cap >= 0 && (long long)off > cap) return HPS_ENOMEM;
+  Shared *sh = new (std::nothrow) Shared();
+  if (!sh) return HPS_ENOMEM;
+  sh->bytes = off;
+  sh->refs = K;
+  {
+    cudaError_t err = cudaMalloc(&sh->arena, off);
+    if (err != cudaSuccess) {
+      delete sh;
+      return cuda_fail(err);
+    }
   }
-  h->Rroot = (double2 *)(base + oRroot);
-  h->tables = base + oTab;
-  h->c_dev = pl.mixed ? (double *)(base + oC) : nullptr;
-  h->d_ints = (int *)(base + oInts);
-  h->d_status = (unsigned int *)(base + oStatus);
-  for (size_t j = 0; j < pl.lv.size(); j++) {
-    Level &L = pl.lv[j];
-    L.d_I1 = h->d_ints + imap[5 * j + 0];
-    L.d_I2 = h->d_ints + imap[5 * j + 1];
-    L.d_I3a = h->d_ints + imap[5 * j + 2];
-    L.d_I3b = h->d_ints + imap[5 * j + 3];
-    L.d_pairs = h->d_ints + imap[5 * j + 4];
+  char *base = (char *)sh->arena;
+  for (int k = 0; k < K; k++) hs[k]->sh = sh;  // from here on hps_free releases it
+
+  // ---- every problem's view of the arena ----
+  int *d_ints = (int *)(base + oInts);
+  unsigned int *d_status = (unsigned int *)(base + oStatus);
+  for (int k = 0; k < K; k++) {
+    hps_handle *h = hs[k];
+    Plan &pl = h->plan;
+    h->X = base + oX + esl * leaf0[k] * n * n;
+    h->GX = base + oGX + esl * leaf0[k] * n * nb;
+    for (int j = 0; j < pl.L; j++) {
+      Level &L = pl.lv[j];
+      const long long pos = first[k][j];
+      const BuildRun *r = nullptr;
+      for (const BuildRun &q : runs[j])
+        if (pos >= q.p0 && pos < q.p0 + q.P) r = &q;
+      const long long d = pos - r->p0, e = esz(r->f32);
+      const long long n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt;
+      const long long per[7] = {n3 * n3, n3 * n3, n3 * n3, n1 * n3, n2 * n3, n3 * nt, n3 * nt};
+      void **dst[7] = {&L.Winv, &L.R33a, &L.R33b, &L.R13a, &L.R23b, &L.Phia, &L.Phib};
+      for (int q = 0; q < 7; q++) *dst[q] = base + r->op[q] + e * d * per[q];
+      L.d_I1 = d_ints + imap[5 * j + 0];
+      L.d_I2 = d_ints + imap[5 * j + 1];
+      L.d_I3a = d_ints + imap[5 * j + 2];
+      L.d_I3b = d_ints + imap[5 * j + 3];
+      L.d_pairs = d_ints + imap[5 * j + 4];
+      if (j == pl.L - 1) h->Rroot = (double2 *)(base + r->root + 16 * d * nt * nt);
+    }
+    if (pl.L == 0) h->Rroot = (double2 *)(base + oRoot1 + 16ULL * (k - k1) * nb * nb);
+    h->tables = base + oTab[k];
+    h->c_dev = mixed ? (double *)(base + oC[k]) : nullptr;
+    h->d_ints = d_ints;
+    h->d_status = d_status;
+    h->d_root_src = d_ints + root_at[k];
+    h->d_outer = d_ints + outer_at[k];
   }
-  h->d_root_src = h->d_ints + root_at;
-  h->d_outer = h->d_ints + outer_at;
 
   // ---- host tables: 1-D differentiation on the leaf, squared, node grid ----
-  const double hx = (h->desc.x1 - h->desc.x0) / pl.m, hy = (h->desc.y1 - h->desc.y0) / pl.m;
-  std::vector<double> x, D1x, D1y;
-  cheb(p, 0.0, hx, x, D1x);
-  cheb(p, 0.0, hy, x, D1y);
   std::vector<unsigned char> tab(tab_bytes);
-  double *T = (double *)tab.data();
-  for (int i = 0; i < p * p; i++) {
-    T[i] = D1x[i];
-    T[p * p + i] = D1y[i];
-  }
-  for (int i = 0; i < p; i++)
-    for (int j = 0; j < p; j++) {
-      double sx = 0.0, sy = 0.0;
-      for (int k = 0; k < p; k++) {
-        sx += D1x[i * p + k] * D1x[k * p + j];
-        sy += D1y[i * p + k] * D1y[k * p + j];
-      }
-      T[2 * p * p + i * p + j] = sx;
-      T[3 * p * p + i * p + j] = sy;
+  for (int k = 0; k < K; k++) {
+    const hps_desc &dk = hs[k]->desc;
+    const int mk = hs[k]->plan.m;
+    const double hx = (dk.x1 - dk.x0) / mk, hy = (dk.y1 - dk.y0) / mk;
+    std::vector<double> x, D1x, D1y;
+    cheb(p, 0.0, hx, x, D1x);
+    cheb(p, 0.0, hy, x, D1y);
+    double *T = (double *)tab.data();
+    for (int i = 0; i < p * p; i++) {
+      T[i] = D1x[i];
+      T[p * p + i] = D1y[i];
     }
-  int *G = (int *)(T + 4 * p * p);
-  int *Loc = G + n;
-  for (int k = 0; k < p * p; k++) Loc[k] = -1;
-  for (int k = 0; k < n; k++) {
-    int ix, iy;
-    local_grid(p, k, ix, iy);
-    G[k] = ix | (iy << 8);
-    Loc[iy * p + ix] = k;
+    for (int i = 0; i < p; i++)
+      for (int jj = 0; jj < p; jj++) {
+        double sx = 0.0, sy = 0.0;
+        for (int q = 0; q < p; q++) {
+          sx += D1x[i * p + q] * D1x[q * p + jj];
+          sy += D1y[i * p + q] * D1y[q * p + jj];
+        }
+        T[2 * p * p + i * p + jj] = sx;
+        T[3 * p * p + i * p + jj] = sy;
+      }
+    int *G = (int *)(T + 4 * p * p);
+    int *Loc = G + n;
+    for (int q = 0; q < p * p; q++) Loc[q] = -1;
+    for (int q = 0; q < n; q++) {
+      int ix, iy;
+      local_grid(p, q, ix, iy);
+      G[q] = ix | (iy << 8);
+      Loc[iy * p + ix] = q;
+    }
+    CK(cudaMemcpyAsync(hs[k]->tables, tab.data(), tab_bytes, cudaMemcpyHostToDevice, st));
   }
-  CK(cudaMemcpyAsync(h->tables, tab.data(), tab_bytes, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(h->d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned int), st));
+  CK(cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d_status, 0, sizeof(unsigned int), st));
 
   // ---- c on the device (the mixed path keeps a copy for its residuals) ----
-  const double *c_dev = c;
-  void *c_stage = nullptr;
-  size_t cbytes = sizeof(double) * (size_t)nl * ni;
-  if (pl.mixed) {
-    CK(cudaMemcpyAsync(h->c_dev, c, cbytes, cudaMemcpyDefault, st));
-    c_dev = h->c_dev;
-  } else if (!is_device_ptr(c)) {
-    CK(cudaMallocAsync(&c_stage, cbytes, st));
-    CK(cudaMemcpyAsync(c_stage, c, cbytes, cudaMemcpyHostToDevice, st));
-    c_dev = (const double *)c_stage;
+  size_t host_c = 0;
+  std::vector<bool> cdev(K);
+  for (int k = 0; k < K; k++) {
+    cdev[k] = is_device_ptr(cin[k]);
+    if (!mixed && !cdev[k]) host_c += align256(sizeof(double) * (size_t)hs[k]->plan.leaves * ni);
   }
+  char *c_stage = nullptr;
+  if (host_c) CK(cudaMallocAsync((void **)&c_stage, host_c, st));
+  std::vector<hps::LeafProb> probs(K);
+  size_t at = 0;
+  for (int k = 0; k < K; k++) {
+    const size_t cb = sizeof(double) * (size_t)hs[k]->plan.leaves * ni;
+    const double *cd = cin[k];
+    if (mixed) {
+      CK(cudaMemcpyAsync(hs[k]->c_dev, cin[k], cb, cudaMemcpyDefault, st));
+      cd = hs[k]->c_dev;
+    } else if (!cdev[k]) {
+      CK(cudaMemcpyAsync(c_stage + at, cin[k], cb, cudaMemcpyHostToDevice, st));
+      cd = (const double *)(c_stage + at);
+      at += align256(cb);
+    }
+    probs[k].tab = (const double *)hs[k]->tables;
+    probs[k].c = cd;
+    probs[k].leaf0 = leaf0[k];
+    probs[k].eta = make_double2(hs[k]->desc.eta_re, hs[k]->desc.eta_im);
+    probs[k].kappa2 = hs[k]->desc.kappa * hs[k]->desc.kappa;
+  }
+  hps::LeafProb *d_probs = (hps::LeafProb *)(base + oProbs);
+  CK(cudaMemcpyAsync(d_probs, probs.data(), sizeof(hps::LeafProb) * K, cudaMemcpyHostToDevice, st));
 
-  // ---- leaves (Sec. 2.1): one cluster launch over all leaves ----
+  // ---- leaves (Sec. 2.1): one cluster launch over every problem's leaves ----
   hps::LeafTables lt;
   lt.p = p;
-  lt.e = pl.e;
+  lt.e = P0.e;
   lt.n = n;
   lt.nb = nb;
   lt.ni = ni;
-  lt.eta = make_double2(h->desc.eta_re, h->desc.eta_im);
-  lt.kappa2 = h->desc.kappa * h->desc.kappa;
+  // cluster per leaf: wider clusters split each leaf finer, which balances
+  // the chip when there are few leaves (measured best: 8 CTAs a leaf for 16
+  // leaves, 4 for 256, 1 from 1024 leaves on)
+  int lcs = 1;
+  while (lcs < 8 && NL * lcs < 1024) lcs *= 2;
+  if (const char *ev = getenv("HPS_LEAF_CLUSTER")) {
+    int v = atoi(ev);
+    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) lcs = v;
+  }
   // scratch for the in-place elimination: leaves go in chunks of at most
   // ~1 GiB of matrices
-  const long long esz = lf ? 8 : 16;
-  const int chunk = (int)std::max<long long>(1, std::min<long long>(nl, (1LL << 30) / (esz * n * n)));
+  const int chunk = (int)std::max<long long>(1, std::min<long long>(NL, (1LL << 30) / (esl * n * n)));
   void *lscr = nullptr;
   int *lmeta = nullptr;
-  CK(cudaMallocAsync(&lscr, (size_t)esz * chunk * n * n, st));
+  CK(cudaMallocAsync(&lscr, (size_t)esl * chunk * n * n, st));
   CK(cudaMallocAsync((void **)&lmeta, sizeof(int) * (size_t)chunk * hps::gj_meta_ints(n), st));
-  h->ev.assign(pl.lv.size() + 2, nullptr);
-  for (cudaEvent_t &e : h->ev) CK(cudaEventCreate(&e));
-  CK(cudaEventRecord(h->ev[0], st));
-  for (int l0 = 0; l0 < nl; l0 += chunk)
-    CK(hps::launch_leaf(lt, h->tables, c_dev, l0, std::min(chunk, nl - l0), h->X, h->GX, lscr, lmeta,
-                        h->d_status, pl.L, h->leaf_cs, lf != 0, st));
-  CK(cudaEventRecord(h->ev[1], st));
+  sh->ev.assign(Lmax + 2, nullptr);
+  for (cudaEvent_t &e : sh->ev) CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(sh->ev[0], st));
+  int launches = 0;
+  for (long long l0 = 0; l0 < NL; l0 += chunk) {
+    CK(hps::launch_leaf(lt, d_probs, K, l0, (int)std::min<long long>(chunk, NL - l0), base + oX, base + oGX,
+                        lscr, lmeta, d_status, Lmax, lcs, lf != 0, st));
+    launches++;
+  }
+  CK(cudaEventRecord(sh->ev[1], st));
   CK(cudaFreeAsync(lscr, st));
   CK(cudaFreeAsync(lmeta, st));
   if (c_stage) CK(cudaFreeAsync(c_stage, st));
 
-  if (pl.lv.empty()) {
-    // a single leaf: the root R is the leaf's R = GX[:, :nb]
+  if (k1 < K) {
+    // single-leaf problems: the root R is the leaf's R = GX[:, :nb]
     CopyBatch cb;
     cb.count = 1;
-    cb.d[0] = copy(nb, nb, 1, mat(h->GX, nb, 0, nullptr, nullptr, lf), mat(h->Rroot, nb, 0));
+    cb.d[0] = copy(nb, nb, K - k1, mat(base + oGX + esl * leaf0[k1] * n * nb, nb, (long long)n * nb, nullptr,
+                                       nullptr, lf),
+                   mat(base + oRoot1, nb, (long long)nb * nb));
     CK(hps::launch_copy(cb, st));
-    return HPS_OK;
+    launches++;
   }
 
   // ---- merges (Sec. 2.2), one level at a time (Algorithm 3's level loop) ----
-  // scratch sized for complex128; complex64 levels use part of it
-  size_t rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
-  for (size_t j = 0; j < pl.lv.size(); j++) {
-    const Level &L = pl.lv[j];
-    rbuf = std::max(rbuf, (size_t)L.P * L.nt * L.nt);
-    qbuf = std::max(qbuf, (size_t)L.P * L.n3 * L.nt);
-    wbuf = std::max(wbuf, (size_t)L.P * L.n3 * L.n3);
-    mbuf = std::max(mbuf, (size_t)L.P * hps::gj_meta_ints(L.n3));
-    const int cf = (j == 0) ? lf : pl.lv[j - 1].f32;
-    if (cf != L.f32) cbuf = std::max(cbuf, (size_t)2 * L.P * L.nc * L.nc);
+  // scratch: two R buffers (children / parents), then Q, W, converted
+  // children (all sized for complex128) and the elimination metadata
+  size_t rbytes = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
+  for (int j = 0; j < Lmax; j++) {
+    const Level &S = P0.lv[j];
+    size_t rb = 0;
+    for (BuildRun &r : runs[j]) {
+      if (!r.finishing) {
+        r.rout = rb;
+        rb = align256(rb + (size_t)(esz(r.f32) * r.P * S.nt * S.nt));
+      }
+      qbuf = std::max(qbuf, (size_t)r.P * S.n3 * S.nt);
+      wbuf = std::max(wbuf, (size_t)r.P * S.n3 * S.n3);
+      mbuf = std::max(mbuf, (size_t)r.P * hps::gj_meta_ints(S.n3));
+      std::vector<ChildPiece> pcs = child_pieces(runs, j, r);
+      const int cf = pcs[0].run < 0 ? lf : runs[j - 1][pcs[0].run].f32;
+      if (pcs.size() > 1 || cf != r.f32) cbuf = std::max(cbuf, (size_t)2 * r.P * S.nc * S.nc);
+    }
+    rbytes = std::max(rbytes, rb);
   }
-  double2 *scratch = nullptr;
+  char *scratch = nullptr;
   int *wmeta = nullptr;
-  CK(cudaMallocAsync((void **)&scratch, sizeof(double2) * (2 * rbuf + qbuf + wbuf + cbuf), st));
-  CK(cudaMallocAsync((void **)&wmeta, sizeof(int) * mbuf, st));
-  double2 *Rbuf[2] = {scratch, scratch + rbuf};
-  double2 *Q = scratch + 2 * rbuf;
+  if (Lmax > 0) {
+    CK(cudaMallocAsync((void **)&scratch, 2 * rbytes + sizeof(double2) * (qbuf + wbuf + cbuf), st));
+    CK(cudaMallocAsync((void **)&wmeta, sizeof(int) * std::max<size_t>(mbuf, 1), st));
+  }
+  char *Rbuf[2] = {scratch, scratch + rbytes};
+  double2 *Q = (double2 *)(scratch + 2 * rbytes);
   double2 *Wscr = Q + qbuf;
   double2 *Rconv = Wscr + wbuf;
 
@@ -920,97 +1120,124 @@ static int build_impl(hps_handle *h, const double *c, cudaStream_t st) {
     m.cmap = c;
     return m;
   };
-  // child R of the first merge: the leaves' R = GX[:, :nb] (ld nb, stride n nb)
-  const void *Rc = h->GX;
-  int rcf = lf;
-  long long ldc = nb, strc = (long long)n * nb;
-  for (size_t j = 0; j < pl.lv.size(); j++) {
-    Level &L = pl.lv[j];
-    const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc, f = L.f32;
-    const bool last = (j + 1 == pl.lv.size());
-    if (rcf != f) {
-      // the first complex128 level: its children's R once in complex128
-      CopyBatch cv;
-      cv.count = 1;
-      cv.d[0] = copy(nc, nc, 2 * P, mat(Rc, ldc, strc, nullptr, nullptr, rcf),
-                     mat(Rconv, nc, (long long)nc * nc));
-      CK(hps::launch_copy(cv, st));
-      Rc = Rconv;
-      rcf = 0;
-      ldc = nc;
-      strc = (long long)nc * nc;
-    }
-    void *Rp = last ? (void *)h->Rroot : (void *)Rbuf[j & 1];
-    const long long s2 = 2 * strc;
-    Mat Ra = mat(Rc, ldc, s2, nullptr, nullptr, rcf), Rb = mat(elem(Rc, strc, rcf), ldc, s2, nullptr, nullptr, rcf);
-    auto M = [&](const void *ptr, long long ld, long long stride) { return mat(ptr, ld, stride, nullptr, nullptr, f); };
-    // stored blocks and the parts of Phi_b and R^tau that are copies
-    CopyBatch cb;
-    cb.count = 0;
-    cb.d[cb.count++] = copy(n3, n3, P, sub(Ra, L.d_I3a, L.d_I3a), M(L.R33a, n3, (long long)n3 * n3));
-    cb.d[cb.count++] = copy(n3, n3, P, sub(Rb, L.d_I3b, L.d_I3b), M(L.R33b, n3, (long long)n3 * n3));
-    cb.d[cb.count++] = copy(n1, n3, P, sub(Ra, L.d_I1, L.d_I3a), M(L.R13a, n1, (long long)n1 * n3));
-    cb.d[cb.count++] = copy(n2, n3, P, sub(Rb, L.d_I2, L.d_I3b), M(L.R23b, n2, (long long)n2 * n3));
-    // Q = [R33b R31a | -R32b]: the right block here, the left one by GEMM below
-    cb.d[cb.count++] = copy(n3, n2, P, sub(Rb, L.d_I3b, L.d_I2),
-                            M(elem(Q, (long long)n1 * n3, f), n3, (long long)n3 * nt), -1.0);
-    // Phi_b starts as -[R31a | 0]
-    cb.d[cb.count++] = copy(n3, n1, P, sub(Ra, L.d_I3a, L.d_I1), M(L.Phib, n3, (long long)n3 * nt), -1.0);
-    cb.d[cb.count++] = copy(n3, n2, P, mat(nullptr, 0, 0), M(elem(L.Phib, (long long)n1 * n3, f), n3, (long long)n3 * nt));
-    // R^tau starts as diag(R11a, R22b)
-    const long long sp = (long long)nt * nt;
-    cb.d[cb.count++] = copy(n1, n1, P, sub(Ra, L.d_I1, L.d_I1), M(Rp, nt, sp));
-    cb.d[cb.count++] = copy(n2, n2, P, sub(Rb, L.d_I2, L.d_I2), M(elem(Rp, (long long)n1 * nt + n1, f), nt, sp));
-    cb.d[cb.count++] = copy(n2, n1, P, mat(nullptr, 0, 0), M(elem(Rp, n1, f), nt, sp));
-    cb.d[cb.count++] = copy(n1, n2, P, mat(nullptr, 0, 0), M(elem(Rp, (long long)n1 * nt, f), nt, sp));
-    CK(hps::launch_copy(cb, st));
+  for (int j = 0; j < Lmax; j++) {
+    const Level &S = P0.lv[j];
+    const int n1 = S.n1, n2 = S.n2, n3 = S.n3, nt = S.nt, nc = S.nc;
+    const int *dI1 = d_ints + imap[5 * j + 0], *dI2 = d_ints + imap[5 * j + 1];
+    const int *dI3a = d_ints + imap[5 * j + 2], *dI3b = d_ints + imap[5 * j + 3];
+    for (const BuildRun &r : runs[j]) {
+      const int P = r.P, f = r.f32;
+      // children's R: in place when one run of this precision holds them all
+      const void *Rc;
+      int rcf;
+      long long ldc, strc;
+      std::vector<ChildPiece> pcs = child_pieces(runs, j, r);
+      auto piece_src = [&](const ChildPiece &c, int &pf) {
+        if (c.run < 0) {
+          pf = lf;
+          return mat(base + oGX + esl * c.c0 * n * nb, nb, (long long)n * nb, nullptr, nullptr, lf);
+        }
+        const BuildRun &q = runs[j - 1][c.run];
+        pf = q.f32;
+        return mat(Rbuf[(j - 1) & 1] + q.rout + esz(q.f32) * (c.c0 - q.p0) * nc * nc, nc, (long long)nc * nc,
+                   nullptr, nullptr, q.f32);
+      };
+      int pf0;
+      Mat m0 = piece_src(pcs[0], pf0);
+      if (pcs.size() == 1 && pf0 == f) {
+        Rc = m0.ptr;
+        rcf = pf0;
+        ldc = m0.ld;
+        strc = m0.stride;
+      } else {
+        // gather (and widen) the children into one complex128 array
+        CopyBatch cv;
+        cv.count = 0;
+        for (const ChildPiece &c : pcs) {
+          int pf;
+          Mat src = piece_src(c, pf);
+          cv.d[cv.count++] = copy(nc, nc, (int)c.count, src,
+                                  mat(Rconv + (c.c0 - 2 * r.p0) * nc * nc, nc, (long long)nc * nc));
+        }
+        CK(hps::launch_copy(cv, st));
+        launches++;
+        Rc = Rconv;
+        rcf = 0;
+        ldc = nc;
+        strc = (long long)nc * nc;
+      }
+      void *Rp = r.finishing ? (void *)(base + r.root) : (void *)(Rbuf[j & 1] + r.rout);
+      void *Winv = base + r.op[0], *R33a = base + r.op[1], *R33b = base + r.op[2], *R13a = base + r.op[3];
+      void *R23b = base + r.op[4], *Phia = base + r.op[5], *Phib = base + r.op[6];
+      const long long s2 = 2 * strc;
+      Mat Ra = mat(Rc, ldc, s2, nullptr, nullptr, rcf), Rb = mat(elem(Rc, strc, rcf), ldc, s2, nullptr, nullptr, rcf);
+      auto M = [&](const void *ptr, long long ld, long long stride) { return mat(ptr, ld, stride, nullptr, nullptr, f); };
+      // stored blocks and the parts of Phi_b and R^tau that are copies
+      CopyBatch cb;
+      cb.count = 0;
+      cb.d[cb.count++] = copy(n3, n3, P, sub(Ra, dI3a, dI3a), M(R33a, n3, (long long)n3 * n3));
+      cb.d[cb.count++] = copy(n3, n3, P, sub(Rb, dI3b, dI3b), M(R33b, n3, (long long)n3 * n3));
+      cb.d[cb.count++] = copy(n1, n3, P, sub(Ra, dI1, dI3a), M(R13a, n1, (long long)n1 * n3));
+      cb.d[cb.count++] = copy(n2, n3, P, sub(Rb, dI2, dI3b), M(R23b, n2, (long long)n2 * n3));
+      // Q = [R33b R31a | -R32b]: the right block here, the left one by GEMM below
+      cb.d[cb.count++] = copy(n3, n2, P, sub(Rb, dI3b, dI2),
+                              M(elem(Q, (long long)n1 * n3, f), n3, (long long)n3 * nt), -1.0);
+      // Phi_b starts as -[R31a | 0]
+      cb.d[cb.count++] = copy(n3, n1, P, sub(Ra, dI3a, dI1), M(Phib, n3, (long long)n3 * nt), -1.0);
+      cb.d[cb.count++] = copy(n3, n2, P, mat(nullptr, 0, 0), M(elem(Phib, (long long)n1 * n3, f), n3, (long long)n3 * nt));
+      // R^tau starts as diag(R11a, R22b)
+      const long long sp = (long long)nt * nt;
+      cb.d[cb.count++] = copy(n1, n1, P, sub(Ra, dI1, dI1), M(Rp, nt, sp));
+      cb.d[cb.count++] = copy(n2, n2, P, sub(Rb, dI2, dI2), M(elem(Rp, (long long)n1 * nt + n1, f), nt, sp));
+      cb.d[cb.count++] = copy(n2, n1, P, mat(nullptr, 0, 0), M(elem(Rp, n1, f), nt, sp));
+      cb.d[cb.count++] = copy(n1, n2, P, mat(nullptr, 0, 0), M(elem(Rp, (long long)n1 * nt, f), nt, sp));
+      CK(hps::launch_copy(cb, st));
 
-    const long long s33 = (long long)n3 * n3, s3t = (long long)n3 * nt;
-    // W = I - R33b R33a (in scratch), then W^{-1} into its stored slot
-    GemmDesc g = gemm(n3, n3, n3, P, M(L.R33b, n3, s33), M(L.R33a, n3, s33), M(Wscr, n3, s33));
-    g.alpha = make_double2(-1.0, 0.0);
-    g.addI = 1;
-    g.cf32 = f;
-    CK(hps::launch_gemm(&g, 1, st));
-    if (L.gj_wide)
-      CK(hps::launch_gj_wide(Wscr, L.Winv, n3, P, L.gj_wide, wmeta, h->d_status, L.lev, f != 0, st));
-    else
-      CK(hps::launch_gj_inverse(Wscr, L.Winv, n3, P, wmeta, h->d_status, L.lev, L.gj_cs, L.gj_tglobal, f != 0, st));
-    // Q(:, :n1) = R33b R31a
-    g = gemm(n3, n1, n3, P, M(L.R33b, n3, s33), sub(Ra, L.d_I3a, L.d_I1), M(Q, n3, s3t));
-    g.cf32 = f;
-    CK(hps::launch_gemm(&g, 1, st));
-    // Phi_a = W^{-1} Q
-    g = gemm(n3, nt, n3, P, M(L.Winv, n3, s33), M(Q, n3, s3t), M(L.Phia, n3, s3t));
-    g.cf32 = f;
-    CK(hps::launch_gemm(&g, 1, st));
-    // Phi_b = -[R31a | 0] - R33a Phi_a
-    g = gemm(n3, nt, n3, P, M(L.R33a, n3, s33), M(L.Phia, n3, s3t), M(L.Phib, n3, s3t));
-    g.alpha = make_double2(-1.0, 0.0);
-    g.D = g.C;
-    g.beta = make_double2(1.0, 0.0);
-    g.cf32 = f;
-    CK(hps::launch_gemm(&g, 1, st));
-    // R^tau = diag(R11a, R22b) + diag(R13a, R23b) [Phi_a; Phi_b]
-    GemmDesc g2[2];
-    g2[0] = gemm(n1, nt, n3, P, M(L.R13a, n1, (long long)n1 * n3), M(L.Phia, n3, s3t), M(Rp, nt, sp));
-    g2[0].D = g2[0].C;
-    g2[0].beta = make_double2(1.0, 0.0);
-    g2[0].cf32 = f;
-    g2[1] = gemm(n2, nt, n3, P, M(L.R23b, n2, (long long)n2 * n3), M(L.Phib, n3, s3t),
-                 M(elem(Rp, n1, f), nt, sp));
-    g2[1].D = g2[1].C;
-    g2[1].beta = make_double2(1.0, 0.0);
-    g2[1].cf32 = f;
-    CK(hps::launch_gemm(g2, 2, st));
-    CK(cudaEventRecord(h->ev[2 + j], st));
-    Rc = Rp;
-    rcf = f;
-    ldc = nt;
-    strc = sp;
+      const long long s33 = (long long)n3 * n3, s3t = (long long)n3 * nt;
+      // W = I - R33b R33a (in scratch), then W^{-1} into its stored slot
+      GemmDesc g = gemm(n3, n3, n3, P, M(R33b, n3, s33), M(R33a, n3, s33), M(Wscr, n3, s33));
+      g.alpha = make_double2(-1.0, 0.0);
+      g.addI = 1;
+      g.cf32 = f;
+      CK(hps::launch_gemm(&g, 1, st));
+      const int lev = S.lev;  // the tallest tree's level numbering
+      if (r.gj.wide)
+        CK(hps::launch_gj_wide(Wscr, Winv, n3, P, r.gj.wide, wmeta, d_status, lev, f != 0, st));
+      else
+        CK(hps::launch_gj_inverse(Wscr, Winv, n3, P, wmeta, d_status, lev, r.gj.cs, r.gj.tglobal, f != 0, st));
+      // Q(:, :n1) = R33b R31a
+      g = gemm(n3, n1, n3, P, M(R33b, n3, s33), sub(Ra, dI3a, dI1), M(Q, n3, s3t));
+      g.cf32 = f;
+      CK(hps::launch_gemm(&g, 1, st));
+      // Phi_a = W^{-1} Q
+      g = gemm(n3, nt, n3, P, M(Winv, n3, s33), M(Q, n3, s3t), M(Phia, n3, s3t));
+      g.cf32 = f;
+      CK(hps::launch_gemm(&g, 1, st));
+      // Phi_b = -[R31a | 0] - R33a Phi_a
+      g = gemm(n3, nt, n3, P, M(R33a, n3, s33), M(Phia, n3, s3t), M(Phib, n3, s3t));
+      g.alpha = make_double2(-1.0, 0.0);
+      g.D = g.C;
+      g.beta = make_double2(1.0, 0.0);
+      g.cf32 = f;
+      CK(hps::launch_gemm(&g, 1, st));
+      // R^tau = diag(R11a, R22b) + diag(R13a, R23b) [Phi_a; Phi_b]
+      GemmDesc g2[2];
+      g2[0] = gemm(n1, nt, n3, P, M(R13a, n1, (long long)n1 * n3), M(Phia, n3, s3t), M(Rp, nt, sp));
+      g2[0].D = g2[0].C;
+      g2[0].beta = make_double2(1.0, 0.0);
+      g2[0].cf32 = f;
+      g2[1] = gemm(n2, nt, n3, P, M(R23b, n2, (long long)n2 * n3), M(Phib, n3, s3t), M(elem(Rp, n1, f), nt, sp));
+      g2[1].D = g2[1].C;
+      g2[1].beta = make_double2(1.0, 0.0);
+      g2[1].cf32 = f;
+      CK(hps::launch_gemm(g2, 2, st));
+      launches += 6 + gj_launches(n3, r.gj);
+    }
+    CK(cudaEventRecord(sh->ev[2 + j], st));
   }
-  CK(cudaFreeAsync(scratch, st));
-  CK(cudaFreeAsync(wmeta, st));
+  if (scratch) CK(cudaFreeAsync(scratch, st));
+  if (wmeta) CK(cudaFreeAsync(wmeta, st));
+  sh->launches = launches;
   return HPS_OK;
 }
 
@@ -1032,28 +1259,19 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
     if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) cs = v;
   }
   h->leaf_cs = cs;
-  for (Level &L : h->plan.lv) {
-    // stage the panels in shared memory while they fit beside the rest
-    L.gj_tglobal = hps::gj_smem_bytes(L.n3, hps::gj_max_cluster(), false, 0, false, L.f32) > 200 * 1024;
-    L.gj_cs = choose_gj_cs(L.n3, L.P, L.gj_tglobal, L.f32);
-    // too few matrices to fill the chip with clusters: one launch per panel
-    // over about two CTAs per SM, each with a slab of at least 4 columns
-    if ((long long)L.P * L.gj_cs < 152 && L.n3 >= 64 && !getenv("HPS_NO_WIDE_GJ")) {
-      int G = (int)std::min<long long>((2 * 152 + L.P - 1) / L.P, L.n3 / 4 + 1);
-      L.gj_wide = std::max(2, G);
-    }
-    if (!L.gj_wide && hps::gj_smem_bytes(L.n3, L.gj_cs, false, 0, L.gj_tglobal, L.f32) > 227 * 1024)
-      return HPS_ENOTSUP;
-  }
   if (hps::gj_smem_bytes(h->plan.n, h->leaf_cs, true, h->plan.p, false, h->plan.leaf_f32) > 227 * 1024)
     return HPS_ENOTSUP;
   fill_info(h->plan, h->info);
-  for (const Level &L : h->plan.lv)
-    if (L.gj_wide) h->info.build_launches += (L.n3 + 7) / 8 + 1;  // np + 2 launches instead of 1
+  for (const Level &L : h->plan.lv) {
+    GJChoice g;
+    if (!choose_gj(L.n3, L.P, L.f32, g)) return HPS_ENOTSUP;
+    h->info.build_launches += gj_launches(L.n3, g) - 1;
+  }
   // transient build memory: the leaf elimination chunk, then the merge scratch
   const Plan &pl = h->plan;
   const long long esz = pl.leaf_f32 ? 8 : 16, n = pl.n;
   const long long chunk = std::max<long long>(1, std::min<long long>(pl.leaves, (1LL << 30) / (esz * n * n)));
+  h->info.build_launches += (int)((pl.leaves + chunk - 1) / chunk) - 1;  // leaf chunks
   long long leaf_scr = esz * chunk * n * n + 4LL * chunk * (long long)hps::gj_meta_ints(pl.n);
   long long rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
   for (size_t j = 0; j < pl.lv.size(); j++) {
@@ -1084,38 +1302,78 @@ int hps_plan(const hps_desc *desc, hps_info_t *info) {
 }
 
 int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **out) {
-  int st0 = check_desc(desc);
-  if (st0) return st0;
-  if (!c || !out) return HPS_EINVAL;
-  hps_handle *h = new (std::nothrow) hps_handle();
-  if (!h) return HPS_ENOMEM;
-  int st = plan_handle(h, desc);
-  if (st != HPS_OK) {
-    delete h;
-    return st;
+  return hps_build_batch(1, desc, &c, stream, out);
+}
+
+int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, void *stream,
+                    hps_handle **out) {
+  if (nprob < 0) return HPS_EINVAL;
+  if (nprob == 0) return HPS_OK;
+  if (!descs || !c || !out) return HPS_EINVAL;
+  for (int k = 0; k < nprob; k++) {
+    int st0 = check_desc(&descs[k]);
+    if (st0) return st0;
+    if (!c[k]) return HPS_EINVAL;
+    if (descs[k].p != descs[0].p || descs[k].precision != descs[0].precision ||
+        descs[k].fp64_levels != descs[0].fp64_levels)
+      return HPS_EINVAL;
+  }
+  std::vector<hps_handle *> hs(nprob, nullptr);
+  auto release = [&]() {
+    for (hps_handle *x : hs) hps_free(x);
+  };
+  long long total = 0;
+  for (int k = 0; k < nprob; k++) {
+    hs[k] = new (std::nothrow) hps_handle();
+    if (!hs[k]) {
+      release();
+      return HPS_ENOMEM;
+    }
+    int st = plan_handle(hs[k], &descs[k]);
+    if (st != HPS_OK) {
+      release();
+      return st;
+    }
+    total += hs[k]->info.operator_bytes;
   }
   long long cap = env_cap();
-  if (cap >= 0 && h->info.operator_bytes > cap) {
-    delete h;
+  if (cap >= 0 && total > cap) {
+    release();
     return HPS_ENOMEM;
   }
-  st = build_impl(h, c, (cudaStream_t)stream);
+  // build order: tallest tree first (stable), so that on every merge level
+  // the problems that still have it come first
+  std::vector<int> order(nprob);
+  for (int k = 0; k < nprob; k++) order[k] = k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return hs[a]->plan.L > hs[b]->plan.L; });
+  std::vector<hps_handle *> sorted(nprob);
+  std::vector<const double *> cs(nprob);
+  for (int k = 0; k < nprob; k++) {
+    sorted[k] = hs[order[k]];
+    cs[k] = c[order[k]];
+  }
+  int st = build_many(sorted, cs, (cudaStream_t)stream);
   if (st != HPS_OK) {
-    hps_free(h);
+    release();
     return st;
   }
-  *out = h;
+  for (int k = 0; k < nprob; k++) {
+    hs[k]->info.build_launches = hs[k]->sh->launches;
+    out[k] = hs[k];
+  }
   return HPS_OK;
 }
 
 int hps_build_times(hps_handle *h, double *ms, int cap) {
   if (!h || (!ms && cap > 0) || cap < 0) return -HPS_EINVAL;
-  const int nph = (int)h->plan.lv.size() + 1;
-  if (h->ev.size() < 2) return -HPS_EINVAL;
-  if (cudaEventSynchronize(h->ev.back()) != cudaSuccess) return -HPS_ECUDA;
+  if (!h->sh || h->sh->ev.size() < 2) return -HPS_EINVAL;
+  const std::vector<cudaEvent_t> &ev = h->sh->ev;
+  const int nph = (int)ev.size() - 1;
+  if (cudaEventSynchronize(ev.back()) != cudaSuccess) return -HPS_ECUDA;
   for (int q = 0; q < nph && q < cap; q++) {
     float t = 0.0f;
-    if (q + 1 >= (int)h->ev.size() || cudaEventElapsedTime(&t, h->ev[q], h->ev[q + 1]) != cudaSuccess)
+    if (cudaEventElapsedTime(&t, ev[q], ev[q + 1]) != cudaSuccess)
       return -HPS_ECUDA;
     ms[q] = t;
   }

@@ -56,8 +56,16 @@ struct CopyBatch {
 // Local node order [S, E, N, W, interior].
 struct LeafTables {
   int p, e, n, nb, ni;
-  double2 eta;       // impedance parameter
-  double kappa2;     // kappa^2
+};
+
+// Per-problem data of a leaf launch that covers the leaves of several
+// problems (same p; leaves numbered problem after problem).
+struct LeafProb {
+  const double *tab;  // D1x, D1y, D2x, D2y (p*p each, scaled to the leaf), then int grid[n]
+  const double *c;    // [leaves of this problem][ni]
+  long long leaf0;    // first leaf of this problem in the launch's numbering
+  double2 eta;        // impedance parameter
+  double kappa2;      // kappa^2
 };
 
 // Device-side status word: 0 = fine; otherwise (code << 28) | (level << 20) | box.
@@ -74,11 +82,11 @@ cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st);
 // CTAs, write X = B^{-1} = [Psi | Y] ([leaf][n][n] column-major) and
 // GX = G X ([leaf][n][nb] column-major: R = GX[:, :nb], Gamma = GX[:, nb:]).
 // The arithmetic and X, GX, S are complex64 when f32, complex128 otherwise.
-//   tab_dev: device tables: double D1x[p*p], D1y[p*p], D2x[p*p], D2y[p*p]
-//            (row-major, scaled to the leaf), then int grid[n] (ix | iy << 8)
+//   probs: device array of nprob problems, ordered by leaf0 (probs[0].leaf0
+//          = 0); leaf l belongs to the last problem whose leaf0 <= l
 //   S, meta: scratch for `count` matrices: count * n * n complex and
 //            count * gj_meta_ints(n) ints
-cudaError_t launch_leaf(const LeafTables &lt, const void *tab_dev, const double *c, int leaf0,
+cudaError_t launch_leaf(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0,
                         int count, void *X, void *GX, void *S, int *meta, unsigned int *status,
                         int level, int cs, bool f32, cudaStream_t st);
 

@@ -26,7 +26,7 @@ HPS_FP64 = 0
 HPS_MIXED = 1
 
 # every entry point include/hps.h declares
-EXPORTS = ("hps_nodes", "hps_build", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
+EXPORTS = ("hps_nodes", "hps_build", "hps_build_batch", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
            "hps_root_R", "hps_leaf_ops", "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
 
 
@@ -76,6 +76,7 @@ def lib():
         D = ctypes.POINTER(hps_desc)
         L.hps_nodes.argtypes = [D, P, P]
         L.hps_build.argtypes = [D, P, P, ctypes.POINTER(ctypes.c_void_p)]
+        L.hps_build_batch.argtypes = [ctypes.c_int, D, P, P, ctypes.POINTER(ctypes.c_void_p)]
         L.hps_solve.argtypes = [P, P, P, P, ctypes.c_int, P]
         L.hps_solve_noalloc.argtypes = [P, P, P, P, ctypes.c_int, P]
         L.hps_solve_batch.argtypes = [P, ctypes.c_int, P, P, P, P, P]
@@ -214,6 +215,21 @@ def hps_build(pr: Problem, c, stream=None) -> Handle:
     h = ctypes.c_void_p()
     _check(lib().hps_build(ctypes.byref(d), _ptr(c), _stream(stream), ctypes.byref(h)), "hps_build")
     return Handle(h.value, pr)
+
+
+def hps_build_batch(problems, cs, stream=None) -> list:
+    """Build several problems together (same p, precision and fp64_levels);
+    one Handle per problem, in the given order."""
+    k = len(problems)
+    if len(cs) != k:
+        raise ValueError("hps_build_batch: one c per problem")
+    if k == 0:
+        return []
+    descs = (hps_desc * k)(*[pr.desc() for pr in problems])
+    cp = (ctypes.c_void_p * k)(*[_ptr(c) for c in cs])
+    out = (ctypes.c_void_p * k)()
+    _check(lib().hps_build_batch(k, descs, cp, _stream(stream), out), "hps_build_batch")
+    return [Handle(out[i], problems[i]) for i in range(k)]
 
 
 def hps_solve(h: Handle, s, t, u, nrhs: int, stream=None):
