@@ -323,6 +323,8 @@ def ours(args, rank, world, local_rank):
     minfo = hm.info()
     hm.free()
 
+    batch_res = batching(dev, st, flush)
+
     if rank != 0:
         return
     leaf_flops = pr.leaves * 8 * (pr.n ** 3 + pr.nb * pr.n * pr.p)
@@ -369,6 +371,7 @@ def ours(args, rank, world, local_rank):
             "rel_err_root_R_vs_fp64_gpu": float(np.linalg.norm(R_mixed - R_gpu) / np.linalg.norm(R_gpu)),
             "operator_bytes": minfo.operator_bytes,
         },
+        "batching": batch_res,
     }
     if world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -382,6 +385,62 @@ def ours(args, rank, world, local_rank):
         line["mixed"]["rel_err_u_vs_oracle"] = float(np.abs(u_mixed - u_ora).max() / np.abs(u_ora).max())
         line["mixed"]["rel_err_root_R_vs_oracle"] = float(np.linalg.norm(R_mixed - R_ora) / np.linalg.norm(R_ora))
     print(json.dumps(line), flush=True)
+
+
+def batching(dev, st, flush, reps=2):
+    """Ragged batch of 32 independent problems (m in {8, 16, 32}, p = 16,
+    kappa = eta in [20, 200], random media, seeds 100..131): the batch built by
+    one hps_build_batch call against the same problems built one hps_build
+    after another, FP64 and mixed; device time with CUDA events."""
+    import torch
+
+    from paper_1812_07167_gb300 import hps
+
+    spec = W.ragged_batch()
+    out = {"problems": len(spec), "m": [m for m, _, _ in spec], "p": P_ORDER,
+           "dof": sum(m * m * (P_ORDER * P_ORDER - 4) for m, _, _ in spec)}
+    cs = []
+    for m, kap, cfun in spec:
+        lxy, _ = hps.hps_nodes(hps.Problem(m, P_ORDER, kap, kap))
+        nb = 4 * (P_ORDER - 2)
+        cs.append(torch.from_numpy(cfun(lxy[:, nb:, 0], lxy[:, nb:, 1])).to(dev))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    us = {}
+    for name, prec in (("fp64", hps.HPS_FP64), ("mixed", hps.HPS_MIXED)):
+        probs = [hps.Problem(m, P_ORDER, kap, kap, precision=prec) for m, kap, _ in spec]
+        res = {}
+        for mode in ("batched", "separate"):
+            ms = []
+            for rep in range(reps + 1):
+                flush.zero_()
+                e0.record(st)
+                if mode == "batched":
+                    hs = hps.hps_build_batch(probs, cs, st)
+                else:
+                    hs = [hps.hps_build(pr, c, st) for pr, c in zip(probs, cs)]
+                e1.record(st)
+                torch.cuda.synchronize()
+                if rep:
+                    ms.append(e0.elapsed_time(e1))
+                if rep == reps:
+                    k = max(range(len(spec)), key=lambda i: spec[i][0])
+                    _, s1, t1 = W.random_data(spec[k][0], P_ORDER, spec[k][1], spec[k][1], seed=9)
+                    u = torch.empty((1, spec[k][0] ** 2, P_ORDER * P_ORDER - 4), dtype=torch.complex128, device=dev)
+                    hps.hps_solve(hs[k], torch.from_numpy(s1[None]).to(dev), torch.from_numpy(t1[None]).to(dev), u, 1, st)
+                    us[(name, mode)] = u.cpu().numpy()
+                    res[f"{mode}_launches"] = (hs[0].info().build_launches if mode == "batched"
+                                               else sum(h.info().build_launches for h in hs))
+                for h in hs:
+                    h.free()
+            res[f"{mode}_ms"] = statistics.median(ms)
+            res[f"{mode}_dof_per_s"] = out["dof"] / (statistics.median(ms) / 1e3)
+        res["speedup"] = res["separate_ms"] / res["batched_ms"]
+        a, b = us[(name, "batched")], us[(name, "separate")]
+        res["rel_diff_u_batched_vs_separate"] = float(np.abs(a - b).max() / np.abs(b).max())
+        out[name] = res
+    a, b = us[("mixed", "batched")], us[("fp64", "batched")]
+    out["mixed"]["rel_err_u_vs_fp64"] = float(np.abs(a - b).max() / np.abs(b).max())
+    return out
 
 
 def serving_run(args, local_rank, precision):

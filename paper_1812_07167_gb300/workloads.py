@@ -295,3 +295,16 @@ def request_stream(seed: int, count: int, rate: float, solve_frac: float = 0.9, 
                             m=int(build_m[int(r[4 * k + 2] * len(build_m))]),
                             kappa=float(lo + (hi - lo) * r[4 * k + 3]), seed=seed * 1000 + k))
     return out
+
+
+def ragged_batch(count: int = 32, seed0: int = 100, p: int = 16, ms=(8, 16, 32), kappa_range=(20.0, 200.0)):
+    """Independent problems of different sizes for batched builds: problem k
+    (seed seed0 + k) has m x m leaves with m uniform in ``ms``, kappa = eta
+    uniform in ``kappa_range`` and the random smooth medium of that seed
+    (32 Fourier modes, c in [0.5, 1.5]).  Returns a list of (m, kappa, c)."""
+    out = []
+    lo, hi = kappa_range
+    for k in range(count):
+        r = uniform(seed0 + k, 2, offset=1 << 44)
+        out.append((int(ms[int(r[0] * len(ms))]), float(lo + (hi - lo) * r[1]), random_medium(seed0 + k)))
+    return out
