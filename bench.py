@@ -323,7 +323,7 @@ def ours(args, rank, world, local_rank):
     minfo = hm.info()
     hm.free()
 
-    batch_res = batching(dev, st, flush)
+    batch_res = None if args.no_batching else batching(dev, st, flush)
 
     if rank != 0:
         return
@@ -441,6 +441,96 @@ def batching(dev, st, flush, reps=2):
     a, b = us[("mixed", "batched")], us[("fp64", "batched")]
     out["mixed"]["rel_err_u_vs_fp64"] = float(np.abs(a - b).max() / np.abs(b).max())
     return out
+
+
+def precision(args, local_rank):
+    """64 x 64 leaves (1,032,192 unknowns), p = 16, kappa = eta = 300, random
+    medium (seed 2) with 8 Gaussian sources, t = 0: the complex128 path
+    against the mixed path (complex64 leaves and lower merges, complex128 top
+    4 levels, complex128 refinement), both against the oracle, whose full
+    build + solve on the host cores is this mode's CPU baseline."""
+    import torch
+
+    from paper_1812_07167_gb300 import hps
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    st = torch.cuda.current_stream()
+    m, p, kappa = 64, P_ORDER, 300.0
+    wl = W.random_medium_sources(m, p, kappa)
+    pr = hps.Problem(m, p, kappa, kappa)
+    lxy, bxy = hps.hps_nodes(pr)
+    c, s, t = wl.sample(lxy, bxy)
+    cd = torch.from_numpy(c).to(dev)
+    sd = torch.from_numpy(np.ascontiguousarray(s[None])).to(dev)
+    td = torch.from_numpy(np.ascontiguousarray(t[None])).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dof = pr.leaves * pr.n
+    out = {"metric": "HPS build DOF/s and solve RHS/s at stated rel. error (64x64 leaves, FP64 vs mixed)",
+           "unit": "DOF/s", "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "helmholtz_random_medium_sources", "leaves": f"{m}x{m}", "p": p, "q": p - 2,
+                      "kappa": kappa, "eta": kappa, "c": "random medium, 32 Fourier modes, seed 2",
+                      "s": "8 Gaussian sources, width 0.01", "t": 0, "dof": dof}}
+    res = {}
+    with ClockSampler(local_rank) as clk:
+        for name, prec in (("fp64", hps.HPS_FP64), ("mixed", hps.HPS_MIXED)):
+            q = hps.Problem(m, p, kappa, kappa, precision=prec)
+            bms = []
+            for rep in range(4):
+                flush.zero_()
+                e0.record(st)
+                h = hps.hps_build(q, cd, st)
+                e1.record(st)
+                torch.cuda.synchronize()
+                if rep:
+                    bms.append(e0.elapsed_time(e1))
+                if rep < 3:
+                    h.free()
+            code = hps.hps_status(h, st)[0]
+            u = torch.empty((1, pr.leaves, pr.n), dtype=torch.complex128, device=dev)
+            sms = []
+            for rep in range(6):
+                flush.zero_()
+                e0.record(st)
+                hps.hps_solve(h, sd, td, u, 1, st)
+                e1.record(st)
+                torch.cuda.synchronize()
+                if rep:
+                    sms.append(e0.elapsed_time(e1))
+            R = np.zeros((pr.nbdry, pr.nbdry), complex)
+            hps.hps_root_R(h, R, st)
+            info = h.info()
+            res[name] = {"u": u.cpu().numpy()[0], "R": R}
+            out[name] = {"status": hps.hps_strerror(code), "build_ms": statistics.median(bms),
+                         "build_dof_per_s": dof / (statistics.median(bms) / 1e3),
+                         "solve_ms_1rhs": statistics.median(sms), "solve_rhs_per_s": 1e3 / statistics.median(sms),
+                         "operator_bytes": info.operator_bytes, "build_launches": info.build_launches,
+                         "leaf_and_level_ms": [float(x) for x in hps.hps_build_times(h)]}
+            h.free()
+    out["clocks"] = clk.summary()
+    uf, um = res["fp64"]["u"], res["mixed"]["u"]
+    Rf, Rm = res["fp64"]["R"], res["mixed"]["R"]
+    out["mixed"]["rel_err_u_vs_fp64_gpu"] = float(np.abs(um - uf).max() / np.abs(uf).max())
+    out["mixed"]["rel_err_root_R_vs_fp64_gpu"] = float(np.linalg.norm(Rm - Rf) / np.linalg.norm(Rf))
+    out["value"] = out["mixed"]["build_dof_per_s"]
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        threads = os.cpu_count() or 1
+        opr = O.Problem(m, p, kappa, kappa)
+        t0 = time.perf_counter()
+        T = O.Tree(opr, c, nthreads=threads)
+        uo = T.solve(s[None], t[None], nthreads=threads)[0]
+        dt = time.perf_counter() - t0
+        Ro = T.root_R()
+        T.close()
+        out["cpu_baseline"] = {"value": dof / dt, "unit": "DOF/s", "cores": threads, "kind": "oracle",
+                               "sample": "one full 64x64-leaf build + 1-RHS solve", "seconds": dt}
+        for name in ("fp64", "mixed"):
+            out[name]["rel_err_u_vs_oracle"] = float(np.abs(res[name]["u"] - uo).max() / np.abs(uo).max())
+            out[name]["rel_err_root_R_vs_oracle"] = float(np.linalg.norm(res[name]["R"] - Ro) / np.linalg.norm(Ro))
+    print(json.dumps(out), flush=True)
 
 
 def serving_run(args, local_rank, precision):
@@ -562,6 +652,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead of the step bench")
+    ap.add_argument("--precision", action="store_true",
+                    help="run the 64x64-leaf FP64-vs-mixed workload (with the oracle) instead of the step bench")
+    ap.add_argument("--no-batching", action="store_true", help="skip the ragged-batch section")
     ap.add_argument("--serve-m", type=int, default=128)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-max-rhs", type=int, default=128)
@@ -574,6 +667,9 @@ def main():
         return
     if args.serve:
         serving(args, local_rank)
+        return
+    if args.precision:
+        precision(args, local_rank)
         return
     if world > 1:
         import torch.distributed as dist
