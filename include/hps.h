@@ -86,6 +86,12 @@ typedef struct {
   int fp64_levels;       /* HPS_MIXED: merge levels kept in complex128, counted
                             from the root; 0 = 4 (clamped to the tree depth) */
   int refine_steps;      /* HPS_MIXED: refinement steps per solve; 0 = 2, < 0 = none */
+  int fp64_native;       /* 0: complex128 merge products large enough to pay for it
+                            (K >= 64, M, N >= 32, M N K batch >= 2^24) are done by
+                            the Ozaki scheme on the bf16 tensor cores (7 slices per
+                            operand, exact FP32 accumulation of the slice products,
+                            complex128 sums: error ~2^-56 max|A_i.| max|B_.j| per
+                            term); 1: every complex128 product on the FP64 pipes */
 } hps_desc;
 
 typedef struct hps_handle hps_handle;
@@ -133,7 +139,7 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
  * sizes of level j (counted from the leaves) depend on j and p only, so the
  * problems' parents on that level form one batch of equal-size merges.
  *   descs[k], c[k]: problem k as for hps_build.  Every desc must have the
- *     same p, precision and fp64_levels (HPS_EINVAL otherwise); m, the
+ *     same p, precision, fp64_levels and fp64_native (HPS_EINVAL otherwise); m, the
  *     domain, kappa and eta may differ.
  *   out[k] receives problem k's handle.  The handles share one device
  *     allocation, released with the last of them; hps_free each one.
@@ -232,6 +238,17 @@ int hps_root_R(hps_handle *h, double *R, void *stream);
  *   complex row-major; any may be NULL.
  * Returns HPS_EINVAL for a leaf index out of range. */
 int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, void *stream);
+
+/* Batched complex GEMM C = A B with the library's product kernels (a
+ * diagnostic of them): batch matrices, column-major and densely strided
+ * (A: M x K, B: K x N, C: M x N; batch strides M K, K N, M N elements).
+ * emulated = 0: complex128 on the FP64 pipes; 1: the Ozaki scheme on the
+ * bf16 tensor cores, as the build runs its large complex128 merge products
+ * (any size is accepted here).  Device arrays only; enqueued on `stream`.
+ * Returns HPS_EINVAL (sizes < 1, NULL or host arrays, emulated not 0 / 1),
+ * HPS_ENOMEM (workspace), HPS_ECUDA. */
+int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, double *C, int emulated,
+              void *stream);
 
 /* Sizes and operation counts of the solver hps_build would create for desc,
  * without building it (host only, no device work): the admission check of a

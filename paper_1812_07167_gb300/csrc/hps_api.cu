@@ -65,6 +65,7 @@ struct Plan {
   bool mixed;                   // HPS_MIXED
   int leaf_f32;                 // leaf operators in complex64
   int refine_steps;             // refinement steps of a mixed solve
+  bool oz;                      // large complex128 merge products on the tensor cores
   std::vector<Level> lv;        // lv[j]: merge j from the leaves up (parents on level L-1-j)
   std::vector<int> root_src;    // root position -> public boundary index
   std::vector<int> outer;       // public boundary index -> leaf * nb + node
@@ -124,6 +125,7 @@ int check_desc(const hps_desc *d) {
   if (d->eta_re == 0.0 || !std::isfinite(d->eta_re) || !std::isfinite(d->eta_im)) return HPS_EINVAL;
   if (d->precision != HPS_FP64 && d->precision != HPS_MIXED) return HPS_EINVAL;
   if (d->fp64_levels < 0) return HPS_EINVAL;
+  if (d->fp64_native != 0 && d->fp64_native != 1) return HPS_EINVAL;
   return HPS_OK;
 }
 
@@ -197,6 +199,7 @@ void make_plan(const hps_desc &d, Plan &pl) {
   pl.mixed = (d.precision == HPS_MIXED);
   pl.leaf_f32 = pl.mixed ? 1 : 0;
   pl.refine_steps = d.refine_steps == 0 ? 2 : (d.refine_steps < 0 ? 0 : d.refine_steps);
+  pl.oz = (d.fp64_native == 0);
   const int top = std::min(pl.L, d.fp64_levels == 0 ? 4 : d.fp64_levels);
   const int e = pl.e;
   std::vector<Canon> cur(pl.nb);
@@ -437,6 +440,49 @@ bool choose_gj(int n3, long long P, int f32, GJChoice &g) {
 }
 
 int gj_launches(int n3, const GJChoice &g) { return g.wide ? (n3 + 7) / 8 + 2 : 1; }
+
+// Does a product of this shape go to the tensor cores (Ozaki scheme)?
+bool oz_shape(int M, int N, int K, int batch, int f32, bool oz) {
+  if (!oz || f32) return false;
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.batch = batch;
+  return hps::oz_eligible(g);
+}
+
+size_t oz_bytes_shape(int M, int N, int K, int batch) {
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.batch = batch;
+  return hps::oz_workspace_bytes(g);
+}
+
+// The six products of one merge run of P parents (Sec. 2.2): W, Q, Phi_a,
+// Phi_b, and the two halves of R^tau, as (M, N, K).
+void merge_products(int n1, int n2, int n3, int nt, int (&mnk)[6][3]) {
+  const int v[6][3] = {{n3, n3, n3}, {n3, n1, n3}, {n3, nt, n3}, {n3, nt, n3}, {n1, nt, n3}, {n2, nt, n3}};
+  memcpy(mnk, v, sizeof(v));
+}
+
+// Kernel launches of one merge run: the copy, W^{-1}, and the products (an
+// emulated product is three launches; the two halves of R^tau share one
+// launch when both run on the FP64 pipes).
+int merge_launches(int n1, int n2, int n3, int nt, int P, int f32, bool oz, const GJChoice &gj) {
+  int mnk[6][3];
+  merge_products(n1, n2, n3, nt, mnk);
+  int n = 1 + gj_launches(n3, gj);
+  for (int q = 0; q < 4; q++) n += oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], P, f32, oz) ? 3 : 1;
+  const bool a = oz_shape(mnk[4][0], mnk[4][1], mnk[4][2], P, f32, oz);
+  const bool b = oz_shape(mnk[5][0], mnk[5][1], mnk[5][2], P, f32, oz);
+  n += (a ? 3 : 0) + (b ? 3 : 0) + ((!a || !b) ? 1 : 0);
+  return n;
+}
 
 int grow(void **buf, size_t *have, size_t need) {
   if (*have >= need) return HPS_OK;
@@ -1104,16 +1150,47 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     }
     rbytes = std::max(rbytes, rb);
   }
+  // workspace of the products done on the tensor cores
+  size_t oz_bytes = 0;
+  for (int j = 0; j < Lmax; j++) {
+    const Level &S = P0.lv[j];
+    int mnk[6][3];
+    merge_products(S.n1, S.n2, S.n3, S.nt, mnk);
+    for (const BuildRun &r : runs[j])
+      for (int q = 0; q < 6; q++)
+        if (oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P, r.f32, P0.oz))
+          oz_bytes = std::max(oz_bytes, oz_bytes_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P));
+  }
   char *scratch = nullptr;
   int *wmeta = nullptr;
+  const size_t sbytes = 2 * rbytes + sizeof(double2) * (qbuf + wbuf + cbuf);
   if (Lmax > 0) {
-    CK(cudaMallocAsync((void **)&scratch, 2 * rbytes + sizeof(double2) * (qbuf + wbuf + cbuf), st));
+    CK(cudaMallocAsync((void **)&scratch, align256(sbytes) + oz_bytes, st));
     CK(cudaMallocAsync((void **)&wmeta, sizeof(int) * std::max<size_t>(mbuf, 1), st));
   }
   char *Rbuf[2] = {scratch, scratch + rbytes};
   double2 *Q = (double2 *)(scratch + 2 * rbytes);
   double2 *Wscr = Q + qbuf;
   double2 *Rconv = Wscr + wbuf;
+  void *ozws = oz_bytes ? scratch + align256(sbytes) : nullptr;
+  // products: emulated ones one at a time, the rest in one launch
+  auto run_gemm = [&](GemmDesc *gd, int nd) -> int {
+    GemmDesc rest[2];
+    int nr = 0;
+    for (int q = 0; q < nd; q++) {
+      if (P0.oz && hps::oz_eligible(gd[q])) {
+        CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, st));
+        launches += 3;
+      } else {
+        rest[nr++] = gd[q];
+      }
+    }
+    if (nr) {
+      CK(hps::launch_gemm(rest, nr, st));
+      launches++;
+    }
+    return HPS_OK;
+  };
 
   auto sub = [&](Mat m, const int *r, const int *c) {
     m.rmap = r;
@@ -1199,7 +1276,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
       g.alpha = make_double2(-1.0, 0.0);
       g.addI = 1;
       g.cf32 = f;
-      CK(hps::launch_gemm(&g, 1, st));
+      if (int rc = run_gemm(&g, 1)) return rc;
       const int lev = S.lev;  // the tallest tree's level numbering
       if (r.gj.wide)
         CK(hps::launch_gj_wide(Wscr, Winv, n3, P, r.gj.wide, wmeta, d_status, lev, f != 0, st));
@@ -1208,18 +1285,18 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
       // Q(:, :n1) = R33b R31a
       g = gemm(n3, n1, n3, P, M(R33b, n3, s33), sub(Ra, dI3a, dI1), M(Q, n3, s3t));
       g.cf32 = f;
-      CK(hps::launch_gemm(&g, 1, st));
+      if (int rc = run_gemm(&g, 1)) return rc;
       // Phi_a = W^{-1} Q
       g = gemm(n3, nt, n3, P, M(Winv, n3, s33), M(Q, n3, s3t), M(Phia, n3, s3t));
       g.cf32 = f;
-      CK(hps::launch_gemm(&g, 1, st));
+      if (int rc = run_gemm(&g, 1)) return rc;
       // Phi_b = -[R31a | 0] - R33a Phi_a
       g = gemm(n3, nt, n3, P, M(R33a, n3, s33), M(Phia, n3, s3t), M(Phib, n3, s3t));
       g.alpha = make_double2(-1.0, 0.0);
       g.D = g.C;
       g.beta = make_double2(1.0, 0.0);
       g.cf32 = f;
-      CK(hps::launch_gemm(&g, 1, st));
+      if (int rc = run_gemm(&g, 1)) return rc;
       // R^tau = diag(R11a, R22b) + diag(R13a, R23b) [Phi_a; Phi_b]
       GemmDesc g2[2];
       g2[0] = gemm(n1, nt, n3, P, M(R13a, n1, (long long)n1 * n3), M(Phia, n3, s3t), M(Rp, nt, sp));
@@ -1230,8 +1307,8 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
       g2[1].D = g2[1].C;
       g2[1].beta = make_double2(1.0, 0.0);
       g2[1].cf32 = f;
-      CK(hps::launch_gemm(g2, 2, st));
-      launches += 6 + gj_launches(n3, r.gj);
+      if (int rc = run_gemm(g2, 2)) return rc;
+      launches += 1 + gj_launches(n3, r.gj);  // the copy and W^{-1}
     }
     CK(cudaEventRecord(sh->ev[2 + j], st));
   }
@@ -1265,7 +1342,8 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
   for (const Level &L : h->plan.lv) {
     GJChoice g;
     if (!choose_gj(L.n3, L.P, L.f32, g)) return HPS_ENOTSUP;
-    h->info.build_launches += gj_launches(L.n3, g) - 1;
+    // fill_info counts 7 launches a level
+    h->info.build_launches += merge_launches(L.n1, L.n2, L.n3, L.nt, L.P, L.f32, h->plan.oz, g) - 7;
   }
   // transient build memory: the leaf elimination chunk, then the merge scratch
   const Plan &pl = h->plan;
@@ -1288,6 +1366,27 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
   SolveWs w1;
   solve_ws_layout(pl, 1, w1);
   h->info.solve_ws_bytes_per_rhs = (long long)w1.bytes;
+  return HPS_OK;
+}
+
+int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, double *C, int emulated,
+              void *stream) {
+  if (M < 1 || N < 1 || K < 1 || batch < 1 || batch > 65535 || (emulated != 0 && emulated != 1)) return HPS_EINVAL;
+  if (!A || !B || !C || !is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C)) return HPS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  GemmDesc g = gemm(M, N, K, batch, mat(A, M, (long long)M * K), mat(B, K, (long long)K * N),
+                    mat(C, M, (long long)M * N));
+  if (!emulated) {
+    CK(hps::launch_gemm(&g, 1, st));
+    return HPS_OK;
+  }
+  const size_t ws = hps::oz_workspace_bytes(g);
+  void *w = nullptr;
+  CK(cudaMallocAsync(&w, ws, st));
+  cudaError_t err = hps::launch_gemm_oz(g, w, ws, st);
+  cudaError_t err2 = cudaFreeAsync(w, st);
+  if (err != cudaSuccess) return cuda_fail(err);
+  if (err2 != cudaSuccess) return cuda_fail(err2);
   return HPS_OK;
 }
 
@@ -1315,7 +1414,7 @@ int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, vo
     if (st0) return st0;
     if (!c[k]) return HPS_EINVAL;
     if (descs[k].p != descs[0].p || descs[k].precision != descs[0].precision ||
-        descs[k].fp64_levels != descs[0].fp64_levels)
+        descs[k].fp64_levels != descs[0].fp64_levels || descs[k].fp64_native != descs[0].fp64_native)
       return HPS_EINVAL;
   }
   std::vector<hps_handle *> hs(nprob, nullptr);

@@ -75,6 +75,14 @@ struct DevStatus {
 
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st);
+
+// Complex128 GEMM emulated on the bf16 tensor cores (Ozaki scheme, 7 slices
+// per operand; accuracy ~2^-56 max|A_i.| max|B_.j| per term).  Same
+// semantics as launch_gemm for one descriptor with cf32 == 0; needs a
+// device workspace of oz_workspace_bytes(g).  Three launches.
+bool oz_eligible(const GemmDesc &g);
+size_t oz_workspace_bytes(const GemmDesc &g);
+cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st);
 cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st);
 
 // Leaf step (Sec. 2.1) for leaves [leaf0, leaf0 + count): assemble B, invert

@@ -27,7 +27,7 @@ HPS_MIXED = 1
 
 # every entry point include/hps.h declares
 EXPORTS = ("hps_nodes", "hps_build", "hps_build_batch", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
-           "hps_root_R", "hps_leaf_ops", "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
+           "hps_root_R", "hps_leaf_ops", "hps_zgemm", "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
 
 
 class hps_desc(ctypes.Structure):
@@ -40,6 +40,7 @@ class hps_desc(ctypes.Structure):
         ("eta_re", ctypes.c_double), ("eta_im", ctypes.c_double),
         ("precision", ctypes.c_int),
         ("fp64_levels", ctypes.c_int), ("refine_steps", ctypes.c_int),
+        ("fp64_native", ctypes.c_int),
     ]
 
 
@@ -81,6 +82,7 @@ def lib():
         L.hps_solve_noalloc.argtypes = [P, P, P, P, ctypes.c_int, P]
         L.hps_solve_batch.argtypes = [P, ctypes.c_int, P, P, P, P, P]
         L.hps_reserve.argtypes = [P, ctypes.c_int]
+        L.hps_zgemm.argtypes = [ctypes.c_int] * 4 + [P, P, P, ctypes.c_int, P]
         L.hps_root_R.argtypes = [P, P, P]
         L.hps_leaf_ops.argtypes = [P, ctypes.c_int, P, P, P, P]
         L.hps_info.argtypes = [P, ctypes.POINTER(hps_info_t)]
@@ -112,12 +114,13 @@ class Problem:
     precision: int = HPS_FP64
     fp64_levels: int = 0
     refine_steps: int = 0
+    fp64_native: int = 0
 
     def desc(self) -> hps_desc:
         eta = complex(self.eta)
         return hps_desc(self.x0, self.x1, self.y0, self.y1, self.m, self.m, self.p, self.p - 2,
                         float(self.kappa), eta.real, eta.imag, int(self.precision),
-                        int(self.fp64_levels), int(self.refine_steps))
+                        int(self.fp64_levels), int(self.refine_steps), int(self.fp64_native))
 
     @property
     def n(self) -> int:
@@ -251,6 +254,16 @@ def hps_solve_batch(h: Handle, s_list, t_list, u_list, nrhs_list, stream=None):
     nr = (ctypes.c_int * max(k, 1))(*[int(x) for x in nrhs_list])
     _check(lib().hps_solve_batch(h.ptr, k, sp, tp, up, nr, _stream(stream)), "hps_solve_batch")
     return u_list
+
+
+def hps_zgemm(A, B, C, emulated: int, stream=None):
+    """C[b] = A[b] B[b] for complex128 device tensors shaped [batch, K, M],
+    [batch, N, K], [batch, N, M] (column-major matrices stored transposed)."""
+    batch, K, M = A.shape
+    N = B.shape[1]
+    _check(lib().hps_zgemm(M, N, K, batch, _ptr(A), _ptr(B), _ptr(C), int(emulated), _stream(stream)),
+           "hps_zgemm")
+    return C
 
 
 def hps_reserve(h: Handle, nrhs: int):

@@ -62,7 +62,7 @@ def _desc(**kw):
     dict(mx=3, my=3), dict(mx=4, my=2), dict(mx=0, my=0), dict(p=3), dict(p=33), dict(q=5),
     dict(kappa=0.0), dict(kappa=-1.0), dict(eta_re=0.0, eta_im=1.0), dict(x1=0.0),
     dict(y1=-1.0), dict(precision=7), dict(precision=-1), dict(kappa=float("nan")),
-    dict(precision=1, fp64_levels=-2),
+    dict(precision=1, fp64_levels=-2), dict(fp64_native=2), dict(fp64_native=-1),
 ])
 def test_invalid_descriptor_is_rejected_before_device_work(bad):
     d = _desc(**bad)
@@ -114,3 +114,12 @@ def test_plan_reports_sizes_without_device_work():
     assert im.operator_bytes < 0.6 * info.operator_bytes
     bad = _desc(mx=3, my=3)
     assert hps.lib().hps_plan(ctypes.byref(bad), ctypes.byref(info)) == hps.HPS_EINVAL
+
+
+def test_zgemm_argument_checks_need_no_device():
+    L = hps.lib()
+    a = np.zeros(16, complex)
+    assert L.hps_zgemm(0, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, 0, None) == hps.HPS_EINVAL
+    assert L.hps_zgemm(2, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, 2, None) == hps.HPS_EINVAL
+    # host arrays are refused (device memory only)
+    assert L.hps_zgemm(2, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, 1, None) == hps.HPS_EINVAL
