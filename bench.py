@@ -533,6 +533,48 @@ def precision(args, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def zgemm(args, local_rank):
+    """One complex GEMM C = A B (M x K times K x N, batch 1) through
+    hps_zgemm: the Ozaki-scheme product on the bf16 tensor cores against the
+    FP64-pipe product, device time from CUDA events (median of 5 after 2
+    warm-ups), with the relative difference of the two results."""
+    import torch
+
+    from paper_1812_07167_gb300 import hps
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    st = torch.cuda.current_stream()
+    M, N, K = args.zgemm
+    g = torch.Generator(device=dev).manual_seed(7)
+    A = torch.randn((1, K, M), dtype=torch.complex128, device=dev, generator=g)
+    B = torch.randn((1, N, K), dtype=torch.complex128, device=dev, generator=g)
+    out = {"metric": "complex GEMM rate (FP64-equivalent flops: 8 M N K)", "unit": "TFLOP/s",
+           "higher_is_better": True, "n_gpus": 1, "data": "synthetic (normal entries)",
+           "config": {"workload": "zgemm", "M": M, "N": N, "K": K}}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Cs = {}
+    for name, emu in (("fp64_pipes", 0), ("tensor_cores", 1)):
+        C = torch.empty((1, N, M), dtype=torch.complex128, device=dev)
+        ts = []
+        for rep in range(7):
+            e0.record(st)
+            hps.hps_zgemm(A, B, C, emu, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            if rep >= 2:
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        out[name] = {"ms": ms, "tflops": 8.0 * M * N * K / (ms / 1e3) / 1e12}
+        Cs[name] = C
+    a, b = Cs["tensor_cores"], Cs["fp64_pipes"]
+    out["rel_diff"] = float(((a - b).abs().max() / b.abs().max()).item())
+    out["value"] = out["tensor_cores"]["tflops"]
+    # bf16 slice products the emulation issues: 45 pairs x 4 real products
+    out["tensor_cores"]["bf16_tflops"] = out["tensor_cores"]["tflops"] * 45
+    print(json.dumps(out), flush=True)
+
+
 def serving_run(args, local_rank, precision):
     """Config-5 serving workload: a 128 x 128-leaf solver (p = 16, kappa = eta
     = 600, random medium, seed 3) resident in HBM, and a Poisson stream of
@@ -655,6 +697,8 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="run the 64x64-leaf FP64-vs-mixed workload (with the oracle) instead of the step bench")
     ap.add_argument("--no-batching", action="store_true", help="skip the ragged-batch section")
+    ap.add_argument("--zgemm", type=int, nargs=3, metavar=("M", "N", "K"),
+                    help="time one complex GEMM on the tensor cores and on the FP64 pipes")
     ap.add_argument("--serve-m", type=int, default=128)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-max-rhs", type=int, default=128)
@@ -670,6 +714,9 @@ def main():
         return
     if args.precision:
         precision(args, local_rank)
+        return
+    if args.zgemm:
+        zgemm(args, local_rank)
         return
     if world > 1:
         import torch.distributed as dist

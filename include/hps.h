@@ -87,10 +87,10 @@ typedef struct {
                             from the root; 0 = 4 (clamped to the tree depth) */
   int refine_steps;      /* HPS_MIXED: refinement steps per solve; 0 = 2, < 0 = none */
   int fp64_native;       /* 0: complex128 merge products large enough to pay for it
-                            (K >= 64, M, N >= 32, M N K batch >= 2^24) are done by
-                            the Ozaki scheme on the bf16 tensor cores (7 slices per
-                            operand, exact FP32 accumulation of the slice products,
-                            complex128 sums: error ~2^-56 max|A_i.| max|B_.j| per
+                            (K >= 64, M, N >= 32, M N K batch >= 2^26) are done by
+                            the Ozaki scheme on the bf16 tensor cores (9 slices of 6
+                            bits per operand, exact FP32 accumulation of the slice products,
+                            complex128 sums: error ~2^-54 max|A_i.| max|B_.j| per
                             term); 1: every complex128 product on the FP64 pipes */
 } hps_desc;
 

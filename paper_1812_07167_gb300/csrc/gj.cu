@@ -30,6 +30,8 @@
 // and wait) per panel; no kernel here spins on a flag.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "hps_internal.h"
 
 namespace cg = cooperative_groups;
@@ -109,19 +111,24 @@ __host__ __device__ inline int npanels(int n) { return (n + KB - 1) / KB; }
 __host__ __device__ inline int meta_ints(int n) { return n + npanels(n) * kMoveInts; }
 
 struct SmemPlan {
-  size_t T, F, x, mvbuf, col, prow, mv, rows, srcs, scal, pinv, perm, dtab, grid, loc, cv, rsc, total;
+  size_t T, F, x, mvbuf, col, prow, krow, red, mv, rows, srcs, scal, pinv, perm, dtab, grid, loc, cv, rsc, total;
 };
 
-__host__ __device__ inline SmemPlan plan_smem(int n, int cw, bool leaf, int p, bool tglobal = false,
+// Panel placement: 0 = the panel being applied (T) and the one being
+// eliminated (F) both in shared memory, 1 = both read in place from the
+// global scratch, 2 = T in place and F in shared memory.
+__host__ __device__ inline SmemPlan plan_smem(int n, int cw, bool leaf, int p, int tmode = 0,
                                                size_t esz = 16) {
   SmemPlan s;
   size_t o = 0;
-  s.T = o;    if (!tglobal) o = align16(o + esz * (size_t)KB * n);
-  s.F = o;    if (!tglobal) o = align16(o + esz * (size_t)KB * n);
+  s.T = o;    if (tmode == 0) o = align16(o + esz * (size_t)KB * n);
+  s.F = o;    if (tmode != 1) o = align16(o + esz * (size_t)KB * n);
   s.x = o;    o = align16(o + esz * (size_t)KB * cw);
   s.mvbuf = o; o = align16(o + esz * (size_t)kMoves * cw);
   s.col = o;  o = align16(o + esz * (size_t)n);
   s.prow = o; o = align16(o + esz * KB);
+  s.krow = o; o = align16(o + esz * KB);
+  s.red = o;  o = align16(o + 16 * (kThreads / 32));
   s.mv = o;   o = align16(o + sizeof(int) * kMoveInts);
   s.rows = o; o = align16(o + sizeof(int) * 2 * KB);
   s.srcs = o; o = align16(o + sizeof(int) * 2 * KB);
@@ -150,6 +157,9 @@ struct Shared {
   C *mvbuf; // [cw][kMoves] values in flight during the row moves
   C *col;   // [n] pivot column of the current elimination step
   C *prow;  // [KB] scaled pivot row within the panel
+  C *krow;  // [KB] row k of the panel before the step's swap
+  unsigned long long *rkey;  // [warps] pivot search: best key of each warp
+  int *ridx;                 // [warps] and its row
   int *mv;        // [kMoveInts] row moves of the panel being applied
   int *rows;      // [2 KB] scratch for building a move list
   int *srcs;      // [2 KB]
@@ -168,6 +178,9 @@ __device__ Shared<C> bind(unsigned char *smem, const SmemPlan &sp, int n, int cw
   s.mvbuf = (C *)(smem + sp.mvbuf);
   s.col = (C *)(smem + sp.col);
   s.prow = (C *)(smem + sp.prow);
+  s.krow = (C *)(smem + sp.krow);
+  s.rkey = (unsigned long long *)(smem + sp.red);
+  s.ridx = (int *)(smem + sp.red + 8 * (kThreads / 32));
   s.mv = (int *)(smem + sp.mv);
   s.rows = (int *)(smem + sp.rows);
   s.srcs = (int *)(smem + sp.srcs);
@@ -181,8 +194,11 @@ __device__ Shared<C> bind(unsigned char *smem, const SmemPlan &sp, int n, int cw
 
 // Eliminate panel [k0, k0 + kbp) of S (column-major, ld n) in shared memory
 // and write it back; record its pivot rows and row moves in `meta`.
-// Returns true if a zero pivot was met.
-template <class C>
+// Returns true if a zero pivot was met.  For short columns one warp finds
+// each pivot; with kLong (long columns) every warp searches a share of the
+// rows and the pivot row is staged beside the pivot column (four barriers
+// a step either way).
+template <class C, bool kLong = false>
 __device__ bool eliminate_panel(const Shared<C> &s, C *S, int *meta, int k0, int kbp) {
   const int tid = threadIdx.x, nthr = blockDim.x, n = s.n;
   bool zero = false;
@@ -190,87 +206,169 @@ __device__ bool eliminate_panel(const Shared<C> &s, C *S, int *meta, int k0, int
   // panel does not fit next to the other buffers
   C *F = s.F ? s.F : S + (size_t)k0 * n;
   if (s.F)
-    for (int e = tid; e < kbp * n; e += nthr) {
-      const int q = e / n, i = e % n;
-      F[q * n + i] = S[(size_t)(k0 + q) * n + i];
-    }
+    for (int q = 0; q < kbp; q++)
+      for (int i = tid; i < n; i += nthr) F[q * n + i] = S[(size_t)(k0 + q) * n + i];
   __syncthreads();
-  for (int q = 0; q < kbp; q++) {
-    const int k = k0 + q;
-    const C *Fk = F + q * n;
-    if (tid < 32) {
+  if (!kLong) {
+    for (int q = 0; q < kbp; q++) {
+      const int k = k0 + q;
+      const C *Fk = F + q * n;
+      if (tid < 32) {
+        unsigned long long best = 0;
+        int bi = n;
+        for (int i = k + tid; i < n; i += 32) {
+          unsigned long long key = CX<C>::key(Fk[i]);
+          if (bi == n || key > best) {
+            best = key;
+            bi = i;
+          }
+        }
+        for (int off = 16; off; off >>= 1) {
+          unsigned long long ov = __shfl_down_sync(0xffffffffu, best, off);
+          int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (oi < n && (bi == n || ov > best || (ov == best && oi < bi))) {
+            best = ov;
+            bi = oi;
+          }
+        }
+        if (tid == 0) {
+          const int r = (bi < n) ? bi : k;
+          const C pv = Fk[r];
+          const bool z = (CX<C>::key(pv) == 0ull);
+          s.scal[0] = r;
+          s.scal[1] = z ? 1 : 0;
+          s.pinv[0] = z ? CX<C>::make(0.0, 0.0) : crecip(pv);
+          meta[k] = r;
+        }
+      }
+      __syncthreads();
+      const int r = s.scal[0];
+      if (s.scal[1]) zero = true;
+      const C pinv = s.pinv[0];
+      // swap rows k and r inside the panel
+      if (r != k)
+        for (int qq = tid; qq < kbp; qq += nthr) {
+          C t = F[qq * n + k];
+          F[qq * n + k] = F[qq * n + r];
+          F[qq * n + r] = t;
+        }
+      __syncthreads();
+      // pivot column with its pivot entry zeroed, and the scaled pivot row
+      for (int i = tid; i < n; i += nthr) s.col[i] = (i == k) ? CX<C>::make(0.0, 0.0) : Fk[i];
+      for (int qq = tid; qq < kbp; qq += nthr) s.prow[qq] = cmul(F[qq * n + k], pinv);
+      __syncthreads();
+      for (int e = tid; e < kbp * n; e += nthr) {
+        const int qq = e / n, i = e % n;
+        C *a = &F[qq * n + i];
+        if (qq == q) {
+          // the eliminated column becomes -col / pivot, 1 / pivot at the pivot
+          if (i == k) {
+            *a = pinv;
+          } else {
+            C f = cmul(s.col[i], pinv);
+            *a = CX<C>::make(-f.x, -f.y);
+          }
+        } else if (i == k) {
+          *a = s.prow[qq];
+        } else {
+          C f = s.col[i], pr = s.prow[qq], v = *a;
+          v.x = CX<C>::fmad(-f.x, pr.x, v.x);
+          v.x = CX<C>::fmad(f.y, pr.y, v.x);
+          v.y = CX<C>::fmad(-f.x, pr.y, v.y);
+          v.y = CX<C>::fmad(-f.y, pr.x, v.y);
+          *a = v;
+        }
+      }
+      __syncthreads();
+    }
+  } else {
+    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    for (int q = 0; q < kbp; q++) {
+      const int k = k0 + q;
+      C *Fk = F + q * n;
+      // pivot: largest max(|Re|, |Im|) at or below row k, lowest row on ties
       unsigned long long best = 0;
       int bi = n;
-      for (int i = k + tid; i < n; i += 32) {
-        unsigned long long key = CX<C>::key(Fk[i]);
+      for (int i = k + tid; i < n; i += nthr) {
+        const unsigned long long key = CX<C>::key(Fk[i]);
         if (bi == n || key > best) {
           best = key;
           bi = i;
         }
       }
       for (int off = 16; off; off >>= 1) {
-        unsigned long long ov = __shfl_down_sync(0xffffffffu, best, off);
-        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        const unsigned long long ov = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
         if (oi < n && (bi == n || ov > best || (ov == best && oi < bi))) {
           best = ov;
           bi = oi;
         }
       }
-      if (tid == 0) {
-        const int r = (bi < n) ? bi : k;
-        const C pv = Fk[r];
-        const bool z = (CX<C>::key(pv) == 0ull);
-        s.scal[0] = r;
-        s.scal[1] = z ? 1 : 0;
-        s.pinv[0] = z ? CX<C>::make(0.0, 0.0) : crecip(pv);
-        meta[k] = r;
+      if (lane == 0) {
+        s.rkey[wid] = best;
+        s.ridx[wid] = bi;
       }
-    }
-    __syncthreads();
-    const int r = s.scal[0];
-    if (s.scal[1]) zero = true;
-    const C pinv = s.pinv[0];
-    // swap rows k and r inside the panel
-    if (r != k)
-      for (int qq = tid; qq < kbp; qq += nthr) {
-        C t = F[qq * n + k];
-        F[qq * n + k] = F[qq * n + r];
-        F[qq * n + r] = t;
-      }
-    __syncthreads();
-    // pivot column with its pivot entry zeroed, and the scaled pivot row
-    for (int i = tid; i < n; i += nthr) s.col[i] = (i == k) ? CX<C>::make(0.0, 0.0) : Fk[i];
-    for (int qq = tid; qq < kbp; qq += nthr) s.prow[qq] = cmul(F[qq * n + k], pinv);
-    __syncthreads();
-    for (int e = tid; e < kbp * n; e += nthr) {
-      const int qq = e / n, i = e % n;
-      C *a = &F[qq * n + i];
-      if (qq == q) {
-        // the eliminated column becomes -col / pivot, 1 / pivot at the pivot
-        if (i == k) {
-          *a = pinv;
-        } else {
-          C f = cmul(s.col[i], pinv);
-          *a = CX<C>::make(-f.x, -f.y);
+      __syncthreads();
+      best = 0;
+      bi = n;
+      for (int w = 0; w < nw; w++) {
+        const unsigned long long ov = s.rkey[w];
+        const int oi = s.ridx[w];
+        if (oi < n && (bi == n || ov > best || (ov == best && oi < bi))) {
+          best = ov;
+          bi = oi;
         }
-      } else if (i == k) {
-        *a = s.prow[qq];
-      } else {
-        C f = s.col[i], pr = s.prow[qq], v = *a;
-        v.x = CX<C>::fmad(-f.x, pr.x, v.x);
-        v.x = CX<C>::fmad(f.y, pr.y, v.x);
-        v.y = CX<C>::fmad(-f.x, pr.y, v.y);
-        v.y = CX<C>::fmad(-f.y, pr.x, v.y);
-        *a = v;
       }
+      const int r = (bi < n) ? bi : k;
+      const C pv = Fk[r];
+      const bool zpiv = CX<C>::key(pv) == 0ull;
+      if (zpiv) zero = true;
+      if (tid == 0) {
+        meta[k] = r;
+        s.pinv[0] = zpiv ? CX<C>::make(0.0, 0.0) : crecip(pv);
+      }
+      __syncthreads();
+      const C pinv = s.pinv[0];
+      // the pivot column after the swap of rows k and r (zero at k), the
+      // scaled pivot row (old row r) and old row k
+      for (int i = tid; i < n; i += nthr) s.col[i] = (i == k) ? CX<C>::make(0.0, 0.0) : Fk[i == r ? k : i];
+      if (tid < kbp) {
+        s.prow[tid] = cmul(F[tid * n + r], pinv);
+        s.krow[tid] = F[tid * n + k];
+      }
+      __syncthreads();
+      for (int qq = 0; qq < kbp; qq++) {
+        C *Fq = F + qq * n;
+        const C pr = s.prow[qq], kr = s.krow[qq];
+        for (int i = tid; i < n; i += nthr) {
+          C v;
+          if (qq == q) {
+            // the eliminated column becomes -col / pivot, 1 / pivot at the pivot
+            if (i == k) {
+              v = pinv;
+            } else {
+              const C f = cmul(s.col[i], pinv);
+              v = CX<C>::make(-f.x, -f.y);
+            }
+          } else if (i == k) {
+            v = pr;
+          } else {
+            const C f = s.col[i];
+            v = (i == r) ? kr : Fq[i];
+            v.x = CX<C>::fmad(-f.x, pr.x, v.x);
+            v.x = CX<C>::fmad(f.y, pr.y, v.x);
+            v.y = CX<C>::fmad(-f.x, pr.y, v.y);
+            v.y = CX<C>::fmad(-f.y, pr.x, v.y);
+          }
+          Fq[i] = v;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   if (s.F)
-    for (int e = tid; e < kbp * n; e += nthr) {
-      const int q = e / n, i = e % n;
-      S[(size_t)(k0 + q) * n + i] = F[q * n + i];
-    }
+    for (int q = 0; q < kbp; q++)
+      for (int i = tid; i < n; i += nthr) S[(size_t)(k0 + q) * n + i] = F[q * n + i];
   if (tid == 0) {
     // net row moves of the panel's swaps: after the swaps (k, piv[k]) in
     // order, row rows[t] holds what row srcs[t] held before
@@ -395,10 +493,8 @@ __device__ bool gj_blocked(const Shared<C> &s, C *S, int *meta, int rank) {
     const int k0 = p * KB, kbp = min(KB, n - k0);
     const C *T = s.T ? s.T : S + (size_t)k0 * n;
     if (s.T)
-      for (int e = threadIdx.x; e < kbp * n; e += blockDim.x) {
-        const int q = e / n, i = e % n;
-        s.T[q * n + i] = S[(size_t)(k0 + q) * n + i];
-      }
+      for (int q = 0; q < kbp; q++)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s.T[q * n + i] = S[(size_t)(k0 + q) * n + i];
     for (int t = threadIdx.x; t < kMoveInts; t += blockDim.x) s.mv[t] = meta[n + p * kMoveInts + t];
     __syncthreads();
     const int kn0 = (p + 1) * KB, kbn = (p + 1 < np) ? min(KB, n - kn0) : 0;
@@ -620,7 +716,7 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
 }
 
 struct GJArgs {
-  int tglobal;    // panels read in place from S instead of shared memory
+  int tglobal;    // panel placement (plan_smem's tmode): 0 shared memory, 1 in place
   void *S;        // [batch][n][n] column-major input, destroyed (element type C)
   void *out;      // [batch][n][n] column-major inverse
   int *meta;      // [batch][meta_ints(n)]
@@ -639,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, 2) gj_kernel(const __grid_constant__
   const int mat = blockIdx.x / cs;
   const int n = a.n, cw = a.cw, c0 = rank * cw;
   const int ncols = max(0, min(cw, n - c0));
-  const SmemPlan sp = plan_smem(n, cw, false, 0, a.tglobal != 0, sizeof(C));
+  const SmemPlan sp = plan_smem(n, cw, false, 0, a.tglobal, sizeof(C));
   const Shared<C> s = bind<C>(smem, sp, n, cw);
   C *S = (C *)a.S + (size_t)mat * n * n;
   int *meta = a.meta + (size_t)mat * meta_ints(n);
@@ -661,7 +757,7 @@ __global__ void __launch_bounds__(kThreads, 2) gj_kernel(const __grid_constant__
 // stream is the barrier between rounds.  Phase -1 eliminates panel 0 only;
 // phase np writes the inverse out with the column permutation.
 struct WideArgs {
-  int tglobal;  // panels read in place from S instead of shared memory
+  int tglobal;  // panel placement (plan_smem's tmode)
   void *S;      // [batch][n][n] column-major input, destroyed
   void *out;    // [batch][n][n] column-major inverse
   int *meta;    // [batch][meta_ints(n)]
@@ -671,12 +767,12 @@ struct WideArgs {
 };
 
 template <class C>
-__global__ void __launch_bounds__(kThreads) gj_wide_kernel(const __grid_constant__ WideArgs a, int phase) {
+__global__ void __launch_bounds__(kThreads, 2) gj_wide_kernel(const __grid_constant__ WideArgs a, int phase) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, G = a.G;
   const int mat = blockIdx.x / G, g = blockIdx.x % G;
   const int cwmax = a.slab > KB ? a.slab : KB;
-  const SmemPlan sp = plan_smem(n, cwmax, false, 0, a.tglobal != 0, sizeof(C));
+  const SmemPlan sp = plan_smem(n, cwmax, false, 0, a.tglobal, sizeof(C));
   const Shared<C> s = bind<C>(smem, sp, n, cwmax);
   C *S = (C *)a.S + (size_t)mat * n * n;
   int *meta = a.meta + (size_t)mat * meta_ints(n);
@@ -685,8 +781,11 @@ __global__ void __launch_bounds__(kThreads) gj_wide_kernel(const __grid_constant
   const int c0 = (g - 1) * a.slab;
   const int nc = (g >= 1) ? max(0, min(a.slab, n - c0)) : 0;
   if (phase < 0) {
-    if (g == 0 && eliminate_panel<C>(s, S, meta, 0, min(KB, n)) && threadIdx.x == 0)
-      record_status(a.status, 2u, a.level, mat);
+    if (g == 0) {
+      const bool z = (n > 512) ? eliminate_panel<C, true>(s, S, meta, 0, min(KB, n))
+                               : eliminate_panel<C, false>(s, S, meta, 0, min(KB, n));
+      if (z && threadIdx.x == 0) record_status(a.status, 2u, a.level, mat);
+    }
     return;
   }
   if (phase >= np) {
@@ -703,17 +802,16 @@ __global__ void __launch_bounds__(kThreads) gj_wide_kernel(const __grid_constant
   const int kn0 = (phase + 1) * KB, kbn = (phase + 1 < np) ? min(KB, n - kn0) : 0;
   const C *T = s.T ? s.T : S + (size_t)k0 * n;
   if (s.T)
-    for (int e = threadIdx.x; e < kbp * n; e += blockDim.x) {
-      const int q = e / n, i = e % n;
-      s.T[q * n + i] = S[(size_t)(k0 + q) * n + i];
-    }
+    for (int q = 0; q < kbp; q++)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) s.T[q * n + i] = S[(size_t)(k0 + q) * n + i];
   for (int t = threadIdx.x; t < kMoveInts; t += blockDim.x) s.mv[t] = meta[n + phase * kMoveInts + t];
   __syncthreads();
   if (g == 0) {
     if (kbn > 0) {
       apply_panel<C>(s, T, S, kn0, 0, kbn, k0, k0 + kbp, 0, 0, k0, kbp);
-      if (eliminate_panel<C>(s, S, meta, kn0, kbn) && threadIdx.x == 0)
-        record_status(a.status, 2u, a.level, mat);
+      const bool z = (n > 512) ? eliminate_panel<C, true>(s, S, meta, kn0, kbn)
+                               : eliminate_panel<C, false>(s, S, meta, kn0, kbn);
+      if (z && threadIdx.x == 0) record_status(a.status, 2u, a.level, mat);
     }
   } else if (nc > 0) {
     apply_panel<C>(s, T, S, c0, 0, nc, k0, k0 + kbp, kn0, kn0 + kbn, k0, kbp);
@@ -755,13 +853,13 @@ int gj_slab(int n, int cs) {
 }
 
 size_t gj_smem_bytes(int n, int cs, bool leaf, int p, bool tglobal, bool f32) {
-  return plan_smem(n, gj_slab(n, cs), leaf, p, tglobal, f32 ? 8 : 16).total;
+  return plan_smem(n, gj_slab(n, cs), leaf, p, tglobal ? 1 : 0, f32 ? 8 : 16).total;
 }
 
 size_t gj_meta_ints(int n) { return (size_t)meta_ints(n); }
 
 size_t gj_wide_smem_bytes(int n, int slab, bool f32, bool tglobal) {
-  return plan_smem(n, slab > KB ? slab : KB, false, 0, tglobal, f32 ? 8 : 16).total;
+  return plan_smem(n, slab > KB ? slab : KB, false, 0, tglobal ? 1 : 0, f32 ? 8 : 16).total;
 }
 
 cudaError_t launch_gj_wide(void *S, void *out, int n, int batch, int G, int *meta,
@@ -773,12 +871,29 @@ cudaError_t launch_gj_wide(void *S, void *out, int n, int batch, int G, int *met
   a.out = out;
   a.meta = meta;
   a.n = n;
-  a.G = G;
-  a.slab = (n + G - 2) / (G - 1);
   a.status = status;
   a.level = level;
-  a.tglobal = gj_wide_smem_bytes(n, a.slab, f32, false) > 200 * 1024 ? 1 : 0;
-  const size_t smem = gj_wide_smem_bytes(n, a.slab, f32, a.tglobal != 0);
+  // Panel placement: both panels in shared memory when they fit; else the
+  // eliminated one (the serial part) there and the applied one read in
+  // place; else both in place.  Every CTA of a panel launch should be
+  // resident at once (one wave): fewer CTAs per matrix when the shared
+  // memory allows less than two per SM.
+  const size_t esz = f32 ? 8 : 16;
+  size_t smem = 0;
+  for (int it = 0; it < 3; it++) {
+    a.G = G;
+    a.slab = (n + G - 2) / (G - 1);
+    const int cwmax = a.slab > KB ? a.slab : KB;
+    a.tglobal = 0;
+    if (plan_smem(n, cwmax, false, 0, 0, esz).total > 200 * 1024)
+      a.tglobal = plan_smem(n, cwmax, false, 0, 2, esz).total <= 200 * 1024 ? 2 : 1;
+    smem = plan_smem(n, cwmax, false, 0, a.tglobal, esz).total;
+    const long long per_sm = std::max<long long>(1, std::min<long long>(2, (227 * 1024) / (long long)smem));
+    if ((long long)batch * G <= 152LL * per_sm) break;
+    const int G2 = (int)std::max<long long>(2, 152LL * per_sm / batch);
+    if (G2 == G) break;
+    G = G2;
+  }
   cudaError_t err = f32 ? cudaFuncSetAttribute(gj_wide_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                         : cudaFuncSetAttribute(gj_wide_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -827,7 +942,7 @@ cudaError_t launch_gj_inverse(void *S, void *out, int n, int batch, int *meta, u
   a.cw = gj_slab(n, cs);
   a.status = status;
   a.level = level;
-  size_t smem = plan_smem(n, a.cw, false, 0, tglobal, f32 ? 8 : 16).total;
+  size_t smem = plan_smem(n, a.cw, false, 0, tglobal ? 1 : 0, f32 ? 8 : 16).total;
   return f32 ? launch_cluster(gj_kernel<float2>, a, batch, cs, smem, st)
              : launch_cluster(gj_kernel<double2>, a, batch, cs, smem, st);
 }

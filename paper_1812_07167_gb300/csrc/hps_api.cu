@@ -453,6 +453,16 @@ bool oz_shape(int M, int N, int K, int batch, int f32, bool oz) {
   return hps::oz_eligible(g);
 }
 
+int oz_launches_shape(int M, int N, int K, int batch) {
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.batch = batch;
+  return hps::oz_launches(g);
+}
+
 size_t oz_bytes_shape(int M, int N, int K, int batch) {
   GemmDesc g;
   memset(&g, 0, sizeof(g));
@@ -471,16 +481,19 @@ void merge_products(int n1, int n2, int n3, int nt, int (&mnk)[6][3]) {
 }
 
 // Kernel launches of one merge run: the copy, W^{-1}, and the products (an
-// emulated product is three launches; the two halves of R^tau share one
+// emulated product is three or four launches; the two halves of R^tau share one
 // launch when both run on the FP64 pipes).
 int merge_launches(int n1, int n2, int n3, int nt, int P, int f32, bool oz, const GJChoice &gj) {
   int mnk[6][3];
   merge_products(n1, n2, n3, nt, mnk);
   int n = 1 + gj_launches(n3, gj);
-  for (int q = 0; q < 4; q++) n += oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], P, f32, oz) ? 3 : 1;
+  for (int q = 0; q < 4; q++)
+    n += oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], P, f32, oz) ? oz_launches_shape(mnk[q][0], mnk[q][1], mnk[q][2], P)
+                                                               : 1;
   const bool a = oz_shape(mnk[4][0], mnk[4][1], mnk[4][2], P, f32, oz);
   const bool b = oz_shape(mnk[5][0], mnk[5][1], mnk[5][2], P, f32, oz);
-  n += (a ? 3 : 0) + (b ? 3 : 0) + ((!a || !b) ? 1 : 0);
+  n += (a ? oz_launches_shape(mnk[4][0], mnk[4][1], mnk[4][2], P) : 0) +
+       (b ? oz_launches_shape(mnk[5][0], mnk[5][1], mnk[5][2], P) : 0) + ((!a || !b) ? 1 : 0);
   return n;
 }
 
@@ -1180,7 +1193,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     for (int q = 0; q < nd; q++) {
       if (P0.oz && hps::oz_eligible(gd[q])) {
         CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, st));
-        launches += 3;
+        launches += hps::oz_launches(gd[q]);
       } else {
         rest[nr++] = gd[q];
       }

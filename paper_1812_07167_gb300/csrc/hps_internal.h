@@ -76,11 +76,13 @@ struct DevStatus {
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st);
 
-// Complex128 GEMM emulated on the bf16 tensor cores (Ozaki scheme, 7 slices
-// per operand; accuracy ~2^-56 max|A_i.| max|B_.j| per term).  Same
+// Complex128 GEMM emulated on the bf16 tensor cores (Ozaki scheme, 9 slices
+// of 6 bits per operand; accuracy ~2^-54 max|A_i.| max|B_.j| per term).  Same
 // semantics as launch_gemm for one descriptor with cf32 == 0; needs a
-// device workspace of oz_workspace_bytes(g).  Three launches.
+// device workspace of oz_workspace_bytes(g).  oz_launches(g) launches (3, or
+// 4 when the slice pairs are split over several CTAs a tile).
 bool oz_eligible(const GemmDesc &g);
+int oz_launches(const GemmDesc &g);
 size_t oz_workspace_bytes(const GemmDesc &g);
 cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st);
 cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st);
