@@ -46,7 +46,7 @@ class _Desc(ctypes.Structure):
     _fields_ = [
         ("x0", ctypes.c_double), ("x1", ctypes.c_double),
         ("y0", ctypes.c_double), ("y1", ctypes.c_double),
-        ("m", ctypes.c_int), ("p", ctypes.c_int),
+        ("mx", ctypes.c_int), ("my", ctypes.c_int), ("p", ctypes.c_int),
         ("kappa", ctypes.c_double),
         ("eta_re", ctypes.c_double), ("eta_im", ctypes.c_double),
         ("first_vertical", ctypes.c_int),
@@ -55,7 +55,8 @@ class _Desc(ctypes.Structure):
 
 @dataclass
 class Problem:
-    """Problem description: rectangle, m x m leaves, p Chebyshev nodes per side."""
+    """Problem description: rectangle, m x my leaves (my = m unless given),
+    p Chebyshev nodes per side."""
     m: int
     p: int
     kappa: float
@@ -64,6 +65,15 @@ class Problem:
     x1: float = 1.0
     y0: float = 0.0
     y1: float = 1.0
+    my: int = 0
+
+    @property
+    def mx(self) -> int:
+        return self.m
+
+    @property
+    def ny(self) -> int:
+        return self.my or self.m
 
     @property
     def e(self) -> int:
@@ -83,11 +93,11 @@ class Problem:
 
     @property
     def leaves(self) -> int:
-        return self.m * self.m
+        return self.m * self.ny
 
     @property
     def nbdry(self) -> int:
-        return 4 * self.m * (self.p - 2)
+        return 2 * (self.m + self.ny) * (self.p - 2)
 
 
 def _lib_handle():
@@ -113,7 +123,7 @@ def _lib_handle():
 
 def _desc(pr: Problem, first_vertical: bool = False) -> _Desc:
     eta = complex(pr.eta)
-    return _Desc(pr.x0, pr.x1, pr.y0, pr.y1, pr.m, pr.p, pr.kappa, eta.real, eta.imag,
+    return _Desc(pr.x0, pr.x1, pr.y0, pr.y1, pr.m, pr.ny, pr.p, pr.kappa, eta.real, eta.imag,
                  1 if first_vertical else 0)
 
 

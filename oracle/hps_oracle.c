@@ -46,12 +46,15 @@
  *     [I1, I2] in the children's own orders, exactly as in Sec. 2.2.
  *
  * Layouts shared with the caller (row-major, complex = (re, im) pairs):
- *   leaf index: Morton order, bit 2i of the index is bit i of the leaf's
- *   column, bit 2i+1 is bit i of its row.  Per leaf, nodes are ordered
- *   [south, east, north, west, interior]; each edge runs in increasing
- *   coordinate and excludes the corners; the interior is row by row, x fastest.
- *   Outer boundary data t: [south, east, north, west] sides, each running in
- *   increasing coordinate over m*(p-2) nodes.
+ *   leaf index: bit k of the index belongs to merge k counted from the
+ *   leaves (merges alternate west/east and south/north, starting west/east;
+ *   see merge_dirs): for a square grid this is the Morton order with bit 2i
+ *   of the index bit i of the leaf's column and bit 2i+1 bit i of its row.
+ *   Per leaf, nodes are ordered [south, east, north, west, interior]; each
+ *   edge runs in increasing coordinate and excludes the corners; the
+ *   interior is row by row, x fastest.  Outer boundary data t: [south, east,
+ *   north, west] sides, each running in increasing coordinate over mx*(p-2)
+ *   (south, north) or my*(p-2) (east, west) nodes.
  */
 #include <complex.h>
 #include <math.h>
@@ -66,7 +69,7 @@ typedef double complex cplx;
 
 typedef struct {
   double x0, x1, y0, y1; /* the rectangle Omega */
-  int m;                 /* leaves per side, a power of two */
+  int mx, my;            /* leaves along x and along y, powers of two */
   int p;                 /* Chebyshev nodes per leaf side (n_c) */
   double kappa;          /* wave number */
   double eta_re, eta_im; /* impedance parameter eta, Re(eta) != 0 */
@@ -224,15 +227,47 @@ static void local_to_grid(int p, int k, int *ix, int *iy) {
   *iy = 1 + k / e;
 }
 
-/* Morton decode of a leaf index: returns the leaf's column and row. */
-static void morton_decode(int idx, int bits, int *col, int *row) {
-  int c = 0, r = 0;
-  for (int i = 0; i < bits; i++) {
-    c |= ((idx >> (2 * i)) & 1) << i;
-    r |= ((idx >> (2 * i + 1)) & 1) << i;
+/* Directions of the merges of an mx x my leaf grid (mx = 2^A, my = 2^B),
+ * counted from the leaves: 0 joins west/east neighbours (halves the boxes'
+ * count along x), 1 joins south/north neighbours.  The two alternate,
+ * starting with west/east (south/north when first_vertical); once one axis
+ * has no halvings left, the other takes the remaining merges.  Returns the
+ * number of merges, A + B. */
+static int merge_dirs(int A, int B, int first_vertical, int *dir) {
+  int a = A, b = B, k = 0, want = first_vertical ? 1 : 0;
+  while (a + b > 0) {
+    int d = want;
+    if (d == 0 && a == 0) d = 1;
+    if (d == 1 && b == 0) d = 0;
+    dir[k++] = d;
+    if (d == 0) a--; else b--;
+    want = 1 - d;
+  }
+  return k;
+}
+
+/* A leaf index whose bit k belongs to merge k: the bits of west/east merges
+ * form the leaf's column, the others its row (lowest merge, lowest bit).
+ * For a square grid starting west/east this is the Morton order with the x
+ * bit lowest. */
+static void leaf_decode(int idx, const int *dir, int L, int *col, int *row) {
+  int c = 0, r = 0, bc = 0, br = 0;
+  for (int k = 0; k < L; k++) {
+    int bit = (idx >> k) & 1;
+    if (dir[k] == 0) c |= bit << bc++;
+    else r |= bit << br++;
   }
   *col = c;
   *row = r;
+}
+
+static int leaf_encode(int col, int row, const int *dir, int L) {
+  int idx = 0, bc = 0, br = 0;
+  for (int k = 0; k < L; k++) {
+    int bit = dir[k] == 0 ? (col >> bc++) & 1 : (row >> br++) & 1;
+    idx |= bit << k;
+  }
+  return idx;
 }
 
 static int log2i(int m) {
@@ -242,7 +277,8 @@ static int log2i(int m) {
 }
 
 static int check_desc(const ora_desc *d) {
-  if (d->m < 1 || (d->m & (d->m - 1))) return 1;
+  if (d->mx < 1 || (d->mx & (d->mx - 1))) return 1;
+  if (d->my < 1 || (d->my & (d->my - 1))) return 1;
   if (d->p < 4) return 1;
   if (!(d->x1 > d->x0) || !(d->y1 > d->y0)) return 1;
   if (d->eta_re == 0.0) return 1;
@@ -250,17 +286,19 @@ static int check_desc(const ora_desc *d) {
 }
 
 /* Coordinates of every leaf node ([leaves][p*p-4][2], public leaf order) and
- * of the outer boundary nodes ([4 m (p-2)][2], sides S, E, N, W). */
+ * of the outer boundary nodes ([2 (mx + my) (p-2)][2], sides S, E, N, W, each
+ * in increasing coordinate). */
 int ora_nodes(const ora_desc *d, double *leaf_xy, double *bdry_xy) {
   if (check_desc(d)) return 1;
-  int p = d->p, m = d->m, e = p - 2, n = p * p - 4, bits = log2i(m);
-  double hx = (d->x1 - d->x0) / m, hy = (d->y1 - d->y0) / m;
+  int p = d->p, e = p - 2, n = p * p - 4;
+  int dir[64], L = merge_dirs(log2i(d->mx), log2i(d->my), 0, dir);
+  double hx = (d->x1 - d->x0) / d->mx, hy = (d->y1 - d->y0) / d->my;
   double *xs = xmalloc(sizeof(double) * p), *ys = xmalloc(sizeof(double) * p);
   double *D = xmalloc(sizeof(double) * p * p);
   if (leaf_xy) {
-    for (int l = 0; l < m * m; l++) {
+    for (int l = 0; l < d->mx * d->my; l++) {
       int c, r;
-      morton_decode(l, bits, &c, &r);
+      leaf_decode(l, dir, L, &c, &r);
       ora_cheb(p, d->x0 + c * hx, d->x0 + (c + 1) * hx, xs, D);
       ora_cheb(p, d->y0 + r * hy, d->y0 + (r + 1) * hy, ys, D);
       for (int k = 0; k < n; k++) {
@@ -273,9 +311,9 @@ int ora_nodes(const ora_desc *d, double *leaf_xy, double *bdry_xy) {
   }
   if (bdry_xy) {
     int q = 0;
-    for (int side = 0; side < 4; side++)
-      for (int c = 0; c < m; c++) {
-        int horizontal = (side == 0 || side == 2);
+    for (int side = 0; side < 4; side++) {
+      int horizontal = (side == 0 || side == 2);
+      for (int c = 0; c < (horizontal ? d->mx : d->my); c++) {
         if (horizontal)
           ora_cheb(p, d->x0 + c * hx, d->x0 + (c + 1) * hx, xs, D);
         else
@@ -290,6 +328,7 @@ int ora_nodes(const ora_desc *d, double *leaf_xy, double *bdry_xy) {
           bdry_xy[2 * q + 1] = y;
         }
       }
+    }
   }
   free(xs);
   free(ys);
@@ -426,7 +465,7 @@ int ora_leaf(const ora_desc *d, const double *c, cplx *Psi, cplx *Y, cplx *R, cp
              cplx *F, cplx *G) {
   if (check_desc(d)) return -1;
   leaf_geom g;
-  leaf_geom_init(&g, d->p, (d->x1 - d->x0) / d->m, (d->y1 - d->y0) / d->m);
+  leaf_geom_init(&g, d->p, (d->x1 - d->x0) / d->mx, (d->y1 - d->y0) / d->my);
   int bad = leaf_ops(&g, d->kappa, d->eta_re + I * d->eta_im, c, Psi, Y, R, Gam, B, F, G);
   leaf_geom_free(&g);
   return bad;
@@ -457,24 +496,16 @@ typedef struct {
   ora_box *box;   /* box[tau], tau = 1..nboxes */
   int e, n, nb, ni;
   int status;
-  double *cond_est; /* unused placeholder for future diagnostics */
+  int dir[64];      /* merge directions of this tree, from the leaves */
+  int pub_dir[64];  /* those of the public leaf order */
 } ora_tree;
 
 static int tree_leaf_public(const ora_tree *T, int slot) {
-  /* slot: position of the leaf in the tree's Morton order */
-  int bits = T->L / 2, c, r;
-  morton_decode(slot, bits, &c, &r);
-  if (T->d.first_vertical) {
-    int tmp = c;
-    c = r;
-    r = tmp;
-  }
-  int idx = 0;
-  for (int i = 0; i < bits; i++) {
-    idx |= ((c >> i) & 1) << (2 * i);
-    idx |= ((r >> i) & 1) << (2 * i + 1);
-  }
-  return idx;
+  /* slot: position of the leaf in the tree's order (its merge directions);
+   * the public order follows the directions that start west/east */
+  int c, r;
+  leaf_decode(slot, T->dir, T->L, &c, &r);
+  return leaf_encode(c, r, T->pub_dir, T->L);
 }
 
 static int same_point(const double *a, const double *b, double tol) {
@@ -638,9 +669,9 @@ static void leaf_box(ora_tree *T, const leaf_geom *g, int tau, const double *c) 
                      b->Y, b->R, b->Gam, NULL, NULL, NULL);
   if (bad && !T->status) T->status = 1;
   /* boundary coordinates of this leaf, in its local order */
-  int p = T->d.p, bits = T->L / 2, col, row;
-  morton_decode(pub, bits, &col, &row);
-  double hx = (T->d.x1 - T->d.x0) / T->d.m, hy = (T->d.y1 - T->d.y0) / T->d.m;
+  int p = T->d.p, col, row;
+  leaf_decode(pub, T->pub_dir, T->L, &col, &row);
+  double hx = (T->d.x1 - T->d.x0) / T->d.mx, hy = (T->d.y1 - T->d.y0) / T->d.my;
   double *xs = xmalloc(sizeof(double) * p), *ys = xmalloc(sizeof(double) * p);
   double *D = xmalloc(sizeof(double) * p * p);
   ora_cheb(p, T->d.x0 + col * hx, T->d.x0 + (col + 1) * hx, xs, D);
@@ -663,7 +694,8 @@ void *ora_build(const ora_desc *d, const double *c, int nthreads) {
   if (check_desc(d)) return NULL;
   ora_tree *T = xmalloc(sizeof(ora_tree));
   T->d = *d;
-  T->L = 2 * log2i(d->m);
+  T->L = merge_dirs(log2i(d->mx), log2i(d->my), d->first_vertical, T->dir);
+  merge_dirs(log2i(d->mx), log2i(d->my), 0, T->pub_dir);
   T->nboxes = (1 << (T->L + 1)) - 1;
   T->box = xmalloc(sizeof(ora_box) * (size_t)(T->nboxes + 1));
   T->e = d->p - 2;
@@ -671,7 +703,7 @@ void *ora_build(const ora_desc *d, const double *c, int nthreads) {
   T->nb = 4 * T->e;
   T->ni = T->e * T->e;
   leaf_geom g;
-  leaf_geom_init(&g, d->p, (d->x1 - d->x0) / d->m, (d->y1 - d->y0) / d->m);
+  leaf_geom_init(&g, d->p, (d->x1 - d->x0) / d->mx, (d->y1 - d->y0) / d->my);
   if (nthreads < 1) nthreads = 1;
   for (int lev = T->L; lev >= 0; lev--) {
     int lo = 1 << lev, hi = (1 << (lev + 1)) - 1;
@@ -692,7 +724,7 @@ int ora_status(void *h) { return ((ora_tree *)h)->status; }
 
 /* root ItI operator reordered to the public [S, E, N, W] boundary order */
 static int *root_order(ora_tree *T) {
-  int nbr = 4 * T->d.m * T->e;
+  int nbr = 2 * (T->d.mx + T->d.my) * T->e;
   double *bxy = xmalloc(sizeof(double) * 2 * nbr);
   ora_nodes(&T->d, NULL, bxy);
   double tol = 1e-10 * fmax(T->d.x1 - T->d.x0, T->d.y1 - T->d.y0);
@@ -737,11 +769,11 @@ int ora_tree_leaf(void *h, int pub, cplx *Psi, cplx *Y, cplx *Gam) {
 }
 
 /* Algorithm 2 for nrhs right-hand sides.
- * s: [nrhs][leaves][(p-2)^2], t: [nrhs][4 m (p-2)], u: [nrhs][leaves][p^2-4]. */
+ * s: [nrhs][leaves][(p-2)^2], t: [nrhs][2 (mx + my) (p-2)], u: [nrhs][leaves][p^2-4]. */
 int ora_solve(void *h, const cplx *s, const cplx *t, cplx *u, int nrhs, int nthreads) {
   ora_tree *T = h;
   int L = T->L, nl = 1 << L, n = T->n, nb = T->nb, ni = T->ni;
-  int nbr = 4 * T->d.m * T->e;
+  int nbr = 2 * (T->d.mx + T->d.my) * T->e;
   int *perm = root_order(T);
   if (nthreads < 1) nthreads = 1;
   cplx **hv = xmalloc(sizeof(cplx *) * (size_t)(T->nboxes + 1));
@@ -890,14 +922,14 @@ void ora_free(void *h) {
 /* ------------------------------------------------------------------ */
 
 /* u: [leaves][p^2-4] for one right-hand side (s: [leaves][(p-2)^2],
- * t: [4 m (p-2)]).  Returns 0, or nonzero when the system is singular. */
+ * t: [2 (mx + my) (p-2)]).  Returns 0, or nonzero when the system is singular. */
 int ora_brute(const ora_desc *d, const double *c, const cplx *s, const cplx *t, cplx *u) {
   if (check_desc(d)) return -1;
-  int m = d->m, p = d->p, e = p - 2, n = p * p - 4, nb = 4 * e, ni = e * e;
-  int nl = m * m, N = nl * n, nbr = 4 * m * e;
+  int p = d->p, e = p - 2, n = p * p - 4, nb = 4 * e, ni = e * e;
+  int nl = d->mx * d->my, N = nl * n, nbr = 2 * (d->mx + d->my) * e;
   double tol = 1e-10 * fmax(d->x1 - d->x0, d->y1 - d->y0);
   leaf_geom g;
-  leaf_geom_init(&g, p, (d->x1 - d->x0) / m, (d->y1 - d->y0) / m);
+  leaf_geom_init(&g, p, (d->x1 - d->x0) / d->mx, (d->y1 - d->y0) / d->my);
   cplx eta = d->eta_re + I * d->eta_im;
   double *xy = xmalloc(sizeof(double) * 2 * (size_t)nl * n);
   double *bxy = xmalloc(sizeof(double) * 2 * nbr);

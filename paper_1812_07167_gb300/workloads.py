@@ -52,9 +52,12 @@ def uniform(seed: int, count: int, offset: int = 0) -> np.ndarray:
 _NORMALS = np.array([[0.0, -1.0], [1.0, 0.0], [0.0, 1.0], [-1.0, 0.0]])
 
 
-def boundary_sides(m: int, p: int) -> np.ndarray:
-    """Side index (0 S, 1 E, 2 N, 3 W) of each public outer-boundary node."""
-    return np.repeat(np.arange(4), m * (p - 2))
+def boundary_sides(m: int, p: int, my: Optional[int] = None) -> np.ndarray:
+    """Side index (0 S, 1 E, 2 N, 3 W) of each public outer-boundary node of
+    an m x my leaf grid (my = m unless given)."""
+    my = m if not my else my
+    e = p - 2
+    return np.concatenate([np.full(m * e, 0), np.full(my * e, 1), np.full(m * e, 2), np.full(my * e, 3)])
 
 
 @dataclass
@@ -72,6 +75,7 @@ class Workload:
     u_exact: Optional[Callable[[np.ndarray, np.ndarray], np.ndarray]] = None
     domain: tuple = (0.0, 1.0, 0.0, 1.0)
     notes: dict = field(default_factory=dict)
+    my: int = 0  # leaves along y (0: m)
 
     def sample(self, leaf_xy: np.ndarray, bdry_xy: np.ndarray):
         """(c_int [leaves, e^2], s [leaves, e^2], t [4 m e]) at the given nodes.
@@ -84,7 +88,7 @@ class Workload:
         yi = leaf_xy[:, nb:, 1]
         c = np.asarray(self.c(xi, yi), dtype=np.float64)
         s = np.asarray(self.s(xi, yi), dtype=np.complex128)
-        side = boundary_sides(self.m, self.p)
+        side = boundary_sides(self.m, self.p, self.my)
         t = np.asarray(self.t(bdry_xy[:, 0], bdry_xy[:, 1], side), dtype=np.complex128)
         return c, s, t
 
@@ -199,7 +203,8 @@ def random_medium_sources(m: int, p: int = 16, kappa: float = 300.0, eta: Option
 
 
 def polynomial_solution(m: int, p: int, kappa: float, eta: complex, seed: int = 7,
-                        c: Optional[Callable] = None, domain=(0.0, 1.0, 0.0, 1.0)) -> Workload:
+                        c: Optional[Callable] = None, domain=(0.0, 1.0, 0.0, 1.0),
+                        my: Optional[int] = None) -> Workload:
     """Manufactured solution that is a polynomial of degree p-1 in x and in y.
 
     u(x, y) = sum_{a,b <= p-1} C_ab X^a Y^b with X, Y the coordinates scaled to
@@ -246,16 +251,20 @@ def polynomial_solution(m: int, p: int, kappa: float, eta: complex, seed: int = 
         nrm = _NORMALS[side]
         return nrm[..., 0] * _ev(x, y, 1, 0) + nrm[..., 1] * _ev(x, y, 0, 1) + 1j * eta * _ev(x, y)
 
-    return Workload("polynomial_solution", m, p, kappa, eta, cfun, s, t, u_exact=u, domain=domain)
+    return Workload("polynomial_solution", m, p, kappa, eta, cfun, s, t, u_exact=u, domain=domain,
+                    my=my or m)
 
 
-def random_data(m: int, p: int, kappa: float, eta: complex, seed: int, nrhs: int = 1):
+def random_data(m: int, p: int, kappa: float, eta: complex, seed: int, nrhs: int = 1,
+                my: Optional[int] = None):
     """Unstructured seeded data: c in [0.5, 1.5] at the (p-2)^2 interior nodes of
-    each leaf, complex s (same nodes) and t (outer boundary), values in the unit
-    box.  Returned as (c [leaves, e^2], s [nrhs, leaves, e^2], t [nrhs, 4 m e])."""
+    each leaf of an m x my grid (my = m unless given), complex s (same nodes)
+    and t (outer boundary), values in the unit box.  Returned as
+    (c [leaves, e^2], s [nrhs, leaves, e^2], t [nrhs, 2 (m + my) e])."""
     e = p - 2
-    L = m * m
-    nb = 4 * m * e
+    my = m if not my else my
+    L = m * my
+    nb = 2 * (m + my) * e
     r = uniform(seed, L * e * e + 2 * nrhs * (L * e * e + nb), offset=1 << 28)
     k = 0
     c = 0.5 + r[k:k + L * e * e].reshape(L, e * e)

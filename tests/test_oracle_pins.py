@@ -155,6 +155,58 @@ def test_merge_order_does_not_change_the_solution():
     assert _rel(Ra, Rb) < 1e-11
 
 
+# ------------------------------------------------ rectangular leaf grids
+
+
+@pytest.mark.parametrize("mx,my,p", [(2, 1, 8), (1, 2, 8), (4, 2, 6), (2, 8, 6), (1, 4, 8)])
+def test_rectangular_grid_polynomial_reproduced(mx, my, p):
+    """mx != my leaf grids (merges alternate, then the longer axis takes the
+    remaining ones): the polynomial solution is still reproduced at every
+    node, on a domain whose aspect ratio differs from the grid's."""
+    wl = W.polynomial_solution(mx, p, 9.0, 4.0 - 1.0j, domain=(0.0, 1.5, -0.5, 0.5), my=my)
+    pr = O.Problem(mx, p, wl.kappa, wl.eta, 0.0, 1.5, -0.5, 0.5, my=my)
+    lxy, bxy = O.nodes(pr)
+    assert lxy.shape[0] == mx * my and bxy.shape[0] == 2 * (mx + my) * (p - 2)
+    c, s, t = wl.sample(lxy, bxy)
+    with O.Tree(pr, c) as T:
+        assert T.status == 0
+        u = T.solve(s[None], t[None])[0]
+    assert _rel(u, wl.u_exact(lxy[..., 0], lxy[..., 1])) < 1e-10
+
+
+@pytest.mark.parametrize("mx,my", [(2, 1), (1, 2), (4, 2), (2, 4)])
+def test_rectangular_grid_equals_dense_global_solve(mx, my):
+    pr = O.Problem(mx, 8, 12.0, 12.0, my=my)
+    c, s, t = W.random_data(mx, 8, 12.0, 12.0, seed=40 + mx * 10 + my, my=my)
+    ub = O.brute(pr, c, s[0], t[0])
+    with O.Tree(pr, c) as T:
+        u = T.solve(s, t)[0]
+    assert _rel(u, ub) < 1e-10
+
+
+def test_rectangular_grid_nodes_cover_the_domain():
+    pr = O.Problem(4, 6, 5.0, 5.0, 0.0, 2.0, 0.0, 0.5, my=1)
+    lxy, bxy = O.nodes(pr)
+    # every leaf inside the domain, leaves side by side along x
+    assert lxy[..., 0].min() == 0.0 and lxy[..., 0].max() == 2.0
+    assert lxy[..., 1].min() == 0.0 and lxy[..., 1].max() == 0.5
+    cols = sorted({round(float(lxy[l, :, 0].min()), 12) for l in range(4)})
+    assert cols == [0.0, 0.5, 1.0, 1.5]
+    # outer boundary: S then E then N then W, 4 + 1 + 4 + 1 leaf edges of 4 nodes
+    assert np.all(bxy[:16, 1] == 0.0) and np.all(bxy[16:20, 0] == 2.0)
+    assert np.all(bxy[20:36, 1] == 0.5) and np.all(bxy[36:, 0] == 0.0)
+
+
+def test_rectangular_merge_order_does_not_change_the_solution():
+    pr = O.Problem(4, 8, 10.0, 10.0, my=2)
+    c, s, t = W.random_data(4, 8, 10.0, 10.0, seed=6, nrhs=2, my=2)
+    with O.Tree(pr, c) as A, O.Tree(pr, c, first_vertical=True) as B:
+        ua, ub = A.solve(s, t), B.solve(s, t)
+        Ra, Rb = A.root_R(), B.root_R()
+    assert _rel(ua, ub) < 1e-11
+    assert _rel(Ra, Rb) < 1e-11
+
+
 def test_threads_change_no_arithmetic():
     pr = O.Problem(4, 8, 11.0, 11.0)
     c, s, t = W.random_data(4, 8, 11.0, 11.0, seed=9, nrhs=3)
