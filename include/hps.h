@@ -18,9 +18,14 @@
  * double complex / CUDA double2 layout).  Arrays are dense and C-ordered as
  * written ([a][b] means index b runs fastest).
  *
- * Leaves: the domain is cut into mx x my equal rectangles (mx == my, a power
- * of two).  Leaves are numbered in Morton order: bit 2i of the leaf index is
- * bit i of the leaf's column (x), bit 2i+1 is bit i of its row (y).
+ * Leaves: the domain is cut into mx x my equal rectangles (powers of two).
+ * The merges of the tree alternate, from the leaves up, between joining
+ * west/east neighbours and joining south/north neighbours, starting west/east;
+ * once one axis has no halvings left the other takes the remaining merges.
+ * Bit k of a leaf index belongs to merge k: the bits of west/east merges form
+ * the leaf's column (x), the others its row (y).  For mx == my this is the
+ * Morton order: bit 2i of the leaf index is bit i of the column, bit 2i+1
+ * bit i of the row.
  *
  * Nodes: each leaf carries the p x p Chebyshev tensor grid with its four
  * corners dropped (p^2 - 4 nodes, Sec. 2.1), ordered
@@ -29,8 +34,9 @@
  * the (p-2)^2 interior nodes run row by row, x fastest.  Nodes on an edge
  * shared by two leaves appear once per leaf.
  *
- * Outer boundary: 4 m (p-2) nodes ordered [south, east, north, west], each side
- * in increasing coordinate (the concatenation of the leaves' edges).
+ * Outer boundary: 2 (mx + my) (p-2) nodes ordered [south, east, north, west]
+ * (mx, my, mx, my leaf edges), each side in increasing coordinate (the
+ * concatenation of the leaves' edges).
  *
  * Memory: every array argument may be host or device memory; the library
  * asks the CUDA runtime which.  Device arrays are used in place; host arrays
@@ -69,7 +75,8 @@ enum { HPS_FP64 = 0, HPS_MIXED = 1 };
 
 typedef struct {
   double x0, x1, y0, y1; /* the rectangle Omega, x1 > x0, y1 > y0 */
-  int mx, my;            /* leaves per side: equal powers of two, 1 .. 1024 */
+  int mx, my;            /* leaves along x and along y: powers of two, 1 .. 1024,
+                            mx my <= 2^20 */
   int p;                 /* Chebyshev nodes per leaf side (the paper's n_c), 4 .. 32 */
   int q;                 /* points per leaf edge for boundary data: 0 or p-2 (the
                             corner-free Chebyshev edge nodes; other values are
@@ -98,9 +105,9 @@ typedef struct hps_handle hps_handle;
 
 typedef struct {
   int leaves;               /* mx * my */
-  int levels;               /* merge levels (2 log2 m) */
+  int levels;               /* merge levels (log2 mx + log2 my) */
   int n_leaf;               /* p^2 - 4 nodes per leaf */
-  int n_bdry;               /* 4 m (p-2) outer boundary nodes */
+  int n_bdry;               /* 2 (mx + my) (p-2) outer boundary nodes */
   long long dof;            /* leaves * (p^2 - 4) */
   long long operator_bytes; /* device bytes of stored operators (Sec. 2.4) */
   long long build_flops;    /* real floating-point operations of one build */
@@ -115,7 +122,7 @@ typedef struct {
 
 /* Node coordinates (host helper, no device work; Sec. 2.1 grid).
  *   leaf_xy: [leaves][p^2-4][2] (x, y) of every leaf node, or NULL
- *   bdry_xy: [4 m (p-2)][2] outer boundary nodes, or NULL
+ *   bdry_xy: [2 (mx + my) (p-2)][2] outer boundary nodes, or NULL
  * Both are host memory.  Returns HPS_EINVAL for an invalid descriptor. */
 int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy);
 
@@ -163,7 +170,7 @@ int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, vo
  * operators with the interface residuals injected into h3 at the merge whose
  * interface holds them.
  *   s: [nrhs][leaves][(p-2)^2] complex body load at the interior nodes
- *   t: [nrhs][4 m (p-2)] complex impedance data du/dnu + i eta u on the
+ *   t: [nrhs][2 (mx + my) (p-2)] complex impedance data du/dnu + i eta u on the
  *      outer boundary
  *   u: [nrhs][leaves][p^2-4] complex solution at every leaf node (written)
  * nrhs == 0 does nothing and returns HPS_OK.  Returns HPS_EINVAL (NULL
@@ -227,7 +234,7 @@ int hps_solve_noalloc(hps_handle *h, const double *s, const double *t, double *u
 
 /* The root ItI operator R (Definition of the ItI map; R f = g on the outer
  * boundary) in the outer-boundary order above.
- *   R: [4 m (p-2)][4 m (p-2)] complex, row-major (R[i][j] maps incoming data
+ *   R: [nb][nb] complex with nb = 2 (mx + my) (p-2), row-major (R[i][j] maps incoming data
  *      at node j to outgoing data at node i)
  * The root R is the last merge's product; the build keeps it.  Returns
  * HPS_EINVAL or HPS_ECUDA. */

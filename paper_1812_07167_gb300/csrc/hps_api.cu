@@ -61,7 +61,7 @@ struct Level {
 };
 
 struct Plan {
-  int m, p, e, n, nb, ni, L, leaves, nbdry;
+  int m, my, p, e, n, nb, ni, L, leaves, nbdry;  // m: leaves along x, my: along y
   bool mixed;                   // HPS_MIXED
   int leaf_f32;                 // leaf operators in complex64
   int refine_steps;             // refinement steps of a mixed solve
@@ -118,7 +118,9 @@ int check_desc(const hps_desc *d) {
   if (!std::isfinite(d->x0) || !std::isfinite(d->x1) || !std::isfinite(d->y0) ||
       !std::isfinite(d->y1))
     return HPS_EINVAL;
-  if (d->mx != d->my || d->mx < 1 || d->mx > 1024 || (d->mx & (d->mx - 1))) return HPS_EINVAL;
+  if (d->mx < 1 || d->mx > 1024 || (d->mx & (d->mx - 1))) return HPS_EINVAL;
+  if (d->my < 1 || d->my > 1024 || (d->my & (d->my - 1))) return HPS_EINVAL;
+  if ((long long)d->mx * d->my > (1 << 20)) return HPS_EINVAL;
   if (d->p < 4 || d->p > 32) return HPS_EINVAL;
   if (d->q != 0 && d->q != d->p - 2) return HPS_EINVAL;
   if (!(d->kappa > 0.0) || !std::isfinite(d->kappa)) return HPS_EINVAL;
@@ -177,25 +179,49 @@ int log2i(int m) {
   return k;
 }
 
-void morton_decode(int idx, int bits, int &col, int &row) {
+// Directions of the merges of an mx x my grid from the leaves up (0: west /
+// east neighbours, halving the boxes along x; 1: south / north): they
+// alternate, starting west/east, and once one axis has no halvings left the
+// other takes the remaining merges.
+std::vector<int> merge_dirs(int mx, int my) {
+  int a = log2i(mx), b = log2i(my), want = 0;
+  std::vector<int> dir;
+  while (a + b > 0) {
+    int d = want;
+    if (d == 0 && a == 0) d = 1;
+    if (d == 1 && b == 0) d = 0;
+    dir.push_back(d);
+    if (d == 0) a--; else b--;
+    want = 1 - d;
+  }
+  return dir;
+}
+
+// Leaf column and row of a public leaf index: bit k of the index belongs to
+// merge k, west/east merges giving the column bits and the others the row
+// bits (for a square grid: Morton order, x bit lowest).
+void leaf_decode(int idx, const std::vector<int> &dir, int &col, int &row) {
   col = row = 0;
-  for (int i = 0; i < bits; i++) {
-    col |= ((idx >> (2 * i)) & 1) << i;
-    row |= ((idx >> (2 * i + 1)) & 1) << i;
+  int bc = 0, br = 0;
+  for (size_t k = 0; k < dir.size(); k++) {
+    const int bit = (idx >> k) & 1;
+    if (dir[k] == 0) col |= bit << bc++;
+    else row |= bit << br++;
   }
 }
 
-// Index maps of every merge level (Sec. 2.2, Fig. 3).
 void make_plan(const hps_desc &d, Plan &pl) {
   pl.m = d.mx;
+  pl.my = d.my;
   pl.p = d.p;
   pl.e = d.p - 2;
   pl.n = d.p * d.p - 4;
   pl.nb = 4 * pl.e;
   pl.ni = pl.e * pl.e;
-  pl.L = 2 * log2i(pl.m);
-  pl.leaves = pl.m * pl.m;
-  pl.nbdry = 4 * pl.m * pl.e;
+  const std::vector<int> dirs = merge_dirs(d.mx, d.my);
+  pl.L = (int)dirs.size();
+  pl.leaves = d.mx * d.my;
+  pl.nbdry = 2 * (d.mx + d.my) * pl.e;
   pl.mixed = (d.precision == HPS_MIXED);
   pl.leaf_f32 = pl.mixed ? 1 : 0;
   pl.refine_steps = d.refine_steps == 0 ? 2 : (d.refine_steps < 0 ? 0 : d.refine_steps);
@@ -217,7 +243,7 @@ void make_plan(const hps_desc &d, Plan &pl) {
     Level L;
     L.lev = pl.L - 1 - j;
     L.P = 1 << L.lev;
-    L.horizontal = (j % 2 == 0);
+    L.horizontal = (dirs[j] == 0);
     L.f32 = (pl.mixed && j < pl.L - top) ? 1 : 0;
     L.nc = (int)cur.size();
     L.leaves_per_parent = 2 * child_leaves;
@@ -286,7 +312,9 @@ void make_plan(const hps_desc &d, Plan &pl) {
   pl.root_src.resize(cur.size());
   pl.outer.resize(cur.size());
   for (size_t pos = 0; pos < cur.size(); pos++) {
-    const int q = cur[pos].side * pl.m * e + cur[pos].off;
+    // public sides S, E, N, W hold mx, my, mx, my leaf edges
+    const int side_off[4] = {0, d.mx * e, (d.mx + d.my) * e, (2 * d.mx + d.my) * e};
+    const int q = side_off[cur[pos].side] + cur[pos].off;
     pl.root_src[pos] = q;
     pl.outer[q] = at[pos].first * pl.nb + at[pos].second;
   }
@@ -767,13 +795,14 @@ const char *hps_strerror(int code) {
 int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy) {
   int st = check_desc(desc);
   if (st) return st;
-  const int m = desc->mx, p = desc->p, e = p - 2, n = p * p - 4, bits = log2i(m);
-  const double hx = (desc->x1 - desc->x0) / m, hy = (desc->y1 - desc->y0) / m;
+  const int mx = desc->mx, my = desc->my, p = desc->p, e = p - 2, n = p * p - 4;
+  const std::vector<int> dirs = merge_dirs(mx, my);
+  const double hx = (desc->x1 - desc->x0) / mx, hy = (desc->y1 - desc->y0) / my;
   std::vector<double> xs, ys, D;
   if (leaf_xy) {
-    for (int l = 0; l < m * m; l++) {
+    for (int l = 0; l < mx * my; l++) {
       int col, row;
-      morton_decode(l, bits, col, row);
+      leaf_decode(l, dirs, col, row);
       cheb(p, desc->x0 + col * hx, desc->x0 + (col + 1) * hx, xs, D);
       cheb(p, desc->y0 + row * hy, desc->y0 + (row + 1) * hy, ys, D);
       for (int k = 0; k < n; k++) {
@@ -786,9 +815,9 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy) {
   }
   if (bdry_xy) {
     size_t q = 0;
-    for (int side = 0; side < 4; side++)
-      for (int c = 0; c < m; c++) {
-        bool horiz = (side == 0 || side == 2);
+    for (int side = 0; side < 4; side++) {
+      const bool horiz = (side == 0 || side == 2);
+      for (int c = 0; c < (horiz ? mx : my); c++) {
         if (horiz)
           cheb(p, desc->x0 + c * hx, desc->x0 + (c + 1) * hx, xs, D);
         else
@@ -800,6 +829,7 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy) {
           bdry_xy[2 * q + 1] = y;
         }
       }
+    }
   }
   return HPS_OK;
 }
@@ -890,6 +920,16 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   std::vector<long long> leaf0(K + 1, 0);
   for (int k = 0; k < K; k++) leaf0[k + 1] = leaf0[k] + hs[k]->plan.leaves;
   const long long NL = leaf0[K];
+
+  // every problem's merge levels must have the tallest tree's shapes (true
+  // for square grids of any size; rectangular ones share the first levels
+  // with a square grid up to where their axes stop alternating)
+  for (int k = 1; k < K; k++)
+    for (int j = 0; j < hs[k]->plan.L; j++) {
+      const Level &A = P0.lv[j], &B = hs[k]->plan.lv[j];
+      if (A.horizontal != B.horizontal || A.nc != B.nc || A.n1 != B.n1 || A.n2 != B.n2 || A.n3 != B.n3)
+        return HPS_EINVAL;
+    }
 
   // ---- runs of every merge level, and each problem's first parent there ----
   std::vector<std::vector<BuildRun>> runs(Lmax);
@@ -1029,8 +1069,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   std::vector<unsigned char> tab(tab_bytes);
   for (int k = 0; k < K; k++) {
     const hps_desc &dk = hs[k]->desc;
-    const int mk = hs[k]->plan.m;
-    const double hx = (dk.x1 - dk.x0) / mk, hy = (dk.y1 - dk.y0) / mk;
+    const double hx = (dk.x1 - dk.x0) / hs[k]->plan.m, hy = (dk.y1 - dk.y0) / hs[k]->plan.my;
     std::vector<double> x, D1x, D1y;
     cheb(p, 0.0, hx, x, D1x);
     cheb(p, 0.0, hy, x, D1y);

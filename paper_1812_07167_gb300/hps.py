@@ -115,10 +115,15 @@ class Problem:
     fp64_levels: int = 0
     refine_steps: int = 0
     fp64_native: int = 0
+    my: int = 0  # leaves along y (0: the same as m, the leaves along x)
+
+    @property
+    def ny(self) -> int:
+        return self.my or self.m
 
     def desc(self) -> hps_desc:
         eta = complex(self.eta)
-        return hps_desc(self.x0, self.x1, self.y0, self.y1, self.m, self.m, self.p, self.p - 2,
+        return hps_desc(self.x0, self.x1, self.y0, self.y1, self.m, self.ny, self.p, self.p - 2,
                         float(self.kappa), eta.real, eta.imag, int(self.precision),
                         int(self.fp64_levels), int(self.refine_steps), int(self.fp64_native))
 
@@ -136,11 +141,11 @@ class Problem:
 
     @property
     def leaves(self) -> int:
-        return self.m * self.m
+        return self.m * self.ny
 
     @property
     def nbdry(self) -> int:
-        return 4 * self.m * (self.p - 2)
+        return 2 * (self.m + self.ny) * (self.p - 2)
 
 
 def _ptr(a) -> int:
@@ -172,7 +177,7 @@ def _check(code: int, what: str):
 
 
 def hps_nodes(pr: Problem):
-    """(leaf_xy [leaves, p^2-4, 2], bdry_xy [4 m (p-2), 2]) as numpy arrays."""
+    """(leaf_xy [leaves, p^2-4, 2], bdry_xy [2 (mx + my) (p-2), 2]) as numpy arrays."""
     lxy = np.zeros((pr.leaves, pr.n, 2))
     bxy = np.zeros((pr.nbdry, 2))
     d = pr.desc()

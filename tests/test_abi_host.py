@@ -42,11 +42,11 @@ def test_strerror_codes():
     assert hps.hps_strerror(99) == "unknown error"
 
 
-@pytest.mark.parametrize("m,p", [(1, 4), (2, 8), (4, 16), (8, 6)])
-def test_nodes_match_oracle(m, p):
-    pr = hps.Problem(m, p, 10.0, 10.0, -1.0, 2.0, 0.5, 1.0)
+@pytest.mark.parametrize("m,my,p", [(1, 1, 4), (2, 2, 8), (4, 4, 16), (8, 8, 6), (4, 2, 6), (1, 8, 6), (16, 2, 4)])
+def test_nodes_match_oracle(m, my, p):
+    pr = hps.Problem(m, p, 10.0, 10.0, -1.0, 2.0, 0.5, 1.0, my=my)
     lxy, bxy = hps.hps_nodes(pr)
-    olxy, obxy = O.nodes(O.Problem(m, p, 10.0, 10.0, -1.0, 2.0, 0.5, 1.0))
+    olxy, obxy = O.nodes(O.Problem(m, p, 10.0, 10.0, -1.0, 2.0, 0.5, 1.0, my=my))
     np.testing.assert_allclose(lxy, olxy, rtol=0, atol=1e-15)
     np.testing.assert_allclose(bxy, obxy, rtol=0, atol=1e-15)
 
@@ -59,7 +59,7 @@ def _desc(**kw):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(mx=3, my=3), dict(mx=4, my=2), dict(mx=0, my=0), dict(p=3), dict(p=33), dict(q=5),
+    dict(mx=3, my=3), dict(mx=4, my=3), dict(mx=2048, my=2), dict(mx=0, my=0), dict(p=3), dict(p=33), dict(q=5),
     dict(kappa=0.0), dict(kappa=-1.0), dict(eta_re=0.0, eta_im=1.0), dict(x1=0.0),
     dict(y1=-1.0), dict(precision=7), dict(precision=-1), dict(kappa=float("nan")),
     dict(precision=1, fp64_levels=-2), dict(fp64_native=2), dict(fp64_native=-1),
@@ -123,3 +123,8 @@ def test_zgemm_argument_checks_need_no_device():
     assert L.hps_zgemm(2, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, 2, None) == hps.HPS_EINVAL
     # host arrays are refused (device memory only)
     assert L.hps_zgemm(2, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, 1, None) == hps.HPS_EINVAL
+
+
+def test_plan_of_a_rectangular_grid():
+    info = hps.hps_plan(hps.Problem(8, 16, 40.0, 40.0, my=2))
+    assert info.leaves == 16 and info.levels == 4 and info.n_bdry == 2 * (8 + 2) * 14

@@ -59,7 +59,7 @@ def _check_against_alone(probs, cs, tol, nrhs=2, tol_R=None):
     assert hps.hps_status(hb[0], st)[0] == hps.HPS_OK
     for k, (pr, c) in enumerate(zip(probs, cs)):
         ha = hps.hps_build(pr, torch.from_numpy(c).cuda(), st)
-        _, s, t = W.random_data(pr.m, pr.p, pr.kappa, pr.eta, seed=900 + k, nrhs=nrhs)
+        _, s, t = W.random_data(pr.m, pr.p, pr.kappa, pr.eta, seed=900 + k, nrhs=nrhs, my=pr.ny)
         assert _rel(_solve(hb[k], s, t), _solve(ha, s, t)) < tol, (k, pr)
         # the root operator of a mixed build carries complex64 rounding from
         # the lower levels (no refinement acts on it)
@@ -158,3 +158,18 @@ def test_planned_launch_count_is_what_the_build_launches(m, precision):
     h = hps.hps_build(pr, torch.from_numpy(c).cuda(), torch.cuda.current_stream())
     assert h.info().build_launches == hps.hps_plan(pr).build_launches
     h.free()
+
+
+def test_batch_with_rectangular_members():
+    """Rectangular grids whose first merges have the square grids' shapes
+    batch with them; a grid whose axes stop alternating earlier does not."""
+    probs = [hps.Problem(4, 8, 10.0, 10.0), hps.Problem(4, 8, 12.0, 12.0, 0.0, 1.0, 0.0, 0.5, my=2),
+             hps.Problem(2, 8, 9.0, 9.0)]
+    cs = [W.random_data(pr.m, 8, pr.kappa, pr.kappa, seed=20 + k, my=pr.ny)[0] for k, pr in enumerate(probs)]
+    for h in _check_against_alone(probs, cs, 1e-12):
+        h.free()
+    bad = [hps.Problem(4, 8, 10.0, 10.0), hps.Problem(2, 8, 10.0, 10.0, my=8)]
+    cb = [W.random_data(pr.m, 8, 10.0, 10.0, seed=1, my=pr.ny)[0] for pr in bad]
+    with pytest.raises(hps.HPSError) as e:
+        hps.hps_build_batch(bad, cb)
+    assert e.value.code == hps.HPS_EINVAL

@@ -233,3 +233,34 @@ def test_64x64_leaves_reproduce_polynomial_and_sampled_leaves():
         assert _rel(Psi, oPsi) < TOL
         assert _rel(Gam, oGam) < 1e-9
     h.free()
+
+
+@pytest.mark.parametrize("mx,my,p,kappa", [(4, 2, 10, 15.0), (2, 8, 8, 12.0), (8, 1, 12, 20.0), (16, 4, 8, 30.0)])
+def test_rectangular_grids_against_oracle(mx, my, p, kappa):
+    """mx != my leaf grids: merges alternate, then the longer axis takes the
+    rest; solution and root operator against the oracle."""
+    dom = (0.0, mx / max(mx, my), 0.0, my / max(mx, my))
+    pr = hps.Problem(mx, p, kappa, kappa, *dom, my=my)
+    opr = O.Problem(mx, p, kappa, kappa, *dom, my=my)
+    c, s, t = W.random_data(mx, p, kappa, kappa, seed=7 * mx + my, nrhs=2, my=my)
+    h = gpu_build(pr, c)
+    u = gpu_solve(h, s, t)
+    R = gpu_root_R(h)
+    with O.Tree(opr, c) as T:
+        uo = T.solve(s, t)
+        Ro = T.root_R()
+    assert _rel(u, uo) < TOL
+    assert _rel(R, Ro) < TOL
+    h.free()
+
+
+def test_rectangular_grid_polynomial_and_mixed_path():
+    wl = W.polynomial_solution(8, 12, 25.0, 25.0, domain=(0.0, 2.0, 0.0, 0.5), my=2)
+    for prec, tol in ((hps.HPS_FP64, 1e-10), (hps.HPS_MIXED, 1e-8)):
+        pr = hps.Problem(8, 12, wl.kappa, wl.eta, 0.0, 2.0, 0.0, 0.5, precision=prec, my=2)
+        lxy, bxy = hps.hps_nodes(pr)
+        c, s, t = wl.sample(lxy, bxy)
+        h = gpu_build(pr, c)
+        u = gpu_solve(h, s[None], t[None])[0]
+        assert _rel(u, wl.u_exact(lxy[..., 0], lxy[..., 1])) < tol, prec
+        h.free()
