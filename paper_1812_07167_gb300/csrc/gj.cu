@@ -417,7 +417,10 @@ __device__ __forceinline__ bool skipped(int j, int a0, int a1, int b0, int b1) {
 
 // Apply the panel [k0, k0+kbp) held in s.T / s.mv to the own columns
 // j = c0 + jj, jj in [ja, jb), except those in [a0, a1) and [b0, b1).
-template <class C>
+// CU columns go through the update together (more loads in flight; the
+// panel values are read once for all of them): 4 for complex64, whose
+// update is short and latency-bound, 1 for complex128.
+template <class C, int CU = (sizeof(C) == 8 ? 4 : 1)>
 __device__ void apply_panel(const Shared<C> &s, const C *T, C *S, int c0, int ja, int jb,
                             int a0, int a1, int b0, int b1, int k0, int kbp) {
   const int tid = threadIdx.x, nthr = blockDim.x, n = s.n, cw = s.cw;
@@ -441,36 +444,84 @@ __device__ void apply_panel(const Shared<C> &s, const C *T, C *S, int c0, int ja
   }
   __syncthreads();
   // 2) a <- a + (T - I[:, P]) x: rows P get T x, the other rows add T x
-  const int cl = tid >> 6, rl = tid & 63;
-  for (int jj = ja + cl; jj < jb; jj += (nthr >> 6)) {
-    const int j = c0 + jj;
-    if (skipped(j, a0, a1, b0, b1)) continue;
-    C *Sj = S + (size_t)j * n;
-    for (int base = 0; base < n; base += 256) {
-      C v[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int i = base + rl + 64 * u;
-        v[u] = (i < n && (i < k0 || i >= k0 + kbp)) ? Sj[i] : CX<C>::make(0.0, 0.0);
-      }
-      for (int q = 0; q < kbp; q++) {
-        const C xv = s.x[q * cw + jj];
-        const C *Tq = T + q * n + base + rl;
+  if (CU == 1) {
+    const int cl = tid >> 6, rl = tid & 63;
+    for (int jj = ja + cl; jj < jb; jj += (nthr >> 6)) {
+      const int j = c0 + jj;
+      if (skipped(j, a0, a1, b0, b1)) continue;
+      C *Sj = S + (size_t)j * n;
+      for (int base = 0; base < n; base += 256) {
+        C v[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-          if (base + rl + 64 * u < n) {
-            const C t = Tq[64 * u];
-            v[u].x = CX<C>::fmad(t.x, xv.x, v[u].x);
-            v[u].x = CX<C>::fmad(-t.y, xv.y, v[u].x);
-            v[u].y = CX<C>::fmad(t.x, xv.y, v[u].y);
-            v[u].y = CX<C>::fmad(t.y, xv.x, v[u].y);
+          const int i = base + rl + 64 * u;
+          v[u] = (i < n && (i < k0 || i >= k0 + kbp)) ? Sj[i] : CX<C>::make(0.0, 0.0);
+        }
+        for (int q = 0; q < kbp; q++) {
+          const C xv = s.x[q * cw + jj];
+          const C *Tq = T + q * n + base + rl;
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            if (base + rl + 64 * u < n) {
+              const C t = Tq[64 * u];
+              v[u].x = CX<C>::fmad(t.x, xv.x, v[u].x);
+              v[u].x = CX<C>::fmad(-t.y, xv.y, v[u].x);
+              v[u].y = CX<C>::fmad(t.x, xv.y, v[u].y);
+              v[u].y = CX<C>::fmad(t.y, xv.x, v[u].y);
+            }
           }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int i = base + rl + 64 * u;
-        if (i < n) Sj[i] = v[u];
+        for (int u = 0; u < 4; u++) {
+          const int i = base + rl + 64 * u;
+          if (i < n) Sj[i] = v[u];
+        }
+      }
+    }
+  } else {
+    const int cl = tid >> 6, rl = tid & 63, lanes = nthr >> 6;
+    for (int j0 = cl; j0 < nj; j0 += lanes * CU) {
+      int jjs[CU];
+      bool ok[CU];
+#pragma unroll
+      for (int u = 0; u < CU; u++) {
+        jjs[u] = ja + j0 + lanes * u;
+        ok[u] = (j0 + lanes * u < nj) && !skipped(c0 + jjs[u], a0, a1, b0, b1);
+      }
+      for (int base = 0; base < n; base += 256) {
+        C v[CU][4];
+#pragma unroll
+        for (int u = 0; u < CU; u++)
+#pragma unroll
+          for (int r = 0; r < 4; r++) {
+            const int i = base + rl + 64 * r;
+            v[u][r] = (ok[u] && i < n && (i < k0 || i >= k0 + kbp)) ? S[(size_t)(c0 + jjs[u]) * n + i]
+                                                                   : CX<C>::make(0.0, 0.0);
+          }
+        for (int q = 0; q < kbp; q++) {
+          const C *Tq = T + q * n + base + rl;
+          C t[4];
+#pragma unroll
+          for (int r = 0; r < 4; r++) t[r] = (base + rl + 64 * r < n) ? Tq[64 * r] : CX<C>::make(0.0, 0.0);
+#pragma unroll
+          for (int u = 0; u < CU; u++) {
+            const C xv = ok[u] ? s.x[q * cw + jjs[u]] : CX<C>::make(0.0, 0.0);
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+              v[u][r].x = CX<C>::fmad(t[r].x, xv.x, v[u][r].x);
+              v[u][r].x = CX<C>::fmad(-t[r].y, xv.y, v[u][r].x);
+              v[u][r].y = CX<C>::fmad(t[r].x, xv.y, v[u][r].y);
+              v[u][r].y = CX<C>::fmad(t[r].y, xv.x, v[u][r].y);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < CU; u++)
+#pragma unroll
+          for (int r = 0; r < 4; r++) {
+            const int i = base + rl + 64 * r;
+            if (ok[u] && i < n) S[(size_t)(c0 + jjs[u]) * n + i] = v[u][r];
+          }
       }
     }
   }

@@ -1143,8 +1143,9 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   // cluster per leaf: wider clusters split each leaf finer, which balances
   // the chip when there are few leaves (measured best: 8 CTAs a leaf for 16
   // leaves, 4 for 256, 1 from 1024 leaves on)
+  // (complex64 leaves are latency-bound: one CTA a leaf from 256 leaves on)
   int lcs = 1;
-  while (lcs < 8 && NL * lcs < 1024) lcs *= 2;
+  while (lcs < 8 && NL * lcs < (lf ? 256 : 1024)) lcs *= 2;
   if (const char *ev = getenv("HPS_LEAF_CLUSTER")) {
     int v = atoi(ev);
     if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) lcs = v;
@@ -1382,7 +1383,7 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
   // chip when there are few leaves (measured best: 8 CTAs a leaf for 16
   // leaves, 4 for 256, 1 from 1024 leaves on)
   int cs = 1;
-  while (cs < 8 && (long long)h->plan.leaves * cs < 1024) cs *= 2;
+  while (cs < 8 && (long long)h->plan.leaves * cs < (h->plan.leaf_f32 ? 256 : 1024)) cs *= 2;
   if (const char *e = getenv("HPS_LEAF_CLUSTER")) {
     int v = atoi(e);
     if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) cs = v;
