@@ -51,6 +51,8 @@ def config_dict(nrhs=1, l2="flushed between steps (256 MiB write)"):
         "c": "1+0.3 sin(4 pi x) cos(6 pi y)", "s": "8 Gaussian sources, width 0.01, seed 1", "t": 0,
         "dof": M * M * (P_ORDER * P_ORDER - 4), "tensor_nodes": M * M * P_ORDER * P_ORDER,
         "nrhs_per_step": nrhs, "l2": l2, "precision": "complex128",
+        "products": "FP64 pipes; merge products of 2^26+ complex multiply-adds by the Ozaki scheme "
+                    "on the bf16 tensor cores (9 slices of 6 bits, exact FP32 slice sums, complex128 totals)",
         "domain": list(wl.domain),
     }
 
