@@ -436,6 +436,21 @@ def batching(dev, st, flush, reps=2):
                     h.free()
             res[f"{mode}_ms"] = statistics.median(ms)
             res[f"{mode}_dof_per_s"] = out["dof"] / (statistics.median(ms) / 1e3)
+        # new coefficients for the same batch: the build replayed as one CUDA graph
+        hs = hps.hps_build_batch(probs, cs, st)
+        hps.hps_rebuild(hs, cs, st)  # captures the graph
+        torch.cuda.synchronize()
+        ms = []
+        for rep in range(reps):
+            flush.zero_()
+            e0.record(st)
+            hps.hps_rebuild(hs, cs, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res["rebuild_graph_ms"] = statistics.median(ms)
+        for h in hs:
+            h.free()
         res["speedup"] = res["separate_ms"] / res["batched_ms"]
         a, b = us[(name, "batched")], us[(name, "separate")]
         res["rel_diff_u_batched_vs_separate"] = float(np.abs(a - b).max() / np.abs(b).max())

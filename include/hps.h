@@ -160,6 +160,20 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
 int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, void *stream,
                     hps_handle **out);
 
+/* Rebuild for new coefficients: recompute every operator of a build (all nh
+ * handles one hps_build or hps_build_batch returned, in any order) from new
+ * samples c[k] of problem k's c, with the same geometry, p, kappa, eta and
+ * precision (Algorithm 1 again, into the same device memory).  The build's
+ * launch sequence is captured into a CUDA graph by the first call and
+ * replayed by every later one, so a rebuild costs one graph launch on top of
+ * the copies of c.
+ *   c[k]: [leaves][(p-2)^2] of hs[k], device or host memory.
+ * Work that used the old operators must be ordered before the call (same
+ * stream, or events).  hps_build_times keeps the first build's phases.
+ * Returns HPS_EINVAL (not exactly the build's handles, a handle of the build
+ * already freed, NULL arrays), HPS_ECUDA. */
+int hps_rebuild(int nh, hps_handle *const *hs, const double *const *c, void *stream);
+
 /* Solve for nrhs right-hand sides (Algorithm 2: upward then downward pass).
  * For an HPS_MIXED handle the solve is iterative refinement: u = S(s, t), then
  * refine_steps times: the residual of the global collocation system (every

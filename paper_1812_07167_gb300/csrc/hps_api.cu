@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <mutex>
 #include <cmath>
 #include <cstdint>
@@ -85,6 +86,11 @@ struct Shared {
   int refs = 0;                 // handles referring to it (guarded by g_shared_mu)
   std::vector<cudaEvent_t> ev;  // [before leaves, after leaves, after merge 0, ...]
   int launches = 0;             // kernels the build launched
+  // the build's device work (reads c and every table from the arena), for
+  // hps_rebuild, and its captured graph
+  std::function<int(cudaStream_t, bool, int &)> compute;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<hps_handle *> order;  // the handles in build order
 };
 static std::mutex g_shared_mu;
 
@@ -844,6 +850,7 @@ int hps_free(hps_handle *h) {
     }
     if (last) {
       for (cudaEvent_t e : sh->ev) cudaEventDestroy(e);
+      if (sh->graph) cudaGraphExecDestroy(sh->graph);
       if (sh->arena) cudaFree(sh->arena);
       delete sh;
     }
@@ -988,7 +995,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   std::vector<size_t> oTab(K), oC(K, 0);
   for (int k = 0; k < K; k++) {
     oTab[k] = take(tab_bytes);
-    if (mixed) oC[k] = take(sizeof(double) * (size_t)hs[k]->plan.leaves * ni);
+    oC[k] = take(sizeof(double) * (size_t)hs[k]->plan.leaves * ni);
   }
   // index maps: per level I1, I2, I3a, I3b, the I3 pairs; per problem the
   // root and outer maps
@@ -1029,6 +1036,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   }
   char *base = (char *)sh->arena;
   for (int k = 0; k < K; k++) hs[k]->sh = sh;  // from here on hps_free releases it
+  sh->order = hs;
 
   // ---- every problem's view of the arena ----
   int *d_ints = (int *)(base + oInts);
@@ -1058,7 +1066,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     }
     if (pl.L == 0) h->Rroot = (double2 *)(base + oRoot1 + 16ULL * (k - k1) * nb * nb);
     h->tables = base + oTab[k];
-    h->c_dev = mixed ? (double *)(base + oC[k]) : nullptr;
+    h->c_dev = (double *)(base + oC[k]);
     h->d_ints = d_ints;
     h->d_status = d_status;
     h->d_root_src = d_ints + root_at[k];
@@ -1102,30 +1110,14 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   CK(cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(d_status, 0, sizeof(unsigned int), st));
 
-  // ---- c on the device (the mixed path keeps a copy for its residuals) ----
-  size_t host_c = 0;
-  std::vector<bool> cdev(K);
-  for (int k = 0; k < K; k++) {
-    cdev[k] = is_device_ptr(cin[k]);
-    if (!mixed && !cdev[k]) host_c += align256(sizeof(double) * (size_t)hs[k]->plan.leaves * ni);
-  }
-  char *c_stage = nullptr;
-  if (host_c) CK(cudaMallocAsync((void **)&c_stage, host_c, st));
+  // ---- c into the arena (the leaf kernel and the mixed path's residual read
+  // it there; hps_rebuild replaces it) ----
   std::vector<hps::LeafProb> probs(K);
-  size_t at = 0;
   for (int k = 0; k < K; k++) {
     const size_t cb = sizeof(double) * (size_t)hs[k]->plan.leaves * ni;
-    const double *cd = cin[k];
-    if (mixed) {
-      CK(cudaMemcpyAsync(hs[k]->c_dev, cin[k], cb, cudaMemcpyDefault, st));
-      cd = hs[k]->c_dev;
-    } else if (!cdev[k]) {
-      CK(cudaMemcpyAsync(c_stage + at, cin[k], cb, cudaMemcpyHostToDevice, st));
-      cd = (const double *)(c_stage + at);
-      at += align256(cb);
-    }
+    CK(cudaMemcpyAsync(hs[k]->c_dev, cin[k], cb, cudaMemcpyDefault, st));
     probs[k].tab = (const double *)hs[k]->tables;
-    probs[k].c = cd;
+    probs[k].c = hs[k]->c_dev;
     probs[k].leaf0 = leaf0[k];
     probs[k].eta = make_double2(hs[k]->desc.eta_re, hs[k]->desc.eta_im);
     probs[k].kappa2 = hs[k]->desc.kappa * hs[k]->desc.kappa;
@@ -1133,240 +1125,249 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   hps::LeafProb *d_probs = (hps::LeafProb *)(base + oProbs);
   CK(cudaMemcpyAsync(d_probs, probs.data(), sizeof(hps::LeafProb) * K, cudaMemcpyHostToDevice, st));
 
-  // ---- leaves (Sec. 2.1): one cluster launch over every problem's leaves ----
-  hps::LeafTables lt;
-  lt.p = p;
-  lt.e = P0.e;
-  lt.n = n;
-  lt.nb = nb;
-  lt.ni = ni;
-  // cluster per leaf: wider clusters split each leaf finer, which balances
-  // the chip when there are few leaves (measured best: 8 CTAs a leaf for 16
-  // leaves, 4 for 256, 1 from 1024 leaves on)
-  // (complex64 leaves are latency-bound: one CTA a leaf from 256 leaves on)
-  int lcs = 1;
-  while (lcs < 8 && NL * lcs < (lf ? 256 : 1024)) lcs *= 2;
-  if (const char *ev = getenv("HPS_LEAF_CLUSTER")) {
-    int v = atoi(ev);
-    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) lcs = v;
-  }
-  // scratch for the in-place elimination: leaves go in chunks of at most
-  // ~1 GiB of matrices
-  const int chunk = (int)std::max<long long>(1, std::min<long long>(NL, (1LL << 30) / (esl * n * n)));
-  void *lscr = nullptr;
-  int *lmeta = nullptr;
-  CK(cudaMallocAsync(&lscr, (size_t)esl * chunk * n * n, st));
-  CK(cudaMallocAsync((void **)&lmeta, sizeof(int) * (size_t)chunk * hps::gj_meta_ints(n), st));
   sh->ev.assign(Lmax + 2, nullptr);
   for (cudaEvent_t &e : sh->ev) CK(cudaEventCreate(&e));
-  CK(cudaEventRecord(sh->ev[0], st));
-  int launches = 0;
-  for (long long l0 = 0; l0 < NL; l0 += chunk) {
-    CK(hps::launch_leaf(lt, d_probs, K, l0, (int)std::min<long long>(chunk, NL - l0), base + oX, base + oGX,
-                        lscr, lmeta, d_status, Lmax, lcs, lf != 0, st));
-    launches++;
-  }
-  CK(cudaEventRecord(sh->ev[1], st));
-  CK(cudaFreeAsync(lscr, st));
-  CK(cudaFreeAsync(lmeta, st));
-  if (c_stage) CK(cudaFreeAsync(c_stage, st));
-
-  if (k1 < K) {
-    // single-leaf problems: the root R is the leaf's R = GX[:, :nb]
-    CopyBatch cb;
-    cb.count = 1;
-    cb.d[0] = copy(nb, nb, K - k1, mat(base + oGX + esl * leaf0[k1] * n * nb, nb, (long long)n * nb, nullptr,
-                                       nullptr, lf),
-                   mat(base + oRoot1, nb, (long long)nb * nb));
-    CK(hps::launch_copy(cb, st));
-    launches++;
-  }
-
-  // ---- merges (Sec. 2.2), one level at a time (Algorithm 3's level loop) ----
-  // scratch: two R buffers (children / parents), then Q, W, converted
-  // children (all sized for complex128) and the elimination metadata
-  size_t rbytes = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
-  for (int j = 0; j < Lmax; j++) {
-    const Level &S = P0.lv[j];
-    size_t rb = 0;
-    for (BuildRun &r : runs[j]) {
-      if (!r.finishing) {
-        r.rout = rb;
-        rb = align256(rb + (size_t)(esz(r.f32) * r.P * S.nt * S.nt));
-      }
-      qbuf = std::max(qbuf, (size_t)r.P * S.n3 * S.nt);
-      wbuf = std::max(wbuf, (size_t)r.P * S.n3 * S.n3);
-      mbuf = std::max(mbuf, (size_t)r.P * hps::gj_meta_ints(S.n3));
-      std::vector<ChildPiece> pcs = child_pieces(runs, j, r);
-      const int cf = pcs[0].run < 0 ? lf : runs[j - 1][pcs[0].run].f32;
-      if (pcs.size() > 1 || cf != r.f32) cbuf = std::max(cbuf, (size_t)2 * r.P * S.nc * S.nc);
+  const std::vector<cudaEvent_t> ev = sh->ev;
+  // the device work of the build from here on: run now, and captured into a
+  // CUDA graph by hps_rebuild (it reads c and every table from the arena)
+  auto compute = [=](cudaStream_t st, bool events, int &launches) mutable -> int {
+    // ---- leaves (Sec. 2.1): one cluster launch over every problem's leaves ----
+    hps::LeafTables lt;
+    lt.p = p;
+    lt.e = P0.e;
+    lt.n = n;
+    lt.nb = nb;
+    lt.ni = ni;
+    // cluster per leaf: wider clusters split each leaf finer, which balances
+    // the chip when there are few leaves (measured best: 8 CTAs a leaf for 16
+    // leaves, 4 for 256, 1 from 1024 leaves on)
+    // (complex64 leaves are latency-bound: one CTA a leaf from 256 leaves on)
+    int lcs = 1;
+    while (lcs < 8 && NL * lcs < (lf ? 256 : 1024)) lcs *= 2;
+    if (const char *ev = getenv("HPS_LEAF_CLUSTER")) {
+      int v = atoi(ev);
+      if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) lcs = v;
     }
-    rbytes = std::max(rbytes, rb);
-  }
-  // workspace of the products done on the tensor cores
-  size_t oz_bytes = 0;
-  for (int j = 0; j < Lmax; j++) {
-    const Level &S = P0.lv[j];
-    int mnk[6][3];
-    merge_products(S.n1, S.n2, S.n3, S.nt, mnk);
-    for (const BuildRun &r : runs[j])
-      for (int q = 0; q < 6; q++)
-        if (oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P, r.f32, P0.oz))
-          oz_bytes = std::max(oz_bytes, oz_bytes_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P));
-  }
-  char *scratch = nullptr;
-  int *wmeta = nullptr;
-  const size_t sbytes = 2 * rbytes + sizeof(double2) * (qbuf + wbuf + cbuf);
-  if (Lmax > 0) {
-    CK(cudaMallocAsync((void **)&scratch, align256(sbytes) + oz_bytes, st));
-    CK(cudaMallocAsync((void **)&wmeta, sizeof(int) * std::max<size_t>(mbuf, 1), st));
-  }
-  char *Rbuf[2] = {scratch, scratch + rbytes};
-  double2 *Q = (double2 *)(scratch + 2 * rbytes);
-  double2 *Wscr = Q + qbuf;
-  double2 *Rconv = Wscr + wbuf;
-  void *ozws = oz_bytes ? scratch + align256(sbytes) : nullptr;
-  // products: emulated ones one at a time, the rest in one launch
-  auto run_gemm = [&](GemmDesc *gd, int nd) -> int {
-    GemmDesc rest[2];
-    int nr = 0;
-    for (int q = 0; q < nd; q++) {
-      if (P0.oz && hps::oz_eligible(gd[q])) {
-        CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, st));
-        launches += hps::oz_launches(gd[q]);
-      } else {
-        rest[nr++] = gd[q];
-      }
-    }
-    if (nr) {
-      CK(hps::launch_gemm(rest, nr, st));
+    // scratch for the in-place elimination: leaves go in chunks of at most
+    // ~1 GiB of matrices
+    const int chunk = (int)std::max<long long>(1, std::min<long long>(NL, (1LL << 30) / (esl * n * n)));
+    void *lscr = nullptr;
+    int *lmeta = nullptr;
+    CK(cudaMallocAsync(&lscr, (size_t)esl * chunk * n * n, st));
+    CK(cudaMallocAsync((void **)&lmeta, sizeof(int) * (size_t)chunk * hps::gj_meta_ints(n), st));
+    if (events) CK(cudaEventRecord(ev[0], st));
+    launches = 0;
+    for (long long l0 = 0; l0 < NL; l0 += chunk) {
+      CK(hps::launch_leaf(lt, d_probs, K, l0, (int)std::min<long long>(chunk, NL - l0), base + oX, base + oGX,
+                          lscr, lmeta, d_status, Lmax, lcs, lf != 0, st));
       launches++;
     }
+    if (events) CK(cudaEventRecord(ev[1], st));
+    CK(cudaFreeAsync(lscr, st));
+    CK(cudaFreeAsync(lmeta, st));
+
+    if (k1 < K) {
+      // single-leaf problems: the root R is the leaf's R = GX[:, :nb]
+      CopyBatch cb;
+      cb.count = 1;
+      cb.d[0] = copy(nb, nb, K - k1, mat(base + oGX + esl * leaf0[k1] * n * nb, nb, (long long)n * nb, nullptr,
+                                         nullptr, lf),
+                     mat(base + oRoot1, nb, (long long)nb * nb));
+      CK(hps::launch_copy(cb, st));
+      launches++;
+    }
+
+    // ---- merges (Sec. 2.2), one level at a time (Algorithm 3's level loop) ----
+    // scratch: two R buffers (children / parents), then Q, W, converted
+    // children (all sized for complex128) and the elimination metadata
+    size_t rbytes = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
+    for (int j = 0; j < Lmax; j++) {
+      const Level &S = P0.lv[j];
+      size_t rb = 0;
+      for (BuildRun &r : runs[j]) {
+        if (!r.finishing) {
+          r.rout = rb;
+          rb = align256(rb + (size_t)(esz(r.f32) * r.P * S.nt * S.nt));
+        }
+        qbuf = std::max(qbuf, (size_t)r.P * S.n3 * S.nt);
+        wbuf = std::max(wbuf, (size_t)r.P * S.n3 * S.n3);
+        mbuf = std::max(mbuf, (size_t)r.P * hps::gj_meta_ints(S.n3));
+        std::vector<ChildPiece> pcs = child_pieces(runs, j, r);
+        const int cf = pcs[0].run < 0 ? lf : runs[j - 1][pcs[0].run].f32;
+        if (pcs.size() > 1 || cf != r.f32) cbuf = std::max(cbuf, (size_t)2 * r.P * S.nc * S.nc);
+      }
+      rbytes = std::max(rbytes, rb);
+    }
+    // workspace of the products done on the tensor cores
+    size_t oz_bytes = 0;
+    for (int j = 0; j < Lmax; j++) {
+      const Level &S = P0.lv[j];
+      int mnk[6][3];
+      merge_products(S.n1, S.n2, S.n3, S.nt, mnk);
+      for (const BuildRun &r : runs[j])
+        for (int q = 0; q < 6; q++)
+          if (oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P, r.f32, P0.oz))
+            oz_bytes = std::max(oz_bytes, oz_bytes_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P));
+    }
+    char *scratch = nullptr;
+    int *wmeta = nullptr;
+    const size_t sbytes = 2 * rbytes + sizeof(double2) * (qbuf + wbuf + cbuf);
+    if (Lmax > 0) {
+      CK(cudaMallocAsync((void **)&scratch, align256(sbytes) + oz_bytes, st));
+      CK(cudaMallocAsync((void **)&wmeta, sizeof(int) * std::max<size_t>(mbuf, 1), st));
+    }
+    char *Rbuf[2] = {scratch, scratch + rbytes};
+    double2 *Q = (double2 *)(scratch + 2 * rbytes);
+    double2 *Wscr = Q + qbuf;
+    double2 *Rconv = Wscr + wbuf;
+    void *ozws = oz_bytes ? scratch + align256(sbytes) : nullptr;
+    // products: emulated ones one at a time, the rest in one launch
+    auto run_gemm = [&](GemmDesc *gd, int nd) -> int {
+      GemmDesc rest[2];
+      int nr = 0;
+      for (int q = 0; q < nd; q++) {
+        if (P0.oz && hps::oz_eligible(gd[q])) {
+          CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, st));
+          launches += hps::oz_launches(gd[q]);
+        } else {
+          rest[nr++] = gd[q];
+        }
+      }
+      if (nr) {
+        CK(hps::launch_gemm(rest, nr, st));
+        launches++;
+      }
+      return HPS_OK;
+    };
+
+    auto sub = [&](Mat m, const int *r, const int *c) {
+      m.rmap = r;
+      m.cmap = c;
+      return m;
+    };
+    for (int j = 0; j < Lmax; j++) {
+      const Level &S = P0.lv[j];
+      const int n1 = S.n1, n2 = S.n2, n3 = S.n3, nt = S.nt, nc = S.nc;
+      const int *dI1 = d_ints + imap[5 * j + 0], *dI2 = d_ints + imap[5 * j + 1];
+      const int *dI3a = d_ints + imap[5 * j + 2], *dI3b = d_ints + imap[5 * j + 3];
+      for (const BuildRun &r : runs[j]) {
+        const int P = r.P, f = r.f32;
+        // children's R: in place when one run of this precision holds them all
+        const void *Rc;
+        int rcf;
+        long long ldc, strc;
+        std::vector<ChildPiece> pcs = child_pieces(runs, j, r);
+        auto piece_src = [&](const ChildPiece &c, int &pf) {
+          if (c.run < 0) {
+            pf = lf;
+            return mat(base + oGX + esl * c.c0 * n * nb, nb, (long long)n * nb, nullptr, nullptr, lf);
+          }
+          const BuildRun &q = runs[j - 1][c.run];
+          pf = q.f32;
+          return mat(Rbuf[(j - 1) & 1] + q.rout + esz(q.f32) * (c.c0 - q.p0) * nc * nc, nc, (long long)nc * nc,
+                     nullptr, nullptr, q.f32);
+        };
+        int pf0;
+        Mat m0 = piece_src(pcs[0], pf0);
+        if (pcs.size() == 1 && pf0 == f) {
+          Rc = m0.ptr;
+          rcf = pf0;
+          ldc = m0.ld;
+          strc = m0.stride;
+        } else {
+          // gather (and widen) the children into one complex128 array
+          CopyBatch cv;
+          cv.count = 0;
+          for (const ChildPiece &c : pcs) {
+            int pf;
+            Mat src = piece_src(c, pf);
+            cv.d[cv.count++] = copy(nc, nc, (int)c.count, src,
+                                    mat(Rconv + (c.c0 - 2 * r.p0) * nc * nc, nc, (long long)nc * nc));
+          }
+          CK(hps::launch_copy(cv, st));
+          launches++;
+          Rc = Rconv;
+          rcf = 0;
+          ldc = nc;
+          strc = (long long)nc * nc;
+        }
+        void *Rp = r.finishing ? (void *)(base + r.root) : (void *)(Rbuf[j & 1] + r.rout);
+        void *Winv = base + r.op[0], *R33a = base + r.op[1], *R33b = base + r.op[2], *R13a = base + r.op[3];
+        void *R23b = base + r.op[4], *Phia = base + r.op[5], *Phib = base + r.op[6];
+        const long long s2 = 2 * strc;
+        Mat Ra = mat(Rc, ldc, s2, nullptr, nullptr, rcf), Rb = mat(elem(Rc, strc, rcf), ldc, s2, nullptr, nullptr, rcf);
+        auto M = [&](const void *ptr, long long ld, long long stride) { return mat(ptr, ld, stride, nullptr, nullptr, f); };
+        // stored blocks and the parts of Phi_b and R^tau that are copies
+        CopyBatch cb;
+        cb.count = 0;
+        cb.d[cb.count++] = copy(n3, n3, P, sub(Ra, dI3a, dI3a), M(R33a, n3, (long long)n3 * n3));
+        cb.d[cb.count++] = copy(n3, n3, P, sub(Rb, dI3b, dI3b), M(R33b, n3, (long long)n3 * n3));
+        cb.d[cb.count++] = copy(n1, n3, P, sub(Ra, dI1, dI3a), M(R13a, n1, (long long)n1 * n3));
+        cb.d[cb.count++] = copy(n2, n3, P, sub(Rb, dI2, dI3b), M(R23b, n2, (long long)n2 * n3));
+        // Q = [R33b R31a | -R32b]: the right block here, the left one by GEMM below
+        cb.d[cb.count++] = copy(n3, n2, P, sub(Rb, dI3b, dI2),
+                                M(elem(Q, (long long)n1 * n3, f), n3, (long long)n3 * nt), -1.0);
+        // Phi_b starts as -[R31a | 0]
+        cb.d[cb.count++] = copy(n3, n1, P, sub(Ra, dI3a, dI1), M(Phib, n3, (long long)n3 * nt), -1.0);
+        cb.d[cb.count++] = copy(n3, n2, P, mat(nullptr, 0, 0), M(elem(Phib, (long long)n1 * n3, f), n3, (long long)n3 * nt));
+        // R^tau starts as diag(R11a, R22b)
+        const long long sp = (long long)nt * nt;
+        cb.d[cb.count++] = copy(n1, n1, P, sub(Ra, dI1, dI1), M(Rp, nt, sp));
+        cb.d[cb.count++] = copy(n2, n2, P, sub(Rb, dI2, dI2), M(elem(Rp, (long long)n1 * nt + n1, f), nt, sp));
+        cb.d[cb.count++] = copy(n2, n1, P, mat(nullptr, 0, 0), M(elem(Rp, n1, f), nt, sp));
+        cb.d[cb.count++] = copy(n1, n2, P, mat(nullptr, 0, 0), M(elem(Rp, (long long)n1 * nt, f), nt, sp));
+        CK(hps::launch_copy(cb, st));
+
+        const long long s33 = (long long)n3 * n3, s3t = (long long)n3 * nt;
+        // W = I - R33b R33a (in scratch), then W^{-1} into its stored slot
+        GemmDesc g = gemm(n3, n3, n3, P, M(R33b, n3, s33), M(R33a, n3, s33), M(Wscr, n3, s33));
+        g.alpha = make_double2(-1.0, 0.0);
+        g.addI = 1;
+        g.cf32 = f;
+        if (int rc = run_gemm(&g, 1)) return rc;
+        const int lev = S.lev;  // the tallest tree's level numbering
+        if (r.gj.wide)
+          CK(hps::launch_gj_wide(Wscr, Winv, n3, P, r.gj.wide, wmeta, d_status, lev, f != 0, st));
+        else
+          CK(hps::launch_gj_inverse(Wscr, Winv, n3, P, wmeta, d_status, lev, r.gj.cs, r.gj.tglobal, f != 0, st));
+        // Q(:, :n1) = R33b R31a
+        g = gemm(n3, n1, n3, P, M(R33b, n3, s33), sub(Ra, dI3a, dI1), M(Q, n3, s3t));
+        g.cf32 = f;
+        if (int rc = run_gemm(&g, 1)) return rc;
+        // Phi_a = W^{-1} Q
+        g = gemm(n3, nt, n3, P, M(Winv, n3, s33), M(Q, n3, s3t), M(Phia, n3, s3t));
+        g.cf32 = f;
+        if (int rc = run_gemm(&g, 1)) return rc;
+        // Phi_b = -[R31a | 0] - R33a Phi_a
+        g = gemm(n3, nt, n3, P, M(R33a, n3, s33), M(Phia, n3, s3t), M(Phib, n3, s3t));
+        g.alpha = make_double2(-1.0, 0.0);
+        g.D = g.C;
+        g.beta = make_double2(1.0, 0.0);
+        g.cf32 = f;
+        if (int rc = run_gemm(&g, 1)) return rc;
+        // R^tau = diag(R11a, R22b) + diag(R13a, R23b) [Phi_a; Phi_b]
+        GemmDesc g2[2];
+        g2[0] = gemm(n1, nt, n3, P, M(R13a, n1, (long long)n1 * n3), M(Phia, n3, s3t), M(Rp, nt, sp));
+        g2[0].D = g2[0].C;
+        g2[0].beta = make_double2(1.0, 0.0);
+        g2[0].cf32 = f;
+        g2[1] = gemm(n2, nt, n3, P, M(R23b, n2, (long long)n2 * n3), M(Phib, n3, s3t), M(elem(Rp, n1, f), nt, sp));
+        g2[1].D = g2[1].C;
+        g2[1].beta = make_double2(1.0, 0.0);
+        g2[1].cf32 = f;
+        if (int rc = run_gemm(g2, 2)) return rc;
+        launches += 1 + gj_launches(n3, r.gj);  // the copy and W^{-1}
+      }
+      if (events) CK(cudaEventRecord(ev[2 + j], st));
+    }
+    if (scratch) CK(cudaFreeAsync(scratch, st));
+    if (wmeta) CK(cudaFreeAsync(wmeta, st));
     return HPS_OK;
   };
-
-  auto sub = [&](Mat m, const int *r, const int *c) {
-    m.rmap = r;
-    m.cmap = c;
-    return m;
-  };
-  for (int j = 0; j < Lmax; j++) {
-    const Level &S = P0.lv[j];
-    const int n1 = S.n1, n2 = S.n2, n3 = S.n3, nt = S.nt, nc = S.nc;
-    const int *dI1 = d_ints + imap[5 * j + 0], *dI2 = d_ints + imap[5 * j + 1];
-    const int *dI3a = d_ints + imap[5 * j + 2], *dI3b = d_ints + imap[5 * j + 3];
-    for (const BuildRun &r : runs[j]) {
-      const int P = r.P, f = r.f32;
-      // children's R: in place when one run of this precision holds them all
-      const void *Rc;
-      int rcf;
-      long long ldc, strc;
-      std::vector<ChildPiece> pcs = child_pieces(runs, j, r);
-      auto piece_src = [&](const ChildPiece &c, int &pf) {
-        if (c.run < 0) {
-          pf = lf;
-          return mat(base + oGX + esl * c.c0 * n * nb, nb, (long long)n * nb, nullptr, nullptr, lf);
-        }
-        const BuildRun &q = runs[j - 1][c.run];
-        pf = q.f32;
-        return mat(Rbuf[(j - 1) & 1] + q.rout + esz(q.f32) * (c.c0 - q.p0) * nc * nc, nc, (long long)nc * nc,
-                   nullptr, nullptr, q.f32);
-      };
-      int pf0;
-      Mat m0 = piece_src(pcs[0], pf0);
-      if (pcs.size() == 1 && pf0 == f) {
-        Rc = m0.ptr;
-        rcf = pf0;
-        ldc = m0.ld;
-        strc = m0.stride;
-      } else {
-        // gather (and widen) the children into one complex128 array
-        CopyBatch cv;
-        cv.count = 0;
-        for (const ChildPiece &c : pcs) {
-          int pf;
-          Mat src = piece_src(c, pf);
-          cv.d[cv.count++] = copy(nc, nc, (int)c.count, src,
-                                  mat(Rconv + (c.c0 - 2 * r.p0) * nc * nc, nc, (long long)nc * nc));
-        }
-        CK(hps::launch_copy(cv, st));
-        launches++;
-        Rc = Rconv;
-        rcf = 0;
-        ldc = nc;
-        strc = (long long)nc * nc;
-      }
-      void *Rp = r.finishing ? (void *)(base + r.root) : (void *)(Rbuf[j & 1] + r.rout);
-      void *Winv = base + r.op[0], *R33a = base + r.op[1], *R33b = base + r.op[2], *R13a = base + r.op[3];
-      void *R23b = base + r.op[4], *Phia = base + r.op[5], *Phib = base + r.op[6];
-      const long long s2 = 2 * strc;
-      Mat Ra = mat(Rc, ldc, s2, nullptr, nullptr, rcf), Rb = mat(elem(Rc, strc, rcf), ldc, s2, nullptr, nullptr, rcf);
-      auto M = [&](const void *ptr, long long ld, long long stride) { return mat(ptr, ld, stride, nullptr, nullptr, f); };
-      // stored blocks and the parts of Phi_b and R^tau that are copies
-      CopyBatch cb;
-      cb.count = 0;
-      cb.d[cb.count++] = copy(n3, n3, P, sub(Ra, dI3a, dI3a), M(R33a, n3, (long long)n3 * n3));
-      cb.d[cb.count++] = copy(n3, n3, P, sub(Rb, dI3b, dI3b), M(R33b, n3, (long long)n3 * n3));
-      cb.d[cb.count++] = copy(n1, n3, P, sub(Ra, dI1, dI3a), M(R13a, n1, (long long)n1 * n3));
-      cb.d[cb.count++] = copy(n2, n3, P, sub(Rb, dI2, dI3b), M(R23b, n2, (long long)n2 * n3));
-      // Q = [R33b R31a | -R32b]: the right block here, the left one by GEMM below
-      cb.d[cb.count++] = copy(n3, n2, P, sub(Rb, dI3b, dI2),
-                              M(elem(Q, (long long)n1 * n3, f), n3, (long long)n3 * nt), -1.0);
-      // Phi_b starts as -[R31a | 0]
-      cb.d[cb.count++] = copy(n3, n1, P, sub(Ra, dI3a, dI1), M(Phib, n3, (long long)n3 * nt), -1.0);
-      cb.d[cb.count++] = copy(n3, n2, P, mat(nullptr, 0, 0), M(elem(Phib, (long long)n1 * n3, f), n3, (long long)n3 * nt));
-      // R^tau starts as diag(R11a, R22b)
-      const long long sp = (long long)nt * nt;
-      cb.d[cb.count++] = copy(n1, n1, P, sub(Ra, dI1, dI1), M(Rp, nt, sp));
-      cb.d[cb.count++] = copy(n2, n2, P, sub(Rb, dI2, dI2), M(elem(Rp, (long long)n1 * nt + n1, f), nt, sp));
-      cb.d[cb.count++] = copy(n2, n1, P, mat(nullptr, 0, 0), M(elem(Rp, n1, f), nt, sp));
-      cb.d[cb.count++] = copy(n1, n2, P, mat(nullptr, 0, 0), M(elem(Rp, (long long)n1 * nt, f), nt, sp));
-      CK(hps::launch_copy(cb, st));
-
-      const long long s33 = (long long)n3 * n3, s3t = (long long)n3 * nt;
-      // W = I - R33b R33a (in scratch), then W^{-1} into its stored slot
-      GemmDesc g = gemm(n3, n3, n3, P, M(R33b, n3, s33), M(R33a, n3, s33), M(Wscr, n3, s33));
-      g.alpha = make_double2(-1.0, 0.0);
-      g.addI = 1;
-      g.cf32 = f;
-      if (int rc = run_gemm(&g, 1)) return rc;
-      const int lev = S.lev;  // the tallest tree's level numbering
-      if (r.gj.wide)
-        CK(hps::launch_gj_wide(Wscr, Winv, n3, P, r.gj.wide, wmeta, d_status, lev, f != 0, st));
-      else
-        CK(hps::launch_gj_inverse(Wscr, Winv, n3, P, wmeta, d_status, lev, r.gj.cs, r.gj.tglobal, f != 0, st));
-      // Q(:, :n1) = R33b R31a
-      g = gemm(n3, n1, n3, P, M(R33b, n3, s33), sub(Ra, dI3a, dI1), M(Q, n3, s3t));
-      g.cf32 = f;
-      if (int rc = run_gemm(&g, 1)) return rc;
-      // Phi_a = W^{-1} Q
-      g = gemm(n3, nt, n3, P, M(Winv, n3, s33), M(Q, n3, s3t), M(Phia, n3, s3t));
-      g.cf32 = f;
-      if (int rc = run_gemm(&g, 1)) return rc;
-      // Phi_b = -[R31a | 0] - R33a Phi_a
-      g = gemm(n3, nt, n3, P, M(R33a, n3, s33), M(Phia, n3, s3t), M(Phib, n3, s3t));
-      g.alpha = make_double2(-1.0, 0.0);
-      g.D = g.C;
-      g.beta = make_double2(1.0, 0.0);
-      g.cf32 = f;
-      if (int rc = run_gemm(&g, 1)) return rc;
-      // R^tau = diag(R11a, R22b) + diag(R13a, R23b) [Phi_a; Phi_b]
-      GemmDesc g2[2];
-      g2[0] = gemm(n1, nt, n3, P, M(R13a, n1, (long long)n1 * n3), M(Phia, n3, s3t), M(Rp, nt, sp));
-      g2[0].D = g2[0].C;
-      g2[0].beta = make_double2(1.0, 0.0);
-      g2[0].cf32 = f;
-      g2[1] = gemm(n2, nt, n3, P, M(R23b, n2, (long long)n2 * n3), M(Phib, n3, s3t), M(elem(Rp, n1, f), nt, sp));
-      g2[1].D = g2[1].C;
-      g2[1].beta = make_double2(1.0, 0.0);
-      g2[1].cf32 = f;
-      if (int rc = run_gemm(g2, 2)) return rc;
-      launches += 1 + gj_launches(n3, r.gj);  // the copy and W^{-1}
-    }
-    CK(cudaEventRecord(sh->ev[2 + j], st));
-  }
-  if (scratch) CK(cudaFreeAsync(scratch, st));
-  if (wmeta) CK(cudaFreeAsync(wmeta, st));
+  sh->compute = compute;
+  int launches = 0;
+  int rc = compute(st, true, launches);
+  if (rc != HPS_OK) return rc;
   sh->launches = launches;
   return HPS_OK;
 }
@@ -1514,6 +1515,50 @@ int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, vo
     hs[k]->info.build_launches = hs[k]->sh->launches;
     out[k] = hs[k];
   }
+  return HPS_OK;
+}
+
+int hps_rebuild(int nh, hps_handle *const *hs, const double *const *c, void *stream) {
+  if (nh < 1 || !hs || !c || !hs[0] || !hs[0]->sh) return HPS_EINVAL;
+  Shared *sh = hs[0]->sh;
+  {
+    std::lock_guard<std::mutex> lock(g_shared_mu);
+    if (sh->refs != (int)sh->order.size()) return HPS_EINVAL;  // a handle of the build was freed
+  }
+  if (nh != (int)sh->order.size() || !sh->compute) return HPS_EINVAL;
+  for (int k = 0; k < nh; k++) {
+    if (!hs[k] || hs[k]->sh != sh || !c[k]) return HPS_EINVAL;
+    for (int q = 0; q < k; q++)
+      if (hs[q] == hs[k]) return HPS_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int k = 0; k < nh; k++) {
+    const size_t cb = sizeof(double) * (size_t)hs[k]->plan.leaves * hs[k]->plan.ni;
+    CK(cudaMemcpyAsync(hs[k]->c_dev, c[k], cb, cudaMemcpyDefault, st));
+  }
+  CK(cudaMemsetAsync(hs[0]->d_status, 0, sizeof(unsigned int), st));
+  if (!sh->graph) {
+    // capture the build's device work once, on a stream of our own (the
+    // caller's may be the legacy stream, which cannot be captured)
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    int launches = 0, rc = HPS_OK;
+    cudaError_t err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (err == cudaSuccess) {
+      rc = sh->compute(cs, false, launches);
+      err = cudaStreamEndCapture(cs, &g);
+    }
+    if (err == cudaSuccess && rc == HPS_OK) err = cudaGraphInstantiate(&sh->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (rc != HPS_OK) return rc;
+    if (err != cudaSuccess) {
+      sh->graph = nullptr;
+      return cuda_fail(err);
+    }
+  }
+  CK(cudaGraphLaunch(sh->graph, st));
   return HPS_OK;
 }
 

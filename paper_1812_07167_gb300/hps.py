@@ -26,7 +26,7 @@ HPS_FP64 = 0
 HPS_MIXED = 1
 
 # every entry point include/hps.h declares
-EXPORTS = ("hps_nodes", "hps_build", "hps_build_batch", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
+EXPORTS = ("hps_nodes", "hps_build", "hps_build_batch", "hps_rebuild", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
            "hps_root_R", "hps_leaf_ops", "hps_zgemm", "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
 
 
@@ -78,6 +78,7 @@ def lib():
         L.hps_nodes.argtypes = [D, P, P]
         L.hps_build.argtypes = [D, P, P, ctypes.POINTER(ctypes.c_void_p)]
         L.hps_build_batch.argtypes = [ctypes.c_int, D, P, P, ctypes.POINTER(ctypes.c_void_p)]
+        L.hps_rebuild.argtypes = [ctypes.c_int, P, P, P]
         L.hps_solve.argtypes = [P, P, P, P, ctypes.c_int, P]
         L.hps_solve_noalloc.argtypes = [P, P, P, P, ctypes.c_int, P]
         L.hps_solve_batch.argtypes = [P, ctypes.c_int, P, P, P, P, P]
@@ -238,6 +239,16 @@ def hps_build_batch(problems, cs, stream=None) -> list:
     out = (ctypes.c_void_p * k)()
     _check(lib().hps_build_batch(k, descs, cp, _stream(stream), out), "hps_build_batch")
     return [Handle(out[i], problems[i]) for i in range(k)]
+
+
+def hps_rebuild(handles, cs, stream=None):
+    """New coefficients for every handle of one build (replayed as a CUDA graph
+    after the first call)."""
+    k = len(handles)
+    hp = (ctypes.c_void_p * max(k, 1))(*[h.ptr for h in handles])
+    cp = (ctypes.c_void_p * max(k, 1))(*[_ptr(c) for c in cs])
+    _check(lib().hps_rebuild(k, hp, cp, _stream(stream)), "hps_rebuild")
+    return handles
 
 
 def hps_solve(h: Handle, s, t, u, nrhs: int, stream=None):

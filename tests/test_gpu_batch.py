@@ -173,3 +173,35 @@ def test_batch_with_rectangular_members():
     with pytest.raises(hps.HPSError) as e:
         hps.hps_build_batch(bad, cb)
     assert e.value.code == hps.HPS_EINVAL
+
+
+@pytest.mark.parametrize("precision", [hps.HPS_FP64, hps.HPS_MIXED])
+def test_rebuild_replays_the_build_as_a_graph(precision):
+    """hps_rebuild with new coefficients gives the operators of a fresh build
+    with those coefficients (first call captures the graph, later ones
+    replay it), for a single build and for a batch."""
+    st = torch.cuda.current_stream()
+    probs = [hps.Problem(4, 10, 14.0, 14.0, precision=precision), hps.Problem(8, 10, 20.0, 20.0, precision=precision),
+             hps.Problem(2, 10, 9.0, 9.0, precision=precision)]
+    c0 = [W.random_data(pr.m, 10, pr.kappa, pr.kappa, seed=60 + k)[0] for k, pr in enumerate(probs)]
+    hb = hps.hps_build_batch(probs, c0, st)
+    for rnd in range(3):
+        cn = [W.random_data(pr.m, 10, pr.kappa, pr.kappa, seed=70 + 10 * rnd + k)[0] for k, pr in enumerate(probs)]
+        # the handles in another order than they were built in
+        perm = [2, 0, 1]
+        hps.hps_rebuild([hb[i] for i in perm], [torch.from_numpy(cn[i]).cuda() for i in perm], st)
+        assert hps.hps_status(hb[0], st)[0] == hps.HPS_OK
+        for k, pr in enumerate(probs):
+            ha = hps.hps_build(pr, cn[k], st)
+            _, s, t = W.random_data(pr.m, 10, pr.kappa, pr.kappa, seed=5 + k, nrhs=2)
+            tol = 1e-12 if precision == hps.HPS_FP64 else 1e-9
+            assert _rel(_solve(hb[k], s, t), _solve(ha, s, t)) < tol, (rnd, k)
+            ha.free()
+    L = hps.lib()
+    arr = (__import__("ctypes").c_void_p * 1)(hb[0].ptr)
+    carr = (__import__("ctypes").c_void_p * 1)(torch.from_numpy(c0[0]).cuda().data_ptr())
+    assert L.hps_rebuild(1, arr, carr, None) == hps.HPS_EINVAL  # not all handles of the batch
+    hb[1].free()
+    assert L.hps_rebuild(1, arr, carr, None) == hps.HPS_EINVAL
+    for h in (hb[0], hb[2]):
+        h.free()
