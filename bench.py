@@ -186,6 +186,11 @@ def ours(args, rank, world, local_rank):
         hps.hps_solve(h, sd, td, ud, 1, st)
         return h
 
+    # measured kernel choices for this problem's shapes (kept for the process)
+    t_tune = time.perf_counter()
+    tuned_shapes = hps.hps_tune([pr], st)
+    tune_s = time.perf_counter() - t_tune
+
     for _ in range(max(args.warmup, 3)):
         h = step()
         torch.cuda.synchronize()
@@ -353,6 +358,9 @@ def ours(args, rank, world, local_rank):
                              "nrhs": 1, "samples": len(lat),
                              "what": "wall clock of hps_solve + stream sync, device-resident s, t, u"},
         "operator_bytes": info.operator_bytes, "build_flops": info.build_flops,
+        "tuning": {"shapes": tuned_shapes, "seconds": tune_s,
+                   "what": "hps_tune: measured tile / tensor-core choice per merge product shape and "
+                           "cluster / panel regime per interface-inverse shape, before the timed steps"},
         "roofline": {"kernel": "leaf_kernel", "bound": "alu", "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": traffic, "leaf_ms": leaf_avg,
@@ -411,6 +419,9 @@ def batching(dev, st, flush, reps=2):
     for name, prec in (("fp64", hps.HPS_FP64), ("mixed", hps.HPS_MIXED)):
         probs = [hps.Problem(m, P_ORDER, kap, kap, precision=prec) for m, kap, _ in spec]
         res = {}
+        # measured kernel choices for the batch's shapes and for each size alone
+        res["tuned_shapes"] = hps.hps_tune(probs, st) + sum(
+            hps.hps_tune([hps.Problem(m, P_ORDER, 50.0, 50.0, precision=prec)], st) for m in sorted({m for m, _, _ in spec}))
         for mode in ("batched", "separate"):
             ms = []
             for rep in range(reps + 1):
@@ -493,6 +504,7 @@ def precision(args, local_rank):
     with ClockSampler(local_rank) as clk:
         for name, prec in (("fp64", hps.HPS_FP64), ("mixed", hps.HPS_MIXED)):
             q = hps.Problem(m, p, kappa, kappa, precision=prec)
+            tuned = hps.hps_tune([q], st)
             bms = []
             for rep in range(4):
                 flush.zero_()
@@ -523,6 +535,7 @@ def precision(args, local_rank):
                          "build_dof_per_s": dof / (statistics.median(bms) / 1e3),
                          "solve_ms_1rhs": statistics.median(sms), "solve_rhs_per_s": 1e3 / statistics.median(sms),
                          "operator_bytes": info.operator_bytes, "build_launches": info.build_launches,
+                         "tuned_shapes": tuned,
                          "leaf_and_level_ms": [float(x) for x in hps.hps_build_times(h)]}
             h.free()
     out["clocks"] = clk.summary()

@@ -271,6 +271,21 @@ int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, v
 int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, double *C, int emulated,
               void *stream);
 
+/* Measure, on this GPU, the kernel choices the builds of these problems would
+ * make, and keep the fastest for every later build in this process: for each
+ * merge product shape (M, N, K, parents, precision) the tile configuration
+ * or the tensor-core product, for each interface-inverse shape (n3, parents,
+ * precision) the cluster size or the panel-per-launch regime.  This is the
+ * GPU form of the paper's calibration of representative actions (Sec. 3,
+ * Table 1, which times a leaf inverse, an interface inverse and a product
+ * per level and thread count).  Shapes measured before are skipped.
+ *   descs: as for hps_build_batch (the same p, precision, fp64_levels and
+ *          fp64_native); their shapes are measured on scratch data.
+ *   ntuned: optional, receives the number of shapes measured.
+ * Synchronizes the stream.  Returns HPS_EINVAL, HPS_ENOTSUP, HPS_ENOMEM,
+ * HPS_ECUDA. */
+int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned);
+
 /* Sizes and operation counts of the solver hps_build would create for desc,
  * without building it (host only, no device work): the admission check of a
  * request loop.  Same HPS_EINVAL / HPS_ENOTSUP results as hps_build. */

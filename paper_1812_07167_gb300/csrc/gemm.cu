@@ -320,6 +320,13 @@ cudaError_t launch_typed(const GemmPack &pk, int maxN, cudaStream_t st) {
   if (maxN <= 2) return launch_gemv<C, 2>(pk, st);
   if (maxN <= 4) return launch_gemv<C, 4>(pk, st);
   if (maxN <= 8) return launch_gemv<C, 8>(pk, st);
+  switch (pk.d[0].cfg) {  // a measured choice (hps_tune)
+    case 1: return launch_cfg<C, 64, 64, 16, 4, 4>(pk, st);
+    case 2: return launch_cfg<C, 32, 32, 16, 2, 2>(pk, st);
+    case 3: return launch_cfg<C, 16, 16, 16, 1, 1>(pk, st);
+    case 4: return launch_cfg<C, 64, 16, 16, 2, 2>(pk, st);
+    default: break;
+  }
   if (maxN < 32) return launch_cfg<C, 64, 16, 16, 2, 2>(pk, st);
   // the largest tile that still gives every SM two CTAs
   const long long want = 2 * 152;

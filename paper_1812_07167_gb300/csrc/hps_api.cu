@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <functional>
+#include <map>
 #include <mutex>
 #include <cmath>
 #include <cstdint>
@@ -446,6 +447,34 @@ int choose_gj_cs(int n, int batch, bool tglobal, int f32) {
   return cs;
 }
 
+// Measured kernel choices (hps_tune), the GPU form of the paper's
+// calibration of representative actions (Sec. 3, Table 1): per product shape
+// the tile configuration or the tensor-core product, per interface-inverse
+// shape the cluster size or the panel-per-launch regime.  Shapes not in the
+// table take the rules below.  Process-wide.
+struct TuneKey {
+  int kind;  // 0: product (M, N, K, batch, f32), 1: interface inverse (n3, P, f32)
+  int M, N, K, batch, f32;
+  bool operator<(const TuneKey &o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (M != o.M) return M < o.M;
+    if (N != o.N) return N < o.N;
+    if (K != o.K) return K < o.K;
+    if (batch != o.batch) return batch < o.batch;
+    return f32 < o.f32;
+  }
+};
+std::map<TuneKey, int> g_tune;  // product: 1..4 tile, 5 tensor cores; inverse: cs > 0, or -G (wide)
+std::mutex g_tune_mu;
+
+bool tuned(const TuneKey &k, int &v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  v = it->second;
+  return true;
+}
+
 // Kernel regime of the interface inverses of one launch: P matrices n3 x n3.
 struct GJChoice {
   int cs = 1;            // cluster size of the cluster kernel
@@ -453,8 +482,30 @@ struct GJChoice {
   int wide = 0;          // > 0: one launch per panel over P * wide CTAs instead
 };
 
+bool choose_gj_rule(int n3, long long P, int f32, GJChoice &g);
+
 // false when no regime fits this build's shared memory
 bool choose_gj(int n3, long long P, int f32, GJChoice &g) {
+  int v;
+  if (P <= (1 << 30) && tuned(TuneKey{1, n3, 0, 0, (int)P, f32}, v)) {
+    GJChoice t;
+    t.tglobal = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, f32) > 200 * 1024;
+    if (v > 0) {
+      t.cs = v;
+      if (hps::gj_smem_bytes(n3, t.cs, false, 0, t.tglobal, f32) <= 227 * 1024) {
+        g = t;
+        return true;
+      }
+    } else if (v < 0) {
+      t.wide = -v;
+      g = t;
+      return true;
+    }
+  }
+  return choose_gj_rule(n3, P, f32, g);
+}
+
+bool choose_gj_rule(int n3, long long P, int f32, GJChoice &g) {
   // stage the panels in shared memory while they fit beside the rest
   g.tglobal = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, f32) > 200 * 1024;
   g.cs = choose_gj_cs(n3, (int)std::min<long long>(P, 1 << 30), g.tglobal, f32);
@@ -478,6 +529,8 @@ int gj_launches(int n3, const GJChoice &g) { return g.wide ? (n3 + 7) / 8 + 2 : 
 // Does a product of this shape go to the tensor cores (Ozaki scheme)?
 bool oz_shape(int M, int N, int K, int batch, int f32, bool oz) {
   if (!oz || f32) return false;
+  int v;
+  if (tuned(TuneKey{0, M, N, K, batch, f32}, v)) return v == 5;
   GemmDesc g;
   memset(&g, 0, sizeof(g));
   g.M = M;
@@ -905,6 +958,46 @@ static std::vector<ChildPiece> child_pieces(const std::vector<std::vector<BuildR
   return out;
 }
 
+// Runs of every merge level of the handles hs (build order) and each
+// problem's first parent on each of its levels, with the kernel regime of
+// every run's interface inverses.
+static int plan_runs(const std::vector<hps_handle *> &hs, std::vector<std::vector<BuildRun>> &runs,
+                     std::vector<std::vector<long long>> &first) {
+  const int K = (int)hs.size();
+  const Plan &P0 = hs[0]->plan;
+  const int Lmax = P0.L;
+  runs.assign(Lmax, {});
+  first.assign(K, {});
+  for (int j = 0; j < Lmax; j++) {
+    long long pos = 0;
+    for (int k = 0; k < K && hs[k]->plan.L > j; k++) {
+      const Level &Lk = hs[k]->plan.lv[j];
+      const bool fin = (hs[k]->plan.L == j + 1);
+      std::vector<BuildRun> &R = runs[j];
+      if (!R.empty() && R.back().f32 == Lk.f32 && R.back().finishing == fin) {
+        R.back().P += Lk.P;
+        R.back().nk++;
+      } else {
+        BuildRun r{};
+        r.p0 = pos;
+        r.P = Lk.P;
+        r.f32 = Lk.f32;
+        r.finishing = fin;
+        r.k0 = k;
+        r.nk = 1;
+        R.push_back(r);
+      }
+      first[k].push_back(pos);
+      pos += Lk.P;
+    }
+    for (BuildRun &r : runs[j]) {
+      if (r.finishing && r.f32) return HPS_ENOTSUP;  // roots are complex128
+      if (!choose_gj(P0.lv[j].n3, r.P, r.f32, r.gj)) return HPS_ENOTSUP;
+    }
+  }
+  return HPS_OK;
+}
+
 // Algorithm 1 for every handle of hs at once.  hs is in build order: tallest
 // tree first, all with the same p, precision and top-level count; each has
 // its plan.  Leaves of all problems are numbered problem after problem and
@@ -939,34 +1032,11 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     }
 
   // ---- runs of every merge level, and each problem's first parent there ----
-  std::vector<std::vector<BuildRun>> runs(Lmax);
-  std::vector<std::vector<long long>> first(K);
-  for (int j = 0; j < Lmax; j++) {
-    long long pos = 0;
-    for (int k = 0; k < K && hs[k]->plan.L > j; k++) {
-      const Level &Lk = hs[k]->plan.lv[j];
-      const bool fin = (hs[k]->plan.L == j + 1);
-      std::vector<BuildRun> &R = runs[j];
-      if (!R.empty() && R.back().f32 == Lk.f32 && R.back().finishing == fin) {
-        R.back().P += Lk.P;
-        R.back().nk++;
-      } else {
-        BuildRun r{};
-        r.p0 = pos;
-        r.P = Lk.P;
-        r.f32 = Lk.f32;
-        r.finishing = fin;
-        r.k0 = k;
-        r.nk = 1;
-        R.push_back(r);
-      }
-      first[k].push_back(pos);
-      pos += Lk.P;
-    }
-    for (BuildRun &r : runs[j]) {
-      if (r.finishing && r.f32) return HPS_ENOTSUP;  // roots are complex128
-      if (!choose_gj(P0.lv[j].n3, r.P, r.f32, r.gj)) return HPS_ENOTSUP;
-    }
+  std::vector<std::vector<BuildRun>> runs;
+  std::vector<std::vector<long long>> first;
+  {
+    int rc = plan_runs(hs, runs, first);
+    if (rc != HPS_OK) return rc;
   }
 
   // ---- one arena: leaf operators, merge operators, roots, tables, maps ----
@@ -1226,7 +1296,10 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
       GemmDesc rest[2];
       int nr = 0;
       for (int q = 0; q < nd; q++) {
-        if (P0.oz && hps::oz_eligible(gd[q])) {
+        int v;
+        if (tuned(TuneKey{0, gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32}, v) && v >= 1 && v <= 4)
+          gd[q].cfg = v;
+        if (oz_shape(gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32, P0.oz)) {
           CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, st));
           launches += hps::oz_launches(gd[q]);
         } else {
@@ -1515,6 +1588,204 @@ int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, vo
     hs[k]->info.build_launches = hs[k]->sh->launches;
     out[k] = hs[k];
   }
+  return HPS_OK;
+}
+
+namespace {
+// Seeded, well-scaled complex values for the tuning runs (timing does not
+// depend on them; the inverse's row swaps do, so they are not diagonal).
+__global__ void tune_fill_kernel(void *p, long long count, int n, int f32) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= count) return;
+  unsigned long long z = (unsigned long long)id * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;
+  const double re = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  const double im = (double)((z * 0x94D049BB133111EBull) >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  const long long r = n > 0 ? id % ((long long)n * n) : 1;
+  const double d = (n > 0 && r % n == r / n) ? 2.0 : 0.0;  // a moderate diagonal
+  if (f32)
+    ((float2 *)p)[id] = make_float2((float)(re + d), (float)im);
+  else
+    ((double2 *)p)[id] = make_double2(re + d, im);
+}
+}  // namespace
+
+int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned) {
+  if (nprob < 1 || !descs) return HPS_EINVAL;
+  for (int k = 0; k < nprob; k++) {
+    int st0 = check_desc(&descs[k]);
+    if (st0) return st0;
+    if (descs[k].p != descs[0].p || descs[k].precision != descs[0].precision ||
+        descs[k].fp64_levels != descs[0].fp64_levels || descs[k].fp64_native != descs[0].fp64_native)
+      return HPS_EINVAL;
+  }
+  std::vector<hps_handle> hv(nprob);
+  std::vector<hps_handle *> hs(nprob);
+  for (int k = 0; k < nprob; k++) {
+    int st = plan_handle(&hv[k], &descs[k]);
+    if (st != HPS_OK) return st;
+    hs[k] = &hv[k];
+  }
+  std::stable_sort(hs.begin(), hs.end(), [](hps_handle *a, hps_handle *b) { return a->plan.L > b->plan.L; });
+  const Plan &P0 = hs[0]->plan;
+  for (int k = 1; k < nprob; k++)
+    for (int j = 0; j < hs[k]->plan.L; j++) {
+      const Level &A = P0.lv[j], &B = hs[k]->plan.lv[j];
+      if (A.horizontal != B.horizontal || A.nc != B.nc || A.n3 != B.n3) return HPS_EINVAL;
+    }
+  std::vector<std::vector<BuildRun>> runs;
+  std::vector<std::vector<long long>> first;
+  int rc = plan_runs(hs, runs, first);
+  if (rc != HPS_OK) return rc;
+  // the shapes the build would launch
+  std::map<TuneKey, int> todo;
+  size_t amax = 1, bmax = 1, cmax = 1, smax = 1, mmax = 1;
+  for (int j = 0; j < P0.L; j++) {
+    const Level &S = P0.lv[j];
+    int mnk[6][3];
+    merge_products(S.n1, S.n2, S.n3, S.nt, mnk);
+    for (const BuildRun &r : runs[j]) {
+      for (int q = 0; q < 6; q++) {
+        if (mnk[q][1] <= 8) continue;  // the skinny kernel has no choice to make
+        todo[TuneKey{0, mnk[q][0], mnk[q][1], mnk[q][2], r.P, r.f32}] = 0;
+        amax = std::max(amax, (size_t)mnk[q][0] * mnk[q][2] * r.P);
+        bmax = std::max(bmax, (size_t)mnk[q][2] * mnk[q][1] * r.P);
+        cmax = std::max(cmax, (size_t)mnk[q][0] * mnk[q][1] * r.P);
+      }
+      todo[TuneKey{1, S.n3, 0, 0, r.P, r.f32}] = 0;
+      smax = std::max(smax, (size_t)S.n3 * S.n3 * r.P);
+      mmax = std::max(mmax, (size_t)hps::gj_meta_ints(S.n3) * r.P);
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto it = todo.begin(); it != todo.end();) it = g_tune.count(it->first) ? todo.erase(it) : std::next(it);
+  }
+  if (ntuned) *ntuned = 0;
+  if (todo.empty()) return HPS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  char *buf = nullptr;
+  const size_t oA = 0, oB = align256(16 * amax), oC = oB + align256(16 * bmax), oS = oC + align256(16 * cmax);
+  const size_t oM = oS + align256(16 * smax), oSt = oM + align256(4 * mmax), total = oSt + 256;
+  CK(cudaMalloc((void **)&buf, total));
+  void *ozws = nullptr;
+  size_t ozb = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ozws) cudaFree(ozws);
+    cudaFree(buf);
+  };
+  auto fail = [&](cudaError_t err) {
+    cleanup();
+    return cuda_fail(err);
+  };
+  cudaError_t err;
+  if ((err = cudaEventCreate(&e0)) != cudaSuccess || (err = cudaEventCreate(&e1)) != cudaSuccess) return fail(err);
+  auto fill = [&](size_t off, size_t count, int n, int f32) {
+    tune_fill_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(buf + off, (long long)count, n, f32);
+    return cudaGetLastError();
+  };
+  // device milliseconds of one call of f after one warm-up call (refill runs
+  // before each call, outside the timed region)
+  auto time_it = [&](auto &&f, auto &&refill, int reps) -> float {
+    if (refill() != cudaSuccess || f() != cudaSuccess) {
+      cudaGetLastError();
+      return -1.0f;
+    }
+    float best = 1e30f;
+    for (int r = 0; r < reps; r++) {
+      if (refill() != cudaSuccess) return -1.0f;
+      cudaEventRecord(e0, st);
+      if (f() != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0f;
+      }
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0f;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    return best;
+  };
+  int count = 0;
+  for (auto &kv : todo) {
+    const TuneKey &k = kv.first;
+    int best = 0;
+    float best_ms = 1e30f;
+    if (k.kind == 0) {
+      if ((err = fill(oA, (size_t)k.M * k.K * k.batch, 0, k.f32)) != cudaSuccess ||
+          (err = fill(oB, (size_t)k.K * k.N * k.batch, 0, k.f32)) != cudaSuccess)
+        return fail(err);
+      GemmDesc g = gemm(k.M, k.N, k.K, k.batch, mat(buf + oA, k.M, (long long)k.M * k.K, nullptr, nullptr, k.f32),
+                        mat(buf + oB, k.K, (long long)k.K * k.N, nullptr, nullptr, k.f32),
+                        mat(buf + oC, k.M, (long long)k.M * k.N, nullptr, nullptr, k.f32));
+      g.cf32 = k.f32;
+      auto none = [&]() { return cudaSuccess; };
+      for (int cand = 1; cand <= 5; cand++) {
+        if (cand == 5 && (k.f32 || !P0.oz || k.K < 32 || k.batch > 65535)) continue;
+        float ms;
+        if (cand == 5) {
+          const size_t need = hps::oz_workspace_bytes(g);
+          if (need > ozb) {
+            if (ozws) cudaFree(ozws);
+            ozws = nullptr;
+            ozb = 0;
+            if (cudaMalloc(&ozws, need) != cudaSuccess) {
+              cudaGetLastError();
+              continue;
+            }
+            ozb = need;
+          }
+          ms = time_it([&]() { return hps::launch_gemm_oz(g, ozws, ozb, st); }, none, 3);
+        } else {
+          GemmDesc gc = g;
+          gc.cfg = cand;
+          ms = time_it([&]() { return hps::launch_gemm(&gc, 1, st); }, none, 3);
+        }
+        if (ms >= 0.0f && ms < best_ms) {
+          best_ms = ms;
+          best = cand;
+        }
+      }
+    } else {
+      const int n3 = k.M, P = k.batch;
+      GJChoice rule;
+      if (!choose_gj_rule(n3, P, k.f32, rule)) continue;
+      const bool tg = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, k.f32) > 200 * 1024;
+      std::vector<int> cands;
+      for (int cs = 1; cs <= hps::gj_max_cluster(); cs *= 2)
+        // every CTA of the cluster owns at least one panel
+        if (hps::gj_smem_bytes(n3, cs, false, 0, tg, k.f32) <= 227 * 1024 && (cs - 1) * hps::gj_slab(n3, cs) < n3)
+          cands.push_back(cs);
+      if (n3 >= 64) {
+        const int G0 = rule.wide ? rule.wide : (int)std::max<long long>(2, std::min<long long>((2 * 152 + P - 1) / P, n3 / 4 + 1));
+        cands.push_back(-G0);
+        if (G0 / 2 >= 2) cands.push_back(-(G0 / 2));
+      }
+      auto refill = [&]() { return fill(oS, (size_t)n3 * n3 * P, n3, k.f32); };
+      for (int v : cands) {
+        float ms;
+        if (v > 0)
+          ms = time_it([&]() { return hps::launch_gj_inverse(buf + oS, buf + oC, n3, P, (int *)(buf + oM), (unsigned *)(buf + oSt), 0, v, tg, k.f32 != 0, st); }, refill, 2);
+        else
+          ms = time_it([&]() { return hps::launch_gj_wide(buf + oS, buf + oC, n3, P, -v, (int *)(buf + oM), (unsigned *)(buf + oSt), 0, k.f32 != 0, st); }, refill, 2);
+        if (ms >= 0.0f && ms < best_ms) {
+          best_ms = ms;
+          best = v;
+        }
+      }
+    }
+    if (best != 0) {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune[k] = best;
+      count++;
+    }
+  }
+  cleanup();
+  if (ntuned) *ntuned = count;
   return HPS_OK;
 }
 

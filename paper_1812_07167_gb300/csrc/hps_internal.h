@@ -32,6 +32,7 @@ struct GemmDesc {
   double2 alpha, beta;
   int addI;
   int cf32;
+  int cfg;  // tile configuration for N > 8: 0 = by rule, 1..4 = 64x64, 32x32, 16x16, 64x16
 };
 
 // One batched mapped copy:  dst(i, j) = alpha * src(i, j) for i < M, j < N

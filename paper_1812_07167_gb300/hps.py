@@ -27,7 +27,7 @@ HPS_MIXED = 1
 
 # every entry point include/hps.h declares
 EXPORTS = ("hps_nodes", "hps_build", "hps_build_batch", "hps_rebuild", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
-           "hps_root_R", "hps_leaf_ops", "hps_zgemm", "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
+           "hps_root_R", "hps_leaf_ops", "hps_zgemm", "hps_tune", "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
 
 
 class hps_desc(ctypes.Structure):
@@ -79,6 +79,7 @@ def lib():
         L.hps_build.argtypes = [D, P, P, ctypes.POINTER(ctypes.c_void_p)]
         L.hps_build_batch.argtypes = [ctypes.c_int, D, P, P, ctypes.POINTER(ctypes.c_void_p)]
         L.hps_rebuild.argtypes = [ctypes.c_int, P, P, P]
+        L.hps_tune.argtypes = [ctypes.c_int, D, P, ctypes.POINTER(ctypes.c_int)]
         L.hps_solve.argtypes = [P, P, P, P, ctypes.c_int, P]
         L.hps_solve_noalloc.argtypes = [P, P, P, P, ctypes.c_int, P]
         L.hps_solve_batch.argtypes = [P, ctypes.c_int, P, P, P, P, P]
@@ -239,6 +240,16 @@ def hps_build_batch(problems, cs, stream=None) -> list:
     out = (ctypes.c_void_p * k)()
     _check(lib().hps_build_batch(k, descs, cp, _stream(stream), out), "hps_build_batch")
     return [Handle(out[i], problems[i]) for i in range(k)]
+
+
+def hps_tune(problems, stream=None) -> int:
+    """Measure the kernel choices of these problems' builds (kept for the
+    process); returns the number of shapes measured."""
+    k = len(problems)
+    descs = (hps_desc * max(k, 1))(*[pr.desc() for pr in problems])
+    n = ctypes.c_int(0)
+    _check(lib().hps_tune(k, descs, _stream(stream), ctypes.byref(n)), "hps_tune")
+    return n.value
 
 
 def hps_rebuild(handles, cs, stream=None):

@@ -205,3 +205,30 @@ def test_rebuild_replays_the_build_as_a_graph(precision):
     assert L.hps_rebuild(1, arr, carr, None) == hps.HPS_EINVAL
     for h in (hb[0], hb[2]):
         h.free()
+
+
+def test_tuned_choices_keep_results_and_launch_counts():
+    """hps_tune measures the kernel choices of a ragged batch; builds after it
+    use them, with the same results (1e-12) and a planned launch count that
+    still equals the launches made."""
+    probs = [hps.Problem(16, 12, 30.0, 30.0), hps.Problem(8, 12, 20.0, 20.0), hps.Problem(4, 12, 9.0, 9.0)]
+    cs = [W.random_data(pr.m, 12, pr.kappa, pr.kappa, seed=90 + k)[0] for k, pr in enumerate(probs)]
+    st = torch.cuda.current_stream()
+    before = []
+    for pr, c in zip(probs, cs):
+        h = hps.hps_build(pr, c, st)
+        _, s, t = W.random_data(pr.m, 12, pr.kappa, pr.kappa, seed=3, nrhs=2)
+        before.append(_solve(h, s, t))
+        h.free()
+    n = hps.hps_tune(probs, st)
+    assert n > 0
+    assert hps.hps_tune(probs, st) == 0  # measured shapes are kept
+    for k, (pr, c) in enumerate(zip(probs, cs)):
+        h = hps.hps_build(pr, c, st)
+        _, s, t = W.random_data(pr.m, 12, pr.kappa, pr.kappa, seed=3, nrhs=2)
+        assert _rel(_solve(h, s, t), before[k]) < 1e-12
+        assert h.info().build_launches == hps.hps_plan(pr).build_launches
+        h.free()
+    hb = _check_against_alone(probs, cs, 1e-12)
+    for h in hb:
+        h.free()
