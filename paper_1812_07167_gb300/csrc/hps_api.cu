@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <functional>
 #include <map>
 #include <mutex>
@@ -568,7 +569,7 @@ void merge_products(int n1, int n2, int n3, int nt, int (&mnk)[6][3]) {
 }
 
 // Kernel launches of one merge run: the copy, W^{-1}, and the products (an
-// emulated product is three or four launches; the two halves of R^tau share one
+// emulated product is four or five launches; the two halves of R^tau share one
 // launch when both run on the FP64 pipes).
 int merge_launches(int n1, int n2, int n3, int nt, int P, int f32, bool oz, const GJChoice &gj) {
   int mnk[6][3];
@@ -609,9 +610,28 @@ struct SolveWs {
   size_t ov = 0, bytes = 0;
   // refinement (HPS_MIXED): residual parts and the correction
   size_t osd = 0, otd = 0, ofu = 0, ogu = 0, oja = 0, ojb = 0, od = 0;
+  // products on the tensor cores (wide right-hand-side blocks): digit planes
+  size_t ooz = 0, oz_bytes = 0;
 };
 
-static void solve_ws_layout(const Plan &pl, int R, SolveWs &w) {
+// The complex128 products of a solve with R right-hand sides (M, K, batch),
+// Algorithm 2's leaf and level actions.
+static void solve_products(const Plan &pl, std::vector<std::array<int, 3>> &out) {
+  out.clear();
+  if (!pl.leaf_f32) {
+    out.push_back({pl.nb, pl.ni, pl.leaves});
+    out.push_back({pl.n, pl.n, pl.leaves});
+  }
+  for (const Level &L : pl.lv) {
+    if (L.f32) continue;
+    out.push_back({L.n3, L.n3, L.P});
+    out.push_back({L.n1, L.n3, L.P});
+    out.push_back({L.n2, L.n3, L.P});
+    out.push_back({L.n3, L.nt, L.P});
+  }
+}
+
+static void solve_ws_layout(const Plan &pl, int R, SolveWs &w, bool allow_oz = true) {
   size_t off = 0;
   auto take = [&](long long count) {
     size_t o = off;
@@ -639,7 +659,58 @@ static void solve_ws_layout(const Plan &pl, int R, SolveWs &w) {
     w.ojb = take((long long)R * std::max(1LL, pl.total_pairs));
     w.od = take((long long)R * pl.leaves * pl.n);
   }
+  // room for the tensor-core digit planes of the largest eligible product,
+  // in batch chunks of at most 512 MiB (a chunk of one matrix at least)
+  w.oz_bytes = 0;
+  if (allow_oz && pl.oz && R >= 32) {
+    std::vector<std::array<int, 3>> pr;
+    solve_products(pl, pr);
+    for (const auto &q : pr)
+      if (oz_shape(q[0], R, q[1], q[2], 0, true)) {
+        const size_t one = oz_bytes_shape(q[0], R, q[1], 1), all = oz_bytes_shape(q[0], R, q[1], q[2]);
+        w.oz_bytes = std::max(w.oz_bytes, std::max(one, std::min(all, (size_t)512 << 20)));
+      }
+    if (w.oz_bytes) {
+      w.ooz = off;
+      off = align256(off + w.oz_bytes);
+    }
+  }
   w.bytes = off;
+}
+
+// Products of a solve: complex128 ones wide enough for the tensor cores run
+// there, the batch cut into chunks whose digit planes fit the workspace's
+// region; the rest in one launch.
+static int solve_gemm(GemmDesc *gd, int nd, cudaStream_t st, char *wb, const SolveWs &ws, bool oz) {
+  GemmDesc rest[2];
+  int nr = 0;
+  for (int q = 0; q < nd; q++) {
+    GemmDesc &g = gd[q];
+    if (oz && ws.oz_bytes && oz_shape(g.M, g.N, g.K, g.batch, g.cf32, true)) {
+      int chunk = g.batch;
+      while (chunk > 1 && oz_bytes_shape(g.M, g.N, g.K, chunk) > ws.oz_bytes) chunk = (chunk + 1) / 2;
+      if (oz_bytes_shape(g.M, g.N, g.K, chunk) <= ws.oz_bytes) {
+        auto shift = [](Mat m, long long b) {
+          if (m.ptr) m.ptr = elem(m.ptr, b * m.stride, m.f32);
+          return m;
+        };
+        for (int b0 = 0; b0 < g.batch; b0 += chunk) {
+          GemmDesc c = g;
+          c.batch = std::min(chunk, g.batch - b0);
+          c.A = shift(g.A, b0);
+          c.B = shift(g.B, b0);
+          c.B2 = shift(g.B2, b0);
+          c.C = shift(g.C, b0);
+          c.D = shift(g.D, b0);
+          CK(hps::launch_gemm_oz(c, wb + ws.ooz, ws.oz_bytes, st));
+        }
+        continue;
+      }
+    }
+    rest[nr++] = g;
+  }
+  if (nr) CK(hps::launch_gemm(rest, nr, st));
+  return HPS_OK;
 }
 
 // Algorithm 2 for R right-hand sides on device arrays s, t, u, with the
@@ -665,7 +736,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
   GemmDesc g = gemm(nb, R, ni, nl, F(elem(h->GX, (long long)nb * nb, lf), nb, (long long)n * nb, lf),
                     mat(s, (long long)nl * ni, ni), mat(W(oh[0]), (long long)nl * nb, nb));
   g.cf32 = lf;
-  CK(hps::launch_gemm(&g, 1, st));
+  if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
   for (size_t j = 0; j < pl.lv.size(); j++) {
     const Level &L = pl.lv[j];
     const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc, f = L.f32;
@@ -693,17 +764,17 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     g.D = h3b;
     g.beta = make_double2(-1.0, 0.0);
     g.cf32 = f;
-    CK(hps::launch_gemm(&g, 1, st));
+    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
     g = gemm(n3, R, n3, P, F(L.Winv, n3, s33, f), mat(v, ldv, n3), mat(ta, ldv, n3));
     g.cf32 = f;
-    CK(hps::launch_gemm(&g, 1, st));
+    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
     // t~3b = -h3a - R33a t~3a  (Upsilon_b [h3a; h3b])
     g = gemm(n3, R, n3, P, F(L.R33a, n3, s33, f), mat(ta, ldv, n3), mat(tb, ldv, n3));
     g.alpha = make_double2(-1.0, 0.0);
     g.D = h3a;
     g.beta = make_double2(-1.0, 0.0);
     g.cf32 = f;
-    CK(hps::launch_gemm(&g, 1, st));
+    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
     // h^tau = [h1a + R13a t~3a ; h2b + R23b t~3b]  (Eq. flux_part)
     const long long ldp = (long long)P * nt;
     GemmDesc g2[2];
@@ -716,7 +787,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     g2[1].D = h2b;
     g2[1].beta = make_double2(1.0, 0.0);
     g2[1].cf32 = f;
-    CK(hps::launch_gemm(g2, 2, st));
+    if (int rc = solve_gemm(g2, 2, st, wb, ws, pl.oz)) return rc;
   }
 
   // ---- downward pass ----
@@ -746,7 +817,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     g2[1].D = mat(W(otb[jj]), ldv, n3);
     g2[1].beta = make_double2(1.0, 0.0);
     g2[1].cf32 = f;
-    CK(hps::launch_gemm(g2, 2, st));
+    if (int rc = solve_gemm(g2, 2, st, wb, ws, pl.oz)) return rc;
     // the rest of the children's incoming data is the parent's: I1 and I2
     CopyBatch cb;
     cb.count = 2;
@@ -760,7 +831,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
   g.B2 = mat(s, (long long)nl * ni, ni);
   g.ksplit = nb;
   g.cf32 = lf;
-  CK(hps::launch_gemm(&g, 1, st));
+  if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
 
   return HPS_OK;
 }
@@ -1979,7 +2050,7 @@ int hps_solve_noalloc(hps_handle *h, const double *s_, const double *t_, double 
   if (!is_device_ptr(s_) || !is_device_ptr(t_) || !is_device_ptr(u_)) return HPS_EINVAL;
   if (h->plan.mixed) return HPS_ENOTSUP;  // refinement needs more workspace than the fixed array
   SolveWs ws;
-  solve_ws_layout(h->plan, nrhs, ws);
+  solve_ws_layout(h->plan, nrhs, ws, false);  // no digit planes: products stay on the FP64 pipes
   if (ws.bytes > (size_t)HPS_NOALLOC_WORKSPACE_BYTES) return HPS_ETOOBIG;
   char *wb = nullptr;
   int st = noalloc_ws_ptr(&wb);

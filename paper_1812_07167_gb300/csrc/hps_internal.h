@@ -80,8 +80,8 @@ cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st);
 // Complex128 GEMM emulated on the bf16 tensor cores (Ozaki scheme, 9 slices
 // of 6 bits per operand; accuracy ~2^-54 max|A_i.| max|B_.j| per term).  Same
 // semantics as launch_gemm for one descriptor with cf32 == 0; needs a
-// device workspace of oz_workspace_bytes(g).  oz_launches(g) launches (3, or
-// 4 when the slice pairs are split over several CTAs a tile).
+// device workspace of oz_workspace_bytes(g).  oz_launches(g) launches (4, or
+// 5 when the slice pairs are split over several CTAs a tile).
 bool oz_eligible(const GemmDesc &g);
 int oz_launches(const GemmDesc &g);
 size_t oz_workspace_bytes(const GemmDesc &g);

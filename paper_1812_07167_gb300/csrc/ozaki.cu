@@ -156,6 +156,55 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const __grid_constant__ G
   }
 }
 
+// Digits of A in two passes, both reading A with neighbouring threads on
+// neighbouring rows (coalesced for the column-major operands).  Pass 1: the
+// exponent of each row (32 rows a block, 8 threads a row over k, combined
+// in shared memory).  Pass 2: one thread per element, digits written k-major
+// ([k][row], rows contiguous).  Padding rows and k get zeros.
+__global__ void __launch_bounds__(256) oz_expo_a_kernel(const __grid_constant__ GemmDesc g, int Mp, int *expo) {
+  __shared__ double part[8][32];
+  const int r = threadIdx.x & 31, kl = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + r, b = blockIdx.y;
+  double mx = 0.0;
+  if (i < g.M)
+    for (int k = kl; k < g.K; k += 8) {
+      const double2 v = oz_lda(g, b, i, k);
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+  part[kl][r] = mx;
+  __syncthreads();
+  if (kl == 0 && i < Mp) {
+    for (int q = 1; q < 8; q++) mx = fmax(mx, part[q][r]);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [1/2, 1): mx 2^-(e+1) in [1/4, 1/2)
+    expo[(size_t)b * Mp + i] = mx > 0.0 ? e + 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) oz_split_a_kernel(const __grid_constant__ GemmDesc g, int Mp, int Kp,
+                                                         __nv_bfloat16 *digits, const int *expo) {
+  const int i = blockIdx.x * 64 + (threadIdx.x & 63);
+  const int k = blockIdx.y * 4 + (threadIdx.x >> 6);
+  const int b = blockIdx.z;
+  if (i >= Mp || k >= Kp) return;
+  double2 v = make_double2(0.0, 0.0);
+  if (i < g.M && k < g.K) v = oz_lda(g, b, i, k);
+  const int sh = expo[(size_t)b * Mp + i];
+  double xr = ldexp(v.x, -sh), xi = ldexp(v.y, -sh);
+  const size_t plane = (size_t)Mp * Kp;
+  __nv_bfloat16 *base = digits + (size_t)b * OZ_S * 2 * plane + (size_t)k * Mp + i;
+#pragma unroll
+  for (int s = 0; s < OZ_S; s++) {
+    xr *= 64.0;
+    xi *= 64.0;
+    const double dr = rint(xr), di = rint(xi);
+    xr -= dr;
+    xi -= di;
+    base[(size_t)(2 * s) * plane] = __float2bfloat16_rn((float)dr);
+    base[(size_t)(2 * s + 1) * plane] = __float2bfloat16_rn((float)di);
+  }
+}
+
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
@@ -173,6 +222,13 @@ __device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const __nv_bfloat16 *p
                : "r"(a));
 }
 
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const __nv_bfloat16 *p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
   asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -186,7 +242,7 @@ struct OzArgs {
   int Mp, Np, Kp;
   int gp;        // pair groups (CTAs a tile)
   double *part;  // gp > 1: partial sums [gp][batch][Mp][Np][2]
-  const __nv_bfloat16 *A;  // [batch][S][2][Mp][Kp]
+  const __nv_bfloat16 *A;  // [batch][S][2][Kp][Mp] (k-major)
   const __nv_bfloat16 *B;  // [batch][S][2][Np][Kp]
   const int *ea;           // [batch][Mp]
   const int *eb;           // [batch][Np]
@@ -195,7 +251,8 @@ struct OzArgs {
 constexpr int OZ_THREADS = 128;  // 4 warps of 32 x 32 outputs
 constexpr int OZ_NACC = 64;      // complex128 outputs x (re, im) per thread
 constexpr int OZ_STAGES = 2;     // cp.async pipeline depth
-typedef __nv_bfloat16 TileA[2][OZ_BM][OZ_LDS];  // [re, im][row][k]
+constexpr int OZ_LDA = OZ_BM + 8;  // shared A row (one k) in bf16: conflict-free transposing loads
+typedef __nv_bfloat16 TileA[2][OZ_BK][OZ_LDA];  // [re, im][k][row]
 typedef __nv_bfloat16 TileB[2][OZ_BN][OZ_LDS];  // [re, im][column][k]
 // shared memory: OZ_STAGES stages of A and B digit tiles, then the
 // complex128 accumulators ([element][thread]: conflict-free)
@@ -265,9 +322,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) oz_gemm_kernel(const __grid_con
     TileB &TB = tileB(st);
     const size_t k0 = (size_t)q.kb * OZ_BK;
 #pragma unroll
-    for (int c = tid; c < 2 * OZ_BM * 4; c += OZ_THREADS) {
-      const int ri = c / (OZ_BM * 4), row = (c >> 2) % OZ_BM, ch = c & 3;
-      cp_async16(&TA[ri][row][ch * 8], Ap + ri * aplane + (size_t)(bm + row) * a.Kp + k0 + ch * 8);
+    for (int c = tid; c < 2 * OZ_BK * (OZ_BM / 8); c += OZ_THREADS) {
+      const int ri = c / (OZ_BK * (OZ_BM / 8)), kr = (c / (OZ_BM / 8)) % OZ_BK, ch = c % (OZ_BM / 8);
+      cp_async16(&TA[ri][kr][ch * 8], Ap + ri * aplane + (k0 + kr) * (size_t)a.Mp + bm + ch * 8);
     }
 #pragma unroll
     for (int c = tid; c < 2 * OZ_BN * 4; c += OZ_THREADS) {
@@ -305,10 +362,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) oz_gemm_kernel(const __grid_con
       unsigned ar[2][4], ai[2][4], br[2][4], bi[2][4];
 #pragma unroll
       for (int mi = 0; mi < 2; mi++) {
-        const int row = wm + mi * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-        const int col = kk + (lane >> 4) * 8;
-        ldsm_x4(ar[mi], &TA[0][row][col]);
-        ldsm_x4(ai[mi], &TA[1][row][col]);
+        // matrix j = lane / 8 of the fragment: rows (k) kk + 8 (j / 2) + lane % 8,
+        // columns (m) wm + 16 mi + 8 (j % 2), read transposed
+        const int kr = kk + ((lane >> 4) << 3) + (lane & 7);
+        const int mc = wm + mi * 16 + (((lane >> 3) & 1) << 3);
+        ldsm_x4_t(ar[mi], &TA[0][kr][mc]);
+        ldsm_x4_t(ai[mi], &TA[1][kr][mc]);
       }
 #pragma unroll
       for (int nj = 0; nj < 2; nj++) {
@@ -455,7 +514,7 @@ __global__ void __launch_bounds__(256) oz_reduce_kernel(const __grid_constant__ 
 
 }  // namespace
 
-int oz_launches(const GemmDesc &g) { return oz_layout(g).gp > 1 ? 4 : 3; }
+int oz_launches(const GemmDesc &g) { return oz_layout(g).gp > 1 ? 5 : 4; }
 
 bool oz_eligible(const GemmDesc &g) {
   // worth the split passes only for sizeable products; complex128 arithmetic only
@@ -474,8 +533,11 @@ cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStr
   char *w = (char *)ws;
   __nv_bfloat16 *Ad = (__nv_bfloat16 *)(w + L.a_off), *Bd = (__nv_bfloat16 *)(w + L.b_off);
   int *ea = (int *)(w + L.ea_off), *eb = (int *)(w + L.eb_off);
-  oz_split_kernel<false><<<dim3((L.Mp + 7) / 8, g.batch), 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
+  oz_expo_a_kernel<<<dim3(L.Mp / 32, g.batch), 256, 0, st>>>(g, L.Mp, ea);
   cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  oz_split_a_kernel<<<dim3(L.Mp / 64, L.Kp / 4, g.batch), 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
+  err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   oz_split_kernel<true><<<dim3((L.Np + 7) / 8, g.batch), 256, 0, st>>>(g, L.Np, L.Kp, Bd, eb);
   err = cudaGetLastError();

@@ -84,3 +84,31 @@ def test_build_with_tensor_core_products_matches_fp64_pipes(m, p, kappa):
     assert np.linalg.norm(Re - Rf) / np.linalg.norm(Rf) < 1e-12
     assert le == pe and lf == pf
     assert le > lf  # the emulated products are three launches each
+
+
+def test_wide_rhs_solve_on_tensor_cores_matches_fp64_pipes_and_oracle():
+    """64 right-hand sides at 16 x 16 leaves: the leaf products of the solve
+    run on the tensor cores; u matches the all-FP64-pipe solve (1e-12) and
+    the oracle (1e-10)."""
+    import os
+    import oracle as O
+    from paper_1812_07167_gb300 import workloads as W
+
+    m, p, kappa, R = 16, 16, 50.0, 64
+    c, s, t = W.random_data(m, p, kappa, kappa, seed=12, nrhs=R)
+    st = torch.cuda.current_stream()
+    us = []
+    for native in (0, 1):
+        pr = hps.Problem(m, p, kappa, kappa, fp64_native=native)
+        h = hps.hps_build(pr, torch.from_numpy(c).cuda(), st)
+        u = torch.empty((R, pr.leaves, pr.n), dtype=torch.complex128, device="cuda")
+        hps.hps_solve(h, torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda(), u, R, st)
+        torch.cuda.synchronize()
+        us.append(u.cpu().numpy())
+        h.free()
+    assert np.abs(us[0] - us[1]).max() / np.abs(us[1]).max() < 1e-12
+    opr = O.Problem(m, p, kappa, kappa)
+    nt = os.cpu_count() or 1
+    with O.Tree(opr, c, nthreads=nt) as T:
+        uo = T.solve(s[:4], t[:4], nthreads=nt)
+    assert np.abs(us[0][:4] - uo).max() / np.abs(uo).max() < 1e-10
