@@ -29,14 +29,14 @@
 // result is scaled back by 2^{a_i + b_j} and combined as C = alpha AB +
 // beta D (+ I).
 //
-// Kernels: one split kernel per operand (a warp per row of A / column of B,
-// writing bf16 digit planes laid out as the tensor-core fragments want them:
-// k fastest), and the product kernel: 64 x 64 output tiles, 4 warps of
-// 32 x 32, mma.sync m16n8k16 bf16 with FP32 accumulation on fragments read
-// by ldmatrix, operand tiles staged through shared memory by cp.async with
-// double buffering, the complex128 accumulators in shared memory.  Products
-// with few output tiles split the slice pairs over several CTAs a tile and
-// sum the partial results in a last pass.
+// Kernels: the split of A (row exponents, then the digits k-major), the
+// split of B (a warp per column, digits k fastest), and the product kernel:
+// 64 x 64 output tiles, 4 warps of 32 x 32, mma.sync m16n8k16 bf16 with FP32
+// accumulation on fragments read by ldmatrix (transposing for the k-major A
+// tiles), operand tiles staged through shared memory by cp.async with double
+// buffering, the complex128 accumulators in shared memory.  Products with few
+// output tiles split the slice pairs over several CTAs a tile and sum the
+// partial results in a last pass.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -115,33 +115,32 @@ __device__ __forceinline__ double2 oz_lda(const GemmDesc &g, int b, int i, int k
   return oz_ld(g.A, oz_off(g.A, b, i, k));
 }
 
-// Digits of one row of A (isb = false) or one column of B (isb = true): a
-// warp per line, lanes over k.  Padding rows / columns / k get zeros.
-template <bool isb>
-__global__ void __launch_bounds__(256) oz_split_kernel(const __grid_constant__ GemmDesc g, int Lp, int Kp,
-                                                       __nv_bfloat16 *digits, int *expo) {
+// Digits of B, a warp per column, lanes over k (neighbouring k are
+// neighbouring in the column-major operands): the column's exponent, then its
+// digits ([column][k], k contiguous).  Padding columns and k get zeros.
+__global__ void __launch_bounds__(256) oz_split_b_kernel(const __grid_constant__ GemmDesc g, int Np, int Kp,
+                                                         __nv_bfloat16 *digits, int *expo) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int line = blockIdx.x * 8 + warp;  // row of A or column of B
+  const int j = blockIdx.x * 8 + warp;
   const int b = blockIdx.y;
-  if (line >= Lp) return;
-  const int nlines = isb ? g.N : g.M;
-  const bool live = line < nlines;
+  if (j >= Np) return;
+  const bool live = j < g.N;
   double mx = 0.0;
   if (live)
     for (int k = lane; k < g.K; k += 32) {
-      const double2 v = isb ? oz_ldb(g, b, k, line) : oz_lda(g, b, line, k);
+      const double2 v = oz_ldb(g, b, k, j);
       mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
     }
   for (int off = 16; off; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   int e = 0;
   if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [1/2, 1): mx 2^-(e+1) in [1/4, 1/2)
   const int sh = mx > 0.0 ? e + 1 : 0;
-  if (lane == 0) expo[(size_t)b * Lp + line] = sh;
-  const size_t plane = (size_t)Lp * Kp;
-  __nv_bfloat16 *base = digits + (size_t)b * OZ_S * 2 * plane + (size_t)line * Kp;
+  if (lane == 0) expo[(size_t)b * Np + j] = sh;
+  const size_t plane = (size_t)Np * Kp;
+  __nv_bfloat16 *base = digits + (size_t)b * OZ_S * 2 * plane + (size_t)j * Kp;
   for (int k = lane; k < Kp; k += 32) {
     double2 v = make_double2(0.0, 0.0);
-    if (live && k < g.K) v = isb ? oz_ldb(g, b, k, line) : oz_lda(g, b, line, k);
+    if (live && k < g.K) v = oz_ldb(g, b, k, j);
     double xr = ldexp(v.x, -sh), xi = ldexp(v.y, -sh);
 #pragma unroll
     for (int s = 0; s < OZ_S; s++) {
@@ -539,7 +538,7 @@ cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStr
   oz_split_a_kernel<<<dim3(L.Mp / 64, L.Kp / 4, g.batch), 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  oz_split_kernel<true><<<dim3((L.Np + 7) / 8, g.batch), 256, 0, st>>>(g, L.Np, L.Kp, Bd, eb);
+  oz_split_b_kernel<<<dim3((L.Np + 7) / 8, g.batch), 256, 0, st>>>(g, L.Np, L.Kp, Bd, eb);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   OzArgs a;
