@@ -186,10 +186,11 @@ __device__ __forceinline__ C ldt(const void *ptr, long long off) {
 
 // k-loop of the skinny product with the storage types of A and B fixed
 template <class C, class TA, class TB, int NN>
-__device__ __forceinline__ void gemv_loop(const GemmDesc &g, int b, int i, int w, C (&acc)[NN]) {
+__device__ __forceinline__ void gemv_loop(const GemmDesc &g, int b, int i, int w, int k0, int k1,
+                                          C (&acc)[NN]) {
   const long long arow = (long long)b * g.A.stride + (g.A.rmap ? (long long)__ldg(g.A.rmap + i) : i);
 #pragma unroll 4
-  for (int k = w; k < g.K; k += 8) {
+  for (int k = k0 + w; k < k1; k += 8) {
     const long long c = g.A.cmap ? (long long)__ldg(g.A.cmap + k) : k;
     const C a = ldt<C, TA>(g.A.ptr, arow + c * g.A.ld);
     const bool second = (g.B2.ptr != nullptr && k >= g.ksplit);
@@ -205,20 +206,27 @@ __device__ __forceinline__ void gemv_loop(const GemmDesc &g, int b, int i, int w
 }
 
 // Skinny products (N <= NN: the solve's right-hand sides).  A CTA computes 32
-// rows of one batch entry; its 8 warps split K (warp w takes k = w, w+8, ...),
-// each lane one row, so the 32 loads of A a warp issues are one coalesced
-// column segment and B(k, :) is a broadcast.  The 8 partial sums meet in
-// shared memory.  Enough CTAs exist even for one large matrix.  B and B2 share
-// one storage type.
+// rows of one batch entry; its 8 warps split its K range (warp w takes
+// k = w, w+8, ...), each lane one row, so the 32 loads of A a warp issues are
+// one coalesced column segment and B(k, :) is a broadcast.  The 8 partial
+// sums meet in shared memory.  When a launch has few row blocks (the top
+// levels of a tree), K is also split over gridDim.y CTAs: each writes its
+// partial sums to scratch, and the last CTA of a row block to arrive (an
+// atomic count) adds them in split order, so results do not depend on
+// timing.  B and B2 share one storage type.
 template <class C, int NN>
 __global__ void __launch_bounds__(256) gemv_kernel(const __grid_constant__ GemmPack pack) {
   __shared__ C red[8][NN][33];
+  __shared__ int last;
   const GemmDesc &g = pack.d[blockIdx.z];
   const int rblocks = (g.M + 31) / 32;
   if ((long long)blockIdx.x >= (long long)rblocks * g.batch) return;
   const int b = blockIdx.x / rblocks;
   const int i = (blockIdx.x % rblocks) * 32 + (threadIdx.x & 31);
-  const int w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int ks = gridDim.y, kid = blockIdx.y;
+  const int kc = ((g.K + ks - 1) / ks + 7) / 8 * 8;
+  const int k0 = min(g.K, kid * kc), k1 = min(g.K, k0 + kc);
   const bool live = i < g.M;
   C acc[NN];
 #pragma unroll
@@ -226,31 +234,64 @@ __global__ void __launch_bounds__(256) gemv_kernel(const __grid_constant__ GemmP
   if (live) {
     if (g.A.f32) {
       if (g.B.f32)
-        gemv_loop<C, float2, float2, NN>(g, b, i, w, acc);
+        gemv_loop<C, float2, float2, NN>(g, b, i, w, k0, k1, acc);
       else
-        gemv_loop<C, float2, double2, NN>(g, b, i, w, acc);
+        gemv_loop<C, float2, double2, NN>(g, b, i, w, k0, k1, acc);
     } else {
       if (g.B.f32)
-        gemv_loop<C, double2, float2, NN>(g, b, i, w, acc);
+        gemv_loop<C, double2, float2, NN>(g, b, i, w, k0, k1, acc);
       else
-        gemv_loop<C, double2, double2, NN>(g, b, i, w, acc);
+        gemv_loop<C, double2, double2, NN>(g, b, i, w, k0, k1, acc);
     }
   }
 #pragma unroll
-  for (int j = 0; j < NN; j++) red[w][j][threadIdx.x & 31] = acc[j];
+  for (int j = 0; j < NN; j++) red[w][j][l] = acc[j];
   __syncthreads();
+  C v[NN];
+  if (w == 0) {
+#pragma unroll
+    for (int j = 0; j < NN; j++) {
+      v[j] = red[0][j][l];
+#pragma unroll
+      for (int q = 1; q < 8; q++) {
+        v[j].x += red[q][j][l].x;
+        v[j].y += red[q][j][l].y;
+      }
+    }
+  }
+  if (ks > 1) {
+    // partial sums of this split; the last split of the row block finishes
+    C *part = (C *)g.part + ((size_t)blockIdx.z * kGemvSlots + (size_t)blockIdx.x * ks) * 32 * NN;
+    unsigned *cnt = g.cnt + (size_t)blockIdx.z * kGemvBlocks + blockIdx.x;
+    if (w == 0) {
+#pragma unroll
+      for (int j = 0; j < NN; j++) part[((size_t)kid * NN + j) * 32 + l] = v[j];
+      __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(cnt, 1u) == (unsigned)ks - 1) ? 1 : 0;
+    __syncthreads();
+    if (!last) return;
+    if (w == 0) {
+      __threadfence();
+#pragma unroll
+      for (int j = 0; j < NN; j++) {
+        C t = CT<C>::make(0.0, 0.0);
+        for (int q = 0; q < ks; q++) {
+          const C p = __ldcg(part + ((size_t)q * NN + j) * 32 + l);  // other SMs' writes: past L1
+          t.x += p.x;
+          t.y += p.y;
+        }
+        v[j] = t;
+      }
+      if (l == 0) *cnt = 0;  // ready for the next launch
+    }
+  }
   if (w == 0 && live) {
-    const int l = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < NN; j++) {
       if (j >= g.N) continue;
-      C v = red[0][j][l];
-#pragma unroll
-      for (int q = 1; q < 8; q++) {
-        v.x += red[q][j][l].x;
-        v.y += red[q][j][l].y;
-      }
-      epilogue<C>(g, b, i, j, v);
+      epilogue<C>(g, b, i, j, v[j]);
     }
   }
 }
@@ -306,10 +347,21 @@ cudaError_t launch_cfg(const GemmPack &pk, cudaStream_t st) {
 template <class C, int NN>
 cudaError_t launch_gemv(const GemmPack &pk, cudaStream_t st) {
   long long blocks = 0;
-  for (int q = 0; q < pk.n; q++)
+  int kmin = 1 << 30;
+  bool scratch = true;
+  for (int q = 0; q < pk.n; q++) {
     blocks = std::max(blocks, (long long)((pk.d[q].M + 31) / 32) * pk.d[q].batch);
+    kmin = std::min(kmin, pk.d[q].K);
+    scratch = scratch && pk.d[q].part && pk.d[q].cnt;
+  }
   if (blocks == 0) return cudaSuccess;
-  dim3 grid((unsigned)blocks, 1, pk.n);
+  // split K over CTAs while the launch has fewer than two CTAs an SM, keeping
+  // at least 64 k a split and at most kGemvBlocks row blocks
+  int ks = 1;
+  if (scratch && blocks <= kGemvBlocks)
+    while (ks < 16 && blocks * ks < 2 * 152 && kmin / (2 * ks) >= 64) ks *= 2;
+  if (blocks * ks > kGemvSlots) ks = 1;  // (cannot happen: the loop stops below 2 x 304)
+  dim3 grid((unsigned)blocks, ks, pk.n);
   gemv_kernel<C, NN><<<grid, 256, 0, st>>>(pk);
   return cudaGetLastError();
 }

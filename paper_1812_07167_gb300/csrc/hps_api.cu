@@ -592,6 +592,8 @@ int grow(void **buf, size_t *have, size_t need) {
   *have = 0;
   CK(cudaMalloc(buf, need));
   *have = need;
+  // the skinny products' counters at the head of a solve workspace start at zero
+  CK(cudaMemset(*buf, 0, std::min(need, hps::gemv_scratch_counters())));
   return HPS_OK;
 }
 
@@ -612,6 +614,10 @@ struct SolveWs {
   size_t osd = 0, otd = 0, ofu = 0, ogu = 0, oja = 0, ojb = 0, od = 0;
   // products on the tensor cores (wide right-hand-side blocks): digit planes
   size_t ooz = 0, oz_bytes = 0;
+  // scratch of the skinny products (up to 8 right-hand sides): counters at
+  // offset 0 of every workspace (zeroed when it is allocated, left zero by
+  // the kernel), partial sums after them
+  size_t ogv = 0;
 };
 
 // The complex128 products of a solve with R right-hand sides (M, K, batch),
@@ -632,7 +638,11 @@ static void solve_products(const Plan &pl, std::vector<std::array<int, 3>> &out)
 }
 
 static void solve_ws_layout(const Plan &pl, int R, SolveWs &w, bool allow_oz = true) {
-  size_t off = 0;
+  size_t off = align256(hps::gemv_scratch_counters());
+  if (R <= 8) {
+    w.ogv = off;
+    off = align256(off + hps::gemv_part_bytes(R));
+  }
   auto take = [&](long long count) {
     size_t o = off;
     off = align256(off + sizeof(double2) * (size_t)count);
@@ -686,6 +696,10 @@ static int solve_gemm(GemmDesc *gd, int nd, cudaStream_t st, char *wb, const Sol
   int nr = 0;
   for (int q = 0; q < nd; q++) {
     GemmDesc &g = gd[q];
+    if (g.N <= 8 && ws.ogv) {
+      g.part = wb + ws.ogv;
+      g.cnt = (unsigned *)wb;
+    }
     if (oz && ws.oz_bytes && oz_shape(g.M, g.N, g.K, g.batch, g.cf32, true)) {
       int chunk = g.batch;
       while (chunk > 1 && oz_bytes_shape(g.M, g.N, g.K, chunk) > ws.oz_bytes) chunk = (chunk + 1) / 2;
