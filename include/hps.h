@@ -135,9 +135,9 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy);
  *   out:  receives the new handle; unchanged on failure
  * Device memory for all operators is allocated here and owned by the handle.
  * Returns HPS_EINVAL (bad descriptor, NULL c/out), HPS_ENOMEM, HPS_ECUDA, or
- * HPS_ENOTSUP when an interface of the tree is too large for this build's
- * interface-inverse kernel (p = 16: 64 x 64 leaves and more), before any
- * device work. */
+ * HPS_ENOTSUP when a leaf matrix or an interface of the tree is too large
+ * for the kernels' shared memory (p > 24, or more than 512 leaves a side at
+ * p = 16), before any device work. */
 int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **out);
 
 /* Build nprob independent solvers together (a ragged batch): Algorithm 1

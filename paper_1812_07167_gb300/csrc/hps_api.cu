@@ -485,7 +485,7 @@ struct GJChoice {
 
 bool choose_gj_rule(int n3, long long P, int f32, GJChoice &g);
 
-// false when no regime fits this build's shared memory
+// false when no regime fits in the kernels' shared memory
 bool choose_gj(int n3, long long P, int f32, GJChoice &g) {
   int v;
   if (P <= (1 << 30) && tuned(TuneKey{1, n3, 0, 0, (int)P, f32}, v)) {
@@ -930,7 +930,7 @@ const char *hps_strerror(int code) {
     case HPS_ESINGULAR: return "zero pivot in a leaf or interface matrix";
     case HPS_ETIMEOUT: return "bounded device wait timed out";
     case HPS_ECUDA: return "CUDA runtime error";
-    case HPS_ENOTSUP: return "not supported by this build";
+    case HPS_ENOTSUP: return "not supported: a matrix of the tree exceeds the kernels' shared memory";
     case HPS_ETOOBIG: return "request needs more than the fixed no-allocation workspace";
     default: return "unknown error";
   }
