@@ -67,7 +67,7 @@ enum {
   HPS_ESINGULAR = 3, /* a leaf matrix B or an interface matrix W had a zero pivot */
   HPS_ETIMEOUT = 4,  /* a bounded device wait gave up */
   HPS_ECUDA = 5,     /* a CUDA runtime call failed (no device, launch error, ...) */
-  HPS_ENOTSUP = 6,   /* a valid request this build does not implement */
+  HPS_ENOTSUP = 6,   /* a valid request the kernels cannot run (sizes; see each call) */
   HPS_ETOOBIG = 7    /* the request needs more than the fixed no-allocation workspace */
 };
 

@@ -930,7 +930,7 @@ const char *hps_strerror(int code) {
     case HPS_ESINGULAR: return "zero pivot in a leaf or interface matrix";
     case HPS_ETIMEOUT: return "bounded device wait timed out";
     case HPS_ECUDA: return "CUDA runtime error";
-    case HPS_ENOTSUP: return "not supported: a matrix of the tree exceeds the kernels' shared memory";
+    case HPS_ENOTSUP: return "not supported for this request (sizes or precision; see the call)";
     case HPS_ETOOBIG: return "request needs more than the fixed no-allocation workspace";
     default: return "unknown error";
   }
