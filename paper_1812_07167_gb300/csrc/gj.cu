@@ -32,7 +32,9 @@
 
 #include <algorithm>
 
+#include "cx.cuh"
 #include "hps_internal.h"
+#include "leaf_geom.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -44,66 +46,6 @@ constexpr int kThreads = 256;
 constexpr int KB = 8;           // panel width
 constexpr int kMoves = 2 * KB;  // row moves of one panel, at most
 constexpr int kMoveInts = 1 + 2 * kMoves;
-
-template <class C>
-struct CX;
-template <>
-struct CX<double2> {
-  using R = double;
-  __device__ static double2 make(double x, double y) { return make_double2(x, y); }
-  __device__ static double fmad(double a, double b, double c) { return fma(a, b, c); }
-  // max(|Re|, |Im|) as the integer image of its IEEE-754 bits (for
-  // non-negative values integer order is numeric order): the pivot search
-  // compares integers instead of spending floating-point instructions
-  __device__ static unsigned long long key(double2 z) {
-    unsigned long long a = (unsigned long long)__double_as_longlong(z.x) & 0x7fffffffffffffffull;
-    unsigned long long b = (unsigned long long)__double_as_longlong(z.y) & 0x7fffffffffffffffull;
-    return a > b ? a : b;
-  }
-};
-template <>
-struct CX<float2> {
-  using R = float;
-  __device__ static float2 make(double x, double y) { return make_float2((float)x, (float)y); }
-  __device__ static float fmad(float a, float b, float c) { return fmaf(a, b, c); }
-  __device__ static unsigned long long key(float2 z) {
-    unsigned int a = __float_as_uint(z.x) & 0x7fffffffu;
-    unsigned int b = __float_as_uint(z.y) & 0x7fffffffu;
-    return a > b ? a : b;
-  }
-};
-
-template <class C>
-__device__ __forceinline__ C cmul(C a, C b) {
-  C r;
-  r.x = a.x * b.x - a.y * b.y;
-  r.y = a.x * b.y + a.y * b.x;
-  return r;
-}
-
-template <class C>
-__device__ __forceinline__ C crecip(C z) {
-  // 1 / z with Smith's scaling (Smith, CACM 1962)
-  using R = typename CX<C>::R;
-  C out;
-  if (fabs(z.x) >= fabs(z.y)) {
-    R r = z.y / z.x, d = z.x + z.y * r;
-    out.x = R(1) / d;
-    out.y = -r / d;
-  } else {
-    R r = z.x / z.y, d = z.x * r + z.y;
-    out.x = r / d;
-    out.y = R(-1) / d;
-  }
-  return out;
-}
-
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline int npanels(int n) { return (n + KB - 1) / KB; }
@@ -584,12 +526,6 @@ __device__ __forceinline__ int dest_col(const int *perm, int n, int j) {
   return loc;
 }
 
-__device__ __forceinline__ void record_status(unsigned int *status, unsigned int code, int level,
-                                              int box) {
-  unsigned int w = (code << 28) | ((unsigned)(level & 0xff) << 20) | ((unsigned)box & 0xfffffu);
-  atomicCAS(status, 0u, w);
-}
-
 struct LeafArgs {
   LeafTables lt;
   const LeafProb *probs;  // per-problem tables, c, kappa^2, eta (device)
@@ -652,66 +588,30 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
   for (int i = tid; i < n; i += nthr) loc[(grid[i] >> 8) * p + (grid[i] & 0xff)] = i;
   __syncthreads();
 
-  // Row equilibration: row i of B is scaled by an exact power of two d_i
-  // that brings its largest entry into [1, 2); the elimination inverts D B
-  // and X = (D B)^{-1} D, i.e. column j of the result is scaled by d_j.
-  // Without it the impedance rows (scale 2/h p^2) and the interior rows
-  // (scale (2/h)^2 p^4) are ~10^5 apart, which costs complex64 most of its
-  // digits.
+  LeafGeom geo;
+  geo.D1x = D1x;
+  geo.D1y = D1y;
+  geo.D2x = D2x;
+  geo.D2y = D2y;
+  geo.grid = grid;
+  geo.cv = cv;
+  geo.p = p;
+  geo.e = e;
+  geo.nb = nb;
+  geo.kappa2 = kappa2;
+  geo.eta = eta;
+  // Row equilibration: row i of B is scaled by an exact power of two d_i;
+  // the elimination inverts D B and X = (D B)^{-1} D, i.e. column j of the
+  // result is scaled by d_j.
   double *rsc = (double *)(smem + sp.rsc);
-  for (int i = tid; i < n; i += nthr) {
-    const int ix = grid[i] & 0xff, iy = grid[i] >> 8;
-    double mx = 0.0;
-    if (i < nb) {
-      const int side = i / e;
-      const double sgn = (side == 0 || side == 3) ? -1.0 : 1.0;
-      for (int t = 0; t < p; t++) {
-        const double v = sgn * ((side == 0) ? D1y[0 * p + t] : (side == 1) ? D1x[(p - 1) * p + t]
-                                : (side == 2) ? D1y[(p - 1) * p + t] : D1x[0 * p + t]);
-        const bool diag = (side == 0 || side == 2) ? (t == iy) : (t == ix);
-        // at the node itself the entry is the derivative weight + i eta
-        mx = fmax(mx, diag ? fmax(fabs(v - eta.y), fabs(eta.x)) : fabs(v));
-      }
-    } else {
-      for (int t = 0; t < p; t++) {
-        if (t != ix) mx = fmax(mx, fabs(D2x[ix * p + t]));
-        if (t != iy) mx = fmax(mx, fabs(D2y[iy * p + t]));
-      }
-      mx = fmax(mx, fabs(D2x[ix * p + ix] + D2y[iy * p + iy] + kappa2 * cv[i - nb]));
-    }
-    int ex = 0;
-    frexp(mx > 0.0 ? mx : 1.0, &ex);
-    rsc[i] = ldexp(1.0, 1 - ex);
-  }
+  for (int i = tid; i < n; i += nthr) rsc[i] = leaf_row_scale(geo, i);
   __syncthreads();
 
   // assemble the own columns of D B (entries computed in FP64, stored as C)
   for (int idx = tid; idx < n * ncols; idx += nthr) {
     const int i = idx % n, jj = idx / n, j = c0 + jj;
-    const int ix = grid[i] & 0xff, iy = grid[i] >> 8;
-    const int jx = grid[j] & 0xff, jy = grid[j] >> 8;
-    double vx = 0.0, vy = 0.0;
-    if (i < nb) {
-      const int side = i / e;
-      if (side == 0) {
-        if (jx == ix) vx = -D1y[0 * p + jy];  // south: -d/dy
-      } else if (side == 1) {
-        if (jy == iy) vx = D1x[(p - 1) * p + jx];  // east: +d/dx
-      } else if (side == 2) {
-        if (jx == ix) vx = D1y[(p - 1) * p + jy];  // north: +d/dy
-      } else {
-        if (jy == iy) vx = -D1x[0 * p + jx];  // west: -d/dx
-      }
-      if (i == j) {  // + i eta
-        vx -= eta.y;
-        vy += eta.x;
-      }
-    } else {
-      if (jy == iy) vx -= D2x[ix * p + jx];
-      if (jx == ix) vx -= D2y[iy * p + jy];
-      if (i == j) vx -= kappa2 * cv[i - nb];
-    }
-    S[(size_t)j * n + i] = CX<C>::make(rsc[i] * vx, rsc[i] * vy);
+    const double2 v = leaf_B(geo, i, j);
+    S[(size_t)j * n + i] = CX<C>::make(rsc[i] * v.x, rsc[i] * v.y);
   }
   __syncthreads();
 
