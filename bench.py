@@ -51,6 +51,8 @@ def config_dict(nrhs=1, l2="flushed between steps (256 MiB write)"):
         "c": "1+0.3 sin(4 pi x) cos(6 pi y)", "s": "8 Gaussian sources, width 0.01, seed 1", "t": 0,
         "dof": M * M * (P_ORDER * P_ORDER - 4), "tensor_nodes": M * M * P_ORDER * P_ORDER,
         "nrhs_per_step": nrhs, "l2": l2, "precision": "complex128",
+        "leaf_form": ("LU factors P D B = L U (leaf kernel), two triangular sweeps a solve" if LEAF_FORM == 0
+                      else "B^-1 by Gauss-Jordan (leaf kernel), one product a solve"),
         "products": "FP64 pipes; merge products of 2^26+ complex multiply-adds by the Ozaki scheme "
                     "on the bf16 tensor cores (9 slices of 6 bits, exact FP32 slice sums, complex128 totals)",
         "domain": list(wl.domain),
@@ -158,6 +160,16 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+LEAF_FORM = 0  # hps.HPS_LEAF_LU; --leaf-form inverse sets HPS_LEAF_INVERSE
+
+
+def _problem(*args, **kw):
+    """hps.Problem with the leaf form chosen on the command line."""
+    from paper_1812_07167_gb300 import hps
+
+    return hps.Problem(*args, leaf_form=LEAF_FORM, **kw)
+
+
 def ours(args, rank, world, local_rank):
     import torch
 
@@ -172,7 +184,7 @@ def ours(args, rank, world, local_rank):
         dist = dist_mod
     st = torch.cuda.current_stream()
     wl = workload()
-    pr = hps.Problem(wl.m, wl.p, wl.kappa, wl.eta)
+    pr = _problem(wl.m, wl.p, wl.kappa, wl.eta)
     lxy, bxy = hps.hps_nodes(pr)
     c, s, t = wl.sample(lxy, bxy)
     cd = torch.from_numpy(c).to(dev)
@@ -295,7 +307,7 @@ def ours(args, rank, world, local_rank):
 
     # ---- mixed-precision path on the same problem (complex64 leaves and lower
     # merges, complex128 top levels and refinement) ----
-    pm = hps.Problem(wl.m, wl.p, wl.kappa, wl.eta, precision=hps.HPS_MIXED)
+    pm = _problem(wl.m, wl.p, wl.kappa, wl.eta, precision=hps.HPS_MIXED)
     mb = []
     for _ in range(4):
         flush.zero_()
@@ -334,15 +346,20 @@ def ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    leaf_flops = pr.leaves * 8 * (pr.n ** 3 + pr.nb * pr.n * pr.p)
+    # leaf kernel flops (one complex multiply-add = 8): LU of [B; G] and the
+    # G-row solve, or Gauss-Jordan and G X
+    lu = LEAF_FORM == 0
+    leaf_flops = (pr.leaves * 8 * (pr.n ** 3 // 3 + pr.nb * pr.n ** 2) if lu
+                  else pr.leaves * 8 * (pr.n ** 3 + pr.nb * pr.n * pr.p))
+    leaf_kernel = "lu_leaf_kernel" if lu else "leaf_kernel"
     leaf_avg = statistics.mean(leaf_ms)
     achieved = leaf_flops / (leaf_avg / 1e3) / 1e12
     traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "leaf_kernel_traffic.json")
+    tr_path = os.path.join(ROOT, "profiles", f"{leaf_kernel}_traffic.json")
     if os.path.exists(tr_path):
         with open(tr_path) as f:
             tr = json.load(f)
-        if tr.get("kernel_hash") == kernel_hash():
+        if tr.get("kernel_hash") == kernel_hash(leaf_kernel):
             traffic = tr.get("bytes_per_launch")
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
@@ -361,7 +378,7 @@ def ours(args, rank, world, local_rank):
         "tuning": {"shapes": tuned_shapes, "seconds": tune_s,
                    "what": "hps_tune: measured tile / tensor-core choice per merge product shape and "
                            "cluster / panel regime per interface-inverse shape, before the timed steps"},
-        "roofline": {"kernel": "leaf_kernel", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": leaf_kernel, "bound": "alu", "achieved": achieved, "flops_per_launch": leaf_flops,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": traffic, "leaf_ms": leaf_avg,
                      "peak_source": "FP64 unit count x max SM clock (152 SM x 4 flop/clk x 2.07 GHz)"},
@@ -411,17 +428,17 @@ def batching(dev, st, flush, reps=2):
            "dof": sum(m * m * (P_ORDER * P_ORDER - 4) for m, _, _ in spec)}
     cs = []
     for m, kap, cfun in spec:
-        lxy, _ = hps.hps_nodes(hps.Problem(m, P_ORDER, kap, kap))
+        lxy, _ = hps.hps_nodes(_problem(m, P_ORDER, kap, kap))
         nb = 4 * (P_ORDER - 2)
         cs.append(torch.from_numpy(cfun(lxy[:, nb:, 0], lxy[:, nb:, 1])).to(dev))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     us = {}
     for name, prec in (("fp64", hps.HPS_FP64), ("mixed", hps.HPS_MIXED)):
-        probs = [hps.Problem(m, P_ORDER, kap, kap, precision=prec) for m, kap, _ in spec]
+        probs = [_problem(m, P_ORDER, kap, kap, precision=prec) for m, kap, _ in spec]
         res = {}
         # measured kernel choices for the batch's shapes and for each size alone
         res["tuned_shapes"] = hps.hps_tune(probs, st) + sum(
-            hps.hps_tune([hps.Problem(m, P_ORDER, 50.0, 50.0, precision=prec)], st) for m in sorted({m for m, _, _ in spec}))
+            hps.hps_tune([_problem(m, P_ORDER, 50.0, 50.0, precision=prec)], st) for m in sorted({m for m, _, _ in spec}))
         for mode in ("batched", "separate"):
             ms = []
             for rep in range(reps + 1):
@@ -486,7 +503,7 @@ def precision(args, local_rank):
     st = torch.cuda.current_stream()
     m, p, kappa = 64, P_ORDER, 300.0
     wl = W.random_medium_sources(m, p, kappa)
-    pr = hps.Problem(m, p, kappa, kappa)
+    pr = _problem(m, p, kappa, kappa)
     lxy, bxy = hps.hps_nodes(pr)
     c, s, t = wl.sample(lxy, bxy)
     cd = torch.from_numpy(c).to(dev)
@@ -503,7 +520,7 @@ def precision(args, local_rank):
     res = {}
     with ClockSampler(local_rank) as clk:
         for name, prec in (("fp64", hps.HPS_FP64), ("mixed", hps.HPS_MIXED)):
-            q = hps.Problem(m, p, kappa, kappa, precision=prec)
+            q = _problem(m, p, kappa, kappa, precision=prec)
             tuned = hps.hps_tune([q], st)
             bms = []
             for rep in range(4):
@@ -619,7 +636,7 @@ def serving_run(args, local_rank, precision):
 
     dev = torch.device("cuda", local_rank)
     m, p, kappa = args.serve_m, P_ORDER, 600.0
-    pr = hps.Problem(m, p, kappa, kappa, precision=precision)
+    pr = _problem(m, p, kappa, kappa, precision=precision)
     lxy, _ = hps.hps_nodes(pr)
     nb = pr.nb
     xi, yi = lxy[:, nb:, 0], lxy[:, nb:, 1]
@@ -644,7 +661,7 @@ def serving_run(args, local_rank, precision):
     builds = {}
     for k, d in enumerate(sched):
         if d["kind"] == "build":
-            bp = hps.Problem(d["m"], p, d["kappa"], d["kappa"], precision=precision)
+            bp = _problem(d["m"], p, d["kappa"], d["kappa"], precision=precision)
             bx, _ = hps.hps_nodes(bp)
             bc = W.random_medium(d["seed"])(bx[:, nb:, 0], bx[:, nb:, 1])
             builds[k] = (bp, torch.from_numpy(bc).to(dev))
@@ -707,12 +724,17 @@ def serving(args, local_rank):
     print(json.dumps(out), flush=True)
 
 
-def kernel_hash():
+def kernel_hash(kernel="lu_leaf_kernel"):
+    """Hash of the sources of a leaf kernel (its file and the device headers
+    it includes), so stored ncu counters are used only for the code they
+    were taken on."""
     import hashlib
 
+    src = "lu.cu" if kernel == "lu_leaf_kernel" else "gj.cu"
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1812_07167_gb300", "csrc", "gj.cu"), "rb") as f:
-        h.update(f.read())
+    for name in (src, "cx.cuh", "leaf_geom.cuh"):
+        with open(os.path.join(ROOT, "paper_1812_07167_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -727,12 +749,16 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="run the 64x64-leaf FP64-vs-mixed workload (with the oracle) instead of the step bench")
     ap.add_argument("--no-batching", action="store_true", help="skip the ragged-batch section")
+    ap.add_argument("--leaf-form", default="lu", choices=["lu", "inverse"],
+                    help="leaf operators as LU factors (default) or as B^-1")
     ap.add_argument("--zgemm", type=int, nargs=3, metavar=("M", "N", "K"),
                     help="time one complex GEMM on the tensor cores and on the FP64 pipes")
     ap.add_argument("--serve-m", type=int, default=128)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-max-rhs", type=int, default=128)
     args = ap.parse_args()
+    global LEAF_FORM
+    LEAF_FORM = 1 if args.leaf_form == "inverse" else 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

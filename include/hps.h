@@ -72,6 +72,7 @@ enum {
 };
 
 enum { HPS_FP64 = 0, HPS_MIXED = 1 };
+enum { HPS_LEAF_LU = 0, HPS_LEAF_INVERSE = 1 };
 
 typedef struct {
   double x0, x1, y0, y1; /* the rectangle Omega, x1 > x0, y1 > y0 */
@@ -99,6 +100,14 @@ typedef struct {
                             bits per operand, exact FP32 accumulation of the slice products,
                             complex128 sums: error ~2^-54 max|A_i.| max|B_.j| per
                             term); 1: every complex128 product on the FP64 pipes */
+  int leaf_form;         /* how the leaf solution operator [Psi | Y] = B^{-1} of Sec. 2.1 is
+                            stored (both give the same operators up to rounding):
+                            HPS_LEAF_LU: the factors P D B = L U (row pivoting P, a
+                            power-of-two row scaling D), about 0.55 of the leaf
+                            flops; a solve applies them by two triangular sweeps.
+                            HPS_LEAF_INVERSE: B^{-1} itself (Gauss-Jordan); a solve
+                            applies it as a product, which runs on the tensor cores
+                            for 32+ right-hand sides unless fp64_native. */
 } hps_desc;
 
 typedef struct hps_handle hps_handle;
@@ -146,7 +155,7 @@ int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **
  * sizes of level j (counted from the leaves) depend on j and p only, so the
  * problems' parents on that level form one batch of equal-size merges.
  *   descs[k], c[k]: problem k as for hps_build.  Every desc must have the
- *     same p, precision, fp64_levels and fp64_native (HPS_EINVAL otherwise); m, the
+ *     same p, precision, fp64_levels, fp64_native and leaf_form (HPS_EINVAL otherwise); m, the
  *     domain, kappa and eta may differ.
  *   out[k] receives problem k's handle.  The handles share one device
  *     allocation, released with the last of them; hps_free each one.
@@ -281,7 +290,7 @@ int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, 
  * GPU form of the paper's calibration of representative actions (Sec. 3,
  * Table 1, which times a leaf inverse, an interface inverse and a product
  * per level and thread count).  Shapes measured before are skipped.
- *   descs: as for hps_build_batch (the same p, precision, fp64_levels and
+ *   descs: as for hps_build_batch (the same p, precision, fp64_levels, leaf_form and
  *          fp64_native); their shapes are measured on scratch data.
  *   ntuned: optional, receives the number of shapes measured.
  * Synchronizes the stream.  Returns HPS_EINVAL, HPS_ENOTSUP, HPS_ENOMEM,

@@ -67,6 +67,7 @@ struct Plan {
   int m, my, p, e, n, nb, ni, L, leaves, nbdry;  // m: leaves along x, my: along y
   bool mixed;                   // HPS_MIXED
   int leaf_f32;                 // leaf operators in complex64
+  bool leaf_lu;                 // leaf operators as LU factors (else B^{-1})
   int refine_steps;             // refinement steps of a mixed solve
   bool oz;                      // large complex128 merge products on the tensor cores
   std::vector<Level> lv;        // lv[j]: merge j from the leaves up (parents on level L-1-j)
@@ -102,6 +103,8 @@ struct hps_handle {
   hps_info_t info;
   Shared *sh = nullptr;
   void *X = nullptr, *GX = nullptr;  // leaf operators (complex64 when plan.leaf_f32)
+  int *lu_perm = nullptr;            // leaf_lu: row k of P D B is row lu_perm[k] of B
+  double *lu_dsc = nullptr;          // leaf_lu: d of that row
   double2 *Rroot = nullptr;
   double *c_dev = nullptr;  // c at the interior nodes (for the refinement residual)
   int *d_outer = nullptr;
@@ -136,6 +139,7 @@ int check_desc(const hps_desc *d) {
   if (d->precision != HPS_FP64 && d->precision != HPS_MIXED) return HPS_EINVAL;
   if (d->fp64_levels < 0) return HPS_EINVAL;
   if (d->fp64_native != 0 && d->fp64_native != 1) return HPS_EINVAL;
+  if (d->leaf_form != HPS_LEAF_LU && d->leaf_form != HPS_LEAF_INVERSE) return HPS_EINVAL;
   return HPS_OK;
 }
 
@@ -232,6 +236,7 @@ void make_plan(const hps_desc &d, Plan &pl) {
   pl.nbdry = 2 * (d.mx + d.my) * pl.e;
   pl.mixed = (d.precision == HPS_MIXED);
   pl.leaf_f32 = pl.mixed ? 1 : 0;
+  pl.leaf_lu = (d.leaf_form == HPS_LEAF_LU);
   pl.refine_steps = d.refine_steps == 0 ? 2 : (d.refine_steps < 0 ? 0 : d.refine_steps);
   pl.oz = (d.fp64_native == 0);
   const int top = std::min(pl.L, d.fp64_levels == 0 ? 4 : d.fp64_levels);
@@ -405,10 +410,14 @@ void fill_info(const Plan &pl, hps_info_t &in) {
   in.n_bdry = pl.nbdry;
   in.dof = (long long)pl.leaves * pl.n;
   long long n = pl.n, nb = pl.nb, ni = pl.ni;
-  long long bf = (long long)pl.leaves * 8 * (n * n * n + nb * n * pl.p);
+  // leaf: Gauss-Jordan n^3 and G X; or LU of [B; G] (n^3/3 + nb n^2/2) and
+  // the G-row solve (nb n^2/2), with n pivots and row scales kept
+  long long bf = pl.leaf_lu ? (long long)pl.leaves * 8 * (n * n * n / 3 + nb * n * n)
+                            : (long long)pl.leaves * 8 * (n * n * n + nb * n * pl.p);
   long long sf = (long long)pl.leaves * 8 * (nb * ni + n * n);
-  long long ob = (long long)pl.leaves * cplx_bytes(n * n + nb * n, pl.leaf_f32);
-  long long sb = (long long)pl.leaves * cplx_bytes(n * n + nb * ni, pl.leaf_f32);
+  const long long lu_aux = pl.leaf_lu ? (long long)pl.leaves * n * (4 + 8) : 0;
+  long long ob = (long long)pl.leaves * cplx_bytes(n * n + nb * n, pl.leaf_f32) + lu_aux;
+  long long sb = (long long)pl.leaves * cplx_bytes(n * n + nb * ni, pl.leaf_f32) + lu_aux;
   for (const Level &L : pl.lv) {
     long long n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, P = L.P;
     bf += P * 8 * (2 * n3 * n3 * n3 + n3 * n3 * n1 + 2 * n3 * n3 * nt + (n1 + n2) * n3 * nt);
@@ -435,6 +444,39 @@ void fill_info(const Plan &pl, hps_info_t &in) {
     sf *= 1 + steps;
     in.solve_flops = sf;
   }
+}
+
+// CTAs a leaf (the leaf kernel's cluster) for a launch over NL leaves, or 0
+// when no cluster fits the kernel's shared memory.  Wider clusters split
+// each leaf finer, which balances the chip when there are few leaves
+// (Gauss-Jordan, measured best: 8 CTAs a leaf for 16 leaves, 4 for 256, 1
+// from 1024 leaves on; complex64 leaves are latency-bound: one CTA a leaf
+// from 256 leaves on).  The LU kernel also widens until two CTAs fit an SM.
+int leaf_cluster(const Plan &pl, long long NL) {
+  const bool f32 = pl.leaf_f32 != 0;
+  auto smem = [&](int cs) {
+    return pl.leaf_lu ? hps::lu_leaf_smem_bytes(pl.n, pl.nb, pl.p, cs, f32)
+                      : hps::gj_smem_bytes(pl.n, cs, true, pl.p, false, f32);
+  };
+  int cs = 1;
+  while (cs < 8 && NL * cs < (f32 ? 256 : 1024)) cs *= 2;
+  if (pl.leaf_lu)
+    while (cs < 8 && smem(cs) > 113 * 1024 && smem(2 * cs) <= 113 * 1024) cs *= 2;
+  if (const char *e = getenv("HPS_LEAF_CLUSTER")) {
+    int v = atoi(e);
+    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) cs = v;
+  }
+  while (cs < 16 && smem(cs) > 227 * 1024) cs *= 2;
+  return smem(cs) <= 227 * 1024 ? cs : 0;
+}
+
+// Leaves a leaf launch covers: Gauss-Jordan works on a scratch copy of the
+// matrices (chunks of ~1 GiB of them), the LU kernel in place (its
+// bookkeeping caps a launch at 16384 leaves).
+long long leaf_chunk(const Plan &pl, long long NL) {
+  const long long esz = pl.leaf_f32 ? 8 : 16, n = pl.n;
+  const long long cap = pl.leaf_lu ? 16384 : (1LL << 30) / (esz * n * n);
+  return std::max<long long>(1, std::min<long long>(NL, cap));
 }
 
 int choose_gj_cs(int n, int batch, bool tglobal, int f32) {
@@ -626,7 +668,7 @@ static void solve_products(const Plan &pl, std::vector<std::array<int, 3>> &out)
   out.clear();
   if (!pl.leaf_f32) {
     out.push_back({pl.nb, pl.ni, pl.leaves});
-    out.push_back({pl.n, pl.n, pl.leaves});
+    if (!pl.leaf_lu) out.push_back({pl.n, pl.n, pl.leaves});
   }
   for (const Level &L : pl.lv) {
     if (L.f32) continue;
@@ -839,13 +881,18 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     cb.d[1] = copy(n2, R, P, mat(tp + n1, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I2));
     CK(hps::launch_copy(cb, st));
   }
-  // leaves: u = Psi t + Y s = X [t; s]
-  g = gemm(n, R, n, nl, F(h->X, n, (long long)n * n, lf), mat(W(ot[0]), (long long)nl * nb, nb),
-           mat(u, (long long)nl * n, n));
-  g.B2 = mat(s, (long long)nl * ni, ni);
-  g.ksplit = nb;
-  g.cf32 = lf;
-  if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
+  // leaves: u = Psi t + Y s = B^{-1} [t; s]
+  if (pl.leaf_lu) {
+    CK(hps::launch_lu_solve(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, W(ot[0]), (long long)nl * nb, nb, s,
+                            (long long)nl * ni, ni, u, (long long)nl * n, n, lf != 0, st));
+  } else {
+    g = gemm(n, R, n, nl, F(h->X, n, (long long)n * n, lf), mat(W(ot[0]), (long long)nl * nb, nb),
+             mat(u, (long long)nl * n, n));
+    g.B2 = mat(s, (long long)nl * ni, ni);
+    g.ksplit = nb;
+    g.cf32 = lf;
+    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
+  }
 
   return HPS_OK;
 }
@@ -1133,6 +1180,8 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   };
   const size_t oX = take((size_t)(esl * NL * n * n));
   const size_t oGX = take((size_t)(esl * NL * n * nb));
+  const size_t oPerm = P0.leaf_lu ? take(sizeof(int) * (size_t)NL * n) : 0;
+  const size_t oDsc = P0.leaf_lu ? take(sizeof(double) * (size_t)NL * n) : 0;
   for (int j = 0; j < Lmax; j++) {
     const Level &S = P0.lv[j];
     const long long n1 = S.n1, n2 = S.n2, n3 = S.n3, nt = S.nt;
@@ -1201,6 +1250,10 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     Plan &pl = h->plan;
     h->X = base + oX + esl * leaf0[k] * n * n;
     h->GX = base + oGX + esl * leaf0[k] * n * nb;
+    if (P0.leaf_lu) {
+      h->lu_perm = (int *)(base + oPerm) + leaf0[k] * n;
+      h->lu_dsc = (double *)(base + oDsc) + leaf0[k] * n;
+    }
     for (int j = 0; j < pl.L; j++) {
       Level &L = pl.lv[j];
       const long long pos = first[k][j];
@@ -1293,32 +1346,28 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     lt.n = n;
     lt.nb = nb;
     lt.ni = ni;
-    // cluster per leaf: wider clusters split each leaf finer, which balances
-    // the chip when there are few leaves (measured best: 8 CTAs a leaf for 16
-    // leaves, 4 for 256, 1 from 1024 leaves on)
-    // (complex64 leaves are latency-bound: one CTA a leaf from 256 leaves on)
-    int lcs = 1;
-    while (lcs < 8 && NL * lcs < (lf ? 256 : 1024)) lcs *= 2;
-    if (const char *ev = getenv("HPS_LEAF_CLUSTER")) {
-      int v = atoi(ev);
-      if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) lcs = v;
-    }
-    // scratch for the in-place elimination: leaves go in chunks of at most
-    // ~1 GiB of matrices
-    const int chunk = (int)std::max<long long>(1, std::min<long long>(NL, (1LL << 30) / (esl * n * n)));
+    const int lcs = leaf_cluster(P0, NL);
+    if (lcs == 0) return HPS_ENOTSUP;
+    const int chunk = (int)leaf_chunk(P0, NL);
     void *lscr = nullptr;
     int *lmeta = nullptr;
-    CK(cudaMallocAsync(&lscr, (size_t)esl * chunk * n * n, st));
-    CK(cudaMallocAsync((void **)&lmeta, sizeof(int) * (size_t)chunk * hps::gj_meta_ints(n), st));
+    if (!P0.leaf_lu) CK(cudaMallocAsync(&lscr, (size_t)esl * chunk * n * n, st));
+    CK(cudaMallocAsync((void **)&lmeta,
+                       sizeof(int) * (size_t)chunk * (P0.leaf_lu ? hps::lu_meta_ints(n) : hps::gj_meta_ints(n)), st));
     if (events) CK(cudaEventRecord(ev[0], st));
     launches = 0;
     for (long long l0 = 0; l0 < NL; l0 += chunk) {
-      CK(hps::launch_leaf(lt, d_probs, K, l0, (int)std::min<long long>(chunk, NL - l0), base + oX, base + oGX,
-                          lscr, lmeta, d_status, Lmax, lcs, lf != 0, st));
+      const int cnt = (int)std::min<long long>(chunk, NL - l0);
+      if (P0.leaf_lu)
+        CK(hps::launch_leaf_lu(lt, d_probs, K, l0, cnt, base + oX, base + oGX, (int *)(base + oPerm),
+                               (double *)(base + oDsc), lmeta, d_status, Lmax, lcs, lf != 0, st));
+      else
+        CK(hps::launch_leaf(lt, d_probs, K, l0, cnt, base + oX, base + oGX, lscr, lmeta, d_status, Lmax, lcs,
+                            lf != 0, st));
       launches++;
     }
     if (events) CK(cudaEventRecord(ev[1], st));
-    CK(cudaFreeAsync(lscr, st));
+    if (lscr) CK(cudaFreeAsync(lscr, st));
     CK(cudaFreeAsync(lmeta, st));
 
     if (k1 < K) {
@@ -1538,18 +1587,8 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
   h->desc = *desc;
   if (h->desc.q == 0) h->desc.q = desc->p - 2;
   make_plan(h->desc, h->plan);
-  // leaf cluster: wider clusters split each leaf finer, which balances the
-  // chip when there are few leaves (measured best: 8 CTAs a leaf for 16
-  // leaves, 4 for 256, 1 from 1024 leaves on)
-  int cs = 1;
-  while (cs < 8 && (long long)h->plan.leaves * cs < (h->plan.leaf_f32 ? 256 : 1024)) cs *= 2;
-  if (const char *e = getenv("HPS_LEAF_CLUSTER")) {
-    int v = atoi(e);
-    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) cs = v;
-  }
-  h->leaf_cs = cs;
-  if (hps::gj_smem_bytes(h->plan.n, h->leaf_cs, true, h->plan.p, false, h->plan.leaf_f32) > 227 * 1024)
-    return HPS_ENOTSUP;
+  h->leaf_cs = leaf_cluster(h->plan, h->plan.leaves);
+  if (h->leaf_cs == 0) return HPS_ENOTSUP;
   fill_info(h->plan, h->info);
   for (const Level &L : h->plan.lv) {
     GJChoice g;
@@ -1560,9 +1599,10 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
   // transient build memory: the leaf elimination chunk, then the merge scratch
   const Plan &pl = h->plan;
   const long long esz = pl.leaf_f32 ? 8 : 16, n = pl.n;
-  const long long chunk = std::max<long long>(1, std::min<long long>(pl.leaves, (1LL << 30) / (esz * n * n)));
+  const long long chunk = leaf_chunk(pl, pl.leaves);
   h->info.build_launches += (int)((pl.leaves + chunk - 1) / chunk) - 1;  // leaf chunks
-  long long leaf_scr = esz * chunk * n * n + 4LL * chunk * (long long)hps::gj_meta_ints(pl.n);
+  long long leaf_scr = pl.leaf_lu ? 4LL * chunk * (long long)hps::lu_meta_ints(pl.n)
+                                  : esz * chunk * n * n + 4LL * chunk * (long long)hps::gj_meta_ints(pl.n);
   long long rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
   for (size_t j = 0; j < pl.lv.size(); j++) {
     const Level &L = pl.lv[j];
@@ -1626,7 +1666,8 @@ int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, vo
     if (st0) return st0;
     if (!c[k]) return HPS_EINVAL;
     if (descs[k].p != descs[0].p || descs[k].precision != descs[0].precision ||
-        descs[k].fp64_levels != descs[0].fp64_levels || descs[k].fp64_native != descs[0].fp64_native)
+        descs[k].fp64_levels != descs[0].fp64_levels || descs[k].fp64_native != descs[0].fp64_native ||
+        descs[k].leaf_form != descs[0].leaf_form)
       return HPS_EINVAL;
   }
   std::vector<hps_handle *> hs(nprob, nullptr);
@@ -1701,7 +1742,8 @@ int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned) {
     int st0 = check_desc(&descs[k]);
     if (st0) return st0;
     if (descs[k].p != descs[0].p || descs[k].precision != descs[0].precision ||
-        descs[k].fp64_levels != descs[0].fp64_levels || descs[k].fp64_native != descs[0].fp64_native)
+        descs[k].fp64_levels != descs[0].fp64_levels || descs[k].fp64_native != descs[0].fp64_native ||
+        descs[k].leaf_form != descs[0].leaf_form)
       return HPS_EINVAL;
   }
   std::vector<hps_handle> hv(nprob);
@@ -2111,35 +2153,70 @@ int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, v
   const int n = h->plan.n, nb = h->plan.nb, ni = h->plan.ni, lf = h->plan.leaf_f32;
   const void *X = elem(h->X, (long long)leaf * n * n, lf);
   const void *GX = elem(h->GX, (long long)leaf * n * nb, lf);
+  int xf = lf;  // precision of the B^{-1} read below
+  void *tmp = nullptr;
+  if (h->plan.leaf_lu && (Psi || Y)) {
+    // B^{-1} from the factors: the leaf's solve with the n unit vectors as
+    // right-hand sides ([t; s] = e_c), into a complex128 n x n scratch
+    const size_t cnt = (size_t)n * n;
+    std::vector<double2> eye(2 * cnt, make_double2(0.0, 0.0));
+    double2 *et = eye.data(), *es = et + (size_t)nb * n;
+    for (int c = 0; c < n; c++) {
+      if (c < nb)
+        et[(size_t)c * nb + c] = make_double2(1.0, 0.0);
+      else
+        es[(size_t)c * ni + (c - nb)] = make_double2(1.0, 0.0);
+    }
+    CK(cudaMallocAsync(&tmp, sizeof(double2) * 3 * cnt, st));
+    double2 *dt = (double2 *)tmp, *ds = dt + (size_t)nb * n, *dx = dt + 2 * cnt;
+    cudaError_t err = cudaMemcpyAsync(dt, eye.data(), sizeof(double2) * 2 * cnt, cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess)
+      err = hps::launch_lu_solve(X, h->lu_perm + (size_t)leaf * n, h->lu_dsc + (size_t)leaf * n, 1, n, nb, n,
+                                 dt, nb, 0, ds, ni, 0, dx, n, 0, lf != 0, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) {
+      cudaFreeAsync(tmp, st);
+      return cuda_fail(err);
+    }
+    X = dx;
+    xf = 0;
+  }
   struct Part {
     double *out;
     int rows, cols;
     const void *src;
     long long ld;
-  } parts[3] = {{Psi, n, nb, X, n}, {Y, n, ni, elem(X, (long long)nb * n, lf), n},
-                {Gam, nb, ni, elem(GX, (long long)nb * nb, lf), nb}};
+    int f32;
+  } parts[3] = {{Psi, n, nb, X, n, xf}, {Y, n, ni, elem(X, (long long)nb * n, xf), n, xf},
+                {Gam, nb, ni, elem(GX, (long long)nb * nb, lf), nb, lf}};
+  int rc = HPS_OK;
   for (const Part &pt : parts) {
+    if (rc != HPS_OK) break;
     if (!pt.out) continue;
     size_t bytes = sizeof(double2) * (size_t)pt.rows * pt.cols;
     const bool dev = is_device_ptr(pt.out);
     double2 *dst = (double2 *)pt.out;
     if (!dev) {
-      int gst = grow(&h->stage, &h->stage_bytes, bytes);
-      if (gst) return gst;
+      rc = grow(&h->stage, &h->stage_bytes, bytes);
+      if (rc) break;
       dst = (double2 *)h->stage;
     }
     // row-major out[i][j] = src(i, j): column-major (j, i) of dst = src(i, j)
     CopyBatch cb;
     cb.count = 1;
-    cb.d[0] = copy(pt.cols, pt.rows, 1, mat(pt.src, pt.ld, 0, nullptr, nullptr, lf), mat(dst, pt.cols, 0));
+    cb.d[0] = copy(pt.cols, pt.rows, 1, mat(pt.src, pt.ld, 0, nullptr, nullptr, pt.f32), mat(dst, pt.cols, 0));
     cb.d[0].trans = 1;
-    CK(hps::launch_copy(cb, st));
-    if (!dev) {
-      CK(cudaMemcpyAsync(pt.out, dst, bytes, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-    }
+    cudaError_t err = hps::launch_copy(cb, st);
+    if (err == cudaSuccess && !dev) err = cudaMemcpyAsync(pt.out, dst, bytes, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess && !dev) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) rc = cuda_fail(err);
   }
-  return HPS_OK;
+  if (tmp) {
+    cudaError_t err = cudaFreeAsync(tmp, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess && rc == HPS_OK) rc = cuda_fail(err);
+  }
+  return rc;
 }
 
 }  // extern "C"

@@ -113,6 +113,30 @@ cudaError_t launch_leaf(const LeafTables &lt, const LeafProb *probs, int nprob, 
                         int count, void *X, void *GX, void *S, int *meta, unsigned int *status,
                         int level, int cs, bool f32, cudaStream_t st);
 
+// Leaf step in factored form for leaves [leaf0, leaf0 + count): assemble
+// [D B; G], factor P D B = L U by blocked right-looking LU with partial
+// pivoting across a cluster of `cs` CTAs (the G rows eliminated along, never
+// pivots), then G B^{-1} by a triangular solve of the G rows.  Writes
+// X = L \ U ([leaf][n][n] column-major, unit diagonal of L implied),
+// GX = G B^{-1} ([leaf][n][nb] column-major), perm ([leaf][n]: row k of P D B
+// is row perm[k] of B) and dsc ([leaf][n]: d of row perm[k]).  X, GX and the
+// arithmetic are complex64 when f32.  meta: count * lu_meta_ints(n) ints.
+cudaError_t launch_leaf_lu(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0,
+                           int count, void *X, void *GX, int *perm, double *dsc, int *meta,
+                           unsigned int *status, int level, int cs, bool f32, cudaStream_t st);
+size_t lu_meta_ints(int n);
+size_t lu_leaf_smem_bytes(int n, int nb, int p, int cs, bool f32);
+
+// u = B^{-1} [t; s] for `leaves` leaves from their factors (launch_leaf_lu)
+// and R right-hand sides: element i < nb of the right-hand side c of leaf l
+// is t[c t_ld + l t_stride + i], element i >= nb is s[c s_ld + l s_stride +
+// i - nb]; u[c u_ld + l u_stride + i] receives the solution.  Vectors are
+// complex128; the sweeps run in the factors' precision.
+cudaError_t launch_lu_solve(const void *LU, const int *perm, const double *dsc, long long leaves, int n,
+                            int nb, int R, const double2 *t, long long t_ld, long long t_stride,
+                            const double2 *s, long long s_ld, long long s_stride, double2 *u,
+                            long long u_ld, long long u_stride, bool f32, cudaStream_t st);
+
 // Inverse of `batch` n x n column-major matrices (leading dim n, batch stride
 // n*n) by blocked Gauss-Jordan with partial pivoting across clusters of `cs`
 // CTAs.  S holds the matrices and is destroyed; the inverses go to out.  With

@@ -24,6 +24,8 @@ HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ETIMEOUT, HPS_ECUDA, HPS_ENOT
 HPS_NOALLOC_WORKSPACE_BYTES = 16 << 20
 HPS_FP64 = 0
 HPS_MIXED = 1
+HPS_LEAF_LU = 0
+HPS_LEAF_INVERSE = 1
 
 # every entry point include/hps.h declares
 EXPORTS = ("hps_nodes", "hps_build", "hps_build_batch", "hps_rebuild", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
@@ -41,6 +43,7 @@ class hps_desc(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("fp64_levels", ctypes.c_int), ("refine_steps", ctypes.c_int),
         ("fp64_native", ctypes.c_int),
+        ("leaf_form", ctypes.c_int),
     ]
 
 
@@ -118,6 +121,7 @@ class Problem:
     refine_steps: int = 0
     fp64_native: int = 0
     my: int = 0  # leaves along y (0: the same as m, the leaves along x)
+    leaf_form: int = HPS_LEAF_LU
 
     @property
     def ny(self) -> int:
@@ -127,7 +131,8 @@ class Problem:
         eta = complex(self.eta)
         return hps_desc(self.x0, self.x1, self.y0, self.y1, self.m, self.ny, self.p, self.p - 2,
                         float(self.kappa), eta.real, eta.imag, int(self.precision),
-                        int(self.fp64_levels), int(self.refine_steps), int(self.fp64_native))
+                        int(self.fp64_levels), int(self.refine_steps), int(self.fp64_native),
+                        int(self.leaf_form))
 
     @property
     def n(self) -> int:

@@ -62,7 +62,8 @@ def _desc(**kw):
     dict(mx=3, my=3), dict(mx=4, my=3), dict(mx=2048, my=2), dict(mx=0, my=0), dict(p=3), dict(p=33), dict(q=5),
     dict(kappa=0.0), dict(kappa=-1.0), dict(eta_re=0.0, eta_im=1.0), dict(x1=0.0),
     dict(y1=-1.0), dict(precision=7), dict(precision=-1), dict(kappa=float("nan")),
-    dict(precision=1, fp64_levels=-2), dict(fp64_native=2), dict(fp64_native=-1),
+    dict(precision=1, fp64_levels=-2), dict(fp64_native=2), dict(fp64_native=-1), dict(leaf_form=2),
+    dict(leaf_form=-1),
 ])
 def test_invalid_descriptor_is_rejected_before_device_work(bad):
     d = _desc(**bad)

@@ -31,9 +31,13 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-def _pair(m, p, kappa, eta, domain=(0.0, 1.0, 0.0, 1.0)):
+FORMS = [hps.HPS_LEAF_LU, hps.HPS_LEAF_INVERSE]
+
+
+def _pair(m, p, kappa, eta, domain=(0.0, 1.0, 0.0, 1.0), leaf_form=hps.HPS_LEAF_LU):
     x0, x1, y0, y1 = domain
-    return (hps.Problem(m, p, kappa, eta, x0, x1, y0, y1), O.Problem(m, p, kappa, eta, x0, x1, y0, y1))
+    return (hps.Problem(m, p, kappa, eta, x0, x1, y0, y1, leaf_form=leaf_form),
+            O.Problem(m, p, kappa, eta, x0, x1, y0, y1))
 
 
 def gpu_build(pr, c):
@@ -63,9 +67,11 @@ def gpu_root_R(h):
     return R
 
 
-@pytest.mark.parametrize("m,p,kappa,eta", [(1, 8, 7.0, 3.0 + 1.0j), (2, 16, 30.0, 30.0), (4, 12, 20.0, 20.0)])
-def test_leaf_operators(m, p, kappa, eta):
-    pr, opr = _pair(m, p, kappa, eta, (0.0, 1.0, 0.0, 0.5))
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("m,p,kappa,eta", [(1, 8, 7.0, 3.0 + 1.0j), (2, 16, 30.0, 30.0), (4, 12, 20.0, 20.0),
+                                           (2, 7, 9.0, 4.0)])
+def test_leaf_operators(m, p, kappa, eta, form):
+    pr, opr = _pair(m, p, kappa, eta, (0.0, 1.0, 0.0, 0.5), form)
     c, _, _ = W.random_data(m, p, kappa, eta, seed=31)
     h = gpu_build(pr, c)
     for leaf in range(pr.leaves):
@@ -91,8 +97,9 @@ def test_leaf_operators(m, p, kappa, eta):
         (8, 16, 40.0, 40.0, (0.0, 1.0, 0.0, 1.0), 5),
     ],
 )
-def test_solution_and_root_operator(m, p, kappa, eta, domain, nrhs):
-    pr, opr = _pair(m, p, kappa, eta, domain)
+@pytest.mark.parametrize("form", FORMS)
+def test_solution_and_root_operator(m, p, kappa, eta, domain, nrhs, form):
+    pr, opr = _pair(m, p, kappa, eta, domain, form)
     c, s, t = W.random_data(m, p, kappa, eta, seed=m * 100 + p, nrhs=nrhs)
     h = gpu_build(pr, c)
     u = gpu_solve(h, s, t)
@@ -264,3 +271,57 @@ def test_rectangular_grid_polynomial_and_mixed_path():
         u = gpu_solve(h, s[None], t[None])[0]
         assert _rel(u, wl.u_exact(lxy[..., 0], lxy[..., 1])) < tol, prec
         h.free()
+
+
+@pytest.mark.parametrize("cs", ["1", "2", "4", "8", "16"])
+def test_leaf_lu_every_cluster_size(cs, monkeypatch):
+    """The LU leaf kernel with each cluster width (panels dealt round-robin to
+    1 .. 16 CTAs, the last panel of n = 252 ragged) against the oracle, with
+    R = 40 right-hand sides (solve tiles of 16, 16 and a ragged 8)."""
+    monkeypatch.setenv("HPS_LEAF_CLUSTER", cs)
+    m, p, kappa, eta = 2, 16, 25.0, 25.0 - 3.0j
+    pr, opr = _pair(m, p, kappa, eta)
+    c, s, t = W.random_data(m, p, kappa, eta, seed=77, nrhs=40)
+    h = gpu_build(pr, c)
+    u = gpu_solve(h, s, t)
+    R = gpu_root_R(h)
+    with O.Tree(opr, c, nthreads=os.cpu_count() or 1) as T:
+        uo = T.solve(s, t, nthreads=os.cpu_count() or 1)
+        Ro = T.root_R()
+    assert _rel(u, uo) < TOL
+    assert _rel(R, Ro) < TOL
+    h.free()
+
+
+@pytest.mark.parametrize("p", [4, 5, 9, 20, 24])
+def test_leaf_lu_orders(p):
+    """Leaf orders whose n = p^2 - 4 leaves every kind of ragged last panel
+    (12, 21, 77, 396, 572) and the largest leaf the kernels take."""
+    m, kappa, eta = 2, 6.0 + p, 5.0 + 1.0j
+    pr, opr = _pair(m, p, kappa, eta, (0.0, 1.0, 0.0, 0.75))
+    c, s, t = W.random_data(m, p, kappa, eta, seed=p, nrhs=2)
+    h = gpu_build(pr, c)
+    u = gpu_solve(h, s, t)
+    R = gpu_root_R(h)
+    with O.Tree(opr, c, nthreads=os.cpu_count() or 1) as T:
+        uo = T.solve(s, t, nthreads=os.cpu_count() or 1)
+        Ro = T.root_R()
+    assert _rel(u, uo) < TOL
+    assert _rel(R, Ro) < TOL
+    h.free()
+
+
+def test_leaf_forms_agree_on_the_bench_problem():
+    """16 x 16 leaves, p = 16, kappa = 80: the factored and the inverse leaf
+    forms give the same solution and root operator (both FP64)."""
+    wl = W.point_sources(16, 16, 80.0)
+    out = []
+    for form in FORMS:
+        pr = hps.Problem(16, 16, 80.0, 80.0, leaf_form=form)
+        lxy, bxy = hps.hps_nodes(pr)
+        c, s, t = wl.sample(lxy, bxy)
+        h = gpu_build(pr, c)
+        out.append((gpu_solve(h, s[None], t[None]), gpu_root_R(h)))
+        h.free()
+    assert _rel(out[0][0], out[1][0]) < TOL
+    assert _rel(out[0][1], out[1][1]) < TOL
