@@ -458,8 +458,10 @@ int leaf_cluster(const Plan &pl, long long NL) {
     return pl.leaf_lu ? hps::lu_leaf_smem_bytes(pl.n, pl.nb, pl.p, cs, f32)
                       : hps::gj_smem_bytes(pl.n, cs, true, pl.p, false, f32);
   };
+  // (LU, measured: 2 CTAs a leaf for 256 and for 4096 leaves; 1 CTA a leaf
+  // would hold only one CTA an SM)
   int cs = 1;
-  while (cs < 8 && NL * cs < (f32 ? 256 : 1024)) cs *= 2;
+  while (cs < 8 && NL * cs < (f32 ? 256 : pl.leaf_lu ? 512 : 1024)) cs *= 2;
   if (pl.leaf_lu)
     while (cs < 8 && smem(cs) > 113 * 1024 && smem(2 * cs) <= 113 * 1024) cs *= 2;
   if (const char *e = getenv("HPS_LEAF_CLUSTER")) {

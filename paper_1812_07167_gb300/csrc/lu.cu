@@ -586,6 +586,31 @@ struct LuSolveArgs {
 
 constexpr int kSB = 32;  // rows of a diagonal block of the sweeps
 
+// y[i] -= sum_{kk < jb} A(i, J0 + kk) y[J0 + kk] for the RB right-hand sides,
+// a = &A(i, J0) (column-major, ld n).  The factor entries are loaded KC at a
+// time ahead of their multiply-adds, so a thread has KC loads in flight (the
+// sweeps of a 1-RHS solve wait on memory, not on arithmetic).
+template <class C, int RB>
+__device__ __forceinline__ void sweep_row(C *y, const C *a, int n, int J0, int jb, int i) {
+  constexpr int KC = RB <= 1 ? 16 : RB <= 4 ? 8 : 4;
+  C acc[RB];
+#pragma unroll
+  for (int c = 0; c < RB; c++) acc[c] = y[i * RB + c];
+  for (int k0 = 0; k0 < jb; k0 += KC) {
+    C l[KC];
+#pragma unroll
+    for (int u = 0; u < KC; u++) l[u] = (k0 + u < jb) ? __ldg(a + (size_t)(k0 + u) * n) : CX<C>::make(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < KC; u++) {
+      if (k0 + u >= jb) break;
+#pragma unroll
+      for (int c = 0; c < RB; c++) acc[c] = cfms(acc[c], l[u], y[(J0 + k0 + u) * RB + c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < RB; c++) y[i * RB + c] = acc[c];
+}
+
 // One CTA per (leaf, RB right-hand sides): y = P D b in shared memory, then
 // the forward sweep with L and the backward sweep with U in blocks of 32
 // rows: a warp solves the diagonal block for one right-hand side with
@@ -623,9 +648,10 @@ __global__ void __launch_bounds__(kThreads, 2) lu_solve_kernel(const __grid_cons
   // forward: L y = P D b
   for (int J0 = 0; J0 < n; J0 += kSB) {
     const int jb = min(kSB, n - J0);
+#pragma unroll 4
     for (int t = tid; t < jb * kSB; t += nthr) {
       const int kk = t / kSB, i = t % kSB;
-      if (i < jb) Db[kk * (kSB + 1) + i] = LU[(size_t)(J0 + kk) * n + J0 + i];
+      if (i < jb) Db[kk * (kSB + 1) + i] = __ldg(&LU[(size_t)(J0 + kk) * n + J0 + i]);
     }
     __syncthreads();
     for (int c = wid; c < nc; c += nw) {
@@ -639,27 +665,17 @@ __global__ void __launch_bounds__(kThreads, 2) lu_solve_kernel(const __grid_cons
       if (lane < jb) y[(J0 + lane) * RB + c] = yv;
     }
     __syncthreads();
-    for (int i = J0 + jb + tid; i < n; i += nthr) {
-      C acc[RB];
-#pragma unroll
-      for (int c = 0; c < RB; c++) acc[c] = y[i * RB + c];
-      for (int kk = 0; kk < jb; kk++) {
-        const C l = LU[(size_t)(J0 + kk) * n + i];
-#pragma unroll
-        for (int c = 0; c < RB; c++) acc[c] = cfms(acc[c], l, y[(J0 + kk) * RB + c]);
-      }
-#pragma unroll
-      for (int c = 0; c < RB; c++) y[i * RB + c] = acc[c];
-    }
+    for (int i = J0 + jb + tid; i < n; i += nthr) sweep_row<C, RB>(y, LU + (size_t)J0 * n + i, n, J0, jb, i);
     __syncthreads();
   }
   // backward: U x = y
   const int nblk = (n + kSB - 1) / kSB;
   for (int b = nblk - 1; b >= 0; b--) {
     const int J0 = b * kSB, jb = min(kSB, n - J0);
+#pragma unroll 4
     for (int t = tid; t < jb * kSB; t += nthr) {
       const int kk = t / kSB, i = t % kSB;
-      if (i < jb) Db[kk * (kSB + 1) + i] = LU[(size_t)(J0 + kk) * n + J0 + i];
+      if (i < jb) Db[kk * (kSB + 1) + i] = __ldg(&LU[(size_t)(J0 + kk) * n + J0 + i]);
     }
     __syncthreads();
     if (tid < jb) dinv[tid] = crecip(Db[tid * (kSB + 1) + tid]);
@@ -676,18 +692,7 @@ __global__ void __launch_bounds__(kThreads, 2) lu_solve_kernel(const __grid_cons
       if (lane < jb) y[(J0 + lane) * RB + c] = yv;
     }
     __syncthreads();
-    for (int i = tid; i < J0; i += nthr) {
-      C acc[RB];
-#pragma unroll
-      for (int c = 0; c < RB; c++) acc[c] = y[i * RB + c];
-      for (int kk = 0; kk < jb; kk++) {
-        const C uv = LU[(size_t)(J0 + kk) * n + i];
-#pragma unroll
-        for (int c = 0; c < RB; c++) acc[c] = cfms(acc[c], uv, y[(J0 + kk) * RB + c]);
-      }
-#pragma unroll
-      for (int c = 0; c < RB; c++) y[i * RB + c] = acc[c];
-    }
+    for (int i = tid; i < J0; i += nthr) sweep_row<C, RB>(y, LU + (size_t)J0 * n + i, n, J0, jb, i);
     __syncthreads();
   }
   for (int idx = tid; idx < n * nc; idx += nthr) {
