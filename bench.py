@@ -636,7 +636,11 @@ def serving_run(args, local_rank, precision):
 
     dev = torch.device("cuda", local_rank)
     m, p, kappa = args.serve_m, P_ORDER, 600.0
-    pr = _problem(m, p, kappa, kappa, precision=precision)
+    # the resident solver only solves (wide batches): leaf operators as B^-1,
+    # whose product runs on the tensor cores; the build requests take the
+    # leaf form given on the command line (LU by default, the faster build)
+    pr = hps.Problem(m, p, kappa, kappa, precision=precision,
+                     leaf_form=hps.HPS_LEAF_INVERSE if args.serve_resident_form == "inverse" else hps.HPS_LEAF_LU)
     lxy, _ = hps.hps_nodes(pr)
     nb = pr.nb
     xi, yi = lxy[:, nb:, 0], lxy[:, nb:, 1]
@@ -689,7 +693,8 @@ def serving_run(args, local_rank, precision):
     srv.run(warm, on_done=drop)
     srv.release_built()
     torch.cuda.synchronize()
-    res = {"resident_build_s": build_s, "resident_operator_bytes": h.info().operator_bytes}
+    res = {"resident_build_s": build_s, "resident_operator_bytes": h.info().operator_bytes,
+           "resident_leaf_form": args.serve_resident_form, "build_leaf_form": args.leaf_form}
     backlog = srv.run(make(0.0), on_done=drop)
     srv.release_built()
     cap = serve.summarize(backlog)
@@ -751,6 +756,8 @@ def main():
     ap.add_argument("--no-batching", action="store_true", help="skip the ragged-batch section")
     ap.add_argument("--leaf-form", default="lu", choices=["lu", "inverse"],
                     help="leaf operators as LU factors (default) or as B^-1")
+    ap.add_argument("--serve-resident-form", default="inverse", choices=["lu", "inverse"],
+                    help="--serve: leaf form of the resident solver (its requests are wide solves)")
     ap.add_argument("--zgemm", type=int, nargs=3, metavar=("M", "N", "K"),
                     help="time one complex GEMM on the tensor cores and on the FP64 pipes")
     ap.add_argument("--serve-m", type=int, default=128)

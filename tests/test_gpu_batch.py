@@ -44,10 +44,10 @@ def _root(h):
     return R
 
 
-def _problems(spec, p, precision=hps.HPS_FP64):
+def _problems(spec, p, precision=hps.HPS_FP64, leaf_form=hps.HPS_LEAF_LU):
     probs, cs = [], []
     for k, (m, kappa, eta, dom) in enumerate(spec):
-        probs.append(hps.Problem(m, p, kappa, eta, *dom, precision=precision))
+        probs.append(hps.Problem(m, p, kappa, eta, *dom, precision=precision, leaf_form=leaf_form))
         c, _, _ = W.random_data(m, p, kappa, eta, seed=500 + k)
         cs.append(c)
     return probs, cs
@@ -69,11 +69,12 @@ def _check_against_alone(probs, cs, tol, nrhs=2, tol_R=None):
     return hb
 
 
-def test_ragged_fp64_batch_matches_separate_builds():
+@pytest.mark.parametrize("form", [hps.HPS_LEAF_LU, hps.HPS_LEAF_INVERSE])
+def test_ragged_fp64_batch_matches_separate_builds(form):
     spec = [(4, 20.0, 20.0, (0, 1, 0, 1)), (1, 7.0, 3.0 + 1.0j, (0, 1, 0, 0.5)),
             (8, 30.0, 30.0, (0, 1, 0, 1)), (2, 9.0, 9.0 - 2.0j, (-1, 1, 0, 1)),
             (4, 15.0, 6.0, (0, 2, 0, 1)), (8, 25.0, 25.0, (0, 1, 0, 1))]
-    probs, cs = _problems(spec, 12)
+    probs, cs = _problems(spec, 12, leaf_form=form)
     hb = _check_against_alone(probs, cs, 1e-12)
     for h in hb:
         h.free()
@@ -149,11 +150,16 @@ def test_batch_argument_errors():
     with pytest.raises(hps.HPSError) as e:
         hps.hps_build_batch(probs, [np.ones((4, 36))] * 2)
     assert e.value.code == hps.HPS_EINVAL
+    probs = [hps.Problem(2, 8, 5.0, 5.0), hps.Problem(2, 8, 5.0, 5.0, leaf_form=hps.HPS_LEAF_INVERSE)]
+    with pytest.raises(hps.HPSError) as e:
+        hps.hps_build_batch(probs, [np.ones((4, 36))] * 2)
+    assert e.value.code == hps.HPS_EINVAL
 
 
-@pytest.mark.parametrize("m,precision", [(1, 0), (4, 0), (16, 0), (64, 0), (16, 1), (64, 1)])
-def test_planned_launch_count_is_what_the_build_launches(m, precision):
-    pr = hps.Problem(m, 16, 40.0, 40.0, precision=precision)
+@pytest.mark.parametrize("m,precision,form", [(1, 0, 0), (4, 0, 0), (16, 0, 0), (64, 0, 0), (16, 1, 0), (64, 1, 0),
+                                              (16, 0, 1), (64, 1, 1)])
+def test_planned_launch_count_is_what_the_build_launches(m, precision, form):
+    pr = hps.Problem(m, 16, 40.0, 40.0, precision=precision, leaf_form=form)
     c, _, _ = W.random_data(m, 16, 40.0, 40.0, seed=2)
     h = hps.hps_build(pr, torch.from_numpy(c).cuda(), torch.cuda.current_stream())
     assert h.info().build_launches == hps.hps_plan(pr).build_launches
@@ -175,14 +181,16 @@ def test_batch_with_rectangular_members():
     assert e.value.code == hps.HPS_EINVAL
 
 
-@pytest.mark.parametrize("precision", [hps.HPS_FP64, hps.HPS_MIXED])
-def test_rebuild_replays_the_build_as_a_graph(precision):
+@pytest.mark.parametrize("precision,form", [(hps.HPS_FP64, hps.HPS_LEAF_LU), (hps.HPS_MIXED, hps.HPS_LEAF_LU),
+                                            (hps.HPS_FP64, hps.HPS_LEAF_INVERSE)])
+def test_rebuild_replays_the_build_as_a_graph(precision, form):
     """hps_rebuild with new coefficients gives the operators of a fresh build
     with those coefficients (first call captures the graph, later ones
     replay it), for a single build and for a batch."""
     st = torch.cuda.current_stream()
-    probs = [hps.Problem(4, 10, 14.0, 14.0, precision=precision), hps.Problem(8, 10, 20.0, 20.0, precision=precision),
-             hps.Problem(2, 10, 9.0, 9.0, precision=precision)]
+    probs = [hps.Problem(4, 10, 14.0, 14.0, precision=precision, leaf_form=form),
+             hps.Problem(8, 10, 20.0, 20.0, precision=precision, leaf_form=form),
+             hps.Problem(2, 10, 9.0, 9.0, precision=precision, leaf_form=form)]
     c0 = [W.random_data(pr.m, 10, pr.kappa, pr.kappa, seed=60 + k)[0] for k, pr in enumerate(probs)]
     hb = hps.hps_build_batch(probs, c0, st)
     for rnd in range(3):
@@ -192,7 +200,7 @@ def test_rebuild_replays_the_build_as_a_graph(precision):
         hps.hps_rebuild([hb[i] for i in perm], [torch.from_numpy(cn[i]).cuda() for i in perm], st)
         assert hps.hps_status(hb[0], st)[0] == hps.HPS_OK
         for k, pr in enumerate(probs):
-            ha = hps.hps_build(pr, cn[k], st)
+            ha = hps.hps_build(pr, cn[k], st)  # pr carries the same leaf form
             _, s, t = W.random_data(pr.m, 10, pr.kappa, pr.kappa, seed=5 + k, nrhs=2)
             tol = 1e-12 if precision == hps.HPS_FP64 else 1e-9
             assert _rel(_solve(hb[k], s, t), _solve(ha, s, t)) < tol, (rnd, k)

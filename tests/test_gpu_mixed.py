@@ -51,17 +51,18 @@ def _solve(h, s, t):
     return ud.cpu().numpy()
 
 
-def _mixed(m, p, kappa, eta, fp64_levels=0, refine_steps=0):
+def _mixed(m, p, kappa, eta, fp64_levels=0, refine_steps=0, leaf_form=hps.HPS_LEAF_LU):
     return hps.Problem(m, p, kappa, eta, precision=hps.HPS_MIXED, fp64_levels=fp64_levels,
-                       refine_steps=refine_steps)
+                       refine_steps=refine_steps, leaf_form=leaf_form)
 
 
-@pytest.mark.parametrize("m,p,kappa,fp64_levels,nrhs", [
-    (2, 10, 15.0, 0, 1), (4, 16, 20.0, 0, 2), (8, 12, 30.0, 0, 3), (8, 16, 40.0, 1, 1), (16, 16, 80.0, 4, 12),
+@pytest.mark.parametrize("m,p,kappa,fp64_levels,nrhs,form", [
+    (2, 10, 15.0, 0, 1, 0), (4, 16, 20.0, 0, 2, 0), (8, 12, 30.0, 0, 3, 0), (8, 16, 40.0, 1, 1, 0),
+    (16, 16, 80.0, 4, 12, 0), (4, 16, 20.0, 0, 2, 1), (16, 16, 80.0, 4, 40, 1), (16, 16, 80.0, 4, 40, 0),
 ])
-def test_mixed_matches_oracle(m, p, kappa, fp64_levels, nrhs):
+def test_mixed_matches_oracle(m, p, kappa, fp64_levels, nrhs, form):
     c, s, t = W.random_data(m, p, kappa, kappa, seed=700 + m + p, nrhs=nrhs)
-    h = _build(_mixed(m, p, kappa, kappa, fp64_levels), c)
+    h = _build(_mixed(m, p, kappa, kappa, fp64_levels, leaf_form=form), c)
     u = _solve(h, s, t)
     nt = os.cpu_count() or 1
     with O.Tree(O.Problem(m, p, kappa, kappa), c, nthreads=nt) as T:
