@@ -43,14 +43,23 @@ namespace hps {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int KB = 8;           // panel width
-constexpr int kMoves = 2 * KB;  // row moves of one panel, at most
-constexpr int kMoveInts = 1 + 2 * kMoves;
+// The panel width KB is a template parameter: 8 where the elimination is
+// FP64-throughput-bound (the leaf, levels with many matrices), 4 where the
+// serial panel chain is the critical path (few, large interface matrices:
+// half the FP64 work a panel on the owning CTA, twice the barriers).  A
+// panel's swaps make at most 2 KB row moves, listed in 1 + 2 (2 KB) ints.
+template <int KB>
+struct Pn {
+  static constexpr int kMoves = 2 * KB;
+  static constexpr int kMoveInts = 1 + 2 * kMoves;
+};
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+template <int KB>
 __host__ __device__ inline int npanels(int n) { return (n + KB - 1) / KB; }
 // ints of per-matrix bookkeeping: pivot rows, then the row moves of each panel
-__host__ __device__ inline int meta_ints(int n) { return n + npanels(n) * kMoveInts; }
+template <int KB>
+__host__ __device__ inline int meta_ints(int n) { return n + npanels<KB>(n) * Pn<KB>::kMoveInts; }
 
 struct SmemPlan {
   size_t T, F, x, mvbuf, col, prow, krow, red, mv, rows, srcs, scal, pinv, perm, dtab, grid, loc, cv, rsc, total;
@@ -59,8 +68,10 @@ struct SmemPlan {
 // Panel placement: 0 = the panel being applied (T) and the one being
 // eliminated (F) both in shared memory, 1 = both read in place from the
 // global scratch, 2 = T in place and F in shared memory.
+template <int KB>
 __host__ __device__ inline SmemPlan plan_smem(int n, int cw, bool leaf, int p, int tmode = 0,
                                                size_t esz = 16) {
+  constexpr int kMoves = Pn<KB>::kMoves, kMoveInts = Pn<KB>::kMoveInts;
   SmemPlan s;
   size_t o = 0;
   s.T = o;    if (tmode == 0) o = align16(o + esz * (size_t)KB * n);
@@ -140,8 +151,9 @@ __device__ Shared<C> bind(unsigned char *smem, const SmemPlan &sp, int n, int cw
 // each pivot; with kLong (long columns) every warp searches a share of the
 // rows and the pivot row is staged beside the pivot column (four barriers
 // a step either way).
-template <class C, bool kLong = false>
+template <class C, int KB, bool kLong = false>
 __device__ bool eliminate_panel(const Shared<C> &s, C *S, int *meta, int k0, int kbp) {
+  constexpr int kMoveInts = Pn<KB>::kMoveInts;
   const int tid = threadIdx.x, nthr = blockDim.x, n = s.n;
   bool zero = false;
   // work on a shared-memory copy of the panel, or in place in S when the
@@ -362,9 +374,10 @@ __device__ __forceinline__ bool skipped(int j, int a0, int a1, int b0, int b1) {
 // CU columns go through the update together (more loads in flight; the
 // panel values are read once for all of them): 4 for complex64, whose
 // update is short and latency-bound, 1 for complex128.
-template <class C, int CU = (sizeof(C) == 8 ? 4 : 1)>
+template <class C, int KB, int CU = (sizeof(C) == 8 ? 4 : 1)>
 __device__ void apply_panel(const Shared<C> &s, const C *T, C *S, int c0, int ja, int jb,
                             int a0, int a1, int b0, int b1, int k0, int kbp) {
+  constexpr int kMoves = Pn<KB>::kMoves;
   const int tid = threadIdx.x, nthr = blockDim.x, n = s.n, cw = s.cw;
   const int nm = s.mv[0];
   // 1) row moves (all loads, then all stores, staged in shared memory), then
@@ -471,14 +484,15 @@ __device__ void apply_panel(const Shared<C> &s, const C *T, C *S, int c0, int ja
 }
 
 // The blocked Gauss-Jordan sweep over the matrix S of this cluster.
-template <class C>
+template <class C, int KB>
 __device__ bool gj_blocked(const Shared<C> &s, C *S, int *meta, int rank) {
+  constexpr int kMoveInts = Pn<KB>::kMoveInts;
   const int n = s.n, cw = s.cw, c0 = rank * cw;
   const int ncols = max(0, min(cw, n - c0));
-  const int np = npanels(n);
+  const int np = npanels<KB>(n);
   bool zero = false;
   // prologue: the owner of panel 0 eliminates it
-  if (0 >= c0 && 0 < c0 + ncols) zero |= eliminate_panel(s, S, meta, 0, min(KB, n));
+  if (0 >= c0 && 0 < c0 + ncols) zero |= eliminate_panel<C, KB>(s, S, meta, 0, min(KB, n));
   __threadfence();
   cluster_arrive();
   cluster_wait();
@@ -494,14 +508,14 @@ __device__ bool gj_blocked(const Shared<C> &s, C *S, int *meta, int rank) {
     const bool next_mine = (kbn > 0) && kn0 >= c0 && kn0 < c0 + ncols;
     if (next_mine) {
       // the next panel's columns first, then eliminate it and publish
-      apply_panel(s, T, S, c0, kn0 - c0, kn0 - c0 + kbn, k0, k0 + kbp, 0, 0, k0, kbp);
-      zero |= eliminate_panel(s, S, meta, kn0, kbn);
+      apply_panel<C, KB>(s, T, S, c0, kn0 - c0, kn0 - c0 + kbn, k0, k0 + kbp, 0, 0, k0, kbp);
+      zero |= eliminate_panel<C, KB>(s, S, meta, kn0, kbn);
       __threadfence();
       cluster_arrive();
-      apply_panel(s, T, S, c0, 0, ncols, k0, k0 + kbp, kn0, kn0 + kbn, k0, kbp);
+      apply_panel<C, KB>(s, T, S, c0, 0, ncols, k0, k0 + kbp, kn0, kn0 + kbn, k0, kbp);
       cluster_wait();
     } else {
-      apply_panel(s, T, S, c0, 0, ncols, k0, k0 + kbp, 0, 0, k0, kbp);
+      apply_panel<C, KB>(s, T, S, c0, 0, ncols, k0, k0 + kbp, 0, 0, k0, kbp);
       cluster_arrive();
       cluster_wait();
     }
@@ -525,6 +539,8 @@ __device__ __forceinline__ int dest_col(const int *perm, int n, int j) {
   }
   return loc;
 }
+
+constexpr int kLeafKB = 8;  // the leaf elimination is FP64-throughput-bound
 
 struct LeafArgs {
   LeafTables lt;
@@ -568,7 +584,7 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
   const int p = a.lt.p, e = a.lt.e, n = a.lt.n, nb = a.lt.nb, ni = a.lt.ni;
   const int cw = a.cw, c0 = rank * cw;
   const int ncols = max(0, min(cw, n - c0));
-  const SmemPlan sp = plan_smem(n, cw, true, p, false, sizeof(C));
+  const SmemPlan sp = plan_smem<kLeafKB>(n, cw, true, p, false, sizeof(C));
   const Shared<C> s = bind<C>(smem, sp, n, cw);
   double *D1x = (double *)(smem + sp.dtab);
   double *D1y = D1x + p * p, *D2x = D1y + p * p, *D2y = D2x + p * p;
@@ -577,7 +593,7 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
   double *cv = (double *)(smem + sp.cv);
   const int tid = threadIdx.x, nthr = blockDim.x;
   C *S = (C *)a.S + (size_t)slot * n * n;
-  int *meta = a.meta + (size_t)slot * meta_ints(n);
+  int *meta = a.meta + (size_t)slot * meta_ints<kLeafKB>(n);
 
   for (int i = tid; i < 4 * p * p; i += nthr) D1x[i] = tab[i];
   const int *gsrc = (const int *)(tab + 4 * p * p);
@@ -615,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
   }
   __syncthreads();
 
-  const bool zero = gj_blocked<C>(s, S, meta, rank);
+  const bool zero = gj_blocked<C, kLeafKB>(s, S, meta, rank);
   if (zero && tid == 0) record_status(a.status, 1u, a.level, (int)leaf);
 
   // X = (D B)^{-1} D: own columns to their destination columns, scaled
@@ -677,7 +693,7 @@ struct GJArgs {
   int level;
 };
 
-template <class C>
+template <class C, int KB>
 __global__ void __launch_bounds__(kThreads, 2) gj_kernel(const __grid_constant__ GJArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -686,11 +702,11 @@ __global__ void __launch_bounds__(kThreads, 2) gj_kernel(const __grid_constant__
   const int mat = blockIdx.x / cs;
   const int n = a.n, cw = a.cw, c0 = rank * cw;
   const int ncols = max(0, min(cw, n - c0));
-  const SmemPlan sp = plan_smem(n, cw, false, 0, a.tglobal, sizeof(C));
+  const SmemPlan sp = plan_smem<KB>(n, cw, false, 0, a.tglobal, sizeof(C));
   const Shared<C> s = bind<C>(smem, sp, n, cw);
   C *S = (C *)a.S + (size_t)mat * n * n;
-  int *meta = a.meta + (size_t)mat * meta_ints(n);
-  const bool zero = gj_blocked<C>(s, S, meta, rank);
+  int *meta = a.meta + (size_t)mat * meta_ints<KB>(n);
+  const bool zero = gj_blocked<C, KB>(s, S, meta, rank);
   if (zero && threadIdx.x == 0) record_status(a.status, 2u, a.level, mat);
   C *O = (C *)a.out + (size_t)mat * n * n;
   for (int idx = threadIdx.x; idx < n * ncols; idx += blockDim.x) {
@@ -717,24 +733,25 @@ struct WideArgs {
   int level;
 };
 
-template <class C>
+template <class C, int KB>
 __global__ void __launch_bounds__(kThreads, 2) gj_wide_kernel(const __grid_constant__ WideArgs a, int phase) {
+  constexpr int kMoveInts = Pn<KB>::kMoveInts;
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n, G = a.G;
   const int mat = blockIdx.x / G, g = blockIdx.x % G;
   const int cwmax = a.slab > KB ? a.slab : KB;
-  const SmemPlan sp = plan_smem(n, cwmax, false, 0, a.tglobal, sizeof(C));
+  const SmemPlan sp = plan_smem<KB>(n, cwmax, false, 0, a.tglobal, sizeof(C));
   const Shared<C> s = bind<C>(smem, sp, n, cwmax);
   C *S = (C *)a.S + (size_t)mat * n * n;
-  int *meta = a.meta + (size_t)mat * meta_ints(n);
-  const int np = npanels(n);
+  int *meta = a.meta + (size_t)mat * meta_ints<KB>(n);
+  const int np = npanels<KB>(n);
   // slab of CTA g >= 1: columns [c0, c0 + slab) of the matrix
   const int c0 = (g - 1) * a.slab;
   const int nc = (g >= 1) ? max(0, min(a.slab, n - c0)) : 0;
   if (phase < 0) {
     if (g == 0) {
-      const bool z = (n > 512) ? eliminate_panel<C, true>(s, S, meta, 0, min(KB, n))
-                               : eliminate_panel<C, false>(s, S, meta, 0, min(KB, n));
+      const bool z = (n > 512) ? eliminate_panel<C, KB, true>(s, S, meta, 0, min(KB, n))
+                               : eliminate_panel<C, KB, false>(s, S, meta, 0, min(KB, n));
       if (z && threadIdx.x == 0) record_status(a.status, 2u, a.level, mat);
     }
     return;
@@ -759,13 +776,13 @@ __global__ void __launch_bounds__(kThreads, 2) gj_wide_kernel(const __grid_const
   __syncthreads();
   if (g == 0) {
     if (kbn > 0) {
-      apply_panel<C>(s, T, S, kn0, 0, kbn, k0, k0 + kbp, 0, 0, k0, kbp);
-      const bool z = (n > 512) ? eliminate_panel<C, true>(s, S, meta, kn0, kbn)
-                               : eliminate_panel<C, false>(s, S, meta, kn0, kbn);
+      apply_panel<C, KB>(s, T, S, kn0, 0, kbn, k0, k0 + kbp, 0, 0, k0, kbp);
+      const bool z = (n > 512) ? eliminate_panel<C, KB, true>(s, S, meta, kn0, kbn)
+                               : eliminate_panel<C, KB, false>(s, S, meta, kn0, kbn);
       if (z && threadIdx.x == 0) record_status(a.status, 2u, a.level, mat);
     }
   } else if (nc > 0) {
-    apply_panel<C>(s, T, S, c0, 0, nc, k0, k0 + kbp, kn0, kn0 + kbn, k0, kbp);
+    apply_panel<C, KB>(s, T, S, c0, 0, nc, k0, k0 + kbp, kn0, kn0 + kbn, k0, kbp);
   }
 }
 
@@ -798,23 +815,75 @@ cudaError_t launch_cluster(Kern kern, const Args &args, int blocks, int cs, size
 
 int gj_max_cluster() { return 16; }
 
-int gj_slab(int n, int cs) {
+int gj_slab(int n, int cs, int kb) {
   int cw = (n + cs - 1) / cs;
-  return ((cw + KB - 1) / KB) * KB;
+  return ((cw + kb - 1) / kb) * kb;
 }
 
-size_t gj_smem_bytes(int n, int cs, bool leaf, int p, bool tglobal, bool f32) {
-  return plan_smem(n, gj_slab(n, cs), leaf, p, tglobal ? 1 : 0, f32 ? 8 : 16).total;
+namespace {
+template <int KB>
+size_t plan_total(int n, int cw, bool leaf, int p, int tmode, size_t esz) {
+  return plan_smem<KB>(n, cw, leaf, p, tmode, esz).total;
+}
+size_t plan_total_kb(int kb, int n, int cw, bool leaf, int p, int tmode, size_t esz) {
+  return kb == 4 ? plan_total<4>(n, cw, leaf, p, tmode, esz) : plan_total<8>(n, cw, leaf, p, tmode, esz);
 }
 
-size_t gj_meta_ints(int n) { return (size_t)meta_ints(n); }
-
-size_t gj_wide_smem_bytes(int n, int slab, bool f32, bool tglobal) {
-  return plan_smem(n, slab > KB ? slab : KB, false, 0, tglobal ? 1 : 0, f32 ? 8 : 16).total;
+template <int KB>
+cudaError_t run_gj_wide(WideArgs a, int batch, int G, bool f32, cudaStream_t st) {
+  // Panel placement: both panels in shared memory when they fit; else the
+  // eliminated one (the serial part) there and the applied one read in
+  // place; else both in place.  Every CTA of a panel launch should be
+  // resident at once (one wave): fewer CTAs per matrix when the shared
+  // memory allows less than two per SM.
+  const int n = a.n;
+  const size_t esz = f32 ? 8 : 16;
+  size_t smem = 0;
+  for (int it = 0; it < 3; it++) {
+    a.G = G;
+    a.slab = (n + G - 2) / (G - 1);
+    const int cwmax = a.slab > KB ? a.slab : KB;
+    a.tglobal = 0;
+    if (plan_total<KB>(n, cwmax, false, 0, 0, esz) > 200 * 1024)
+      a.tglobal = plan_total<KB>(n, cwmax, false, 0, 2, esz) <= 200 * 1024 ? 2 : 1;
+    smem = plan_total<KB>(n, cwmax, false, 0, a.tglobal, esz);
+    const long long per_sm = std::max<long long>(1, std::min<long long>(2, (227 * 1024) / (long long)smem));
+    if ((long long)batch * G <= 152LL * per_sm) break;
+    const int G2 = (int)std::max<long long>(2, 152LL * per_sm / batch);
+    if (G2 == G) break;
+    G = G2;
+  }
+  cudaError_t err = f32 ? cudaFuncSetAttribute(gj_wide_kernel<float2, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                        : cudaFuncSetAttribute(gj_wide_kernel<double2, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int np = npanels<KB>(n);
+  for (int phase = -1; phase <= np; phase++) {
+    if (f32)
+      gj_wide_kernel<float2, KB><<<batch * G, kThreads, smem, st>>>(a, phase);
+    else
+      gj_wide_kernel<double2, KB><<<batch * G, kThreads, smem, st>>>(a, phase);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
 }
+}  // namespace
+
+size_t gj_smem_bytes(int n, int cs, bool leaf, int p, bool tglobal, bool f32, int kb) {
+  if (leaf) kb = kLeafKB;
+  return plan_total_kb(kb, n, gj_slab(n, cs, kb), leaf, p, tglobal ? 1 : 0, f32 ? 8 : 16);
+}
+
+size_t gj_meta_ints(int n) { return (size_t)std::max(meta_ints<4>(n), meta_ints<8>(n)); }
+
+size_t gj_wide_smem_bytes(int n, int slab, bool f32, bool tglobal, int kb) {
+  return plan_total_kb(kb, n, slab > kb ? slab : kb, false, 0, tglobal ? 1 : 0, f32 ? 8 : 16);
+}
+
+int gj_wide_launches(int n, int kb) { return (n + kb - 1) / kb + 2; }
 
 cudaError_t launch_gj_wide(void *S, void *out, int n, int batch, int G, int *meta,
-                           unsigned int *status, int level, bool f32, cudaStream_t st) {
+                           unsigned int *status, int level, bool f32, cudaStream_t st, int kb) {
   if (batch <= 0 || n <= 0) return cudaSuccess;
   if (G < 2) G = 2;
   WideArgs a;
@@ -824,40 +893,7 @@ cudaError_t launch_gj_wide(void *S, void *out, int n, int batch, int G, int *met
   a.n = n;
   a.status = status;
   a.level = level;
-  // Panel placement: both panels in shared memory when they fit; else the
-  // eliminated one (the serial part) there and the applied one read in
-  // place; else both in place.  Every CTA of a panel launch should be
-  // resident at once (one wave): fewer CTAs per matrix when the shared
-  // memory allows less than two per SM.
-  const size_t esz = f32 ? 8 : 16;
-  size_t smem = 0;
-  for (int it = 0; it < 3; it++) {
-    a.G = G;
-    a.slab = (n + G - 2) / (G - 1);
-    const int cwmax = a.slab > KB ? a.slab : KB;
-    a.tglobal = 0;
-    if (plan_smem(n, cwmax, false, 0, 0, esz).total > 200 * 1024)
-      a.tglobal = plan_smem(n, cwmax, false, 0, 2, esz).total <= 200 * 1024 ? 2 : 1;
-    smem = plan_smem(n, cwmax, false, 0, a.tglobal, esz).total;
-    const long long per_sm = std::max<long long>(1, std::min<long long>(2, (227 * 1024) / (long long)smem));
-    if ((long long)batch * G <= 152LL * per_sm) break;
-    const int G2 = (int)std::max<long long>(2, 152LL * per_sm / batch);
-    if (G2 == G) break;
-    G = G2;
-  }
-  cudaError_t err = f32 ? cudaFuncSetAttribute(gj_wide_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                        : cudaFuncSetAttribute(gj_wide_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  const int np = npanels(n);
-  for (int phase = -1; phase <= np; phase++) {
-    if (f32)
-      gj_wide_kernel<float2><<<batch * G, kThreads, smem, st>>>(a, phase);
-    else
-      gj_wide_kernel<double2><<<batch * G, kThreads, smem, st>>>(a, phase);
-    err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-  }
-  return cudaSuccess;
+  return kb == 4 ? run_gj_wide<4>(a, batch, G, f32, st) : run_gj_wide<8>(a, batch, G, f32, st);
 }
 
 cudaError_t launch_leaf(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0,
@@ -875,14 +911,14 @@ cudaError_t launch_leaf(const LeafTables &lt, const LeafProb *probs, int nprob, 
   a.leaf0 = leaf0;
   a.status = status;
   a.level = level;
-  a.cw = gj_slab(lt.n, cs);
-  size_t smem = plan_smem(lt.n, a.cw, true, lt.p, false, f32 ? 8 : 16).total;
+  a.cw = gj_slab(lt.n, cs, kLeafKB);
+  size_t smem = plan_total<kLeafKB>(lt.n, a.cw, true, lt.p, 0, f32 ? 8 : 16);
   return f32 ? launch_cluster(leaf_kernel<float2>, a, count, cs, smem, st)
              : launch_cluster(leaf_kernel<double2>, a, count, cs, smem, st);
 }
 
 cudaError_t launch_gj_inverse(void *S, void *out, int n, int batch, int *meta, unsigned int *status,
-                              int level, int cs, bool tglobal, bool f32, cudaStream_t st) {
+                              int level, int cs, bool tglobal, bool f32, cudaStream_t st, int kb) {
   if (batch <= 0 || n <= 0) return cudaSuccess;
   GJArgs a;
   a.tglobal = tglobal ? 1 : 0;
@@ -890,12 +926,15 @@ cudaError_t launch_gj_inverse(void *S, void *out, int n, int batch, int *meta, u
   a.out = out;
   a.meta = meta;
   a.n = n;
-  a.cw = gj_slab(n, cs);
+  a.cw = gj_slab(n, cs, kb);
   a.status = status;
   a.level = level;
-  size_t smem = plan_smem(n, a.cw, false, 0, tglobal ? 1 : 0, f32 ? 8 : 16).total;
-  return f32 ? launch_cluster(gj_kernel<float2>, a, batch, cs, smem, st)
-             : launch_cluster(gj_kernel<double2>, a, batch, cs, smem, st);
+  const size_t smem = plan_total_kb(kb, n, a.cw, false, 0, tglobal ? 1 : 0, f32 ? 8 : 16);
+  if (kb == 4)
+    return f32 ? launch_cluster(gj_kernel<float2, 4>, a, batch, cs, smem, st)
+               : launch_cluster(gj_kernel<double2, 4>, a, batch, cs, smem, st);
+  return f32 ? launch_cluster(gj_kernel<float2, 8>, a, batch, cs, smem, st)
+             : launch_cluster(gj_kernel<double2, 8>, a, batch, cs, smem, st);
 }
 
 }  // namespace hps

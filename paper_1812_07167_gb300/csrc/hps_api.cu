@@ -525,24 +525,35 @@ struct GJChoice {
   int cs = 1;            // cluster size of the cluster kernel
   bool tglobal = false;  // cluster kernel: panels read in place from global memory
   int wide = 0;          // > 0: one launch per panel over P * wide CTAs instead
+  int kb = 8;            // panel width (8, or 4 for a shorter serial chain)
 };
+// a measured choice as one int of the tuning table: cs, or -wide; panel
+// width 4 adds 2^20 to the magnitude
+int gj_encode(const GJChoice &g) {
+  const int v = g.wide ? g.wide : g.cs;
+  const int m = v + (g.kb == 4 ? (1 << 20) : 0);
+  return g.wide ? -m : m;
+}
+GJChoice gj_decode(int v) {
+  GJChoice g;
+  const int m = v < 0 ? -v : v;
+  g.kb = (m >> 20) ? 4 : 8;
+  if (v > 0)
+    g.cs = m & ((1 << 20) - 1);
+  else
+    g.wide = m & ((1 << 20) - 1);
+  return g;
+}
 
 bool choose_gj_rule(int n3, long long P, int f32, GJChoice &g);
 
 // false when no regime fits in the kernels' shared memory
 bool choose_gj(int n3, long long P, int f32, GJChoice &g) {
   int v;
-  if (P <= (1 << 30) && tuned(TuneKey{1, n3, 0, 0, (int)P, f32}, v)) {
-    GJChoice t;
-    t.tglobal = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, f32) > 200 * 1024;
-    if (v > 0) {
-      t.cs = v;
-      if (hps::gj_smem_bytes(n3, t.cs, false, 0, t.tglobal, f32) <= 227 * 1024) {
-        g = t;
-        return true;
-      }
-    } else if (v < 0) {
-      t.wide = -v;
+  if (P <= (1 << 30) && tuned(TuneKey{1, n3, 0, 0, (int)P, f32}, v) && v != 0) {
+    GJChoice t = gj_decode(v);
+    t.tglobal = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, f32, t.kb) > 200 * 1024;
+    if (t.wide || hps::gj_smem_bytes(n3, t.cs, false, 0, t.tglobal, f32, t.kb) <= 227 * 1024) {
       g = t;
       return true;
     }
@@ -569,7 +580,7 @@ bool choose_gj_rule(int n3, long long P, int f32, GJChoice &g) {
   return true;
 }
 
-int gj_launches(int n3, const GJChoice &g) { return g.wide ? (n3 + 7) / 8 + 2 : 1; }
+int gj_launches(int n3, const GJChoice &g) { return g.wide ? hps::gj_wide_launches(n3, g.kb) : 1; }
 
 // Does a product of this shape go to the tensor cores (Ozaki scheme)?
 bool oz_shape(int M, int N, int K, int batch, int f32, bool oz) {
@@ -1536,9 +1547,10 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
         if (int rc = run_gemm(&g, 1)) return rc;
         const int lev = S.lev;  // the tallest tree's level numbering
         if (r.gj.wide)
-          CK(hps::launch_gj_wide(Wscr, Winv, n3, P, r.gj.wide, wmeta, d_status, lev, f != 0, st));
+          CK(hps::launch_gj_wide(Wscr, Winv, n3, P, r.gj.wide, wmeta, d_status, lev, f != 0, st, r.gj.kb));
         else
-          CK(hps::launch_gj_inverse(Wscr, Winv, n3, P, wmeta, d_status, lev, r.gj.cs, r.gj.tglobal, f != 0, st));
+          CK(hps::launch_gj_inverse(Wscr, Winv, n3, P, wmeta, d_status, lev, r.gj.cs, r.gj.tglobal, f != 0, st,
+                                    r.gj.kb));
         // Q(:, :n1) = R33b R31a
         g = gemm(n3, n1, n3, P, M(R33b, n3, s33), sub(Ra, dI3a, dI1), M(Q, n3, s3t));
         g.cf32 = f;
@@ -1883,27 +1895,40 @@ int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned) {
       const int n3 = k.M, P = k.batch;
       GJChoice rule;
       if (!choose_gj_rule(n3, P, k.f32, rule)) continue;
-      const bool tg = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, k.f32) > 200 * 1024;
-      std::vector<int> cands;
-      for (int cs = 1; cs <= hps::gj_max_cluster(); cs *= 2)
-        // every CTA of the cluster owns at least one panel
-        if (hps::gj_smem_bytes(n3, cs, false, 0, tg, k.f32) <= 227 * 1024 && (cs - 1) * hps::gj_slab(n3, cs) < n3)
-          cands.push_back(cs);
-      if (n3 >= 64) {
-        const int G0 = rule.wide ? rule.wide : (int)std::max<long long>(2, std::min<long long>((2 * 152 + P - 1) / P, n3 / 4 + 1));
-        cands.push_back(-G0);
-        if (G0 / 2 >= 2) cands.push_back(-(G0 / 2));
+      std::vector<GJChoice> cands;
+      for (int kb : {8, 4}) {
+        const bool tg = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, k.f32, kb) > 200 * 1024;
+        for (int cs = 1; cs <= hps::gj_max_cluster(); cs *= 2)
+          // every CTA of the cluster owns at least one panel
+          if (hps::gj_smem_bytes(n3, cs, false, 0, tg, k.f32, kb) <= 227 * 1024 &&
+              (cs - 1) * hps::gj_slab(n3, cs, kb) < n3) {
+            GJChoice c;
+            c.cs = cs;
+            c.tglobal = tg;
+            c.kb = kb;
+            cands.push_back(c);
+          }
+        if (n3 >= 64) {
+          const int G0 = rule.wide ? rule.wide : (int)std::max<long long>(2, std::min<long long>((2 * 152 + P - 1) / P, n3 / 4 + 1));
+          for (int G : {G0, G0 / 2})
+            if (G >= 2) {
+              GJChoice c;
+              c.wide = G;
+              c.kb = kb;
+              cands.push_back(c);
+            }
+        }
       }
       auto refill = [&]() { return fill(oS, (size_t)n3 * n3 * P, n3, k.f32); };
-      for (int v : cands) {
+      for (const GJChoice &c : cands) {
         float ms;
-        if (v > 0)
-          ms = time_it([&]() { return hps::launch_gj_inverse(buf + oS, buf + oC, n3, P, (int *)(buf + oM), (unsigned *)(buf + oSt), 0, v, tg, k.f32 != 0, st); }, refill, 2);
+        if (!c.wide)
+          ms = time_it([&]() { return hps::launch_gj_inverse(buf + oS, buf + oC, n3, P, (int *)(buf + oM), (unsigned *)(buf + oSt), 0, c.cs, c.tglobal, k.f32 != 0, st, c.kb); }, refill, 2);
         else
-          ms = time_it([&]() { return hps::launch_gj_wide(buf + oS, buf + oC, n3, P, -v, (int *)(buf + oM), (unsigned *)(buf + oSt), 0, k.f32 != 0, st); }, refill, 2);
+          ms = time_it([&]() { return hps::launch_gj_wide(buf + oS, buf + oC, n3, P, c.wide, (int *)(buf + oM), (unsigned *)(buf + oSt), 0, k.f32 != 0, st, c.kb); }, refill, 2);
         if (ms >= 0.0f && ms < best_ms) {
           best_ms = ms;
-          best = v;
+          best = gj_encode(c);
         }
       }
     }

@@ -142,8 +142,10 @@ cudaError_t launch_lu_solve(const void *LU, const int *perm, const double *dsc, 
 // CTAs.  S holds the matrices and is destroyed; the inverses go to out.  With
 // tglobal the panels are read in place from S (large n) instead of being
 // staged in shared memory; with f32 everything is complex64.
+// kb: panel width, 8 or 4 (4 halves the serial FP64 work a panel on the
+// owning CTA, for few large matrices).
 cudaError_t launch_gj_inverse(void *S, void *out, int n, int batch, int *meta, unsigned int *status,
-                              int level, int cs, bool tglobal, bool f32, cudaStream_t st);
+                              int level, int cs, bool tglobal, bool f32, cudaStream_t st, int kb = 8);
 
 // ---- complex128 residual of the global collocation system (refinement) ----
 constexpr int kMaxLevels = 24;
@@ -175,13 +177,14 @@ cudaError_t launch_residual(const ResidualSetup &rs, const double2 *u, const dou
 // over batch * G CTAs (CTA 0 of a matrix eliminates the next panel, the
 // others update slabs of columns), so a single matrix uses the whole chip.
 cudaError_t launch_gj_wide(void *S, void *out, int n, int batch, int G, int *meta,
-                           unsigned int *status, int level, bool f32, cudaStream_t st);
-size_t gj_wide_smem_bytes(int n, int slab, bool f32, bool tglobal);
+                           unsigned int *status, int level, bool f32, cudaStream_t st, int kb = 8);
+size_t gj_wide_smem_bytes(int n, int slab, bool f32, bool tglobal, int kb = 8);
+int gj_wide_launches(int n, int kb);
 
 // Cluster limits and scratch / shared-memory sizes of the Gauss-Jordan kernels.
 int gj_max_cluster();
-int gj_slab(int n, int cs);
-size_t gj_smem_bytes(int n, int cs, bool leaf, int p, bool tglobal = false, bool f32 = false);
-size_t gj_meta_ints(int n);
+int gj_slab(int n, int cs, int kb = 8);
+size_t gj_smem_bytes(int n, int cs, bool leaf, int p, bool tglobal = false, bool f32 = false, int kb = 8);
+size_t gj_meta_ints(int n);  // enough for either panel width
 
 }  // namespace hps
