@@ -10,8 +10,11 @@
 // imaginary part lies in [1/4, 1/2); column j of B by 2^-b_j likewise.  Each
 // scaled value x (real and imaginary parts separately) is written as
 //     x = sum_{s < S} d_s 2^{-6(s+1)} + r,   d_s integers, |d_s| <= 32,
-// taking d_s = rint(64 x_s), x_{s+1} = 64 x_s - d_s (every step exact in
-// FP64), so |r| <= 2^{-6S-1}.  The digits are exact in bf16.
+// with |r| <= 2^{-6S-1}: D = round(x 2^{6S}) is formed from the IEEE-754
+// fields of x as a 64-bit integer and cut into balanced base-64 digits
+// (every step exact; integer work only, since this part's FP64 pipe is 64
+// times slower than its integer and FP32 pipes).  The digits are exact in
+// bf16.
 //
 // Products.  The slice pairs (s, t) with s + t < S are taken group by group
 // of equal shift e = s + t, whose products all carry the weight 2^{-6(e+2)}.
@@ -115,6 +118,50 @@ __device__ __forceinline__ double2 oz_lda(const GemmDesc &g, int b, int i, int k
   return oz_ld(g.A, oz_off(g.A, b, i, k));
 }
 
+// max(|Re|, |Im|) as the integer image of its IEEE-754 bits (integer order is
+// numeric order for non-negative values)
+__device__ __forceinline__ unsigned long long oz_mag(double2 v) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffull;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffull;
+  return a > b ? a : b;
+}
+
+// The scaling exponent sh of a row or column whose largest magnitude has the
+// bits m: m 2^-sh lies in [1/4, 1/2) (m = 1.f 2^(E-1023) = 0.1f 2^(E-1022),
+// so sh = E - 1021); 0 for an all-zero row.
+__device__ __forceinline__ int oz_shift(unsigned long long m) {
+  return m ? (int)(m >> 52) - 1021 : 0;
+}
+
+// D = round(v 2^(6S - sh)) for |v 2^-sh| < 1/2 (so |D| <= 2^53), from the
+// fields of v: v = +-M 2^(E' - 1075) with the 53-bit significand M.
+__device__ __forceinline__ long long oz_fixed(double v, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const unsigned long long M = (b & 0xfffffffffffffull) | (E ? (1ull << 52) : 0ull);
+  const int t = (E ? E : 1) - 1075 + 6 * OZ_S - sh;  // D = round(M 2^t)
+  long long D;
+  if (M == 0 || t < -62)
+    D = 0;
+  else if (t >= 0)
+    D = (long long)(M << t);  // only for tiny M: the product stays below 2^53
+  else
+    D = (long long)((M + (1ull << (-t - 1))) >> -t);
+  return (b >> 63) ? -D : D;
+}
+
+// the S balanced base-64 digits of D, most significant first:
+// D = sum_s d_s 64^(S-1-s), d_s in [-32, 32]
+__device__ __forceinline__ void oz_digits(long long D, int (&d)[OZ_S]) {
+#pragma unroll
+  for (int s = OZ_S - 1; s > 0; s--) {
+    const int v = (int)((D + 32) & 63) - 32;
+    d[s] = v;
+    D = (D - v) >> 6;
+  }
+  d[0] = (int)D;
+}
+
 // Digits of B, a warp per column, lanes over k (neighbouring k are
 // neighbouring in the column-major operands): the column's exponent, then its
 // digits ([column][k], k contiguous).  Padding columns and k get zeros.
@@ -125,32 +172,30 @@ __global__ void __launch_bounds__(256) oz_split_b_kernel(const __grid_constant__
   const int b = blockIdx.y;
   if (j >= Np) return;
   const bool live = j < g.N;
-  double mx = 0.0;
+  unsigned long long mx = 0;
   if (live)
     for (int k = lane; k < g.K; k += 32) {
-      const double2 v = oz_ldb(g, b, k, j);
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      const unsigned long long m = oz_mag(oz_ldb(g, b, k, j));
+      mx = m > mx ? m : mx;
     }
-  for (int off = 16; off; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [1/2, 1): mx 2^-(e+1) in [1/4, 1/2)
-  const int sh = mx > 0.0 ? e + 1 : 0;
+  for (int off = 16; off; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+    mx = o > mx ? o : mx;
+  }
+  const int sh = oz_shift(mx);
   if (lane == 0) expo[(size_t)b * Np + j] = sh;
   const size_t plane = (size_t)Np * Kp;
   __nv_bfloat16 *base = digits + (size_t)b * OZ_S * 2 * plane + (size_t)j * Kp;
   for (int k = lane; k < Kp; k += 32) {
     double2 v = make_double2(0.0, 0.0);
     if (live && k < g.K) v = oz_ldb(g, b, k, j);
-    double xr = ldexp(v.x, -sh), xi = ldexp(v.y, -sh);
+    int dr[OZ_S], di[OZ_S];
+    oz_digits(oz_fixed(v.x, sh), dr);
+    oz_digits(oz_fixed(v.y, sh), di);
 #pragma unroll
-    for (int s = 0; s < OZ_S; s++) {
-      xr *= 64.0;
-      xi *= 64.0;
-      const double dr = rint(xr), di = rint(xi);
-      xr -= dr;
-      xi -= di;
-      base[(size_t)(2 * s) * plane + k] = __float2bfloat16_rn((float)dr);
-      base[(size_t)(2 * s + 1) * plane + k] = __float2bfloat16_rn((float)di);
+    for (int q = 0; q < OZ_S; q++) {
+      base[(size_t)(2 * q) * plane + k] = __int2bfloat16_rn(dr[q]);
+      base[(size_t)(2 * q + 1) * plane + k] = __int2bfloat16_rn(di[q]);
     }
   }
 }
@@ -161,22 +206,20 @@ __global__ void __launch_bounds__(256) oz_split_b_kernel(const __grid_constant__
 // in shared memory).  Pass 2: one thread per element, digits written k-major
 // ([k][row], rows contiguous).  Padding rows and k get zeros.
 __global__ void __launch_bounds__(256) oz_expo_a_kernel(const __grid_constant__ GemmDesc g, int Mp, int *expo) {
-  __shared__ double part[8][32];
+  __shared__ unsigned long long part[8][32];
   const int r = threadIdx.x & 31, kl = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + r, b = blockIdx.y;
-  double mx = 0.0;
+  unsigned long long mx = 0;
   if (i < g.M)
     for (int k = kl; k < g.K; k += 8) {
-      const double2 v = oz_lda(g, b, i, k);
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      const unsigned long long m = oz_mag(oz_lda(g, b, i, k));
+      mx = m > mx ? m : mx;
     }
   part[kl][r] = mx;
   __syncthreads();
   if (kl == 0 && i < Mp) {
-    for (int q = 1; q < 8; q++) mx = fmax(mx, part[q][r]);
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [1/2, 1): mx 2^-(e+1) in [1/4, 1/2)
-    expo[(size_t)b * Mp + i] = mx > 0.0 ? e + 1 : 0;
+    for (int q = 1; q < 8; q++) mx = part[q][r] > mx ? part[q][r] : mx;
+    expo[(size_t)b * Mp + i] = oz_shift(mx);
   }
 }
 
@@ -189,18 +232,15 @@ __global__ void __launch_bounds__(256) oz_split_a_kernel(const __grid_constant__
   double2 v = make_double2(0.0, 0.0);
   if (i < g.M && k < g.K) v = oz_lda(g, b, i, k);
   const int sh = expo[(size_t)b * Mp + i];
-  double xr = ldexp(v.x, -sh), xi = ldexp(v.y, -sh);
   const size_t plane = (size_t)Mp * Kp;
   __nv_bfloat16 *base = digits + (size_t)b * OZ_S * 2 * plane + (size_t)k * Mp + i;
+  int dr[OZ_S], di[OZ_S];
+  oz_digits(oz_fixed(v.x, sh), dr);
+  oz_digits(oz_fixed(v.y, sh), di);
 #pragma unroll
-  for (int s = 0; s < OZ_S; s++) {
-    xr *= 64.0;
-    xi *= 64.0;
-    const double dr = rint(xr), di = rint(xi);
-    xr -= dr;
-    xi -= di;
-    base[(size_t)(2 * s) * plane] = __float2bfloat16_rn((float)dr);
-    base[(size_t)(2 * s + 1) * plane] = __float2bfloat16_rn((float)di);
+  for (int q = 0; q < OZ_S; q++) {
+    base[(size_t)(2 * q) * plane] = __int2bfloat16_rn(dr[q]);
+    base[(size_t)(2 * q + 1) * plane] = __int2bfloat16_rn(di[q]);
   }
 }
 
