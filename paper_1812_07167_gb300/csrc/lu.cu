@@ -249,7 +249,7 @@ __device__ bool lu_factor_panel(const Work<C> &w, const LuShared &sh, int *meta,
 // the columns at once, so their memory accesses overlap; the update runs
 // over a flat (column, row) index, so a short trailing block costs only the
 // multiply-adds it needs (on this part the FP64 pipe is the bound).
-template <class C, int RPL = (sizeof(C) == 8 ? 4 : 2)>
+template <class C, int RPL = (sizeof(C) == 8 ? 8 : 2)>
 __device__ void lu_apply(const Work<C> &w, const LuShared &sh, int rank, int cs, int P, int k0, int kbp,
                          int ma, int mb, int ta, int tb) {
   const int tid = threadIdx.x, nthr = blockDim.x, n = w.n, rows = w.n + w.nb;
