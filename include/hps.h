@@ -145,8 +145,8 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy);
  * Device memory for all operators is allocated here and owned by the handle.
  * Returns HPS_EINVAL (bad descriptor, NULL c/out), HPS_ENOMEM, HPS_ECUDA, or
  * HPS_ENOTSUP when a leaf matrix or an interface of the tree is too large
- * for the kernels' shared memory (p > 24, or more than 512 leaves a side at
- * p = 16), before any device work. */
+ * for the kernels' shared memory (p > 25; more than 512 leaves a side at
+ * p = 16, more than 256 at p = 24), before any device work. */
 int hps_build(const hps_desc *desc, const double *c, void *stream, hps_handle **out);
 
 /* Build nprob independent solvers together (a ragged batch): Algorithm 1

@@ -129,3 +129,21 @@ def test_zgemm_argument_checks_need_no_device():
 def test_plan_of_a_rectangular_grid():
     info = hps.hps_plan(hps.Problem(8, 16, 40.0, 40.0, my=2))
     assert info.leaves == 16 and info.levels == 4 and info.n_bdry == 2 * (8 + 2) * 14
+
+
+@pytest.mark.parametrize("form", [hps.HPS_LEAF_LU, hps.HPS_LEAF_INVERSE])
+def test_plan_limits_match_the_documented_sizes(form):
+    """hps_plan's HPS_ENOTSUP boundary is the one include/hps.h states for
+    hps_build: p <= 25, up to 512 leaves a side at p = 16, 256 at p = 24."""
+    def code(m, p):
+        try:
+            hps.hps_plan(hps.Problem(m, p, 10.0, 10.0, leaf_form=form))
+            return hps.HPS_OK
+        except hps.HPSError as e:
+            return e.code
+    assert code(1, 25) == hps.HPS_OK
+    assert code(1, 26) == hps.HPS_ENOTSUP
+    assert code(512, 16) == hps.HPS_OK
+    assert code(1024, 16) == hps.HPS_ENOTSUP
+    assert code(256, 24) == hps.HPS_OK
+    assert code(512, 24) == hps.HPS_ENOTSUP
