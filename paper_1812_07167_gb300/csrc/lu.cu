@@ -586,16 +586,17 @@ struct LuSolveArgs {
 
 constexpr int kSB = 32;  // rows of a diagonal block of the sweeps
 
-// y[i] -= sum_{kk < jb} A(i, J0 + kk) y[J0 + kk] for the RB right-hand sides,
-// a = &A(i, J0) (column-major, ld n).  The factor entries are loaded KC at a
-// time ahead of their multiply-adds, so a thread has KC loads in flight (the
-// sweeps of a 1-RHS solve wait on memory, not on arithmetic).
-template <class C, int RB>
-__device__ __forceinline__ void sweep_row(C *y, const C *a, int n, int J0, int jb, int i) {
-  constexpr int KC = RB <= 1 ? 16 : RB <= 4 ? 8 : 4;
-  C acc[RB];
+// y[i] -= sum_{kk < jb} A(i, J0 + kk) y[J0 + kk] for CPT of the RB
+// right-hand sides (from c0), a = &A(i, J0) (column-major, ld n).  The factor
+// entries are loaded KC at a time ahead of their multiply-adds, so a thread
+// has KC loads in flight (the sweeps of a 1-RHS solve wait on memory, not on
+// arithmetic).
+template <class C, int RB, int CPT>
+__device__ __forceinline__ void sweep_row(C *y, const C *a, int n, int J0, int jb, int i, int c0) {
+  constexpr int KC = CPT <= 1 ? 16 : CPT <= 4 ? 8 : 4;
+  C acc[CPT];
 #pragma unroll
-  for (int c = 0; c < RB; c++) acc[c] = y[i * RB + c];
+  for (int c = 0; c < CPT; c++) acc[c] = y[i * RB + c0 + c];
   for (int k0 = 0; k0 < jb; k0 += KC) {
     C l[KC];
 #pragma unroll
@@ -604,11 +605,39 @@ __device__ __forceinline__ void sweep_row(C *y, const C *a, int n, int J0, int j
     for (int u = 0; u < KC; u++) {
       if (k0 + u >= jb) break;
 #pragma unroll
-      for (int c = 0; c < RB; c++) acc[c] = cfms(acc[c], l[u], y[(J0 + k0 + u) * RB + c]);
+      for (int c = 0; c < CPT; c++) acc[c] = cfms(acc[c], l[u], y[(J0 + k0 + u) * RB + c0 + c]);
     }
   }
 #pragma unroll
-  for (int c = 0; c < RB; c++) y[i * RB + c] = acc[c];
+  for (int c = 0; c < CPT; c++) y[i * RB + c0 + c] = acc[c];
+}
+
+// The update of rows [i0, i0 + rows) by the block's jb solved rows: a thread
+// per (row, share of the right-hand sides), the right-hand sides split S ways
+// while the rows are fewer than the threads, so that short updates keep the
+// FP64 pipes of every warp busy.
+template <class C, int RB, int S>
+__device__ __forceinline__ void sweep_rows_s(C *y, const C *LU, int n, int J0, int jb, int i0, int rows) {
+  for (int t = threadIdx.x; t < rows * S; t += blockDim.x) {
+    const int i = i0 + t / S, c0 = (t % S) * (RB / S);
+    sweep_row<C, RB, RB / S>(y, LU + (size_t)J0 * n + i, n, J0, jb, i, c0);
+  }
+}
+
+template <class C, int RB>
+__device__ __forceinline__ void sweep_rows(C *y, const C *LU, int n, int J0, int jb, int i0, int rows) {
+  if (rows <= 0) return;
+  const int want = (int)blockDim.x / rows;  // right-hand-side shares that keep every thread busy
+  if (RB >= 16 && want >= 16)
+    sweep_rows_s<C, RB, (RB >= 16 ? 16 : 1)>(y, LU, n, J0, jb, i0, rows);
+  else if (RB >= 8 && want >= 8)
+    sweep_rows_s<C, RB, (RB >= 8 ? 8 : 1)>(y, LU, n, J0, jb, i0, rows);
+  else if (RB >= 4 && want >= 4)
+    sweep_rows_s<C, RB, (RB >= 4 ? 4 : 1)>(y, LU, n, J0, jb, i0, rows);
+  else if (RB >= 2 && want >= 2)
+    sweep_rows_s<C, RB, (RB >= 2 ? 2 : 1)>(y, LU, n, J0, jb, i0, rows);
+  else
+    sweep_rows_s<C, RB, 1>(y, LU, n, J0, jb, i0, rows);
 }
 
 // One CTA per (leaf, RB right-hand sides): y = P D b in shared memory, then
@@ -665,7 +694,7 @@ __global__ void __launch_bounds__(kThreads, 2) lu_solve_kernel(const __grid_cons
       if (lane < jb) y[(J0 + lane) * RB + c] = yv;
     }
     __syncthreads();
-    for (int i = J0 + jb + tid; i < n; i += nthr) sweep_row<C, RB>(y, LU + (size_t)J0 * n + i, n, J0, jb, i);
+    sweep_rows<C, RB>(y, LU, n, J0, jb, J0 + jb, n - J0 - jb);
     __syncthreads();
   }
   // backward: U x = y
@@ -692,7 +721,7 @@ __global__ void __launch_bounds__(kThreads, 2) lu_solve_kernel(const __grid_cons
       if (lane < jb) y[(J0 + lane) * RB + c] = yv;
     }
     __syncthreads();
-    for (int i = tid; i < J0; i += nthr) sweep_row<C, RB>(y, LU + (size_t)J0 * n + i, n, J0, jb, i);
+    sweep_rows<C, RB>(y, LU, n, J0, jb, 0, J0);
     __syncthreads();
   }
   for (int idx = tid; idx < n * nc; idx += nthr) {
