@@ -342,6 +342,47 @@ def ours(args, rank, world, local_rank):
     minfo = hm.info()
     hm.free()
 
+    # ---- the other leaf form on the same problem (LU factors vs B^-1): its
+    # build, 1-RHS latency and 64-RHS rate, and its u against this run's ----
+    po = hps.Problem(wl.m, wl.p, wl.kappa, wl.eta, leaf_form=1 - LEAF_FORM)
+    ob = []
+    for _ in range(4):
+        flush.zero_()
+        e0.record(st)
+        ho = hps.hps_build(po, cd, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ob.append(e0.elapsed_time(e1))
+        ho.free()
+    ho = hps.hps_build(po, cd, st)
+    uo = torch.empty_like(ud)
+    olat = []
+    for k in range(60):
+        st.synchronize()
+        t0 = time.perf_counter()
+        hps.hps_solve(ho, sd, td, uo, 1, st)
+        st.synchronize()
+        if k >= 10:
+            olat.append((time.perf_counter() - t0) * 1e3)
+    Uo = torch.empty_like(U)
+    hps.hps_solve(ho, S, T, Uo, nb, st)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(5):
+        hps.hps_solve(ho, S, T, Uo, nb, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    obatch_ms = e0.elapsed_time(e1) / 5
+    u_other = uo.cpu().numpy()[0]
+    ho.free()
+    other = {
+        "leaf_form": "B^-1 (Gauss-Jordan)" if LEAF_FORM == 0 else "LU factors",
+        "build_ms_median": statistics.median(ob), "build_dof_per_s": dof / (statistics.median(ob) / 1e3),
+        "solve_rhs_per_s": nb / (obatch_ms / 1e3), "solve_nrhs_batch": nb,
+        "solve_latency_ms_p50": float(np.percentile(olat, 50)),
+        "rel_diff_u_vs_this_form": float(np.abs(u_other - u_gpu).max() / np.abs(u_gpu).max()),
+    }
+
     batch_res = None if args.no_batching else batching(dev, st, flush)
 
     if rank != 0:
@@ -398,6 +439,7 @@ def ours(args, rank, world, local_rank):
             "rel_err_root_R_vs_fp64_gpu": float(np.linalg.norm(R_mixed - R_gpu) / np.linalg.norm(R_gpu)),
             "operator_bytes": minfo.operator_bytes,
         },
+        "other_leaf_form": other,
         "batching": batch_res,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -45,6 +45,15 @@ __device__ __forceinline__ C cmul(C a, C b) {
 }
 
 template <class C>
+__device__ __forceinline__ C cfms(C acc, C a, C b) {  // acc - a b
+  acc.x = CX<C>::fmad(-a.x, b.x, acc.x);
+  acc.x = CX<C>::fmad(a.y, b.y, acc.x);
+  acc.y = CX<C>::fmad(-a.x, b.y, acc.y);
+  acc.y = CX<C>::fmad(-a.y, b.x, acc.y);
+  return acc;
+}
+
+template <class C>
 __device__ __forceinline__ C crecip(C z) {
   // 1 / z with Smith's scaling (Smith, CACM 1962)
   using R = typename CX<C>::R;
