@@ -772,16 +772,20 @@ def serving(args, local_rank):
 
 
 def kernel_hash(kernel="lu_leaf_kernel"):
-    """Hash of the sources of a leaf kernel (its file and the device headers
-    it includes), so stored ncu counters are used only for the code they
-    were taken on."""
+    """Hash of the code of a leaf kernel (its file and the device headers it
+    includes, comments left out), so stored ncu counters are used only for
+    the code they were taken on."""
     import hashlib
 
     src = "lu.cu" if kernel == "lu_leaf_kernel" else "gj.cu"
     h = hashlib.sha256()
     for name in (src, "cx.cuh", "leaf_geom.cuh"):
-        with open(os.path.join(ROOT, "paper_1812_07167_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1812_07167_gb300", "csrc", name)) as f:
+            # the code only: // comments and blank lines do not change the kernel
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

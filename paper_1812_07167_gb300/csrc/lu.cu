@@ -1,5 +1,5 @@
-// Leaf step in factored form (Sec. 2.1) and the leaf action of the solve
-// that goes with it.
+// Leaf step in factored form (Sec. 2.1); the solve's leaf action from these
+// factors is in lu_solve.cu.
 //
 // The leaf system is B u = [t; s] (B = [F; A-hat(I_i, :)], the impedance rows
 // first).  Algorithm 2 needs u = B^{-1} [t; s] on the way down and the build
@@ -27,7 +27,8 @@
 // updates their trailing rows, G rows included.  Look-ahead: the owner of
 // panel P+1 updates and factors it first and publishes it (cluster barrier
 // arrive) before it updates the rest of its columns.  The working matrix
-// lives in X and GX themselves (it stays in L2).  One hardware cluster
+// lives in X and GX themselves (in L2 while a launch's leaves fit there; the
+// trailing updates stream through HBM beyond that).  One hardware cluster
 // barrier per panel; no kernel here spins on a flag.
 #include <cooperative_groups.h>
 
