@@ -110,6 +110,7 @@ __device__ __forceinline__ void epilogue(const GemmDesc &g, int b, int i, int j,
 template <class C, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     gemm_kernel(const __grid_constant__ GemmPack pack) {
+  chain_enter();
   constexpr int NTX = BM / TM, NTY = BN / TN, NT = NTX * NTY;
   __shared__ C As[BK][BM];
   __shared__ C Bs[BK][BN];
@@ -216,6 +217,7 @@ __device__ __forceinline__ void gemv_loop(const GemmDesc &g, int b, int i, int w
 // timing.  B and B2 share one storage type.
 template <class C, int NN>
 __global__ void __launch_bounds__(256) gemv_kernel(const __grid_constant__ GemmPack pack) {
+  chain_enter();
   __shared__ C red[8][NN][33];
   __shared__ int last;
   const GemmDesc &g = pack.d[blockIdx.z];
@@ -297,6 +299,7 @@ __global__ void __launch_bounds__(256) gemv_kernel(const __grid_constant__ GemmP
 }
 
 __global__ void __launch_bounds__(256) copy_kernel(const __grid_constant__ CopyBatch cb) {
+  chain_enter();
   const CopyDesc &d = cb.d[blockIdx.z];
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long total = (long long)d.M * d.N;
@@ -340,8 +343,7 @@ cudaError_t launch_cfg(const GemmPack &pk, cudaStream_t st) {
   }
   if (maxtiles == 0 || maxbatch == 0) return cudaSuccess;
   dim3 grid(maxtiles, maxbatch < 65535 ? maxbatch : 65535, pk.n);
-  gemm_kernel<C, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(pk);
-  return cudaGetLastError();
+  return launch_k(gemm_kernel<C, BM, BN, BK, TM, TN>, grid, dim3((BM / TM) * (BN / TN)), 0, st, pk);
 }
 
 template <class C, int NN>
@@ -362,8 +364,7 @@ cudaError_t launch_gemv(const GemmPack &pk, cudaStream_t st) {
     while (ks < 16 && blocks * ks < 2 * 152 && kmin / (2 * ks) >= 64) ks *= 2;
   if (blocks * ks > kGemvSlots) ks = 1;  // (cannot happen: the loop stops below 2 x 304)
   dim3 grid((unsigned)blocks, ks, pk.n);
-  gemv_kernel<C, NN><<<grid, 256, 0, st>>>(pk);
-  return cudaGetLastError();
+  return launch_k(gemv_kernel<C, NN>, grid, dim3(256), 0, st, pk);
 }
 
 template <class C>
@@ -388,6 +389,11 @@ cudaError_t launch_typed(const GemmPack &pk, int maxN, cudaStream_t st) {
 }
 
 }  // namespace
+
+static thread_local bool t_chained = false;
+LaunchChain::LaunchChain() : prev(t_chained) { t_chained = true; }
+LaunchChain::~LaunchChain() { t_chained = prev; }
+bool launch_chained() { return t_chained; }
 
 cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st) {
   if (ndesc < 1 || ndesc > 2) return cudaErrorInvalidValue;
@@ -418,8 +424,7 @@ cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st) {
   }
   if (maxel == 0 || maxbatch == 0) return cudaSuccess;
   dim3 grid((unsigned)((maxel + 255) / 256), maxbatch < 65535 ? maxbatch : 65535, cb.count);
-  copy_kernel<<<grid, 256, 0, st>>>(cb);
-  return cudaGetLastError();
+  return launch_k(copy_kernel, grid, dim3(256), 0, st, cb);
 }
 
 }  // namespace hps

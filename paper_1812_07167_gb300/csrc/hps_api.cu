@@ -20,6 +20,7 @@
 #include <array>
 #include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <cmath>
 #include <cstdint>
@@ -791,6 +792,12 @@ static int solve_gemm(GemmDesc *gd, int nd, cudaStream_t st, char *wb, const Sol
 static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, double2 *u, int R,
                         char *wb, const SolveWs &ws, cudaStream_t st, const double2 *JA = nullptr,
                         const double2 *JB = nullptr) {
+  // with one or two right-hand sides the solve is a chain of small
+  // dependent launches: let each be scheduled while the previous one drains
+  // (measured at 16 x 16 leaves: 1 RHS 0.85 -> 0.75 ms; with 16 or 64
+  // right-hand sides the chained launches were slower)
+  std::unique_ptr<hps::LaunchChain> chain;
+  if (R <= 2) chain.reset(new hps::LaunchChain());
   const Plan &pl = h->plan;
   const int n = pl.n, nb = pl.nb, ni = pl.ni, nl = pl.leaves, lf = pl.leaf_f32;
   const size_t *oh = ws.oh, *ot = ws.ot, *ota = ws.ota, *otb = ws.otb;

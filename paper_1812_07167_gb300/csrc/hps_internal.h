@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace hps {
 
 // Element (i, j) of batch b of a strided, optionally index-mapped complex
@@ -85,6 +87,49 @@ struct LeafProb {
 struct DevStatus {
   unsigned int word;
 };
+
+// Chained launches: while a LaunchChain is alive on a thread, the GEMM,
+// skinny-product, copy and LU-sweep launchers of that thread launch with
+// programmatic stream serialization, so a kernel's CTAs may be scheduled
+// while the previous kernel on the stream drains; every such kernel waits
+// (griddepcontrol.wait) for the previous one to finish before it reads
+// anything, so results are unchanged.  Used for the solve's chain of small
+// dependent launches.
+struct LaunchChain {
+  LaunchChain();
+  ~LaunchChain();
+  bool prev;
+};
+bool launch_chained();
+// launch kern<<<grid, block, smem, st>>>(args...), chained if a LaunchChain is alive
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (launch_chained()) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+#ifdef __CUDACC__
+// Start of a kernel that may run chained after the previous one on its
+// stream (LaunchChain): wait until that kernel has finished and its writes
+// are visible, then let the next kernel be scheduled.  No-ops for a kernel
+// launched the ordinary way.
+__device__ __forceinline__ void chain_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+#endif
 
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st);

@@ -88,6 +88,7 @@ __device__ __forceinline__ void sweep_rows(C *y, const C *LU, int n, int J0, int
 // shuffles, then every thread updates one row of the rest for all RB.
 template <class C, int RB>
 __global__ void __launch_bounds__(kThreads, 2) lu_solve_kernel(const __grid_constant__ LuSolveArgs a) {
+  chain_enter();
   extern __shared__ __align__(16) unsigned char smem[];
   using R = typename CX<C>::R;
   const int n = a.n, nb = a.nb;
@@ -180,8 +181,7 @@ cudaError_t solve_rb(const LuSolveArgs &a, long long leaves, cudaStream_t st) {
                                          (int)smem);
   if (err != cudaSuccess) return err;
   dim3 grid((unsigned)leaves, (unsigned)((a.R + RB - 1) / RB), 1);
-  lu_solve_kernel<C, RB><<<grid, kThreads, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_k(lu_solve_kernel<C, RB>, grid, dim3(kThreads), smem, st, a);
 }
 
 template <class C>
