@@ -218,7 +218,8 @@ __device__ __forceinline__ void gemv_loop(const GemmDesc &g, int b, int i, int w
 template <class C, int NN>
 __global__ void __launch_bounds__(256) gemv_kernel(const __grid_constant__ GemmPack pack) {
   chain_enter();
-  __shared__ C red[8][NN][33];
+  constexpr int NR = NN < 8 ? NN : 8;  // right-hand sides a reduction round (fits static shared memory)
+  __shared__ C red[8][NR][33];
   __shared__ int last;
   const GemmDesc &g = pack.d[blockIdx.z];
   const int rblocks = (g.M + 31) / 32;
@@ -246,18 +247,23 @@ __global__ void __launch_bounds__(256) gemv_kernel(const __grid_constant__ GemmP
         gemv_loop<C, double2, double2, NN>(g, b, i, w, k0, k1, acc);
     }
   }
-#pragma unroll
-  for (int j = 0; j < NN; j++) red[w][j][l] = acc[j];
-  __syncthreads();
   C v[NN];
-  if (w == 0) {
 #pragma unroll
-    for (int j = 0; j < NN; j++) {
-      v[j] = red[0][j][l];
+  for (int j0 = 0; j0 < NN; j0 += NR) {
+    if (j0 > 0) __syncthreads();  // warp 0 has read the previous round
 #pragma unroll
-      for (int q = 1; q < 8; q++) {
-        v[j].x += red[q][j][l].x;
-        v[j].y += red[q][j][l].y;
+    for (int j = 0; j < NR; j++) red[w][j][l] = acc[j0 + j];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+      for (int j = 0; j < NR; j++) {
+        C t = red[0][j][l];
+#pragma unroll
+        for (int q = 1; q < 8; q++) {
+          t.x += red[q][j][l].x;
+          t.y += red[q][j][l].y;
+        }
+        v[j0 + j] = t;
       }
     }
   }
@@ -373,6 +379,11 @@ cudaError_t launch_typed(const GemmPack &pk, int maxN, cudaStream_t st) {
   if (maxN <= 2) return launch_gemv<C, 2>(pk, st);
   if (maxN <= 4) return launch_gemv<C, 4>(pk, st);
   if (maxN <= 8) return launch_gemv<C, 8>(pk, st);
+  // 9 .. 16 right-hand sides of a solve (its products carry split-K scratch):
+  // the skinny kernel too, which splits K where the level has few row blocks
+  bool scratch = true;
+  for (int q = 0; q < pk.n; q++) scratch = scratch && pk.d[q].part && pk.d[q].cnt;
+  if (maxN <= 16 && scratch) return launch_gemv<C, 16>(pk, st);
   switch (pk.d[0].cfg) {  // a measured choice (hps_tune)
     case 1: return launch_cfg<C, 64, 64, 16, 4, 4>(pk, st);
     case 2: return launch_cfg<C, 32, 32, 16, 2, 2>(pk, st);

@@ -695,7 +695,7 @@ static void solve_products(const Plan &pl, std::vector<std::array<int, 3>> &out)
 
 static void solve_ws_layout(const Plan &pl, int R, SolveWs &w, bool allow_oz = true) {
   size_t off = align256(hps::gemv_scratch_counters());
-  if (R <= 8) {
+  if (R <= 16) {
     w.ogv = off;
     off = align256(off + hps::gemv_part_bytes(R));
   }
@@ -752,7 +752,7 @@ static int solve_gemm(GemmDesc *gd, int nd, cudaStream_t st, char *wb, const Sol
   int nr = 0;
   for (int q = 0; q < nd; q++) {
     GemmDesc &g = gd[q];
-    if (g.N <= 8 && ws.ogv) {
+    if (g.N <= 16 && ws.ogv) {
       g.part = wb + ws.ogv;
       g.cnt = (unsigned *)wb;
     }

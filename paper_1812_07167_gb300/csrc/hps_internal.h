@@ -35,7 +35,8 @@ struct GemmDesc {
   int addI;
   int cf32;
   int cfg;  // tile configuration for N > 8: 0 = by rule, 1..4 = 64x64, 32x32, 16x16, 64x16
-  // N <= 8: scratch that lets the skinny kernel split K over several CTAs
+  // N <= 16: scratch that lets the skinny kernel split K over several CTAs
+  // (without it, products with 9 .. 16 columns take the tiled kernel)
   // (partial sums of up to kGemvBlocks row blocks x 16 splits x 32 rows x N,
   // and kGemvBlocks counters that must be zero; the kernel leaves them zero)
   void *part;
@@ -44,9 +45,9 @@ struct GemmDesc {
 constexpr int kGemvBlocks = 1024;  // row blocks a skinny launch may split (per descriptor)
 constexpr int kGemvSlots = 608;    // (row block, split) pairs a split launch has at most (< 4 x 152)
 // bytes of the skinny kernel's scratch (two descriptors a launch): counters,
-// then partial sums for up to N (rounded up to 1, 2, 4, 8) right-hand sides
+// then partial sums for up to N (rounded up to 1, 2, 4, 8, 16) right-hand sides
 inline size_t gemv_scratch_counters() { return 2 * kGemvBlocks * sizeof(unsigned); }
-inline int gemv_nn(int N) { return N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : 8; }
+inline int gemv_nn(int N) { return N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : 16; }
 inline size_t gemv_part_bytes(int N) { return 2ull * kGemvSlots * 32 * gemv_nn(N) * 16; }
 
 // One batched mapped copy:  dst(i, j) = alpha * src(i, j) for i < M, j < N
