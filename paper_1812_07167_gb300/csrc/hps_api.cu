@@ -676,13 +676,27 @@ struct SolveWs {
   size_t ogv = 0;
 };
 
+// Rows of the first diagonal block when a wide solve in LU form splits each
+// leaf's sweeps in two (a multiple of the sweep kernel's 32-row blocks), or
+// 0 when the leaf is too small to gain from it.
+static int lu_split(int n) {
+  const int b1 = (n / 2 + 16) / 32 * 32;
+  return (b1 >= 64 && b1 < n) ? b1 : 0;
+}
+
 // The complex128 products of a solve with R right-hand sides (M, K, batch),
 // Algorithm 2's leaf and level actions.
 static void solve_products(const Plan &pl, std::vector<std::array<int, 3>> &out) {
   out.clear();
   if (!pl.leaf_f32) {
     out.push_back({pl.nb, pl.ni, pl.leaves});
-    if (!pl.leaf_lu) out.push_back({pl.n, pl.n, pl.leaves});
+    if (!pl.leaf_lu) {
+      out.push_back({pl.n, pl.n, pl.leaves});
+    } else if (const int b1 = lu_split(pl.n)) {
+      // the off-diagonal blocks of a blocked wide LU solve
+      out.push_back({pl.n - b1, b1, pl.leaves});
+      out.push_back({b1, pl.n - b1, pl.leaves});
+    }
   }
   for (const Level &L : pl.lv) {
     if (L.f32) continue;
@@ -902,7 +916,32 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     CK(hps::launch_copy(cb, st));
   }
   // leaves: u = Psi t + Y s = B^{-1} [t; s]
-  if (pl.leaf_lu) {
+  const int b1 = lu_split(n);
+  if (pl.leaf_lu && !lf && R >= 32 && b1 && ws.oz_bytes && oz_shape(n - b1, R, b1, nl, 0, pl.oz)) {
+    // wide solve: each leaf's sweeps in two diagonal blocks, the products
+    // with the off-diagonal blocks L21 and U12 batched over the leaves (on
+    // the tensor cores at this width):
+    //   y1 = L11^-1 (P D b)_1;  (P D b)_2 -= L21 y1;  y2 = L22^-1 (P D b)_2;
+    //   x2 = U22^-1 y2;  y1 -= U12 x2;  x1 = U11^-1 y1
+    const long long ldu = (long long)nl * n, s2 = (long long)n * n;
+    CK(hps::launch_lu_solve_part(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, W(ot[0]), (long long)nl * nb, nb, s,
+                                 (long long)nl * ni, ni, u, ldu, n, false, 0, b1, true, true, false, st));
+    GemmDesc gl = gemm(n - b1, R, b1, nl, F(elem(h->X, b1, 0), n, s2, 0), mat(u, ldu, n), mat(u + b1, ldu, n));
+    gl.alpha = make_double2(-1.0, 0.0);
+    gl.D = mat(u + b1, ldu, n);
+    gl.beta = make_double2(1.0, 0.0);
+    if (int rc = solve_gemm(&gl, 1, st, wb, ws, pl.oz)) return rc;
+    CK(hps::launch_lu_solve_part(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, nullptr, 0, 0, nullptr, 0, 0, u, ldu,
+                                 n, false, b1, n, false, true, true, st));
+    GemmDesc gu = gemm(b1, R, n - b1, nl, F(elem(h->X, (long long)b1 * n, 0), n, s2, 0), mat(u + b1, ldu, n),
+                       mat(u, ldu, n));
+    gu.alpha = make_double2(-1.0, 0.0);
+    gu.D = mat(u, ldu, n);
+    gu.beta = make_double2(1.0, 0.0);
+    if (int rc = solve_gemm(&gu, 1, st, wb, ws, pl.oz)) return rc;
+    CK(hps::launch_lu_solve_part(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, nullptr, 0, 0, nullptr, 0, 0, u, ldu,
+                                 n, false, 0, b1, false, false, true, st));
+  } else if (pl.leaf_lu) {
     CK(hps::launch_lu_solve(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, W(ot[0]), (long long)nl * nb, nb, s,
                             (long long)nl * ni, ni, u, (long long)nl * n, n, lf != 0, st));
   } else {

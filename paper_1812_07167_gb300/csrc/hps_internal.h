@@ -182,6 +182,16 @@ cudaError_t launch_lu_solve(const void *LU, const int *perm, const double *dsc, 
                             int nb, int R, const double2 *t, long long t_ld, long long t_stride,
                             const double2 *s, long long s_ld, long long s_stride, double2 *u,
                             long long u_ld, long long u_stride, bool f32, cudaStream_t st);
+// One stage of a blocked solve on the rows [r0, r1) of every leaf: with
+// gather, u = P D [t; s] on all n rows first (rows outside the range straight
+// to u), else the rows [r0, r1) are read from u; then the forward (L) and/or
+// backward (U) sweep with the diagonal block of those rows only, written
+// back to u.  The products with the off-diagonal blocks are the caller's.
+cudaError_t launch_lu_solve_part(const void *LU, const int *perm, const double *dsc, long long leaves, int n,
+                                 int nb, int R, const double2 *t, long long t_ld, long long t_stride,
+                                 const double2 *s, long long s_ld, long long s_stride, double2 *u,
+                                 long long u_ld, long long u_stride, bool f32, int r0, int r1, bool gather,
+                                 bool fwd, bool bwd, cudaStream_t st);
 
 // Inverse of `batch` n x n column-major matrices (leading dim n, batch stride
 // n*n) by blocked Gauss-Jordan with partial pivoting across clusters of `cs`
