@@ -90,10 +90,14 @@ __device__ __forceinline__ void sweep_rows(C *y, const C *LU, int n, int J0, int
     sweep_rows_s<C, RB, 1>(y, LU, n, J0, jb, i0, rows);
 }
 
-// One CTA per (leaf, RB right-hand sides): y = P D b in shared memory, then
-// the forward sweep with L and the backward sweep with U in blocks of 32
-// rows: a warp solves the diagonal block for one right-hand side with
-// shuffles, then every thread updates one row of the rest for all RB.
+// One CTA per (leaf, RB right-hand sides): the rows [r0, r1) of y (= P D b,
+// gathered here, or the partial result in u) in shared memory, then the
+// forward sweep with L and/or the backward sweep with U over those rows in
+// blocks of 32: a warp solves the diagonal block for one right-hand side
+// with shuffles, then the threads update the rest of the range (a row, or a
+// share of a row's right-hand sides, each).  The whole solve is one launch
+// over [0, n); a blocked wide solve runs it on two ranges with the products
+// between them done elsewhere.
 template <class C, int RB>
 __global__ void __launch_bounds__(kThreads, 2) lu_solve_kernel(const __grid_constant__ LuSolveArgs a) {
   chain_enter();
