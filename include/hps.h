@@ -265,10 +265,14 @@ int hps_solve_noalloc(hps_handle *h, const double *s, const double *t, double *u
  * HPS_EINVAL or HPS_ECUDA. */
 int hps_root_R(hps_handle *h, double *R, void *stream);
 
-/* Stored operators of one leaf (Sec. 2.1.1, 2.1.2, 2.4), for inspection.
+/* Operators of one leaf (Sec. 2.1.1, 2.1.2, 2.4), for inspection.
  *   Psi: [p^2-4][4(p-2)], Y: [p^2-4][(p-2)^2], Gam: [4(p-2)][(p-2)^2], each
- *   complex row-major; any may be NULL.
- * Returns HPS_EINVAL for a leaf index out of range. */
+ *   complex row-major; any may be NULL; host or device memory.
+ * In HPS_LEAF_LU form Psi and Y (the columns of B^{-1}) are not stored: they
+ * are formed here by solving with the leaf's factors for every unit vector
+ * (in the leaves' precision), with a temporary device allocation of
+ * 3 (p^2-4)^2 complex values.  Synchronizes the stream.
+ * Returns HPS_EINVAL for a leaf index out of range, HPS_ECUDA. */
 int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, void *stream);
 
 /* Batched complex GEMM C = A B with the library's product kernels (a
