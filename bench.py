@@ -246,7 +246,7 @@ def ours(args, rank, world, local_rank):
     # ---- separate build / solve figures (device-resident inputs) ----
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     build_ms = []
-    for _ in range(5):
+    for _ in range(10):
         flush.zero_()
         e0.record(st)
         h = hps.hps_build(pr, cd, st)
@@ -447,6 +447,10 @@ def ours(args, rank, world, local_rank):
         dt, u_ora, R_ora = run_oracle_step(c, s, t, threads)
         line["cpu_baseline"] = {"value": dof / dt, "unit": "DOF/s", "cores": threads, "kind": "oracle",
                                 "sample": "one full 16x16-leaf build + 1-RHS solve"}
+        # the same oracle on one thread, for the scale of its OpenMP speedup
+        dt1, _, _ = run_oracle_step(c, s, t, 1)
+        line["cpu_baseline_single_thread"] = {"value": dof / dt1, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                                              "sample": "one full 16x16-leaf build + 1-RHS solve"}
         line["rel_err_vs_oracle"] = {
             "u": float(np.abs(u_gpu - u_ora).max() / np.abs(u_ora).max()),
             "root_R": float(np.linalg.norm(R_gpu - R_ora) / np.linalg.norm(R_ora)),
