@@ -147,3 +147,17 @@ def test_plan_limits_match_the_documented_sizes(form):
     assert code(1024, 16) == hps.HPS_ENOTSUP
     assert code(256, 24) == hps.HPS_OK
     assert code(512, 24) == hps.HPS_ENOTSUP
+
+
+def test_plan_counts_of_the_two_leaf_forms():
+    """hps_plan's flop and byte counts follow the leaf form: the LU form's
+    leaf work is n^3/3 + nb n^2 complex multiply-adds against n^3 + nb n p,
+    and it stores n row indices and n row scales a leaf beside the factors."""
+    m, p = 8, 16
+    lu = hps.hps_plan(hps.Problem(m, p, 10.0, 10.0, leaf_form=hps.HPS_LEAF_LU))
+    inv = hps.hps_plan(hps.Problem(m, p, 10.0, 10.0, leaf_form=hps.HPS_LEAF_INVERSE))
+    n, nb, leaves = p * p - 4, 4 * (p - 2), m * m
+    assert inv.build_flops - lu.build_flops == leaves * 8 * ((n ** 3 + nb * n * p) - (n ** 3 // 3 + nb * n * n))
+    assert lu.operator_bytes - inv.operator_bytes == leaves * n * (4 + 8)
+    assert lu.solve_flops == inv.solve_flops
+    assert lu.build_launches == inv.build_launches and lu.solve_launches == inv.solve_launches
