@@ -140,7 +140,9 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy);
  * merge level W^{-1}, R33a, R33b, R13a, R23b, Phi_a, Phi_b, up to the root
  * ItI operator.
  *   c:    [leaves][(p-2)^2] real c(x) at each leaf's interior nodes (the
- *         boundary rows of the leaf system do not involve c)
+ *         boundary rows of the leaf system do not involve c), finite; a
+ *         host array with a NaN or infinity is HPS_EINVAL (device arrays
+ *         are not scanned: non-finite values there give non-finite operators)
  *   out:  receives the new handle; unchanged on failure
  * Device memory for all operators is allocated here and owned by the handle.
  * Returns HPS_EINVAL (bad descriptor, NULL c/out), HPS_ENOMEM, HPS_ECUDA, or
@@ -176,7 +178,8 @@ int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, vo
  * launch sequence is captured into a CUDA graph by the first call and
  * replayed by every later one, so a rebuild costs one graph launch on top of
  * the copies of c.
- *   c[k]: [leaves][(p-2)^2] of hs[k], device or host memory.
+ *   c[k]: [leaves][(p-2)^2] of hs[k], device or host memory (finite, as for
+ *         hps_build).
  * Work that used the old operators must be ordered before the call (same
  * stream, or events).  hps_build_times keeps the first build's phases.
  * Returns HPS_EINVAL (not exactly the build's handles, a handle of the build

@@ -1729,6 +1729,12 @@ int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, vo
         descs[k].fp64_levels != descs[0].fp64_levels || descs[k].fp64_native != descs[0].fp64_native ||
         descs[k].leaf_form != descs[0].leaf_form)
       return HPS_EINVAL;
+    // host samples of c are checked here (device ones are not scanned)
+    if (!is_device_ptr(c[k])) {
+      const long long cnt = (long long)descs[k].mx * descs[k].my * (descs[k].p - 2) * (descs[k].p - 2);
+      for (long long i = 0; i < cnt; i++)
+        if (!std::isfinite(c[k][i])) return HPS_EINVAL;
+    }
   }
   std::vector<hps_handle *> hs(nprob, nullptr);
   auto release = [&]() {
@@ -2001,6 +2007,11 @@ int hps_rebuild(int nh, hps_handle *const *hs, const double *const *c, void *str
     if (!hs[k] || hs[k]->sh != sh || !c[k]) return HPS_EINVAL;
     for (int q = 0; q < k; q++)
       if (hs[q] == hs[k]) return HPS_EINVAL;
+    if (!is_device_ptr(c[k])) {  // host samples are checked (device ones are not scanned)
+      const long long cnt = (long long)hs[k]->plan.leaves * hs[k]->plan.ni;
+      for (long long i = 0; i < cnt; i++)
+        if (!std::isfinite(c[k][i])) return HPS_EINVAL;
+    }
   }
   cudaStream_t st = (cudaStream_t)stream;
   for (int k = 0; k < nh; k++) {

@@ -161,3 +161,14 @@ def test_plan_counts_of_the_two_leaf_forms():
     assert lu.operator_bytes - inv.operator_bytes == leaves * n * (4 + 8)
     assert lu.solve_flops == inv.solve_flops
     assert lu.build_launches == inv.build_launches and lu.solve_launches == inv.solve_launches
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -float("inf")])
+def test_non_finite_host_coefficients_are_rejected(bad):
+    """A host c with a NaN or an infinity is HPS_EINVAL before any device work."""
+    d = _desc()
+    c = np.ones(4 * 4 * 36)
+    c[77] = bad
+    h = ctypes.c_void_p()
+    assert hps.lib().hps_build(ctypes.byref(d), c.ctypes.data, None, ctypes.byref(h)) == hps.HPS_EINVAL
+    assert h.value is None
