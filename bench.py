@@ -668,6 +668,73 @@ def zgemm(args, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def scaling(args, local_rank):
+    """Build and solve times across leaf counts (4 x 4 ... 128 x 128, p = 16,
+    kappa = eta = 80, the point-source workload at each size) for the LU and
+    inverse leaf forms in complex128 and the LU form on the mixed path: one
+    JSON line per problem.  Builds: median of 3 (2 at 128 x 128) after the
+    problem's kernel choices are measured; solves with device-resident
+    vectors, 1 RHS (median of 10) and a wide batch (64 RHS, 16 at 128 x 128)."""
+    import torch
+
+    from paper_1812_07167_gb300 import hps
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    st = torch.cuda.current_stream()
+    for m in (4, 8, 16, 32, 64, 128):
+        wl = W.point_sources(m=m, p=P_ORDER, kappa=KAPPA)
+        for form, prec in ((hps.HPS_LEAF_LU, hps.HPS_FP64), (hps.HPS_LEAF_INVERSE, hps.HPS_FP64),
+                           (hps.HPS_LEAF_LU, hps.HPS_MIXED)):
+            pr = hps.Problem(m, P_ORDER, KAPPA, KAPPA, precision=prec, leaf_form=form)
+            lxy, bxy = hps.hps_nodes(pr)
+            c, s, t = wl.sample(lxy, bxy)
+            cd = torch.from_numpy(c).to(dev)
+            hps.hps_tune([pr], st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            bt = []
+            for _ in range(3 if m < 128 else 2):
+                e0.record(st)
+                h = hps.hps_build(pr, cd, st)
+                e1.record(st)
+                torch.cuda.synchronize()
+                bt.append(e0.elapsed_time(e1))
+                h.free()
+            h = hps.hps_build(pr, cd, st)
+            sd = torch.from_numpy(np.ascontiguousarray(s[None])).to(dev)
+            td = torch.from_numpy(np.ascontiguousarray(t[None])).to(dev)
+            ud = torch.empty((1, pr.leaves, pr.n), dtype=torch.complex128, device=dev)
+            lt = []
+            for k in range(12):
+                e0.record(st)
+                hps.hps_solve(h, sd, td, ud, 1, st)
+                e1.record(st)
+                torch.cuda.synchronize()
+                if k >= 2:
+                    lt.append(e0.elapsed_time(e1))
+            R = 64 if m <= 64 else 16
+            S = sd.repeat(R, 1, 1).contiguous()
+            T = td.repeat(R, 1).contiguous()
+            U = torch.empty((R, pr.leaves, pr.n), dtype=torch.complex128, device=dev)
+            hps.hps_solve(h, S, T, U, R, st)
+            torch.cuda.synchronize()
+            e0.record(st)
+            hps.hps_solve(h, S, T, U, R, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            wide = e0.elapsed_time(e1)
+            info = h.info()
+            h.free()
+            del S, T, U
+            torch.cuda.empty_cache()
+            dof = pr.leaves * pr.n
+            print(json.dumps({"m": m, "leaf_form": "lu" if form == hps.HPS_LEAF_LU else "inverse",
+                              "precision": "fp64" if prec == hps.HPS_FP64 else "mixed",
+                              "build_ms": statistics.median(bt), "build_dof_per_s": dof / (statistics.median(bt) / 1e3),
+                              "solve_1rhs_ms": statistics.median(lt), "wide_nrhs": R, "wide_ms": wide,
+                              "wide_rhs_per_s": R / (wide / 1e3), "operator_bytes": info.operator_bytes}), flush=True)
+
+
 def serving_run(args, local_rank, precision):
     """Config-5 serving workload: a 128 x 128-leaf solver (p = 16, kappa = eta
     = 600, random medium, seed 3) resident in HBM, and a Poisson stream of
@@ -804,6 +871,8 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="run the 64x64-leaf FP64-vs-mixed workload (with the oracle) instead of the step bench")
     ap.add_argument("--no-batching", action="store_true", help="skip the ragged-batch section")
+    ap.add_argument("--scaling", action="store_true",
+                    help="build and solve times from 4 x 4 to 128 x 128 leaves, both leaf forms")
     ap.add_argument("--leaf-form", default="lu", choices=["lu", "inverse"],
                     help="leaf operators as LU factors (default) or as B^-1")
     ap.add_argument("--serve-resident-form", default="inverse", choices=["lu", "inverse"],
@@ -830,6 +899,9 @@ def main():
         return
     if args.zgemm:
         zgemm(args, local_rank)
+        return
+    if args.scaling:
+        scaling(args, local_rank)
         return
     if world > 1:
         import torch.distributed as dist
