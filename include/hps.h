@@ -247,8 +247,8 @@ int hps_reserve(hps_handle *h, int nrhs);
  * workspace than the array holds.
  * Returns HPS_ETOOBIG when nrhs right-hand sides of this handle's tree need
  * more workspace than the array holds (about 1.8 MB per right-hand side for
- * 16 x 16 leaves with p = 16, plus 0.6 to 5 MB for the partial sums of the
- * skinny products of up to 8 right-hand sides), HPS_EINVAL for bad
+ * 16 x 16 leaves with p = 16, plus 0.6 to 10 MB for the partial sums of the
+ * skinny products of up to 16 right-hand sides), HPS_EINVAL for bad
  * arguments, HPS_ECUDA if the
  * workspace address cannot be obtained.  nrhs == 0 returns HPS_OK.
  * The first call on a device looks up the array's device address (once per
