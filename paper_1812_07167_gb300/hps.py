@@ -121,7 +121,7 @@ class Problem:
     refine_steps: int = 0
     fp64_native: int = 0
     my: int = 0  # leaves along y (0: the same as m, the leaves along x)
-    leaf_form: int = HPS_LEAF_LU
+    leaf_form: int = HPS_LEAF_LU  # leaf operators as LU factors, or HPS_LEAF_INVERSE: as B^-1
 
     @property
     def ny(self) -> int:
