@@ -551,15 +551,23 @@ bool choose_gj_rule(int n3, long long P, int f32, GJChoice &g);
 // false when no regime fits in the kernels' shared memory
 bool choose_gj(int n3, long long P, int f32, GJChoice &g) {
   int v;
+  bool ok = false;
   if (P <= (1 << 30) && tuned(TuneKey{1, n3, 0, 0, (int)P, f32}, v) && v != 0) {
     GJChoice t = gj_decode(v);
     t.tglobal = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, f32, t.kb) > 200 * 1024;
     if (t.wide || hps::gj_smem_bytes(n3, t.cs, false, 0, t.tglobal, f32, t.kb) <= 227 * 1024) {
       g = t;
-      return true;
+      ok = true;
     }
   }
-  return choose_gj_rule(n3, P, f32, g);
+  if (!ok) ok = choose_gj_rule(n3, P, f32, g);
+  // HPS_GJ_KB=4: panels of 4 columns whatever was chosen (it needs less
+  // shared memory than 8, so the choice still fits); for tests of that width
+  if (ok) {
+    const char *e = getenv("HPS_GJ_KB");
+    if (e && atoi(e) == 4) g.kb = 4;
+  }
+  return ok;
 }
 
 bool choose_gj_rule(int n3, long long P, int f32, GJChoice &g) {

@@ -325,3 +325,29 @@ def test_leaf_forms_agree_on_the_bench_problem():
         h.free()
     assert _rel(out[0][0], out[1][0]) < TOL
     assert _rel(out[0][1], out[1][1]) < TOL
+
+
+@pytest.mark.parametrize("wide", ["0", "1"])
+def test_interface_inverse_panels_of_four(wide, monkeypatch):
+    """The interface inverses with panels of 4 columns (the width hps_tune
+    picks for the top levels), in the cluster and in the panel-per-launch
+    kernel, against the oracle."""
+    monkeypatch.setenv("HPS_GJ_KB", "4")
+    if wide == "0":
+        monkeypatch.setenv("HPS_NO_WIDE_GJ", "1")
+    else:
+        monkeypatch.delenv("HPS_NO_WIDE_GJ", raising=False)
+    # p = 14: interface shapes no other test tunes, so the rules (and the
+    # switch between the two kernels) decide
+    m, p, kappa, eta = 8, 14, 30.0, 30.0 - 2.0j
+    pr, opr = _pair(m, p, kappa, eta)
+    c, s, t = W.random_data(m, p, kappa, eta, seed=88, nrhs=2)
+    h = gpu_build(pr, c)
+    u = gpu_solve(h, s, t)
+    R = gpu_root_R(h)
+    with O.Tree(opr, c, nthreads=os.cpu_count() or 1) as T:
+        uo = T.solve(s, t, nthreads=os.cpu_count() or 1)
+        Ro = T.root_R()
+    assert _rel(u, uo) < TOL
+    assert _rel(R, Ro) < TOL
+    h.free()
