@@ -219,7 +219,7 @@ def test_64x64_leaves_reproduce_polynomial_and_sampled_leaves():
     At this size the oracle's own polynomial error is 6.4e-11 (measured once:
     it takes ~7 min on 8 cores, too long for a test).  The leaf matrices at
     h = 1/64 have condition numbers ~1e6 before row scaling, so two correct
-    FP64 inversions (LU in the oracle, equilibrated Gauss-Jordan here) differ
+    FP64 solutions (LU in the oracle, equilibrated LU by default here) differ
     by up to ~1e-10 in their smallest-scale operator Gamma; the bar for these
     intermediate operators is 1e-9."""
     wl = W.polynomial_solution(64, 16, 40.0, 40.0)
