@@ -735,6 +735,64 @@ def scaling(args, local_rank):
                               "wide_rhs_per_s": R / (wide / 1e3), "operator_bytes": info.operator_bytes}), flush=True)
 
 
+def polynomial(args, local_rank):
+    """Capacity check: an m x m-leaf problem (p = 16, kappa = eta = 40) whose
+    exact solution is a polynomial of degree p - 1 in x and y, which the
+    discretisation reproduces at every node to rounding.  Builds it twice
+    (CUDA events), solves once and reports the largest nodal error against
+    the polynomial and the device memory in use.  At m = 256 the host
+    sampling of s and t takes a few minutes."""
+    import torch
+
+    from paper_1812_07167_gb300 import hps
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    st = torch.cuda.current_stream()
+    m = args.polynomial
+    wl = W.polynomial_solution(m, P_ORDER, 40.0, 40.0)
+    pr = _problem(m, P_ORDER, wl.kappa, wl.eta)
+    lxy, bxy = hps.hps_nodes(pr)
+    c, s, t = wl.sample(lxy, bxy)
+    ue = wl.u_exact(lxy[..., 0], lxy[..., 1])
+    info = hps.hps_plan(pr)
+    cd = torch.from_numpy(c).to(dev)
+    hps.hps_tune([pr], st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bt = []
+    for k in range(2):
+        e0.record(st)
+        h = hps.hps_build(pr, cd, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        bt.append(e0.elapsed_time(e1))
+        code = hps.hps_status(h, st)[0]
+        if code != hps.HPS_OK:
+            raise RuntimeError(hps.hps_strerror(code))
+        phases = hps.hps_build_times(h)
+        if k == 0:
+            h.free()
+    sd = torch.from_numpy(np.ascontiguousarray(s[None])).to(dev)
+    td = torch.from_numpy(np.ascontiguousarray(t[None])).to(dev)
+    ud = torch.empty((1, pr.leaves, pr.n), dtype=torch.complex128, device=dev)
+    for _ in range(3):
+        e0.record(st)
+        hps.hps_solve(h, sd, td, ud, 1, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+    free, total = torch.cuda.mem_get_info()
+    u = ud.cpu().numpy()[0]
+    h.free()
+    dof = pr.leaves * pr.n
+    print(json.dumps({"workload": "polynomial solution", "m": m, "p": P_ORDER, "dof": dof,
+                      "leaf_form": "lu" if LEAF_FORM == 0 else "inverse",
+                      "build_ms": min(bt), "build_dof_per_s": dof / (min(bt) / 1e3),
+                      "build_phases_ms": [float(x) for x in phases], "solve_1rhs_ms": solve_ms,
+                      "rel_err_u_vs_polynomial": float(np.abs(u - ue).max() / np.abs(ue).max()),
+                      "operator_bytes": info.operator_bytes, "device_bytes_in_use": total - free}), flush=True)
+
+
 def serving_run(args, local_rank, precision):
     """Config-5 serving workload: a 128 x 128-leaf solver (p = 16, kappa = eta
     = 600, random medium, seed 3) resident in HBM, and a Poisson stream of
@@ -871,6 +929,8 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="run the 64x64-leaf FP64-vs-mixed workload (with the oracle) instead of the step bench")
     ap.add_argument("--no-batching", action="store_true", help="skip the ragged-batch section")
+    ap.add_argument("--polynomial", type=int, metavar="M",
+                    help="capacity check: M x M leaves, polynomial solution, nodal error and memory")
     ap.add_argument("--scaling", action="store_true",
                     help="build and solve times from 4 x 4 to 128 x 128 leaves, both leaf forms")
     ap.add_argument("--leaf-form", default="lu", choices=["lu", "inverse"],
@@ -902,6 +962,9 @@ def main():
         return
     if args.scaling:
         scaling(args, local_rank)
+        return
+    if args.polynomial:
+        polynomial(args, local_rank)
         return
     if world > 1:
         import torch.distributed as dist
