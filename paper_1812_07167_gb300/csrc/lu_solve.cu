@@ -63,7 +63,8 @@ __device__ __forceinline__ void sweep_row(C *y, const C *a, int n, int J0, int j
 // The update of rows [i0, i0 + rows) by the block's jb solved rows: a thread
 // per (row, share of the right-hand sides), the right-hand sides split S ways
 // while the rows are fewer than the threads, so that short updates keep the
-// FP64 pipes of every warp busy.
+// FP64 pipes of every warp busy.  y: the shared vector block from its row J0
+// (rows i and J0 + kk are at (i - J0) and kk; both lie in the block's range).
 template <class C, int RB, int S>
 __device__ __forceinline__ void sweep_rows_s(C *y, const C *LU, int n, int J0, int jb, int i0, int rows) {
   for (int t = threadIdx.x; t < rows * S; t += blockDim.x) {
@@ -71,8 +72,6 @@ __device__ __forceinline__ void sweep_rows_s(C *y, const C *LU, int n, int J0, i
     sweep_row<C, RB, RB / S>(y, LU + (size_t)J0 * n + i, n, J0, jb, i, c0);
   }
 }
-// (y: the shared vector block from its row J0, so rows i and J0 + kk index
-// it as (i - J0) and kk; both lie in the block's row range)
 
 template <class C, int RB>
 __device__ __forceinline__ void sweep_rows(C *y, const C *LU, int n, int J0, int jb, int i0, int rows) {
