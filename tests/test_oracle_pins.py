@@ -13,6 +13,7 @@ from numpy.polynomial import chebyshev as Ch
 from numpy.polynomial import legendre as Lg
 
 import oracle as O
+from _geometry import coincident_pairs
 from paper_1812_07167_gb300 import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -239,6 +240,25 @@ def test_leaf_identity_in_the_tree():
             Psi2, Y2, Gam2 = T.leaf_ops(leaf)
             np.testing.assert_array_equal(Psi2, Psi)
             np.testing.assert_array_equal(Gam2, Gam)
+
+
+def test_duplicate_interface_values_agree():
+    """Subtracting the two impedance-matching rows of a shared edge node
+    (Sec. 2.2) leaves 2 i eta (u_alpha - u_beta) = 0, so for eta != 0 both
+    copies of every interface node carry the same value to rounding."""
+    pr = O.Problem(4, 10, 13.0, 5.0 - 2.0j, 0.0, 1.0, -0.5, 0.5)
+    c, s, t = W.random_data(4, 10, 13.0, 5.0 - 2.0j, seed=31, nrhs=2)
+    lxy, _ = O.nodes(pr)
+    (la, lb), (na, nb) = coincident_pairs(lxy)
+    # 4 x 4 leaves: 24 interior leaf edges of p - 2 nodes each
+    assert la.size == 24 * (pr.p - 2)
+    with O.Tree(pr, c) as T:
+        u = T.solve(s, t)
+    d = np.abs(u[:, la, na] - u[:, lb, nb]).max()
+    assert d < 1e-11 * np.abs(u).max()
+    # and it is a property of the solution, not of the data: a single leaf's
+    # own solve does not have it
+    assert np.abs(u[:, la, na]).max() > 1e-3 * np.abs(u).max()
 
 
 # --------------------------------------------------------- convergence, ItI
