@@ -110,3 +110,46 @@ def test_mixed_equals_fp64_path_on_the_benchmark_problem():
     print("root R, mixed vs FP64:", relR)
     assert relR < 1e-3
     assert hmx.info().operator_bytes < h64.info().operator_bytes
+
+
+def test_random_medium_64x64_full_size():
+    """64 x 64 leaves, p = 16, kappa = eta = 300, random smooth medium with
+    eight Gaussian sources: the full-size random-medium workload, in the
+    launch configuration the benchmark times, checked through properties that
+    hold at any size (the oracle's full solve takes minutes):
+    the mixed path agrees with the FP64 path to the mixed bar; the two copies
+    of every shared interface node agree (Sec. 2.2); sampled leaves satisfy
+    their interior collocation rows (Sec. 2.1) and their operators match the
+    oracle's."""
+    from _geometry import coincident_pairs
+
+    wl = W.random_medium_sources(64, 16, 300.0)
+    pf = hps.Problem(wl.m, wl.p, wl.kappa, wl.eta)
+    lxy, bxy = hps.hps_nodes(pf)
+    c, s, t = wl.sample(lxy, bxy)
+    h64 = _build(pf, c)
+    u64 = _solve(h64, s[None], t[None])[0]
+    hmx = _build(_mixed(wl.m, wl.p, wl.kappa, wl.eta), c)  # library defaults: top 4 levels FP64, 2 steps
+    umx = _solve(hmx, s[None], t[None])[0]
+    hmx.free()
+    rel = _rel(umx, u64)
+    print("64 x 64, kappa 300: mixed vs FP64", rel)
+    assert rel <= TOL_MIXED
+    (la, lb), (na, nb) = coincident_pairs(lxy)
+    assert la.size == 2 * 64 * 63 * (wl.p - 2)
+    umax = np.abs(u64).max()
+    assert np.abs(u64[la, na] - u64[lb, nb]).max() <= 1e-10 * umax
+    assert np.abs(umx[la, na] - umx[lb, nb]).max() <= TOL_MIXED * umax
+    opr = O.Problem(wl.m, wl.p, wl.kappa, wl.eta)
+    nb_ = pf.nb
+    for leaf in (0, 63, 2080, 4095):
+        Psi, Y, R, Gam, B, F, G = O.leaf(opr, c[leaf], with_matrices=True)
+        r = B[nb_:] @ u64[leaf] - s[leaf]
+        bound = 1e-10 * np.abs(B[nb_:]).sum(axis=1).max() * np.abs(u64[leaf]).max()
+        assert np.abs(r).max() <= bound, (leaf, np.abs(r).max(), bound)
+        gPsi = np.zeros((pf.n, pf.nb), complex)
+        gGam = np.zeros((pf.nb, pf.ni), complex)
+        hps.hps_leaf_ops(h64, leaf, gPsi, None, gGam, torch.cuda.current_stream())
+        assert _rel(gPsi, Psi) < 1e-10
+        assert _rel(gGam, Gam) < 1e-9
+    h64.free()
