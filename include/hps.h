@@ -263,10 +263,17 @@ int hps_solve_noalloc(hps_handle *h, const double *s, const double *t, double *u
 /* The root ItI operator R (Definition of the ItI map; R f = g on the outer
  * boundary) in the outer-boundary order above.
  *   R: [nb][nb] complex with nb = 2 (mx + my) (p-2), row-major (R[i][j] maps incoming data
- *      at node j to outgoing data at node i)
+ *      at node j to outgoing data at node i); host or device memory
+ *   gauss_basis: 0 = R on the corner-free Chebyshev edge nodes (the basis the
+ *      solver works in); 1 = R_G = diag(P) R diag(P)^-1 on q = p-2 Gauss-Legendre
+ *      nodes per edge, P the polynomial interpolation from an edge's Chebyshev
+ *      nodes to its Gauss-Legendre nodes (an exact change of basis, since both
+ *      sets have p-2 points; the Gauss nodes of an edge run in increasing
+ *      coordinate like its Chebyshev nodes).  The change of basis runs on the
+ *      device in two batched products and takes a temporary of nb^2 complex.
  * The root R is the last merge's product; the build keeps it.  Returns
- * HPS_EINVAL or HPS_ECUDA. */
-int hps_root_R(hps_handle *h, double *R, void *stream);
+ * HPS_EINVAL (null h or R, gauss_basis not 0 or 1), HPS_ENOMEM or HPS_ECUDA. */
+int hps_root_R(hps_handle *h, double *R, int gauss_basis, void *stream);
 
 /* Operators of one leaf (Sec. 2.1.1, 2.1.2, 2.4), for inspection.
  *   Psi: [p^2-4][4(p-2)], Y: [p^2-4][(p-2)^2], Gam: [4(p-2)][(p-2)^2], each

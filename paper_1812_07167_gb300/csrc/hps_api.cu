@@ -1034,6 +1034,88 @@ static int noalloc_ws_ptr(char **out) {
   return HPS_OK;
 }
 
+namespace {
+
+// Gauss-Legendre nodes on [-1, 1], increasing: the roots of the Legendre
+// polynomial P_q, each by Newton's method from the asymptotic estimate
+// -cos(pi (i + 3/4) / (q + 1/2)), with P_q and P_q' from the three-term
+// recurrence k P_k = (2k - 1) z P_{k-1} - (k - 1) P_{k-2}.
+std::vector<double> gauss_legendre_nodes(int q) {
+  const double pi = std::acos(-1.0);
+  std::vector<double> x(q);
+  for (int i = 0; i < q; i++) {
+    double z = -std::cos(pi * (i + 0.75) / (q + 0.5));
+    for (int it = 0; it < 64; it++) {
+      double pm = 1.0, pk = z;  // P_{k-1}, P_k at k = 1
+      for (int k = 2; k <= q; k++) {
+        const double pn = ((2.0 * k - 1.0) * z * pk - (k - 1.0) * pm) / k;
+        pm = pk;
+        pk = pn;
+      }
+      const double dz = pk / (q * (z * pk - pm) / (z * z - 1.0));
+      z -= dz;
+      if (std::fabs(dz) <= 1e-15) break;
+    }
+    x[i] = z;
+  }
+  std::sort(x.begin(), x.end());
+  return x;
+}
+
+// L[i][j] = l_j(y_i), row-major: the Lagrange basis of the nodes x at the
+// points y, i.e. the map from values at x to values at y of the polynomial
+// of degree < |x| through them
+void lagrange_matrix(const std::vector<double> &x, const std::vector<double> &y, double2 *L) {
+  const int n = (int)x.size();
+  for (int i = 0; i < (int)y.size(); i++)
+    for (int j = 0; j < n; j++) {
+      double v = 1.0;
+      for (int k = 0; k < n; k++)
+        if (k != j) v *= (y[i] - x[k]) / (x[j] - x[k]);
+      L[(size_t)i * n + j] = make_double2(v, 0.0);
+    }
+}
+
+// The root ItI operator in the Gauss-Legendre basis of the boundary data:
+// with P the interpolation from the p - 2 corner-free Chebyshev nodes of an
+// edge to its q = p - 2 Gauss-Legendre nodes (an invertible change of basis
+// between polynomials of degree < q, the same on every edge, which all run
+// in increasing coordinate), R_G = diag(P) R diag(P)^-1.  Rt holds R^T
+// column-major (the public row-major R) and is overwritten with R_G^T =
+// diag(P^-T) R^T diag(P^T): two batched products over the edges, through a
+// temporary of the size of R.
+int root_R_to_gauss(const Plan &pl, double2 *Rt, cudaStream_t st) {
+  const int e = pl.e, nbr = pl.nbdry, edges = nbr / e;
+  std::vector<double> xc(e);
+  for (int j = 0; j < e; j++) xc[j] = -std::cos(std::acos(-1.0) * (j + 1) / (pl.p - 1));
+  const std::vector<double> xg = gauss_legendre_nodes(e);
+  std::vector<double2> tab(2 * (size_t)e * e);
+  lagrange_matrix(xc, xg, tab.data());                   // P
+  lagrange_matrix(xg, xc, tab.data() + (size_t)e * e);   // P^-1
+  const size_t tbytes = align256(sizeof(double2) * tab.size());
+  char *tmp = nullptr;
+  CK(cudaMallocAsync((void **)&tmp, tbytes + sizeof(double2) * (size_t)nbr * nbr, st));
+  const double2 *dP = (const double2 *)tmp, *dPi = dP + (size_t)e * e;
+  double2 *T = (double2 *)(tmp + tbytes);
+  // host tables are pageable: the copy has taken them when it returns
+  cudaError_t err = cudaMemcpyAsync(tmp, tab.data(), sizeof(double2) * tab.size(), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) {
+    // a row-major P read as a column-major matrix is P^T
+    // T = diag(P^-T) R^T: edge r's rows of T from edge r's rows of R^T
+    GemmDesc g1 = gemm(e, nbr, e, edges, mat(dPi, e, 0), mat(Rt, nbr, e), mat(T, nbr, e));
+    // R_G^T = T diag(P^T): edge c's columns
+    GemmDesc g2 = gemm(nbr, e, e, edges, mat(T, nbr, (long long)e * nbr), mat(dP, e, 0),
+                       mat(Rt, nbr, (long long)e * nbr));
+    err = hps::launch_gemm(&g1, 1, st);
+    if (err == cudaSuccess) err = hps::launch_gemm(&g2, 1, st);
+  }
+  const cudaError_t ferr = cudaFreeAsync(tmp, st);
+  if (err != cudaSuccess) return cuda_fail(err);
+  return cuda_fail(ferr);
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *hps_strerror(int code) {
@@ -2209,8 +2291,8 @@ int hps_solve_noalloc(hps_handle *h, const double *s_, const double *t_, double 
                       (cudaStream_t)stream);
 }
 
-int hps_root_R(hps_handle *h, double *R, void *stream) {
-  if (!h || !R) return HPS_EINVAL;
+int hps_root_R(hps_handle *h, double *R, int gauss_basis, void *stream) {
+  if (!h || !R || (gauss_basis != 0 && gauss_basis != 1)) return HPS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const int nbr = h->plan.nbdry;
   const bool dev = is_device_ptr(R);
@@ -2232,6 +2314,8 @@ int hps_root_R(hps_handle *h, double *R, void *stream) {
   cb.d[0] = copy(nr, nr, 1, mat(h->Rroot, nr, 0), mat(dst, nbr, 0, h->d_root_src, h->d_root_src));
   cb.d[0].trans = 1;
   CK(hps::launch_copy(cb, st));
+  if (gauss_basis)
+    if (int rc = root_R_to_gauss(h->plan, dst, st)) return rc;
   if (!dev) {
     CK(cudaMemcpyAsync(R, dst, bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

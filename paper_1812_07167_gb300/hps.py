@@ -88,7 +88,7 @@ def lib():
         L.hps_solve_batch.argtypes = [P, ctypes.c_int, P, P, P, P, P]
         L.hps_reserve.argtypes = [P, ctypes.c_int]
         L.hps_zgemm.argtypes = [ctypes.c_int] * 4 + [P, P, P, ctypes.c_int, P]
-        L.hps_root_R.argtypes = [P, P, P]
+        L.hps_root_R.argtypes = [P, P, ctypes.c_int, P]
         L.hps_leaf_ops.argtypes = [P, ctypes.c_int, P, P, P, P]
         L.hps_info.argtypes = [P, ctypes.POINTER(hps_info_t)]
         L.hps_plan.argtypes = [D, ctypes.POINTER(hps_info_t)]
@@ -311,8 +311,8 @@ def hps_solve_noalloc(h: Handle, s, t, u, nrhs: int, stream=None):
     return u
 
 
-def hps_root_R(h: Handle, R, stream=None):
-    _check(lib().hps_root_R(h.ptr, _ptr(R), _stream(stream)), "hps_root_R")
+def hps_root_R(h: Handle, R, stream=None, gauss_basis: bool = False):
+    _check(lib().hps_root_R(h.ptr, _ptr(R), int(bool(gauss_basis)), _stream(stream)), "hps_root_R")
     return R
 
 

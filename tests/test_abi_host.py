@@ -80,7 +80,7 @@ def test_null_arguments():
     assert hps.lib().hps_build(ctypes.byref(d), None, None, ctypes.byref(h)) == hps.HPS_EINVAL
     assert hps.lib().hps_build(None, None, None, ctypes.byref(h)) == hps.HPS_EINVAL
     assert hps.lib().hps_solve(None, None, None, None, 1, None) == hps.HPS_EINVAL
-    assert hps.lib().hps_root_R(None, None, None) == hps.HPS_EINVAL
+    assert hps.lib().hps_root_R(None, None, 0, None) == hps.HPS_EINVAL
     assert hps.lib().hps_leaf_ops(None, 0, None, None, None, None) == hps.HPS_EINVAL
     assert hps.lib().hps_status(None, None, None, None) == hps.HPS_EINVAL
     assert hps.lib().hps_info(None, None) == hps.HPS_EINVAL

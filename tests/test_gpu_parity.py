@@ -67,6 +67,78 @@ def gpu_root_R(h):
     return R
 
 
+def _cheb_to_gauss(p):
+    """Interpolation from the p-2 corner-free Chebyshev nodes of [-1, 1] to
+    the p-2 Gauss-Legendre nodes, through Legendre Vandermonde matrices, and
+    the Gauss weights."""
+    e = p - 2
+    xc = -np.cos(np.pi * np.arange(1, p - 1) / (p - 1))
+    g, w = np.polynomial.legendre.leggauss(e)
+    V = lambda x: np.polynomial.legendre.legvander(x, e - 1)
+    return V(g) @ np.linalg.inv(V(xc)), w
+
+
+@pytest.mark.parametrize("mx,my,p,kappa,eta", [(4, 4, 12, 20.0, 20.0), (4, 2, 10, 15.0, 6.0 - 2.0j),
+                                               (1, 1, 16, 12.0, 12.0), (2, 4, 6, 9.0, 9.0)])
+def test_root_R_in_gauss_basis(mx, my, p, kappa, eta):
+    """hps_root_R's Gauss-Legendre export (q = p - 2 nodes per edge): R_G =
+    diag(P) R diag(P)^-1 against the oracle's R taken to that basis by an
+    independent interpolation matrix."""
+    pr = hps.Problem(mx, p, kappa, eta, my=my)
+    opr = O.Problem(mx, p, kappa, eta, my=my)
+    c, _, _ = W.random_data(mx, p, kappa, eta, seed=3 * mx + my + p, my=my)
+    h = gpu_build(pr, c)
+    nb = pr.nbdry
+    RG = np.zeros((nb, nb), complex)
+    hps.hps_root_R(h, RG, torch.cuda.current_stream(), gauss_basis=True)
+    Rd = torch.zeros((nb, nb), dtype=torch.complex128, device="cuda")
+    hps.hps_root_R(h, Rd, torch.cuda.current_stream(), gauss_basis=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(Rd.cpu().numpy(), RG)
+    RC = gpu_root_R(h)
+    bad = np.zeros((nb, nb), complex)
+    assert hps.lib().hps_root_R(h.ptr, bad.ctypes.data, 2, None) == hps.HPS_EINVAL
+    with O.Tree(opr, c) as T:
+        Ro = T.root_R()
+    Pe, _ = _cheb_to_gauss(p)
+    Pb = np.kron(np.eye(nb // (p - 2)), Pe)
+    expect = Pb @ Ro @ np.linalg.inv(Pb)
+    assert _rel(RG, expect) < TOL
+    assert _rel(RC, Ro) < TOL
+    h.free()
+
+
+def test_gauss_basis_root_R_is_an_isometry():
+    """Real kappa, c and eta: in the Gauss-Legendre basis the L2 norm on an
+    edge is the weighted sum w |f|^2 h / 2, and the exported R_G preserves it
+    for smooth incoming data (Green's identity) and is symmetric in the
+    weighted bilinear pairing (reciprocity)."""
+    m, p = 4, 16
+    wl = W.plane_wave_bump(m=m, p=p)
+    pr = hps.Problem(wl.m, wl.p, wl.kappa, wl.eta)
+    lxy, bxy = hps.hps_nodes(pr)
+    c, _, _ = wl.sample(lxy, bxy)
+    h = gpu_build(pr, c)
+    RG = np.zeros((pr.nbdry, pr.nbdry), complex)
+    hps.hps_root_R(h, RG, torch.cuda.current_stream(), gauss_basis=True)
+    h.free()
+    Pe, w = _cheb_to_gauss(p)
+    Pb = np.kron(np.eye(4 * m), Pe)
+    Wg = np.kron(np.eye(4 * m), np.diag(w / (2 * m)))
+    side = W.boundary_sides(m, p)
+    F = []
+    for k, ang in enumerate(np.linspace(0.1, 2.9, 5)):
+        u, dudn = W._plane_wave(20.0 * (0.5 + 0.2 * k), ang)
+        F.append(dudn(bxy[:, 0], bxy[:, 1], side) + 1j * 20.0 * u(bxy[:, 0], bxy[:, 1]))
+    FG = Pb @ np.array(F).T
+    GG = RG @ FG
+    nf = np.real(np.einsum("ik,ij,jk->k", FG.conj(), Wg, FG))
+    ng = np.real(np.einsum("ik,ij,jk->k", GG.conj(), Wg, GG))
+    assert np.max(np.abs(ng - nf) / nf) < 1e-7  # 1.7e-9 with the oracle's R
+    S = FG.T @ Wg @ RG @ FG
+    assert np.abs(S - S.T).max() / np.abs(S).max() < 1e-7  # 3.8e-9 with the oracle's R
+
+
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("m,p,kappa,eta", [(1, 8, 7.0, 3.0 + 1.0j), (2, 16, 30.0, 30.0), (4, 12, 20.0, 20.0),
                                            (2, 7, 9.0, 4.0)])
