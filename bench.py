@@ -126,8 +126,9 @@ def run_oracle_step(c, s, t, threads):
     u = T.solve(s[None], t[None], nthreads=threads)[0]
     dt = time.perf_counter() - t0
     R = T.root_R()
+    cond = T.cond_W()
     T.close()
-    return dt, u, R
+    return dt, u, R, cond
 
 
 def reference_arm(args, rank, world):
@@ -444,16 +445,18 @@ def ours(args, rank, world, local_rank):
     }
     if world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        dt, u_ora, R_ora = run_oracle_step(c, s, t, threads)
+        dt, u_ora, R_ora, cond_ora = run_oracle_step(c, s, t, threads)
         line["cpu_baseline"] = {"value": dof / dt, "unit": "DOF/s", "cores": threads, "kind": "oracle",
                                 "sample": "one full 16x16-leaf build + 1-RHS solve"}
         # the same oracle on one thread, for the scale of its OpenMP speedup
-        dt1, _, _ = run_oracle_step(c, s, t, 1)
+        dt1 = run_oracle_step(c, s, t, 1)[0]
         line["cpu_baseline_single_thread"] = {"value": dof / dt1, "unit": "DOF/s", "cores": 1, "kind": "oracle",
                                               "sample": "one full 16x16-leaf build + 1-RHS solve"}
         line["rel_err_vs_oracle"] = {
             "u": float(np.abs(u_gpu - u_ora).max() / np.abs(u_ora).max()),
             "root_R": float(np.linalg.norm(R_gpu - R_ora) / np.linalg.norm(R_ora)),
+            # conditioning that bounds the agreement of two correct FP64 builds
+            "cond1_W_per_level_from_root": [float(f"{v:.3g}") for v in cond_ora],
         }
         line["mixed"]["rel_err_u_vs_oracle"] = float(np.abs(u_mixed - u_ora).max() / np.abs(u_ora).max())
         line["mixed"]["rel_err_root_R_vs_oracle"] = float(np.linalg.norm(R_mixed - R_ora) / np.linalg.norm(R_ora))
@@ -617,9 +620,11 @@ def precision(args, local_rank):
         uo = T.solve(s[None], t[None], nthreads=threads)[0]
         dt = time.perf_counter() - t0
         Ro = T.root_R()
+        cond = T.cond_W()
         T.close()
         out["cpu_baseline"] = {"value": dof / dt, "unit": "DOF/s", "cores": threads, "kind": "oracle",
                                "sample": "one full 64x64-leaf build + 1-RHS solve", "seconds": dt}
+        out["cond1_W_per_level_from_root"] = [float(f"{v:.3g}") for v in cond]
         for name in ("fp64", "mixed"):
             out[name]["rel_err_u_vs_oracle"] = float(np.abs(res[name]["u"] - uo).max() / np.abs(uo).max())
             out[name]["rel_err_root_R_vs_oracle"] = float(np.linalg.norm(res[name]["R"] - Ro) / np.linalg.norm(Ro))

@@ -117,6 +117,8 @@ def _lib_handle():
         lib.ora_free.argtypes = [P]
         lib.ora_brute.argtypes = [ctypes.POINTER(_Desc), P, P, P, P]
         lib.ora_max_threads.restype = ctypes.c_int
+        lib.ora_cond_W.argtypes = [P, ctypes.c_int]
+        lib.ora_cond_W.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -201,6 +203,18 @@ class Tree:
         if _lib_handle().ora_root_R(self._h, _ptr(R)):
             raise RuntimeError("root R not available")
         return R
+
+    def cond_W(self):
+        """Per merge level from the root down, the largest 1-norm condition
+        number of the interface matrices W = I - R33b R33a (Sec. 2.2)."""
+        out = []
+        lev = 0
+        while True:
+            v = float(_lib_handle().ora_cond_W(self._h, lev))
+            if v < 0:
+                return out
+            out.append(v)
+            lev += 1
 
     def leaf_ops(self, pub: int):
         pr = self.pr

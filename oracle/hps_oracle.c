@@ -101,6 +101,17 @@ static void matmul(int r, int k, int c, const cplx *A, const cplx *B, cplx *C) {
 
 static double cabs1(cplx z) { return fabs(creal(z)) + fabs(cimag(z)); }
 
+/* 1-norm of an n x n matrix: the largest column sum of moduli */
+static double norm1(int n, const cplx *A) {
+  double best = 0.0;
+  for (int j = 0; j < n; j++) {
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += cabs(A[(size_t)i * n + j]);
+    if (s > best) best = s;
+  }
+  return best;
+}
+
 /* LU factorisation with partial pivoting, in place (the zgetrf step).
  * Returns 0, or 1 + the column of the first exactly zero pivot. */
 static int lu_factor(int n, cplx *A, int *piv) {
@@ -487,6 +498,7 @@ typedef struct {
   int n1, n2, n3;
   int *I1, *I2, *I3a, *I3b;
   cplx *Winv, *R33a, *R33b, *R13a, *R23b, *Phia, *Phib;
+  double condW;        /* ||W||_1 ||W^{-1}||_1 of this merge */
 } ora_box;
 
 typedef struct {
@@ -572,6 +584,7 @@ static void merge_box(ora_tree *T, int tau) {
   }
   int bad = lu_solve_many(n3, W, n3, Id, Winv);
   if (bad && !T->status) T->status = 2;
+  P->condW = norm1(n3, W) * norm1(n3, Winv);
   /* Phi_a = W^{-1} [R33b R31a | -R32b] */
   cplx *T1 = xmalloc(sizeof(cplx) * n3 * n1), *Q = xmalloc(sizeof(cplx) * n3 * nt);
   matmul(n3, n3, n1, R33b, R31a, T1);
@@ -752,6 +765,18 @@ int ora_root_R(void *h, cplx *Rout) {
     for (int j = 0; j < nbr; j++) Rout[(size_t)i * nbr + j] = r->R[(size_t)perm[i] * nbr + perm[j]];
   free(perm);
   return 0;
+}
+
+/* The largest 1-norm condition number ||W||_1 ||W^{-1}||_1 of the interface
+ * matrices W = I - R33b R33a (Sec. 2.2) over the merges whose parent lies on
+ * tree level lev (0: the root's merge); -1 for a level without merges. */
+double ora_cond_W(void *h, int lev) {
+  ora_tree *T = h;
+  if (lev < 0 || lev >= T->L) return -1.0;
+  double best = 0.0;
+  for (int tau = 1 << lev; tau < (1 << (lev + 1)); tau++)
+    if (T->box[tau].condW > best) best = T->box[tau].condW;
+  return best;
 }
 
 /* Leaf operators as stored by the build, for the leaf with public index pub. */

@@ -242,6 +242,32 @@ def test_leaf_identity_in_the_tree():
             np.testing.assert_array_equal(Gam2, Gam)
 
 
+def test_interface_condition_number_of_two_leaves():
+    """cond_1(W) reported for the one merge of a 2 x 1 grid equals that of
+    W = I - R33b R33a assembled here from the two leaves' own ItI operators:
+    I3 is the west leaf's east edge and the east leaf's west edge (nodes
+    [e, 2e) and [3e, 4e) of the [S, E, N, W] order, both running upwards)."""
+    for kappa, eta in ((10.0, 10.0), (25.0, 4.0 - 3.0j)):
+        pr = O.Problem(2, 10, kappa, eta, my=1)
+        c, _, _ = W.random_data(2, 10, kappa, eta, seed=17, my=1)
+        e = pr.e
+        Ra = O.leaf(pr, c[0])[2]
+        Rb = O.leaf(pr, c[1])[2]
+        Wm = np.eye(e) - Rb[3 * e:, 3 * e:] @ Ra[e:2 * e, e:2 * e]
+        with O.Tree(pr, c) as T:
+            cw = T.cond_W()
+        assert len(cw) == 1
+        assert cw[0] == pytest.approx(np.linalg.cond(Wm, 1), rel=1e-8)
+
+
+def test_interface_condition_numbers_per_level():
+    pr = O.Problem(4, 8, 20.0, 20.0)
+    c, _, _ = W.random_data(4, 8, 20.0, 20.0, seed=2)
+    with O.Tree(pr, c) as T:
+        cw = T.cond_W()
+    assert len(cw) == 4 and all(v >= 1.0 for v in cw)
+
+
 def test_duplicate_interface_values_agree():
     """Subtracting the two impedance-matching rows of a shared edge node
     (Sec. 2.2) leaves 2 i eta (u_alpha - u_beta) = 0, so for eta != 0 both
