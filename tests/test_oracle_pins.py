@@ -140,7 +140,7 @@ def test_hps_equals_dense_global_solve(m, p, kappa, eta):
     ub = O.brute(pr, c, s[0], t[0])
     with O.Tree(pr, c) as T:
         u = T.solve(s, t)[0]
-    assert _rel(u, ub) < 1e-10
+    assert _rel(u, ub) < 1e-12  # the brute-force bar; measured 2e-15 ... 4.9e-13
 
 
 def test_merge_order_does_not_change_the_solution():
@@ -182,7 +182,7 @@ def test_rectangular_grid_equals_dense_global_solve(mx, my):
     ub = O.brute(pr, c, s[0], t[0])
     with O.Tree(pr, c) as T:
         u = T.solve(s, t)[0]
-    assert _rel(u, ub) < 1e-10
+    assert _rel(u, ub) < 1e-12  # the brute-force bar; measured 2e-15 ... 4.9e-13
 
 
 def test_rectangular_grid_nodes_cover_the_domain():
