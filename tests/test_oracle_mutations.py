@@ -2,8 +2,8 @@
 
 Each case plants one mistake (a wrong sign, a dropped term, a transposed
 operand, a wrong index) in a copy of the oracle's C source, compiles it on
-the CPU, and checks that the polynomial-exactness pin or the dense
-global-solve pin then fails.  The unmodified oracle passes both (see
+the CPU, and checks that the polynomial-exactness pin, the dense
+global-solve pin or the two-leaf interface-conditioning pin then fails.  The unmodified oracle passes both (see
 test_oracle_pins.py)."""
 import os
 import shutil
@@ -31,6 +31,8 @@ MUTATIONS = {
     "down_t3a_sign": ("tv[2 * tau][b->I3a[i]] = t3a[i] + tta[tau][i];",
                       "tv[2 * tau][b->I3a[i]] = t3a[i] - tta[tau][i];"),
     "Rtau_diag_block": ("((j >= n1) ? R22b[i * n2 + (j - n1)] : 0.0)", "0.0"),
+    "norm1_row_sums": ("s += cabs(A[(size_t)i * n + j]);", "s += cabs(A[(size_t)j * n + i]);"),
+    "condW_without_inverse": ("P->condW = norm1(n3, W) * norm1(n3, Winv);", "P->condW = norm1(n3, W);"),
 }
 
 CHECK = r"""
@@ -56,7 +58,17 @@ try:
     brute = float(np.nan_to_num(np.abs(u2 - ub).max() / np.abs(ub).max(), nan=1e300))
 except Exception:
     brute = 1e300
-print(poly, brute)
+# cond_1(W) of the one merge of a 2 x 1 grid against W assembled from the
+# leaves' ItI operators (west leaf's east edge, east leaf's west edge)
+pr3 = O.Problem(2, 8, 12.0, 3.0 - 2.0j, my=1)
+c3, _, _ = W.random_data(2, 8, 12.0, 3.0 - 2.0j, seed=5, my=1)
+e = pr3.e
+Ra, Rb = O.leaf(pr3, c3[0])[2], O.leaf(pr3, c3[1])[2]
+Wm = np.eye(e) - Rb[3 * e:, 3 * e:] @ Ra[e:2 * e, e:2 * e]
+with O.Tree(pr3, c3) as T3:
+    cw = T3.cond_W()[0]
+cond = abs(cw / np.linalg.cond(Wm, 1) - 1.0)
+print(poly, brute, cond)
 """
 
 
@@ -71,19 +83,18 @@ def _run_variant(tmp_path, old, new):
     env = dict(os.environ, HPS_ORACLE_LIB=str(lib), OMP_NUM_THREADS="1")
     out = subprocess.run([sys.executable, "-c", CHECK % {"root": ROOT}], env=env, check=True,
                          capture_output=True, text=True, timeout=300)
-    poly, brute = map(float, out.stdout.split()[-2:])
-    return poly, brute
+    return tuple(map(float, out.stdout.split()[-3:]))
 
 
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(name, tmp_path):
     old, new = MUTATIONS[name]
-    poly, brute = _run_variant(tmp_path, old, new)
-    assert poly > 1e-6 or brute > 1e-6, (name, poly, brute)
+    poly, brute, cond = _run_variant(tmp_path, old, new)
+    assert poly > 1e-6 or brute > 1e-6 or cond > 1e-6, (name, poly, brute, cond)
 
 
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
 def test_unmutated_copy_passes(tmp_path):
-    poly, brute = _run_variant(tmp_path, "int ora_max_threads(void) {", "int ora_max_threads(void) {")
-    assert poly < 1e-10 and brute < 1e-10
+    poly, brute, cond = _run_variant(tmp_path, "int ora_max_threads(void) {", "int ora_max_threads(void) {")
+    assert poly < 1e-10 and brute < 1e-10 and cond < 1e-8
