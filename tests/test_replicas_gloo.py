@@ -32,7 +32,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_aggregation():
     world = 2
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of this multi-threaded process
         out = mgr.dict()
         mp.start_processes(_worker, args=(world, _free_port(), out), nprocs=world, start_method="spawn")
         res = dict(out)
