@@ -172,3 +172,14 @@ def test_non_finite_host_coefficients_are_rejected(bad):
     h = ctypes.c_void_p()
     assert hps.lib().hps_build(ctypes.byref(d), c.ctypes.data, None, ctypes.byref(h)) == hps.HPS_EINVAL
     assert h.value is None
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    """No CPU fallback: with the shared library absent, the first call raises
+    instead of computing anything."""
+    monkeypatch.setattr(hps, "_lib", None)
+    monkeypatch.setattr(hps, "LIB_PATH", os.path.join(os.path.dirname(hps.LIB_PATH), "missing_libhps.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        hps.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        hps.hps_plan(hps.Problem(4, 8, 10.0, 10.0))
