@@ -40,7 +40,9 @@ def _stale(target: str, deps) -> bool:
 
 def build(verbose: bool = False, force: bool = False, extra=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, "hps_internal.h"), os.path.join(ROOT, "include", "hps.h")]
+    # every header a translation unit may include
+    headers = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".h", ".cuh"))]
+    headers.append(os.path.join(ROOT, "include", "hps.h"))
     cc = nvcc()
     objs = []
     jobs = []
