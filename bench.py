@@ -243,6 +243,8 @@ def ours(args, rank, world, local_rank):
                 handles.pop(0).free()
         torch.cuda.synchronize()
         t_wall1 = time.perf_counter()
+    if dist:
+        dist.barrier()  # every rank's timed region has ended
     for hh in handles:
         leaf_ms.append(hps.hps_build_times(hh)[0])
         hh.free()
