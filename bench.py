@@ -226,10 +226,10 @@ def ours(args, rank, world, local_rank):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     leaf_ms = []
     handles = []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
+    with ClockSampler(local_rank) as clk:  # started (first sample seen) before the barrier
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         t_wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
