@@ -16,7 +16,9 @@
  *     (Sec. 2.1, Eqs. for A-hat, N, F, G; Sec. 2.1.1 and 2.1.2).
  *   - Merge of two siblings: I1/I2/I3 split, W = I - R33b R33a, Phi_a,
  *     Upsilon_a, Phi_b, Upsilon_b, R^tau (Sec. 2.2, Eqs. (talpha), (tbeta),
- *     (out), (flux_part)); stored operators as in Sec. 2.4.
+ *     (out), (flux_part)); stored operators as in Sec. 2.4; and, as a
+ *     diagnostic, ||W||_1 ||W^{-1}||_1 of every merge (the conditioning that
+ *     bounds how far two correct FP64 builds can drift apart).
  *   - Build: Algorithm 1 (boxes processed from the largest index down to the
  *     root); the optional thread team processes one level at a time as in
  *     Algorithm 3, which changes no arithmetic.
