@@ -240,6 +240,10 @@ def test_leaf_identity_in_the_tree():
             Psi2, Y2, Gam2 = T.leaf_ops(leaf)
             np.testing.assert_array_equal(Psi2, Psi)
             np.testing.assert_array_equal(Gam2, Gam)
+            # outgoing data: G u = R t + Gamma s with t = F u the incoming data
+            tl = r[:pr.nb]
+            np.testing.assert_allclose(G @ u[leaf], R @ tl + Gam @ s[0, leaf],
+                                       atol=1e-12 * np.abs(G @ u[leaf]).max())  # ~2e-14 measured
 
 
 def test_interface_condition_number_of_two_leaves():
