@@ -49,6 +49,10 @@
  * return once the work is enqueued.  A handle must not be used from two
  * host threads at the same time.
  *
+ * Devices: a handle's operators live on the device that was current when it
+ * was built; hps_solve, hps_solve_batch, hps_solve_noalloc and hps_reserve
+ * return HPS_EINVAL when another device is current.
+ *
  * Errors: every call returns one of the HPS_* codes below; nothing aborts
  * and no kernel traps.  Numerical failures found on the device (an exactly
  * zero pivot) are recorded in the handle and reported by hps_status().
@@ -253,10 +257,17 @@ int hps_reserve(hps_handle *h, int nrhs);
  * workspace address cannot be obtained.  nrhs == 0 returns HPS_OK.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array: calls whose work overlaps on the
- * GPU (different streams, or different handles, without ordering between
- * them) race on it and must be serialized by the caller.  Nothing in the
- * array needs to start at zero; each call overwrites what it reads. */
+ * capture.  All calls share the one array, which keeps what the last call
+ * left in it: calls whose work overlaps on the GPU (different streams, or
+ * different handles, without ordering between them) race on it and must be
+ * serialized by the caller; such a race gives wrong solutions for the calls
+ * involved.  The solve vectors in the array are written before they are
+ * read; the arrival counters of the split skinny products at its head must
+ * start at zero, and every call clears them (a cudaMemsetAsync on `stream`,
+ * which allocates nothing) before its first launch, so a race does not
+ * carry over into later, ordered calls.
+ * Returns HPS_EINVAL when the current device is not the one the handle was
+ * built on. */
 int hps_solve_noalloc(hps_handle *h, const double *s, const double *t, double *u, int nrhs,
                       void *stream);
 

@@ -114,6 +114,7 @@ struct hps_handle {
   int *d_root_src = nullptr;
   unsigned int *d_status = nullptr;
   int leaf_cs = 8;
+  int device = -1;  // the CUDA device the operators live on (current at build time)
   // solve workspace (grown on demand)
   void *ws = nullptr;
   size_t ws_bytes = 0;
@@ -1016,6 +1017,14 @@ static int solve_refine(hps_handle *h, const double2 *s, const double2 *t, doubl
 // cudaGetSymbolAddress, taken once per device with that device current.
 static __device__ __align__(256) unsigned char g_noalloc_ws[HPS_NOALLOC_WORKSPACE_BYTES];
 
+// HPS_OK when the current device is the one the handle's operators live on;
+// launches from another device would read them through the wrong context.
+static int on_handle_device(const hps_handle *h) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  return dev == h->device ? HPS_OK : HPS_EINVAL;
+}
+
 static int noalloc_ws_ptr(char **out) {
   constexpr int kMaxDev = 64;
   static std::mutex mu;
@@ -1849,6 +1858,12 @@ int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, vo
     release();
     return HPS_ENOMEM;
   }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    release();
+    return HPS_ECUDA;
+  }
+  for (hps_handle *x : hs) x->device = dev;
   // build order: tallest tree first (stable), so that on every merge level
   // the problems that still have it come first
   std::vector<int> order(nprob);
@@ -2163,6 +2178,7 @@ int hps_solve(hps_handle *h, const double *s_, const double *t_, double *u_, int
   if (!h || nrhs < 0) return HPS_EINVAL;
   if (nrhs == 0) return HPS_OK;
   if (!s_ || !t_ || !u_) return HPS_EINVAL;
+  if (int dst = on_handle_device(h)) return dst;
   cudaStream_t st = (cudaStream_t)stream;
   const Plan &pl = h->plan;
   const int n = pl.n, ni = pl.ni, nl = pl.leaves, R = nrhs;
@@ -2213,6 +2229,7 @@ int hps_solve(hps_handle *h, const double *s_, const double *t_, double *u_, int
 
 int hps_reserve(hps_handle *h, int nrhs) {
   if (!h || nrhs < 0) return HPS_EINVAL;
+  if (int dst = on_handle_device(h)) return dst;
   const Plan &pl = h->plan;
   SolveWs ws;
   solve_ws_layout(pl, std::max(nrhs, 1), ws);
@@ -2229,6 +2246,7 @@ int hps_solve_batch(hps_handle *h, int nreq, const double *const *s_, const doub
   if (!h || nreq < 0) return HPS_EINVAL;
   if (nreq == 0) return HPS_OK;
   if (!s_ || !t_ || !u_ || !nrhs) return HPS_EINVAL;
+  if (int dst = on_handle_device(h)) return dst;
   long long Rl = 0;
   bool all_dev = true;
   for (int k = 0; k < nreq; k++) {
@@ -2278,6 +2296,7 @@ int hps_solve_noalloc(hps_handle *h, const double *s_, const double *t_, double 
   if (nrhs == 0) return HPS_OK;
   if (!s_ || !t_ || !u_) return HPS_EINVAL;
   if (!is_device_ptr(s_) || !is_device_ptr(t_) || !is_device_ptr(u_)) return HPS_EINVAL;
+  if (int dst = on_handle_device(h)) return dst;
   if (h->plan.mixed) return HPS_ENOTSUP;  // refinement needs more workspace than the fixed array
   SolveWs ws;
   solve_ws_layout(h->plan, nrhs, ws, false);  // no digit planes: products stay on the FP64 pipes
@@ -2285,8 +2304,13 @@ int hps_solve_noalloc(hps_handle *h, const double *s_, const double *t_, double 
   char *wb = nullptr;
   int st = noalloc_ws_ptr(&wb);
   if (st) return st;
-  // every buffer of the workspace is written before it is read, so nothing
-  // left there by an earlier call needs clearing
+  // The vectors of the workspace are written before they are read, but the
+  // split skinny products keep arrival counters at its head that must be
+  // zero when a launch starts (each launch leaves them zero when it
+  // finishes).  Two calls that overlapped on the GPU can leave them
+  // nonzero, so every call clears them first, in stream order; a memset
+  // allocates nothing.
+  CK(cudaMemsetAsync(wb, 0, hps::gemv_scratch_counters(), (cudaStream_t)stream));
   return solve_launch(h, (const double2 *)s_, (const double2 *)t_, (double2 *)u_, nrhs, wb, ws,
                       (cudaStream_t)stream);
 }

@@ -240,9 +240,20 @@ class Server:
                 build_q.popleft()
                 k = next(j for j in range(len(self.build_streams)) if j not in building)
                 r.launched = clock() - t0
-                r.handle, ev = self.be.launch_build(r.problem, r.c, self.build_streams[k])
-                building[k] = (r, ev)
                 busy = True
+                try:
+                    r.handle, ev = self.be.launch_build(r.problem, r.c, self.build_streams[k])
+                except hps.HPSError as exc:
+                    # the free-memory estimate can be wrong either way (the
+                    # allocator caches and pools): fail this request, keep serving
+                    r.handle = None
+                    r.error = hps.hps_strerror(exc.code)
+                    r.done = clock() - t0
+                    if on_done:
+                        on_done(r)
+                    left -= 1
+                    continue
+                building[k] = (r, ev)
             if not busy:
                 sleep(idle_s)
         return requests

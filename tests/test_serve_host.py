@@ -202,6 +202,40 @@ def test_build_larger_than_the_device_fails_with_enomem():
     assert reqs[1].error is None
 
 
+class FailingBuildBackend(FakeBackend):
+    """launch_build raises for problems of size fail_m, as hps_build does when
+    its arena allocation fails although the free-memory estimate admitted it."""
+
+    def __init__(self, clock, fail_m, **kw):
+        super().__init__(clock, **kw)
+        self.fail_m = fail_m
+
+    def launch_build(self, problem, c, stream):
+        if problem.m == self.fail_m:
+            raise hps.HPSError(hps.HPS_ENOMEM, "hps_build")
+        return super().launch_build(problem, c, stream)
+
+
+def test_failed_build_launch_fails_only_its_request():
+    clock = Clock()
+    be = FailingBuildBackend(clock, fail_m=32)
+    reqs = [serve.Request(0, 0.0, "build", problem=hps.Problem(32, 16, 50.0, 50.0)),
+            serve.Request(1, 0.0, "solve", key="main", nrhs=3),
+            serve.Request(2, 0.001, "build", problem=hps.Problem(16, 16, 50.0, 50.0)),
+            serve.Request(3, 0.002, "solve", key="main", nrhs=1)]
+    seen = []
+    srv = serve.Server(be, reserve_bytes=0)
+    srv.add_solver("main", Handle(0))
+    srv.run(reqs, clock=clock, sleep=clock.sleep, on_done=seen.append)
+    bad, s1, good, s2 = reqs
+    assert bad.error == hps.hps_strerror(hps.HPS_ENOMEM) and bad.handle is None
+    assert bad.done >= bad.launched
+    assert good.error is None and good.handle is not None and good.handle.alive
+    assert s1.error is None and s2.error is None and s1.u is not None and s2.u is not None
+    # every request completed exactly once
+    assert sorted(r.rid for r in seen) == [0, 1, 2, 3]
+
+
 def test_unknown_solver_is_refused():
     clock = Clock()
     srv = serve.Server(FakeBackend(clock))

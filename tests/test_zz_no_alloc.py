@@ -24,15 +24,19 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-def test_noalloc_solve_matches_solve_on_two_calls():
+# nrhs = 1 runs the chained launches of a one-column solve; 3 the split
+# skinny products, whose arrival counters sit at the head of the array; 20
+# the tiled products with no partial-sum region (it fits the array only on
+# a 4 x 4-leaf tree)
+@pytest.mark.parametrize("m,nrhs", [(16, 1), (16, 3), (4, 20)])
+def test_noalloc_solve_matches_solve_on_two_calls(m, nrhs):
     assert torch.cuda.is_available(), "needs a CUDA device"
-    wl = W.point_sources()  # 16 x 16 leaves, p = 16, kappa = eta = 80
+    wl = W.point_sources(m=m)  # p = 16, kappa = eta = 80
     pr = hps.Problem(wl.m, wl.p, wl.kappa, wl.eta)
     lxy, bxy = hps.hps_nodes(pr)
     c, _, _ = wl.sample(lxy, bxy)
     st = torch.cuda.current_stream()
     h = hps.hps_build(pr, torch.from_numpy(c).cuda(), st)
-    nrhs = 3
     for call in range(2):
         # different right-hand sides on each call, so a stale workspace shows
         _, s, t = W.random_data(wl.m, wl.p, wl.kappa, wl.eta, seed=500 + call, nrhs=nrhs)
@@ -66,3 +70,12 @@ def test_noalloc_solve_rejects_what_it_cannot_serve():
     assert L.hps_solve_noalloc(h.ptr, s.ctypes.data, t.ctypes.data, u_host.ctypes.data, 1, None) == hps.HPS_EINVAL
     assert L.hps_solve_noalloc(h.ptr, sd.data_ptr(), td.data_ptr(), u.data_ptr(), 0, None) == hps.HPS_OK
     h.free()
+    # a mixed-precision solver refines every solve, which needs more workspace
+    # than the fixed array holds: refused, not run
+    pm = hps.Problem(4, 16, wl.kappa, wl.eta, precision=hps.HPS_MIXED)
+    cm, sm, tm = W.random_data(4, 16, wl.kappa, wl.eta, seed=10)
+    hm = hps.hps_build(pm, torch.from_numpy(cm).cuda(), st)
+    smd, tmd = torch.from_numpy(sm).cuda(), torch.from_numpy(tm).cuda()
+    um = torch.empty((1, pm.leaves, pm.n), dtype=torch.complex128, device="cuda")
+    assert L.hps_solve_noalloc(hm.ptr, smd.data_ptr(), tmd.data_ptr(), um.data_ptr(), 1, None) == hps.HPS_ENOTSUP
+    hm.free()
