@@ -69,7 +69,8 @@ enum {
   HPS_EINVAL = 1,    /* an argument is out of range (see each call) */
   HPS_ENOMEM = 2,    /* a device allocation failed or the handle's memory cap was hit */
   HPS_ESINGULAR = 3, /* a leaf matrix B or an interface matrix W had a zero pivot */
-  HPS_ETIMEOUT = 4,  /* a bounded device wait gave up */
+  HPS_ETIMEOUT = 4,  /* a bounded device wait gave up (the tensor-core product's
+                        pipeline waits, 2 s each; reported by hps_status) */
   HPS_ECUDA = 5,     /* a CUDA runtime call failed (no device, launch error, ...) */
   HPS_ENOTSUP = 6,   /* a valid request the kernels cannot run (sizes; see each call) */
   HPS_ETOOBIG = 7    /* the request needs more than the fixed no-allocation workspace */
@@ -339,7 +340,9 @@ int hps_build_times(hps_handle *h, double *ms, int cap);
 
 /* Wait for the handle's work on `stream` and report device-side failures:
  * HPS_ESINGULAR with *level / *box (may be NULL) set to the tree level
- * (leaf level = levels) and box index of the first zero pivot, or HPS_OK. */
+ * (leaf level = levels) and box index of the first zero pivot;
+ * HPS_ETIMEOUT when a wait inside a tensor-core product gave up (its
+ * results are then unspecified; *box = the output tile); or HPS_OK. */
 int hps_status(hps_handle *h, void *stream, int *level, int *box);
 
 /* Release the handle and all its device memory.  NULL is allowed. */

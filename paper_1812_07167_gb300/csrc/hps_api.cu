@@ -770,7 +770,8 @@ static void solve_ws_layout(const Plan &pl, int R, SolveWs &w, bool allow_oz = t
 // Products of a solve: complex128 ones wide enough for the tensor cores run
 // there, the batch cut into chunks whose digit planes fit the workspace's
 // region; the rest in one launch.
-static int solve_gemm(GemmDesc *gd, int nd, cudaStream_t st, char *wb, const SolveWs &ws, bool oz) {
+static int solve_gemm(GemmDesc *gd, int nd, cudaStream_t st, char *wb, const SolveWs &ws, bool oz,
+                      unsigned *status) {
   GemmDesc rest[2];
   int nr = 0;
   for (int q = 0; q < nd; q++) {
@@ -795,7 +796,7 @@ static int solve_gemm(GemmDesc *gd, int nd, cudaStream_t st, char *wb, const Sol
           c.B2 = shift(g.B2, b0);
           c.C = shift(g.C, b0);
           c.D = shift(g.D, b0);
-          CK(hps::launch_gemm_oz(c, wb + ws.ooz, ws.oz_bytes, st));
+          CK(hps::launch_gemm_oz(c, wb + ws.ooz, ws.oz_bytes, st, status));
         }
         continue;
       }
@@ -835,7 +836,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
   GemmDesc g = gemm(nb, R, ni, nl, F(elem(h->GX, (long long)nb * nb, lf), nb, (long long)n * nb, lf),
                     mat(s, (long long)nl * ni, ni), mat(W(oh[0]), (long long)nl * nb, nb));
   g.cf32 = lf;
-  if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
+  if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
   for (size_t j = 0; j < pl.lv.size(); j++) {
     const Level &L = pl.lv[j];
     const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc, f = L.f32;
@@ -863,17 +864,17 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     g.D = h3b;
     g.beta = make_double2(-1.0, 0.0);
     g.cf32 = f;
-    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
+    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
     g = gemm(n3, R, n3, P, F(L.Winv, n3, s33, f), mat(v, ldv, n3), mat(ta, ldv, n3));
     g.cf32 = f;
-    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
+    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
     // t~3b = -h3a - R33a t~3a  (Upsilon_b [h3a; h3b])
     g = gemm(n3, R, n3, P, F(L.R33a, n3, s33, f), mat(ta, ldv, n3), mat(tb, ldv, n3));
     g.alpha = make_double2(-1.0, 0.0);
     g.D = h3a;
     g.beta = make_double2(-1.0, 0.0);
     g.cf32 = f;
-    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
+    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
     // h^tau = [h1a + R13a t~3a ; h2b + R23b t~3b]  (Eq. flux_part)
     const long long ldp = (long long)P * nt;
     GemmDesc g2[2];
@@ -886,7 +887,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     g2[1].D = h2b;
     g2[1].beta = make_double2(1.0, 0.0);
     g2[1].cf32 = f;
-    if (int rc = solve_gemm(g2, 2, st, wb, ws, pl.oz)) return rc;
+    if (int rc = solve_gemm(g2, 2, st, wb, ws, pl.oz, h->d_status)) return rc;
   }
 
   // ---- downward pass ----
@@ -916,7 +917,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     g2[1].D = mat(W(otb[jj]), ldv, n3);
     g2[1].beta = make_double2(1.0, 0.0);
     g2[1].cf32 = f;
-    if (int rc = solve_gemm(g2, 2, st, wb, ws, pl.oz)) return rc;
+    if (int rc = solve_gemm(g2, 2, st, wb, ws, pl.oz, h->d_status)) return rc;
     // the rest of the children's incoming data is the parent's: I1 and I2
     CopyBatch cb;
     cb.count = 2;
@@ -939,7 +940,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     gl.alpha = make_double2(-1.0, 0.0);
     gl.D = mat(u + b1, ldu, n);
     gl.beta = make_double2(1.0, 0.0);
-    if (int rc = solve_gemm(&gl, 1, st, wb, ws, pl.oz)) return rc;
+    if (int rc = solve_gemm(&gl, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
     CK(hps::launch_lu_solve_part(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, nullptr, 0, 0, nullptr, 0, 0, u, ldu,
                                  n, false, b1, n, false, true, true, st));
     GemmDesc gu = gemm(b1, R, n - b1, nl, F(elem(h->X, (long long)b1 * n, 0), n, s2, 0), mat(u + b1, ldu, n),
@@ -947,7 +948,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     gu.alpha = make_double2(-1.0, 0.0);
     gu.D = mat(u, ldu, n);
     gu.beta = make_double2(1.0, 0.0);
-    if (int rc = solve_gemm(&gu, 1, st, wb, ws, pl.oz)) return rc;
+    if (int rc = solve_gemm(&gu, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
     CK(hps::launch_lu_solve_part(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, nullptr, 0, 0, nullptr, 0, 0, u, ldu,
                                  n, false, 0, b1, false, false, true, st));
   } else if (pl.leaf_lu) {
@@ -959,7 +960,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     g.B2 = mat(s, (long long)nl * ni, ni);
     g.ksplit = nb;
     g.cf32 = lf;
-    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz)) return rc;
+    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
   }
 
   return HPS_OK;
@@ -1592,7 +1593,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
         if (tuned(TuneKey{0, gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32}, v) && v >= 1 && v <= 4)
           gd[q].cfg = v;
         if (oz_shape(gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32, P0.oz)) {
-          CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, st));
+          CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, st, d_status));
           launches += hps::oz_launches(gd[q]);
         } else {
           rest[nr++] = gd[q];
@@ -2171,7 +2172,10 @@ int hps_status(hps_handle *h, void *stream, int *level, int *box) {
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   if (level) *level = w ? (int)((w >> 20) & 0xff) : -1;
   if (box) *box = w ? (int)(w & 0xfffff) : -1;
-  return w ? HPS_ESINGULAR : HPS_OK;
+  if (!w) return HPS_OK;
+  // codes 1, 2: a zero pivot of a leaf matrix or an interface matrix; 3: a
+  // pipeline wait of the tensor-core product gave up
+  return (w >> 28) == 3u ? HPS_ETIMEOUT : HPS_ESINGULAR;
 }
 
 int hps_solve(hps_handle *h, const double *s_, const double *t_, double *u_, int nrhs, void *stream) {

@@ -136,14 +136,18 @@ __device__ __forceinline__ void chain_enter() {
 cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st);
 
 // Complex128 GEMM emulated on the bf16 tensor cores (Ozaki scheme, 9 slices
-// of 6 bits per operand; accuracy ~2^-54 max|A_i.| max|B_.j| per term).  Same
-// semantics as launch_gemm for one descriptor with cf32 == 0; needs a
+// of 6 bits per operand; accuracy ~2^-54 max|A_i.| max|B_.j| per term), the
+// slice products by tcgen05.mma from TMA-staged tiles.  Same semantics as
+// launch_gemm for one descriptor with cf32 == 0; needs a 256-byte aligned
 // device workspace of oz_workspace_bytes(g).  oz_launches(g) launches (4, or
-// 5 when the slice pairs are split over several CTAs a tile).
+// 5 when the slice pairs are split over several CTAs a tile).  A pipeline
+// wait that gives up (2 s) records code 3 in *status (if given) and leaves C
+// unspecified.
 bool oz_eligible(const GemmDesc &g);
 int oz_launches(const GemmDesc &g);
 size_t oz_workspace_bytes(const GemmDesc &g);
-cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st);
+cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st,
+                           unsigned *status = nullptr);
 cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st);
 
 // Leaf step (Sec. 2.1) for leaves [leaf0, leaf0 + count): assemble B, invert

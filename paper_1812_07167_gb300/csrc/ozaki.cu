@@ -1,4 +1,6 @@
-// Complex128 GEMM emulated on the bf16 tensor cores (Ozaki scheme).
+// Complex128 GEMM emulated on the bf16 tensor cores (Ozaki scheme), with the
+// products on tcgen05 (accumulators in tensor memory, operand tiles staged in
+// shared memory by TMA).
 //
 // Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
 // multiplication by using fast routines of matrix multiplication and its
@@ -14,65 +16,116 @@
 // fields of x as a 64-bit integer and cut into balanced base-64 digits
 // (every step exact; integer work only, since this part's FP64 pipe is 64
 // times slower than its integer and FP32 pipes).  The digits are exact in
-// bf16.
+// bf16.  Both operands' digit planes are stored K-major ([row][k], k
+// contiguous), the layout the tensor cores read without transposition.
 //
 // Products.  The slice pairs (s, t) with s + t < S are taken group by group
 // of equal shift e = s + t, whose products all carry the weight 2^{-6(e+2)}.
-// The tensor core multiplies the digit matrices with FP32 accumulation; a
-// digit product is at most 2^10 in magnitude, a complex combination (ar br -
-// ai bi or ar bi + ai br) at most 2^11, and a group has at most S = 9 pairs:
-// over a K chunk of OZ_KC = 896 every partial sum of a whole group is an
-// integer below 9 * 896 * 2^11 < 2^24, so the FP32 accumulation is exact.
-// After each group (and K chunk) the sum is added, times its weight, into
-// complex128 accumulators: 9 FP64 updates an output for K <= 896, which
-// keeps the FP64 pipe (2 operations per clock per SM on this part) well
-// below the tensor-core work.  Pairs with s + t >= S are dropped: with the
-// remainders they bound the error of every term by ~2^{-6S} max|A_i.|
-// max|B_.j| (2^-54 for S = 9), the size of a complex128 rounding.  The
-// result is scaled back by 2^{a_i + b_j} and combined as C = alpha AB +
-// beta D (+ I).
+// A group's complex product over a K chunk of OZ_KC = 896 is accumulated in
+// FP32 in tensor memory: a digit product is at most 2^10 in magnitude, a
+// complex combination (ar br - ai bi or ar bi + ai br) at most 2^11, and a
+// group has at most S = 9 pairs, so every partial sum is an integer below
+// 9 * 896 * 2^11 < 2^24 and the FP32 accumulation is exact.  After each
+// group (and K chunk) the sum is added, times its weight, into complex128
+// partial sums: 9 FP64 updates an output for K <= 896, which keeps this
+// part's FP64 pipe (2 operations per clock per SM) well below the
+// tensor-core work.  Pairs with s + t >= S are dropped: with the remainders
+// they bound the error of every term by ~2^{-6S} max|A_i.| max|B_.j|
+// (2^-54 for S = 9), the size of a complex128 rounding.  The result is
+// scaled back by 2^{a_i + b_j} and combined as C = alpha AB + beta D (+ I).
 //
-// Kernels: the split of A (row exponents, then the digits k-major), the
-// split of B (a warp per column, digits k fastest), and the product kernel:
-// 64 x 64 output tiles, 4 warps of 32 x 32, mma.sync m16n8k16 bf16 with FP32
-// accumulation on fragments read by ldmatrix (transposing for the k-major A
-// tiles), operand tiles staged through shared memory by cp.async with double
-// buffering, the complex128 accumulators in shared memory.  Products with few
-// output tiles split the slice pairs over several CTAs a tile and sum the
-// partial results in a last pass.
+// Kernels: the exponents of A's rows; the digits of A (64 x 32 blocks
+// transposed through shared memory so that both the reads of the
+// column-major operand and the K-major digit writes are contiguous); the
+// digits of B (a warp per column, lanes over k); and the product kernel, one
+// CTA per 128 x BN output tile (BN = 128, or 64 for narrow products) and
+// share of the slice pairs:
+//   warp 0   one thread issues the TMA copies of the digit tiles (real and
+//            imaginary parts of an A slice and a B slice, 64 k each, 128-byte
+//            swizzled) into a ring of shared-memory stages;
+//   warp 1   allocates the tensor memory; one thread issues tcgen05.mma
+//            (M = 128, N = BN, K = 16 per instruction; the real part
+//            Re += Ar Br + (-Ai) Bi through the instruction's negate-A bit,
+//            the imaginary part Im += Ar Bi + Ai Br) into one of two
+//            accumulator buffers, and commits each stage back to its slot and
+//            each finished group to the epilogue;
+//   warps 2-9  read a finished group's FP32 sums out of tensor memory
+//            (tcgen05.ld), hand the buffer back, and add the sums with the
+//            group's weight into the tile's complex128 partial sums (global
+//            scratch, resident in L2), or, after the last group, write
+//            C = alpha 2^(a_i + b_j) sum + beta D (+ I).
+// Products with few output tiles split the slice pairs over several CTAs a
+// tile and sum the partial results in a last pass.  Every wait on a barrier
+// gives up after 2 s (recording a timeout in the status word), so that a
+// stalled pipeline ends the kernel with an error instead of hanging the GPU.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
+#include "cx.cuh"
 #include "hps_internal.h"
+#include "tc_desc.h"
 
 namespace hps {
 
 namespace {
 
-constexpr int OZ_S = 9;              // slices per operand (6 bits each)
-constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32;
-constexpr int OZ_KC = 896;           // K per exact FP32 accumulation of a shift group
-constexpr int OZ_LDS = OZ_BK + 8;    // shared row length in bf16: conflict-free fragment loads
-
+constexpr int OZ_S = 9;                          // slices per operand (6 bits each)
 constexpr int OZ_PAIRS = OZ_S * (OZ_S + 1) / 2;  // slice pairs with s + t < S
+constexpr int OZ_KC = 896;                       // K per exact FP32 accumulation of a shift group
+constexpr int TC_BM = 128, TC_BK = 64;           // tile rows; k per stage (one 128-byte swizzle row)
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
+constexpr unsigned kStatusTimeout = 3u;          // status-word code of a pipeline wait that gave up
+
+template <int BN>
+struct TcCfg {
+  static constexpr int kStages = BN == 128 ? 3 : 4;
+  static constexpr int kTileA = TC_BM * TC_BK * 2;  // bytes of one A digit tile (16 KB)
+  static constexpr int kTileB = BN * TC_BK * 2;
+  static constexpr int kStage = 2 * kTileA + 2 * kTileB;  // Ar, Ai, Br, Bi
+  static constexpr size_t kSmem = (size_t)kStages * kStage + 1024;  // + alignment slack
+  static constexpr uint32_t kTmemCols = 4 * BN;     // two buffers of [Re | Im] x BN columns
+  static constexpr size_t kAcc = (size_t)TC_BM * 2 * BN;  // doubles of a tile's partial sums
+};
+
+int num_sms() {
+  static int n = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 148;
+    }
+  });
+  return n;
+}
 
 struct OzLayout {
-  int Mp, Np, Kp;         // padded sizes (multiples of 64, 64, 32)
+  int Mp, Np, Kp;         // padded sizes (multiples of 128, BN, 64)
+  int bn;                 // output tile width: 128, or 64 for N <= 64
+  int tm, tn;             // output tiles along M and N
   int gp;                 // CTAs per output tile, each summing a share of the slice pairs
   size_t a_off, b_off;    // byte offsets of the digit planes
   size_t ea_off, eb_off;  // byte offsets of the row / column exponents
-  size_t part_off;        // gp > 1: per-group complex128 partial sums [gp][batch][Mp][Np]
+  size_t acc_off;         // complex128 partial sums [gp][batch][tm][tn][2 bn][128]
   size_t total;
 };
 
 inline size_t oz_align(size_t x) { return (x + 255) & ~(size_t)255; }
 
-OzLayout oz_layout(const GemmDesc &g) {
+OzLayout oz_layout(const GemmDesc &g, int nsm) {
   OzLayout L;
-  L.Mp = (g.M + OZ_BM - 1) / OZ_BM * OZ_BM;
-  L.Np = (g.N + OZ_BN - 1) / OZ_BN * OZ_BN;
-  L.Kp = (g.K + OZ_BK - 1) / OZ_BK * OZ_BK;
+  L.bn = g.N <= 64 ? 64 : 128;
+  L.Mp = (g.M + TC_BM - 1) / TC_BM * TC_BM;
+  L.Np = (g.N + L.bn - 1) / L.bn * L.bn;
+  L.Kp = (g.K + TC_BK - 1) / TC_BK * TC_BK;
+  L.tm = L.Mp / TC_BM;
+  L.tn = L.Np / L.bn;
   const size_t B = (size_t)g.batch;
   size_t o = 0;
   L.a_off = o;
@@ -83,13 +136,26 @@ OzLayout oz_layout(const GemmDesc &g) {
   o = oz_align(o + B * (size_t)L.Mp * sizeof(int));
   L.eb_off = o;
   o = oz_align(o + B * (size_t)L.Np * sizeof(int));
-  // products with few output tiles split the slice pairs over several CTAs
-  // a tile, aiming at two waves of one CTA on each SM
-  const long long tiles = (long long)(L.Mp / OZ_BM) * (L.Np / OZ_BN) * g.batch;
-  L.gp = (int)std::min<long long>(12, std::max<long long>(1, (2 * 152 + tiles - 1) / tiles));
+  // one CTA an SM (the tile's stages fill shared memory): with fewer tiles
+  // than SMs the slice pairs are split over up to 9 CTAs a tile (5 pairs or
+  // more each), picking the split that leaves the last wave fullest
+  const long long tiles = (long long)L.tm * L.tn * g.batch;
+  L.gp = 1;
+  if (tiles < nsm) {
+    double best = 0.0;
+    for (int q = 1; q <= 9; q++) {
+      const long long ctas = tiles * q;
+      const long long waves = (ctas + nsm - 1) / nsm;
+      const double eff = (double)ctas / (double)(waves * nsm);
+      if (eff > best * 1.02) {
+        best = eff;
+        L.gp = q;
+      }
+    }
+  }
   while (L.gp > 1 && (long long)g.batch * L.gp > 65535) L.gp--;
-  L.part_off = o;
-  if (L.gp > 1) o = oz_align(o + (size_t)L.gp * B * L.Mp * L.Np * 2 * sizeof(double));
+  L.acc_off = o;
+  o = oz_align(o + (size_t)L.gp * B * L.Mp * L.Np * 2 * sizeof(double));
   L.total = o;
   return L;
 }
@@ -200,11 +266,8 @@ __global__ void __launch_bounds__(256) oz_split_b_kernel(const __grid_constant__
   }
 }
 
-// Digits of A in two passes, both reading A with neighbouring threads on
-// neighbouring rows (coalesced for the column-major operands).  Pass 1: the
-// exponent of each row (32 rows a block, 8 threads a row over k, combined
-// in shared memory).  Pass 2: one thread per element, digits written k-major
-// ([k][row], rows contiguous).  Padding rows and k get zeros.
+// Exponent of each row of A (32 rows a block, 8 threads a row over k,
+// combined in shared memory; neighbouring threads on neighbouring rows).
 __global__ void __launch_bounds__(256) oz_expo_a_kernel(const __grid_constant__ GemmDesc g, int Mp, int *expo) {
   __shared__ unsigned long long part[8][32];
   const int r = threadIdx.x & 31, kl = threadIdx.x >> 5;
@@ -223,295 +286,437 @@ __global__ void __launch_bounds__(256) oz_expo_a_kernel(const __grid_constant__ 
   }
 }
 
+// Digits of A, K-major ([row][k]), for a block of 32 rows x 32 k: each thread
+// reads elements with neighbouring threads on neighbouring rows (coalesced
+// for the column-major operands), the 18 digit planes are transposed in
+// shared memory, and each row's 32 digits leave as four 16-byte stores.
+// Padding rows and k get zeros.
+constexpr int OZA_R = 32, OZA_K = 32, OZA_LD = OZA_K + 8;  // shared row: 80 bytes (16-byte aligned)
 __global__ void __launch_bounds__(256) oz_split_a_kernel(const __grid_constant__ GemmDesc g, int Mp, int Kp,
                                                          __nv_bfloat16 *digits, const int *expo) {
-  const int i = blockIdx.x * 64 + (threadIdx.x & 63);
-  const int k = blockIdx.y * 4 + (threadIdx.x >> 6);
-  const int b = blockIdx.z;
-  if (i >= Mp || k >= Kp) return;
-  double2 v = make_double2(0.0, 0.0);
-  if (i < g.M && k < g.K) v = oz_lda(g, b, i, k);
+  __shared__ __align__(16) __nv_bfloat16 tile[2 * OZ_S][OZA_R][OZA_LD];
+  const int r = threadIdx.x & 31, kq = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * OZA_R, k0 = blockIdx.y * OZA_K, b = blockIdx.z;
+  const int i = i0 + r;
   const int sh = expo[(size_t)b * Mp + i];
-  const size_t plane = (size_t)Mp * Kp;
-  __nv_bfloat16 *base = digits + (size_t)b * OZ_S * 2 * plane + (size_t)k * Mp + i;
-  int dr[OZ_S], di[OZ_S];
-  oz_digits(oz_fixed(v.x, sh), dr);
-  oz_digits(oz_fixed(v.y, sh), di);
+  for (int kk = kq; kk < OZA_K; kk += 8) {
+    const int k = k0 + kk;
+    double2 v = make_double2(0.0, 0.0);
+    if (i < g.M && k < g.K) v = oz_lda(g, b, i, k);
+    int dr[OZ_S], di[OZ_S];
+    oz_digits(oz_fixed(v.x, sh), dr);
+    oz_digits(oz_fixed(v.y, sh), di);
 #pragma unroll
-  for (int q = 0; q < OZ_S; q++) {
-    base[(size_t)(2 * q) * plane] = __int2bfloat16_rn(dr[q]);
-    base[(size_t)(2 * q + 1) * plane] = __int2bfloat16_rn(di[q]);
+    for (int q = 0; q < OZ_S; q++) {
+      tile[2 * q][r][kk] = __int2bfloat16_rn(dr[q]);
+      tile[2 * q + 1][r][kk] = __int2bfloat16_rn(di[q]);
+    }
+  }
+  __syncthreads();
+  const size_t plane = (size_t)Mp * Kp;
+  __nv_bfloat16 *base = digits + (size_t)b * OZ_S * 2 * plane;
+  constexpr int VPR = OZA_K / 8;  // 16-byte vectors a row
+  for (int v = threadIdx.x; v < 2 * OZ_S * OZA_R * VPR; v += 256) {
+    const int pl = v / (OZA_R * VPR), rem = v % (OZA_R * VPR), row = rem / VPR, c = rem % VPR;
+    const uint4 val = *reinterpret_cast<const uint4 *>(&tile[pl][row][c * 8]);
+    *reinterpret_cast<uint4 *>(base + (size_t)pl * plane + (size_t)(i0 + row) * Kp + k0 + c * 8) = val;
   }
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// ---- PTX wrappers: mbarriers, TMA, tcgen05 ---------------------------------
 
-// four 8 x 8 bf16 matrices from shared memory (lane l gives the address of
-// row l % 8 of matrix l / 8); register j holds matrix j's row (lane / 4),
-// elements 2 (lane % 4) and 2 (lane % 4) + 1
-__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const __nv_bfloat16 *p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
 }
 
-__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const __nv_bfloat16 *p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
+constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
+
+// Wait for the phase of `bar` with the given parity to complete.  Gives up
+// (false) when another role of the CTA has given up (*abort set; unless
+// drain, for the waits that let work in flight finish before the CTA exits)
+// or after kWaitNs, then sets *abort and records a timeout in the status word.
+__device__ __noinline__ bool bar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, unsigned *status,
+                                      bool drain = false) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    for (int q = 0; q < 64; q++)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (!drain && *abort) return false;
+    if (global_ns() - t0 > kWaitNs) {
+      *abort = 1;
+      if (status) record_status(status, kStatusTimeout, 0, (int)(blockIdx.x + gridDim.x * blockIdx.y));
+      return false;
+    }
+  }
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                            int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap *map) {
+  asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)map) : "memory");
 }
 
-struct OzArgs {
+__device__ __forceinline__ void tc_alloc(uint32_t *dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+// D (tensor memory) (+)= A B, A and B from shared-memory descriptors
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive once on `bar` when every tcgen05.mma this thread issued so far has completed
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+// 32 consecutive 32-bit columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+        "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+        "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// pair index p (ordered by shift e = s + t, then s) -> (e, s)
+__device__ __forceinline__ void pair_decode(int p, int &e, int &s) {
+  e = 0;
+  while (p > e) {
+    p -= e + 1;
+    e++;
+  }
+  s = p;
+}
+
+struct TcArgs {
   GemmDesc g;
   int Mp, Np, Kp;
-  int gp;        // pair groups (CTAs a tile)
-  double *part;  // gp > 1: partial sums [gp][batch][Mp][Np][2]
-  const __nv_bfloat16 *A;  // [batch][S][2][Kp][Mp] (k-major)
-  const __nv_bfloat16 *B;  // [batch][S][2][Np][Kp]
-  const int *ea;           // [batch][Mp]
-  const int *eb;           // [batch][Np]
+  int tm, tn;        // output tiles along M and N
+  int gp;            // CTAs a tile (shares of the slice pairs)
+  double *acc;       // partial sums [gp][batch][tm][tn][2 BN][128] ([Re columns, Im columns][row])
+  const int *ea;     // [batch][Mp]
+  const int *eb;     // [batch][Np]
+  unsigned *status;  // build status word for timeouts, or null
 };
 
-constexpr int OZ_THREADS = 128;  // 4 warps of 32 x 32 outputs
-constexpr int OZ_NACC = 64;      // complex128 outputs x (re, im) per thread
-constexpr int OZ_STAGES = 2;     // cp.async pipeline depth
-constexpr int OZ_LDA = OZ_BM + 8;  // shared A row (one k) in bf16: conflict-free transposing loads
-typedef __nv_bfloat16 TileA[2][OZ_BK][OZ_LDA];  // [re, im][k][row]
-typedef __nv_bfloat16 TileB[2][OZ_BN][OZ_LDS];  // [re, im][column][k]
-// shared memory: OZ_STAGES stages of A and B digit tiles, then the
-// complex128 accumulators ([element][thread]: conflict-free)
-constexpr size_t OZ_STAGE = sizeof(TileA) + sizeof(TileB);
-constexpr size_t OZ_SMEM = OZ_STAGES * OZ_STAGE + sizeof(double) * OZ_NACC * OZ_THREADS;
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    oz_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ TcArgs a) {
+  using Cfg = TcCfg<BN>;
+  constexpr int S_ = Cfg::kStages;
+  extern __shared__ unsigned char tc_smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S_], empty_bar[S_], accf_bar[2], acce_bar[2], drain_bar;
+  __shared__ uint32_t tmem_sh;
+  __shared__ volatile int abort_sh;
+  __shared__ int issued_sh;
 
-__device__ __forceinline__ void cp_async_wait_stages() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(OZ_STAGES - 1) : "memory");
-}
+  const uint32_t sbase = (smem_u32(tc_smem_raw) + 1023u) & ~1023u;  // 128-byte swizzle atoms: 1 KB aligned
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tn = blockIdx.x, tm = blockIdx.y;
+  const int b = blockIdx.z / a.gp, grp = blockIdx.z % a.gp;
+  const int p0 = grp * OZ_PAIRS / a.gp, p1 = (grp + 1) * OZ_PAIRS / a.gp;
+  const int nkb = a.Kp / TC_BK;
+  constexpr int CKB = OZ_KC / TC_BK;  // k-blocks of a chunk
+  const int nch = (nkb + CKB - 1) / CKB;
 
-__global__ void __launch_bounds__(OZ_THREADS, 2) oz_gemm_kernel(const __grid_constant__ OzArgs a) {
-  extern __shared__ __align__(16) unsigned char oz_smem[];
-  double *acc = (double *)(oz_smem + OZ_STAGES * OZ_STAGE);
-  const GemmDesc &g = a.g;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, grp = lane >> 2, tig = lane & 3;
-  const int b = blockIdx.z / a.gp, bm = blockIdx.y * OZ_BM, bn = blockIdx.x * OZ_BN;
-  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
-  const size_t aplane = (size_t)a.Mp * a.Kp, bplane = (size_t)a.Np * a.Kp;
-  const __nv_bfloat16 *Ab = a.A + (size_t)b * OZ_S * 2 * aplane;
-  const __nv_bfloat16 *Bb = a.B + (size_t)b * OZ_S * 2 * bplane;
-  const int nkb = a.Kp / OZ_BK;
-  constexpr int CKB = OZ_KC / OZ_BK;  // k-blocks of a chunk
-  auto tileA = [&](int st) -> TileA & { return *(TileA *)(oz_smem + st * OZ_STAGE); };
-  auto tileB = [&](int st) -> TileB & { return *(TileB *)(oz_smem + st * OZ_STAGE + sizeof(TileA)); };
-
-  for (int e = 0; e < OZ_NACC; e++) acc[e * OZ_THREADS + tid] = 0.0;
-
-  // this CTA's slice pairs: a contiguous share of the list ordered by shift
-  // e = s + t, then s: (0,0), (0,1), (1,0), (0,2), ...
-  const int grp_id = blockIdx.z % a.gp;
-  const int p0 = grp_id * OZ_PAIRS / a.gp, p1 = (grp_id + 1) * OZ_PAIRS / a.gp;
-  struct Pos {
-    int c, p, e, s, kb;  // K chunk, pair index, its shift and A slice, k-block
-  };
-  auto set_pair = [&](Pos &q, int p) {
-    q.p = p;
-    q.e = 0;
-    while (p > q.e) {
-      p -= q.e + 1;
-      q.e++;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < S_; q++) {
+      mbar_init(&full_bar[q], 1);   // the producer's arrive.expect_tx (+ the copies' bytes)
+      mbar_init(&empty_bar[q], 1);  // one tcgen05.commit
     }
-    q.s = p;
-  };
-  auto chunk_end = [&](int c) { return min(nkb, (c + 1) * CKB); };
-  auto advance = [&](Pos &q) {
-    if (++q.kb < chunk_end(q.c)) return;
-    if (q.p + 1 < p1) {
-      q.p++;
-      if (++q.s > q.e) {
-        q.e++;
-        q.s = 0;
-      }
-      q.kb = q.c * CKB;
-    } else {
-      q.c++;
-      set_pair(q, p0);
-      q.kb = q.c * CKB;
+    for (int q = 0; q < 2; q++) {
+      mbar_init(&accf_bar[q], 1);             // one tcgen05.commit
+      mbar_init(&acce_bar[q], TC_EPI_WARPS);  // one arrival per epilogue warp
     }
-  };
-  // one pipeline over (chunk, pair, k-block): the next tiles are in flight
-  // while the current ones are multiplied
-  const int nit = (p1 - p0) * nkb;  // the chunks together cover every k-block once per pair
-  auto load = [&](int st, const Pos &q) {
-    const __nv_bfloat16 *Ap = Ab + (size_t)(2 * q.s) * aplane;  // real digits; imaginary at + aplane
-    const __nv_bfloat16 *Bp = Bb + (size_t)(2 * (q.e - q.s)) * bplane;
-    TileA &TA = tileA(st);
-    TileB &TB = tileB(st);
-    const size_t k0 = (size_t)q.kb * OZ_BK;
-#pragma unroll
-    for (int c = tid; c < 2 * OZ_BK * (OZ_BM / 8); c += OZ_THREADS) {
-      const int ri = c / (OZ_BK * (OZ_BM / 8)), kr = (c / (OZ_BM / 8)) % OZ_BK, ch = c % (OZ_BM / 8);
-      cp_async16(&TA[ri][kr][ch * 8], Ap + ri * aplane + (k0 + kr) * (size_t)a.Mp + bm + ch * 8);
-    }
-#pragma unroll
-    for (int c = tid; c < 2 * OZ_BN * 4; c += OZ_THREADS) {
-      const int ri = c / (OZ_BN * 4), row = (c >> 2) % OZ_BN, ch = c & 3;
-      cp_async16(&TB[ri][row][ch * 8], Bp + ri * bplane + (size_t)(bn + row) * a.Kp + k0 + ch * 8);
-    }
-  };
-  float cr[2][4][4], ci[2][4][4];
-#pragma unroll
-  for (int mi = 0; mi < 2; mi++)
-#pragma unroll
-    for (int ni = 0; ni < 4; ni++)
-#pragma unroll
-      for (int e = 0; e < 4; e++) cr[mi][ni][e] = ci[mi][ni][e] = 0.f;
-  Pos cur;
-  cur.c = 0;
-  set_pair(cur, p0);
-  cur.kb = 0;
-  Pos ld = cur;
-  for (int st = 0; st < OZ_STAGES - 1; st++) {
-    if (st < nit) load(st, ld);
-    cp_async_commit();
-    advance(ld);
+    mbar_init(&drain_bar, 1);
+    abort_sh = 0;
+    issued_sh = 0;
+    fence_mbar_init();
   }
-  for (int it = 0; it < nit; it++) {
-    if (it + OZ_STAGES - 1 < nit) load((it + OZ_STAGES - 1) % OZ_STAGES, ld);
-    cp_async_commit();
-    advance(ld);
-    cp_async_wait_stages();
-    __syncthreads();
-    TileA &TA = tileA(it % OZ_STAGES);
-    TileB &TB = tileB(it % OZ_STAGES);
-#pragma unroll
-    for (int kk = 0; kk < OZ_BK; kk += 16) {
-      unsigned ar[2][4], ai[2][4], br[2][4], bi[2][4];
-#pragma unroll
-      for (int mi = 0; mi < 2; mi++) {
-        // matrix j = lane / 8 of the fragment: rows (k) kk + 8 (j / 2) + lane % 8,
-        // columns (m) wm + 16 mi + 8 (j % 2), read transposed
-        const int kr = kk + ((lane >> 4) << 3) + (lane & 7);
-        const int mc = wm + mi * 16 + (((lane >> 3) & 1) << 3);
-        ldsm_x4_t(ar[mi], &TA[0][kr][mc]);
-        ldsm_x4_t(ai[mi], &TA[1][kr][mc]);
-      }
-#pragma unroll
-      for (int nj = 0; nj < 2; nj++) {
-        // n8 tiles 2 nj and 2 nj + 1: registers b0, b1 of the first, then of the second
-        const int n = wn + nj * 16 + (lane & 7) + ((lane >> 4) & 1) * 8;
-        const int col = kk + ((lane >> 3) & 1) * 8;
-        ldsm_x4(br[nj], &TB[0][n][col]);
-        ldsm_x4(bi[nj], &TB[1][n][col]);
-      }
-      // the four real products in rounds, so that the two products into one
-      // accumulator are 16 independent instructions apart
-#pragma unroll
-      for (int round = 0; round < 4; round++)
-#pragma unroll
-        for (int mi = 0; mi < 2; mi++)
-#pragma unroll
-          for (int ni = 0; ni < 4; ni++) {
-            const unsigned b0 = br[ni >> 1][2 * (ni & 1)], b1 = br[ni >> 1][2 * (ni & 1) + 1];
-            const unsigned c0 = bi[ni >> 1][2 * (ni & 1)], c1 = bi[ni >> 1][2 * (ni & 1) + 1];
-            if (round == 0) mma_bf16(cr[mi][ni], ar[mi], b0, b1);
-            if (round == 1) mma_bf16(ci[mi][ni], ar[mi], c0, c1);
-            if (round == 2) mma_bf16(cr[mi][ni], ai[mi], c0 ^ 0x80008000u, c1 ^ 0x80008000u);  // - Ai Bi
-            if (round == 3) mma_bf16(ci[mi][ni], ai[mi], b0, b1);
-          }
-    }
-    __syncthreads();
-    // end of a shift group within this chunk: its sums are exact integers,
-    // add them into complex128 with the group's weight
-    const bool last_kb = cur.kb + 1 == chunk_end(cur.c);
-    const bool group_end = cur.p + 1 == p1 || cur.s == cur.e;
-    if (last_kb && group_end) {
-      const double scale = ldexp(1.0, -6 * (cur.e + 2));
-#pragma unroll
-      for (int mi = 0; mi < 2; mi++)
-#pragma unroll
-        for (int ni = 0; ni < 4; ni++)
-#pragma unroll
-          for (int e = 0; e < 4; e++) {
-            const int idx = ((mi * 4 + ni) * 4 + e) * 2;
-            double *pr = acc + idx * OZ_THREADS + tid, *pi = pr + OZ_THREADS;
-            *pr = fma((double)cr[mi][ni][e], scale, *pr);
-            *pi = fma((double)ci[mi][ni][e], scale, *pi);
-            cr[mi][ni][e] = ci[mi][ni][e] = 0.f;
-          }
-    }
-    advance(cur);
+  if (warp == 1) {
+    tc_alloc(&tmem_sh, Cfg::kTmemCols);
+    tc_relinquish();
   }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_sh;
 
-  if (a.gp > 1) {
-    // partial sums of this pair group; oz_reduce_kernel finishes the tile
-#pragma unroll
-    for (int mi = 0; mi < 2; mi++)
-#pragma unroll
-      for (int ni = 0; ni < 4; ni++)
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-          const int i = bm + wm + mi * 16 + grp + ((e >> 1) << 3);
-          const int j = bn + wn + ni * 8 + 2 * tig + (e & 1);
-          const int idx = ((mi * 4 + ni) * 4 + e) * 2;
-          const size_t o = ((((size_t)grp_id * g.batch + b) * a.Mp + i) * a.Np + j) * 2;
-          a.part[o] = acc[idx * OZ_THREADS + tid];
-          a.part[o + 1] = acc[(idx + 1) * OZ_THREADS + tid];
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    tma_prefetch_map(&tmA);
+    tma_prefetch_map(&tmB);
+    int it = 0;
+    bool ok = true;
+    for (int c = 0; c < nch && ok; c++) {
+      const int kb0 = c * CKB, kb1 = min(nkb, kb0 + CKB);
+      for (int p = p0; p < p1 && ok; p++) {
+        int e, s;
+        pair_decode(p, e, s);
+        const int zA = (b * OZ_S + s) * 2, zB = (b * OZ_S + (e - s)) * 2;
+        for (int kb = kb0; kb < kb1; kb++) {
+          const int st = it % S_;
+          const uint32_t ph = (uint32_t)(it / S_) & 1u;
+          if (!bar_wait(&empty_bar[st], ph ^ 1u, &abort_sh, a.status)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full_bar[st], Cfg::kStage);
+          const uint32_t sb = sbase + st * Cfg::kStage;
+          tma_load_3d(sb, &tmA, &full_bar[st], kb * TC_BK, tm * TC_BM, zA);
+          tma_load_3d(sb + Cfg::kTileA, &tmA, &full_bar[st], kb * TC_BK, tm * TC_BM, zA + 1);
+          tma_load_3d(sb + 2 * Cfg::kTileA, &tmB, &full_bar[st], kb * TC_BK, tn * BN, zB);
+          tma_load_3d(sb + 2 * Cfg::kTileA + Cfg::kTileB, &tmB, &full_bar[st], kb * TC_BK, tn * BN, zB + 1);
+          it++;
         }
-    return;
-  }
-
-  // epilogue: C = alpha 2^(a_i + b_j) acc + beta D (+ I)
+      }
+    }
+    issued_sh = it;
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    constexpr uint32_t id_pos = tc::idesc_bf16_f32(TC_BM, BN, false);
+    constexpr uint32_t id_neg = tc::idesc_bf16_f32(TC_BM, BN, true);
+    int it = 0, gi = 0;
+    bool ok = true;
+    for (int c = 0; c < nch && ok; c++) {
+      const int kb0 = c * CKB, kb1 = min(nkb, kb0 + CKB);
+      bool open = false, first = true;
+      for (int p = p0; p < p1 && ok; p++) {
+        int e, s;
+        pair_decode(p, e, s);
+        const int buf = gi & 1;
+        if (!open) {
+          // the epilogue has drained this buffer's previous group
+          if (!bar_wait(&acce_bar[buf], ((uint32_t)(gi >> 1) & 1u) ^ 1u, &abort_sh, a.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          open = true;
+          first = true;
+        }
+        const uint32_t dre = tmem + (uint32_t)(buf * 2 * BN), dim = dre + BN;
+        for (int kb = kb0; kb < kb1; kb++) {
+          const int st = it % S_;
+          const uint32_t ph = (uint32_t)(it / S_) & 1u;
+          if (!bar_wait(&full_bar[st], ph, &abort_sh, a.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sb = sbase + st * Cfg::kStage;
 #pragma unroll
-  for (int mi = 0; mi < 2; mi++)
+          for (int kk = 0; kk < TC_BK / 16; kk++) {
+            const uint64_t ar = tc::smem_desc_sw128_kmajor(sb + kk * 32);
+            const uint64_t ai = tc::smem_desc_sw128_kmajor(sb + Cfg::kTileA + kk * 32);
+            const uint64_t br = tc::smem_desc_sw128_kmajor(sb + 2 * Cfg::kTileA + kk * 32);
+            const uint64_t bi = tc::smem_desc_sw128_kmajor(sb + 2 * Cfg::kTileA + Cfg::kTileB + kk * 32);
+            const uint32_t accum = first ? 0u : 1u;
+            tc_mma(dre, ar, br, id_pos, accum);
+            tc_mma(dim, ar, bi, id_pos, accum);
+            tc_mma(dre, ai, bi, id_neg, 1u);
+            tc_mma(dim, ai, br, id_pos, 1u);
+            first = false;
+          }
+          tc_commit(&empty_bar[st]);  // the stage's slot is free once these products are done
+          it++;
+        }
+        if (ok && (s == e || p == p1 - 1)) {
+          tc_commit(&accf_bar[buf]);  // the group's sums are complete
+          gi++;
+          open = false;
+        }
+      }
+    }
+    tc_commit(&drain_bar);
+  } else if (warp >= 2) {
+    // ---- epilogue: FP32 group sums -> complex128 ----
+    constexpr int NC = BN / 2;   // columns of each part a warp handles
+    constexpr int NL = NC / 32;  // 32-column loads per part
+    const int q = warp & 3;      // tensor-memory lanes 32 q .. 32 q + 31 are this warp's
+    const int hf = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    const int i = tm * TC_BM + row;
+    const GemmDesc &g = a.g;
+    double *slab = a.acc + ((((size_t)grp * g.batch + b) * a.tm + tm) * a.tn + tn) * Cfg::kAcc;
+    const int sha = (i < a.Mp) ? __ldg(a.ea + (size_t)b * a.Mp + i) : 0;
+    int gi = 0;
+    bool first = true, ok = true;
+    for (int c = 0; c < nch && ok; c++) {
+      for (int p = p0; p < p1 && ok; p++) {
+        int e, s;
+        pair_decode(p, e, s);
+        if (!(s == e || p == p1 - 1)) continue;
+        const int buf = gi & 1;
+        const bool got = bar_wait(&accf_bar[buf], (uint32_t)(gi >> 1) & 1u, &abort_sh, a.status);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * BN + hf * NC);
+        const double w = ldexp(1.0, -6 * (e + 2));
+        const bool fin = (c == nch - 1) && (p == p1 - 1) && a.gp == 1;
+        // 32 columns of both parts at a time: tensor memory -> registers -> complex128
+#pragma unroll 1
+        for (int l = 0; l < NL; l++) {
+          uint32_t vr[32], vi[32];
+          tc_ld32(tb + l * 32, vr);
+          tc_ld32(tb + BN + l * 32, vi);
+          tc_wait_ld();
+          if (l == NL - 1) {
+            // the buffer is free for the next group but one
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce_bar[buf]);
+          }
+          if (fin) {
+            // C = alpha 2^(a_i + b_j) sum + beta D (+ I)
 #pragma unroll
-    for (int ni = 0; ni < 4; ni++)
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        const int i = bm + wm + mi * 16 + grp + ((e >> 1) << 3);
-        const int j = bn + wn + ni * 8 + 2 * tig + (e & 1);
-        if (i >= g.M || j >= g.N) continue;
-        const int idx = ((mi * 4 + ni) * 4 + e) * 2;
-        const int sh = __ldg(a.ea + (size_t)b * a.Mp + i) + __ldg(a.eb + (size_t)b * a.Np + j);
-        const double vr = ldexp(acc[idx * OZ_THREADS + tid], sh);
-        const double vi = ldexp(acc[(idx + 1) * OZ_THREADS + tid], sh);
-        double outr = g.alpha.x * vr - g.alpha.y * vi;
-        double outi = g.alpha.x * vi + g.alpha.y * vr;
-        if (g.D.ptr) {
-          const long long od = oz_off(g.D, b, i, j);
-          double2 d;
-          if (g.D.f32) {
-            const float2 f = ((const float2 *)g.D.ptr)[od];
-            d = make_double2(f.x, f.y);
+            for (int jj = 0; jj < 32; jj++) {
+              const int jl = hf * NC + l * 32 + jj;
+              const int j = tn * BN + jl;
+              double sr = (double)__uint_as_float(vr[jj]) * w;
+              double si = (double)__uint_as_float(vi[jj]) * w;
+              if (!first) {
+                sr += slab[(size_t)jl * TC_BM + row];
+                si += slab[(size_t)(BN + jl) * TC_BM + row];
+              }
+              if (i >= g.M || j >= g.N) continue;
+              const int sh = sha + __ldg(a.eb + (size_t)b * a.Np + j);
+              const double vre = ldexp(sr, sh), vim = ldexp(si, sh);
+              double outr = g.alpha.x * vre - g.alpha.y * vim;
+              double outi = g.alpha.x * vim + g.alpha.y * vre;
+              if (g.D.ptr) {
+                const long long od = oz_off(g.D, b, i, j);
+                double2 d;
+                if (g.D.f32) {
+                  const float2 f = ((const float2 *)g.D.ptr)[od];
+                  d = make_double2(f.x, f.y);
+                } else {
+                  d = ((const double2 *)g.D.ptr)[od];
+                }
+                outr += g.beta.x * d.x - g.beta.y * d.y;
+                outi += g.beta.x * d.y + g.beta.y * d.x;
+              }
+              if (g.addI && i == j) outr += 1.0;
+              const long long oc = oz_off(g.C, b, i, j);
+              if (g.C.f32)
+                ((float2 *)g.C.ptr)[oc] = make_float2((float)outr, (float)outi);
+              else
+                ((double2 *)g.C.ptr)[oc] = make_double2(outr, outi);
+            }
           } else {
-            d = ((const double2 *)g.D.ptr)[od];
+            double *pr = slab + (size_t)(hf * NC + l * 32) * TC_BM + row;
+            double *pi = pr + (size_t)BN * TC_BM;
+            if (first) {
+#pragma unroll
+              for (int jj = 0; jj < 32; jj++) {
+                pr[(size_t)jj * TC_BM] = (double)__uint_as_float(vr[jj]) * w;
+                pi[(size_t)jj * TC_BM] = (double)__uint_as_float(vi[jj]) * w;
+              }
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 32; jj++) {
+                pr[(size_t)jj * TC_BM] = fma((double)__uint_as_float(vr[jj]), w, pr[(size_t)jj * TC_BM]);
+                pi[(size_t)jj * TC_BM] = fma((double)__uint_as_float(vi[jj]), w, pi[(size_t)jj * TC_BM]);
+              }
+            }
           }
-          outr += g.beta.x * d.x - g.beta.y * d.y;
-          outi += g.beta.x * d.y + g.beta.y * d.x;
         }
-        if (g.addI && i == j) outr += 1.0;
-        const long long oc = oz_off(g.C, b, i, j);
-        if (g.C.f32)
-          ((float2 *)g.C.ptr)[oc] = make_float2((float)outr, (float)outi);
-        else
-          ((double2 *)g.C.ptr)[oc] = make_double2(outr, outi);
+        gi++;
+        first = false;
       }
+    }
+  }
+
+  // ---- teardown: every role has finished or given up ----
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    if (lane == 0) bar_wait(&drain_bar, 0u, &abort_sh, nullptr, true);  // the MMAs this thread issued
+    __syncwarp();
+  }
+  if (warp == 0 && lane == 0 && abort_sh) {
+    // copies still in flight after a give-up land before shared memory is released
+    const int n = issued_sh;
+    for (int k = max(0, n - S_); k < n; k++)
+      bar_wait(&full_bar[k % S_], (uint32_t)(k / S_) & 1u, &abort_sh, nullptr, true);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tc_dealloc(tmem, Cfg::kTmemCols);
+  }
 }
 
 // Sum of the pair groups' partial results of a split product, and the
-// epilogue C = alpha 2^(a_i + b_j) sum + beta D (+ I): one thread per entry.
-__global__ void __launch_bounds__(256) oz_reduce_kernel(const __grid_constant__ OzArgs a) {
+// epilogue C = alpha 2^(a_i + b_j) sum + beta D (+ I): one thread per entry,
+// neighbouring threads on neighbouring rows.
+template <int BN>
+__global__ void __launch_bounds__(256) oz_reduce_kernel(const __grid_constant__ TcArgs a) {
   const GemmDesc &g = a.g;
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long per = (long long)g.M * g.N;
@@ -519,11 +724,12 @@ __global__ void __launch_bounds__(256) oz_reduce_kernel(const __grid_constant__ 
   const int b = (int)(id / per);
   const long long r = id % per;
   const int j = (int)(r / g.M), i = (int)(r % g.M);
+  const int tm = i / TC_BM, il = i % TC_BM, tn = j / BN, jl = j % BN;
   double vr = 0.0, vi = 0.0;
   for (int q = 0; q < a.gp; q++) {
-    const size_t o = ((((size_t)q * g.batch + b) * a.Mp + i) * a.Np + j) * 2;
-    vr += a.part[o];
-    vi += a.part[o + 1];
+    const double *slab = a.acc + ((((size_t)q * g.batch + b) * a.tm + tm) * a.tn + tn) * TcCfg<BN>::kAcc;
+    vr += slab[(size_t)jl * TC_BM + il];
+    vi += slab[(size_t)(BN + jl) * TC_BM + il];
   }
   const int sh = __ldg(a.ea + (size_t)b * a.Mp + i) + __ldg(a.eb + (size_t)b * a.Np + j);
   vr = ldexp(vr, sh);
@@ -550,55 +756,99 @@ __global__ void __launch_bounds__(256) oz_reduce_kernel(const __grid_constant__ 
     ((double2 *)g.C.ptr)[oc] = make_double2(outr, outi);
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependence on libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of `planes` digit planes of rows x Kp bf16 (K-major, k
+// contiguous), copied as boxes of 64 k x box_rows rows into 128-byte-swizzled
+// shared memory.
+bool digit_map(CUtensorMap *m, const void *base, int Kp, int rows, long long planes, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * (cuuint64_t)rows};
+  const cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_product(const OzLayout &L, const TcArgs &a, const void *Ad, const void *Bd, cudaStream_t st) {
+  const GemmDesc &g = a.g;
+  CUtensorMap mA, mB;
+  if (!digit_map(&mA, Ad, L.Kp, L.Mp, (long long)g.batch * OZ_S * 2, TC_BM) ||
+      !digit_map(&mB, Bd, L.Kp, L.Np, (long long)g.batch * OZ_S * 2, BN))
+    return cudaErrorInvalidValue;
+  cudaError_t err =
+      cudaFuncSetAttribute(oz_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<BN>::kSmem);
+  if (err != cudaSuccess) return err;
+  oz_tc_kernel<BN><<<dim3(L.tn, L.tm, g.batch * L.gp), TC_THREADS, TcCfg<BN>::kSmem, st>>>(mA, mB, a);
+  err = cudaGetLastError();
+  if (err != cudaSuccess || L.gp == 1) return err;
+  const long long n = (long long)g.M * g.N * g.batch;
+  oz_reduce_kernel<BN><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-int oz_launches(const GemmDesc &g) { return oz_layout(g).gp > 1 ? 5 : 4; }
+int oz_launches(const GemmDesc &g) { return oz_layout(g, num_sms()).gp > 1 ? 5 : 4; }
 
 bool oz_eligible(const GemmDesc &g) {
-  // worth the split passes only for sizeable products; complex128 arithmetic only
-  // (measured: from ~2^26 complex multiply-adds a launch the emulation beats
-  // the FP64 pipes; 2^23 per product is too small for the fixed costs)
-  return !g.cf32 && g.K >= 64 && g.M >= 32 && g.N >= 32 && g.batch <= 65535 &&
+  // worth the split passes only for sizeable products whose tiles are mostly
+  // live (M padded to 128, N to 64 or 128); complex128 arithmetic only
+  return !g.cf32 && g.K >= 64 && g.M >= 96 && g.N >= 48 && g.batch <= 65535 &&
          (double)g.M * g.N * g.K * g.batch >= (double)(1 << 26);
 }
 
-size_t oz_workspace_bytes(const GemmDesc &g) { return oz_layout(g).total; }
+size_t oz_workspace_bytes(const GemmDesc &g) { return oz_layout(g, num_sms()).total; }
 
-cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st) {
+cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st, unsigned *status) {
   if (g.batch <= 0 || g.M <= 0 || g.N <= 0) return cudaSuccess;
-  const OzLayout L = oz_layout(g);
-  if (!ws || ws_bytes < L.total || g.batch > 65535) return cudaErrorInvalidValue;
+  const OzLayout L = oz_layout(g, num_sms());
+  if (!ws || ws_bytes < L.total || g.batch > 65535 || ((uintptr_t)ws & 255)) return cudaErrorInvalidValue;
   char *w = (char *)ws;
   __nv_bfloat16 *Ad = (__nv_bfloat16 *)(w + L.a_off), *Bd = (__nv_bfloat16 *)(w + L.b_off);
   int *ea = (int *)(w + L.ea_off), *eb = (int *)(w + L.eb_off);
   oz_expo_a_kernel<<<dim3(L.Mp / 32, g.batch), 256, 0, st>>>(g, L.Mp, ea);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  oz_split_a_kernel<<<dim3(L.Mp / 64, L.Kp / 4, g.batch), 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
+  oz_split_a_kernel<<<dim3(L.Mp / OZA_R, L.Kp / OZA_K, g.batch), 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   oz_split_b_kernel<<<dim3((L.Np + 7) / 8, g.batch), 256, 0, st>>>(g, L.Np, L.Kp, Bd, eb);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  OzArgs a;
+  TcArgs a;
   a.g = g;
   a.Mp = L.Mp;
   a.Np = L.Np;
   a.Kp = L.Kp;
-  a.A = Ad;
-  a.B = Bd;
+  a.tm = L.tm;
+  a.tn = L.tn;
+  a.gp = L.gp;
+  a.acc = (double *)(w + L.acc_off);
   a.ea = ea;
   a.eb = eb;
-  a.gp = L.gp;
-  a.part = L.gp > 1 ? (double *)(w + L.part_off) : nullptr;
-  err = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
-  if (err != cudaSuccess) return err;
-  oz_gemm_kernel<<<dim3(L.Np / OZ_BN, L.Mp / OZ_BM, g.batch * L.gp), OZ_THREADS, OZ_SMEM, st>>>(a);
-  err = cudaGetLastError();
-  if (err != cudaSuccess || L.gp == 1) return err;
-  const long long n = (long long)g.M * g.N * g.batch;
-  oz_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
-  return cudaGetLastError();
+  a.status = status;
+  return L.bn == 64 ? launch_product<64>(L, a, Ad, Bd, st) : launch_product<128>(L, a, Ad, Bd, st);
 }
 
 }  // namespace hps

@@ -26,8 +26,12 @@ def _run(A, B, emulated):
     return Cd.cpu().numpy()
 
 
-@pytest.mark.parametrize("M,N,K,batch", [(64, 64, 64, 1), (100, 37, 83, 3), (224, 448, 224, 2),
-                                         (33, 130, 300, 1), (896, 512, 600, 1)])
+# one 128 x 128 tile (its slice pairs split over 9 CTAs and summed by the
+# reduce pass), 64-wide tiles (N <= 64), ragged edges in M, N and K, a
+# batch, two K chunks of 896, and many tiles with one CTA each
+@pytest.mark.parametrize("M,N,K,batch", [(128, 128, 64, 1), (64, 64, 64, 1), (100, 37, 83, 3),
+                                         (224, 448, 224, 2), (33, 130, 300, 1), (896, 512, 600, 1),
+                                         (300, 200, 1000, 1), (252, 48, 252, 7), (1100, 1300, 200, 1)])
 def test_emulated_product_matches_fp64(M, N, K, batch):
     rng = np.random.default_rng(M * 7 + N)
     # stored transposed: A[b] is K x M row-major = M x K column-major
