@@ -34,29 +34,38 @@ from paper_1812_07167_gb300 import workloads as W  # noqa: E402
 
 METRIC = "HPS build DOF/s and solve RHS/s at stated rel. error; p50/p99 solve latency"
 M, P_ORDER, KAPPA = 16, 16, 80.0
-# FP64 peak from unit counts: 152 SMs x 2 FP64 FMA/clk/SM (4 flop) x 2.07 GHz
-# (the 1.25 TFLOP/s nominal of the part)
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# FP64 peak from unit counts: 2 FP64 FMA a clock per SM (4 flop) on this part,
+# times the SM count the device reports and its maximum SM clock (152 SMs at
+# 2.07 GHz: the 1.25 TFLOP/s nominal of the part)
+FP64_FLOP_PER_CLK_PER_SM = 4
 
 
 def workload():
     return W.point_sources(m=M, p=P_ORDER, kappa=KAPPA)
 
 
-def config_dict(nrhs=1, l2="flushed between steps (256 MiB write)"):
+def config_dict(nrhs=1, l2="flushed between steps (256 MiB write)", gpu=True):
+    """The workload of a step; with gpu, also how the GPU path computes it
+    (the reference arm, the oracle on the host cores, has no such choices)."""
     wl = workload()
-    return {
+    out = {
         "workload": "helmholtz_impedance_point_sources",
         "leaves": f"{M}x{M}", "p": P_ORDER, "q": P_ORDER - 2, "kappa": KAPPA, "eta": KAPPA,
         "c": "1+0.3 sin(4 pi x) cos(6 pi y)", "s": "8 Gaussian sources, width 0.01, seed 1", "t": 0,
         "dof": M * M * (P_ORDER * P_ORDER - 4), "tensor_nodes": M * M * P_ORDER * P_ORDER,
         "nrhs_per_step": nrhs, "l2": l2, "precision": "complex128",
-        "leaf_form": ("LU factors P D B = L U (leaf kernel), two triangular sweeps a solve" if LEAF_FORM == 0
-                      else "B^-1 by Gauss-Jordan (leaf kernel), one product a solve"),
-        "products": "FP64 pipes; merge products of 2^26+ complex multiply-adds by the Ozaki scheme "
-                    "on the bf16 tensor cores (9 slices of 6 bits, exact FP32 slice sums, complex128 totals)",
         "domain": list(wl.domain),
     }
+    if gpu:
+        out["leaf_form"] = ("LU factors P D B = L U (leaf kernel), two triangular sweeps a solve" if LEAF_FORM == 0
+                            else "B^-1 (leaf kernel), one product a solve")
+        out["products"] = ("FP64 pipes; merge products of 2^26+ complex multiply-adds by the Ozaki scheme "
+                           "on the bf16 tensor cores (tcgen05; 9 slices of 6 bits, exact FP32 slice sums, "
+                           "complex128 totals)")
+    else:
+        out["program"] = ("the oracle (oracle/hps_oracle.c): Algorithm 1 and 2 in plain C99 complex128, "
+                          "dense LU per leaf, OpenMP over the boxes of a level")
+    return out
 
 
 class ClockSampler:
@@ -160,7 +169,7 @@ def reference_arm(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(l2="n/a (CPU)"),
+        "config": config_dict(l2="n/a (CPU)", gpu=False),
         "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": threads, "kind": "oracle",
                          "sample": "full 16x16-leaf build + 1-RHS solve per step"},
         "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -394,6 +403,13 @@ def ours(args, rank, world, local_rank):
     }
 
     batch_res = None if args.no_batching else batching(dev, st, flush)
+    # the 64 x 64-leaf, kappa = 300 workload (FP64 and mixed; the oracle's
+    # comparison is added on rank 0 below)
+    c3 = c3_data = None
+    if world == 1 and not args.no_config3:
+        c3, c3_data = precision_run(dev, st, flush)
+    fp64_measured = hps.hps_fp64_rate(st)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
 
     if rank != 0:
         return
@@ -405,6 +421,9 @@ def ours(args, rank, world, local_rank):
     leaf_kernel = "lu_leaf_kernel" if lu else "leaf_kernel"
     leaf_avg = statistics.mean(leaf_ms)
     achieved = leaf_flops / (leaf_avg / 1e3) / 1e12
+    clocks = clk.summary()
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    fp64_nominal = n_sm * FP64_FLOP_PER_CLK_PER_SM * max_mhz * 1e6 / 1e12
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", f"{leaf_kernel}_traffic.json")
     if os.path.exists(tr_path):
@@ -430,14 +449,17 @@ def ours(args, rank, world, local_rank):
                    "what": "hps_tune: measured tile / tensor-core choice per merge product shape and "
                            "cluster / panel regime per interface-inverse shape, before the timed steps"},
         "roofline": {"kernel": leaf_kernel, "bound": "alu", "achieved": achieved, "flops_per_launch": leaf_flops,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak": fp64_nominal, "unit": "TFLOP/s", "frac": achieved / fp64_nominal,
                      "traffic": traffic, "leaf_ms": leaf_avg,
-                     "peak_source": "FP64 unit count x max SM clock (152 SM x 4 flop/clk x 2.07 GHz)"},
+                     "peak_source": f"FP64 unit count x max SM clock ({n_sm} SMs x "
+                                    f"{FP64_FLOP_PER_CLK_PER_SM} flop/clk x {max_mhz:.0f} MHz)",
+                     "peak_measured": fp64_measured, "frac_of_measured": achieved / fp64_measured,
+                     "peak_measured_source": "hps_fp64_rate: independent FMA chains on every SM, CUDA events"},
         "e2e": {"value": e2e_value, "unit": "DOF/s",
                 "h2d_bytes_per_step": int(c.nbytes + s.nbytes + t.nbytes),
                 "d2h_bytes_per_step": int(u_gpu.nbytes)},
         "gpu_launches": args.steps * (info.build_launches + info.solve_launches),
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "wall_s_timed_region": t_wall1 - t_wall0,
         "mixed": {
             "what": "complex64 leaves and lower merges, complex128 top 4 levels, 2 complex128 refinement steps",
@@ -469,6 +491,10 @@ def ours(args, rank, world, local_rank):
         }
         line["mixed"]["rel_err_u_vs_oracle"] = float(np.abs(u_mixed - u_ora).max() / np.abs(u_ora).max())
         line["mixed"]["rel_err_root_R_vs_oracle"] = float(np.linalg.norm(R_mixed - R_ora) / np.linalg.norm(R_ora))
+        if c3 is not None:
+            precision_oracle(c3, c3_data)
+    if c3 is not None:
+        line["config3_64x64"] = c3
     print(json.dumps(line), flush=True)
 
 
@@ -546,19 +572,16 @@ def batching(dev, st, flush, reps=2):
     return out
 
 
-def precision(args, local_rank):
+def precision_run(dev, st, flush):
     """64 x 64 leaves (1,032,192 unknowns), p = 16, kappa = eta = 300, random
     medium (seed 2) with 8 Gaussian sources, t = 0: the complex128 path
     against the mixed path (complex64 leaves and lower merges, complex128 top
-    4 levels, complex128 refinement), both against the oracle, whose full
-    build + solve on the host cores is this mode's CPU baseline."""
+    4 levels, complex128 refinement), on the GPU.  Returns the JSON part and
+    what precision_oracle needs to add the oracle's figures."""
     import torch
 
     from paper_1812_07167_gb300 import hps
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    st = torch.cuda.current_stream()
     m, p, kappa = 64, P_ORDER, 300.0
     wl = W.random_medium_sources(m, p, kappa)
     pr = _problem(m, p, kappa, kappa)
@@ -567,76 +590,99 @@ def precision(args, local_rank):
     cd = torch.from_numpy(c).to(dev)
     sd = torch.from_numpy(np.ascontiguousarray(s[None])).to(dev)
     td = torch.from_numpy(np.ascontiguousarray(t[None])).to(dev)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     dof = pr.leaves * pr.n
-    out = {"metric": "HPS build DOF/s and solve RHS/s at stated rel. error (64x64 leaves, FP64 vs mixed)",
-           "unit": "DOF/s", "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
-           "config": {"workload": "helmholtz_random_medium_sources", "leaves": f"{m}x{m}", "p": p, "q": p - 2,
+    out = {"config": {"workload": "helmholtz_random_medium_sources", "leaves": f"{m}x{m}", "p": p, "q": p - 2,
                       "kappa": kappa, "eta": kappa, "c": "random medium, 32 Fourier modes, seed 2",
                       "s": "8 Gaussian sources, width 0.01", "t": 0, "dof": dof}}
     res = {}
-    with ClockSampler(local_rank) as clk:
-        for name, prec in (("fp64", hps.HPS_FP64), ("mixed", hps.HPS_MIXED)):
-            q = _problem(m, p, kappa, kappa, precision=prec)
-            tuned = hps.hps_tune([q], st)
-            bms = []
-            for rep in range(4):
-                flush.zero_()
-                e0.record(st)
-                h = hps.hps_build(q, cd, st)
-                e1.record(st)
-                torch.cuda.synchronize()
-                if rep:
-                    bms.append(e0.elapsed_time(e1))
-                if rep < 3:
-                    h.free()
-            code = hps.hps_status(h, st)[0]
-            u = torch.empty((1, pr.leaves, pr.n), dtype=torch.complex128, device=dev)
-            sms = []
-            for rep in range(6):
-                flush.zero_()
-                e0.record(st)
-                hps.hps_solve(h, sd, td, u, 1, st)
-                e1.record(st)
-                torch.cuda.synchronize()
-                if rep:
-                    sms.append(e0.elapsed_time(e1))
-            R = np.zeros((pr.nbdry, pr.nbdry), complex)
-            hps.hps_root_R(h, R, st)
-            info = h.info()
-            res[name] = {"u": u.cpu().numpy()[0], "R": R}
-            out[name] = {"status": hps.hps_strerror(code), "build_ms": statistics.median(bms),
-                         "build_dof_per_s": dof / (statistics.median(bms) / 1e3),
-                         "solve_ms_1rhs": statistics.median(sms), "solve_rhs_per_s": 1e3 / statistics.median(sms),
-                         "operator_bytes": info.operator_bytes, "build_launches": info.build_launches,
-                         "tuned_shapes": tuned,
-                         "leaf_and_level_ms": [float(x) for x in hps.hps_build_times(h)]}
-            h.free()
-    out["clocks"] = clk.summary()
+    for name, prec in (("fp64", hps.HPS_FP64), ("mixed", hps.HPS_MIXED)):
+        q = _problem(m, p, kappa, kappa, precision=prec)
+        tuned = hps.hps_tune([q], st)
+        bms = []
+        for rep in range(4):
+            flush.zero_()
+            e0.record(st)
+            h = hps.hps_build(q, cd, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            if rep:
+                bms.append(e0.elapsed_time(e1))
+            if rep < 3:
+                h.free()
+        code = hps.hps_status(h, st)[0]
+        u = torch.empty((1, pr.leaves, pr.n), dtype=torch.complex128, device=dev)
+        sms = []
+        for rep in range(6):
+            flush.zero_()
+            e0.record(st)
+            hps.hps_solve(h, sd, td, u, 1, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            if rep:
+                sms.append(e0.elapsed_time(e1))
+        R = np.zeros((pr.nbdry, pr.nbdry), complex)
+        hps.hps_root_R(h, R, st)
+        info = h.info()
+        res[name] = {"u": u.cpu().numpy()[0], "R": R}
+        out[name] = {"status": hps.hps_strerror(code), "build_ms": statistics.median(bms),
+                     "build_dof_per_s": dof / (statistics.median(bms) / 1e3),
+                     "solve_ms_1rhs": statistics.median(sms), "solve_rhs_per_s": 1e3 / statistics.median(sms),
+                     "operator_bytes": info.operator_bytes, "build_launches": info.build_launches,
+                     "tuned_shapes": tuned,
+                     "leaf_and_level_ms": [round(float(x), 3) for x in hps.hps_build_times(h)]}
+        h.free()
     uf, um = res["fp64"]["u"], res["mixed"]["u"]
     Rf, Rm = res["fp64"]["R"], res["mixed"]["R"]
     out["mixed"]["rel_err_u_vs_fp64_gpu"] = float(np.abs(um - uf).max() / np.abs(uf).max())
     out["mixed"]["rel_err_root_R_vs_fp64_gpu"] = float(np.linalg.norm(Rm - Rf) / np.linalg.norm(Rf))
+    return out, (c, s, t, res)
+
+
+def precision_oracle(out, data):
+    """Add to precision_run's result the oracle's full 64 x 64-leaf build +
+    solve on the host cores (its time is the CPU baseline) and the errors of
+    both GPU paths against it."""
+    import oracle as O
+
+    c, s, t, res = data
+    m, p, kappa = 64, P_ORDER, 300.0
+    dof = m * m * (p * p - 4)
+    threads = os.cpu_count() or 1
+    opr = O.Problem(m, p, kappa, kappa)
+    t0 = time.perf_counter()
+    T = O.Tree(opr, c, nthreads=threads)
+    uo = T.solve(s[None], t[None], nthreads=threads)[0]
+    dt = time.perf_counter() - t0
+    Ro = T.root_R()
+    cond = T.cond_W()
+    T.close()
+    out["cpu_baseline"] = {"value": dof / dt, "unit": "DOF/s", "cores": threads, "kind": "oracle",
+                           "sample": "one full 64x64-leaf build + 1-RHS solve", "seconds": dt}
+    out["cond1_W_per_level_from_root"] = [float(f"{v:.3g}") for v in cond]
+    for name in ("fp64", "mixed"):
+        out[name]["rel_err_u_vs_oracle"] = float(np.abs(res[name]["u"] - uo).max() / np.abs(uo).max())
+        out[name]["rel_err_root_R_vs_oracle"] = float(np.linalg.norm(res[name]["R"] - Ro) / np.linalg.norm(Ro))
+    return out
+
+
+def precision(args, local_rank):
+    """The 64 x 64-leaf, kappa = 300 run of precision_run as its own JSON line."""
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    st = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    with ClockSampler(local_rank) as clk:
+        res, data = precision_run(dev, st, flush)
+    out = {"metric": "HPS build DOF/s and solve RHS/s at stated rel. error (64x64 leaves, FP64 vs mixed)",
+           "unit": "DOF/s", "higher_is_better": True, "n_gpus": 1, "data": "synthetic"}
+    out.update(res)
+    out["clocks"] = clk.summary()
     out["value"] = out["mixed"]["build_dof_per_s"]
     if not args.no_cpu_baseline:
-        import oracle as O
-
-        threads = os.cpu_count() or 1
-        opr = O.Problem(m, p, kappa, kappa)
-        t0 = time.perf_counter()
-        T = O.Tree(opr, c, nthreads=threads)
-        uo = T.solve(s[None], t[None], nthreads=threads)[0]
-        dt = time.perf_counter() - t0
-        Ro = T.root_R()
-        cond = T.cond_W()
-        T.close()
-        out["cpu_baseline"] = {"value": dof / dt, "unit": "DOF/s", "cores": threads, "kind": "oracle",
-                               "sample": "one full 64x64-leaf build + 1-RHS solve", "seconds": dt}
-        out["cond1_W_per_level_from_root"] = [float(f"{v:.3g}") for v in cond]
-        for name in ("fp64", "mixed"):
-            out[name]["rel_err_u_vs_oracle"] = float(np.abs(res[name]["u"] - uo).max() / np.abs(uo).max())
-            out[name]["rel_err_root_R_vs_oracle"] = float(np.linalg.norm(res[name]["R"] - Ro) / np.linalg.norm(Ro))
+        precision_oracle(out, data)
     print(json.dumps(out), flush=True)
 
 
@@ -943,6 +989,8 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="run the 64x64-leaf FP64-vs-mixed workload (with the oracle) instead of the step bench")
     ap.add_argument("--no-batching", action="store_true", help="skip the ragged-batch section")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the 64x64-leaf kappa=300 section (FP64 and mixed, and the oracle on the host cores)")
     ap.add_argument("--polynomial", type=int, metavar="M",
                     help="capacity check: M x M leaves, polynomial solution, nodal error and memory")
     ap.add_argument("--scaling", action="store_true",

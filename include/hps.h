@@ -308,6 +308,14 @@ int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, v
 int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, double *C, int emulated,
               void *stream);
 
+/* The FP64 fused multiply-add rate of the current device, measured: a
+ * kernel of independent FMA chains on every SM, timed with CUDA events on
+ * `stream` (best of 3 after a warm-up, about 20 ms each).  *tflops receives
+ * TFLOP/s (2 flop an FMA).  A diagnostic beside the solver, for the roofline
+ * of its complex128 kernels on the FMA pipes; the paper has no counterpart.
+ * Synchronizes the stream.  Returns HPS_EINVAL (NULL tflops), HPS_ECUDA. */
+int hps_fp64_rate(double *tflops, void *stream);
+
 /* Measure, on this GPU, the kernel choices the builds of these problems would
  * make, and keep the fastest for every later build in this process: for each
  * merge product shape (M, N, K, parents, precision) the tile configuration

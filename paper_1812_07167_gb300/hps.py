@@ -29,7 +29,7 @@ HPS_LEAF_INVERSE = 1
 
 # every entry point include/hps.h declares
 EXPORTS = ("hps_nodes", "hps_build", "hps_build_batch", "hps_rebuild", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
-           "hps_root_R", "hps_leaf_ops", "hps_zgemm", "hps_tune", "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
+           "hps_root_R", "hps_leaf_ops", "hps_zgemm", "hps_fp64_rate", "hps_tune", "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
 
 
 class hps_desc(ctypes.Structure):
@@ -88,6 +88,7 @@ def lib():
         L.hps_solve_batch.argtypes = [P, ctypes.c_int, P, P, P, P, P]
         L.hps_reserve.argtypes = [P, ctypes.c_int]
         L.hps_zgemm.argtypes = [ctypes.c_int] * 4 + [P, P, P, ctypes.c_int, P]
+        L.hps_fp64_rate.argtypes = [P, P]
         L.hps_root_R.argtypes = [P, P, ctypes.c_int, P]
         L.hps_leaf_ops.argtypes = [P, ctypes.c_int, P, P, P, P]
         L.hps_info.argtypes = [P, ctypes.POINTER(hps_info_t)]
@@ -296,6 +297,13 @@ def hps_zgemm(A, B, C, emulated: int, stream=None):
     _check(lib().hps_zgemm(M, N, K, batch, _ptr(A), _ptr(B), _ptr(C), int(emulated), _stream(stream)),
            "hps_zgemm")
     return C
+
+
+def hps_fp64_rate(stream=None) -> float:
+    """Measured FP64 FMA rate of the current device in TFLOP/s."""
+    out = ctypes.c_double(0.0)
+    _check(lib().hps_fp64_rate(ctypes.byref(out), _stream(stream)), "hps_fp64_rate")
+    return out.value
 
 
 def hps_reserve(h: Handle, nrhs: int):

@@ -23,7 +23,7 @@ def built():
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "hps.h")).read()
-    return sorted(set(re.findall(r"\b(hps_[a-zA-Z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(hps_[a-zA-Z0-9_]+)\s*\(", src)))
 
 
 def test_header_and_binding_agree():
