@@ -960,6 +960,44 @@ def serving(args, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def profile_step(args, local_rank):
+    """One bench step (build + 1-RHS solve of the 16 x 16-leaf workload) between
+    cudaProfilerStart and cudaProfilerStop, after the tuner and three warm-up
+    steps, for `ncu --profile-from-start off`: the profiler then sees exactly
+    the kernels of one timed step, with the kernel choices the bench makes."""
+    import torch
+
+    from paper_1812_07167_gb300 import hps
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    st = torch.cuda.current_stream()
+    wl = workload()
+    pr = _problem(wl.m, wl.p, wl.kappa, wl.eta)
+    lxy, bxy = hps.hps_nodes(pr)
+    c, s, t = wl.sample(lxy, bxy)
+    cd = torch.from_numpy(c).to(dev)
+    sd = torch.from_numpy(np.ascontiguousarray(s[None])).to(dev)
+    td = torch.from_numpy(np.ascontiguousarray(t[None])).to(dev)
+    ud = torch.empty((1, pr.leaves, pr.n), dtype=torch.complex128, device=dev)
+    hps.hps_tune([pr], st)
+    for _ in range(3):
+        h = hps.hps_build(pr, cd, st)
+        hps.hps_solve(h, sd, td, ud, 1, st)
+        torch.cuda.synchronize()
+        h.free()
+    torch.cuda.profiler.start()
+    h = hps.hps_build(pr, cd, st)
+    hps.hps_solve(h, sd, td, ud, 1, st)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    info = h.info()
+    code = hps.hps_status(h, st)[0]
+    h.free()
+    print(json.dumps({"profiled_step": "16x16 build + 1-RHS solve", "status": hps.hps_strerror(code),
+                      "build_launches": info.build_launches, "solve_launches": info.solve_launches}), flush=True)
+
+
 def kernel_hash(kernel="lu_leaf_kernel"):
     """Hash of the code of a leaf kernel (its file and the device headers it
     includes, comments left out), so stored ncu counters are used only for
@@ -1001,6 +1039,8 @@ def main():
                     help="--serve: leaf form of the resident solver (its requests are wide solves)")
     ap.add_argument("--zgemm", type=int, nargs=3, metavar=("M", "N", "K"),
                     help="time one complex GEMM on the tensor cores and on the FP64 pipes")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="one tuned step between cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--serve-m", type=int, default=128)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-max-rhs", type=int, default=128)
@@ -1021,6 +1061,9 @@ def main():
         return
     if args.zgemm:
         zgemm(args, local_rank)
+        return
+    if args.profile_step:
+        profile_step(args, local_rank)
         return
     if args.scaling:
         scaling(args, local_rank)

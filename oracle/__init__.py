@@ -50,13 +50,16 @@ class _Desc(ctypes.Structure):
         ("kappa", ctypes.c_double),
         ("eta_re", ctypes.c_double), ("eta_im", ctypes.c_double),
         ("first_vertical", ctypes.c_int),
+        ("gauss_q", ctypes.c_int),
     ]
 
 
 @dataclass
 class Problem:
     """Problem description: rectangle, m x my leaves (my = m unless given),
-    p Chebyshev nodes per side."""
+    p Chebyshev nodes per side; q > 0 puts the boundary data on q
+    Gauss-Legendre nodes per leaf edge (0: the p-2 corner-free Chebyshev
+    edge nodes of the paper's scheme)."""
     m: int
     p: int
     kappa: float
@@ -66,6 +69,7 @@ class Problem:
     y0: float = 0.0
     y1: float = 1.0
     my: int = 0
+    q: int = 0
 
     @property
     def mx(self) -> int:
@@ -96,8 +100,18 @@ class Problem:
         return self.m * self.ny
 
     @property
+    def qe(self) -> int:
+        """Boundary-data points per leaf edge."""
+        return self.q or self.p - 2
+
+    @property
+    def nbi(self) -> int:
+        """Boundary-data points of a leaf (its interface with its neighbours)."""
+        return 4 * self.qe
+
+    @property
     def nbdry(self) -> int:
-        return 2 * (self.m + self.ny) * (self.p - 2)
+        return 2 * (self.m + self.ny) * self.qe
 
 
 def _lib_handle():
@@ -117,6 +131,8 @@ def _lib_handle():
         lib.ora_free.argtypes = [P]
         lib.ora_brute.argtypes = [ctypes.POINTER(_Desc), P, P, P, P]
         lib.ora_max_threads.restype = ctypes.c_int
+        lib.ora_gauss_nodes.argtypes = [ctypes.c_int, P]
+        lib.ora_edge_interp.argtypes = [ctypes.c_int, ctypes.c_int, P, P]
         lib.ora_cond_W.argtypes = [P, ctypes.c_int]
         lib.ora_cond_W.restype = ctypes.c_double
         _lib = lib
@@ -126,7 +142,7 @@ def _lib_handle():
 def _desc(pr: Problem, first_vertical: bool = False) -> _Desc:
     eta = complex(pr.eta)
     return _Desc(pr.x0, pr.x1, pr.y0, pr.y1, pr.m, pr.ny, pr.p, pr.kappa, eta.real, eta.imag,
-                 1 if first_vertical else 0)
+                 1 if first_vertical else 0, int(pr.q))
 
 
 def _ptr(a: np.ndarray):
@@ -144,6 +160,24 @@ def cheb(p: int, a: float = -1.0, b: float = 1.0):
     D = np.zeros((p, p))
     _lib_handle().ora_cheb(p, a, b, _ptr(x), _ptr(D))
     return x, D
+
+
+def gauss_nodes(q: int) -> np.ndarray:
+    """The q Gauss-Legendre nodes on [-1, 1], increasing."""
+    z = np.zeros(q)
+    if _lib_handle().ora_gauss_nodes(int(q), _ptr(z)):
+        raise ValueError("q < 1")
+    return z
+
+
+def edge_interp(p: int, q: int):
+    """(P [q, p-2], Q [p-2, q]): interpolation from an edge's corner-free
+    Chebyshev nodes to its q Gauss nodes and back."""
+    Pm = np.zeros((q, p - 2))
+    Qm = np.zeros((p - 2, q))
+    if _lib_handle().ora_edge_interp(int(p), int(q), _ptr(Pm), _ptr(Qm)):
+        raise ValueError("bad p or q")
+    return Pm, Qm
 
 
 def nodes(pr: Problem):
@@ -217,10 +251,12 @@ class Tree:
             lev += 1
 
     def leaf_ops(self, pub: int):
+        """(Psi [n, nbi], Y [n, ni], Gamma [nbi, ni]) of a leaf as the build
+        stores them (on the Gauss nodes when q > 0)."""
         pr = self.pr
-        Psi = np.zeros((pr.n, pr.nb), complex)
+        Psi = np.zeros((pr.n, pr.nbi), complex)
         Y = np.zeros((pr.n, pr.ni), complex)
-        Gam = np.zeros((pr.nb, pr.ni), complex)
+        Gam = np.zeros((pr.nbi, pr.ni), complex)
         if _lib_handle().ora_tree_leaf(self._h, int(pub), _ptr(Psi), _ptr(Y), _ptr(Gam)):
             raise IndexError(pub)
         return Psi, Y, Gam

@@ -76,6 +76,11 @@ typedef struct {
   double kappa;          /* wave number */
   double eta_re, eta_im; /* impedance parameter eta, Re(eta) != 0 */
   int first_vertical;    /* 0: first merge joins west/east leaves */
+  int gauss_q;           /* 0: boundary data on the p-2 corner-free Chebyshev
+                            nodes of every leaf edge (the paper's scheme);
+                            q > 0: on q Gauss-Legendre nodes per leaf edge,
+                            reached by polynomial interpolation (the
+                            interface of the earlier ItI work the paper cites) */
 } ora_desc;
 
 /* ------------------------------------------------------------------ */
@@ -222,6 +227,91 @@ int ora_cheb(int p, double a, double b, double *x, double *D) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Gauss-Legendre interface nodes and interpolation (gauss_q > 0)       */
+/* ------------------------------------------------------------------ */
+
+/* Legendre polynomial P_q(z) by the three-term recurrence
+ * k P_k = (2k - 1) z P_{k-1} - (k - 1) P_{k-2}, P_0 = 1, P_1 = z. */
+static double legendre(int q, double z) {
+  double a = 1.0, b = z;
+  if (q == 0) return a;
+  for (int k = 2; k <= q; k++) {
+    double c = ((2.0 * k - 1.0) * z * b - (k - 1.0) * a) / k;
+    a = b;
+    b = c;
+  }
+  return b;
+}
+
+/* The q Gauss-Legendre nodes on [-1, 1] (the roots of P_q), increasing: every
+ * sign change of P_q on a fine grid, then bisection to the last bit. */
+int ora_gauss_nodes(int q, double *z) {
+  if (q < 1) return 1;
+  int found = 0, steps = 64 * q;
+  double x0 = -1.0, f0 = legendre(q, x0);
+  for (int k = 1; k <= steps && found < q; k++) {
+    double x1 = -cos(M_PI * k / steps), f1 = legendre(q, x1);
+    if (f0 == 0.0) {
+      z[found++] = x0;
+    } else if (f0 * f1 < 0.0) {
+      double lo = x0, hi = x1, flo = f0;
+      for (int it = 0; it < 200 && hi - lo > 0.0; it++) {
+        double mid = 0.5 * (lo + hi), fm = legendre(q, mid);
+        if (mid <= lo || mid >= hi) break;
+        if ((fm < 0.0) == (flo < 0.0)) {
+          lo = mid;
+          flo = fm;
+        } else {
+          hi = mid;
+        }
+      }
+      z[found++] = 0.5 * (lo + hi);
+    }
+    x0 = x1;
+    f0 = f1;
+  }
+  return found == q ? 0 : 1;
+}
+
+/* Lagrange basis polynomial j of the m nodes xs, evaluated at x. */
+static double lagrange(int m, const double *xs, int j, double x) {
+  double v = 1.0;
+  for (int k = 0; k < m; k++)
+    if (k != j) v *= (x - xs[k]) / (xs[j] - xs[k]);
+  return v;
+}
+
+/* Interpolation between the e = p-2 corner-free Chebyshev nodes of an edge
+ * and its q Gauss-Legendre nodes (both on the reference edge [-1, 1]; the
+ * matrices do not depend on the edge's position or length):
+ *   Pm (q x e): the Chebyshev-node interpolant (degree e-1) at the Gauss nodes
+ *   Qm (e x q): the Gauss-node interpolant (degree q-1) at the Chebyshev nodes
+ * Outgoing data g (Chebyshev) becomes Pm g on the Gauss nodes; incoming Gauss
+ * data t_G becomes Qm t_G on the Chebyshev nodes. */
+static void edge_interp(int p, int q, double *Pm, double *Qm) {
+  int e = p - 2;
+  double *xc = xmalloc(sizeof(double) * p), *D = xmalloc(sizeof(double) * p * p);
+  double *zg = xmalloc(sizeof(double) * q);
+  ora_cheb(p, -1.0, 1.0, xc, D);
+  ora_gauss_nodes(q, zg);
+  const double *ce = xc + 1; /* the corner-free nodes x_1 .. x_{p-2} */
+  for (int a = 0; a < q; a++)
+    for (int j = 0; j < e; j++) Pm[a * e + j] = lagrange(e, ce, j, zg[a]);
+  for (int j = 0; j < e; j++)
+    for (int a = 0; a < q; a++) Qm[j * q + a] = lagrange(q, zg, a, ce[j]);
+  free(xc);
+  free(D);
+  free(zg);
+}
+
+/* Public for tests: Pm (q x e) and Qm (e x q) of edge_interp. */
+int ora_edge_interp(int p, int q, double *Pm, double *Qm) {
+  if (p < 4 || q < 1) return 1;
+  edge_interp(p, q, Pm, Qm);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* leaf geometry and ordering                                            */
 /* ------------------------------------------------------------------ */
 
@@ -290,6 +380,7 @@ static int log2i(int m) {
 }
 
 static int check_desc(const ora_desc *d) {
+  if (d->gauss_q < 0 || d->gauss_q > 64) return 1;
   if (d->mx < 1 || (d->mx & (d->mx - 1))) return 1;
   if (d->my < 1 || (d->my & (d->my - 1))) return 1;
   if (d->p < 4) return 1;
@@ -298,9 +389,12 @@ static int check_desc(const ora_desc *d) {
   return 0;
 }
 
+/* boundary-data points per leaf edge: p-2 Chebyshev nodes, or gauss_q */
+static int edge_pts(const ora_desc *d) { return d->gauss_q ? d->gauss_q : d->p - 2; }
+
 /* Coordinates of every leaf node ([leaves][p*p-4][2], public leaf order) and
- * of the outer boundary nodes ([2 (mx + my) (p-2)][2], sides S, E, N, W, each
- * in increasing coordinate). */
+ * of the outer boundary nodes ([2 (mx + my) q][2], q = edge_pts: sides S, E,
+ * N, W, each in increasing coordinate). */
 int ora_nodes(const ora_desc *d, double *leaf_xy, double *bdry_xy) {
   if (check_desc(d)) return 1;
   int p = d->p, e = p - 2, n = p * p - 4;
@@ -323,30 +417,55 @@ int ora_nodes(const ora_desc *d, double *leaf_xy, double *bdry_xy) {
     }
   }
   if (bdry_xy) {
-    int q = 0;
+    int q = 0, gq = d->gauss_q;
+    double *zg = xmalloc(sizeof(double) * (gq ? gq : 1));
+    if (gq) ora_gauss_nodes(gq, zg);
     for (int side = 0; side < 4; side++) {
       int horizontal = (side == 0 || side == 2);
       for (int c = 0; c < (horizontal ? d->mx : d->my); c++) {
+        double lo = horizontal ? d->x0 + c * hx : d->y0 + c * hy;
+        double len = horizontal ? hx : hy;
         if (horizontal)
           ora_cheb(p, d->x0 + c * hx, d->x0 + (c + 1) * hx, xs, D);
         else
           ora_cheb(p, d->y0 + c * hy, d->y0 + (c + 1) * hy, ys, D);
-        for (int k = 1; k <= e; k++, q++) {
+        for (int k = 1; k <= (gq ? gq : e); k++, q++) {
+          /* the k-th node of this leaf edge along the side: Chebyshev node k,
+           * or Gauss node k-1 mapped from [-1, 1] */
+          double along = gq ? lo + 0.5 * (zg[k - 1] + 1.0) * len : (horizontal ? xs[k] : ys[k]);
           double x, y;
-          if (side == 0) { x = xs[k]; y = d->y0; }
-          else if (side == 1) { x = d->x1; y = ys[k]; }
-          else if (side == 2) { x = xs[k]; y = d->y1; }
-          else { x = d->x0; y = ys[k]; }
+          if (side == 0) { x = along; y = d->y0; }
+          else if (side == 1) { x = d->x1; y = along; }
+          else if (side == 2) { x = along; y = d->y1; }
+          else { x = d->x0; y = along; }
           bdry_xy[2 * q] = x;
           bdry_xy[2 * q + 1] = y;
         }
       }
     }
+    free(zg);
   }
   free(xs);
   free(ys);
   free(D);
   return 0;
+}
+
+/* Gauss nodes zg (q of them, on [-1, 1]) of the four edges [S, E, N, W] of
+ * the leaf in column col, row row, each edge in increasing coordinate:
+ * xy [4 q][2]. */
+static void leaf_gauss_xy(const ora_desc *d, int col, int row, int q, const double *zg, double *xy) {
+  double hx = (d->x1 - d->x0) / d->mx, hy = (d->y1 - d->y0) / d->my;
+  double xl = d->x0 + col * hx, yl = d->y0 + row * hy;
+  for (int side = 0; side < 4; side++)
+    for (int a = 0; a < q; a++) {
+      double *pt = &xy[2 * (side * q + a)];
+      double sx = xl + 0.5 * (zg[a] + 1.0) * hx, sy = yl + 0.5 * (zg[a] + 1.0) * hy;
+      if (side == 0) { pt[0] = sx; pt[1] = yl; }
+      else if (side == 1) { pt[0] = xl + hx; pt[1] = sy; }
+      else if (side == 2) { pt[0] = sx; pt[1] = yl + hy; }
+      else { pt[0] = xl; pt[1] = sy; }
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -508,7 +627,8 @@ typedef struct {
   int L;          /* leaf level */
   int nboxes;     /* 2^(L+1) - 1, boxes numbered 1..nboxes */
   ora_box *box;   /* box[tau], tau = 1..nboxes */
-  int e, n, nb, ni;
+  int e, n, nb, ni;  /* nb: boundary-data points of a leaf (4 edge_pts) */
+  double *Pm, *Qm;   /* gauss_q > 0: edge interpolation (edge_interp) */
   int status;
   int dir[64];      /* merge directions of this tree, from the leaves */
   int pub_dir[64];  /* those of the public leaf order */
@@ -672,17 +792,46 @@ static void leaf_box(ora_tree *T, const leaf_geom *g, int tau, const double *c) 
   ora_box *b = &T->box[tau];
   int slot = tau - (1 << T->L);
   int pub = tree_leaf_public(T, slot);
-  int n = T->n, nb = T->nb, ni = T->ni;
+  int n = T->n, nb = T->nb, ni = T->ni, nbc = g->nb; /* nbc: Chebyshev edge nodes of a leaf */
   b->is_leaf = 1;
   b->pub = pub;
   b->nb = nb;
-  b->Psi = xmalloc(sizeof(cplx) * (size_t)n * nb);
+  b->Psi = xmalloc(sizeof(cplx) * (size_t)n * nbc);
   b->Y = xmalloc(sizeof(cplx) * (size_t)n * ni);
-  b->Gam = xmalloc(sizeof(cplx) * (size_t)nb * ni);
-  b->R = xmalloc(sizeof(cplx) * (size_t)nb * nb);
+  b->Gam = xmalloc(sizeof(cplx) * (size_t)nbc * ni);
+  b->R = xmalloc(sizeof(cplx) * (size_t)nbc * nbc);
   int bad = leaf_ops(g, T->d.kappa, T->d.eta_re + I * T->d.eta_im, c + (size_t)pub * ni, b->Psi,
                      b->Y, b->R, b->Gam, NULL, NULL, NULL);
   if (bad && !T->status) T->status = 1;
+  if (T->d.gauss_q) {
+    /* boundary data on the Gauss nodes: incoming t_G enters as Qh t_G on the
+     * Chebyshev edge nodes, outgoing data leaves as Ph g; so Psi_G = Psi Qh,
+     * R_G = Ph R Qh, Gamma_G = Ph Gamma with Ph = diag(Pm, Pm, Pm, Pm) and
+     * Qh = diag(Qm, Qm, Qm, Qm) over the edges [S, E, N, W] */
+    int q = T->d.gauss_q, e = T->e;
+    cplx *Ph = xmalloc(sizeof(cplx) * (size_t)nb * nbc), *Qh = xmalloc(sizeof(cplx) * (size_t)nbc * nb);
+    for (int side = 0; side < 4; side++) {
+      for (int a = 0; a < q; a++)
+        for (int j = 0; j < e; j++) Ph[(size_t)(side * q + a) * nbc + side * e + j] = T->Pm[a * e + j];
+      for (int j = 0; j < e; j++)
+        for (int a = 0; a < q; a++) Qh[(size_t)(side * e + j) * nb + side * q + a] = T->Qm[j * q + a];
+    }
+    cplx *Psi = xmalloc(sizeof(cplx) * (size_t)n * nb), *Gam = xmalloc(sizeof(cplx) * (size_t)nb * ni);
+    cplx *RQ = xmalloc(sizeof(cplx) * (size_t)nbc * nb), *R = xmalloc(sizeof(cplx) * (size_t)nb * nb);
+    matmul(n, nbc, nb, b->Psi, Qh, Psi);
+    matmul(nbc, nbc, nb, b->R, Qh, RQ);
+    matmul(nb, nbc, nb, Ph, RQ, R);
+    matmul(nb, nbc, ni, Ph, b->Gam, Gam);
+    free(b->Psi);
+    free(b->R);
+    free(b->Gam);
+    b->Psi = Psi;
+    b->R = R;
+    b->Gam = Gam;
+    free(Ph);
+    free(Qh);
+    free(RQ);
+  }
   /* boundary coordinates of this leaf, in its local order */
   int p = T->d.p, col, row;
   leaf_decode(pub, T->pub_dir, T->L, &col, &row);
@@ -692,11 +841,20 @@ static void leaf_box(ora_tree *T, const leaf_geom *g, int tau, const double *c) 
   ora_cheb(p, T->d.x0 + col * hx, T->d.x0 + (col + 1) * hx, xs, D);
   ora_cheb(p, T->d.y0 + row * hy, T->d.y0 + (row + 1) * hy, ys, D);
   b->bxy = xmalloc(sizeof(double) * 2 * nb);
-  for (int k = 0; k < nb; k++) {
-    int ix, iy;
-    local_to_grid(p, k, &ix, &iy);
-    b->bxy[2 * k] = xs[ix];
-    b->bxy[2 * k + 1] = ys[iy];
+  if (!T->d.gauss_q) {
+    for (int k = 0; k < nb; k++) {
+      int ix, iy;
+      local_to_grid(p, k, &ix, &iy);
+      b->bxy[2 * k] = xs[ix];
+      b->bxy[2 * k + 1] = ys[iy];
+    }
+  } else {
+    /* the Gauss nodes of the edges [S, E, N, W], each in increasing coordinate */
+    int q = T->d.gauss_q;
+    double *zg = xmalloc(sizeof(double) * q);
+    ora_gauss_nodes(q, zg);
+    leaf_gauss_xy(&T->d, col, row, q, zg, b->bxy);
+    free(zg);
   }
   free(xs);
   free(ys);
@@ -715,8 +873,14 @@ void *ora_build(const ora_desc *d, const double *c, int nthreads) {
   T->box = xmalloc(sizeof(ora_box) * (size_t)(T->nboxes + 1));
   T->e = d->p - 2;
   T->n = d->p * d->p - 4;
-  T->nb = 4 * T->e;
+  T->nb = 4 * edge_pts(d);
   T->ni = T->e * T->e;
+  T->Pm = T->Qm = NULL;
+  if (d->gauss_q) {
+    T->Pm = xmalloc(sizeof(double) * d->gauss_q * T->e);
+    T->Qm = xmalloc(sizeof(double) * d->gauss_q * T->e);
+    edge_interp(d->p, d->gauss_q, T->Pm, T->Qm);
+  }
   leaf_geom g;
   leaf_geom_init(&g, d->p, (d->x1 - d->x0) / d->mx, (d->y1 - d->y0) / d->my);
   if (nthreads < 1) nthreads = 1;
@@ -739,7 +903,7 @@ int ora_status(void *h) { return ((ora_tree *)h)->status; }
 
 /* root ItI operator reordered to the public [S, E, N, W] boundary order */
 static int *root_order(ora_tree *T) {
-  int nbr = 2 * (T->d.mx + T->d.my) * T->e;
+  int nbr = 2 * (T->d.mx + T->d.my) * edge_pts(&T->d);
   double *bxy = xmalloc(sizeof(double) * 2 * nbr);
   ora_nodes(&T->d, NULL, bxy);
   double tol = 1e-10 * fmax(T->d.x1 - T->d.x0, T->d.y1 - T->d.y0);
@@ -796,11 +960,12 @@ int ora_tree_leaf(void *h, int pub, cplx *Psi, cplx *Y, cplx *Gam) {
 }
 
 /* Algorithm 2 for nrhs right-hand sides.
- * s: [nrhs][leaves][(p-2)^2], t: [nrhs][2 (mx + my) (p-2)], u: [nrhs][leaves][p^2-4]. */
+ * s: [nrhs][leaves][(p-2)^2], t: [nrhs][2 (mx + my) q] (q = edge_pts),
+ * u: [nrhs][leaves][p^2-4]. */
 int ora_solve(void *h, const cplx *s, const cplx *t, cplx *u, int nrhs, int nthreads) {
   ora_tree *T = h;
   int L = T->L, nl = 1 << L, n = T->n, nb = T->nb, ni = T->ni;
-  int nbr = 2 * (T->d.mx + T->d.my) * T->e;
+  int nbr = 2 * (T->d.mx + T->d.my) * edge_pts(&T->d);
   int *perm = root_order(T);
   if (nthreads < 1) nthreads = 1;
   cplx **hv = xmalloc(sizeof(cplx *) * (size_t)(T->nboxes + 1));
@@ -941,6 +1106,8 @@ void ora_free(void *h) {
     free(b->Phib);
   }
   free(T->box);
+  free(T->Pm);
+  free(T->Qm);
   free(T);
 }
 
@@ -948,10 +1115,128 @@ void ora_free(void *h) {
 /* brute force: the global collocation system, dense LU                */
 /* ------------------------------------------------------------------ */
 
+/* The global system with boundary data on q Gauss nodes per leaf edge.
+ * Unknowns per leaf: its nodal values u (p^2-4) and its incoming data t_G on
+ * the Gauss nodes of its edges (4 q).  Equations per leaf: the impedance rows
+ * F u = Qh t_G on its Chebyshev edge nodes, its interior collocation rows,
+ * and per Gauss node either t_G = t (outer boundary) or, with the coincident
+ * Gauss node of the neighbouring leaf, t_G(here) = -(Ph G u)(there), the
+ * condition t3a = -g3b / t3b = -g3a of Sec. 2.2 on the Gauss nodes. */
+static int brute_gauss(const ora_desc *d, const double *c, const cplx *s, const cplx *t, cplx *u) {
+  int p = d->p, e = p - 2, n = p * p - 4, nbc = 4 * e, ni = e * e, q = d->gauss_q, nbq = 4 * q;
+  int nl = d->mx * d->my, nu = n + nbq, N = nl * nu, nbr = 2 * (d->mx + d->my) * q;
+  double tol = 1e-10 * fmax(d->x1 - d->x0, d->y1 - d->y0);
+  leaf_geom g;
+  leaf_geom_init(&g, p, (d->x1 - d->x0) / d->mx, (d->y1 - d->y0) / d->my);
+  cplx eta = d->eta_re + I * d->eta_im;
+  double *Pm = xmalloc(sizeof(double) * q * e), *Qm = xmalloc(sizeof(double) * e * q);
+  edge_interp(p, q, Pm, Qm);
+  double *zg = xmalloc(sizeof(double) * q);
+  ora_gauss_nodes(q, zg);
+  double *bxy = xmalloc(sizeof(double) * 2 * nbr);
+  ora_nodes(d, NULL, bxy);
+  double *gxy = xmalloc(sizeof(double) * 2 * (size_t)nl * nbq); /* Gauss nodes of every leaf */
+  int dir[64], L = merge_dirs(log2i(d->mx), log2i(d->my), 0, dir);
+  for (int l = 0; l < nl; l++) {
+    int col, row;
+    leaf_decode(l, dir, L, &col, &row);
+    leaf_gauss_xy(d, col, row, q, zg, gxy + 2 * (size_t)l * nbq);
+  }
+  cplx *Bl = xmalloc(sizeof(cplx) * (size_t)nl * n * n);
+  cplx *Fl = xmalloc(sizeof(cplx) * (size_t)nl * nbc * n);
+  cplx *Gl = xmalloc(sizeof(cplx) * (size_t)nl * nbc * n);
+  cplx *Psi = xmalloc(sizeof(cplx) * (size_t)n * nbc), *Y = xmalloc(sizeof(cplx) * (size_t)n * ni);
+  cplx *R = xmalloc(sizeof(cplx) * (size_t)nbc * nbc), *Gam = xmalloc(sizeof(cplx) * (size_t)nbc * ni);
+  for (int l = 0; l < nl; l++)
+    leaf_ops(&g, d->kappa, eta, c + (size_t)l * ni, Psi, Y, R, Gam, Bl + (size_t)l * n * n,
+             Fl + (size_t)l * nbc * n, Gl + (size_t)l * nbc * n);
+  cplx *A = xmalloc(sizeof(cplx) * (size_t)N * N);
+  cplx *rhs = xmalloc(sizeof(cplx) * (size_t)N);
+  for (int l = 0; l < nl; l++) {
+    size_t base = (size_t)l * nu, tbase = base + n;
+    const cplx *F = Fl + (size_t)l * nbc * n, *B = Bl + (size_t)l * n * n;
+    /* F u - Qh t_G = 0 on the Chebyshev edge nodes */
+    for (int k = 0; k < nbc; k++) {
+      size_t row = base + k;
+      int side = k / e, j = k % e;
+      for (int jj = 0; jj < n; jj++) A[row * N + base + jj] = F[(size_t)k * n + jj];
+      for (int a = 0; a < q; a++) A[row * N + tbase + side * q + a] = -Qm[j * q + a];
+      rhs[row] = 0.0;
+    }
+    /* interior collocation rows */
+    for (int i = 0; i < ni; i++) {
+      size_t row = base + nbc + i;
+      for (int jj = 0; jj < n; jj++) A[row * N + base + jj] = B[(size_t)(nbc + i) * n + jj];
+      rhs[row] = s[(size_t)l * ni + i];
+    }
+    /* one row per Gauss node of this leaf */
+    for (int k = 0; k < nbq; k++) {
+      size_t row = tbase + k;
+      const double *pt = &gxy[2 * ((size_t)l * nbq + k)];
+      A[row * N + tbase + k] = 1.0;
+      int outer = -1;
+      for (int qb = 0; qb < nbr; qb++)
+        if (same_point(pt, &bxy[2 * qb], tol)) {
+          outer = qb;
+          break;
+        }
+      if (outer >= 0) {
+        rhs[row] = t[outer];
+        continue;
+      }
+      int found = 0;
+      for (int l2 = 0; l2 < nl && !found; l2++) {
+        if (l2 == l) continue;
+        for (int k2 = 0; k2 < nbq; k2++)
+          if (same_point(pt, &gxy[2 * ((size_t)l2 * nbq + k2)], tol)) {
+            /* + (Ph G u)(k2) of the neighbour: row k2 of Ph is Pm's row a2 on side2 */
+            int side2 = k2 / q, a2 = k2 % q;
+            const cplx *G2 = Gl + (size_t)l2 * nbc * n;
+            for (int j = 0; j < e; j++) {
+              double w = Pm[a2 * e + j];
+              for (int jj = 0; jj < n; jj++)
+                A[row * N + (size_t)l2 * nu + jj] += w * G2[(size_t)(side2 * e + j) * n + jj];
+            }
+            found = 1;
+            break;
+          }
+      }
+      rhs[row] = 0.0;
+      if (!found) {
+        fprintf(stderr, "hps_oracle: unmatched Gauss node\n");
+        abort();
+      }
+    }
+  }
+  int *piv = xmalloc(sizeof(int) * (size_t)N);
+  int bad = lu_factor(N, A, piv);
+  if (!bad) lu_solve(N, A, piv, rhs);
+  for (int l = 0; l < nl; l++) memcpy(u + (size_t)l * n, rhs + (size_t)l * nu, sizeof(cplx) * n);
+  free(piv);
+  free(A);
+  free(rhs);
+  free(Bl);
+  free(Fl);
+  free(Gl);
+  free(Psi);
+  free(Y);
+  free(R);
+  free(Gam);
+  free(Pm);
+  free(Qm);
+  free(zg);
+  free(bxy);
+  free(gxy);
+  leaf_geom_free(&g);
+  return bad;
+}
+
 /* u: [leaves][p^2-4] for one right-hand side (s: [leaves][(p-2)^2],
- * t: [2 (mx + my) (p-2)]).  Returns 0, or nonzero when the system is singular. */
+ * t: [2 (mx + my) q], q = edge_pts).  Returns 0, or nonzero when the system
+ * is singular. */
 int ora_brute(const ora_desc *d, const double *c, const cplx *s, const cplx *t, cplx *u) {
   if (check_desc(d)) return -1;
+  if (d->gauss_q) return brute_gauss(d, c, s, t, u);
   int p = d->p, e = p - 2, n = p * p - 4, nb = 4 * e, ni = e * e;
   int nl = d->mx * d->my, N = nl * n, nbr = 2 * (d->mx + d->my) * e;
   double tol = 1e-10 * fmax(d->x1 - d->x0, d->y1 - d->y0);

@@ -52,11 +52,12 @@ def uniform(seed: int, count: int, offset: int = 0) -> np.ndarray:
 _NORMALS = np.array([[0.0, -1.0], [1.0, 0.0], [0.0, 1.0], [-1.0, 0.0]])
 
 
-def boundary_sides(m: int, p: int, my: Optional[int] = None) -> np.ndarray:
+def boundary_sides(m: int, p: int, my: Optional[int] = None, per_edge: Optional[int] = None) -> np.ndarray:
     """Side index (0 S, 1 E, 2 N, 3 W) of each public outer-boundary node of
-    an m x my leaf grid (my = m unless given)."""
+    an m x my leaf grid (my = m unless given), with per_edge nodes on each
+    leaf edge (p - 2 unless given)."""
     my = m if not my else my
-    e = p - 2
+    e = per_edge or p - 2
     return np.concatenate([np.full(m * e, 0), np.full(my * e, 1), np.full(m * e, 2), np.full(my * e, 3)])
 
 
@@ -88,7 +89,8 @@ class Workload:
         yi = leaf_xy[:, nb:, 1]
         c = np.asarray(self.c(xi, yi), dtype=np.float64)
         s = np.asarray(self.s(xi, yi), dtype=np.complex128)
-        side = boundary_sides(self.m, self.p, self.my)
+        my = self.my or self.m
+        side = boundary_sides(self.m, self.p, self.my, per_edge=len(bdry_xy) // (2 * (self.m + my)))
         t = np.asarray(self.t(bdry_xy[:, 0], bdry_xy[:, 1], side), dtype=np.complex128)
         return c, s, t
 
@@ -204,8 +206,8 @@ def random_medium_sources(m: int, p: int = 16, kappa: float = 300.0, eta: Option
 
 def polynomial_solution(m: int, p: int, kappa: float, eta: complex, seed: int = 7,
                         c: Optional[Callable] = None, domain=(0.0, 1.0, 0.0, 1.0),
-                        my: Optional[int] = None) -> Workload:
-    """Manufactured solution that is a polynomial of degree p-1 in x and in y.
+                        my: Optional[int] = None, deg: Optional[int] = None) -> Workload:
+    """Manufactured solution that is a polynomial of degree p-1 (or deg) in x and in y.
 
     u(x, y) = sum_{a,b <= p-1} C_ab X^a Y^b with X, Y the coordinates scaled to
     [-1, 1] over the domain and seeded complex coefficients that decay with
@@ -214,7 +216,7 @@ def polynomial_solution(m: int, p: int, kappa: float, eta: complex, seed: int = 
     condition of the discretisation holds exactly for u at the nodes.
     """
     x0, x1, y0, y1 = domain
-    deg = p - 1
+    deg = p - 1 if deg is None else deg
     r = uniform(seed, 2 * (deg + 1) ** 2, offset=1 << 24)
     C = (r[0::2] - 0.5 + 1j * (r[1::2] - 0.5)).reshape(deg + 1, deg + 1)
     decay = np.array([[0.7 ** (a + b) for b in range(deg + 1)] for a in range(deg + 1)])
