@@ -28,6 +28,20 @@
  *     collocation rows, the impedance rows F u = t on the outer boundary and,
  *     for each pair of coincident nodes on a shared edge, the two conditions
  *     t3a = -g3b and g3a = -t3b of Sec. 2.2, solved by dense LU.
+ *   - Gauss-Legendre interfaces (gauss_q = q > 0), the variant of the earlier
+ *     ItI work the paper cites in Sec. 1 (boundary operators represented on
+ *     edges through interpolation): every leaf edge carries its boundary data
+ *     on q Gauss-Legendre nodes; incoming data t_G enter the leaf as Qm t_G
+ *     on its corner-free Chebyshev edge nodes, outgoing data leave as Pm g
+ *     (Qm, Pm: Lagrange interpolation between the two node sets), so the leaf
+ *     operators become Psi Qh, Ph R Qh, Ph Gamma (Qh, Ph block-diagonal over
+ *     the four edges), and the merges and Algorithm 2 run unchanged on the
+ *     Gauss nodes.  Its brute force is the global system of that
+ *     discretisation (unknowns: nodal values and incoming Gauss data of every
+ *     leaf).  For q >= p-2 the solution equals the Chebyshev-edge one (the
+ *     data stay polynomials of degree p-3 per edge); for q < p-2 it is a
+ *     coarser interface space.  The Gauss nodes are the roots of P_q found by
+ *     bisection between sign changes on a fine grid.
  *
  * Readings of the paper taken here (the paper is silent or garbled there):
  *   - Chebyshev nodes increase: x_j = -cos(j pi/(p-1)) mapped to the leaf
