@@ -34,9 +34,10 @@
  * the (p-2)^2 interior nodes run row by row, x fastest.  Nodes on an edge
  * shared by two leaves appear once per leaf.
  *
- * Outer boundary: 2 (mx + my) (p-2) nodes ordered [south, east, north, west]
+ * Outer boundary: 2 (mx + my) qe nodes ordered [south, east, north, west]
  * (mx, my, mx, my leaf edges), each side in increasing coordinate (the
- * concatenation of the leaves' edges).
+ * concatenation of the leaves' edges); qe = p-2 corner-free Chebyshev nodes
+ * per leaf edge, or q Gauss-Legendre nodes (see hps_desc.q).
  *
  * Memory: every array argument may be host or device memory; the library
  * asks the CUDA runtime which.  Device arrays are used in place; host arrays
@@ -84,9 +85,21 @@ typedef struct {
   int mx, my;            /* leaves along x and along y: powers of two, 1 .. 1024,
                             mx my <= 2^20 */
   int p;                 /* Chebyshev nodes per leaf side (the paper's n_c), 4 .. 32 */
-  int q;                 /* points per leaf edge for boundary data: 0 or p-2 (the
-                            corner-free Chebyshev edge nodes; other values are
-                            HPS_EINVAL) */
+  int q;                 /* points per leaf edge for boundary data.  0 or p-2: the
+                            corner-free Chebyshev edge nodes of Sec. 2.1 (the paper's
+                            scheme).  1 .. 64 otherwise: q Gauss-Legendre nodes per
+                            leaf edge, the interface of the earlier ItI work the paper
+                            cites in Sec. 1: each leaf's incoming data reach its
+                            Chebyshev edge nodes through the degree q-1 interpolant
+                            of the Gauss values, and its outgoing data leave as the
+                            Chebyshev interpolant evaluated at the Gauss nodes, so
+                            the merges and the solve run on the Gauss nodes.  For
+                            q > p-2 the solution is the Chebyshev scheme's (the data
+                            stay polynomials of degree p-3 per edge); for q < p-2 the
+                            interface space is coarser.  Then t and the root R are on
+                            the Gauss nodes (hps_nodes lists them), HPS_MIXED is
+                            HPS_ENOTSUP and a batch shares one q.  Other values:
+                            HPS_EINVAL. */
   double kappa;          /* wave number, > 0 */
   double eta_re, eta_im; /* impedance parameter eta, Re(eta) != 0 */
   int precision;         /* HPS_FP64: complex128 throughout.
@@ -136,7 +149,7 @@ typedef struct {
 
 /* Node coordinates (host helper, no device work; Sec. 2.1 grid).
  *   leaf_xy: [leaves][p^2-4][2] (x, y) of every leaf node, or NULL
- *   bdry_xy: [2 (mx + my) (p-2)][2] outer boundary nodes, or NULL
+ *   bdry_xy: [2 (mx + my) qe][2] outer boundary nodes (see hps_desc.q), or NULL
  * Both are host memory.  Returns HPS_EINVAL for an invalid descriptor. */
 int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy);
 
@@ -201,7 +214,7 @@ int hps_rebuild(int nh, hps_handle *const *hs, const double *const *c, void *str
  * operators with the interface residuals injected into h3 at the merge whose
  * interface holds them.
  *   s: [nrhs][leaves][(p-2)^2] complex body load at the interior nodes
- *   t: [nrhs][2 (mx + my) (p-2)] complex impedance data du/dnu + i eta u on the
+ *   t: [nrhs][2 (mx + my) qe] complex impedance data du/dnu + i eta u on the
  *      outer boundary
  *   u: [nrhs][leaves][p^2-4] complex solution at every leaf node (written)
  * nrhs == 0 does nothing and returns HPS_OK.  Returns HPS_EINVAL (NULL
@@ -273,7 +286,9 @@ int hps_solve_noalloc(hps_handle *h, const double *s, const double *t, double *u
                       void *stream);
 
 /* The root ItI operator R (Definition of the ItI map; R f = g on the outer
- * boundary) in the outer-boundary order above.
+ * boundary) in the outer-boundary order above.  With Gauss-Legendre boundary
+ * data (hps_desc.q != p-2) R is on those nodes and gauss_basis must be 1
+ * (0 is HPS_EINVAL).
  *   R: [nb][nb] complex with nb = 2 (mx + my) (p-2), row-major (R[i][j] maps incoming data
  *      at node j to outgoing data at node i); host or device memory
  *   gauss_basis: 0 = R on the corner-free Chebyshev edge nodes (the basis the

@@ -66,6 +66,10 @@ struct Level {
 
 struct Plan {
   int m, my, p, e, n, nb, ni, L, leaves, nbdry;  // m: leaves along x, my: along y
+  // boundary data points per leaf edge: e (the corner-free Chebyshev nodes),
+  // or q Gauss-Legendre nodes (gauss); nbi = 4 qe per leaf
+  int qe, nbi;
+  bool gauss;
   bool mixed;                   // HPS_MIXED
   int leaf_f32;                 // leaf operators in complex64
   bool leaf_lu;                 // leaf operators as LU factors (else B^{-1})
@@ -104,6 +108,12 @@ struct hps_handle {
   hps_info_t info;
   Shared *sh = nullptr;
   void *X = nullptr, *GX = nullptr;  // leaf operators (complex64 when plan.leaf_f32)
+  // the leaves' interface operators [R | Gamma] on the boundary data points
+  // (nbi x (nbi + ni) each; GX itself unless plan.gauss) and, with
+  // plan.gauss, the edge interpolation from the Gauss to the Chebyshev nodes
+  void *GXi = nullptr;
+  long long gxi_ld = 0, gxi_stride = 0;
+  const double2 *d_Qcm = nullptr;
   int *lu_perm = nullptr;            // leaf_lu: row k of P D B is row lu_perm[k] of B
   double *lu_dsc = nullptr;          // leaf_lu: d of that row
   double2 *Rroot = nullptr;
@@ -135,7 +145,7 @@ int check_desc(const hps_desc *d) {
   if (d->my < 1 || d->my > 1024 || (d->my & (d->my - 1))) return HPS_EINVAL;
   if ((long long)d->mx * d->my > (1 << 20)) return HPS_EINVAL;
   if (d->p < 4 || d->p > 32) return HPS_EINVAL;
-  if (d->q != 0 && d->q != d->p - 2) return HPS_EINVAL;
+  if (d->q != 0 && d->q != d->p - 2 && (d->q < 1 || d->q > 64)) return HPS_EINVAL;
   if (!(d->kappa > 0.0) || !std::isfinite(d->kappa)) return HPS_EINVAL;
   if (d->eta_re == 0.0 || !std::isfinite(d->eta_re) || !std::isfinite(d->eta_im)) return HPS_EINVAL;
   if (d->precision != HPS_FP64 && d->precision != HPS_MIXED) return HPS_EINVAL;
@@ -232,21 +242,25 @@ void make_plan(const hps_desc &d, Plan &pl) {
   pl.n = d.p * d.p - 4;
   pl.nb = 4 * pl.e;
   pl.ni = pl.e * pl.e;
+  pl.gauss = (d.q != 0 && d.q != pl.e);
+  pl.qe = pl.gauss ? d.q : pl.e;
+  pl.nbi = 4 * pl.qe;
   const std::vector<int> dirs = merge_dirs(d.mx, d.my);
   pl.L = (int)dirs.size();
   pl.leaves = d.mx * d.my;
-  pl.nbdry = 2 * (d.mx + d.my) * pl.e;
+  pl.nbdry = 2 * (d.mx + d.my) * pl.qe;
   pl.mixed = (d.precision == HPS_MIXED);
   pl.leaf_f32 = pl.mixed ? 1 : 0;
   pl.leaf_lu = (d.leaf_form == HPS_LEAF_LU);
   pl.refine_steps = d.refine_steps == 0 ? 2 : (d.refine_steps < 0 ? 0 : d.refine_steps);
   pl.oz = (d.fp64_native == 0);
   const int top = std::min(pl.L, d.fp64_levels == 0 ? 4 : d.fp64_levels);
-  const int e = pl.e;
-  std::vector<Canon> cur(pl.nb);
+  // the interface bookkeeping runs on the boundary data points of the edges
+  const int e = pl.qe;
+  std::vector<Canon> cur(pl.nbi);
   // (leaf within the box, node within the leaf) of every boundary position
-  std::vector<std::pair<int, int>> at(pl.nb);
-  for (int k = 0; k < pl.nb; k++) {
+  std::vector<std::pair<int, int>> at(pl.nbi);
+  for (int k = 0; k < pl.nbi; k++) {
     cur[k] = {k / e, k % e};
     at[k] = {0, k};
   }
@@ -331,7 +345,7 @@ void make_plan(const hps_desc &d, Plan &pl) {
     const int side_off[4] = {0, d.mx * e, (d.mx + d.my) * e, (2 * d.mx + d.my) * e};
     const int q = side_off[cur[pos].side] + cur[pos].off;
     pl.root_src[pos] = q;
-    pl.outer[q] = at[pos].first * pl.nb + at[pos].second;
+    pl.outer[q] = at[pos].first * pl.nbi + at[pos].second;
   }
 }
 
@@ -416,10 +430,16 @@ void fill_info(const Plan &pl, hps_info_t &in) {
   // the G-row solve (nb n^2/2), with n pivots and row scales kept
   long long bf = pl.leaf_lu ? (long long)pl.leaves * 8 * (n * n * n / 3 + nb * n * n)
                             : (long long)pl.leaves * 8 * (n * n * n + nb * n * pl.p);
-  long long sf = (long long)pl.leaves * 8 * (nb * ni + n * n);
+  const long long nbi = pl.nbi, qe = pl.qe, e = pl.e;
+  long long sf = (long long)pl.leaves * 8 * (nbi * ni + n * n + (pl.gauss ? nb * qe : 0));
   const long long lu_aux = pl.leaf_lu ? (long long)pl.leaves * n * (4 + 8) : 0;
   long long ob = (long long)pl.leaves * cplx_bytes(n * n + nb * n, pl.leaf_f32) + lu_aux;
-  long long sb = (long long)pl.leaves * cplx_bytes(n * n + nb * ni, pl.leaf_f32) + lu_aux;
+  long long sb = (long long)pl.leaves * cplx_bytes(n * n + nbi * ni, pl.leaf_f32) + lu_aux;
+  if (pl.gauss) {
+    // the interface operators [Ph R Qh | Ph Gamma] and the products that form them
+    ob += (long long)pl.leaves * cplx_bytes(nbi * (nbi + ni));
+    bf += (long long)pl.leaves * 8 * (nbi * e * n + nbi * nb * qe);
+  }
   for (const Level &L : pl.lv) {
     long long n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, P = L.P;
     bf += P * 8 * (2 * n3 * n3 * n3 + n3 * n3 * n1 + 2 * n3 * n3 * nt + (n1 + n2) * n3 * nt);
@@ -434,6 +454,10 @@ void fill_info(const Plan &pl, hps_info_t &in) {
   in.solve_bytes = sb;
   in.build_launches = pl.lv.empty() ? 2 : 1 + 7 * (int)pl.lv.size();
   in.solve_launches = 3 + 6 * (int)pl.lv.size();
+  if (pl.gauss) {
+    in.build_launches += 5 * (int)((pl.leaves + 2047) / 2048);  // the interface operators, per pass
+    in.solve_launches += 1;                                     // t = Qh t_G
+  }
   if (pl.mixed) {
     int conv = 0;
     for (size_t j = 0; j < pl.lv.size(); j++)
@@ -679,6 +703,7 @@ struct SolveWs {
   size_t osd = 0, otd = 0, ofu = 0, ogu = 0, oja = 0, ojb = 0, od = 0;
   // products on the tensor cores (wide right-hand-side blocks): digit planes
   size_t ooz = 0, oz_bytes = 0;
+  size_t otc = 0;
   // scratch of the skinny products (up to 8 right-hand sides): counters at
   // offset 0 of every workspace (zeroed when it is allocated, left zero by
   // the kernel), partial sums after them
@@ -698,7 +723,7 @@ static int lu_split(int n) {
 static void solve_products(const Plan &pl, std::vector<std::array<int, 3>> &out) {
   out.clear();
   if (!pl.leaf_f32) {
-    out.push_back({pl.nb, pl.ni, pl.leaves});
+    out.push_back({pl.nbi, pl.ni, pl.leaves});
     if (!pl.leaf_lu) {
       out.push_back({pl.n, pl.n, pl.leaves});
     } else if (const int b1 = lu_split(pl.n)) {
@@ -727,8 +752,11 @@ static void solve_ws_layout(const Plan &pl, int R, SolveWs &w, bool allow_oz = t
     off = align256(off + sizeof(double2) * (size_t)count);
     return o;
   };
-  w.oh[0] = take((long long)R * pl.leaves * pl.nb);
-  w.ot[0] = take((long long)R * pl.leaves * pl.nb);
+  w.oh[0] = take((long long)R * pl.leaves * pl.nbi);
+  w.ot[0] = take((long long)R * pl.leaves * pl.nbi);
+  // boundary data on Gauss nodes: the leaves' incoming data on their
+  // Chebyshev edge nodes (Qh t) before the leaf step
+  if (pl.gauss) w.otc = take((long long)R * pl.leaves * pl.nb);
   long long vmax = 1;
   for (size_t j = 0; j < pl.lv.size(); j++) {
     const Level &L = pl.lv[j];
@@ -832,9 +860,11 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
   };
 
   // ---- upward pass ----
-  // leaves: h = Gamma s  (Gamma = GX[:, nb:])
-  GemmDesc g = gemm(nb, R, ni, nl, F(elem(h->GX, (long long)nb * nb, lf), nb, (long long)n * nb, lf),
-                    mat(s, (long long)nl * ni, ni), mat(W(oh[0]), (long long)nl * nb, nb));
+  // leaves: h = Gamma s  (Gamma = GX[:, nb:], on the boundary data points: nbi rows)
+  const int nbi = pl.nbi;
+  const int gf = pl.gauss ? 0 : lf;
+  GemmDesc g = gemm(nbi, R, ni, nl, F(elem(h->GXi, h->gxi_ld * nbi, gf), h->gxi_ld, h->gxi_stride, gf),
+                    mat(s, (long long)nl * ni, ni), mat(W(oh[0]), (long long)nl * nbi, nbi));
   g.cf32 = lf;
   if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
   for (size_t j = 0; j < pl.lv.size(); j++) {
@@ -892,7 +922,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
 
   // ---- downward pass ----
   const size_t top = pl.lv.size();
-  const int ntop = top ? pl.lv.back().nt : nb;
+  const int ntop = top ? pl.lv.back().nt : nbi;
   {
     // root incoming data: public [S, E, N, W] order -> the root's [I1, I2] order
     CopyBatch cb;
@@ -925,7 +955,17 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     cb.d[1] = copy(n2, R, P, mat(tp + n1, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I2));
     CK(hps::launch_copy(cb, st));
   }
-  // leaves: u = Psi t + Y s = B^{-1} [t; s]
+  // leaves: u = Psi t + Y s = B^{-1} [t; s], t on the leaves' Chebyshev edge
+  // nodes: with boundary data on Gauss nodes, t = Qh t_G first (every
+  // (leaf, edge) pair one product with the e x qe table)
+  const double2 *tl = W(ot[0]);
+  if (pl.gauss) {
+    const int qe = pl.qe, e = pl.e;
+    GemmDesc gq = gemm(e, R, qe, 4 * nl, mat(h->d_Qcm, e, 0), mat(W(ot[0]), (long long)nl * nbi, qe),
+                       mat(W(ws.otc), (long long)nl * nb, e));
+    if (int rc = solve_gemm(&gq, 1, st, wb, ws, false, h->d_status)) return rc;
+    tl = W(ws.otc);
+  }
   const int b1 = lu_split(n);
   if (pl.leaf_lu && !lf && R >= 32 && b1 && ws.oz_bytes && oz_shape(n - b1, R, b1, nl, 0, pl.oz)) {
     // wide solve: each leaf's sweeps in two diagonal blocks, the products
@@ -934,7 +974,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     //   y1 = L11^-1 (P D b)_1;  (P D b)_2 -= L21 y1;  y2 = L22^-1 (P D b)_2;
     //   x2 = U22^-1 y2;  y1 -= U12 x2;  x1 = U11^-1 y1
     const long long ldu = (long long)nl * n, s2 = (long long)n * n;
-    CK(hps::launch_lu_solve_part(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, W(ot[0]), (long long)nl * nb, nb, s,
+    CK(hps::launch_lu_solve_part(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, tl, (long long)nl * nb, nb, s,
                                  (long long)nl * ni, ni, u, ldu, n, false, 0, b1, true, true, false, st));
     GemmDesc gl = gemm(n - b1, R, b1, nl, F(elem(h->X, b1, 0), n, s2, 0), mat(u, ldu, n), mat(u + b1, ldu, n));
     gl.alpha = make_double2(-1.0, 0.0);
@@ -952,10 +992,10 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     CK(hps::launch_lu_solve_part(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, nullptr, 0, 0, nullptr, 0, 0, u, ldu,
                                  n, false, 0, b1, false, false, true, st));
   } else if (pl.leaf_lu) {
-    CK(hps::launch_lu_solve(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, W(ot[0]), (long long)nl * nb, nb, s,
+    CK(hps::launch_lu_solve(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, tl, (long long)nl * nb, nb, s,
                             (long long)nl * ni, ni, u, (long long)nl * n, n, lf != 0, st));
   } else {
-    g = gemm(n, R, n, nl, F(h->X, n, (long long)n * n, lf), mat(W(ot[0]), (long long)nl * nb, nb),
+    g = gemm(n, R, n, nl, F(h->X, n, (long long)n * n, lf), mat(tl, (long long)nl * nb, nb),
              mat(u, (long long)nl * n, n));
     g.B2 = mat(s, (long long)nl * ni, ni);
     g.ksplit = nb;
@@ -1164,6 +1204,9 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy) {
     }
   }
   if (bdry_xy) {
+    // q Gauss-Legendre nodes per leaf edge when q is neither 0 nor p - 2
+    const bool gauss = desc->q != 0 && desc->q != e;
+    const std::vector<double> zg = gauss ? gauss_legendre_nodes(desc->q) : std::vector<double>();
     size_t q = 0;
     for (int side = 0; side < 4; side++) {
       const bool horiz = (side == 0 || side == 2);
@@ -1172,9 +1215,11 @@ int hps_nodes(const hps_desc *desc, double *leaf_xy, double *bdry_xy) {
           cheb(p, desc->x0 + c * hx, desc->x0 + (c + 1) * hx, xs, D);
         else
           cheb(p, desc->y0 + c * hy, desc->y0 + (c + 1) * hy, ys, D);
-        for (int k = 1; k <= e; k++, q++) {
-          double x = horiz ? xs[k] : (side == 1 ? desc->x1 : desc->x0);
-          double y = horiz ? (side == 0 ? desc->y0 : desc->y1) : ys[k];
+        const double lo = horiz ? desc->x0 + c * hx : desc->y0 + c * hy, len = horiz ? hx : hy;
+        for (int k = 1; k <= (gauss ? desc->q : e); k++, q++) {
+          const double along = gauss ? lo + 0.5 * (zg[k - 1] + 1.0) * len : (horiz ? xs[k] : ys[k]);
+          double x = horiz ? along : (side == 1 ? desc->x1 : desc->x0);
+          double y = horiz ? (side == 0 ? desc->y0 : desc->y1) : along;
           bdry_xy[2 * q] = x;
           bdry_xy[2 * q + 1] = y;
         }
@@ -1341,6 +1386,17 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   const size_t oGX = take((size_t)(esl * NL * n * nb));
   const size_t oPerm = P0.leaf_lu ? take(sizeof(int) * (size_t)NL * n) : 0;
   const size_t oDsc = P0.leaf_lu ? take(sizeof(double) * (size_t)NL * n) : 0;
+  // boundary data on Gauss-Legendre nodes: the leaves' interface operators
+  // [Ph R Qh | Ph Gamma] and the edge interpolation tables P (qe x e) and
+  // Q (e x qe), column-major
+  const bool gauss = P0.gauss;
+  const int nbi = P0.nbi, qe = P0.qe, e0 = P0.e;
+  const size_t oGXi = gauss ? take(16ULL * NL * nbi * (nbi + ni)) : 0;
+  const size_t oIP = gauss ? take(16ULL * 2 * qe * e0) : 0;
+  const size_t gxi_off = gauss ? oGXi : oGX;
+  const long long gxi_ld = gauss ? nbi : nb, gxi_stride = gauss ? (long long)nbi * (nbi + ni) : (long long)n * nb;
+  const int gxi_f32 = gauss ? 0 : lf;
+  const long long gxi_es = gauss ? 16 : esl;
   for (int j = 0; j < Lmax; j++) {
     const Level &S = P0.lv[j];
     const long long n1 = S.n1, n2 = S.n2, n3 = S.n3, nt = S.nt;
@@ -1353,7 +1409,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   // problems with a single leaf: the root is the leaf's R
   int k1 = K;
   while (k1 > 0 && hs[k1 - 1]->plan.L == 0) k1--;
-  const size_t oRoot1 = take(16ULL * (K - k1) * nb * nb);
+  const size_t oRoot1 = take(16ULL * (K - k1) * nbi * nbi);
   const size_t tab_bytes = sizeof(double) * 4 * p * p + sizeof(int) * (n + p * p);
   std::vector<size_t> oTab(K), oC(K, 0);
   for (int k = 0; k < K; k++) {
@@ -1409,6 +1465,10 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     Plan &pl = h->plan;
     h->X = base + oX + esl * leaf0[k] * n * n;
     h->GX = base + oGX + esl * leaf0[k] * n * nb;
+    h->GXi = base + gxi_off + gxi_es * leaf0[k] * gxi_stride;
+    h->gxi_ld = gxi_ld;
+    h->gxi_stride = gxi_stride;
+    if (gauss) h->d_Qcm = (const double2 *)(base + oIP) + (size_t)qe * e0;
     if (P0.leaf_lu) {
       h->lu_perm = (int *)(base + oPerm) + leaf0[k] * n;
       h->lu_dsc = (double *)(base + oDsc) + leaf0[k] * n;
@@ -1431,7 +1491,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
       L.d_pairs = d_ints + imap[5 * j + 4];
       if (j == pl.L - 1) h->Rroot = (double2 *)(base + r->root + 16 * d * nt * nt);
     }
-    if (pl.L == 0) h->Rroot = (double2 *)(base + oRoot1 + 16ULL * (k - k1) * nb * nb);
+    if (pl.L == 0) h->Rroot = (double2 *)(base + oRoot1 + 16ULL * (k - k1) * nbi * nbi);
     h->tables = base + oTab[k];
     h->c_dev = (double *)(base + oC[k]);
     h->d_ints = d_ints;
@@ -1476,6 +1536,23 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   }
   CK(cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(d_status, 0, sizeof(unsigned int), st));
+  if (gauss) {
+    // P: the Chebyshev-edge interpolant at the Gauss nodes; Q: the
+    // Gauss-node interpolant at the Chebyshev edge nodes (reference edge)
+    std::vector<double> xc(e0);
+    for (int j = 0; j < e0; j++) xc[j] = -std::cos(std::acos(-1.0) * (j + 1) / (p - 1));
+    const std::vector<double> zg = gauss_legendre_nodes(qe);
+    std::vector<double2> Prm((size_t)qe * e0), Qrm((size_t)e0 * qe), tab2(2 * (size_t)qe * e0);
+    lagrange_matrix(xc, zg, Prm.data());  // row-major qe x e0
+    lagrange_matrix(zg, xc, Qrm.data());  // row-major e0 x qe
+    for (int a = 0; a < qe; a++)
+      for (int j = 0; j < e0; j++) {
+        tab2[(size_t)a + (size_t)j * qe] = Prm[(size_t)a * e0 + j];                 // P column-major
+        tab2[(size_t)qe * e0 + j + (size_t)a * e0] = Qrm[(size_t)j * qe + a];       // Q column-major
+      }
+    // (pageable host memory: the copy has taken the table when it returns)
+    CK(cudaMemcpyAsync(base + oIP, tab2.data(), sizeof(double2) * tab2.size(), cudaMemcpyHostToDevice, st));
+  }
 
   // ---- c into the arena (the leaf kernel and the mixed path's residual read
   // it there; hps_rebuild replaces it) ----
@@ -1525,17 +1602,53 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
                             lf != 0, st));
       launches++;
     }
+    if (gauss) {
+      // boundary data on the Gauss nodes: the leaves' interface operators
+      // Ph [R | Gamma] then R_G = (Ph R) Qh, with Ph = diag(P, P, P, P),
+      // Qh = diag(Q, Q, Q, Q) over the edges [S, E, N, W]: per edge one
+      // product with the qe x e (or e x qe) table, batched over the leaves
+      const double2 *dP = (const double2 *)(base + oIP), *dQ = dP + (size_t)qe * e0;
+      const long long tch = 2048;  // leaves a pass (bounds the temporary)
+      double2 *T1 = nullptr;
+      CK(cudaMallocAsync((void **)&T1, 16ULL * std::min<long long>(tch, NL) * nbi * n, st));
+      for (long long l0 = 0; l0 < NL; l0 += tch) {
+        const int cnt = (int)std::min<long long>(tch, NL - l0);
+        const char *gx = base + oGX + 16 * l0 * n * nb;
+        char *gxi = base + oGXi + 16 * l0 * nbi * (nbi + ni);
+        GemmDesc gd[4];
+        for (int sd = 0; sd < 4; sd++) {  // T1 rows of edge sd = P GX rows of edge sd
+          gd[sd] = gemm(qe, n, e0, cnt, mat(dP, qe, 0), mat(gx + 16LL * sd * e0, nb, (long long)n * nb),
+                        mat(T1 + (size_t)sd * qe, nbi, (long long)nbi * n));
+        }
+        CK(hps::launch_gemm(gd, 2, st));
+        CK(hps::launch_gemm(gd + 2, 2, st));
+        for (int sd = 0; sd < 4; sd++) {  // R_G columns of edge sd = (Ph R) columns of edge sd times Q
+          gd[sd] = gemm(nbi, qe, e0, cnt, mat(T1 + (size_t)sd * e0 * nbi, nbi, (long long)nbi * n), mat(dQ, e0, 0),
+                        mat(gxi + 16LL * sd * qe * nbi, nbi, (long long)nbi * (nbi + ni)));
+        }
+        CK(hps::launch_gemm(gd, 2, st));
+        CK(hps::launch_gemm(gd + 2, 2, st));
+        CopyBatch cg;
+        cg.count = 1;  // Gamma_G = Ph Gamma
+        cg.d[0] = copy(nbi, ni, cnt, mat(T1 + (size_t)nb * nbi, nbi, (long long)nbi * n),
+                       mat(gxi + 16LL * nbi * nbi, nbi, (long long)nbi * (nbi + ni)));
+        CK(hps::launch_copy(cg, st));
+        launches += 5;
+      }
+      CK(cudaFreeAsync(T1, st));
+    }
     if (events) CK(cudaEventRecord(ev[1], st));
     if (lscr) CK(cudaFreeAsync(lscr, st));
     CK(cudaFreeAsync(lmeta, st));
 
     if (k1 < K) {
-      // single-leaf problems: the root R is the leaf's R = GX[:, :nb]
+      // single-leaf problems: the root R is the leaf's R = GX[:, :nb] (on the
+      // boundary data points)
       CopyBatch cb;
       cb.count = 1;
-      cb.d[0] = copy(nb, nb, K - k1, mat(base + oGX + esl * leaf0[k1] * n * nb, nb, (long long)n * nb, nullptr,
-                                         nullptr, lf),
-                     mat(base + oRoot1, nb, (long long)nb * nb));
+      cb.d[0] = copy(nbi, nbi, K - k1, mat(base + gxi_off + gxi_es * leaf0[k1] * gxi_stride, gxi_ld, gxi_stride,
+                                           nullptr, nullptr, gxi_f32),
+                     mat(base + oRoot1, nbi, (long long)nbi * nbi));
       CK(hps::launch_copy(cb, st));
       launches++;
     }
@@ -1625,8 +1738,8 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
         std::vector<ChildPiece> pcs = child_pieces(runs, j, r);
         auto piece_src = [&](const ChildPiece &c, int &pf) {
           if (c.run < 0) {
-            pf = lf;
-            return mat(base + oGX + esl * c.c0 * n * nb, nb, (long long)n * nb, nullptr, nullptr, lf);
+            pf = gxi_f32;
+            return mat(base + gxi_off + gxi_es * c.c0 * gxi_stride, gxi_ld, gxi_stride, nullptr, nullptr, gxi_f32);
           }
           const BuildRun &q = runs[j - 1][c.run];
           pf = q.f32;
@@ -1746,6 +1859,8 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
   if (st0) return st0;
   h->desc = *desc;
   if (h->desc.q == 0) h->desc.q = desc->p - 2;
+  // the mixed path's refinement residual is that of the Chebyshev-edge system
+  if (h->desc.q != desc->p - 2 && desc->precision == HPS_MIXED) return HPS_ENOTSUP;
   make_plan(h->desc, h->plan);
   h->leaf_cs = leaf_cluster(h->plan, h->plan.leaves);
   if (h->leaf_cs == 0) return HPS_ENOTSUP;
@@ -1827,7 +1942,8 @@ int hps_build_batch(int nprob, const hps_desc *descs, const double *const *c, vo
     if (!c[k]) return HPS_EINVAL;
     if (descs[k].p != descs[0].p || descs[k].precision != descs[0].precision ||
         descs[k].fp64_levels != descs[0].fp64_levels || descs[k].fp64_native != descs[0].fp64_native ||
-        descs[k].leaf_form != descs[0].leaf_form)
+        descs[k].leaf_form != descs[0].leaf_form ||
+        (descs[k].q ? descs[k].q : descs[k].p - 2) != (descs[0].q ? descs[0].q : descs[0].p - 2))
       return HPS_EINVAL;
     // host samples of c are checked here (device ones are not scanned)
     if (!is_device_ptr(c[k])) {
@@ -2321,6 +2437,8 @@ int hps_solve_noalloc(hps_handle *h, const double *s_, const double *t_, double 
 
 int hps_root_R(hps_handle *h, double *R, int gauss_basis, void *stream) {
   if (!h || !R || (gauss_basis != 0 && gauss_basis != 1)) return HPS_EINVAL;
+  // boundary data on q != p - 2 Gauss nodes: R exists only in that basis
+  if (h->plan.gauss && !gauss_basis) return HPS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const int nbr = h->plan.nbdry;
   const bool dev = is_device_ptr(R);
@@ -2331,7 +2449,7 @@ int hps_root_R(hps_handle *h, double *R, int gauss_basis, void *stream) {
     if (gst) return gst;
     dst = (double2 *)h->stage;
   }
-  const int nr = h->plan.lv.empty() ? h->plan.nb : h->plan.lv.back().nt;
+  const int nr = h->plan.lv.empty() ? h->plan.nbi : h->plan.lv.back().nt;
   // public row-major R[a][b] = root(src^-1 ...): with the root order map
   // root position -> public index, R_pub[pub(i)][pub(j)] = R_root(i, j).
   // As a column-major matrix R_pub^T: element (pub(j), pub(i)) = R_root(i, j),
@@ -2342,7 +2460,7 @@ int hps_root_R(hps_handle *h, double *R, int gauss_basis, void *stream) {
   cb.d[0] = copy(nr, nr, 1, mat(h->Rroot, nr, 0), mat(dst, nbr, 0, h->d_root_src, h->d_root_src));
   cb.d[0].trans = 1;
   CK(hps::launch_copy(cb, st));
-  if (gauss_basis)
+  if (gauss_basis && !h->plan.gauss)
     if (int rc = root_R_to_gauss(h->plan, dst, st)) return rc;
   if (!dev) {
     CK(cudaMemcpyAsync(R, dst, bytes, cudaMemcpyDeviceToHost, st));

@@ -123,14 +123,25 @@ class Problem:
     fp64_native: int = 0
     my: int = 0  # leaves along y (0: the same as m, the leaves along x)
     leaf_form: int = HPS_LEAF_LU  # leaf operators as LU factors, or HPS_LEAF_INVERSE: as B^-1
+    q: int = 0  # boundary data points per leaf edge: 0 / p-2 Chebyshev, else Gauss-Legendre
 
     @property
     def ny(self) -> int:
         return self.my or self.m
 
+    @property
+    def qe(self) -> int:
+        """Boundary data points per leaf edge."""
+        return self.q or self.p - 2
+
+    @property
+    def nbi(self) -> int:
+        """Boundary data points of a leaf."""
+        return 4 * self.qe
+
     def desc(self) -> hps_desc:
         eta = complex(self.eta)
-        return hps_desc(self.x0, self.x1, self.y0, self.y1, self.m, self.ny, self.p, self.p - 2,
+        return hps_desc(self.x0, self.x1, self.y0, self.y1, self.m, self.ny, self.p, self.qe,
                         float(self.kappa), eta.real, eta.imag, int(self.precision),
                         int(self.fp64_levels), int(self.refine_steps), int(self.fp64_native),
                         int(self.leaf_form))
@@ -153,7 +164,7 @@ class Problem:
 
     @property
     def nbdry(self) -> int:
-        return 2 * (self.m + self.ny) * (self.p - 2)
+        return 2 * (self.m + self.ny) * self.qe
 
 
 def _ptr(a) -> int:

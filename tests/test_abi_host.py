@@ -59,7 +59,7 @@ def _desc(**kw):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(mx=3, my=3), dict(mx=4, my=3), dict(mx=2048, my=2), dict(mx=0, my=0), dict(p=3), dict(p=33), dict(q=5),
+    dict(mx=3, my=3), dict(mx=4, my=3), dict(mx=2048, my=2), dict(mx=0, my=0), dict(p=3), dict(p=33), dict(q=65), dict(q=-2),
     dict(kappa=0.0), dict(kappa=-1.0), dict(eta_re=0.0, eta_im=1.0), dict(x1=0.0),
     dict(y1=-1.0), dict(precision=7), dict(precision=-1), dict(kappa=float("nan")),
     dict(precision=1, fp64_levels=-2), dict(fp64_native=2), dict(fp64_native=-1), dict(leaf_form=2),
@@ -183,3 +183,25 @@ def test_binding_fails_loudly_without_the_library(monkeypatch):
         hps.lib()
     with pytest.raises(RuntimeError, match="not built"):
         hps.hps_plan(hps.Problem(4, 8, 10.0, 10.0))
+
+
+def test_gauss_interface_arguments():
+    """q: 0 or p-2 (Chebyshev edge nodes) or 1..64 Gauss-Legendre nodes per
+    leaf edge; the mixed path keeps the Chebyshev edges (its refinement
+    residual is that system's); a batch shares one q.  Checked before any
+    device work."""
+    info = hps.hps_info_t()
+    for q, code in ((0, hps.HPS_OK), (14, hps.HPS_OK), (1, hps.HPS_OK), (12, hps.HPS_OK), (64, hps.HPS_OK),
+                    (65, hps.HPS_EINVAL), (-1, hps.HPS_EINVAL)):
+        d = hps.Problem(4, 16, 10.0, 10.0).desc()
+        d.q = q
+        assert hps.lib().hps_plan(ctypes.byref(d), ctypes.byref(info)) == code, q
+        if code == hps.HPS_OK:
+            assert info.n_bdry == 2 * 8 * (q or 14)
+    dm = hps.Problem(4, 16, 10.0, 10.0, precision=hps.HPS_MIXED, q=12).desc()
+    assert hps.lib().hps_plan(ctypes.byref(dm), ctypes.byref(info)) == hps.HPS_ENOTSUP
+    ds = (hps.hps_desc * 2)(hps.Problem(4, 8, 10.0, 10.0, q=4).desc(), hps.Problem(4, 8, 10.0, 10.0, q=5).desc())
+    c = np.ones(16 * 36)
+    cs = (ctypes.c_void_p * 2)(c.ctypes.data, c.ctypes.data)
+    hs = (ctypes.c_void_p * 2)()
+    assert hps.lib().hps_build_batch(2, ds, cs, None, hs) == hps.HPS_EINVAL
