@@ -64,6 +64,8 @@ struct Level {
   void *Phia = nullptr, *Phib = nullptr;
 };
 
+constexpr int kLeafRefineSteps = 2;  // refinement steps of the complex64 leaf inverse
+
 struct Plan {
   int m, my, p, e, n, nb, ni, L, leaves, nbdry;  // m: leaves along x, my: along y
   // boundary data points per leaf edge: e (the corner-free Chebyshev nodes),
@@ -73,6 +75,7 @@ struct Plan {
   bool mixed;                   // HPS_MIXED
   int leaf_f32;                 // leaf operators in complex64
   bool leaf_lu;                 // leaf operators as LU factors (else B^{-1})
+  bool leaf_refined;            // complex128 B^{-1} by a refined complex64 inverse (else Gauss-Jordan)
   int refine_steps;             // refinement steps of a mixed solve
   bool oz;                      // large complex128 merge products on the tensor cores
   std::vector<Level> lv;        // lv[j]: merge j from the leaves up (parents on level L-1-j)
@@ -252,6 +255,9 @@ void make_plan(const hps_desc &d, Plan &pl) {
   pl.mixed = (d.precision == HPS_MIXED);
   pl.leaf_f32 = pl.mixed ? 1 : 0;
   pl.leaf_lu = (d.leaf_form == HPS_LEAF_LU);
+  // the inverse form in complex128: a complex64 inverse refined on the tensor
+  // cores (HPS_LEAF_GJ64 set: complex128 Gauss-Jordan on the FP64 pipes)
+  pl.leaf_refined = !pl.leaf_lu && !pl.leaf_f32 && !getenv("HPS_LEAF_GJ64");
   pl.refine_steps = d.refine_steps == 0 ? 2 : (d.refine_steps < 0 ? 0 : d.refine_steps);
   pl.oz = (d.fp64_native == 0);
   const int top = std::min(pl.L, d.fp64_levels == 0 ? 4 : d.fp64_levels);
@@ -430,6 +436,9 @@ void fill_info(const Plan &pl, hps_info_t &in) {
   // the G-row solve (nb n^2/2), with n pivots and row scales kept
   long long bf = pl.leaf_lu ? (long long)pl.leaves * 8 * (n * n * n / 3 + nb * n * n)
                             : (long long)pl.leaves * 8 * (n * n * n + nb * n * pl.p);
+  // refined inverse: the complex64 inverse, then per step the residual
+  // product (tensor cores) and the complex64 correction product
+  if (pl.leaf_refined) bf += (long long)pl.leaves * 8 * (2LL * kLeafRefineSteps * n * n * n);
   const long long nbi = pl.nbi, qe = pl.qe, e = pl.e;
   long long sf = (long long)pl.leaves * 8 * (nbi * ni + n * n + (pl.gauss ? nb * qe : 0));
   const long long lu_aux = pl.leaf_lu ? (long long)pl.leaves * n * (4 + 8) : 0;
@@ -503,7 +512,8 @@ int leaf_cluster(const Plan &pl, long long NL) {
 // bookkeeping caps a launch at 16384 leaves).
 long long leaf_chunk(const Plan &pl, long long NL) {
   const long long esz = pl.leaf_f32 ? 8 : 16, n = pl.n;
-  const long long cap = pl.leaf_lu ? 16384 : (1LL << 30) / (esz * n * n);
+  // (refined inverse: ~10 MB of scratch a leaf at p = 16)
+  const long long cap = pl.leaf_lu ? 16384 : pl.leaf_refined ? 512 : (1LL << 30) / (esz * n * n);
   return std::max<long long>(1, std::min<long long>(NL, cap));
 }
 
@@ -1587,20 +1597,36 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     const int chunk = (int)leaf_chunk(P0, NL);
     void *lscr = nullptr;
     int *lmeta = nullptr;
-    if (!P0.leaf_lu) CK(cudaMallocAsync(&lscr, (size_t)esl * chunk * n * n, st));
-    CK(cudaMallocAsync((void **)&lmeta,
-                       sizeof(int) * (size_t)chunk * (P0.leaf_lu ? hps::lu_meta_ints(n) : hps::gj_meta_ints(n)), st));
+    const size_t rscr = P0.leaf_refined ? hps::leaf_refined_scratch_bytes(lt, chunk) : 0;
+    if (P0.leaf_refined)
+      CK(cudaMallocAsync(&lscr, rscr, st));
+    else if (!P0.leaf_lu)
+      CK(cudaMallocAsync(&lscr, (size_t)esl * chunk * n * n, st));
+    if (!P0.leaf_refined)
+      CK(cudaMallocAsync((void **)&lmeta,
+                         sizeof(int) * (size_t)chunk * (P0.leaf_lu ? hps::lu_meta_ints(n) : hps::gj_meta_ints(n)),
+                         st));
+    // the complex64 inverse of the refined form: its own cluster rule
+    Plan P32 = P0;
+    P32.leaf_f32 = 1;
+    const int lcs32 = P0.leaf_refined ? leaf_cluster(P32, std::min<long long>(chunk, NL)) : 0;
+    if (P0.leaf_refined && lcs32 == 0) return HPS_ENOTSUP;
     if (events) CK(cudaEventRecord(ev[0], st));
     launches = 0;
     for (long long l0 = 0; l0 < NL; l0 += chunk) {
       const int cnt = (int)std::min<long long>(chunk, NL - l0);
-      if (P0.leaf_lu)
+      if (P0.leaf_lu) {
         CK(hps::launch_leaf_lu(lt, d_probs, K, l0, cnt, base + oX, base + oGX, (int *)(base + oPerm),
                                (double *)(base + oDsc), lmeta, d_status, Lmax, lcs, lf != 0, st));
-      else
+        launches++;
+      } else if (P0.leaf_refined) {
+        CK(hps::launch_leaf_refined(lt, d_probs, K, l0, cnt, base + oX, base + oGX, lscr, rscr, d_status, Lmax,
+                                    lcs32, kLeafRefineSteps, st, &launches));
+      } else {
         CK(hps::launch_leaf(lt, d_probs, K, l0, cnt, base + oX, base + oGX, lscr, lmeta, d_status, Lmax, lcs,
                             lf != 0, st));
-      launches++;
+        launches++;
+      }
     }
     if (gauss) {
       // boundary data on the Gauss nodes: the leaves' interface operators
@@ -1639,7 +1665,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     }
     if (events) CK(cudaEventRecord(ev[1], st));
     if (lscr) CK(cudaFreeAsync(lscr, st));
-    CK(cudaFreeAsync(lmeta, st));
+    if (lmeta) CK(cudaFreeAsync(lmeta, st));
 
     if (k1 < K) {
       // single-leaf problems: the root R is the leaf's R = GX[:, :nb] (on the
@@ -1875,9 +1901,26 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
   const Plan &pl = h->plan;
   const long long esz = pl.leaf_f32 ? 8 : 16, n = pl.n;
   const long long chunk = leaf_chunk(pl, pl.leaves);
-  h->info.build_launches += (int)((pl.leaves + chunk - 1) / chunk) - 1;  // leaf chunks
+  const int nchunks = (int)((pl.leaves + chunk - 1) / chunk);
+  h->info.build_launches += nchunks - 1;  // leaf chunks
   long long leaf_scr = pl.leaf_lu ? 4LL * chunk * (long long)hps::lu_meta_ints(pl.n)
                                   : esz * chunk * n * n + 4LL * chunk * (long long)hps::gj_meta_ints(pl.n);
+  if (pl.leaf_refined) {
+    hps::LeafTables lt;
+    lt.p = pl.p;
+    lt.e = pl.e;
+    lt.n = pl.n;
+    lt.nb = pl.nb;
+    lt.ni = pl.ni;
+    leaf_scr = (long long)hps::leaf_refined_scratch_bytes(lt, (int)chunk);
+    // per chunk: complex64 inverse, B, X = X0, per step the residual product
+    // and the correction (product and add), G X
+    GemmDesc g;
+    memset(&g, 0, sizeof(g));
+    g.M = g.N = g.K = pl.n;
+    g.batch = (int)chunk;
+    h->info.build_launches += nchunks * (3 + kLeafRefineSteps * (hps::oz_launches(g) + 2));
+  }
   long long rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
   for (size_t j = 0; j < pl.lv.size(); j++) {
     const Level &L = pl.lv[j];

@@ -175,6 +175,19 @@ cudaError_t launch_leaf_lu(const LeafTables &lt, const LeafProb *probs, int npro
                            int count, void *X, void *GX, int *perm, double *dsc, int *meta,
                            unsigned int *status, int level, int cs, bool f32, cudaStream_t st);
 size_t lu_meta_ints(int n);
+
+// Leaf step in inverse form for complex128 leaves by refinement of a
+// complex64 inverse (leaf_refine.cu): X0 = B^-1 in complex64 (launch_leaf
+// with cluster size cs32), then `steps` times E = I - B X (Ozaki product on
+// the tensor cores) and X += X0 E, then GX = G X.  Writes X and GX of leaves
+// [leaf0, leaf0 + count) ([leaf][n][n], [leaf][n][nb] column-major, indexed
+// by the absolute leaf number, like launch_leaf).  scr: 256-byte aligned
+// device scratch of leaf_refined_scratch_bytes(lt, count).  *launches is
+// increased by the kernels launched.
+size_t leaf_refined_scratch_bytes(const LeafTables &lt, int count);
+cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0, int count,
+                                void *X, void *GX, void *scr, size_t scr_bytes, unsigned int *status, int level,
+                                int cs32, int steps, cudaStream_t st, int *launches);
 size_t lu_leaf_smem_bytes(int n, int nb, int p, int cs, bool f32);
 
 // u = B^{-1} [t; s] for `leaves` leaves from their factors (launch_leaf_lu)
