@@ -58,7 +58,8 @@ def config_dict(nrhs=1, l2="flushed between steps (256 MiB write)", gpu=True):
     }
     if gpu:
         out["leaf_form"] = ("LU factors P D B = L U (leaf kernel), two triangular sweeps a solve" if LEAF_FORM == 0
-                            else "B^-1 (leaf kernel), one product a solve")
+                            else "B^-1: complex64 Gauss-Jordan inverse refined to complex128 by two steps of "
+                                 "E = I - B X (Ozaki product on tcgen05) and X += X0 E; one product a solve")
         out["products"] = ("FP64 pipes; merge products of 2^26+ complex multiply-adds by the Ozaki scheme "
                            "on the bf16 tensor cores (tcgen05; 9 slices of 6 bits, exact FP32 slice sums, "
                            "complex128 totals)")
@@ -177,7 +178,7 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-LEAF_FORM = 0  # hps.HPS_LEAF_LU; --leaf-form inverse sets HPS_LEAF_INVERSE
+LEAF_FORM = 1  # hps.HPS_LEAF_INVERSE (the default); --leaf-form lu sets HPS_LEAF_LU
 
 
 def _problem(*args, **kw):
@@ -234,6 +235,7 @@ def ours(args, rank, world, local_rank):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     leaf_ms = []
+    prod_times = []  # per timed step: (ms, bf16 flops) of each tensor-core product kernel
     handles = []
     with ClockSampler(local_rank) as clk:  # started (first sample seen) before the barrier
         if dist:
@@ -249,6 +251,7 @@ def ours(args, rank, world, local_rank):
             if len(handles) > 1:  # free the previous step's operators outside the timed pair
                 torch.cuda.synchronize()
                 leaf_ms.append(hps.hps_build_times(handles[0])[0])
+                prod_times.append(hps.hps_build_product_times(handles[0]))
                 handles.pop(0).free()
         torch.cuda.synchronize()
         t_wall1 = time.perf_counter()
@@ -256,6 +259,7 @@ def ours(args, rank, world, local_rank):
         dist.barrier()  # every rank's timed region has ended
     for hh in handles:
         leaf_ms.append(hps.hps_build_times(hh)[0])
+        prod_times.append(hps.hps_build_product_times(hh))
         hh.free()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dof = pr.leaves * pr.n
@@ -413,24 +417,51 @@ def ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    # leaf kernel flops (one complex multiply-add = 8): LU of [B; G] and the
-    # G-row solve, or Gauss-Jordan and G X
     lu = LEAF_FORM == 0
-    leaf_flops = (pr.leaves * 8 * (pr.n ** 3 // 3 + pr.nb * pr.n ** 2) if lu
-                  else pr.leaves * 8 * (pr.n ** 3 + pr.nb * pr.n * pr.p))
-    leaf_kernel = "lu_leaf_kernel" if lu else "leaf_kernel"
     leaf_avg = statistics.mean(leaf_ms)
-    achieved = leaf_flops / (leaf_avg / 1e3) / 1e12
     clocks = clk.summary()
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     fp64_nominal = n_sm * FP64_FLOP_PER_CLK_PER_SM * max_mhz * 1e6 / 1e12
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", f"{leaf_kernel}_traffic.json")
-    if os.path.exists(tr_path):
-        with open(tr_path) as f:
-            tr = json.load(f)
-        if tr.get("kernel_hash") == kernel_hash(leaf_kernel):
-            traffic = tr.get("bytes_per_launch")
+    if lu:
+        # the dominant kernel is the LU leaf kernel, bound by the FP64 pipes:
+        # LU of [B; G] and the G-row solve (one complex multiply-add = 8 flop)
+        leaf_kernel = "lu_leaf_kernel"
+        leaf_flops = pr.leaves * 8 * (pr.n ** 3 // 3 + pr.nb * pr.n ** 2)
+        achieved = leaf_flops / (leaf_avg / 1e3) / 1e12
+        traffic = stored_traffic(leaf_kernel)
+        roofline = {"kernel": leaf_kernel, "bound": "alu", "achieved": achieved, "flops_per_launch": leaf_flops,
+                    "peak": fp64_nominal, "unit": "TFLOP/s", "frac": achieved / fp64_nominal,
+                    "traffic": traffic, "leaf_ms": leaf_avg,
+                    "peak_source": f"FP64 unit count x max SM clock ({n_sm} SMs x "
+                                   f"{FP64_FLOP_PER_CLK_PER_SM} flop/clk x {max_mhz:.0f} MHz)",
+                    "peak_measured": fp64_measured, "frac_of_measured": achieved / fp64_measured,
+                    "peak_measured_source": "hps_fp64_rate: independent FMA chains on every SM, CUDA events"}
+    else:
+        # the dominant kernel is the tensor-core product (oz_tc_kernel); its
+        # largest launches are the leaf step's residuals E = I - B X (n x n x n
+        # over the leaves, the first products of a build), timed by the events
+        # the build records around each product kernel
+        steps_refine = 2
+        lead = [(ms[:steps_refine], fl[:steps_refine]) for ms, fl in prod_times]
+        r_ms = sum(float(m.sum()) for m, _ in lead)
+        r_fl = sum(float(f.sum()) for _, f in lead)
+        n_launch = sum(len(m) for m, _ in lead)
+        achieved = r_fl / (r_ms / 1e3) / 1e12
+        all_ms = sum(float(m.sum()) for m, _ in prod_times)
+        all_fl = sum(float(f.sum()) for _, f in prod_times)
+        bf16_peak, peak_src = bf16_peak_sustained()
+        roofline = {"kernel": "oz_tc_kernel", "bound": "tensor", "achieved": achieved,
+                    "flops_per_launch": r_fl / max(n_launch, 1), "unit": "TFLOP/s", "peak": bf16_peak,
+                    "frac": achieved / bf16_peak, "traffic": stored_traffic("oz_tc_kernel"),
+                    "launch_ms": r_ms / max(n_launch, 1), "launches_timed": n_launch,
+                    "what": f"the leaf residual products E = I - B X ({pr.n} x {pr.n} x {pr.n} over {pr.leaves} "
+                            "leaves, bf16 slice flops = 45 pairs x 4 real products x 2 M N K), CUDA events "
+                            "around each product kernel on the build's stream",
+                    "peak_source": peak_src,
+                    "all_tensor_core_products": {"launches_per_step": len(prod_times[0][0]) if prod_times else 0,
+                                                 "achieved": all_fl / (all_ms / 1e3) / 1e12,
+                                                 "frac": all_fl / (all_ms / 1e3) / 1e12 / bf16_peak},
+                    "leaf_phase_ms": leaf_avg}
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -448,13 +479,10 @@ def ours(args, rank, world, local_rank):
         "tuning": {"shapes": tuned_shapes, "seconds": tune_s,
                    "what": "hps_tune: measured tile / tensor-core choice per merge product shape and "
                            "cluster / panel regime per interface-inverse shape, before the timed steps"},
-        "roofline": {"kernel": leaf_kernel, "bound": "alu", "achieved": achieved, "flops_per_launch": leaf_flops,
-                     "peak": fp64_nominal, "unit": "TFLOP/s", "frac": achieved / fp64_nominal,
-                     "traffic": traffic, "leaf_ms": leaf_avg,
-                     "peak_source": f"FP64 unit count x max SM clock ({n_sm} SMs x "
-                                    f"{FP64_FLOP_PER_CLK_PER_SM} flop/clk x {max_mhz:.0f} MHz)",
-                     "peak_measured": fp64_measured, "frac_of_measured": achieved / fp64_measured,
-                     "peak_measured_source": "hps_fp64_rate: independent FMA chains on every SM, CUDA events"},
+        "roofline": roofline,
+        "fp64_peak": {"nominal": fp64_nominal, "measured": fp64_measured,
+                      "nominal_source": f"{n_sm} SMs x {FP64_FLOP_PER_CLK_PER_SM} flop/clk x {max_mhz:.0f} MHz",
+                      "measured_source": "hps_fp64_rate"},
         "e2e": {"value": e2e_value, "unit": "DOF/s",
                 "h2d_bytes_per_step": int(c.nbytes + s.nbytes + t.nbytes),
                 "d2h_bytes_per_step": int(u_gpu.nbytes)},
@@ -687,7 +715,7 @@ def precision(args, local_rank):
 
 
 def zgemm(args, local_rank):
-    """One complex GEMM C = A B (M x K times K x N, batch 1) through
+    """One complex GEMM C = A B (M x K times K x N, batch 1 or the given batch) through
     hps_zgemm: the Ozaki-scheme product on the bf16 tensor cores against the
     FP64-pipe product, device time from CUDA events (median of 5 after 2
     warm-ups), with the relative difference of the two results."""
@@ -698,17 +726,18 @@ def zgemm(args, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     st = torch.cuda.current_stream()
-    M, N, K = args.zgemm
+    M, N, K = args.zgemm[:3]
+    batch = args.zgemm[3] if len(args.zgemm) > 3 else 1
     g = torch.Generator(device=dev).manual_seed(7)
-    A = torch.randn((1, K, M), dtype=torch.complex128, device=dev, generator=g)
-    B = torch.randn((1, N, K), dtype=torch.complex128, device=dev, generator=g)
+    A = torch.randn((batch, K, M), dtype=torch.complex128, device=dev, generator=g)
+    B = torch.randn((batch, N, K), dtype=torch.complex128, device=dev, generator=g)
     out = {"metric": "complex GEMM rate (FP64-equivalent flops: 8 M N K)", "unit": "TFLOP/s",
            "higher_is_better": True, "n_gpus": 1, "data": "synthetic (normal entries)",
-           "config": {"workload": "zgemm", "M": M, "N": N, "K": K}}
+           "config": {"workload": "zgemm", "M": M, "N": N, "K": K, "batch": batch}}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     Cs = {}
     for name, emu in (("fp64_pipes", 0), ("tensor_cores", 1)):
-        C = torch.empty((1, N, M), dtype=torch.complex128, device=dev)
+        C = torch.empty((batch, N, M), dtype=torch.complex128, device=dev)
         ts = []
         for rep in range(7):
             e0.record(st)
@@ -718,7 +747,7 @@ def zgemm(args, local_rank):
             if rep >= 2:
                 ts.append(e0.elapsed_time(e1))
         ms = statistics.median(ts)
-        out[name] = {"ms": ms, "tflops": 8.0 * M * N * K / (ms / 1e3) / 1e12}
+        out[name] = {"ms": ms, "tflops": 8.0 * M * N * K * batch / (ms / 1e3) / 1e12}
         Cs[name] = C
     a, b = Cs["tensor_cores"], Cs["fp64_pipes"]
     out["rel_diff"] = float(((a - b).abs().max() / b.abs().max()).item())
@@ -998,15 +1027,41 @@ def profile_step(args, local_rank):
                       "build_launches": info.build_launches, "solve_launches": info.solve_launches}), flush=True)
 
 
+def bf16_peak_sustained():
+    """The measured sustained bf16 tensor rate of the GB300s
+    (MEASURED_PEAKS.json), else the profiling recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["bf16_tflops_sustained"])
+        return v, "measured sustained bf16 (cuBLAS loop under the power cap, MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback: sustained bf16 ~1.7 PFLOP/s (one earlier GB300 measurement)"
+
+
+def stored_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu capture of `kernel`
+    (profiles/<kernel>_traffic.json), or None once the kernel's source has
+    changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        tr = json.load(f)
+    return tr.get("bytes_per_launch") if tr.get("kernel_hash") == kernel_hash(kernel) else None
+
+
 def kernel_hash(kernel="lu_leaf_kernel"):
     """Hash of the code of a leaf kernel (its file and the device headers it
     includes, comments left out), so stored ncu counters are used only for
     the code they were taken on."""
     import hashlib
 
-    src = "lu.cu" if kernel == "lu_leaf_kernel" else "gj.cu"
+    srcs = {"lu_leaf_kernel": ("lu.cu", "cx.cuh", "leaf_geom.cuh"),
+            "leaf_kernel": ("gj.cu", "cx.cuh", "leaf_geom.cuh"),
+            "oz_tc_kernel": ("ozaki.cu", "cx.cuh", "tc_desc.h", "hps_internal.h")}[kernel]
     h = hashlib.sha256()
-    for name in (src, "cx.cuh", "leaf_geom.cuh"):
+    for name in srcs:
         with open(os.path.join(ROOT, "paper_1812_07167_gb300", "csrc", name)) as f:
             # the code only: // comments and blank lines do not change the kernel
             for line in f:
@@ -1033,12 +1088,13 @@ def main():
                     help="capacity check: M x M leaves, polynomial solution, nodal error and memory")
     ap.add_argument("--scaling", action="store_true",
                     help="build and solve times from 4 x 4 to 128 x 128 leaves, both leaf forms")
-    ap.add_argument("--leaf-form", default="lu", choices=["lu", "inverse"],
-                    help="leaf operators as LU factors (default) or as B^-1")
+    ap.add_argument("--leaf-form", default="inverse", choices=["lu", "inverse"],
+                    help="leaf operators as B^-1 (default; a complex64 inverse refined to complex128 on the "
+                         "tensor cores) or as LU factors")
     ap.add_argument("--serve-resident-form", default="inverse", choices=["lu", "inverse"],
                     help="--serve: leaf form of the resident solver (its requests are wide solves)")
-    ap.add_argument("--zgemm", type=int, nargs=3, metavar=("M", "N", "K"),
-                    help="time one complex GEMM on the tensor cores and on the FP64 pipes")
+    ap.add_argument("--zgemm", type=int, nargs="+", metavar="M N K [BATCH]",
+                    help="time one (batched) complex GEMM on the tensor cores and on the FP64 pipes")
     ap.add_argument("--profile-step", action="store_true",
                     help="one tuned step between cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--serve-m", type=int, default=128)

@@ -361,6 +361,17 @@ int hps_info(const hps_handle *h, hps_info_t *info);
  * HPS_* code.  Waits for the build to finish. */
 int hps_build_times(hps_handle *h, double *ms, int cap);
 
+/* Device time of each tensor-core product kernel of the handle's build (the
+ * complex128 products done by the Ozaki scheme, hps_desc.fp64_native == 0),
+ * from CUDA events the build recorded on its stream around those kernels
+ * alone (not the digit splits): ms[k] and flops[k] = the product's bf16 slice
+ * flops (45 slice pairs x 4 real products x 2 M N K), in launch order, for
+ * the measurement of that kernel against its roofline.  Writes at most cap
+ * of each and returns how many products the build timed (the first 256), or
+ * a negative HPS_* code.  Waits for them to finish.  A diagnostic; the paper
+ * has no counterpart. */
+int hps_build_product_times(hps_handle *h, double *ms, double *flops, int cap);
+
 /* Wait for the handle's work on `stream` and report device-side failures:
  * HPS_ESINGULAR with *level / *box (may be NULL) set to the tree level
  * (leaf level = levels) and box index of the first zero pivot;

@@ -102,6 +102,11 @@ struct Shared {
   std::function<int(cudaStream_t, bool, int &)> compute;
   cudaGraphExec_t graph = nullptr;
   std::vector<hps_handle *> order;  // the handles in build order
+  // the build's tensor-core products: events around each product kernel
+  static constexpr int kOzTimed = 256;
+  std::vector<cudaEvent_t> oz_ev;
+  std::vector<double> oz_flops;
+  int oz_n = 0;
 };
 static std::mutex g_shared_mu;
 
@@ -1249,6 +1254,8 @@ int hps_free(hps_handle *h) {
     }
     if (last) {
       for (cudaEvent_t e : sh->ev) cudaEventDestroy(e);
+      for (cudaEvent_t e : sh->oz_ev)
+        if (e) cudaEventDestroy(e);
       if (sh->graph) cudaGraphExecDestroy(sh->graph);
       if (sh->arena) cudaFree(sh->arena);
       delete sh;
@@ -1872,7 +1879,14 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
   };
   sh->compute = compute;
   int launches = 0;
+  // time the product kernels of the tensor-core products of this build
+  sh->oz_ev.assign(2 * Shared::kOzTimed, nullptr);  // created as products are launched
+  sh->oz_flops.assign(Shared::kOzTimed, 0.0);
+  hps::OzTimer timer{sh->oz_ev.data(), sh->oz_flops.data(), Shared::kOzTimed, 0};
+  hps::oz_set_timer(&timer);
   int rc = compute(st, true, launches);
+  hps::oz_set_timer(nullptr);
+  sh->oz_n = timer.n;
   if (rc != HPS_OK) return rc;
   sh->launches = launches;
   return HPS_OK;
@@ -1919,7 +1933,7 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
     memset(&g, 0, sizeof(g));
     g.M = g.N = g.K = pl.n;
     g.batch = (int)chunk;
-    h->info.build_launches += nchunks * (3 + kLeafRefineSteps * (hps::oz_launches(g) + 2));
+    h->info.build_launches += nchunks * (3 + kLeafRefineSteps * (hps::oz_launches(g) + 2) - 2);
   }
   long long rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
   for (size_t j = 0; j < pl.lv.size(); j++) {
@@ -2322,6 +2336,22 @@ int hps_build_times(hps_handle *h, double *ms, int cap) {
     ms[q] = t;
   }
   return nph;
+}
+
+int hps_build_product_times(hps_handle *h, double *ms, double *flops, int cap) {
+  if (!h || cap < 0 || (cap > 0 && (!ms || !flops))) return -HPS_EINVAL;
+  if (!h->sh) return -HPS_EINVAL;
+  const Shared *sh = h->sh;
+  const int n = sh->oz_n;
+  for (int k = 0; k < n && k < cap; k++) {
+    float t = 0.0f;
+    if (cudaEventSynchronize(sh->oz_ev[2 * k + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, sh->oz_ev[2 * k], sh->oz_ev[2 * k + 1]) != cudaSuccess)
+      return -HPS_ECUDA;
+    ms[k] = t;
+    flops[k] = sh->oz_flops[k];
+  }
+  return n;
 }
 
 int hps_status(hps_handle *h, void *stream, int *level, int *box) {

@@ -142,12 +142,24 @@ cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st);
 // device workspace of oz_workspace_bytes(g).  oz_launches(g) launches (4, or
 // 5 when the slice pairs are split over several CTAs a tile).  A pipeline
 // wait that gives up (2 s) records code 3 in *status (if given) and leaves C
-// unspecified.
+// unspecified.  reuse_a: the workspace already holds A's digits from the
+// previous call with the same A and shape (that call's A split is reused;
+// 2 launches fewer).
+// Per-launch CUDA events around the product kernel (oz_tc_kernel) of the
+// tensor-core products launched by this host thread while a timer is set:
+// product k records ev[2k] before and ev[2k + 1] after its product kernel on
+// the product's stream, and flops[k] = its bf16 slice flops (360 M N K batch).
+struct OzTimer {
+  cudaEvent_t *ev;  // 2 cap events, created on first use (null until then)
+  double *flops;
+  int cap, n;
+};
+void oz_set_timer(OzTimer *t);  // nullptr: stop timing
 bool oz_eligible(const GemmDesc &g);
-int oz_launches(const GemmDesc &g);
+int oz_launches(const GemmDesc &g, bool reuse_a = false);
 size_t oz_workspace_bytes(const GemmDesc &g);
 cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st,
-                           unsigned *status = nullptr);
+                           unsigned *status = nullptr, bool reuse_a = false);
 cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st);
 
 // Leaf step (Sec. 2.1) for leaves [leaf0, leaf0 + count): assemble B, invert

@@ -252,8 +252,9 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
     GemmDesc g = plain_gemm(n, n, n, count, Bm, 0, Xl, 0, E);
     g.alpha = make_double2(-1.0, 0.0);
     g.addI = 1;
-    if ((err = launch_gemm_oz(g, w + L.oz, L.total - L.oz, st, status)) != cudaSuccess) return err;
-    nl += oz_launches(g);
+    // (B's digits are the same in every step: split once)
+    if ((err = launch_gemm_oz(g, w + L.oz, L.total - L.oz, st, status, it > 0)) != cudaSuccess) return err;
+    nl += oz_launches(g, it > 0);
     // T = X0 E in complex64 arithmetic (stored complex128), then X += T in FP64
     GemmDesc c = plain_gemm(n, n, n, count, X0, 1, E, 0, T);
     c.cf32 = 1;

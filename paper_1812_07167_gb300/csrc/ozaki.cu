@@ -88,7 +88,12 @@ struct TcCfg {
   static constexpr int kTileB = BN * TC_BK * 2;
   static constexpr int kStage = 2 * kTileA + 2 * kTileB;  // Ar, Ai, Br, Bi
   static constexpr size_t kSmem = (size_t)kStages * kStage + 1024;  // + alignment slack
-  static constexpr uint32_t kTmemCols = 4 * BN;     // two buffers of [Re | Im] x BN columns
+  // two accumulator buffers of [Re | Im] x BN columns; with BN = 64 the other
+  // half of tensor memory holds the tile's running complex128 sums (each
+  // double as two 32-bit columns: Re of column j at 2 j, Im at 2 (BN + j))
+  static constexpr bool kStateInTmem = (BN == 64);
+  static constexpr uint32_t kStateCol = 4 * BN;
+  static constexpr uint32_t kTmemCols = kStateInTmem ? 8 * BN : 4 * BN;
   static constexpr size_t kAcc = (size_t)TC_BM * 2 * BN;  // doubles of a tile's partial sums
 };
 
@@ -120,7 +125,12 @@ inline size_t oz_align(size_t x) { return (x + 255) & ~(size_t)255; }
 
 OzLayout oz_layout(const GemmDesc &g, int nsm) {
   OzLayout L;
+  // 64-wide tiles (N <= 64) keep their complex128 running sums in tensor
+  // memory; 128-wide ones read half the operand bytes per product, which
+  // measured faster at every K (1792 x 3584 x 896: 2.06 vs 3.34 ms;
+  // 252^3 x 256: 3.22 vs 3.70 ms)
   L.bn = g.N <= 64 ? 64 : 128;
+  if (const char *v = getenv("HPS_OZ_BN")) L.bn = atoi(v) == 64 ? 64 : 128;
   L.Mp = (g.M + TC_BM - 1) / TC_BM * TC_BM;
   L.Np = (g.N + L.bn - 1) / L.bn * L.bn;
   L.Kp = (g.K + TC_BK - 1) / TC_BK * TC_BK;
@@ -437,6 +447,43 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+// 16 consecutive 32-bit columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+// store 32 consecutive 32-bit columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// s 2^k as a double, exactly, for an integer-valued float s with |s| < 2^24
+// (a shift group's FP32 sum) and a weight exponent k >= -60: the double is
+// assembled from the float's fields with integer instructions (sign; biased
+// exponent + 1023 - 127 + k; significand shifted to 52 bits), so a flush
+// costs one FP64 add a value on this part's 1/64-rate FP64 pipe instead of
+// a conversion and a multiply-add.
+__device__ __forceinline__ double oz_term(float s, int k) {
+  const unsigned b = __float_as_uint(s);
+  if ((b & 0x7fffffffu) == 0u) return 0.0;
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned long long ex = (unsigned long long)(((b >> 23) & 0xffu) + 896 + k) << 52;
+  const unsigned long long man = (unsigned long long)(b & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(sign | ex | man));
+}
 
 // pair index p (ordered by shift e = s + t, then s) -> (e, s)
 __device__ __forceinline__ void pair_decode(int p, int &e, int &s) {
@@ -448,6 +495,9 @@ __device__ __forceinline__ void pair_decode(int p, int &e, int &s) {
   s = p;
 }
 
+struct TcArgs;
+__device__ __forceinline__ void oz_out(const TcArgs &a, int b, int i, int j, int sha, double sr, double si);
+
 struct TcArgs {
   GemmDesc g;
   int Mp, Np, Kp;
@@ -458,6 +508,33 @@ struct TcArgs {
   const int *eb;     // [batch][Np]
   unsigned *status;  // build status word for timeouts, or null
 };
+
+// C(i, j) = alpha 2^(a_i + b_j) (sr + i si) + beta D(i, j) (+ 1 on the diagonal)
+__device__ __forceinline__ void oz_out(const TcArgs &a, int b, int i, int j, int sha, double sr, double si) {
+  const GemmDesc &g = a.g;
+  const int sh = sha + __ldg(a.eb + (size_t)b * a.Np + j);
+  const double vre = ldexp(sr, sh), vim = ldexp(si, sh);
+  double outr = g.alpha.x * vre - g.alpha.y * vim;
+  double outi = g.alpha.x * vim + g.alpha.y * vre;
+  if (g.D.ptr) {
+    const long long od = oz_off(g.D, b, i, j);
+    double2 d;
+    if (g.D.f32) {
+      const float2 f = ((const float2 *)g.D.ptr)[od];
+      d = make_double2(f.x, f.y);
+    } else {
+      d = ((const double2 *)g.D.ptr)[od];
+    }
+    outr += g.beta.x * d.x - g.beta.y * d.y;
+    outi += g.beta.x * d.y + g.beta.y * d.x;
+  }
+  if (g.addI && i == j) outr += 1.0;
+  const long long oc = oz_off(g.C, b, i, j);
+  if (g.C.f32)
+    ((float2 *)g.C.ptr)[oc] = make_float2((float)outr, (float)outi);
+  else
+    ((double2 *)g.C.ptr)[oc] = make_double2(outr, outi);
+}
 
 template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -616,71 +693,98 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * BN + hf * NC);
-        const double w = ldexp(1.0, -6 * (e + 2));
-        const bool fin = (c == nch - 1) && (p == p1 - 1) && a.gp == 1;
-        // 32 columns of both parts at a time: tensor memory -> registers -> complex128
+        const int wk = -6 * (e + 2);  // the group's weight 2^wk
+        const bool last = (c == nch - 1) && (p == p1 - 1);
+        const bool fin = last && a.gp == 1;
+        if constexpr (Cfg::kStateInTmem) {
+          // this warp's 32 columns, 16 at a time: the group's FP32 sums and
+          // the running complex128 sums, both in tensor memory
+          const uint32_t ts = tmem + ((uint32_t)(q * 32) << 16) + Cfg::kStateCol;
 #pragma unroll 1
-        for (int l = 0; l < NL; l++) {
-          uint32_t vr[32], vi[32];
-          tc_ld32(tb + l * 32, vr);
-          tc_ld32(tb + BN + l * 32, vi);
-          tc_wait_ld();
-          if (l == NL - 1) {
-            // the buffer is free for the next group but one
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce_bar[buf]);
-          }
-          if (fin) {
-            // C = alpha 2^(a_i + b_j) sum + beta D (+ I)
-#pragma unroll
-            for (int jj = 0; jj < 32; jj++) {
-              const int jl = hf * NC + l * 32 + jj;
-              const int j = tn * BN + jl;
-              double sr = (double)__uint_as_float(vr[jj]) * w;
-              double si = (double)__uint_as_float(vi[jj]) * w;
-              if (!first) {
-                sr += slab[(size_t)jl * TC_BM + row];
-                si += slab[(size_t)(BN + jl) * TC_BM + row];
-              }
-              if (i >= g.M || j >= g.N) continue;
-              const int sh = sha + __ldg(a.eb + (size_t)b * a.Np + j);
-              const double vre = ldexp(sr, sh), vim = ldexp(si, sh);
-              double outr = g.alpha.x * vre - g.alpha.y * vim;
-              double outi = g.alpha.x * vim + g.alpha.y * vre;
-              if (g.D.ptr) {
-                const long long od = oz_off(g.D, b, i, j);
-                double2 d;
-                if (g.D.f32) {
-                  const float2 f = ((const float2 *)g.D.ptr)[od];
-                  d = make_double2(f.x, f.y);
-                } else {
-                  d = ((const double2 *)g.D.ptr)[od];
-                }
-                outr += g.beta.x * d.x - g.beta.y * d.y;
-                outi += g.beta.x * d.y + g.beta.y * d.x;
-              }
-              if (g.addI && i == j) outr += 1.0;
-              const long long oc = oz_off(g.C, b, i, j);
-              if (g.C.f32)
-                ((float2 *)g.C.ptr)[oc] = make_float2((float)outr, (float)outi);
-              else
-                ((double2 *)g.C.ptr)[oc] = make_double2(outr, outi);
+          for (int l = 0; l < NC / 16; l++) {
+            const int j0 = hf * NC + l * 16;  // first tile column of this piece
+            uint32_t vr[16], vi[16], wr[32], wi[32];
+            tc_ld16(tb + l * 16, vr);
+            tc_ld16(tb + BN + l * 16, vi);
+            if (!first) {
+              tc_ld32(ts + 2 * j0, wr);
+              tc_ld32(ts + 2 * (BN + j0), wi);
             }
-          } else {
+            tc_wait_ld();
+            if (l == NC / 16 - 1) {
+              // the accumulator buffer is free for the next group but one
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&acce_bar[buf]);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) {
+              double sr = oz_term(__uint_as_float(vr[jj]), wk);
+              double si = oz_term(__uint_as_float(vi[jj]), wk);
+              if (!first) {
+                sr += __hiloint2double((int)wr[2 * jj + 1], (int)wr[2 * jj]);
+                si += __hiloint2double((int)wi[2 * jj + 1], (int)wi[2 * jj]);
+              }
+              const int jl = j0 + jj, j = tn * BN + jl;
+              if (fin) {
+                if (i < g.M && j < g.N) oz_out(a, b, i, j, sha, sr, si);
+              } else if (last) {
+                // this CTA's share of the slice pairs, for the reduce pass
+                slab[(size_t)jl * TC_BM + row] = sr;
+                slab[(size_t)(BN + jl) * TC_BM + row] = si;
+              } else {
+                wr[2 * jj] = (uint32_t)__double2loint(sr);
+                wr[2 * jj + 1] = (uint32_t)__double2hiint(sr);
+                wi[2 * jj] = (uint32_t)__double2loint(si);
+                wi[2 * jj + 1] = (uint32_t)__double2hiint(si);
+              }
+            }
+            if (!last) {
+              tc_st32(ts + 2 * j0, wr);
+              tc_st32(ts + 2 * (BN + j0), wi);
+              tc_wait_st();
+            }
+          }
+        } else {
+          // 32 columns of both parts at a time: tensor memory -> registers ->
+          // the running complex128 sums in global scratch (or C)
+#pragma unroll 1
+          for (int l = 0; l < NL; l++) {
+            uint32_t vr[32], vi[32];
+            tc_ld32(tb + l * 32, vr);
+            tc_ld32(tb + BN + l * 32, vi);
+            tc_wait_ld();
+            if (l == NL - 1) {
+              // the buffer is free for the next group but one
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&acce_bar[buf]);
+            }
             double *pr = slab + (size_t)(hf * NC + l * 32) * TC_BM + row;
             double *pi = pr + (size_t)BN * TC_BM;
-            if (first) {
+            if (fin) {
 #pragma unroll
               for (int jj = 0; jj < 32; jj++) {
-                pr[(size_t)jj * TC_BM] = (double)__uint_as_float(vr[jj]) * w;
-                pi[(size_t)jj * TC_BM] = (double)__uint_as_float(vi[jj]) * w;
+                const int j = tn * BN + hf * NC + l * 32 + jj;
+                double sr = oz_term(__uint_as_float(vr[jj]), wk);
+                double si = oz_term(__uint_as_float(vi[jj]), wk);
+                if (!first) {
+                  sr += pr[(size_t)jj * TC_BM];
+                  si += pi[(size_t)jj * TC_BM];
+                }
+                if (i < g.M && j < g.N) oz_out(a, b, i, j, sha, sr, si);
+              }
+            } else if (first) {
+#pragma unroll
+              for (int jj = 0; jj < 32; jj++) {
+                pr[(size_t)jj * TC_BM] = oz_term(__uint_as_float(vr[jj]), wk);
+                pi[(size_t)jj * TC_BM] = oz_term(__uint_as_float(vi[jj]), wk);
               }
             } else {
 #pragma unroll
               for (int jj = 0; jj < 32; jj++) {
-                pr[(size_t)jj * TC_BM] = fma((double)__uint_as_float(vr[jj]), w, pr[(size_t)jj * TC_BM]);
-                pi[(size_t)jj * TC_BM] = fma((double)__uint_as_float(vi[jj]), w, pi[(size_t)jj * TC_BM]);
+                pr[(size_t)jj * TC_BM] += oz_term(__uint_as_float(vr[jj]), wk);
+                pi[(size_t)jj * TC_BM] += oz_term(__uint_as_float(vi[jj]), wk);
               }
             }
           }
@@ -789,6 +893,8 @@ bool digit_map(CUtensorMap *m, const void *base, int Kp, int rows, long long pla
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+thread_local OzTimer *g_oz_timer = nullptr;
+
 template <int BN>
 cudaError_t launch_product(const OzLayout &L, const TcArgs &a, const void *Ad, const void *Bd, cudaStream_t st) {
   const GemmDesc &g = a.g;
@@ -799,8 +905,21 @@ cudaError_t launch_product(const OzLayout &L, const TcArgs &a, const void *Ad, c
   cudaError_t err =
       cudaFuncSetAttribute(oz_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<BN>::kSmem);
   if (err != cudaSuccess) return err;
+  OzTimer *tm = g_oz_timer;
+  bool timed = tm && tm->n < tm->cap;
+  for (int q = 0; timed && q < 2; q++)
+    if (!tm->ev[2 * tm->n + q] && cudaEventCreate(&tm->ev[2 * tm->n + q]) != cudaSuccess) {
+      cudaGetLastError();
+      timed = false;
+    }
+  if (timed) cudaEventRecord(tm->ev[2 * tm->n], st);
   oz_tc_kernel<BN><<<dim3(L.tn, L.tm, g.batch * L.gp), TC_THREADS, TcCfg<BN>::kSmem, st>>>(mA, mB, a);
   err = cudaGetLastError();
+  if (timed) {
+    cudaEventRecord(tm->ev[2 * tm->n + 1], st);
+    tm->flops[tm->n] = 360.0 * g.M * g.N * g.K * g.batch;  // 45 slice pairs x 4 real products
+    tm->n++;
+  }
   if (err != cudaSuccess || L.gp == 1) return err;
   const long long n = (long long)g.M * g.N * g.batch;
   oz_reduce_kernel<BN><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
@@ -809,7 +928,11 @@ cudaError_t launch_product(const OzLayout &L, const TcArgs &a, const void *Ad, c
 
 }  // namespace
 
-int oz_launches(const GemmDesc &g) { return oz_layout(g, num_sms()).gp > 1 ? 5 : 4; }
+void oz_set_timer(OzTimer *t) { g_oz_timer = t; }
+
+int oz_launches(const GemmDesc &g, bool reuse_a) {
+  return (oz_layout(g, num_sms()).gp > 1 ? 5 : 4) - (reuse_a ? 2 : 0);
+}
 
 bool oz_eligible(const GemmDesc &g) {
   // worth the split passes only for sizeable products whose tiles are mostly
@@ -820,19 +943,23 @@ bool oz_eligible(const GemmDesc &g) {
 
 size_t oz_workspace_bytes(const GemmDesc &g) { return oz_layout(g, num_sms()).total; }
 
-cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st, unsigned *status) {
+cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st, unsigned *status,
+                           bool reuse_a) {
   if (g.batch <= 0 || g.M <= 0 || g.N <= 0) return cudaSuccess;
   const OzLayout L = oz_layout(g, num_sms());
   if (!ws || ws_bytes < L.total || g.batch > 65535 || ((uintptr_t)ws & 255)) return cudaErrorInvalidValue;
   char *w = (char *)ws;
   __nv_bfloat16 *Ad = (__nv_bfloat16 *)(w + L.a_off), *Bd = (__nv_bfloat16 *)(w + L.b_off);
   int *ea = (int *)(w + L.ea_off), *eb = (int *)(w + L.eb_off);
-  oz_expo_a_kernel<<<dim3(L.Mp / 32, g.batch), 256, 0, st>>>(g, L.Mp, ea);
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
-  oz_split_a_kernel<<<dim3(L.Mp / OZA_R, L.Kp / OZA_K, g.batch), 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
-  err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
+  cudaError_t err = cudaSuccess;
+  if (!reuse_a) {
+    oz_expo_a_kernel<<<dim3(L.Mp / 32, g.batch), 256, 0, st>>>(g, L.Mp, ea);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    oz_split_a_kernel<<<dim3(L.Mp / OZA_R, L.Kp / OZA_K, g.batch), 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
   oz_split_b_kernel<<<dim3((L.Np + 7) / 8, g.batch), 256, 0, st>>>(g, L.Np, L.Kp, Bd, eb);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;

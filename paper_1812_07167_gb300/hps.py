@@ -29,7 +29,7 @@ HPS_LEAF_INVERSE = 1
 
 # every entry point include/hps.h declares
 EXPORTS = ("hps_nodes", "hps_build", "hps_build_batch", "hps_rebuild", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
-           "hps_root_R", "hps_leaf_ops", "hps_zgemm", "hps_fp64_rate", "hps_tune", "hps_plan", "hps_info", "hps_build_times", "hps_status", "hps_free", "hps_strerror")
+           "hps_root_R", "hps_leaf_ops", "hps_zgemm", "hps_fp64_rate", "hps_tune", "hps_plan", "hps_info", "hps_build_times", "hps_build_product_times", "hps_status", "hps_free", "hps_strerror")
 
 
 class hps_desc(ctypes.Structure):
@@ -94,6 +94,7 @@ def lib():
         L.hps_info.argtypes = [P, ctypes.POINTER(hps_info_t)]
         L.hps_plan.argtypes = [D, ctypes.POINTER(hps_info_t)]
         L.hps_build_times.argtypes = [P, P, ctypes.c_int]
+        L.hps_build_product_times.argtypes = [P, P, P, ctypes.c_int]
         L.hps_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.hps_free.argtypes = [P]
         L.hps_strerror.argtypes = [ctypes.c_int]
@@ -339,6 +340,16 @@ def hps_leaf_ops(h: Handle, leaf: int, Psi=None, Y=None, Gam=None, stream=None):
     _check(lib().hps_leaf_ops(h.ptr, int(leaf), _ptr(Psi), _ptr(Y), _ptr(Gam), _stream(stream)),
            "hps_leaf_ops")
     return Psi, Y, Gam
+
+
+def hps_build_product_times(h: Handle):
+    """(ms, bf16 flops) of each tensor-core product kernel of the build."""
+    ms = np.zeros(256)
+    fl = np.zeros(256)
+    n = lib().hps_build_product_times(h.ptr, _ptr(ms), _ptr(fl), len(ms))
+    if n < 0:
+        raise HPSError(-n, "hps_build_product_times")
+    return ms[:n].copy(), fl[:n].copy()
 
 
 def hps_build_times(h: Handle):
