@@ -567,18 +567,22 @@ struct GJChoice {
   bool tglobal = false;  // cluster kernel: panels read in place from global memory
   int wide = 0;          // > 0: one launch per panel over P * wide CTAs instead
   int kb = 8;            // panel width (8, or 4 for a shorter serial chain)
+  // complex128 matrices: a complex64 inverse (the kernel and regime above, in
+  // complex64) refined by two complex128 residual steps (w_inverse)
+  bool refined = false;
 };
 // a measured choice as one int of the tuning table: cs, or -wide; panel
-// width 4 adds 2^20 to the magnitude
+// width 4 adds 2^20 to the magnitude, the refined regime 2^21
 int gj_encode(const GJChoice &g) {
   const int v = g.wide ? g.wide : g.cs;
-  const int m = v + (g.kb == 4 ? (1 << 20) : 0);
+  const int m = v + (g.kb == 4 ? (1 << 20) : 0) + (g.refined ? (1 << 21) : 0);
   return g.wide ? -m : m;
 }
 GJChoice gj_decode(int v) {
   GJChoice g;
   const int m = v < 0 ? -v : v;
-  g.kb = (m >> 20) ? 4 : 8;
+  g.kb = ((m >> 20) & 1) ? 4 : 8;
+  g.refined = ((m >> 21) & 1) != 0;
   if (v > 0)
     g.cs = m & ((1 << 20) - 1);
   else
@@ -594,13 +598,24 @@ bool choose_gj(int n3, long long P, int f32, GJChoice &g) {
   bool ok = false;
   if (P <= (1 << 30) && tuned(TuneKey{1, n3, 0, 0, (int)P, f32}, v) && v != 0) {
     GJChoice t = gj_decode(v);
-    t.tglobal = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, f32, t.kb) > 200 * 1024;
-    if (t.wide || hps::gj_smem_bytes(n3, t.cs, false, 0, t.tglobal, f32, t.kb) <= 227 * 1024) {
+    const int kf = (f32 || t.refined) ? 1 : 0;  // the precision the elimination runs in
+    t.tglobal = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, kf, t.kb) > 200 * 1024;
+    if (t.wide || hps::gj_smem_bytes(n3, t.cs, false, 0, t.tglobal, kf, t.kb) <= 227 * 1024) {
       g = t;
       ok = true;
     }
   }
-  if (!ok) ok = choose_gj_rule(n3, P, f32, g);
+  if (!ok) {
+    ok = choose_gj_rule(n3, P, f32, g);
+    // complex128 matrices too few to fill the chip (the panel-per-launch
+    // regime): their inverse is a serial chain of panel eliminations on the
+    // 1/64-rate FP64 pipe, so refine a complex64 inverse instead
+    GJChoice r;
+    if (ok && !f32 && g.wide && !getenv("HPS_W_GJ64") && choose_gj_rule(n3, P, 1, r)) {
+      g = r;
+      g.refined = true;
+    }
+  }
   // HPS_GJ_KB=4: panels of 4 columns whatever was chosen (it needs less
   // shared memory than 8, so the choice still fits); for tests of that width
   if (ok) {
@@ -629,7 +644,18 @@ bool choose_gj_rule(int n3, long long P, int f32, GJChoice &g) {
   return true;
 }
 
-int gj_launches(int n3, const GJChoice &g) { return g.wide ? hps::gj_wide_launches(n3, g.kb) : 1; }
+int gj_elim_launches(int n3, const GJChoice &g) { return g.wide ? hps::gj_wide_launches(n3, g.kb) : 1; }
+bool oz_shape(int M, int N, int K, int batch, int f32, bool oz);
+int oz_launches_shape(int M, int N, int K, int batch);
+// launches of an interface inverse: the elimination, or for the refined
+// regime the conversion, the complex64 elimination, the widening copy and
+// per step the residual product, the correction product and its addition
+int gj_launches(int n3, long long P, bool oz, const GJChoice &g) {
+  if (!g.refined) return gj_elim_launches(n3, g);
+  const bool ozr = oz_shape(n3, n3, n3, (int)P, 0, oz);
+  const int prod = ozr ? oz_launches_shape(n3, n3, n3, (int)P) : 1;
+  return 2 + gj_elim_launches(n3, g) + (prod + 2) + ((ozr ? prod - 2 : 1) + 2);
+}
 
 // Does a product of this shape go to the tensor cores (Ozaki scheme)?
 bool oz_shape(int M, int N, int K, int batch, int f32, bool oz) {
@@ -665,6 +691,81 @@ size_t oz_bytes_shape(int M, int N, int K, int batch) {
   return hps::oz_workspace_bytes(g);
 }
 
+// Scratch of the refined interface inverse of P complex128 n3 x n3 matrices:
+// W in complex64, its complex64 inverse X0, the residual E, the correction
+// T, and the tensor-core product's workspace when the residual goes there.
+struct WRef {
+  size_t w32, x0, e, t, oz, total;
+};
+WRef wref_layout(int n3, long long P, bool oz) {
+  const size_t n2 = (size_t)n3 * n3 * P;
+  WRef L;
+  L.w32 = 0;
+  L.x0 = align256(8 * n2);
+  L.e = L.x0 + align256(8 * n2);
+  L.t = L.e + align256(16 * n2);
+  L.oz = L.t + align256(16 * n2);
+  L.total = L.oz + (oz_shape(n3, n3, n3, (int)P, 0, oz) ? oz_bytes_shape(n3, n3, n3, (int)P) : 0);
+  return L;
+}
+
+// W^{-1} of P n3 x n3 matrices (Sec. 2.2's interface inverse) into Winv.
+// The elimination regimes destroy W; the refined one keeps it (its residuals
+// read it): X0 = the complex64 inverse of W, then two steps of E = I - W X
+// (complex128-accurate: the Ozaki product on the tensor cores where that shape
+// goes there, else the FP64 pipes) and X += X0 E (complex64 arithmetic, added
+// in FP64).  W's 1-norm condition numbers stay below ~100 at every workload
+// here, so ||I - W X0|| ~ 1e-6 and two steps reach complex128 rounding.
+int w_inverse(const GJChoice &g, void *W, void *Winv, int n3, int P, int *meta, unsigned *status, int lev,
+              bool f32, char *rscr, bool oz, cudaStream_t st, int &launches) {
+  if (!g.refined || f32) {
+    if (g.wide)
+      CK(hps::launch_gj_wide(W, Winv, n3, P, g.wide, meta, status, lev, f32, st, g.kb));
+    else
+      CK(hps::launch_gj_inverse(W, Winv, n3, P, meta, status, lev, g.cs, g.tglobal, f32, st, g.kb));
+    launches += gj_elim_launches(n3, g);
+    return HPS_OK;
+  }
+  const WRef L = wref_layout(n3, P, oz);
+  void *W32 = rscr + L.w32, *X0 = rscr + L.x0;
+  double2 *E = (double2 *)(rscr + L.e), *T = (double2 *)(rscr + L.t);
+  const long long s2 = (long long)n3 * n3;
+  CopyBatch cb;
+  cb.count = 1;
+  cb.d[0] = copy(n3, n3, P, mat(W, n3, s2), mat(W32, n3, s2, nullptr, nullptr, 1));
+  CK(hps::launch_copy(cb, st));
+  if (g.wide)
+    CK(hps::launch_gj_wide(W32, X0, n3, P, g.wide, meta, status, lev, true, st, g.kb));
+  else
+    CK(hps::launch_gj_inverse(W32, X0, n3, P, meta, status, lev, g.cs, g.tglobal, true, st, g.kb));
+  cb.d[0] = copy(n3, n3, P, mat(X0, n3, s2, nullptr, nullptr, 1), mat(Winv, n3, s2));
+  CK(hps::launch_copy(cb, st));
+  launches += 2 + gj_elim_launches(n3, g);
+  const bool ozr = oz_shape(n3, n3, n3, P, 0, oz);
+  for (int it = 0; it < 2; it++) {
+    GemmDesc gr = gemm(n3, n3, n3, P, mat(W, n3, s2), mat(Winv, n3, s2), mat(E, n3, s2));
+    gr.alpha = make_double2(-1.0, 0.0);
+    gr.addI = 1;
+    if (ozr) {
+      CK(hps::launch_gemm_oz(gr, rscr + L.oz, L.total - L.oz, st, status, it > 0));
+      launches += hps::oz_launches(gr, it > 0);
+    } else {
+      int v;
+      if (tuned(TuneKey{0, n3, n3, n3, P, 0}, v) && v >= 1 && v <= 4) gr.cfg = v;
+      CK(hps::launch_gemm(&gr, 1, st));
+      launches++;
+    }
+    GemmDesc gc = gemm(n3, n3, n3, P, mat(X0, n3, s2, nullptr, nullptr, 1), mat(E, n3, s2), mat(T, n3, s2));
+    gc.cf32 = 1;
+    CK(hps::launch_gemm(&gc, 1, st));
+    cb.d[0] = copy(n3, n3, P, mat(T, n3, s2), mat(Winv, n3, s2));
+    cb.d[0].accumulate = 1;
+    CK(hps::launch_copy(cb, st));
+    launches += 2;
+  }
+  return HPS_OK;
+}
+
 // The six products of one merge run of P parents (Sec. 2.2): W, Q, Phi_a,
 // Phi_b, and the two halves of R^tau, as (M, N, K).
 void merge_products(int n1, int n2, int n3, int nt, int (&mnk)[6][3]) {
@@ -678,7 +779,7 @@ void merge_products(int n1, int n2, int n3, int nt, int (&mnk)[6][3]) {
 int merge_launches(int n1, int n2, int n3, int nt, int P, int f32, bool oz, const GJChoice &gj) {
   int mnk[6][3];
   merge_products(n1, n2, n3, nt, mnk);
-  int n = 1 + gj_launches(n3, gj);
+  int n = 1 + gj_launches(n3, P, oz, gj);
   for (int q = 0; q < 4; q++)
     n += oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], P, f32, oz) ? oz_launches_shape(mnk[q][0], mnk[q][1], mnk[q][2], P)
                                                                : 1;
@@ -1718,11 +1819,16 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
           if (oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P, r.f32, P0.oz))
             oz_bytes = std::max(oz_bytes, oz_bytes_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P));
     }
+    // the refined interface inverses' scratch
+    size_t wref_bytes = 0;
+    for (int j = 0; j < Lmax; j++)
+      for (const BuildRun &r : runs[j])
+        if (r.gj.refined && !r.f32) wref_bytes = std::max(wref_bytes, wref_layout(P0.lv[j].n3, r.P, P0.oz).total);
     char *scratch = nullptr;
     int *wmeta = nullptr;
     const size_t sbytes = 2 * rbytes + sizeof(double2) * (qbuf + wbuf + cbuf);
     if (Lmax > 0) {
-      CK(cudaMallocAsync((void **)&scratch, align256(sbytes) + oz_bytes, st));
+      CK(cudaMallocAsync((void **)&scratch, align256(sbytes) + align256(oz_bytes) + wref_bytes, st));
       CK(cudaMallocAsync((void **)&wmeta, sizeof(int) * std::max<size_t>(mbuf, 1), st));
     }
     char *Rbuf[2] = {scratch, scratch + rbytes};
@@ -1730,6 +1836,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     double2 *Wscr = Q + qbuf;
     double2 *Rconv = Wscr + wbuf;
     void *ozws = oz_bytes ? scratch + align256(sbytes) : nullptr;
+    char *wrscr = wref_bytes ? scratch + align256(sbytes) + align256(oz_bytes) : nullptr;
     // products: emulated ones one at a time, the rest in one launch
     auto run_gemm = [&](GemmDesc *gd, int nd) -> int {
       GemmDesc rest[2];
@@ -1838,11 +1945,8 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
         g.cf32 = f;
         if (int rc = run_gemm(&g, 1)) return rc;
         const int lev = S.lev;  // the tallest tree's level numbering
-        if (r.gj.wide)
-          CK(hps::launch_gj_wide(Wscr, Winv, n3, P, r.gj.wide, wmeta, d_status, lev, f != 0, st, r.gj.kb));
-        else
-          CK(hps::launch_gj_inverse(Wscr, Winv, n3, P, wmeta, d_status, lev, r.gj.cs, r.gj.tglobal, f != 0, st,
-                                    r.gj.kb));
+        if (int rc = w_inverse(r.gj, Wscr, Winv, n3, P, wmeta, d_status, lev, f != 0, wrscr, P0.oz, st, launches))
+          return rc;
         // Q(:, :n1) = R33b R31a
         g = gemm(n3, n1, n3, P, M(R33b, n3, s33), sub(Ra, dI3a, dI1), M(Q, n3, s3t));
         g.cf32 = f;
@@ -1869,7 +1973,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
         g2[1].beta = make_double2(1.0, 0.0);
         g2[1].cf32 = f;
         if (int rc = run_gemm(g2, 2)) return rc;
-        launches += 1 + gj_launches(n3, r.gj);  // the copy and W^{-1}
+        launches += 1;  // the copy (W^{-1} counted by w_inverse)
       }
       if (events) CK(cudaEventRecord(ev[2 + j], st));
     }
@@ -1935,9 +2039,12 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
     g.batch = (int)chunk;
     h->info.build_launches += nchunks * (3 + kLeafRefineSteps * (hps::oz_launches(g) + 2) - 2);
   }
-  long long rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0;
+  long long rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0, wref = 0;
   for (size_t j = 0; j < pl.lv.size(); j++) {
     const Level &L = pl.lv[j];
+    GJChoice gq;
+    if (!L.f32 && choose_gj(L.n3, L.P, 0, gq) && gq.refined)
+      wref = std::max(wref, (long long)wref_layout(L.n3, L.P, pl.oz).total);
     rbuf = std::max(rbuf, (long long)L.P * L.nt * L.nt);
     qbuf = std::max(qbuf, (long long)L.P * L.n3 * L.nt);
     wbuf = std::max(wbuf, (long long)L.P * L.n3 * L.n3);
@@ -1945,7 +2052,7 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
     const int cf = (j == 0) ? pl.leaf_f32 : pl.lv[j - 1].f32;
     if (cf != L.f32) cbuf = std::max(cbuf, 2LL * L.P * L.nc * L.nc);
   }
-  const long long merge_scr = 16 * (2 * rbuf + qbuf + wbuf + cbuf) + 4 * mbuf;
+  const long long merge_scr = 16 * (2 * rbuf + qbuf + wbuf + cbuf) + 4 * mbuf + wref;
   h->info.build_scratch_bytes = std::max(leaf_scr, merge_scr) + (pl.mixed ? 0 : 8LL * pl.leaves * pl.ni);
   SolveWs w1;
   solve_ws_layout(pl, 1, w1);
@@ -2140,13 +2247,14 @@ int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned) {
   const size_t oA = 0, oB = align256(16 * amax), oC = oB + align256(16 * bmax), oS = oC + align256(16 * cmax);
   const size_t oM = oS + align256(16 * smax), oSt = oM + align256(4 * mmax), total = oSt + 256;
   CK(cudaMalloc((void **)&buf, total));
-  void *ozws = nullptr;
-  size_t ozb = 0;
+  void *ozws = nullptr, *wrefws = nullptr;
+  size_t ozb = 0, wrefb = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto cleanup = [&]() {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (ozws) cudaFree(ozws);
+    if (wrefws) cudaFree(wrefws);
     cudaFree(buf);
   };
   auto fail = [&](cudaError_t err) {
@@ -2227,33 +2335,59 @@ int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned) {
       GJChoice rule;
       if (!choose_gj_rule(n3, P, k.f32, rule)) continue;
       std::vector<GJChoice> cands;
-      for (int kb : {8, 4}) {
-        const bool tg = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, k.f32, kb) > 200 * 1024;
-        for (int cs = 1; cs <= hps::gj_max_cluster(); cs *= 2)
-          // every CTA of the cluster owns at least one panel
-          if (hps::gj_smem_bytes(n3, cs, false, 0, tg, k.f32, kb) <= 227 * 1024 &&
-              (cs - 1) * hps::gj_slab(n3, cs, kb) < n3) {
-            GJChoice c;
-            c.cs = cs;
-            c.tglobal = tg;
-            c.kb = kb;
-            cands.push_back(c);
-          }
-        if (n3 >= 64) {
-          const int G0 = rule.wide ? rule.wide : (int)std::max<long long>(2, std::min<long long>((2 * 152 + P - 1) / P, n3 / 4 + 1));
-          for (int G : {G0, G0 / 2})
-            if (G >= 2) {
+      // the eliminations in the matrices' own precision, and for complex128
+      // matrices the same regimes in complex64 as the start of a refined inverse
+      for (int refined = 0; refined <= (k.f32 ? 0 : 1); refined++) {
+        const int ef = (k.f32 || refined) ? 1 : 0;
+        for (int kb : {8, 4}) {
+          const bool tg = hps::gj_smem_bytes(n3, hps::gj_max_cluster(), false, 0, false, ef, kb) > 200 * 1024;
+          for (int cs = 1; cs <= hps::gj_max_cluster(); cs *= 2)
+            // every CTA of the cluster owns at least one panel
+            if (hps::gj_smem_bytes(n3, cs, false, 0, tg, ef, kb) <= 227 * 1024 &&
+                (cs - 1) * hps::gj_slab(n3, cs, kb) < n3) {
               GJChoice c;
-              c.wide = G;
+              c.cs = cs;
+              c.tglobal = tg;
               c.kb = kb;
+              c.refined = refined != 0;
               cands.push_back(c);
             }
+          if (n3 >= 64) {
+            const int G0 = rule.wide ? rule.wide : (int)std::max<long long>(2, std::min<long long>((2 * 152 + P - 1) / P, n3 / 4 + 1));
+            for (int G : {G0, G0 / 2})
+              if (G >= 2) {
+                GJChoice c;
+                c.wide = G;
+                c.kb = kb;
+                c.refined = refined != 0;
+                cands.push_back(c);
+              }
+          }
         }
+      }
+      size_t wrb = 0;
+      for (const GJChoice &c : cands)
+        if (c.refined) wrb = wref_layout(n3, P, P0.oz).total;
+      if (wrb > wrefb) {
+        if (wrefws) cudaFree(wrefws);
+        wrefws = nullptr;
+        wrefb = 0;
+        if (cudaMalloc(&wrefws, wrb) == cudaSuccess)
+          wrefb = wrb;
+        else
+          cudaGetLastError();
       }
       auto refill = [&]() { return fill(oS, (size_t)n3 * n3 * P, n3, k.f32); };
       for (const GJChoice &c : cands) {
         float ms;
-        if (!c.wide)
+        if (c.refined) {
+          if (!wrefws) continue;
+          int nl = 0;
+          ms = time_it([&]() {
+            return w_inverse(c, buf + oS, buf + oC, n3, P, (int *)(buf + oM), (unsigned *)(buf + oSt), 0, false,
+                             (char *)wrefws, P0.oz, st, nl) == HPS_OK ? cudaSuccess : cudaErrorUnknown;
+          }, refill, 2);
+        } else if (!c.wide)
           ms = time_it([&]() { return hps::launch_gj_inverse(buf + oS, buf + oC, n3, P, (int *)(buf + oM), (unsigned *)(buf + oSt), 0, c.cs, c.tglobal, k.f32 != 0, st, c.kb); }, refill, 2);
         else
           ms = time_it([&]() { return hps::launch_gj_wide(buf + oS, buf + oC, n3, P, c.wide, (int *)(buf + oM), (unsigned *)(buf + oSt), 0, k.f32 != 0, st, c.kb); }, refill, 2);
