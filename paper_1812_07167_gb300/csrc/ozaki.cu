@@ -115,6 +115,8 @@ struct OzLayout {
   int bn;                 // output tile width: 128, or 64 for N <= 64
   int tm, tn;             // output tiles along M and N
   int gp;                 // CTAs per output tile, each summing a share of the slice pairs
+  int units, ctas;        // work units (tile, share) and CTAs launched
+  bool persistent;        // more tiles than SMs: one CTA an SM loops over them
   size_t a_off, b_off;    // byte offsets of the digit planes
   size_t ea_off, eb_off;  // byte offsets of the row / column exponents
   size_t acc_off;         // complex128 partial sums [gp][batch][tm][tn][2 bn][128]
@@ -164,8 +166,14 @@ OzLayout oz_layout(const GemmDesc &g, int nsm) {
     }
   }
   while (L.gp > 1 && (long long)g.batch * L.gp > 65535) L.gp--;
+  // one CTA an SM: with more tiles than SMs, persistent CTAs loop over the
+  // tiles and each keeps one partial-sum slab (L2-resident) for all of them
+  L.units = (int)(tiles * L.gp);
+  L.persistent = L.gp == 1 && tiles > nsm;
+  L.ctas = L.persistent ? nsm : L.units;
   L.acc_off = o;
-  o = oz_align(o + (size_t)L.gp * B * L.Mp * L.Np * 2 * sizeof(double));
+  o = oz_align(o + (L.persistent ? (size_t)nsm * TC_BM * 2 * L.bn * sizeof(double)
+                                 : (size_t)L.gp * B * L.Mp * L.Np * 2 * sizeof(double)));
   L.total = o;
   return L;
 }
@@ -503,7 +511,10 @@ struct TcArgs {
   int Mp, Np, Kp;
   int tm, tn;        // output tiles along M and N
   int gp;            // CTAs a tile (shares of the slice pairs)
-  double *acc;       // partial sums [gp][batch][tm][tn][2 BN][128] ([Re columns, Im columns][row])
+  int units;         // work units: tn tm batch gp (tile and share), tn fastest
+  int persistent;    // 1: CTAs loop over the units with one partial-sum slab each
+  double *acc;       // partial sums [gp][batch][tm][tn][2 BN][128] ([Re columns, Im columns][row]),
+                     // or [CTA][2 BN][128] when persistent
   const int *ea;     // [batch][Mp]
   const int *eb;     // [batch][Np]
   unsigned *status;  // build status word for timeouts, or null
@@ -550,9 +561,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const uint32_t sbase = (smem_u32(tc_smem_raw) + 1023u) & ~1023u;  // 128-byte swizzle atoms: 1 KB aligned
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tn = blockIdx.x, tm = blockIdx.y;
-  const int b = blockIdx.z / a.gp, grp = blockIdx.z % a.gp;
-  const int p0 = grp * OZ_PAIRS / a.gp, p1 = (grp + 1) * OZ_PAIRS / a.gp;
+  // work unit u: its output tile (tn, tm), batch entry b and share grp of the
+  // slice pairs [p0, p1); a CTA takes units blockIdx.x, + gridDim.x, ...
+  struct Unit {
+    int tn, tm, b, grp, p0, p1;
+  };
+  auto unit = [&](int u) {
+    Unit w;
+    w.tn = u % a.tn;
+    w.tm = (u / a.tn) % a.tm;
+    const int z = u / (a.tn * a.tm);
+    w.b = z / a.gp;
+    w.grp = z % a.gp;
+    w.p0 = w.grp * OZ_PAIRS / a.gp;
+    w.p1 = (w.grp + 1) * OZ_PAIRS / a.gp;
+    return w;
+  };
   const int nkb = a.Kp / TC_BK;
   constexpr int CKB = OZ_KC / TC_BK;  // k-blocks of a chunk
   const int nch = (nkb + CKB - 1) / CKB;
@@ -586,7 +610,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tma_prefetch_map(&tmB);
     int it = 0;
     bool ok = true;
-    for (int c = 0; c < nch && ok; c++) {
+    for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+     const Unit w = unit(u);
+     const int tm = w.tm, tn = w.tn, b = w.b, p0 = w.p0, p1 = w.p1;
+     for (int c = 0; c < nch && ok; c++) {
       const int kb0 = c * CKB, kb1 = min(nkb, kb0 + CKB);
       for (int p = p0; p < p1 && ok; p++) {
         int e, s;
@@ -608,6 +635,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           it++;
         }
       }
+     }
     }
     issued_sh = it;
   } else if (warp == 1 && lane == 0) {
@@ -616,7 +644,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr uint32_t id_neg = tc::idesc_bf16_f32(TC_BM, BN, true);
     int it = 0, gi = 0;
     bool ok = true;
-    for (int c = 0; c < nch && ok; c++) {
+    for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+     const Unit w = unit(u);
+     const int p0 = w.p0, p1 = w.p1;
+     for (int c = 0; c < nch && ok; c++) {
       const int kb0 = c * CKB, kb1 = min(nkb, kb0 + CKB);
       bool open = false, first = true;
       for (int p = p0; p < p1 && ok; p++) {
@@ -665,6 +696,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           open = false;
         }
       }
+     }
     }
     tc_commit(&drain_bar);
   } else if (warp >= 2) {
@@ -674,13 +706,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int q = warp & 3;      // tensor-memory lanes 32 q .. 32 q + 31 are this warp's
     const int hf = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    const int i = tm * TC_BM + row;
     const GemmDesc &g = a.g;
-    double *slab = a.acc + ((((size_t)grp * g.batch + b) * a.tm + tm) * a.tn + tn) * Cfg::kAcc;
-    const int sha = (i < a.Mp) ? __ldg(a.ea + (size_t)b * a.Mp + i) : 0;
     int gi = 0;
-    bool first = true, ok = true;
-    for (int c = 0; c < nch && ok; c++) {
+    bool ok = true;
+    for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+     const Unit w = unit(u);
+     const int tm = w.tm, tn = w.tn, b = w.b, p0 = w.p0, p1 = w.p1;
+     const int i = tm * TC_BM + row;
+     // the running sums: the CTA's own slab when persistent, else the unit's
+     double *slab = a.acc + (a.persistent ? (size_t)blockIdx.x
+                                          : (((size_t)w.grp * g.batch + b) * a.tm + tm) * a.tn + tn) * Cfg::kAcc;
+     const int sha = (i < a.Mp) ? __ldg(a.ea + (size_t)b * a.Mp + i) : 0;
+     bool first = true;
+     for (int c = 0; c < nch && ok; c++) {
       for (int p = p0; p < p1 && ok; p++) {
         int e, s;
         pair_decode(p, e, s);
@@ -792,6 +830,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         gi++;
         first = false;
       }
+     }
     }
   }
 
@@ -913,7 +952,7 @@ cudaError_t launch_product(const OzLayout &L, const TcArgs &a, const void *Ad, c
       timed = false;
     }
   if (timed) cudaEventRecord(tm->ev[2 * tm->n], st);
-  oz_tc_kernel<BN><<<dim3(L.tn, L.tm, g.batch * L.gp), TC_THREADS, TcCfg<BN>::kSmem, st>>>(mA, mB, a);
+  oz_tc_kernel<BN><<<L.ctas, TC_THREADS, TcCfg<BN>::kSmem, st>>>(mA, mB, a);
   err = cudaGetLastError();
   if (timed) {
     cudaEventRecord(tm->ev[2 * tm->n + 1], st);
@@ -971,6 +1010,8 @@ cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStr
   a.tm = L.tm;
   a.tn = L.tn;
   a.gp = L.gp;
+  a.units = L.units;
+  a.persistent = L.persistent ? 1 : 0;
   a.acc = (double *)(w + L.acc_off);
   a.ea = ea;
   a.eb = eb;
