@@ -95,6 +95,20 @@ __device__ __forceinline__ C cmul(C a, C b) {
 // alpha * acc + beta * D(i, j) (+ 1 on the diagonal), stored to C(i, j)
 template <class C>
 __device__ __forceinline__ void epilogue(const GemmDesc &g, int b, int i, int j, C acc) {
+  if (g.wide_epilogue) {
+    // the product in its arithmetic's precision, the combination in FP64
+    const double2 a = make_double2((double)acc.x, (double)acc.y);
+    double2 w = cmul(g.alpha, a);
+    if (g.D.ptr) {
+      const double2 d = ldm_rw<double2>(g.D, mat_off(g.D, b, i, j));
+      const double2 t = cmul(g.beta, d);
+      w.x += t.x;
+      w.y += t.y;
+    }
+    if (g.addI && i == j) w.x += 1;
+    stm(g.C, mat_off(g.C, b, i, j), w);
+    return;
+  }
   C v = cmul(CT<C>::make(g.alpha.x, g.alpha.y), acc);
   if (g.D.ptr) {
     C t = cmul(CT<C>::make(g.beta.x, g.beta.y), ldm_rw<C>(g.D, mat_off(g.D, b, i, j)));

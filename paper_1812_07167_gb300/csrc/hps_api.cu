@@ -649,12 +649,12 @@ bool oz_shape(int M, int N, int K, int batch, int f32, bool oz);
 int oz_launches_shape(int M, int N, int K, int batch);
 // launches of an interface inverse: the elimination, or for the refined
 // regime the conversion, the complex64 elimination, the widening copy and
-// per step the residual product, the correction product and its addition
+// per step the residual product and the correction product (its FP64 addition in the epilogue)
 int gj_launches(int n3, long long P, bool oz, const GJChoice &g) {
   if (!g.refined) return gj_elim_launches(n3, g);
   const bool ozr = oz_shape(n3, n3, n3, (int)P, 0, oz);
   const int prod = ozr ? oz_launches_shape(n3, n3, n3, (int)P) : 1;
-  return 2 + gj_elim_launches(n3, g) + (prod + 2) + ((ozr ? prod - 2 : 1) + 2);
+  return 2 + gj_elim_launches(n3, g) + (prod + 1) + ((ozr ? prod - 2 : 1) + 1);
 }
 
 // Does a product of this shape go to the tensor cores (Ozaki scheme)?
@@ -695,7 +695,7 @@ size_t oz_bytes_shape(int M, int N, int K, int batch) {
 // W in complex64, its complex64 inverse X0, the residual E, the correction
 // T, and the tensor-core product's workspace when the residual goes there.
 struct WRef {
-  size_t w32, x0, e, t, oz, total;
+  size_t w32, x0, e, oz, total;
 };
 WRef wref_layout(int n3, long long P, bool oz) {
   const size_t n2 = (size_t)n3 * n3 * P;
@@ -703,8 +703,7 @@ WRef wref_layout(int n3, long long P, bool oz) {
   L.w32 = 0;
   L.x0 = align256(8 * n2);
   L.e = L.x0 + align256(8 * n2);
-  L.t = L.e + align256(16 * n2);
-  L.oz = L.t + align256(16 * n2);
+  L.oz = L.e + align256(16 * n2);
   L.total = L.oz + (oz_shape(n3, n3, n3, (int)P, 0, oz) ? oz_bytes_shape(n3, n3, n3, (int)P) : 0);
   return L;
 }
@@ -728,7 +727,7 @@ int w_inverse(const GJChoice &g, void *W, void *Winv, int n3, int P, int *meta, 
   }
   const WRef L = wref_layout(n3, P, oz);
   void *W32 = rscr + L.w32, *X0 = rscr + L.x0;
-  double2 *E = (double2 *)(rscr + L.e), *T = (double2 *)(rscr + L.t);
+  double2 *E = (double2 *)(rscr + L.e);
   const long long s2 = (long long)n3 * n3;
   CopyBatch cb;
   cb.count = 1;
@@ -755,13 +754,14 @@ int w_inverse(const GJChoice &g, void *W, void *Winv, int n3, int P, int *meta, 
       CK(hps::launch_gemm(&gr, 1, st));
       launches++;
     }
-    GemmDesc gc = gemm(n3, n3, n3, P, mat(X0, n3, s2, nullptr, nullptr, 1), mat(E, n3, s2), mat(T, n3, s2));
+    // X += X0 E: complex64 product, FP64 addition in its epilogue
+    GemmDesc gc = gemm(n3, n3, n3, P, mat(X0, n3, s2, nullptr, nullptr, 1), mat(E, n3, s2), mat(Winv, n3, s2));
     gc.cf32 = 1;
+    gc.wide_epilogue = 1;
+    gc.D = gc.C;
+    gc.beta = make_double2(1.0, 0.0);
     CK(hps::launch_gemm(&gc, 1, st));
-    cb.d[0] = copy(n3, n3, P, mat(T, n3, s2), mat(Winv, n3, s2));
-    cb.d[0].accumulate = 1;
-    CK(hps::launch_copy(cb, st));
-    launches += 2;
+    launches += 1;
   }
   return HPS_OK;
 }
@@ -2037,7 +2037,7 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
     memset(&g, 0, sizeof(g));
     g.M = g.N = g.K = pl.n;
     g.batch = (int)chunk;
-    h->info.build_launches += nchunks * (3 + kLeafRefineSteps * (hps::oz_launches(g) + 2) - 2);
+    h->info.build_launches += nchunks * (3 + kLeafRefineSteps * (hps::oz_launches(g) + 1) - 2);
   }
   long long rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0, wref = 0;
   for (size_t j = 0; j < pl.lv.size(); j++) {

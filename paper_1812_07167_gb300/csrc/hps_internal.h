@@ -34,6 +34,9 @@ struct GemmDesc {
   double2 alpha, beta;
   int addI;
   int cf32;
+  // with cf32: alpha AB + beta D (+ I) formed in FP64 from the complex64
+  // product (a complex64 correction added to a complex128 matrix)
+  int wide_epilogue;
   int cfg;  // tile configuration for N > 8: 0 = by rule, 1..4 = 64x64, 32x32, 16x16, 64x16
   // N <= 16: scratch that lets the skinny kernel split K over several CTAs
   // (without it, products with 9 .. 16 columns take the tiled kernel)

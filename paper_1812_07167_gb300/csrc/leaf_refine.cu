@@ -5,7 +5,8 @@
 // accuracy by steps of
 //     E = I - B X      (complex128-accurate: the Ozaki product on the tensor
 //                       cores, B assembled exactly in FP64)
-//     X = X + X0 E     (the correction in complex64 arithmetic, added in FP64)
+//     X = X + X0 E     (the correction product in complex64 arithmetic, added
+//                       in FP64 in the product's epilogue)
 // Each step multiplies the residual norm by ~||I - B X0|| (~1e-5), and the
 // complex64 rounding of the correction is ~1e-7 of a term of that size, so
 // two steps reach the complex128 rounding level.  Then G X = [R | Gamma] in
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(256) leaf_GX_kernel(LeafTables lt, const LeafP
 }
 
 struct RefineLayout {
-  size_t x0, gx0, s, meta, b, e, t, oz, total;
+  size_t x0, gx0, s, meta, b, e, oz, total;
 };
 
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -193,8 +194,6 @@ RefineLayout refine_layout(const LeafTables &lt, int count) {
   o = al256(o + 16 * c * n * n);
   L.e = o;
   o = al256(o + 16 * c * n * n);
-  L.t = o;
-  o = al256(o + 16 * c * n * n);
   L.oz = o;
   GemmDesc g = plain_gemm((int)n, (int)n, (int)n, count, nullptr, 0, nullptr, 1, nullptr);
   o = al256(o + oz_workspace_bytes(g));
@@ -215,7 +214,7 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
   char *w = (char *)scr;
   const int n = lt.n, nb = lt.nb;
   void *X0 = w + L.x0;
-  double2 *Bm = (double2 *)(w + L.b), *E = (double2 *)(w + L.e), *T = (double2 *)(w + L.t);
+  double2 *Bm = (double2 *)(w + L.b), *E = (double2 *)(w + L.e);
   double2 *Xl = (double2 *)X + (size_t)leaf0 * n * n;
   double2 *GXl = (double2 *)GX + (size_t)leaf0 * n * nb;
   int nl = 0;
@@ -255,15 +254,13 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
     // (B's digits are the same in every step: split once)
     if ((err = launch_gemm_oz(g, w + L.oz, L.total - L.oz, st, status, it > 0)) != cudaSuccess) return err;
     nl += oz_launches(g, it > 0);
-    // T = X0 E in complex64 arithmetic (stored complex128), then X += T in FP64
-    GemmDesc c = plain_gemm(n, n, n, count, X0, 1, E, 0, T);
+    // X += X0 E: the product in complex64 arithmetic, the addition in FP64
+    GemmDesc c = plain_gemm(n, n, n, count, X0, 1, E, 0, Xl);
     c.cf32 = 1;
+    c.wide_epilogue = 1;
+    c.D = c.C;
+    c.beta = make_double2(1.0, 0.0);
     if ((err = launch_gemm(&c, 1, st)) != cudaSuccess) return err;
-    nl++;
-    cb.d[0].src.ptr = T;
-    cb.d[0].src.f32 = 0;
-    cb.d[0].accumulate = 1;
-    if ((err = launch_copy(cb, st)) != cudaSuccess) return err;
     nl++;
   }
   // G X = [R | Gamma]
