@@ -317,8 +317,11 @@ int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, v
  * (A: M x K, B: K x N, C: M x N; batch strides M K, K N, M N elements).
  * emulated = 0: complex128 on the FP64 pipes; 1: the Ozaki scheme on the
  * bf16 tensor cores, as the build runs its large complex128 merge products
- * (any size is accepted here).  Device arrays only; enqueued on `stream`.
- * Returns HPS_EINVAL (sizes < 1, NULL or host arrays, emulated not 0 / 1),
+ * (9 slices of 6 bits an operand, error ~2^-54 max|A_i.| max|B_.j| a term);
+ * 2: the same with 5 slices, as the build runs its complex64 products (the
+ * mixed path's lower levels): error ~5 2^-29 max|A_i.| max|B_.j| a term, the
+ * accuracy of complex64 arithmetic (any size is accepted here).  Device arrays only; enqueued on `stream`.
+ * Returns HPS_EINVAL (sizes < 1, NULL or host arrays, emulated not 0 .. 2),
  * HPS_ENOMEM (workspace), HPS_ECUDA. */
 int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, double *C, int emulated,
               void *stream);

@@ -62,7 +62,8 @@ template <int KB>
 __host__ __device__ inline int meta_ints(int n) { return n + npanels<KB>(n) * Pn<KB>::kMoveInts; }
 
 struct SmemPlan {
-  size_t T, F, x, mvbuf, col, prow, krow, red, mv, rows, srcs, scal, pinv, perm, dtab, grid, loc, cv, rsc, total;
+  size_t T, F, x, mvbuf, col, prow, krow, red, mv, rows, srcs, scal, pinv, perm, dcol, dtab, grid, loc, cv, rsc,
+      total;
 };
 
 // Panel placement: 0 = the panel being applied (T) and the one being
@@ -88,6 +89,7 @@ __host__ __device__ inline SmemPlan plan_smem(int n, int cw, bool leaf, int p, i
   s.scal = o; o = align16(o + sizeof(int) * 4);
   s.pinv = o; o = align16(o + esz);
   s.perm = o; o = align16(o + sizeof(int) * (size_t)n);
+  s.dcol = o; o = align16(o + sizeof(int) * (size_t)cw);
   if (leaf) {
     int ni = (p - 2) * (p - 2);
     s.dtab = o; o = align16(o + sizeof(double) * 4 * (size_t)p * p);
@@ -119,6 +121,7 @@ struct Shared {
   int *scal;      // [4] pivot row, zero flag
   C *pinv;  // [1] reciprocal of the pivot
   int *perm;      // [n] pivot rows, for the final column permutation
+  int *dcol;      // [cw] destination column of each own column
   int n, cw;
 };
 
@@ -140,6 +143,7 @@ __device__ Shared<C> bind(unsigned char *smem, const SmemPlan &sp, int n, int cw
   s.scal = (int *)(smem + sp.scal);
   s.pinv = (C *)(smem + sp.pinv);
   s.perm = (int *)(smem + sp.perm);
+  s.dcol = (int *)(smem + sp.dcol);
   s.n = n;
   s.cw = cw;
   return s;
@@ -540,6 +544,14 @@ __device__ __forceinline__ int dest_col(const int *perm, int n, int j) {
   return loc;
 }
 
+// s.dcol[jj] = destination of column c0 + jj, jj < ncols (s.perm filled);
+// one O(n) walk a column instead of one an element.
+template <class C>
+__device__ void fill_dcol(const Shared<C> &s, int c0, int ncols) {
+  for (int jj = threadIdx.x; jj < ncols; jj += blockDim.x) s.dcol[jj] = dest_col(s.perm, s.n, c0 + jj);
+  __syncthreads();
+}
+
 constexpr int kLeafKB = 8;  // the leaf elimination is FP64-throughput-bound
 
 struct LeafArgs {
@@ -633,12 +645,13 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
 
   const bool zero = gj_blocked<C, kLeafKB>(s, S, meta, rank);
   if (zero && tid == 0) record_status(a.status, 1u, a.level, (int)leaf);
+  fill_dcol(s, c0, ncols);
 
   // X = (D B)^{-1} D: own columns to their destination columns, scaled
   C *Xl = (C *)a.X + (size_t)leaf * n * n;
   for (int idx = tid; idx < n * ncols; idx += nthr) {
     const int i = idx % n, jj = idx / n, j = c0 + jj;
-    const int dc = dest_col(s.perm, n, j);
+    const int dc = s.dcol[jj];
     const R d = (R)rsc[dc];
     const C v = S[(size_t)j * n + i];
     Xl[(size_t)dc * n + i] = CX<C>::make(d * v.x, d * v.y);
@@ -676,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, 2) leaf_kernel(const __grid_constant
     const C ie = cmul(ieta, Sj[r]);  // - i eta x_r
     acc.x -= ie.x;
     acc.y -= ie.y;
-    const int dc = dest_col(s.perm, n, j);
+    const int dc = s.dcol[jj];
     const R d = (R)rsc[dc];
     GXl[(size_t)dc * nb + r] = CX<C>::make(d * acc.x, d * acc.y);
   }
@@ -708,10 +721,11 @@ __global__ void __launch_bounds__(kThreads, 2) gj_kernel(const __grid_constant__
   int *meta = a.meta + (size_t)mat * meta_ints<KB>(n);
   const bool zero = gj_blocked<C, KB>(s, S, meta, rank);
   if (zero && threadIdx.x == 0) record_status(a.status, 2u, a.level, mat);
+  fill_dcol(s, c0, ncols);
   C *O = (C *)a.out + (size_t)mat * n * n;
   for (int idx = threadIdx.x; idx < n * ncols; idx += blockDim.x) {
     const int i = idx % n, jj = idx / n, j = c0 + jj;
-    O[(size_t)dest_col(s.perm, n, j) * n + i] = S[(size_t)j * n + i];
+    O[(size_t)s.dcol[jj] * n + i] = S[(size_t)j * n + i];
   }
 }
 
@@ -759,10 +773,11 @@ __global__ void __launch_bounds__(kThreads, 2) gj_wide_kernel(const __grid_const
   if (phase >= np) {
     for (int t = threadIdx.x; t < n; t += blockDim.x) s.perm[t] = meta[t];
     __syncthreads();
+    fill_dcol(s, c0, nc);
     C *O = (C *)a.out + (size_t)mat * n * n;
     for (int idx = threadIdx.x; idx < n * nc; idx += blockDim.x) {
       const int i = idx % n, jj = idx / n, j = c0 + jj;
-      O[(size_t)dest_col(s.perm, n, j) * n + i] = S[(size_t)j * n + i];
+      O[(size_t)s.dcol[jj] * n + i] = S[(size_t)j * n + i];
     }
     return;
   }

@@ -646,10 +646,12 @@ bool choose_gj_rule(int n3, long long P, int f32, GJChoice &g) {
 
 int gj_elim_launches(int n3, const GJChoice &g) { return g.wide ? hps::gj_wide_launches(n3, g.kb) : 1; }
 bool oz_shape(int M, int N, int K, int batch, int f32, bool oz);
-int oz_launches_shape(int M, int N, int K, int batch);
+int oz_launches_shape(int M, int N, int K, int batch, int f32 = 0);
 // launches of an interface inverse: the elimination, or for the refined
 // regime the conversion, the complex64 elimination, the widening copy and
-// per step the residual product and the correction product (its FP64 addition in the epilogue)
+// per step the residual product and the correction product (its FP64
+// addition in the epilogue); the second step reuses the first one's split of
+// W where the residual runs on the tensor cores
 int gj_launches(int n3, long long P, bool oz, const GJChoice &g) {
   if (!g.refined) return gj_elim_launches(n3, g);
   const bool ozr = oz_shape(n3, n3, n3, (int)P, 0, oz);
@@ -657,9 +659,10 @@ int gj_launches(int n3, long long P, bool oz, const GJChoice &g) {
   return 2 + gj_elim_launches(n3, g) + (prod + 1) + ((ozr ? prod - 2 : 1) + 1);
 }
 
-// Does a product of this shape go to the tensor cores (Ozaki scheme)?
+// Does a product of this shape go to the tensor cores (Ozaki scheme: 9
+// slices an operand in complex128, 4 for the complex64 products)?
 bool oz_shape(int M, int N, int K, int batch, int f32, bool oz) {
-  if (!oz || f32) return false;
+  if (!oz) return false;
   int v;
   if (tuned(TuneKey{0, M, N, K, batch, f32}, v)) return v == 5;
   GemmDesc g;
@@ -668,32 +671,36 @@ bool oz_shape(int M, int N, int K, int batch, int f32, bool oz) {
   g.N = N;
   g.K = K;
   g.batch = batch;
+  g.cf32 = f32;
   return hps::oz_eligible(g);
 }
 
-int oz_launches_shape(int M, int N, int K, int batch) {
+int oz_launches_shape(int M, int N, int K, int batch, int f32) {
   GemmDesc g;
   memset(&g, 0, sizeof(g));
   g.M = M;
   g.N = N;
   g.K = K;
   g.batch = batch;
+  g.cf32 = f32;
   return hps::oz_launches(g);
 }
 
-size_t oz_bytes_shape(int M, int N, int K, int batch) {
+size_t oz_bytes_shape(int M, int N, int K, int batch, int f32 = 0) {
   GemmDesc g;
   memset(&g, 0, sizeof(g));
   g.M = M;
   g.N = N;
   g.K = K;
   g.batch = batch;
+  g.cf32 = f32;
   return hps::oz_workspace_bytes(g);
 }
 
 // Scratch of the refined interface inverse of P complex128 n3 x n3 matrices:
-// W in complex64, its complex64 inverse X0, the residual E, the correction
-// T, and the tensor-core product's workspace when the residual goes there.
+// W in complex64, its complex64 inverse X0, the residual E, and the
+// tensor-core workspace of the residual product where that goes there (it
+// keeps W's digits for the second step).
 struct WRef {
   size_t w32, x0, e, oz, total;
 };
@@ -754,7 +761,9 @@ int w_inverse(const GJChoice &g, void *W, void *Winv, int n3, int P, int *meta, 
       CK(hps::launch_gemm(&gr, 1, st));
       launches++;
     }
-    // X += X0 E: complex64 product, FP64 addition in its epilogue
+    // X += X0 E: complex64 product (elementwise complex64 arithmetic: its
+    // error is amplified by cond(W) in the next residual), FP64 addition in
+    // its epilogue
     GemmDesc gc = gemm(n3, n3, n3, P, mat(X0, n3, s2, nullptr, nullptr, 1), mat(E, n3, s2), mat(Winv, n3, s2));
     gc.cf32 = 1;
     gc.wide_epilogue = 1;
@@ -781,12 +790,13 @@ int merge_launches(int n1, int n2, int n3, int nt, int P, int f32, bool oz, cons
   merge_products(n1, n2, n3, nt, mnk);
   int n = 1 + gj_launches(n3, P, oz, gj);
   for (int q = 0; q < 4; q++)
-    n += oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], P, f32, oz) ? oz_launches_shape(mnk[q][0], mnk[q][1], mnk[q][2], P)
-                                                               : 1;
+    n += oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], P, f32, oz)
+             ? oz_launches_shape(mnk[q][0], mnk[q][1], mnk[q][2], P, f32)
+             : 1;
   const bool a = oz_shape(mnk[4][0], mnk[4][1], mnk[4][2], P, f32, oz);
   const bool b = oz_shape(mnk[5][0], mnk[5][1], mnk[5][2], P, f32, oz);
-  n += (a ? oz_launches_shape(mnk[4][0], mnk[4][1], mnk[4][2], P) : 0) +
-       (b ? oz_launches_shape(mnk[5][0], mnk[5][1], mnk[5][2], P) : 0) + ((!a || !b) ? 1 : 0);
+  n += (a ? oz_launches_shape(mnk[4][0], mnk[4][1], mnk[4][2], P, f32) : 0) +
+       (b ? oz_launches_shape(mnk[5][0], mnk[5][1], mnk[5][2], P, f32) : 0) + ((!a || !b) ? 1 : 0);
   return n;
 }
 
@@ -926,8 +936,8 @@ static int solve_gemm(GemmDesc *gd, int nd, cudaStream_t st, char *wb, const Sol
     }
     if (oz && ws.oz_bytes && oz_shape(g.M, g.N, g.K, g.batch, g.cf32, true)) {
       int chunk = g.batch;
-      while (chunk > 1 && oz_bytes_shape(g.M, g.N, g.K, chunk) > ws.oz_bytes) chunk = (chunk + 1) / 2;
-      if (oz_bytes_shape(g.M, g.N, g.K, chunk) <= ws.oz_bytes) {
+      while (chunk > 1 && oz_bytes_shape(g.M, g.N, g.K, chunk, g.cf32) > ws.oz_bytes) chunk = (chunk + 1) / 2;
+      if (oz_bytes_shape(g.M, g.N, g.K, chunk, g.cf32) <= ws.oz_bytes) {
         auto shift = [](Mat m, long long b) {
           if (m.ptr) m.ptr = elem(m.ptr, b * m.stride, m.f32);
           return m;
@@ -1817,7 +1827,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
       for (const BuildRun &r : runs[j])
         for (int q = 0; q < 6; q++)
           if (oz_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P, r.f32, P0.oz))
-            oz_bytes = std::max(oz_bytes, oz_bytes_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P));
+            oz_bytes = std::max(oz_bytes, oz_bytes_shape(mnk[q][0], mnk[q][1], mnk[q][2], r.P, r.f32));
     }
     // the refined interface inverses' scratch
     size_t wref_bytes = 0;
@@ -2032,12 +2042,8 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
     lt.ni = pl.ni;
     leaf_scr = (long long)hps::leaf_refined_scratch_bytes(lt, (int)chunk);
     // per chunk: complex64 inverse, B, X = X0, per step the residual product
-    // and the correction (product and add), G X
-    GemmDesc g;
-    memset(&g, 0, sizeof(g));
-    g.M = g.N = g.K = pl.n;
-    g.batch = (int)chunk;
-    h->info.build_launches += nchunks * (3 + kLeafRefineSteps * (hps::oz_launches(g) + 1) - 2);
+    // and the correction (product and FP64 add), G X
+    h->info.build_launches += nchunks * (hps::leaf_refined_launches(lt, (int)chunk, kLeafRefineSteps) - 1);
   }
   long long rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0, wref = 0;
   for (size_t j = 0; j < pl.lv.size(); j++) {
@@ -2062,11 +2068,12 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
 
 int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, double *C, int emulated,
               void *stream) {
-  if (M < 1 || N < 1 || K < 1 || batch < 1 || batch > 65535 || (emulated != 0 && emulated != 1)) return HPS_EINVAL;
+  if (M < 1 || N < 1 || K < 1 || batch < 1 || batch > 65535 || emulated < 0 || emulated > 2) return HPS_EINVAL;
   if (!A || !B || !C || !is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C)) return HPS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   GemmDesc g = gemm(M, N, K, batch, mat(A, M, (long long)M * K), mat(B, K, (long long)K * N),
                     mat(C, M, (long long)M * N));
+  g.cf32 = emulated == 2 ? 1 : 0;  // the 4-slice product of the complex64 products
   if (!emulated) {
     CK(hps::launch_gemm(&g, 1, st));
     return HPS_OK;
@@ -2305,7 +2312,7 @@ int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned) {
       g.cf32 = k.f32;
       auto none = [&]() { return cudaSuccess; };
       for (int cand = 1; cand <= 5; cand++) {
-        if (cand == 5 && (k.f32 || !P0.oz || k.K < 32 || k.batch > 65535)) continue;
+        if (cand == 5 && (!P0.oz || k.K < 32 || k.batch > 65535)) continue;
         float ms;
         if (cand == 5) {
           const size_t need = hps::oz_workspace_bytes(g);

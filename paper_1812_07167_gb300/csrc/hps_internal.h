@@ -138,11 +138,13 @@ __device__ __forceinline__ void chain_enter() {
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st);
 
-// Complex128 GEMM emulated on the bf16 tensor cores (Ozaki scheme, 9 slices
-// of 6 bits per operand; accuracy ~2^-54 max|A_i.| max|B_.j| per term), the
-// slice products by tcgen05.mma from TMA-staged tiles.  Same semantics as
-// launch_gemm for one descriptor with cf32 == 0; needs a 256-byte aligned
-// device workspace of oz_workspace_bytes(g).  oz_launches(g) launches (4, or
+// Complex GEMM emulated on the bf16 tensor cores (Ozaki scheme, slices of 6
+// bits per operand: 9 with cf32 == 0, accuracy ~2^-54 max|A_i.| max|B_.j|
+// per term; 5 with cf32 set, ~5 2^-29, the accuracy of complex64 arithmetic),
+// the slice products by tcgen05.mma from TMA-staged tiles.  Same semantics
+// as launch_gemm for one descriptor (the epilogue is always formed in FP64,
+// as with wide_epilogue); needs a 256-byte aligned device workspace of
+// oz_workspace_bytes(g).  oz_launches(g) launches (4, or
 // 5 when the slice pairs are split over several CTAs a tile).  A pipeline
 // wait that gives up (2 s) records code 3 in *status (if given) and leaves C
 // unspecified.  reuse_a: the workspace already holds A's digits from the
@@ -151,7 +153,8 @@ cudaError_t launch_gemm(const GemmDesc *descs, int ndesc, cudaStream_t st);
 // Per-launch CUDA events around the product kernel (oz_tc_kernel) of the
 // tensor-core products launched by this host thread while a timer is set:
 // product k records ev[2k] before and ev[2k + 1] after its product kernel on
-// the product's stream, and flops[k] = its bf16 slice flops (360 M N K batch).
+// the product's stream, and flops[k] = its bf16 slice flops (8 pairs M N K
+// batch: 360 M N K batch for 9 slices, 120 for 5).
 struct OzTimer {
   cudaEvent_t *ev;  // 2 cap events, created on first use (null until then)
   double *flops;
@@ -198,8 +201,9 @@ size_t lu_meta_ints(int n);
 // [leaf0, leaf0 + count) ([leaf][n][n], [leaf][n][nb] column-major, indexed
 // by the absolute leaf number, like launch_leaf).  scr: 256-byte aligned
 // device scratch of leaf_refined_scratch_bytes(lt, count).  *launches is
-// increased by the kernels launched.
+// increased by the kernels launched, leaf_refined_launches(lt, count, steps).
 size_t leaf_refined_scratch_bytes(const LeafTables &lt, int count);
+int leaf_refined_launches(const LeafTables &lt, int count, int steps);
 cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0, int count,
                                 void *X, void *GX, void *scr, size_t scr_bytes, unsigned int *status, int level,
                                 int cs32, int steps, cudaStream_t st, int *launches);

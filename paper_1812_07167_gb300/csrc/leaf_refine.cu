@@ -205,6 +205,13 @@ RefineLayout refine_layout(const LeafTables &lt, int count) {
 
 size_t leaf_refined_scratch_bytes(const LeafTables &lt, int count) { return refine_layout(lt, count).total; }
 
+int leaf_refined_launches(const LeafTables &lt, int count, int steps) {
+  GemmDesc g = plain_gemm(lt.n, lt.n, lt.n, count, nullptr, 0, nullptr, 1, nullptr);
+  int n = 4;  // X0, B, X = X0, G X
+  for (int it = 0; it < steps; it++) n += oz_launches(g, it > 0) + 1;  // residual, correction
+  return n;
+}
+
 cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0, int count,
                                 void *X, void *GX, void *scr, size_t scr_bytes, unsigned int *status, int level,
                                 int cs32, int steps, cudaStream_t st, int *launches) {
@@ -255,6 +262,10 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
     if ((err = launch_gemm_oz(g, w + L.oz, L.total - L.oz, st, status, it > 0)) != cudaSuccess) return err;
     nl += oz_launches(g, it > 0);
     // X += X0 E: the product in complex64 arithmetic, the addition in FP64
+    // (the error of this product is amplified by cond(B) in the next
+    // residual, so it stays in elementwise complex64 arithmetic: a 4-slice
+    // tensor-core product, accurate relative to row and column maxima only,
+    // left 3e-8 in u)
     GemmDesc c = plain_gemm(n, n, n, count, X0, 1, E, 0, Xl);
     c.cf32 = 1;
     c.wide_epilogue = 1;

@@ -73,8 +73,13 @@ namespace hps {
 
 namespace {
 
-constexpr int OZ_S = 9;                          // slices per operand (6 bits each)
-constexpr int OZ_PAIRS = OZ_S * (OZ_S + 1) / 2;  // slice pairs with s + t < S
+// Slices per operand (6 bits each): 9 for complex128 products (every term
+// to ~2^-54 of its row and column scale), 5 for the products wanted to
+// complex64 accuracy (the cf32 products: ~5 2^-29 a term, at or below the
+// rounding of complex64 arithmetic), which take 15 slice pairs instead of 45.
+constexpr int OZ_S = 9;
+constexpr int OZ_S32 = 5;
+inline int oz_slices(const GemmDesc &g) { return g.cf32 ? OZ_S32 : OZ_S; }
 constexpr int OZ_KC = 896;                       // K per exact FP32 accumulation of a shift group
 constexpr int TC_BM = 128, TC_BK = 64;           // tile rows; k per stage (one 128-byte swizzle row)
 constexpr int TC_EPI_WARPS = 8;
@@ -112,6 +117,7 @@ int num_sms() {
 
 struct OzLayout {
   int Mp, Np, Kp;         // padded sizes (multiples of 128, BN, 64)
+  int S, npairs;          // slices per operand; slice pairs (s + t < S)
   int bn;                 // output tile width: 128, or 64 for N <= 64
   int tm, tn;             // output tiles along M and N
   int gp;                 // CTAs per output tile, each summing a share of the slice pairs
@@ -138,12 +144,14 @@ OzLayout oz_layout(const GemmDesc &g, int nsm) {
   L.Kp = (g.K + TC_BK - 1) / TC_BK * TC_BK;
   L.tm = L.Mp / TC_BM;
   L.tn = L.Np / L.bn;
+  L.S = oz_slices(g);
+  L.npairs = L.S * (L.S + 1) / 2;
   const size_t B = (size_t)g.batch;
   size_t o = 0;
   L.a_off = o;
-  o = oz_align(o + B * OZ_S * 2 * (size_t)L.Mp * L.Kp * sizeof(__nv_bfloat16));
+  o = oz_align(o + B * L.S * 2 * (size_t)L.Mp * L.Kp * sizeof(__nv_bfloat16));
   L.b_off = o;
-  o = oz_align(o + B * OZ_S * 2 * (size_t)L.Np * L.Kp * sizeof(__nv_bfloat16));
+  o = oz_align(o + B * L.S * 2 * (size_t)L.Np * L.Kp * sizeof(__nv_bfloat16));
   L.ea_off = o;
   o = oz_align(o + B * (size_t)L.Mp * sizeof(int));
   L.eb_off = o;
@@ -155,7 +163,7 @@ OzLayout oz_layout(const GemmDesc &g, int nsm) {
   L.gp = 1;
   if (tiles < nsm) {
     double best = 0.0;
-    for (int q = 1; q <= 9; q++) {
+    for (int q = 1; q <= std::max(1, L.npairs / 5); q++) {
       const long long ctas = tiles * q;
       const long long waves = (ctas + nsm - 1) / nsm;
       const double eff = (double)ctas / (double)(waves * nsm);
@@ -219,11 +227,12 @@ __device__ __forceinline__ int oz_shift(unsigned long long m) {
 
 // D = round(v 2^(6S - sh)) for |v 2^-sh| < 1/2 (so |D| <= 2^53), from the
 // fields of v: v = +-M 2^(E' - 1075) with the 53-bit significand M.
+template <int S>
 __device__ __forceinline__ long long oz_fixed(double v, int sh) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const int E = (int)((b >> 52) & 0x7ff);
   const unsigned long long M = (b & 0xfffffffffffffull) | (E ? (1ull << 52) : 0ull);
-  const int t = (E ? E : 1) - 1075 + 6 * OZ_S - sh;  // D = round(M 2^t)
+  const int t = (E ? E : 1) - 1075 + 6 * S - sh;  // D = round(M 2^t)
   long long D;
   if (M == 0 || t < -62)
     D = 0;
@@ -236,9 +245,10 @@ __device__ __forceinline__ long long oz_fixed(double v, int sh) {
 
 // the S balanced base-64 digits of D, most significant first:
 // D = sum_s d_s 64^(S-1-s), d_s in [-32, 32]
-__device__ __forceinline__ void oz_digits(long long D, int (&d)[OZ_S]) {
+template <int S>
+__device__ __forceinline__ void oz_digits(long long D, int (&d)[S]) {
 #pragma unroll
-  for (int s = OZ_S - 1; s > 0; s--) {
+  for (int s = S - 1; s > 0; s--) {
     const int v = (int)((D + 32) & 63) - 32;
     d[s] = v;
     D = (D - v) >> 6;
@@ -249,6 +259,7 @@ __device__ __forceinline__ void oz_digits(long long D, int (&d)[OZ_S]) {
 // Digits of B, a warp per column, lanes over k (neighbouring k are
 // neighbouring in the column-major operands): the column's exponent, then its
 // digits ([column][k], k contiguous).  Padding columns and k get zeros.
+template <int S>
 __global__ void __launch_bounds__(256) oz_split_b_kernel(const __grid_constant__ GemmDesc g, int Np, int Kp,
                                                          __nv_bfloat16 *digits, int *expo) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -269,15 +280,15 @@ __global__ void __launch_bounds__(256) oz_split_b_kernel(const __grid_constant__
   const int sh = oz_shift(mx);
   if (lane == 0) expo[(size_t)b * Np + j] = sh;
   const size_t plane = (size_t)Np * Kp;
-  __nv_bfloat16 *base = digits + (size_t)b * OZ_S * 2 * plane + (size_t)j * Kp;
+  __nv_bfloat16 *base = digits + (size_t)b * S * 2 * plane + (size_t)j * Kp;
   for (int k = lane; k < Kp; k += 32) {
     double2 v = make_double2(0.0, 0.0);
     if (live && k < g.K) v = oz_ldb(g, b, k, j);
-    int dr[OZ_S], di[OZ_S];
-    oz_digits(oz_fixed(v.x, sh), dr);
-    oz_digits(oz_fixed(v.y, sh), di);
+    int dr[S], di[S];
+    oz_digits<S>(oz_fixed<S>(v.x, sh), dr);
+    oz_digits<S>(oz_fixed<S>(v.y, sh), di);
 #pragma unroll
-    for (int q = 0; q < OZ_S; q++) {
+    for (int q = 0; q < S; q++) {
       base[(size_t)(2 * q) * plane + k] = __int2bfloat16_rn(dr[q]);
       base[(size_t)(2 * q + 1) * plane + k] = __int2bfloat16_rn(di[q]);
     }
@@ -310,9 +321,10 @@ __global__ void __launch_bounds__(256) oz_expo_a_kernel(const __grid_constant__ 
 // shared memory, and each row's 32 digits leave as four 16-byte stores.
 // Padding rows and k get zeros.
 constexpr int OZA_R = 32, OZA_K = 32, OZA_LD = OZA_K + 8;  // shared row: 80 bytes (16-byte aligned)
+template <int S>
 __global__ void __launch_bounds__(256) oz_split_a_kernel(const __grid_constant__ GemmDesc g, int Mp, int Kp,
                                                          __nv_bfloat16 *digits, const int *expo) {
-  __shared__ __align__(16) __nv_bfloat16 tile[2 * OZ_S][OZA_R][OZA_LD];
+  __shared__ __align__(16) __nv_bfloat16 tile[2 * S][OZA_R][OZA_LD];
   const int r = threadIdx.x & 31, kq = threadIdx.x >> 5;
   const int i0 = blockIdx.x * OZA_R, k0 = blockIdx.y * OZA_K, b = blockIdx.z;
   const int i = i0 + r;
@@ -321,20 +333,20 @@ __global__ void __launch_bounds__(256) oz_split_a_kernel(const __grid_constant__
     const int k = k0 + kk;
     double2 v = make_double2(0.0, 0.0);
     if (i < g.M && k < g.K) v = oz_lda(g, b, i, k);
-    int dr[OZ_S], di[OZ_S];
-    oz_digits(oz_fixed(v.x, sh), dr);
-    oz_digits(oz_fixed(v.y, sh), di);
+    int dr[S], di[S];
+    oz_digits<S>(oz_fixed<S>(v.x, sh), dr);
+    oz_digits<S>(oz_fixed<S>(v.y, sh), di);
 #pragma unroll
-    for (int q = 0; q < OZ_S; q++) {
+    for (int q = 0; q < S; q++) {
       tile[2 * q][r][kk] = __int2bfloat16_rn(dr[q]);
       tile[2 * q + 1][r][kk] = __int2bfloat16_rn(di[q]);
     }
   }
   __syncthreads();
   const size_t plane = (size_t)Mp * Kp;
-  __nv_bfloat16 *base = digits + (size_t)b * OZ_S * 2 * plane;
+  __nv_bfloat16 *base = digits + (size_t)b * S * 2 * plane;
   constexpr int VPR = OZA_K / 8;  // 16-byte vectors a row
-  for (int v = threadIdx.x; v < 2 * OZ_S * OZA_R * VPR; v += 256) {
+  for (int v = threadIdx.x; v < 2 * S * OZA_R * VPR; v += 256) {
     const int pl = v / (OZA_R * VPR), rem = v % (OZA_R * VPR), row = rem / VPR, c = rem % VPR;
     const uint4 val = *reinterpret_cast<const uint4 *>(&tile[pl][row][c * 8]);
     *reinterpret_cast<uint4 *>(base + (size_t)pl * plane + (size_t)(i0 + row) * Kp + k0 + c * 8) = val;
@@ -509,6 +521,7 @@ __device__ __forceinline__ void oz_out(const TcArgs &a, int b, int i, int j, int
 struct TcArgs {
   GemmDesc g;
   int Mp, Np, Kp;
+  int S, npairs;     // slices per operand, slice pairs taken
   int tm, tn;        // output tiles along M and N
   int gp;            // CTAs a tile (shares of the slice pairs)
   int units;         // work units: tn tm batch gp (tile and share), tn fastest
@@ -573,8 +586,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int z = u / (a.tn * a.tm);
     w.b = z / a.gp;
     w.grp = z % a.gp;
-    w.p0 = w.grp * OZ_PAIRS / a.gp;
-    w.p1 = (w.grp + 1) * OZ_PAIRS / a.gp;
+    w.p0 = w.grp * a.npairs / a.gp;
+    w.p1 = (w.grp + 1) * a.npairs / a.gp;
     return w;
   };
   const int nkb = a.Kp / TC_BK;
@@ -618,7 +631,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int p = p0; p < p1 && ok; p++) {
         int e, s;
         pair_decode(p, e, s);
-        const int zA = (b * OZ_S + s) * 2, zB = (b * OZ_S + (e - s)) * 2;
+        const int zA = (b * a.S + s) * 2, zB = (b * a.S + (e - s)) * 2;
         for (int kb = kb0; kb < kb1; kb++) {
           const int st = it % S_;
           const uint32_t ph = (uint32_t)(it / S_) & 1u;
@@ -938,8 +951,8 @@ template <int BN>
 cudaError_t launch_product(const OzLayout &L, const TcArgs &a, const void *Ad, const void *Bd, cudaStream_t st) {
   const GemmDesc &g = a.g;
   CUtensorMap mA, mB;
-  if (!digit_map(&mA, Ad, L.Kp, L.Mp, (long long)g.batch * OZ_S * 2, TC_BM) ||
-      !digit_map(&mB, Bd, L.Kp, L.Np, (long long)g.batch * OZ_S * 2, BN))
+  if (!digit_map(&mA, Ad, L.Kp, L.Mp, (long long)g.batch * L.S * 2, TC_BM) ||
+      !digit_map(&mB, Bd, L.Kp, L.Np, (long long)g.batch * L.S * 2, BN))
     return cudaErrorInvalidValue;
   cudaError_t err =
       cudaFuncSetAttribute(oz_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<BN>::kSmem);
@@ -956,7 +969,7 @@ cudaError_t launch_product(const OzLayout &L, const TcArgs &a, const void *Ad, c
   err = cudaGetLastError();
   if (timed) {
     cudaEventRecord(tm->ev[2 * tm->n + 1], st);
-    tm->flops[tm->n] = 360.0 * g.M * g.N * g.K * g.batch;  // 45 slice pairs x 4 real products
+    tm->flops[tm->n] = 8.0 * L.npairs * g.M * g.N * g.K * g.batch;  // slice pairs x 4 real products
     tm->n++;
   }
   if (err != cudaSuccess || L.gp == 1) return err;
@@ -975,8 +988,8 @@ int oz_launches(const GemmDesc &g, bool reuse_a) {
 
 bool oz_eligible(const GemmDesc &g) {
   // worth the split passes only for sizeable products whose tiles are mostly
-  // live (M padded to 128, N to 64 or 128); complex128 arithmetic only
-  return !g.cf32 && g.K >= 64 && g.M >= 96 && g.N >= 48 && g.batch <= 65535 &&
+  // live (M padded to 128, N to 64 or 128)
+  return g.K >= 64 && g.M >= 96 && g.N >= 48 && g.batch <= 65535 &&
          (double)g.M * g.N * g.K * g.batch >= (double)(1 << 26);
 }
 
@@ -991,15 +1004,24 @@ cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStr
   __nv_bfloat16 *Ad = (__nv_bfloat16 *)(w + L.a_off), *Bd = (__nv_bfloat16 *)(w + L.b_off);
   int *ea = (int *)(w + L.ea_off), *eb = (int *)(w + L.eb_off);
   cudaError_t err = cudaSuccess;
+  const bool s32 = L.S == OZ_S32;
   if (!reuse_a) {
     oz_expo_a_kernel<<<dim3(L.Mp / 32, g.batch), 256, 0, st>>>(g, L.Mp, ea);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    oz_split_a_kernel<<<dim3(L.Mp / OZA_R, L.Kp / OZA_K, g.batch), 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
+    const dim3 ga(L.Mp / OZA_R, L.Kp / OZA_K, g.batch);
+    if (s32)
+      oz_split_a_kernel<OZ_S32><<<ga, 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
+    else
+      oz_split_a_kernel<OZ_S><<<ga, 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
-  oz_split_b_kernel<<<dim3((L.Np + 7) / 8, g.batch), 256, 0, st>>>(g, L.Np, L.Kp, Bd, eb);
+  const dim3 gb((L.Np + 7) / 8, g.batch);
+  if (s32)
+    oz_split_b_kernel<OZ_S32><<<gb, 256, 0, st>>>(g, L.Np, L.Kp, Bd, eb);
+  else
+    oz_split_b_kernel<OZ_S><<<gb, 256, 0, st>>>(g, L.Np, L.Kp, Bd, eb);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   TcArgs a;
@@ -1007,6 +1029,8 @@ cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStr
   a.Mp = L.Mp;
   a.Np = L.Np;
   a.Kp = L.Kp;
+  a.S = L.S;
+  a.npairs = L.npairs;
   a.tm = L.tm;
   a.tn = L.tn;
   a.gp = L.gp;

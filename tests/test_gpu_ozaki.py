@@ -1,7 +1,8 @@
 """The complex128 product emulated on the bf16 tensor cores (Ozaki scheme)
 against the FP64-pipe product and against numpy, on shapes that span tiles
 with ragged edges, and on rows and columns of very different magnitudes (the
-scheme scales each row of A and column of B separately)."""
+scheme scales each row of A and column of B separately); the 5-slice form
+(complex64 accuracy) against its error bound."""
 import numpy as np
 import pytest
 
@@ -60,10 +61,35 @@ def test_rows_and_columns_of_wide_dynamic_range():
     assert np.all(np.abs(Ce - ref) <= bound)
 
 
+# the 5-slice product (the build's complex64 products: the mixed path's lower
+# levels): every entry within K 2^-26 max|A_i.| max|B_.j| of the exact
+# product, the complex64 level, also for rows and columns of very different
+# magnitudes; and truly a 5-slice product (far from the 9-slice accuracy)
+@pytest.mark.parametrize("M,N,K,batch,wide", [(128, 128, 64, 1, False), (100, 37, 83, 3, False),
+                                              (252, 252, 252, 4, False), (896, 512, 600, 1, False),
+                                              (300, 200, 1000, 1, False), (96, 80, 128, 1, True)])
+def test_five_slice_product_has_complex64_accuracy(M, N, K, batch, wide):
+    rng = np.random.default_rng(M + 3 * K)
+    A = _rand((batch, K, M), rng)
+    B = _rand((batch, N, K), rng)
+    if wide:
+        A = A * (10.0 ** rng.integers(-12, 12, size=M))[None, None, :]
+        B = B * (10.0 ** rng.integers(-12, 12, size=N))[None, :, None]
+    C4 = _run(A, B, 2)
+    ref = np.einsum("bki,bjk->bji", A, B)
+    ra = np.abs(A).max(axis=1)  # [batch][M]: max over k of row i of A
+    cb = np.abs(B).max(axis=2)  # [batch][N]: max over k of column j of B
+    scale = cb[:, :, None] * ra[:, None, :]
+    err = np.abs(C4 - ref) / scale
+    assert err.max() <= K * 2.0 ** -26
+    assert err.max() > 2.0 ** -45
+
+
 def test_zero_operand_gives_zero():
     A = np.zeros((1, 70, 40), complex)
     B = _rand((1, 50, 70), np.random.default_rng(1))
     assert np.all(_run(A, B, 1) == 0)
+    assert np.all(_run(A, B, 2) == 0)
 
 
 @pytest.mark.parametrize("m,p,kappa", [(16, 16, 80.0), (32, 12, 60.0)])
