@@ -1,6 +1,6 @@
 // Leaf step (Sec. 2.1) in complex128 by a refined inverse: the leaf matrix
-// B is inverted in complex64 (blocked Gauss-Jordan, leaf_kernel in its
-// complex64 form: X0 ~ B^-1 to ~1e-5 for the row-equilibrated leaf matrices,
+// B is inverted in complex64 (blocked Gauss-Jordan with 32-column panels,
+// leaf_gj32.cu: X0 ~ B^-1 to ~1e-5 for the row-equilibrated leaf matrices,
 // whose condition numbers are ~5e2), and X0 is refined to complex128
 // accuracy by steps of
 //     E = I - B X      (complex128-accurate: the Ozaki product on the tensor
@@ -225,10 +225,15 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
   double2 *Xl = (double2 *)X + (size_t)leaf0 * n * n;
   double2 *GXl = (double2 *)GX + (size_t)leaf0 * n * nb;
   int nl = 0;
-  // X0: the complex64 inverse (its complex64 G X0 is not used)
-  cudaError_t err = launch_leaf(lt, probs, nprob, leaf0, count, (float2 *)X0 - (size_t)leaf0 * n * n,
-                                (float2 *)(w + L.gx0) - (size_t)leaf0 * n * nb, w + L.s, (int *)(w + L.meta),
-                                status, level, cs32, true, st);
+  // X0: the complex64 inverse (32-column panels, one CTA a leaf; the
+  // cluster kernel where the panel does not fit; its G X0 is not used)
+  cudaError_t err =
+      gj32_supported(lt)
+          ? launch_leaf_gj32(lt, probs, nprob, leaf0, count, (float2 *)X0 - (size_t)leaf0 * n * n, w + L.s, status,
+                             level, st)
+          : launch_leaf(lt, probs, nprob, leaf0, count, (float2 *)X0 - (size_t)leaf0 * n * n,
+                        (float2 *)(w + L.gx0) - (size_t)leaf0 * n * nb, w + L.s, (int *)(w + L.meta), status, level,
+                        cs32, true, st);
   if (err != cudaSuccess) return err;
   nl++;
   // B in FP64

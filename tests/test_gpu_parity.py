@@ -365,12 +365,16 @@ def test_leaf_lu_every_cluster_size(cs, monkeypatch):
     h.free()
 
 
-@pytest.mark.parametrize("p", [4, 5, 9, 20, 24])
-def test_leaf_lu_orders(p):
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("p", [4, 5, 9, 17, 18, 20, 24])
+def test_leaf_orders(p, form):
     """Leaf orders whose n = p^2 - 4 leaves every kind of ragged last panel
-    (12, 21, 77, 396, 572) and the largest leaf the kernels take."""
+    (12, 21, 77, 285, 320, 396, 572) and the largest leaf the kernels take;
+    in the inverse form n <= 256 and 256 < n <= 384 take the two register
+    blockings of the 32-column complex64 elimination, larger n the cluster
+    kernel."""
     m, kappa, eta = 2, 6.0 + p, 5.0 + 1.0j
-    pr, opr = _pair(m, p, kappa, eta, (0.0, 1.0, 0.0, 0.75))
+    pr, opr = _pair(m, p, kappa, eta, (0.0, 1.0, 0.0, 0.75), form)
     c, s, t = W.random_data(m, p, kappa, eta, seed=p, nrhs=2)
     h = gpu_build(pr, c)
     u = gpu_solve(h, s, t)
