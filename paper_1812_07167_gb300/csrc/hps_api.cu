@@ -1740,6 +1740,10 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
       } else if (P0.leaf_refined) {
         CK(hps::launch_leaf_refined(lt, d_probs, K, l0, cnt, base + oX, base + oGX, lscr, rscr, d_status, Lmax,
                                     lcs32, kLeafRefineSteps, st, &launches));
+      } else if (lf && hps::gj32_supported(lt)) {
+        // complex64 inverse form: 32-column panels, one CTA a leaf
+        CK(hps::launch_leaf_gj32(lt, d_probs, K, l0, cnt, base + oX, base + oGX, lscr, d_status, Lmax, st));
+        launches++;
       } else {
         CK(hps::launch_leaf(lt, d_probs, K, l0, cnt, base + oX, base + oGX, lscr, lmeta, d_status, Lmax, lcs,
                             lf != 0, st));

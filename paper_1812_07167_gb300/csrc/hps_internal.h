@@ -204,13 +204,14 @@ size_t lu_meta_ints(int n);
 // increased by the kernels launched, leaf_refined_launches(lt, count, steps).
 // Complex64 inverse of the leaf matrices, one CTA a leaf, 32-column panels
 // (leaf_gj32.cu): X0 = (D B)^{-1} D of leaves [leaf0, leaf0 + count) into X0
-// ([leaf][n][n] complex64 column-major, by absolute leaf number), with the
-// scratch S ([count][n][n] complex64).  For n <= 384 (gj32_supported); a zero
-// pivot records code 1 in *status.
+// ([leaf][n][n] complex64 column-major, by absolute leaf number) and, if GX
+// is not null, G X0 into GX ([leaf][n][nb]), with the scratch S
+// ([count][n][n] complex64).  For n <= 384 (gj32_supported); a zero pivot
+// records code 1 in *status.
 bool gj32_supported(const LeafTables &lt);
 size_t gj32_smem_bytes(const LeafTables &lt);
 cudaError_t launch_leaf_gj32(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0, int count,
-                             void *X0, void *S, unsigned int *status, int level, cudaStream_t st);
+                             void *X0, void *GX, void *S, unsigned int *status, int level, cudaStream_t st);
 size_t leaf_refined_scratch_bytes(const LeafTables &lt, int count);
 int leaf_refined_launches(const LeafTables &lt, int count, int steps);
 cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0, int count,

@@ -77,6 +77,7 @@ struct Gj32Args {
   int nprob;
   long long leaf0;    // first leaf of the launch
   float2 *X0;         // [leaf][n][n] column-major, indexed by the absolute leaf number
+  float2 *GX;         // [leaf][n][nb] column-major (G X0), or null
   float2 *S;          // [launch slot][n][n] scratch
   unsigned *status;
   int level;
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(kGjThreads, 2) gj32_leaf_kernel(const __grid_c
   for (int i = tid; i < ni; i += kGjThreads) cv[i] = cl[i];
   for (int i = tid; i < p * p; i += kGjThreads) loc[i] = -1;
   __syncthreads();
+  for (int i = tid; i < n; i += kGjThreads) loc[(grid[i] >> 8) * p + (grid[i] & 0xff)] = i;
   LeafGeom geo;
   geo.D1x = D1x;
   geo.D1y = D1x + p * p;
@@ -453,6 +455,46 @@ __global__ void __launch_bounds__(kGjThreads, 2) gj32_leaf_kernel(const __grid_c
     const float2 v = S[idx];
     Xl[(size_t)dc * n + i] = make_float2(d * v.x, d * v.y);
   }
+  if (!a.GX) return;
+  // G X0: row r of G is the outward normal derivative along the grid line
+  // through boundary node r (p entries), minus i eta at r itself
+  const int e = a.lt.e, nb = a.lt.nb;
+  const double *D1y = D1x + p * p;
+  float2 *GXl = a.GX + (size_t)leaf * n * nb;
+  const float2 ieta = make_float2((float)-pb.eta.y, (float)pb.eta.x);
+  for (int idx = tid; idx < nb * n; idx += kGjThreads) {
+    const int r = idx % nb, j = idx / nb;
+    const float2 *Sj = S + (size_t)j * n;
+    const int side = r / e, ix = grid[r] & 0xff, iy = grid[r] >> 8;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int t = 0; t < p; t++) {
+      double w;
+      int q;
+      if (side == 0) {
+        w = -D1y[0 * p + t];
+        q = loc[t * p + ix];
+      } else if (side == 1) {
+        w = D1x[(p - 1) * p + t];
+        q = loc[iy * p + t];
+      } else if (side == 2) {
+        w = D1y[(p - 1) * p + t];
+        q = loc[t * p + ix];
+      } else {
+        w = -D1x[0 * p + t];
+        q = loc[iy * p + t];
+      }
+      if (q < 0) continue;
+      const float2 x = Sj[q];
+      acc.x = fmaf((float)w, x.x, acc.x);
+      acc.y = fmaf((float)w, x.y, acc.y);
+    }
+    const float2 ie = cmul(ieta, Sj[r]);  // - i eta x_r
+    acc.x -= ie.x;
+    acc.y -= ie.y;
+    const int dc = dcol[j];
+    const float d = (float)rsc[dc];
+    GXl[(size_t)dc * nb + r] = make_float2(d * acc.x, d * acc.y);
+  }
 }
 
 template <int RT, int CU>
@@ -472,7 +514,7 @@ size_t gj32_smem_bytes(const LeafTables &lt) {
 bool gj32_supported(const LeafTables &lt) { return lt.n <= 384 && gj32_smem_bytes(lt) <= 227 * 1024; }
 
 cudaError_t launch_leaf_gj32(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0, int count,
-                             void *X0, void *S, unsigned int *status, int level, cudaStream_t st) {
+                             void *X0, void *GX, void *S, unsigned int *status, int level, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   if (!gj32_supported(lt)) return cudaErrorInvalidValue;
   Gj32Args a;
@@ -481,6 +523,7 @@ cudaError_t launch_leaf_gj32(const LeafTables &lt, const LeafProb *probs, int np
   a.nprob = nprob;
   a.leaf0 = leaf0;
   a.X0 = (float2 *)X0;
+  a.GX = (float2 *)GX;
   a.S = (float2 *)S;
   a.status = status;
   a.level = level;

@@ -229,8 +229,8 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
   // cluster kernel where the panel does not fit; its G X0 is not used)
   cudaError_t err =
       gj32_supported(lt)
-          ? launch_leaf_gj32(lt, probs, nprob, leaf0, count, (float2 *)X0 - (size_t)leaf0 * n * n, w + L.s, status,
-                             level, st)
+          ? launch_leaf_gj32(lt, probs, nprob, leaf0, count, (float2 *)X0 - (size_t)leaf0 * n * n, nullptr, w + L.s,
+                             status, level, st)
           : launch_leaf(lt, probs, nprob, leaf0, count, (float2 *)X0 - (size_t)leaf0 * n * n,
                         (float2 *)(w + L.gx0) - (size_t)leaf0 * n * nb, w + L.s, (int *)(w + L.meta), status, level,
                         cs32, true, st);
