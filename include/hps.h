@@ -217,7 +217,12 @@ int hps_rebuild(int nh, hps_handle *const *hs, const double *const *c, void *str
  *   t: [nrhs][2 (mx + my) qe] complex impedance data du/dnu + i eta u on the
  *      outer boundary
  *   u: [nrhs][leaves][p^2-4] complex solution at every leaf node (written)
- * nrhs == 0 does nothing and returns HPS_OK.  Returns HPS_EINVAL (NULL
+ * nrhs == 0 does nothing and returns HPS_OK.  With the environment variable
+ * HPS_SOLVE_ENGINE=1, a solve with 1 or 2 right-hand sides runs as one
+ * persistent cooperative launch over a program recorded for the handle at
+ * the first such call (kept until hps_free; a pipeline wait that gives up
+ * after 2 s reports HPS_ETIMEOUT through hps_status); by default the steps
+ * are separate launches, which measured faster.  Returns HPS_EINVAL (NULL
  * handle or array, nrhs < 0), HPS_ENOMEM (workspace), HPS_ECUDA. */
 int hps_solve(hps_handle *h, const double *s, const double *t, double *u, int nrhs, void *stream);
 

@@ -19,6 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libhps.so")
 SOURCES = ["gemm.cu", "gj.cu", "lu.cu", "lu_solve.cu", "residual.cu", "ozaki.cu", "leaf_refine.cu", "leaf_gj32.cu",
+           "solve_engine.cu",
            "probe.cu", "hps_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -139,6 +139,14 @@ struct hps_handle {
   // staging for host arrays
   void *stage = nullptr;
   size_t stage_bytes = 0;
+  // one-launch solve programs for 1 and 2 right-hand sides, without and with
+  // the refinement's interface jumps (recorded at the first such solve)
+  struct EnProg {
+    hps::EnOp *d_ops = nullptr;
+    int nops = 0;
+    bool lu_tail = false;  // the leaf step (LU form) follows as its own launch
+    bool failed = false;   // the solve has a step the engine does not take
+  } eng[2][2];
 };
 
 namespace {
@@ -372,6 +380,12 @@ int cuda_fail(cudaError_t err) {
   do {                                           \
     cudaError_t err_ = (call);                   \
     if (err_ != cudaSuccess) return cuda_fail(err_); \
+  } while (0)
+// the same for functions that return minus the error code
+#define CK_NEG(call)                                  \
+  do {                                                \
+    cudaError_t err_ = (call);                        \
+    if (err_ != cudaSuccess) return -cuda_fail(err_); \
   } while (0)
 
 bool is_device_ptr(const void *p) {
@@ -834,7 +848,17 @@ struct SolveWs {
   // offset 0 of every workspace (zeroed when it is allocated, left zero by
   // the kernel), partial sums after them
   size_t ogv = 0;
+  // one-launch solves (1 or 2 right-hand sides): barrier words and arrival
+  // counters (cleared before every launch), then the split products'
+  // partial sums
+  size_t oen = 0, en_clear = 0, en_part = 0;
 };
+
+// The one-launch solve's scratch budget: counters and partial sums of the
+// split products of one phase, for grids of up to kEnGridMax CTAs.
+constexpr int kEnGridMax = 320;
+constexpr long long kEnCounters = 2LL * kEnGridMax;
+inline long long en_part_budget(int R) { return 4LL * kEnGridMax * 32 * R; }
 
 // Rows of the first diagonal block when a wide solve in LU form splits each
 // leaf's sweeps in two (a multiple of the sweep kernel's 32-row blocks), or
@@ -872,6 +896,12 @@ static void solve_ws_layout(const Plan &pl, int R, SolveWs &w, bool allow_oz = t
   if (R <= 16) {
     w.ogv = off;
     off = align256(off + hps::gemv_part_bytes(R));
+  }
+  if (R <= 2) {
+    w.oen = off;
+    w.en_clear = align256(sizeof(unsigned) * (4 + (size_t)kEnCounters));
+    w.en_part = w.oen + w.en_clear;
+    off = align256(w.en_part + sizeof(double2) * (size_t)en_part_budget(R));
   }
   auto take = [&](long long count) {
     size_t o = off;
@@ -921,6 +951,121 @@ static void solve_ws_layout(const Plan &pl, int R, SolveWs &w, bool allow_oz = t
   w.bytes = off;
 }
 
+// The steps of a solve with one or two right-hand sides as a program for the
+// one-launch solve (solve_engine.cu): solve_launch, given a recorder, hands
+// it its products and copies instead of launching them.  Operands are
+// recorded relative to the call's s, t, u and workspace (so that the program
+// serves every later call), or by address (the handle's operators and maps).
+struct SolveRec {
+  const char *lo[5] = {}, *hi[5] = {};  // ranges of s, t, u, workspace (1..4)
+  std::vector<hps::EnOp> ops;
+  int phase0 = 0;  // first op of the open phase
+  long long part = 0, cnt = 0;
+  bool ok = true, lu_tail = false;
+  int grid = 0, R = 0;
+
+  hps::EnMat conv(const Mat &m, bool allow_rmap) {
+    hps::EnMat e;
+    memset(&e, 0, sizeof(e));
+    e.base = -1;
+    if (!m.ptr) return e;
+    if (m.cmap || (m.rmap && !allow_rmap)) ok = false;
+    const char *p = (const char *)m.ptr;
+    e.base = 0;
+    e.off = (long long)(uintptr_t)p;
+    for (int b = 1; b <= 4; b++)
+      if (p >= lo[b] && p < hi[b]) {
+        e.base = b;
+        e.off = p - lo[b];
+        break;
+      }
+    e.ld = m.ld;
+    e.stride = m.stride;
+    e.rmap = m.rmap;
+    e.f32 = m.f32;
+    return e;
+  }
+  void open(bool same_phase) {
+    if (same_phase && !ops.empty()) {
+      ops.back().phase_end = 0;  // reopen the last phase
+      return;
+    }
+    phase0 = (int)ops.size();
+    part = cnt = 0;
+  }
+  void close() {
+    if (!ops.empty()) ops.back().phase_end = 1;
+    if (part > en_part_budget(R) || cnt > kEnCounters) ok = false;
+  }
+  int next_unit() const { return (int)ops.size() > phase0 ? ops.back().unit0 + ops.back().units : 0; }
+  void gemm(const GemmDesc *gd, int nd) {
+    open(false);
+    for (int q = 0; q < nd; q++) {
+      const GemmDesc &g = gd[q];
+      if (g.N != R || g.addI || g.A.rmap || g.A.cmap) ok = false;
+      hps::EnOp o;
+      memset(&o, 0, sizeof(o));
+      o.kind = 0;
+      o.M = g.M;
+      o.K = g.K;
+      o.batch = g.batch;
+      o.R = R;
+      o.ksplit = g.B2.ptr ? g.ksplit : g.K;
+      o.cf32 = g.cf32;
+      o.A = conv(g.A, false);
+      o.x = conv(g.B, true);
+      o.x2 = conv(g.B2, true);
+      o.y = conv(g.C, true);
+      o.D = conv(g.D, true);
+      o.alpha = g.alpha;
+      o.beta = g.beta;
+      // K cut into chunks when the row blocks alone would leave most of the
+      // grid idle
+      const int rows = hps::engine_unit_rows();
+      o.nrb = (g.M + rows - 1) / rows;
+      const long long base = (long long)g.batch * o.nrb;
+      int nkc = (g.K + hps::engine_max_kc() - 1) / hps::engine_max_kc();
+      if (base < grid / 2 && g.K >= 48)
+        nkc = std::max(nkc, (int)std::min<long long>((g.K + 23) / 24, (grid + base - 1) / base));
+      o.kc = (g.K + nkc - 1) / nkc;
+      o.nkc = (g.K + o.kc - 1) / o.kc;
+      o.units = (int)std::min<long long>(base * o.nkc, 1LL << 30);
+      o.unit0 = next_unit();
+      if (o.nkc > 1) {
+        o.part_off = part;
+        o.cnt_off = cnt;
+        part += base * o.nkc * rows * R;
+        cnt += base;
+      }
+      ops.push_back(o);
+    }
+    close();
+  }
+  void copy(const CopyBatch &cb, bool same_phase) {
+    open(same_phase);
+    for (int q = 0; q < cb.count; q++) {
+      const CopyDesc &d = cb.d[q];
+      if (d.trans || d.N != R || !d.src.ptr) ok = false;
+      hps::EnOp o;
+      memset(&o, 0, sizeof(o));
+      o.kind = 1;
+      o.M = d.M;
+      o.batch = d.batch;
+      o.R = R;
+      o.accumulate = d.accumulate;
+      o.x = conv(d.src, true);
+      o.y = conv(d.dst, true);
+      o.D.base = -1;
+      o.alpha = d.alpha;
+      const long long el = (long long)d.M * R * d.batch;
+      o.units = (int)((el + hps::engine_copy_unit() - 1) / hps::engine_copy_unit());
+      o.unit0 = next_unit();
+      ops.push_back(o);
+    }
+    close();
+  }
+};
+
 // Products of a solve: complex128 ones wide enough for the tensor cores run
 // there, the batch cut into chunks whose digit planes fit the workspace's
 // region; the rest in one launch.
@@ -967,15 +1112,49 @@ static int solve_gemm(GemmDesc *gd, int nd, cudaStream_t st, char *wb, const Sol
 // (optional, [R][total_pairs]): residuals of the two interface conditions of
 // every I3 pair, injected as h3a -= JB, h3b -= JA before the level's Upsilon
 // actions (the right-hand side of t3a = -g3b + JA, t3b = -g3a + JB).
+// The leaf step of a solve in LU form: u = B^{-1} [t; s] by the leaves' sweeps.
+static cudaError_t lu_leaf_solve(hps_handle *h, const double2 *s, const double2 *tl, double2 *u, int R,
+                                 cudaStream_t st) {
+  const Plan &pl = h->plan;
+  const int n = pl.n, nb = pl.nb, ni = pl.ni, nl = pl.leaves;
+  return hps::launch_lu_solve(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, tl, (long long)nl * nb, nb, s,
+                              (long long)nl * ni, ni, u, (long long)nl * n, n, pl.leaf_f32 != 0, st);
+}
+
+static int run_engine(hps_handle *h, const double2 *s, const double2 *t, double2 *u, int R, char *wb,
+                      const SolveWs &ws, cudaStream_t st, const double2 *JA, const double2 *JB, bool may_alloc);
+
 static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, double2 *u, int R,
                         char *wb, const SolveWs &ws, cudaStream_t st, const double2 *JA = nullptr,
-                        const double2 *JB = nullptr) {
+                        const double2 *JB = nullptr, SolveRec *rec = nullptr, bool may_alloc = true) {
+  // one or two right-hand sides: the whole solve as one launch
+  if (!rec && R <= 2) {
+    const int used = run_engine(h, s, t, u, R, wb, ws, st, JA, JB, may_alloc);
+    if (used < 0) return -used;
+    if (used > 0) return HPS_OK;
+  }
   // with one or two right-hand sides the solve is a chain of small
   // dependent launches: let each be scheduled while the previous one drains
   // (measured at 16 x 16 leaves: 1 RHS 0.85 -> 0.75 ms; with 16 or 64
   // right-hand sides the chained launches were slower)
   std::unique_ptr<hps::LaunchChain> chain;
-  if (R <= 2) chain.reset(new hps::LaunchChain());
+  if (R <= 2 && !rec) chain.reset(new hps::LaunchChain());
+  // the steps, launched or recorded
+  auto gemms = [&](GemmDesc *gd, int nd) -> int {
+    if (rec) {
+      rec->gemm(gd, nd);
+      return HPS_OK;
+    }
+    return solve_gemm(gd, nd, st, wb, ws, h->plan.oz, h->d_status);
+  };
+  auto copies = [&](const CopyBatch &cb, bool same_phase) -> int {
+    if (rec) {
+      rec->copy(cb, same_phase);
+      return HPS_OK;
+    }
+    CK(hps::launch_copy(cb, st));
+    return HPS_OK;
+  };
   const Plan &pl = h->plan;
   const int n = pl.n, nb = pl.nb, ni = pl.ni, nl = pl.leaves, lf = pl.leaf_f32;
   const size_t *oh = ws.oh, *ot = ws.ot, *ota = ws.ota, *otb = ws.otb;
@@ -992,7 +1171,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
   GemmDesc g = gemm(nbi, R, ni, nl, F(elem(h->GXi, h->gxi_ld * nbi, gf), h->gxi_ld, h->gxi_stride, gf),
                     mat(s, (long long)nl * ni, ni), mat(W(oh[0]), (long long)nl * nbi, nbi));
   g.cf32 = lf;
-  if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
+  if (int rc = gemms(&g, 1)) return rc;
   for (size_t j = 0; j < pl.lv.size(); j++) {
     const Level &L = pl.lv[j];
     const int P = L.P, n1 = L.n1, n2 = L.n2, n3 = L.n3, nt = L.nt, nc = L.nc, f = L.f32;
@@ -1011,7 +1190,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
       cb.d[0].accumulate = 1;
       cb.d[1] = copy(n3, R, P, mat(JA + L.jump_off, pl.total_pairs, n3), h3b, -1.0);
       cb.d[1].accumulate = 1;
-      CK(hps::launch_copy(cb, st));
+      if (int rc = copies(cb, false)) return rc;
     }
     const long long s33 = (long long)n3 * n3, ldv = (long long)P * n3;
     double2 *v = W(ov), *ta = W(ota[j]), *tb = W(otb[j]);
@@ -1020,17 +1199,17 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     g.D = h3b;
     g.beta = make_double2(-1.0, 0.0);
     g.cf32 = f;
-    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
+    if (int rc = gemms(&g, 1)) return rc;
     g = gemm(n3, R, n3, P, F(L.Winv, n3, s33, f), mat(v, ldv, n3), mat(ta, ldv, n3));
     g.cf32 = f;
-    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
+    if (int rc = gemms(&g, 1)) return rc;
     // t~3b = -h3a - R33a t~3a  (Upsilon_b [h3a; h3b])
     g = gemm(n3, R, n3, P, F(L.R33a, n3, s33, f), mat(ta, ldv, n3), mat(tb, ldv, n3));
     g.alpha = make_double2(-1.0, 0.0);
     g.D = h3a;
     g.beta = make_double2(-1.0, 0.0);
     g.cf32 = f;
-    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
+    if (int rc = gemms(&g, 1)) return rc;
     // h^tau = [h1a + R13a t~3a ; h2b + R23b t~3b]  (Eq. flux_part)
     const long long ldp = (long long)P * nt;
     GemmDesc g2[2];
@@ -1043,7 +1222,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     g2[1].D = h2b;
     g2[1].beta = make_double2(1.0, 0.0);
     g2[1].cf32 = f;
-    if (int rc = solve_gemm(g2, 2, st, wb, ws, pl.oz, h->d_status)) return rc;
+    if (int rc = gemms(g2, 2)) return rc;
   }
 
   // ---- downward pass ----
@@ -1054,7 +1233,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     CopyBatch cb;
     cb.count = 1;
     cb.d[0] = copy(ntop, R, 1, mat(t, pl.nbdry, 0, h->d_root_src), mat(W(ot[top]), ntop, 0));
-    CK(hps::launch_copy(cb, st));
+    if (int rc = copies(cb, false)) return rc;
   }
   for (size_t jj = top; jj-- > 0;) {
     const Level &L = pl.lv[jj];
@@ -1073,13 +1252,14 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     g2[1].D = mat(W(otb[jj]), ldv, n3);
     g2[1].beta = make_double2(1.0, 0.0);
     g2[1].cf32 = f;
-    if (int rc = solve_gemm(g2, 2, st, wb, ws, pl.oz, h->d_status)) return rc;
+    if (int rc = gemms(g2, 2)) return rc;
     // the rest of the children's incoming data is the parent's: I1 and I2
     CopyBatch cb;
     cb.count = 2;
     cb.d[0] = copy(n1, R, P, mat(tp, ldp, nt), mat(tc, ldc2, 2LL * nc, L.d_I1));
     cb.d[1] = copy(n2, R, P, mat(tp + n1, ldp, nt), mat(tc + nc, ldc2, 2LL * nc, L.d_I2));
-    CK(hps::launch_copy(cb, st));
+    // (rows I1, I2 of the children: independent of the products' rows I3)
+    if (int rc = copies(cb, true)) return rc;
   }
   // leaves: u = Psi t + Y s = B^{-1} [t; s], t on the leaves' Chebyshev edge
   // nodes: with boundary data on Gauss nodes, t = Qh t_G first (every
@@ -1089,7 +1269,7 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     const int qe = pl.qe, e = pl.e;
     GemmDesc gq = gemm(e, R, qe, 4 * nl, mat(h->d_Qcm, e, 0), mat(W(ot[0]), (long long)nl * nbi, qe),
                        mat(W(ws.otc), (long long)nl * nb, e));
-    if (int rc = solve_gemm(&gq, 1, st, wb, ws, false, h->d_status)) return rc;
+    if (int rc = rec ? gemms(&gq, 1) : solve_gemm(&gq, 1, st, wb, ws, false, h->d_status)) return rc;
     tl = W(ws.otc);
   }
   const int b1 = lu_split(n);
@@ -1118,18 +1298,91 @@ static int solve_launch(hps_handle *h, const double2 *s, const double2 *t, doubl
     CK(hps::launch_lu_solve_part(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, nullptr, 0, 0, nullptr, 0, 0, u, ldu,
                                  n, false, 0, b1, false, false, true, st));
   } else if (pl.leaf_lu) {
-    CK(hps::launch_lu_solve(h->X, h->lu_perm, h->lu_dsc, nl, n, nb, R, tl, (long long)nl * nb, nb, s,
-                            (long long)nl * ni, ni, u, (long long)nl * n, n, lf != 0, st));
+    if (rec)
+      rec->lu_tail = true;  // its own launch after the program
+    else
+      CK(lu_leaf_solve(h, s, tl, u, R, st));
   } else {
     g = gemm(n, R, n, nl, F(h->X, n, (long long)n * n, lf), mat(tl, (long long)nl * nb, nb),
              mat(u, (long long)nl * n, n));
     g.B2 = mat(s, (long long)nl * ni, ni);
     g.ksplit = nb;
     g.cf32 = lf;
-    if (int rc = solve_gemm(&g, 1, st, wb, ws, pl.oz, h->d_status)) return rc;
+    if (int rc = gemms(&g, 1)) return rc;
   }
 
   return HPS_OK;
+}
+
+// A solve with one or two right-hand sides as one launch: the program of
+// the handle for (R, refinement jumps or not), recorded from solve_launch at
+// the first such call (may_alloc: its device copy may be allocated now),
+// then the engine over this call's s, t, u and workspace, and for leaves in
+// LU form their sweeps.  Returns 1 when the solve was launched, 0 when the
+// caller launches it step by step, or minus an error code.
+static int run_engine(hps_handle *h, const double2 *s, const double2 *t, double2 *u, int R, char *wb,
+                      const SolveWs &ws, cudaStream_t st, const double2 *JA, const double2 *JB, bool may_alloc) {
+  if (R < 1 || R > 2 || !ws.oen) return 0;
+  // opt-in: measured at 16 x 16 leaves, p = 16, 1 right-hand side, the
+  // program takes 0.80 ms against 0.59 ms for the step-by-step launches (a
+  // grid barrier costs ~2.7 us and a work unit ~4-5 us of dependent-load
+  // latency, over 43 dependent phases)
+  const char *e = getenv("HPS_SOLVE_ENGINE");
+  if (!e || e[0] != '1') return 0;
+  const int grid = hps::engine_grid();
+  if (grid <= 0 || grid > kEnGridMax) return 0;
+  const Plan &pl = h->plan;
+  hps_handle::EnProg &pg = h->eng[R - 1][(JA && JB) ? 1 : 0];
+  if (pg.failed) return 0;
+  if (!pg.d_ops) {
+    if (!may_alloc) return 0;
+    SolveRec rec;
+    rec.grid = grid;
+    rec.R = R;
+    const char *b[5] = {nullptr, (const char *)s, (const char *)t, (const char *)u, wb};
+    const size_t sz[5] = {0, sizeof(double2) * (size_t)R * pl.leaves * pl.ni, sizeof(double2) * (size_t)R * pl.nbdry,
+                          sizeof(double2) * (size_t)R * pl.leaves * pl.n, ws.bytes};
+    for (int k = 1; k <= 4; k++) {
+      rec.lo[k] = b[k];
+      rec.hi[k] = b[k] + sz[k];
+    }
+    for (int k = 1; k <= 3; k++)
+      for (int m = k + 1; m <= 3; m++)
+        if (rec.lo[k] < rec.hi[m] && rec.lo[m] < rec.hi[k]) rec.ok = false;  // s, t, u overlap
+    if (rec.ok) {
+      const int rc = solve_launch(h, s, t, u, R, wb, ws, st, JA, JB, &rec);
+      if (rc) return -rc;
+    }
+    if (!rec.ok || rec.ops.empty()) {
+      pg.failed = true;
+      return 0;
+    }
+    const size_t bytes = sizeof(hps::EnOp) * rec.ops.size();
+    CK_NEG(cudaMalloc((void **)&pg.d_ops, bytes));
+    CK_NEG(cudaMemcpy(pg.d_ops, rec.ops.data(), bytes, cudaMemcpyHostToDevice));
+    pg.nops = (int)rec.ops.size();
+    pg.lu_tail = rec.lu_tail;
+  }
+  CK_NEG(cudaMemsetAsync(wb + ws.oen, 0, ws.en_clear, st));
+  hps::EnArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ops = pg.d_ops;
+  a.nops = pg.nops;
+  a.base[0] = nullptr;
+  a.base[1] = s;
+  a.base[2] = t;
+  a.base[3] = u;
+  a.base[4] = wb;
+  a.bar = (unsigned *)(wb + ws.oen);
+  a.cnt = a.bar + 4;
+  a.part = (double2 *)(wb + ws.en_part);
+  a.status = h->d_status;
+  CK_NEG(hps::launch_solve_engine(a, st));
+  if (pg.lu_tail) {
+    const double2 *tl = (const double2 *)(wb + (pl.gauss ? ws.otc : ws.ot[0]));
+    CK_NEG(lu_leaf_solve(h, s, tl, u, R, st));
+  }
+  return 1;
 }
 
 // Iterative refinement of an HPS_MIXED solve: u = S(s, t), then per step the
@@ -1374,6 +1627,9 @@ int hps_free(hps_handle *h) {
   }
   if (h->ws) cudaFree(h->ws);
   if (h->stage) cudaFree(h->stage);
+  for (auto &row : h->eng)
+    for (auto &pg : row)
+      if (pg.d_ops) cudaFree(pg.d_ops);
   delete h;
   return HPS_OK;
 }
@@ -2650,7 +2906,7 @@ int hps_solve_noalloc(hps_handle *h, const double *s_, const double *t_, double 
   // allocates nothing.
   CK(cudaMemsetAsync(wb, 0, hps::gemv_scratch_counters(), (cudaStream_t)stream));
   return solve_launch(h, (const double2 *)s_, (const double2 *)t_, (double2 *)u_, nrhs, wb, ws,
-                      (cudaStream_t)stream);
+                      (cudaStream_t)stream, nullptr, nullptr, nullptr, false);
 }
 
 int hps_root_R(hps_handle *h, double *R, int gauss_basis, void *stream) {

@@ -168,6 +168,47 @@ cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStr
                            unsigned *status = nullptr, bool reuse_a = false);
 cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st);
 
+// ---- one-launch solves (solve_engine.cu) ----
+// An operand of a solve step: element (i, c) of batch entry b is
+//   ((char *)base[base] + off)[b stride + c ld + (rmap ? rmap[i] : i)]
+// (complex128, or complex64 with f32), base[0] = null (off is the address),
+// base[1..4] = the solve's s, t, u and workspace; base = -1: no operand.
+struct EnMat {
+  long long off, ld, stride;
+  const int *rmap;
+  int base, f32;
+};
+// A step: kind 0, y = alpha A x (+ beta D) with A M x K per batch entry
+// (column-major, ld A.ld, no maps; rows k >= ksplit of x come from x2), R <= 2
+// columns, accumulated in complex64 with cf32; kind 1, y = alpha x (+ y if
+// accumulate), M x R per batch entry.  A phase is a run of independent steps
+// closed by phase_end; units: the work units of the step (unit0: the first
+// within its phase).  Products in nkc > 1 K chunks of kc keep partial sums at
+// part_off (complex) and arrival counters at cnt_off.
+struct EnOp {
+  int kind, M, K, batch, R, ksplit, cf32, accumulate;
+  int nrb, nkc, kc, units, unit0, phase_end;
+  long long part_off, cnt_off;
+  EnMat A, x, x2, y, D;
+  double2 alpha, beta;
+};
+struct EnArgs {
+  const EnOp *ops;  // device program
+  int nops;
+  const void *base[5];
+  double2 *part;    // partial sums of split products
+  unsigned *cnt;    // their arrival counters (zero on entry, left zero)
+  unsigned *bar;    // grid barrier: count, generation, abort (zero on entry)
+  unsigned *status;
+};
+// CTAs of an engine launch (every one resident; 0 if the device cannot run
+// it), rows of a product unit, its longest K chunk, elements of a copy unit.
+int engine_grid();
+int engine_unit_rows();
+int engine_max_kc();
+int engine_copy_unit();
+cudaError_t launch_solve_engine(const EnArgs &a, cudaStream_t st);
+
 // Leaf step (Sec. 2.1) for leaves [leaf0, leaf0 + count): assemble B, invert
 // it by blocked Gauss-Jordan with partial pivoting across a cluster of `cs`
 // CTAs, write X = B^{-1} = [Psi | Y] ([leaf][n][n] column-major) and
