@@ -325,8 +325,11 @@ int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, v
  * (9 slices of 6 bits an operand, error ~2^-54 max|A_i.| max|B_.j| a term);
  * 2: the same with 5 slices, as the build runs its complex64 products (the
  * mixed path's lower levels): error ~5 2^-29 max|A_i.| max|B_.j| a term, the
- * accuracy of complex64 arithmetic (any size is accepted here).  Device arrays only; enqueued on `stream`.
- * Returns HPS_EINVAL (sizes < 1, NULL or host arrays, emulated not 0 .. 2),
+ * accuracy of complex64 arithmetic; 3: complex64 arithmetic on the FP32
+ * pipes (operands rounded to complex64, results widened), the kernel the
+ * refinement corrections take (any size is accepted here).  Device arrays
+ * only; enqueued on `stream`.
+ * Returns HPS_EINVAL (sizes < 1, NULL or host arrays, emulated not 0 .. 3),
  * HPS_ENOMEM (workspace), HPS_ECUDA. */
 int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, double *C, int emulated,
               void *stream);

@@ -97,7 +97,14 @@ template <class C>
 __device__ __forceinline__ void epilogue(const GemmDesc &g, int b, int i, int j, C acc) {
   if (g.wide_epilogue) {
     // the product in its arithmetic's precision, the combination in FP64
+    // (C = D + AB, the refinement corrections: two additions, since this
+    // part's FP64 pipe is slow)
     const double2 a = make_double2((double)acc.x, (double)acc.y);
+    if (g.alpha.x == 1.0 && g.alpha.y == 0.0 && g.beta.x == 1.0 && g.beta.y == 0.0 && g.D.ptr && !g.addI) {
+      const double2 d = ldm_rw<double2>(g.D, mat_off(g.D, b, i, j));
+      stm(g.C, mat_off(g.C, b, i, j), make_double2(d.x + a.x, d.y + a.y));
+      return;
+    }
     double2 w = cmul(g.alpha, a);
     if (g.D.ptr) {
       const double2 d = ldm_rw<double2>(g.D, mat_off(g.D, b, i, j));
@@ -188,6 +195,87 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       for (int c = 0; c < TN; c++) {
         int i = m0 + tx + r * NTX, j = n0 + ty + c * NTY;
         if (i < g.M && j < g.N) epilogue<C>(g, b, i, j, acc[r][c]);
+      }
+  }
+}
+
+// Complex64 products without index maps (the refinement corrections X0 E,
+// the mixed path's dense products): 128 x 128 tiles, 256 threads with 8 x 8
+// outputs each at rows tx + 16 r and columns ty + 16 c (64 complex
+// multiply-adds for 16 shared-memory loads a k), K in steps of 16 with the
+// next step's tiles loaded into registers while the current one is
+// multiplied.  TA, TB: the storage types of A and B (complex64 or complex128,
+// converted on load).
+constexpr int kCg = 128, kCgK = 16;
+template <class TA, class TB>
+__global__ void __launch_bounds__(256, 1) cgemm64_kernel(const __grid_constant__ GemmPack pack) {
+  chain_enter();
+  __shared__ float2 As[kCgK][kCg];
+  __shared__ float2 Bs[kCgK][kCg];
+  const GemmDesc &g = pack.d[blockIdx.z];
+  const int tiles_m = (g.M + kCg - 1) / kCg, tiles_n = (g.N + kCg - 1) / kCg;
+  if ((int)blockIdx.x >= tiles_m * tiles_n) return;
+  const int m0 = (blockIdx.x % tiles_m) * kCg, n0 = (blockIdx.x / tiles_m) * kCg;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int b = blockIdx.y; b < g.batch; b += gridDim.y) {
+    const TA *A = (const TA *)g.A.ptr + (size_t)b * g.A.stride;
+    const TB *B = (const TB *)g.B.ptr + (size_t)b * g.B.stride;
+    // element q of this thread's share of a tile: A rows (tid % 128), k pairs
+    // (tid / 128 + 2 q); B k (tid % 16), columns (tid / 16 + 16 q)
+    float2 pa[8], pb[8];
+    auto fetch = [&](int k0) {
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int i = m0 + (tid & 127), k = k0 + (tid >> 7) + 2 * q;
+        float2 v = make_float2(0.f, 0.f);
+        if (i < g.M && k < g.K) {
+          const TA t = __ldg(A + i + (size_t)k * g.A.ld);
+          v = make_float2((float)t.x, (float)t.y);
+        }
+        pa[q] = v;
+        const int kb = k0 + (tid & 15), j = n0 + (tid >> 4) + 16 * q;
+        float2 w = make_float2(0.f, 0.f);
+        if (kb < g.K && j < g.N) {
+          const TB t = __ldg(B + kb + (size_t)j * g.B.ld);
+          w = make_float2((float)t.x, (float)t.y);
+        }
+        pb[q] = w;
+      }
+    };
+    float2 acc[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; r++)
+#pragma unroll
+      for (int c = 0; c < 8; c++) acc[r][c] = make_float2(0.f, 0.f);
+    fetch(0);
+    for (int k0 = 0; k0 < g.K; k0 += kCgK) {
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        As[(tid >> 7) + 2 * q][tid & 127] = pa[q];
+        Bs[tid & 15][(tid >> 4) + 16 * q] = pb[q];
+      }
+      __syncthreads();
+      if (k0 + kCgK < g.K) fetch(k0 + kCgK);
+#pragma unroll 4
+      for (int k = 0; k < kCgK; k++) {
+        float2 a[8], bv[8];
+#pragma unroll
+        for (int r = 0; r < 8; r++) a[r] = As[k][tx + 16 * r];
+#pragma unroll
+        for (int c = 0; c < 8; c++) bv[c] = Bs[k][ty + 16 * c];
+#pragma unroll
+        for (int r = 0; r < 8; r++)
+#pragma unroll
+          for (int c = 0; c < 8; c++) cmac(acc[r][c], a[r], bv[c]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 8; r++)
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const int i = m0 + tx + 16 * r, j = n0 + ty + 16 * c;
+        if (i < g.M && j < g.N) epilogue<float2>(g, b, i, j, acc[r][c]);
       }
   }
 }
@@ -387,6 +475,35 @@ cudaError_t launch_gemv(const GemmPack &pk, cudaStream_t st) {
   return launch_k(gemv_kernel<C, NN>, grid, dim3(256), 0, st, pk);
 }
 
+// Complex64 products that the 128 x 128 kernel takes: no index maps, no
+// second B, every tile mostly live, and one storage type for A (and for B)
+// over the launch's descriptors.
+bool cg64_fits(const GemmPack &pk) {
+  for (int q = 0; q < pk.n; q++) {
+    const GemmDesc &g = pk.d[q];
+    if (g.A.rmap || g.A.cmap || g.B.rmap || g.B.cmap || g.B2.ptr || g.C.rmap || g.C.cmap || g.D.rmap ||
+        g.D.cmap || g.M < 96 || g.N < 96 || g.A.f32 != pk.d[0].A.f32 || g.B.f32 != pk.d[0].B.f32)
+      return false;
+  }
+  return true;
+}
+
+cudaError_t launch_cg64(const GemmPack &pk, cudaStream_t st) {
+  int maxtiles = 0, maxbatch = 0;
+  for (int q = 0; q < pk.n; q++) {
+    const GemmDesc &g = pk.d[q];
+    maxtiles = std::max(maxtiles, ((g.M + kCg - 1) / kCg) * ((g.N + kCg - 1) / kCg));
+    maxbatch = std::max(maxbatch, g.batch);
+  }
+  if (maxtiles == 0 || maxbatch == 0) return cudaSuccess;
+  dim3 grid(maxtiles, maxbatch < 65535 ? maxbatch : 65535, pk.n);
+  const bool af = pk.d[0].A.f32, bf = pk.d[0].B.f32;
+  if (af && bf) return launch_k(cgemm64_kernel<float2, float2>, grid, dim3(256), 0, st, pk);
+  if (af) return launch_k(cgemm64_kernel<float2, double2>, grid, dim3(256), 0, st, pk);
+  if (bf) return launch_k(cgemm64_kernel<double2, float2>, grid, dim3(256), 0, st, pk);
+  return launch_k(cgemm64_kernel<double2, double2>, grid, dim3(256), 0, st, pk);
+}
+
 template <class C>
 cudaError_t launch_typed(const GemmPack &pk, int maxN, cudaStream_t st) {
   if (maxN <= 1) return launch_gemv<C, 1>(pk, st);
@@ -398,7 +515,11 @@ cudaError_t launch_typed(const GemmPack &pk, int maxN, cudaStream_t st) {
   bool scratch = true;
   for (int q = 0; q < pk.n; q++) scratch = scratch && pk.d[q].part && pk.d[q].cnt;
   if (maxN <= 16 && scratch) return launch_gemv<C, 16>(pk, st);
+  const bool c64 = sizeof(C) == sizeof(float2) && cg64_fits(pk);
   switch (pk.d[0].cfg) {  // a measured choice (hps_tune)
+    case 6:
+      if (c64) return launch_cg64(pk, st);
+      break;
     case 1: return launch_cfg<C, 64, 64, 16, 4, 4>(pk, st);
     case 2: return launch_cfg<C, 32, 32, 16, 2, 2>(pk, st);
     case 3: return launch_cfg<C, 16, 16, 16, 1, 1>(pk, st);
@@ -406,8 +527,10 @@ cudaError_t launch_typed(const GemmPack &pk, int maxN, cudaStream_t st) {
     default: break;
   }
   if (maxN < 32) return launch_cfg<C, 64, 16, 16, 2, 2>(pk, st);
-  // the largest tile that still gives every SM two CTAs
+  // the largest tile that still gives every SM two CTAs (one for the
+  // complex64 128 x 128 tiles)
   const long long want = 2 * 152;
+  if (c64 && cfg_ctas<128, 128>(pk) >= want / 2) return launch_cg64(pk, st);
   if (cfg_ctas<64, 64>(pk) >= want) return launch_cfg<C, 64, 64, 16, 4, 4>(pk, st);
   if (cfg_ctas<32, 32>(pk) >= want) return launch_cfg<C, 32, 32, 16, 2, 2>(pk, st);
   return launch_cfg<C, 16, 16, 16, 1, 1>(pk, st);

@@ -723,8 +723,8 @@ WRef wref_layout(int n3, long long P, bool oz) {
   WRef L;
   L.w32 = 0;
   L.x0 = align256(8 * n2);
-  L.e = L.x0 + align256(8 * n2);
-  L.oz = L.e + align256(16 * n2);
+  L.e = L.x0 + align256(8 * n2);  // the residual, in complex64
+  L.oz = L.e + align256(8 * n2);
   L.total = L.oz + (oz_shape(n3, n3, n3, (int)P, 0, oz) ? oz_bytes_shape(n3, n3, n3, (int)P) : 0);
   return L;
 }
@@ -748,7 +748,7 @@ int w_inverse(const GJChoice &g, void *W, void *Winv, int n3, int P, int *meta, 
   }
   const WRef L = wref_layout(n3, P, oz);
   void *W32 = rscr + L.w32, *X0 = rscr + L.x0;
-  double2 *E = (double2 *)(rscr + L.e);
+  float2 *E = (float2 *)(rscr + L.e);
   const long long s2 = (long long)n3 * n3;
   CopyBatch cb;
   cb.count = 1;
@@ -763,7 +763,9 @@ int w_inverse(const GJChoice &g, void *W, void *Winv, int n3, int P, int *meta, 
   launches += 2 + gj_elim_launches(n3, g);
   const bool ozr = oz_shape(n3, n3, n3, P, 0, oz);
   for (int it = 0; it < 2; it++) {
-    GemmDesc gr = gemm(n3, n3, n3, P, mat(W, n3, s2), mat(Winv, n3, s2), mat(E, n3, s2));
+    // (E accurate to complex128 rounding, stored in complex64: only the
+    // complex64 correction reads it)
+    GemmDesc gr = gemm(n3, n3, n3, P, mat(W, n3, s2), mat(Winv, n3, s2), mat(E, n3, s2, nullptr, nullptr, 1));
     gr.alpha = make_double2(-1.0, 0.0);
     gr.addI = 1;
     if (ozr) {
@@ -778,7 +780,8 @@ int w_inverse(const GJChoice &g, void *W, void *Winv, int n3, int P, int *meta, 
     // X += X0 E: complex64 product (elementwise complex64 arithmetic: its
     // error is amplified by cond(W) in the next residual), FP64 addition in
     // its epilogue
-    GemmDesc gc = gemm(n3, n3, n3, P, mat(X0, n3, s2, nullptr, nullptr, 1), mat(E, n3, s2), mat(Winv, n3, s2));
+    GemmDesc gc = gemm(n3, n3, n3, P, mat(X0, n3, s2, nullptr, nullptr, 1), mat(E, n3, s2, nullptr, nullptr, 1),
+                       mat(Winv, n3, s2));
     gc.cf32 = 1;
     gc.wide_epilogue = 1;
     gc.D = gc.C;
@@ -2113,7 +2116,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
       int nr = 0;
       for (int q = 0; q < nd; q++) {
         int v;
-        if (tuned(TuneKey{0, gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32}, v) && v >= 1 && v <= 4)
+        if (tuned(TuneKey{0, gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32}, v) && v >= 1 && v <= 6 && v != 5)
           gd[q].cfg = v;
         if (oz_shape(gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32, P0.oz)) {
           CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, st, d_status));
@@ -2328,13 +2331,13 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
 
 int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, double *C, int emulated,
               void *stream) {
-  if (M < 1 || N < 1 || K < 1 || batch < 1 || batch > 65535 || emulated < 0 || emulated > 2) return HPS_EINVAL;
+  if (M < 1 || N < 1 || K < 1 || batch < 1 || batch > 65535 || emulated < 0 || emulated > 3) return HPS_EINVAL;
   if (!A || !B || !C || !is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C)) return HPS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   GemmDesc g = gemm(M, N, K, batch, mat(A, M, (long long)M * K), mat(B, K, (long long)K * N),
                     mat(C, M, (long long)M * N));
-  g.cf32 = emulated == 2 ? 1 : 0;  // the 4-slice product of the complex64 products
-  if (!emulated) {
+  g.cf32 = emulated >= 2 ? 1 : 0;  // the complex64 products: 5 slices, or complex64 arithmetic
+  if (emulated == 0 || emulated == 3) {
     CK(hps::launch_gemm(&g, 1, st));
     return HPS_OK;
   }
@@ -2571,8 +2574,9 @@ int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned) {
                         mat(buf + oC, k.M, (long long)k.M * k.N, nullptr, nullptr, k.f32));
       g.cf32 = k.f32;
       auto none = [&]() { return cudaSuccess; };
-      for (int cand = 1; cand <= 5; cand++) {
+      for (int cand = 1; cand <= 6; cand++) {
         if (cand == 5 && (!P0.oz || k.K < 32 || k.batch > 65535)) continue;
+        if (cand == 6 && (!k.f32 || k.M < 96 || k.N < 96)) continue;
         float ms;
         if (cand == 5) {
           const size_t need = hps::oz_workspace_bytes(g);

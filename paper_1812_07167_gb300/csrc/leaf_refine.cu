@@ -4,7 +4,9 @@
 // whose condition numbers are ~5e2), and X0 is refined to complex128
 // accuracy by steps of
 //     E = I - B X      (complex128-accurate: the Ozaki product on the tensor
-//                       cores, B assembled exactly in FP64)
+//                       cores, B assembled exactly in FP64; E is then
+//                       rounded to complex64, which costs the correction
+//                       nothing: it is formed in complex64 anyway)
 //     X = X + X0 E     (the correction product in complex64 arithmetic, added
 //                       in FP64 in the product's epilogue)
 // Each step multiplies the residual norm by ~||I - B X0|| (~1e-5), and the
@@ -192,8 +194,8 @@ RefineLayout refine_layout(const LeafTables &lt, int count) {
   o = al256(o + sizeof(int) * c * gj_meta_ints((int)n));
   L.b = o;
   o = al256(o + 16 * c * n * n);
-  L.e = o;
-  o = al256(o + 16 * c * n * n);
+  L.e = o;  // the residual E, stored in complex64 (an operand of the complex64 correction only)
+  o = al256(o + 8 * c * n * n);
   L.oz = o;
   GemmDesc g = plain_gemm((int)n, (int)n, (int)n, count, nullptr, 0, nullptr, 1, nullptr);
   o = al256(o + oz_workspace_bytes(g));
@@ -221,7 +223,8 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
   char *w = (char *)scr;
   const int n = lt.n, nb = lt.nb;
   void *X0 = w + L.x0;
-  double2 *Bm = (double2 *)(w + L.b), *E = (double2 *)(w + L.e);
+  double2 *Bm = (double2 *)(w + L.b);
+  float2 *E = (float2 *)(w + L.e);
   double2 *Xl = (double2 *)X + (size_t)leaf0 * n * n;
   double2 *GXl = (double2 *)GX + (size_t)leaf0 * n * nb;
   int nl = 0;
@@ -261,6 +264,7 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
   for (int it = 0; it < steps; it++) {
     // E = I - B X, complex128-accurate on the tensor cores
     GemmDesc g = plain_gemm(n, n, n, count, Bm, 0, Xl, 0, E);
+    g.C.f32 = 1;  // (accurate to complex128 rounding, then rounded to complex64)
     g.alpha = make_double2(-1.0, 0.0);
     g.addI = 1;
     // (B's digits are the same in every step: split once)
@@ -271,7 +275,7 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
     // residual, so it stays in elementwise complex64 arithmetic: a 4-slice
     // tensor-core product, accurate relative to row and column maxima only,
     // left 3e-8 in u)
-    GemmDesc c = plain_gemm(n, n, n, count, X0, 1, E, 0, Xl);
+    GemmDesc c = plain_gemm(n, n, n, count, X0, 1, E, 1, Xl);
     c.cf32 = 1;
     c.wide_epilogue = 1;
     c.D = c.C;

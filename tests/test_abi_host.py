@@ -121,7 +121,7 @@ def test_zgemm_argument_checks_need_no_device():
     L = hps.lib()
     a = np.zeros(16, complex)
     assert L.hps_zgemm(0, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, 0, None) == hps.HPS_EINVAL
-    assert L.hps_zgemm(2, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, 3, None) == hps.HPS_EINVAL
+    assert L.hps_zgemm(2, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, 4, None) == hps.HPS_EINVAL
     # host arrays are refused (device memory only)
     assert L.hps_zgemm(2, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, 1, None) == hps.HPS_EINVAL
 

@@ -142,3 +142,21 @@ def test_wide_rhs_solve_on_tensor_cores_matches_fp64_pipes_and_oracle():
     with O.Tree(opr, c, nthreads=nt) as T:
         uo = T.solve(s[:4], t[:4], nthreads=nt)
     assert np.abs(us[0][:4] - uo).max() / np.abs(uo).max() < 1e-10
+
+
+# complex64 arithmetic on the FP32 pipes (the refinement corrections' and the
+# mixed path's products): the 128 x 128-tile kernel where the shape allows
+# (M, N >= 96), the index-mapped tile kernels otherwise; every entry within
+# K 2^-21 (|A| |B|)(i, j) of the exact product (operands rounded to complex64
+# and the sums in complex64)
+@pytest.mark.parametrize("M,N,K,batch", [(252, 252, 252, 4), (128, 128, 16, 1), (250, 130, 77, 2),
+                                         (1000, 300, 200, 1), (100, 37, 83, 3), (96, 96, 1, 5)])
+def test_complex64_product_has_complex64_accuracy(M, N, K, batch):
+    rng = np.random.default_rng(M + N + K)
+    A = _rand((batch, K, M), rng)
+    B = _rand((batch, N, K), rng)
+    C = _run(A, B, 3)
+    ref = np.einsum("bki,bjk->bji", A, B)
+    bound = K * 2.0 ** -21 * np.einsum("bki,bjk->bji", np.abs(A), np.abs(B))
+    assert np.all(np.abs(C - ref) <= bound)
+    assert np.abs(C - ref).max() / np.abs(ref).max() > 1e-12  # (truly complex64)
