@@ -353,8 +353,11 @@ int hps_fp64_rate(double *tflops, void *stream);
  *   descs: as for hps_build_batch (the same p, precision, fp64_levels, leaf_form and
  *          fp64_native); their shapes are measured on scratch data.
  *   ntuned: optional, receives the number of shapes measured.
- * Synchronizes the stream.  Returns HPS_EINVAL, HPS_ENOTSUP, HPS_ENOMEM,
- * HPS_ECUDA. */
+ * With the environment variable HPS_TUNE_CACHE naming a file, the choices
+ * found there are taken without measuring and all choices are written back
+ * after measuring (text, one shape a line), so that another process makes
+ * the same choices.  Synchronizes the stream.  Returns HPS_EINVAL,
+ * HPS_ENOTSUP, HPS_ENOMEM, HPS_ECUDA. */
 int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned);
 
 /* Sizes and operation counts of the solver hps_build would create for desc,

@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -566,6 +567,34 @@ struct TuneKey {
 };
 std::map<TuneKey, int> g_tune;  // product: 1..4 tile, 5 tensor cores; inverse: cs > 0, or -G (wide)
 std::mutex g_tune_mu;
+
+// The measured choices can be kept in a text file (environment variable
+// HPS_TUNE_CACHE): hps_tune reads it before measuring (shapes found there
+// are not measured again) and rewrites it after, so that another process
+// (a profiler run, whose serialised kernels would time differently) makes
+// the same choices.  One line a shape: kind M N K batch f32 choice.
+void tune_cache_load() {
+  const char *path = getenv("HPS_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  TuneKey k;
+  int v;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  while (fscanf(f, "%d %d %d %d %d %d %d", &k.kind, &k.M, &k.N, &k.K, &k.batch, &k.f32, &v) == 7) g_tune[k] = v;
+  fclose(f);
+}
+void tune_cache_store() {
+  const char *path = getenv("HPS_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE *f = fopen(path, "w");
+  if (!f) return;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (const auto &kv : g_tune)
+    fprintf(f, "%d %d %d %d %d %d %d\n", kv.first.kind, kv.first.M, kv.first.N, kv.first.K, kv.first.batch,
+            kv.first.f32, kv.second);
+  fclose(f);
+}
 
 bool tuned(const TuneKey &k, int &v) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -2506,6 +2535,7 @@ int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned) {
       mmax = std::max(mmax, (size_t)hps::gj_meta_ints(S.n3) * r.P);
     }
   }
+  tune_cache_load();
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     for (auto it = todo.begin(); it != todo.end();) it = g_tune.count(it->first) ? todo.erase(it) : std::next(it);
@@ -2676,6 +2706,7 @@ int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned) {
   }
   cleanup();
   if (ntuned) *ntuned = count;
+  tune_cache_store();
   return HPS_OK;
 }
 

@@ -389,6 +389,21 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
+// L2 cache policy "evict last" and loads / stores that carry it
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ double ld_keep(const double *a, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;\n" : "=d"(v) : "l"(a), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_keep(double *a, double v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;\n" ::"l"(a), "d"(v), "l"(pol) : "memory");
+}
+
 // Wait for the phase of `bar` with the given parity to complete.  Gives up
 // (false) when another role of the CTA has given up (*abort set; unless
 // drain, for the waits that let work in flight finish before the CTA exits)
@@ -720,6 +735,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int hf = (warp - 2) >> 2;
     const int row = q * 32 + lane;
     const GemmDesc &g = a.g;
+    // the running sums stay in L2 while the digit planes stream past them
+    const uint64_t keep = l2_evict_last();
     int gi = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
@@ -820,22 +837,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 double sr = oz_term(__uint_as_float(vr[jj]), wk);
                 double si = oz_term(__uint_as_float(vi[jj]), wk);
                 if (!first) {
-                  sr += pr[(size_t)jj * TC_BM];
-                  si += pi[(size_t)jj * TC_BM];
+                  sr += ld_keep(pr + (size_t)jj * TC_BM, keep);
+                  si += ld_keep(pi + (size_t)jj * TC_BM, keep);
                 }
                 if (i < g.M && j < g.N) oz_out(a, b, i, j, sha, sr, si);
               }
             } else if (first) {
 #pragma unroll
               for (int jj = 0; jj < 32; jj++) {
-                pr[(size_t)jj * TC_BM] = oz_term(__uint_as_float(vr[jj]), wk);
-                pi[(size_t)jj * TC_BM] = oz_term(__uint_as_float(vi[jj]), wk);
+                st_keep(pr + (size_t)jj * TC_BM, oz_term(__uint_as_float(vr[jj]), wk), keep);
+                st_keep(pi + (size_t)jj * TC_BM, oz_term(__uint_as_float(vi[jj]), wk), keep);
               }
             } else {
 #pragma unroll
               for (int jj = 0; jj < 32; jj++) {
-                pr[(size_t)jj * TC_BM] += oz_term(__uint_as_float(vr[jj]), wk);
-                pi[(size_t)jj * TC_BM] += oz_term(__uint_as_float(vi[jj]), wk);
+                st_keep(pr + (size_t)jj * TC_BM,
+                        ld_keep(pr + (size_t)jj * TC_BM, keep) + oz_term(__uint_as_float(vr[jj]), wk), keep);
+                st_keep(pi + (size_t)jj * TC_BM,
+                        ld_keep(pi + (size_t)jj * TC_BM, keep) + oz_term(__uint_as_float(vi[jj]), wk), keep);
               }
             }
           }
