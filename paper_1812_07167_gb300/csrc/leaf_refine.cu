@@ -209,7 +209,7 @@ size_t leaf_refined_scratch_bytes(const LeafTables &lt, int count) { return refi
 
 int leaf_refined_launches(const LeafTables &lt, int count, int steps) {
   GemmDesc g = plain_gemm(lt.n, lt.n, lt.n, count, nullptr, 0, nullptr, 1, nullptr);
-  int n = 4;  // X0, B, X = X0, G X
+  int n = 3;  // X0, B, G X
   for (int it = 0; it < steps; it++) n += oz_launches(g, it > 0) + 1;  // residual, correction
   return n;
 }
@@ -244,26 +244,10 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
   leaf_B_kernel<<<count, 256, tsm, st>>>(lt, probs, nprob, leaf0, Bm);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   nl++;
-  // X = X0 (widened)
-  CopyBatch cb;
-  memset(&cb, 0, sizeof(cb));
-  cb.count = 1;
-  cb.d[0].M = n;
-  cb.d[0].N = n;
-  cb.d[0].batch = count;
-  cb.d[0].src.ptr = X0;
-  cb.d[0].src.ld = n;
-  cb.d[0].src.stride = (long long)n * n;
-  cb.d[0].src.f32 = 1;
-  cb.d[0].dst.ptr = Xl;
-  cb.d[0].dst.ld = n;
-  cb.d[0].dst.stride = (long long)n * n;
-  cb.d[0].alpha = make_double2(1.0, 0.0);
-  if ((err = launch_copy(cb, st)) != cudaSuccess) return err;
-  nl++;
   for (int it = 0; it < steps; it++) {
-    // E = I - B X, complex128-accurate on the tensor cores
-    GemmDesc g = plain_gemm(n, n, n, count, Bm, 0, Xl, 0, E);
+    // E = I - B X, complex128-accurate on the tensor cores (X = X0 in the
+    // first step, read in complex64)
+    GemmDesc g = it == 0 ? plain_gemm(n, n, n, count, Bm, 0, X0, 1, E) : plain_gemm(n, n, n, count, Bm, 0, Xl, 0, E);
     g.C.f32 = 1;  // (accurate to complex128 rounding, then rounded to complex64)
     g.alpha = make_double2(-1.0, 0.0);
     g.addI = 1;
@@ -275,10 +259,12 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
     // residual, so it stays in elementwise complex64 arithmetic: a 4-slice
     // tensor-core product, accurate relative to row and column maxima only,
     // left 3e-8 in u)
+    // (first step: X = X0 + X0 E, the widening of X0 folded into the epilogue)
     GemmDesc c = plain_gemm(n, n, n, count, X0, 1, E, 1, Xl);
     c.cf32 = 1;
     c.wide_epilogue = 1;
     c.D = c.C;
+    if (it == 0) c.D = c.A;
     c.beta = make_double2(1.0, 0.0);
     if ((err = launch_gemm(&c, 1, st)) != cudaSuccess) return err;
     nl++;
