@@ -760,8 +760,8 @@ def zgemm(args, local_rank):
 def scaling(args, local_rank):
     """Build and solve times across leaf counts (4 x 4 ... 128 x 128, p = 16,
     kappa = eta = 80, the point-source workload at each size) for the LU and
-    inverse leaf forms in complex128 and the LU form on the mixed path: one
-    JSON line per problem.  Builds: median of 3 (2 at 128 x 128) after the
+    inverse leaf forms in complex128 and the inverse form on the mixed path:
+    one JSON line per problem.  Builds: median of 3 (2 at 128 x 128) after the
     problem's kernel choices are measured; solves with device-resident
     vectors, 1 RHS (median of 10) and a wide batch (64 RHS, 16 at 128 x 128)."""
     import torch
@@ -774,7 +774,7 @@ def scaling(args, local_rank):
     for m in (4, 8, 16, 32, 64, 128):
         wl = W.point_sources(m=m, p=P_ORDER, kappa=KAPPA)
         for form, prec in ((hps.HPS_LEAF_LU, hps.HPS_FP64), (hps.HPS_LEAF_INVERSE, hps.HPS_FP64),
-                           (hps.HPS_LEAF_LU, hps.HPS_MIXED)):
+                           (hps.HPS_LEAF_INVERSE, hps.HPS_MIXED)):
             pr = hps.Problem(m, P_ORDER, KAPPA, KAPPA, precision=prec, leaf_form=form)
             lxy, bxy = hps.hps_nodes(pr)
             c, s, t = wl.sample(lxy, bxy)
