@@ -200,29 +200,31 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 }
 
 // Complex64 products without index maps (the refinement corrections X0 E,
-// the mixed path's dense products): 128 x 128 tiles, 256 threads with 8 x 8
-// outputs each at rows tx + 16 r and columns ty + 16 c (64 complex
-// multiply-adds for 16 shared-memory loads a k), K in steps of 16 with the
-// next step's tiles loaded into registers while the current one is
-// multiplied.  TA, TB: the storage types of A and B (complex64 or complex128,
-// converted on load).
+// the mixed path's dense products): 128 x BN tiles (BN = 128 or 64), 256
+// threads with 8 x TN outputs each (TN = BN / 16) at rows tx + 16 r and
+// columns ty + 16 c (8 TN complex multiply-adds for 8 + TN shared-memory
+// loads a k), K in steps of 16 with the next step's tiles loaded into
+// registers while the current one is multiplied.  BN = 64 halves the
+// registers, so that two CTAs share an SM.  TA, TB: the storage types of A
+// and B (complex64 or complex128, converted on load).
 constexpr int kCg = 128, kCgK = 16;
-template <class TA, class TB>
-__global__ void __launch_bounds__(256, 1) cgemm64_kernel(const __grid_constant__ GemmPack pack) {
+template <class TA, class TB, int BN>
+__global__ void __launch_bounds__(256, BN == 128 ? 1 : 2) cgemm64_kernel(const __grid_constant__ GemmPack pack) {
   chain_enter();
+  constexpr int TN = BN / 16, QB = BN / 16;  // outputs a thread along N; B elements a thread loads
   __shared__ float2 As[kCgK][kCg];
-  __shared__ float2 Bs[kCgK][kCg];
+  __shared__ float2 Bs[kCgK][BN];
   const GemmDesc &g = pack.d[blockIdx.z];
-  const int tiles_m = (g.M + kCg - 1) / kCg, tiles_n = (g.N + kCg - 1) / kCg;
+  const int tiles_m = (g.M + kCg - 1) / kCg, tiles_n = (g.N + BN - 1) / BN;
   if ((int)blockIdx.x >= tiles_m * tiles_n) return;
-  const int m0 = (blockIdx.x % tiles_m) * kCg, n0 = (blockIdx.x / tiles_m) * kCg;
+  const int m0 = (blockIdx.x % tiles_m) * kCg, n0 = (blockIdx.x / tiles_m) * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int b = blockIdx.y; b < g.batch; b += gridDim.y) {
     const TA *A = (const TA *)g.A.ptr + (size_t)b * g.A.stride;
     const TB *B = (const TB *)g.B.ptr + (size_t)b * g.B.stride;
     // element q of this thread's share of a tile: A rows (tid % 128), k pairs
     // (tid / 128 + 2 q); B k (tid % 16), columns (tid / 16 + 16 q)
-    float2 pa[8], pb[8];
+    float2 pa[8], pb[QB];
     auto fetch = [&](int k0) {
 #pragma unroll
       for (int q = 0; q < 8; q++) {
@@ -233,6 +235,9 @@ __global__ void __launch_bounds__(256, 1) cgemm64_kernel(const __grid_constant__
           v = make_float2((float)t.x, (float)t.y);
         }
         pa[q] = v;
+      }
+#pragma unroll
+      for (int q = 0; q < QB; q++) {
         const int kb = k0 + (tid & 15), j = n0 + (tid >> 4) + 16 * q;
         float2 w = make_float2(0.f, 0.f);
         if (kb < g.K && j < g.N) {
@@ -242,38 +247,37 @@ __global__ void __launch_bounds__(256, 1) cgemm64_kernel(const __grid_constant__
         pb[q] = w;
       }
     };
-    float2 acc[8][8];
+    float2 acc[8][TN];
 #pragma unroll
     for (int r = 0; r < 8; r++)
 #pragma unroll
-      for (int c = 0; c < 8; c++) acc[r][c] = make_float2(0.f, 0.f);
+      for (int c = 0; c < TN; c++) acc[r][c] = make_float2(0.f, 0.f);
     fetch(0);
     for (int k0 = 0; k0 < g.K; k0 += kCgK) {
 #pragma unroll
-      for (int q = 0; q < 8; q++) {
-        As[(tid >> 7) + 2 * q][tid & 127] = pa[q];
-        Bs[tid & 15][(tid >> 4) + 16 * q] = pb[q];
-      }
+      for (int q = 0; q < 8; q++) As[(tid >> 7) + 2 * q][tid & 127] = pa[q];
+#pragma unroll
+      for (int q = 0; q < QB; q++) Bs[tid & 15][(tid >> 4) + 16 * q] = pb[q];
       __syncthreads();
       if (k0 + kCgK < g.K) fetch(k0 + kCgK);
 #pragma unroll 4
       for (int k = 0; k < kCgK; k++) {
-        float2 a[8], bv[8];
+        float2 a[8], bv[TN];
 #pragma unroll
         for (int r = 0; r < 8; r++) a[r] = As[k][tx + 16 * r];
 #pragma unroll
-        for (int c = 0; c < 8; c++) bv[c] = Bs[k][ty + 16 * c];
+        for (int c = 0; c < TN; c++) bv[c] = Bs[k][ty + 16 * c];
 #pragma unroll
         for (int r = 0; r < 8; r++)
 #pragma unroll
-          for (int c = 0; c < 8; c++) cmac(acc[r][c], a[r], bv[c]);
+          for (int c = 0; c < TN; c++) cmac(acc[r][c], a[r], bv[c]);
       }
       __syncthreads();
     }
 #pragma unroll
     for (int r = 0; r < 8; r++)
 #pragma unroll
-      for (int c = 0; c < 8; c++) {
+      for (int c = 0; c < TN; c++) {
         const int i = m0 + tx + 16 * r, j = n0 + ty + 16 * c;
         if (i < g.M && j < g.N) epilogue<float2>(g, b, i, j, acc[r][c]);
       }
@@ -488,20 +492,28 @@ bool cg64_fits(const GemmPack &pk) {
   return true;
 }
 
-cudaError_t launch_cg64(const GemmPack &pk, cudaStream_t st) {
+template <int BN>
+cudaError_t launch_cg64_bn(const GemmPack &pk, cudaStream_t st) {
   int maxtiles = 0, maxbatch = 0;
   for (int q = 0; q < pk.n; q++) {
     const GemmDesc &g = pk.d[q];
-    maxtiles = std::max(maxtiles, ((g.M + kCg - 1) / kCg) * ((g.N + kCg - 1) / kCg));
+    maxtiles = std::max(maxtiles, ((g.M + kCg - 1) / kCg) * ((g.N + BN - 1) / BN));
     maxbatch = std::max(maxbatch, g.batch);
   }
   if (maxtiles == 0 || maxbatch == 0) return cudaSuccess;
   dim3 grid(maxtiles, maxbatch < 65535 ? maxbatch : 65535, pk.n);
   const bool af = pk.d[0].A.f32, bf = pk.d[0].B.f32;
-  if (af && bf) return launch_k(cgemm64_kernel<float2, float2>, grid, dim3(256), 0, st, pk);
-  if (af) return launch_k(cgemm64_kernel<float2, double2>, grid, dim3(256), 0, st, pk);
-  if (bf) return launch_k(cgemm64_kernel<double2, float2>, grid, dim3(256), 0, st, pk);
-  return launch_k(cgemm64_kernel<double2, double2>, grid, dim3(256), 0, st, pk);
+  if (af && bf) return launch_k(cgemm64_kernel<float2, float2, BN>, grid, dim3(256), 0, st, pk);
+  if (af) return launch_k(cgemm64_kernel<float2, double2, BN>, grid, dim3(256), 0, st, pk);
+  if (bf) return launch_k(cgemm64_kernel<double2, float2, BN>, grid, dim3(256), 0, st, pk);
+  return launch_k(cgemm64_kernel<double2, double2, BN>, grid, dim3(256), 0, st, pk);
+}
+
+// 128 x 128 tiles (cfg 6) or 128 x 64 (cfg 7); by rule the narrower tile
+// (two CTAs an SM)
+cudaError_t launch_cg64(const GemmPack &pk, cudaStream_t st) {
+  if (pk.d[0].cfg == 6) return launch_cg64_bn<128>(pk, st);
+  return launch_cg64_bn<64>(pk, st);
 }
 
 template <class C>
@@ -518,6 +530,7 @@ cudaError_t launch_typed(const GemmPack &pk, int maxN, cudaStream_t st) {
   const bool c64 = sizeof(C) == sizeof(float2) && cg64_fits(pk);
   switch (pk.d[0].cfg) {  // a measured choice (hps_tune)
     case 6:
+    case 7:
       if (c64) return launch_cg64(pk, st);
       break;
     case 1: return launch_cfg<C, 64, 64, 16, 4, 4>(pk, st);

@@ -2145,7 +2145,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
       int nr = 0;
       for (int q = 0; q < nd; q++) {
         int v;
-        if (tuned(TuneKey{0, gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32}, v) && v >= 1 && v <= 6 && v != 5)
+        if (tuned(TuneKey{0, gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32}, v) && v >= 1 && v <= 7 && v != 5)
           gd[q].cfg = v;
         if (oz_shape(gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32, P0.oz)) {
           CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, st, d_status));
@@ -2604,9 +2604,9 @@ int hps_tune(int nprob, const hps_desc *descs, void *stream, int *ntuned) {
                         mat(buf + oC, k.M, (long long)k.M * k.N, nullptr, nullptr, k.f32));
       g.cf32 = k.f32;
       auto none = [&]() { return cudaSuccess; };
-      for (int cand = 1; cand <= 6; cand++) {
+      for (int cand = 1; cand <= 7; cand++) {
         if (cand == 5 && (!P0.oz || k.K < 32 || k.batch > 65535)) continue;
-        if (cand == 6 && (!k.f32 || k.M < 96 || k.N < 96)) continue;
+        if (cand >= 6 && (!k.f32 || k.M < 96 || k.N < 96)) continue;
         float ms;
         if (cand == 5) {
           const size_t need = hps::oz_workspace_bytes(g);

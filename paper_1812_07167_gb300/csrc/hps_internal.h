@@ -38,7 +38,7 @@ struct GemmDesc {
   // product (a complex64 correction added to a complex128 matrix)
   int wide_epilogue;
   int cfg;  // tile configuration for N > 8: 0 = by rule, 1..4 = 64x64, 32x32, 16x16, 64x16,
-           // 6 = 128x128 (complex64 products without index maps)
+           // 6, 7 = 128x128, 128x64 (complex64 products without index maps)
   // N <= 16: scratch that lets the skinny kernel split K over several CTAs
   // (without it, products with 9 .. 16 columns take the tiled kernel)
   // (partial sums of up to kGemvBlocks row blocks x 16 splits x 32 rows x N,
