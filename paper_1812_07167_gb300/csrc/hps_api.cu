@@ -703,11 +703,14 @@ int gj_launches(int n3, long long P, bool oz, const GJChoice &g) {
 }
 
 // Does a product of this shape go to the tensor cores (Ozaki scheme: 9
-// slices an operand in complex128, 4 for the complex64 products)?
+// slices an operand in complex128, 5 for the complex64 products)?  Complex64
+// products only where hps_tune measured it faster (at the mixed path's
+// shapes it chose the FP32-pipe tiles every time: 64 x 64 leaves, p = 16).
 bool oz_shape(int M, int N, int K, int batch, int f32, bool oz) {
   if (!oz) return false;
   int v;
   if (tuned(TuneKey{0, M, N, K, batch, f32}, v)) return v == 5;
+  if (f32) return false;
   GemmDesc g;
   memset(&g, 0, sizeof(g));
   g.M = M;

@@ -59,6 +59,9 @@ def _mixed(m, p, kappa, eta, fp64_levels=0, refine_steps=0, leaf_form=hps.HPS_LE
 @pytest.mark.parametrize("m,p,kappa,fp64_levels,nrhs,form", [
     (2, 10, 15.0, 0, 1, 0), (4, 16, 20.0, 0, 2, 0), (8, 12, 30.0, 0, 3, 0), (8, 16, 40.0, 1, 1, 0),
     (16, 16, 80.0, 4, 12, 0), (4, 16, 20.0, 0, 2, 1), (16, 16, 80.0, 4, 40, 1), (16, 16, 80.0, 4, 40, 0),
+    # complex64 inverse-form leaves with n = p^2 - 4 in (256, 384] (the 6-row blocking of the
+    # 32-column leaf kernel, with G X0) and above 384 (the cluster kernel)
+    (4, 18, 30.0, 0, 2, 1), (2, 20, 25.0, 0, 1, 1), (4, 9, 12.0, 0, 1, 1),
 ])
 def test_mixed_matches_oracle(m, p, kappa, fp64_levels, nrhs, form):
     c, s, t = W.random_data(m, p, kappa, kappa, seed=700 + m + p, nrhs=nrhs)
