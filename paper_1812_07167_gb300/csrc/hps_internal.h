@@ -167,6 +167,10 @@ int oz_launches(const GemmDesc &g, bool reuse_a = false);
 size_t oz_workspace_bytes(const GemmDesc &g);
 cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st,
                            unsigned *status = nullptr, bool reuse_a = false);
+// A's exponents and digits alone (2 launches), for a later launch_gemm_oz
+// with reuse_a on the same workspace (the split can then run ahead, on
+// another stream, while what B depends on is still being computed).
+cudaError_t launch_oz_split_a(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st);
 cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st);
 
 // ---- one-launch solves (solve_engine.cu) ----

@@ -17,6 +17,7 @@
 // inversion, with most of the work off this part's FP64 pipes.
 #include <algorithm>
 #include <cstring>
+#include <map>
 
 #include "cx.cuh"
 #include "hps_internal.h"
@@ -25,6 +26,26 @@
 namespace hps {
 
 namespace {
+
+// A second stream of the same device and priority as st for work that can
+// run beside st's (one a host thread and priority, created once).
+cudaStream_t side_stream(cudaStream_t st) {
+  int prio = 0, dev = 0;
+  if (cudaStreamGetPriority(st, &prio) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  thread_local std::map<std::pair<int, int>, cudaStream_t> streams;
+  auto it = streams.find({dev, prio});
+  if (it != streams.end()) return it->second;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio) != cudaSuccess) {
+    cudaGetLastError();
+    s = nullptr;
+  }
+  streams[{dev, prio}] = s;
+  return s;
+}
 
 // the problem of leaf `leaf`: the last one starting at or before it
 __device__ __forceinline__ int leaf_problem(const LeafProb *probs, int nprob, long long leaf) {
@@ -228,22 +249,50 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
   double2 *Xl = (double2 *)X + (size_t)leaf0 * n * n;
   double2 *GXl = (double2 *)GX + (size_t)leaf0 * n * nb;
   int nl = 0;
+  // B in FP64 and its digit split (the residuals' first operand) do not
+  // depend on X0: they run on a side stream while the complex64 inverse
+  // (whose 256 CTAs leave a third of the SMs half empty) runs on st
+  const size_t tsm = leaf_tables_smem(lt);
+  GemmDesc g0 = plain_gemm(n, n, n, count, Bm, 0, X0, 1, E);
+  cudaStream_t side = side_stream(st);
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaError_t err = cudaSuccess;
+  if (side && (err = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) == cudaSuccess &&
+      (err = cudaEventCreateWithFlags(&join, cudaEventDisableTiming)) == cudaSuccess &&
+      (err = cudaEventRecord(fork, st)) == cudaSuccess && (err = cudaStreamWaitEvent(side, fork, 0)) == cudaSuccess) {
+    leaf_B_kernel<<<count, 256, tsm, side>>>(lt, probs, nprob, leaf0, Bm);
+    if ((err = cudaGetLastError()) == cudaSuccess) err = launch_oz_split_a(g0, w + L.oz, L.total - L.oz, side);
+    if (err == cudaSuccess) err = cudaEventRecord(join, side);
+  } else {
+    cudaGetLastError();
+    side = nullptr;
+  }
+  if (err != cudaSuccess) {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    return err;
+  }
+  nl += 3;  // B, A's exponents and digits
   // X0: the complex64 inverse (32-column panels, one CTA a leaf; the
   // cluster kernel where the panel does not fit; its G X0 is not used)
-  cudaError_t err =
+  err =
       gj32_supported(lt)
           ? launch_leaf_gj32(lt, probs, nprob, leaf0, count, (float2 *)X0 - (size_t)leaf0 * n * n, nullptr, w + L.s,
                              status, level, st)
           : launch_leaf(lt, probs, nprob, leaf0, count, (float2 *)X0 - (size_t)leaf0 * n * n,
                         (float2 *)(w + L.gx0) - (size_t)leaf0 * n * nb, w + L.s, (int *)(w + L.meta), status, level,
                         cs32, true, st);
+  if (err == cudaSuccess) nl++;
+  if (side) {
+    // (without a side stream: B and its split here, in order)
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, join, 0);
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
+  } else if (err == cudaSuccess) {
+    leaf_B_kernel<<<count, 256, tsm, st>>>(lt, probs, nprob, leaf0, Bm);
+    if ((err = cudaGetLastError()) == cudaSuccess) err = launch_oz_split_a(g0, w + L.oz, L.total - L.oz, st);
+  }
   if (err != cudaSuccess) return err;
-  nl++;
-  // B in FP64
-  const size_t tsm = leaf_tables_smem(lt);
-  leaf_B_kernel<<<count, 256, tsm, st>>>(lt, probs, nprob, leaf0, Bm);
-  if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  nl++;
   for (int it = 0; it < steps; it++) {
     // E = I - B X, complex128-accurate on the tensor cores (X = X0 in the
     // first step, read in complex64)
@@ -252,8 +301,9 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
     g.alpha = make_double2(-1.0, 0.0);
     g.addI = 1;
     // (B's digits are the same in every step: split once)
-    if ((err = launch_gemm_oz(g, w + L.oz, L.total - L.oz, st, status, it > 0)) != cudaSuccess) return err;
-    nl += oz_launches(g, it > 0);
+    // (B's digits are in the workspace already: split once, above)
+    if ((err = launch_gemm_oz(g, w + L.oz, L.total - L.oz, st, status, true)) != cudaSuccess) return err;
+    nl += oz_launches(g, true);
     // X += X0 E: the product in complex64 arithmetic, the addition in FP64
     // (the error of this product is amplified by cond(B) in the next
     // residual, so it stays in elementwise complex64 arithmetic: a 4-slice

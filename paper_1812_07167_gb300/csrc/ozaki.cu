@@ -1014,6 +1014,24 @@ bool oz_eligible(const GemmDesc &g) {
 
 size_t oz_workspace_bytes(const GemmDesc &g) { return oz_layout(g, num_sms()).total; }
 
+cudaError_t launch_oz_split_a(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st) {
+  if (g.batch <= 0 || g.M <= 0 || g.N <= 0) return cudaSuccess;
+  const OzLayout L = oz_layout(g, num_sms());
+  if (!ws || ws_bytes < L.total || g.batch > 65535 || ((uintptr_t)ws & 255)) return cudaErrorInvalidValue;
+  char *w = (char *)ws;
+  int *ea = (int *)(w + L.ea_off);
+  oz_expo_a_kernel<<<dim3(L.Mp / 32, g.batch), 256, 0, st>>>(g, L.Mp, ea);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const dim3 ga(L.Mp / OZA_R, L.Kp / OZA_K, g.batch);
+  __nv_bfloat16 *Ad = (__nv_bfloat16 *)(w + L.a_off);
+  if (L.S == OZ_S32)
+    oz_split_a_kernel<OZ_S32><<<ga, 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
+  else
+    oz_split_a_kernel<OZ_S><<<ga, 256, 0, st>>>(g, L.Mp, L.Kp, Ad, ea);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st, unsigned *status,
                            bool reuse_a) {
   if (g.batch <= 0 || g.M <= 0 || g.N <= 0) return cudaSuccess;
