@@ -2183,7 +2183,7 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
     void *ozws = oz_bytes ? scratch + align256(sbytes) : nullptr;
     char *wrscr = wref_bytes ? scratch + align256(sbytes) + align256(oz_bytes) : nullptr;
     // products: emulated ones one at a time, the rest in one launch
-    auto run_gemm = [&](GemmDesc *gd, int nd) -> int {
+    auto run_gemm_on = [&](GemmDesc *gd, int nd, cudaStream_t s) -> int {
       GemmDesc rest[2];
       int nr = 0;
       for (int q = 0; q < nd; q++) {
@@ -2191,18 +2191,36 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
         if (tuned(TuneKey{0, gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32}, v) && v >= 1 && v <= 7 && v != 5)
           gd[q].cfg = v;
         if (oz_shape(gd[q].M, gd[q].N, gd[q].K, gd[q].batch, gd[q].cf32, P0.oz)) {
-          CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, st, d_status));
+          CK(hps::launch_gemm_oz(gd[q], ozws, oz_bytes, s, d_status));
           launches += hps::oz_launches(gd[q]);
         } else {
           rest[nr++] = gd[q];
         }
       }
       if (nr) {
-        CK(hps::launch_gemm(rest, nr, st));
+        CK(hps::launch_gemm(rest, nr, s));
         launches++;
       }
       return HPS_OK;
     };
+    auto run_gemm = [&](GemmDesc *gd, int nd) -> int { return run_gemm_on(gd, nd, st); };
+    // Q = R33b R31a does not depend on W^{-1}: it runs on a side stream while
+    // W^{-1} (a chain of small dependent launches) is formed.  (W^{-1} uses
+    // no part of the products' workspace, so Q may use it meanwhile.)
+    cudaStream_t side = hps::side_stream(st);
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (side && (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      side = nullptr;
+    }
+    struct EvGuard {
+      cudaEvent_t &a, &b;
+      ~EvGuard() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+      }
+    } ev_guard{fork, join};
 
     auto sub = [&](Mat m, const int *r, const int *c) {
       m.rmap = r;
@@ -2290,12 +2308,20 @@ static int build_many(const std::vector<hps_handle *> &hs, const std::vector<con
         g.cf32 = f;
         if (int rc = run_gemm(&g, 1)) return rc;
         const int lev = S.lev;  // the tallest tree's level numbering
-        if (int rc = w_inverse(r.gj, Wscr, Winv, n3, P, wmeta, d_status, lev, f != 0, wrscr, P0.oz, st, launches))
-          return rc;
-        // Q(:, :n1) = R33b R31a
+        // Q(:, :n1) = R33b R31a, beside W^{-1} when there is a side stream
         g = gemm(n3, n1, n3, P, M(R33b, n3, s33), sub(Ra, dI3a, dI1), M(Q, n3, s3t));
         g.cf32 = f;
-        if (int rc = run_gemm(&g, 1)) return rc;
+        if (side) {
+          CK(cudaEventRecord(fork, st));
+          CK(cudaStreamWaitEvent(side, fork, 0));
+          if (int rc = run_gemm_on(&g, 1, side)) return rc;
+          CK(cudaEventRecord(join, side));
+        } else if (int rc = run_gemm(&g, 1)) {
+          return rc;
+        }
+        if (int rc = w_inverse(r.gj, Wscr, Winv, n3, P, wmeta, d_status, lev, f != 0, wrscr, P0.oz, st, launches))
+          return rc;
+        if (side) CK(cudaStreamWaitEvent(st, join, 0));
         // Phi_a = W^{-1} Q
         g = gemm(n3, nt, n3, P, M(Winv, n3, s33), M(Q, n3, s3t), M(Phia, n3, s3t));
         g.cf32 = f;

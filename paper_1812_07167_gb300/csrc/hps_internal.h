@@ -259,6 +259,9 @@ size_t gj32_smem_bytes(const LeafTables &lt);
 cudaError_t launch_leaf_gj32(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0, int count,
                              void *X0, void *GX, void *S, unsigned int *status, int level, cudaStream_t st);
 size_t leaf_refined_scratch_bytes(const LeafTables &lt, int count);
+// A second stream of st's device and priority, for work that can run beside
+// st's (one a host thread, device and priority; null if it cannot be made).
+cudaStream_t side_stream(cudaStream_t st);
 int leaf_refined_launches(const LeafTables &lt, int count, int steps);
 cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int nprob, long long leaf0, int count,
                                 void *X, void *GX, void *scr, size_t scr_bytes, unsigned int *status, int level,

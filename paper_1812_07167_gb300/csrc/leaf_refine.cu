@@ -27,26 +27,6 @@ namespace hps {
 
 namespace {
 
-// A second stream of the same device and priority as st for work that can
-// run beside st's (one a host thread and priority, created once).
-cudaStream_t side_stream(cudaStream_t st) {
-  int prio = 0, dev = 0;
-  if (cudaStreamGetPriority(st, &prio) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  thread_local std::map<std::pair<int, int>, cudaStream_t> streams;
-  auto it = streams.find({dev, prio});
-  if (it != streams.end()) return it->second;
-  cudaStream_t s = nullptr;
-  if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio) != cudaSuccess) {
-    cudaGetLastError();
-    s = nullptr;
-  }
-  streams[{dev, prio}] = s;
-  return s;
-}
-
 // the problem of leaf `leaf`: the last one starting at or before it
 __device__ __forceinline__ int leaf_problem(const LeafProb *probs, int nprob, long long leaf) {
   int pk = 0;
@@ -225,6 +205,26 @@ RefineLayout refine_layout(const LeafTables &lt, int count) {
 }
 
 }  // namespace
+
+// A second stream of the same device and priority as st for work that can
+// run beside st's (one a host thread and priority, created once).
+cudaStream_t side_stream(cudaStream_t st) {
+  int prio = 0, dev = 0;
+  if (cudaStreamGetPriority(st, &prio) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  thread_local std::map<std::pair<int, int>, cudaStream_t> streams;
+  auto it = streams.find({dev, prio});
+  if (it != streams.end()) return it->second;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio) != cudaSuccess) {
+    cudaGetLastError();
+    s = nullptr;
+  }
+  streams[{dev, prio}] = s;
+  return s;
+}
 
 size_t leaf_refined_scratch_bytes(const LeafTables &lt, int count) { return refine_layout(lt, count).total; }
 
