@@ -898,7 +898,7 @@ def serving_run(args, local_rank, precision):
     m, p, kappa = args.serve_m, P_ORDER, 600.0
     # the resident solver only solves (wide batches): leaf operators as B^-1,
     # whose product runs on the tensor cores; the build requests take the
-    # leaf form given on the command line (LU by default, the faster build)
+    # leaf form given on the command line (B^-1 by default, the faster build)
     pr = hps.Problem(m, p, kappa, kappa, precision=precision,
                      leaf_form=hps.HPS_LEAF_INVERSE if args.serve_resident_form == "inverse" else hps.HPS_LEAF_LU)
     lxy, _ = hps.hps_nodes(pr)
