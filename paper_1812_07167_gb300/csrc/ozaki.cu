@@ -407,16 +407,16 @@ __device__ __forceinline__ void st_keep(double *a, double v, uint64_t pol) {
 // Wait for the phase of `bar` with the given parity to complete.  Gives up
 // (false) when another role of the CTA has given up (*abort set; unless
 // drain, for the waits that let work in flight finish before the CTA exits)
-// or after kWaitNs, then sets *abort and records a timeout in the status word.
+// or after limit_ns, then sets *abort and records a timeout in the status word.
 __device__ __noinline__ bool bar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, unsigned *status,
-                                      bool drain = false) {
+                                      bool drain = false, uint64_t limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (true) {
     for (int q = 0; q < 64; q++)
       if (mbar_try_wait(bar, parity)) return true;
     if (!drain && *abort) return false;
-    if (global_ns() - t0 > kWaitNs) {
+    if (global_ns() - t0 > limit_ns) {
       *abort = 1;
       if (status) record_status(status, kStatusTimeout, 0, (int)(blockIdx.x + gridDim.x * blockIdx.y));
       return false;
@@ -997,6 +997,20 @@ cudaError_t launch_product(const OzLayout &L, const TcArgs &a, const void *Ad, c
   return cudaGetLastError();
 }
 
+// One thread waits, with the pipeline's bounded wait, on an mbarrier that
+// nothing arrives at: phase 0 of a barrier initialised for one arrival
+// completes only with that arrival.  The wait gives up after limit_ns and
+// records a timeout in the status word; the kernel then returns.
+__global__ void wait_check_kernel(unsigned *status, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_sh;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  abort_sh = 0;
+  fence_mbar_init();
+  bar_wait(&bar, 0u, &abort_sh, status, false, limit_ns);
+}
+
 }  // namespace
 
 void oz_set_timer(OzTimer *t) { g_oz_timer = t; }
@@ -1078,6 +1092,12 @@ cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStr
   a.eb = eb;
   a.status = status;
   return L.bn == 64 ? launch_product<64>(L, a, Ad, Bd, st) : launch_product<128>(L, a, Ad, Bd, st);
+}
+
+cudaError_t launch_wait_check(unsigned *status, int limit_ms, cudaStream_t st) {
+  if (!status || limit_ms < 1) return cudaErrorInvalidValue;
+  wait_check_kernel<<<1, 32, 0, st>>>(status, (uint64_t)limit_ms * 1000000ull);
+  return cudaGetLastError();
 }
 
 }  // namespace hps
