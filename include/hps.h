@@ -334,6 +334,40 @@ int hps_leaf_ops(hps_handle *h, int leaf, double *Psi, double *Y, double *Gam, v
 int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, double *C, int emulated,
               void *stream);
 
+/* Batched inverse of complex128 matrices with the library's interface-inverse
+ * kernels (Sec. 2.2's W^{-1}: Gauss-Jordan elimination with partial pivoting
+ * in panels of 8 (or 4) columns, one CTA or thread-block cluster a matrix, or,
+ * when the batch is too small to fill the device, one launch a panel over
+ * CTAs that share each matrix).  A: batch n x n matrices, column-major,
+ * complex128 interleaved (re, im), batch stride n^2 complex, device memory,
+ * read only (a copy is eliminated); Ainv: the same layout, device memory,
+ * written (it may be A itself).
+ * mode = 0: the elimination in complex128.  mode = 1: the regime a build takes
+ * for this (n, batch): where the elimination would be a chain of per-panel
+ * launches, a complex64 inverse refined by two complex128 residual steps
+ * (E = I - A X on the tensor cores or the FP64 pipes, X += X0 E), which
+ * reaches complex128 accuracy for matrices whose entries complex64 represents
+ * and whose condition number is far below 1e7 (the interface matrices: < 100).
+ * Returns HPS_OK; HPS_ESINGULAR when an elimination met an exactly zero pivot
+ * column (*bad, when not NULL, receives the index of the matrix the device
+ * recorded first; that matrix's Ainv is unspecified, the others are valid);
+ * HPS_EINVAL (n < 2, batch < 1 or > 2^20, mode not 0 or 1, NULL or host
+ * arrays, or no regime of the kernels fits this n); HPS_ENOMEM (scratch of
+ * about 16 n^2 batch bytes, three times that with mode 1); HPS_ETIMEOUT (a wait
+ * of the tensor-core residual gave up); HPS_ECUDA.  Synchronizes the stream
+ * (it reads the device status word).  *bad = -1 unless HPS_ESINGULAR. */
+int hps_zinv(int n, int batch, const double *A, double *Ainv, int mode, int *bad, void *stream);
+
+/* A check of the device-side failure reporting that needs no failing
+ * computation: one thread of one CTA runs the tensor-core product's bounded
+ * pipeline wait (the mbarrier wait with a time limit) on a barrier that
+ * nothing completes, with a limit of limit_ms milliseconds instead of the
+ * products' 2 s.  The wait gives up, records a timeout in a status word and
+ * the kernel returns, leaving the context usable.  Returns HPS_ETIMEOUT (the
+ * expected result), HPS_OK only if the wait completed, HPS_EINVAL (limit_ms
+ * not in 1 .. 2000), HPS_ENOMEM, HPS_ECUDA.  Synchronizes the stream. */
+int hps_check_wait(int limit_ms, void *stream);
+
 /* The FP64 fused multiply-add rate of the current device, measured: a
  * kernel of independent FMA chains on every SM, timed with CUDA events on
  * `stream` (best of 3 after a warm-up, about 20 ms each).  *tflops receives

@@ -2449,6 +2449,66 @@ int hps_zgemm(int M, int N, int K, int batch, const double *A, const double *B, 
   return HPS_OK;
 }
 
+int hps_zinv(int n, int batch, const double *A, double *Ainv, int mode, int *bad, void *stream) {
+  if (bad) *bad = -1;
+  if (n < 2 || batch < 1 || batch > (1 << 20) || mode < 0 || mode > 1) return HPS_EINVAL;
+  if (!A || !Ainv || !is_device_ptr(A) || !is_device_ptr(Ainv)) return HPS_EINVAL;
+  // the regime: as the build chooses for P = batch interface matrices of
+  // order n (mode 1), or its complex128 elimination (mode 0)
+  GJChoice g;
+  if (mode == 1 ? !choose_gj(n, batch, 0, g) : !choose_gj_rule(n, batch, 0, g)) return HPS_EINVAL;
+  if (mode == 0) g.refined = false;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t elems = (size_t)n * n * batch;
+  const size_t o_meta = align256(16 * elems);
+  const size_t o_status = o_meta + align256(sizeof(int) * hps::gj_meta_ints(n) * (size_t)batch);
+  const size_t o_ref = o_status + 256;
+  const size_t total = o_ref + (g.refined ? wref_layout(n, batch, true).total : 0);
+  char *w = nullptr;
+  CK(lib_malloc_async((void **)&w, total, st));
+  unsigned *status = (unsigned *)(w + o_status);
+  unsigned word = 0;
+  int launches = 0;
+  int rc = HPS_OK;
+  cudaError_t err = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(w, A, 16 * elems, cudaMemcpyDeviceToDevice, st);
+  if (err == cudaSuccess)
+    rc = w_inverse(g, w, Ainv, n, batch, (int *)(w + o_meta), status, 0, false, g.refined ? w + o_ref : nullptr,
+                   true, st, launches);
+  if (err == cudaSuccess && rc == HPS_OK)
+    err = cudaMemcpyAsync(&word, status, sizeof(word), cudaMemcpyDeviceToHost, st);
+  const cudaError_t err_free = cudaFreeAsync(w, st);
+  const cudaError_t err_sync = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) return cuda_fail(err);
+  if (rc != HPS_OK) return rc;
+  if (err_free != cudaSuccess) return cuda_fail(err_free);
+  if (err_sync != cudaSuccess) return cuda_fail(err_sync);
+  if (!word) return HPS_OK;
+  // codes 1, 2: a zero pivot (box = the matrix); 3: a wait of the
+  // tensor-core residual product gave up (box = its CTA)
+  if ((word >> 28) == 3u) return HPS_ETIMEOUT;
+  if (bad) *bad = (int)(word & 0xfffff);
+  return HPS_ESINGULAR;
+}
+
+int hps_check_wait(int limit_ms, void *stream) {
+  if (limit_ms < 1 || limit_ms > 2000) return HPS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned *status = nullptr;
+  CK(lib_malloc_async((void **)&status, sizeof(unsigned), st));
+  unsigned word = 0;
+  cudaError_t err = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
+  if (err == cudaSuccess) err = hps::launch_wait_check(status, limit_ms, st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&word, status, sizeof(word), cudaMemcpyDeviceToHost, st);
+  const cudaError_t err_free = cudaFreeAsync(status, st);
+  const cudaError_t err_sync = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) return cuda_fail(err);
+  if (err_free != cudaSuccess) return cuda_fail(err_free);
+  if (err_sync != cudaSuccess) return cuda_fail(err_sync);
+  if (!word) return HPS_OK;
+  return (word >> 28) == 3u ? HPS_ETIMEOUT : HPS_ECUDA;
+}
+
 int hps_plan(const hps_desc *desc, hps_info_t *info) {
   if (!info) return HPS_EINVAL;
   hps_handle *h = new (std::nothrow) hps_handle();

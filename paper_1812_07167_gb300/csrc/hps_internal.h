@@ -171,6 +171,10 @@ cudaError_t launch_gemm_oz(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStr
 // with reuse_a on the same workspace (the split can then run ahead, on
 // another stream, while what B depends on is still being computed).
 cudaError_t launch_oz_split_a(const GemmDesc &g, void *ws, size_t ws_bytes, cudaStream_t st);
+// One thread runs the products' bounded mbarrier wait on a barrier that
+// nothing completes, with a limit of limit_ms: it gives up, records code 3 in
+// *status and returns (a check of the failure reporting).
+cudaError_t launch_wait_check(unsigned *status, int limit_ms, cudaStream_t st);
 cudaError_t launch_copy(const CopyBatch &cb, cudaStream_t st);
 
 // ---- one-launch solves (solve_engine.cu) ----

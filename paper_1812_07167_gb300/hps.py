@@ -29,7 +29,7 @@ HPS_LEAF_INVERSE = 1
 
 # every entry point include/hps.h declares
 EXPORTS = ("hps_nodes", "hps_build", "hps_build_batch", "hps_rebuild", "hps_solve", "hps_solve_batch", "hps_reserve", "hps_solve_noalloc",
-           "hps_root_R", "hps_leaf_ops", "hps_zgemm", "hps_fp64_rate", "hps_tune", "hps_plan", "hps_info", "hps_build_times", "hps_build_product_times", "hps_status", "hps_free", "hps_strerror")
+           "hps_root_R", "hps_leaf_ops", "hps_zgemm", "hps_zinv", "hps_check_wait", "hps_fp64_rate", "hps_tune", "hps_plan", "hps_info", "hps_build_times", "hps_build_product_times", "hps_status", "hps_free", "hps_strerror")
 
 
 class hps_desc(ctypes.Structure):
@@ -88,6 +88,8 @@ def lib():
         L.hps_solve_batch.argtypes = [P, ctypes.c_int, P, P, P, P, P]
         L.hps_reserve.argtypes = [P, ctypes.c_int]
         L.hps_zgemm.argtypes = [ctypes.c_int] * 4 + [P, P, P, ctypes.c_int, P]
+        L.hps_zinv.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), P]
+        L.hps_check_wait.argtypes = [ctypes.c_int, P]
         L.hps_fp64_rate.argtypes = [P, P]
         L.hps_root_R.argtypes = [P, P, ctypes.c_int, P]
         L.hps_leaf_ops.argtypes = [P, ctypes.c_int, P, P, P, P]
@@ -309,6 +311,28 @@ def hps_zgemm(A, B, C, emulated: int, stream=None):
     _check(lib().hps_zgemm(M, N, K, batch, _ptr(A), _ptr(B), _ptr(C), int(emulated), _stream(stream)),
            "hps_zgemm")
     return C
+
+
+def hps_zinv(A, Ainv, mode: int = 0, stream=None):
+    """Ainv[b] = A[b]^-1 for complex128 device tensors shaped [batch, n, n]
+    (column-major matrices stored transposed; the inverse of the transpose is
+    the transpose of the inverse, so row-major input works the same).
+    Returns (code, bad): HPS_OK or HPS_ESINGULAR with the index of a matrix
+    that had a zero pivot column; raises for every other code."""
+    batch, n, n2 = A.shape
+    if n2 != n or tuple(Ainv.shape) != (batch, n, n):
+        raise ValueError("A and Ainv must be [batch, n, n]")
+    bad = ctypes.c_int(-1)
+    code = lib().hps_zinv(n, batch, _ptr(A), _ptr(Ainv), int(mode), ctypes.byref(bad), _stream(stream))
+    if code not in (HPS_OK, HPS_ESINGULAR):
+        raise HPSError(code, "hps_zinv")
+    return code, bad.value
+
+
+def hps_check_wait(limit_ms: int, stream=None) -> int:
+    """Run the products' bounded wait on a barrier nothing completes; returns
+    the status code (HPS_ETIMEOUT expected)."""
+    return lib().hps_check_wait(int(limit_ms), _stream(stream))
 
 
 def hps_fp64_rate(stream=None) -> float:

@@ -126,6 +126,20 @@ def test_zgemm_argument_checks_need_no_device():
     assert L.hps_zgemm(2, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, 1, None) == hps.HPS_EINVAL
 
 
+def test_zinv_and_wait_check_argument_checks_need_no_device():
+    L = hps.lib()
+    a = np.zeros(16, complex)
+    bad = ctypes.c_int(7)
+    # n < 2, batch < 1, mode not 0 / 1, host arrays: refused before any device work
+    assert L.hps_zinv(1, 1, a.ctypes.data, a.ctypes.data, 0, ctypes.byref(bad), None) == hps.HPS_EINVAL
+    assert bad.value == -1
+    assert L.hps_zinv(2, 0, a.ctypes.data, a.ctypes.data, 0, None, None) == hps.HPS_EINVAL
+    assert L.hps_zinv(2, 1, a.ctypes.data, a.ctypes.data, 2, None, None) == hps.HPS_EINVAL
+    assert L.hps_zinv(2, 1, a.ctypes.data, a.ctypes.data, 0, None, None) == hps.HPS_EINVAL
+    assert L.hps_check_wait(0, None) == hps.HPS_EINVAL
+    assert L.hps_check_wait(2001, None) == hps.HPS_EINVAL
+
+
 def test_plan_of_a_rectangular_grid():
     info = hps.hps_plan(hps.Problem(8, 16, 40.0, 40.0, my=2))
     assert info.leaves == 16 and info.levels == 4 and info.n_bdry == 2 * (8 + 2) * 14
