@@ -497,10 +497,8 @@ void fill_info(const Plan &pl, hps_info_t &in) {
   long long bf = pl.leaf_lu ? (long long)pl.leaves * 8 * (n * n * n / 3 + nb * n * n)
                             : (long long)pl.leaves * 8 * (n * n * n + nb * n * pl.p);
   // refined inverse: the complex64 inverse, then per step the residual
-  // product (tensor cores) and the complex64 correction product; G X0 and
-  // the last correction's product with it, (G X0) E
-  if (pl.leaf_refined)
-    bf += (long long)pl.leaves * 8 * (2LL * kLeafRefineSteps * n * n * n + nb * n * pl.p + nb * n * n);
+  // product (tensor cores) and the complex64 correction product
+  if (pl.leaf_refined) bf += (long long)pl.leaves * 8 * (2LL * kLeafRefineSteps * n * n * n);
   const long long nbi = pl.nbi, qe = pl.qe, e = pl.e;
   long long sf = (long long)pl.leaves * 8 * (nbi * ni + n * n + (pl.gauss ? nb * qe : 0));
   const long long lu_aux = pl.leaf_lu ? (long long)pl.leaves * n * (4 + 8) : 0;
@@ -2404,9 +2402,8 @@ static int plan_handle(hps_handle *h, const hps_desc *desc) {
     lt.nb = pl.nb;
     lt.ni = pl.ni;
     leaf_scr = (long long)hps::leaf_refined_scratch_bytes(lt, (int)chunk);
-    // per chunk: complex64 inverse, B, G X0, per step the residual product
-    // and the correction (product and FP64 add), G X before the last
-    // correction and its update
+    // per chunk: complex64 inverse, B, X = X0, per step the residual product
+    // and the correction (product and FP64 add), G X
     h->info.build_launches += nchunks * (hps::leaf_refined_launches(lt, (int)chunk, kLeafRefineSteps) - 1);
   }
   long long rbuf = 0, qbuf = 0, wbuf = 0, mbuf = 0, cbuf = 0, wref = 0;

@@ -245,11 +245,9 @@ cudaError_t launch_leaf_lu(const LeafTables &lt, const LeafProb *probs, int npro
 size_t lu_meta_ints(int n);
 
 // Leaf step in inverse form for complex128 leaves by refinement of a
-// complex64 inverse (leaf_refine.cu): X0 = B^-1 in complex64 (gj32, or
-// launch_leaf with cluster size cs32 where the panel does not fit), then
-// `steps` (>= 1) times E = I - B X (Ozaki product on the tensor cores) and
-// X += X0 E; GX = G X, from G X before the last correction (on a second
-// stream beside the last residual) plus (G X0) E.  Writes X and GX of leaves
+// complex64 inverse (leaf_refine.cu): X0 = B^-1 in complex64 (launch_leaf
+// with cluster size cs32), then `steps` times E = I - B X (Ozaki product on
+// the tensor cores) and X += X0 E, then GX = G X.  Writes X and GX of leaves
 // [leaf0, leaf0 + count) ([leaf][n][n], [leaf][n][nb] column-major, indexed
 // by the absolute leaf number, like launch_leaf).  scr: 256-byte aligned
 // device scratch of leaf_refined_scratch_bytes(lt, count).  *launches is

@@ -11,13 +11,10 @@
 //                       in FP64 in the product's epilogue)
 // Each step multiplies the residual norm by ~||I - B X0|| (~1e-5), and the
 // complex64 rounding of the correction is ~1e-7 of a term of that size, so
-// two steps reach the complex128 rounding level.  G X = [R | Gamma] comes from
-// the sparse G in FP64, applied to X before the last correction on a second
-// stream beside the last residual (a memory-bound tensor-core product that
-// leaves the FP64 pipes idle), then updated by (G X0) E, the last correction
-// with G in front.  The result is the inverse form of the leaf operators
-// (X = B^-1 = [Psi | Y], GX), to the accuracy of a complex128 inversion, with
-// most of the work off this part's FP64 pipes.
+// two steps reach the complex128 rounding level.  Then G X = [R | Gamma] in
+// FP64 with the sparse G.  The result is the inverse form of the leaf
+// operators (X = B^-1 = [Psi | Y], GX), to the accuracy of a complex128
+// inversion, with most of the work off this part's FP64 pipes.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -111,26 +108,20 @@ __global__ void __launch_bounds__(256) leaf_B_kernel(LeafTables lt, const LeafPr
 
 // GX = G X for leaves [leaf0, leaf0 + gridDim.x): X n x n, GX nb x n,
 // column-major.  Row r of G is the outward normal derivative along the grid
-// line through boundary node r (p entries), minus i eta at r itself.  The
-// sums are formed in FP64 whatever the storage types (X complex128 or
-// complex64; GX likewise, rounded on the store).
-__device__ __forceinline__ void gx_store(double2 *d, double2 v) { *d = v; }
-__device__ __forceinline__ void gx_store(float2 *d, double2 v) { *d = make_float2((float)v.x, (float)v.y); }
-
-template <class TX, class TG>
+// line through boundary node r (p entries), minus i eta at r itself.
 __global__ void __launch_bounds__(256) leaf_GX_kernel(LeafTables lt, const LeafProb *probs, int nprob,
-                                                      long long leaf0, const TX *X, TG *GX) {
+                                                      long long leaf0, const double2 *X, double2 *GX) {
   extern __shared__ __align__(16) unsigned char lsm[];
   const long long leaf = leaf0 + blockIdx.x;
   const LeafProb &pb = probs[leaf_problem(probs, nprob, leaf)];
   const LeafSmem t = load_leaf_tables(lsm, lt, pb, leaf);
   const int p = lt.p, e = lt.e, n = lt.n, nb = lt.nb;
-  const TX *Xl = X + (size_t)blockIdx.x * n * n;
-  TG *GXl = GX + (size_t)blockIdx.x * n * nb;
+  const double2 *Xl = X + (size_t)blockIdx.x * n * n;
+  double2 *GXl = GX + (size_t)blockIdx.x * n * nb;
   const double2 ieta = make_double2(-pb.eta.y, pb.eta.x);
   for (int idx = threadIdx.x; idx < nb * n; idx += blockDim.x) {
     const int r = idx % nb, j = idx / nb;
-    const TX *Xj = Xl + (size_t)j * n;
+    const double2 *Xj = Xl + (size_t)j * n;
     const int side = r / e, ix = t.grid[r] & 0xff, iy = t.grid[r] >> 8;
     double2 acc = make_double2(0.0, 0.0);
     for (int k = 0; k < p; k++) {
@@ -150,15 +141,14 @@ __global__ void __launch_bounds__(256) leaf_GX_kernel(LeafTables lt, const LeafP
         q = t.loc[iy * p + k];
       }
       if (q < 0) continue;  // (lines through non-corner edge nodes hold no corner; a guard)
-      const TX x = Xj[q];
-      acc.x = fma(w, (double)x.x, acc.x);
-      acc.y = fma(w, (double)x.y, acc.y);
+      const double2 x = Xj[q];
+      acc.x = fma(w, x.x, acc.x);
+      acc.y = fma(w, x.y, acc.y);
     }
-    const TX xr = Xj[r];
-    const double2 ie = cmul(ieta, make_double2(xr.x, xr.y));  // - i eta x_r
+    const double2 ie = cmul(ieta, Xj[r]);  // - i eta x_r
     acc.x -= ie.x;
     acc.y -= ie.y;
-    gx_store(GXl + (size_t)j * nb + r, acc);
+    GXl[(size_t)j * nb + r] = acc;
   }
 }
 
@@ -240,7 +230,7 @@ size_t leaf_refined_scratch_bytes(const LeafTables &lt, int count) { return refi
 
 int leaf_refined_launches(const LeafTables &lt, int count, int steps) {
   GemmDesc g = plain_gemm(lt.n, lt.n, lt.n, count, nullptr, 0, nullptr, 1, nullptr);
-  int n = 5;  // X0, B, G X0, G X before the last step, its update
+  int n = 3;  // X0, B, G X
   for (int it = 0; it < steps; it++) n += oz_launches(g, it > 0) + 1;  // residual, correction
   return n;
 }
@@ -249,7 +239,6 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
                                 void *X, void *GX, void *scr, size_t scr_bytes, unsigned int *status, int level,
                                 int cs32, int steps, cudaStream_t st, int *launches) {
   if (count <= 0) return cudaSuccess;
-  if (steps < 1) return cudaErrorInvalidValue;
   const RefineLayout L = refine_layout(lt, count);
   if (!scr || scr_bytes < L.total) return cudaErrorInvalidValue;
   char *w = (char *)scr;
@@ -265,96 +254,56 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
   // (whose 256 CTAs leave a third of the SMs half empty) runs on st
   const size_t tsm = leaf_tables_smem(lt);
   GemmDesc g0 = plain_gemm(n, n, n, count, Bm, 0, X0, 1, E);
-  float2 *GX0 = (float2 *)(w + L.gx0);
   cudaStream_t side = side_stream(st);
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // fork, join, X0 ready, join of G X
-  auto destroy = [&]() {
-    for (cudaEvent_t &e : ev)
-      if (e) cudaEventDestroy(e);
-  };
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaError_t err = cudaSuccess;
-  if (side) {
-    for (int q = 0; q < 4 && err == cudaSuccess; q++) err = cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
-    if (err == cudaSuccess) err = cudaEventRecord(ev[0], st);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(side, ev[0], 0);
-    if (err == cudaSuccess) {
-      leaf_B_kernel<<<count, 256, tsm, side>>>(lt, probs, nprob, leaf0, Bm);
-      err = cudaGetLastError();
-    }
-    if (err == cudaSuccess) err = launch_oz_split_a(g0, w + L.oz, L.total - L.oz, side);
-    if (err == cudaSuccess) err = cudaEventRecord(ev[1], side);
-    if (err != cudaSuccess) {
-      destroy();
-      return err;
-    }
+  if (side && (err = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) == cudaSuccess &&
+      (err = cudaEventCreateWithFlags(&join, cudaEventDisableTiming)) == cudaSuccess &&
+      (err = cudaEventRecord(fork, st)) == cudaSuccess && (err = cudaStreamWaitEvent(side, fork, 0)) == cudaSuccess) {
+    leaf_B_kernel<<<count, 256, tsm, side>>>(lt, probs, nprob, leaf0, Bm);
+    if ((err = cudaGetLastError()) == cudaSuccess) err = launch_oz_split_a(g0, w + L.oz, L.total - L.oz, side);
+    if (err == cudaSuccess) err = cudaEventRecord(join, side);
+  } else {
+    cudaGetLastError();
+    side = nullptr;
+  }
+  if (err != cudaSuccess) {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    return err;
   }
   nl += 3;  // B, A's exponents and digits
   // X0: the complex64 inverse (32-column panels, one CTA a leaf; the
-  // cluster kernel where the panel does not fit; its G X0 is formed below)
+  // cluster kernel where the panel does not fit; its G X0 is not used)
   err =
       gj32_supported(lt)
           ? launch_leaf_gj32(lt, probs, nprob, leaf0, count, (float2 *)X0 - (size_t)leaf0 * n * n, nullptr, w + L.s,
                              status, level, st)
           : launch_leaf(lt, probs, nprob, leaf0, count, (float2 *)X0 - (size_t)leaf0 * n * n,
-                        GX0 - (size_t)leaf0 * n * nb, w + L.s, (int *)(w + L.meta), status, level, cs32, true, st);
+                        (float2 *)(w + L.gx0) - (size_t)leaf0 * n * nb, w + L.s, (int *)(w + L.meta), status, level,
+                        cs32, true, st);
   if (err == cudaSuccess) nl++;
-  // (without a side stream: B and its split here, in order)
-  if (err == cudaSuccess && !side) {
+  if (side) {
+    // (without a side stream: B and its split here, in order)
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, join, 0);
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
+  } else if (err == cudaSuccess) {
     leaf_B_kernel<<<count, 256, tsm, st>>>(lt, probs, nprob, leaf0, Bm);
     if ((err = cudaGetLastError()) == cudaSuccess) err = launch_oz_split_a(g0, w + L.oz, L.total - L.oz, st);
   }
-  // G X0 (complex64; its product with the last residual updates G X at the
-  // end): on the side stream, beside the first residual
-  cudaStream_t gs = side ? side : st;
-  if (err == cudaSuccess && side) err = cudaEventRecord(ev[2], st);
-  if (err == cudaSuccess && side) err = cudaStreamWaitEvent(side, ev[2], 0);
-  if (err == cudaSuccess) {
-    leaf_GX_kernel<<<count, 256, tsm, gs>>>(lt, probs, nprob, leaf0, (const float2 *)X0, GX0);
-    if ((err = cudaGetLastError()) == cudaSuccess) nl++;
-  }
-  if (err == cudaSuccess && side) err = cudaStreamWaitEvent(st, ev[1], 0);
-  if (err != cudaSuccess) {
-    destroy();
-    return err;
-  }
+  if (err != cudaSuccess) return err;
   for (int it = 0; it < steps; it++) {
-    const bool last = it == steps - 1;
-    if (last) {
-      // X is final but for the last correction: G X (FP64, the sparse G)
-      // runs on the side stream beside the last residual, whose product is
-      // bound by memory and leaves the FP64 pipes idle
-      if (side) err = cudaEventRecord(ev[2], st);
-      if (err == cudaSuccess && side) err = cudaStreamWaitEvent(side, ev[2], 0);
-      if (err == cudaSuccess) {
-        if (it == 0)
-          leaf_GX_kernel<<<count, 256, tsm, gs>>>(lt, probs, nprob, leaf0, (const float2 *)X0, GXl);
-        else
-          leaf_GX_kernel<<<count, 256, tsm, gs>>>(lt, probs, nprob, leaf0, (const double2 *)Xl, GXl);
-        if ((err = cudaGetLastError()) == cudaSuccess) nl++;
-      }
-      if (err == cudaSuccess && side) err = cudaEventRecord(ev[3], side);
-      if (err != cudaSuccess) {
-        destroy();
-        return err;
-      }
-    }
     // E = I - B X, complex128-accurate on the tensor cores (X = X0 in the
     // first step, read in complex64)
     GemmDesc g = it == 0 ? plain_gemm(n, n, n, count, Bm, 0, X0, 1, E) : plain_gemm(n, n, n, count, Bm, 0, Xl, 0, E);
     g.C.f32 = 1;  // (accurate to complex128 rounding, then rounded to complex64)
     g.alpha = make_double2(-1.0, 0.0);
     g.addI = 1;
+    // (B's digits are the same in every step: split once)
     // (B's digits are in the workspace already: split once, above)
-    if ((err = launch_gemm_oz(g, w + L.oz, L.total - L.oz, st, status, true)) != cudaSuccess) {
-      destroy();
-      return err;
-    }
+    if ((err = launch_gemm_oz(g, w + L.oz, L.total - L.oz, st, status, true)) != cudaSuccess) return err;
     nl += oz_launches(g, true);
-    // the last correction overwrites the X that G X reads
-    if (last && side && (err = cudaStreamWaitEvent(st, ev[3], 0)) != cudaSuccess) {
-      destroy();
-      return err;
-    }
     // X += X0 E: the product in complex64 arithmetic, the addition in FP64
     // (the error of this product is amplified by cond(B) in the next
     // residual, so it stays in elementwise complex64 arithmetic: a 4-slice
@@ -367,23 +316,12 @@ cudaError_t launch_leaf_refined(const LeafTables &lt, const LeafProb *probs, int
     c.D = c.C;
     if (it == 0) c.D = c.A;
     c.beta = make_double2(1.0, 0.0);
-    if ((err = launch_gemm(&c, 1, st)) != cudaSuccess) {
-      destroy();
-      return err;
-    }
+    if ((err = launch_gemm(&c, 1, st)) != cudaSuccess) return err;
     nl++;
   }
-  // G X = [R | Gamma] of the final X: G X (before the last correction) +
-  // (G X0) E, the last correction's product with G in front (complex64
-  // arithmetic, FP64 addition: its terms are ~|E| ~1e-10 of G X)
-  GemmDesc gu = plain_gemm(nb, n, n, count, GX0, 1, E, 1, GXl);
-  gu.cf32 = 1;
-  gu.wide_epilogue = 1;
-  gu.D = gu.C;
-  gu.beta = make_double2(1.0, 0.0);
-  err = launch_gemm(&gu, 1, st);
-  destroy();
-  if (err != cudaSuccess) return err;
+  // G X = [R | Gamma]
+  leaf_GX_kernel<<<count, 256, tsm, st>>>(lt, probs, nprob, leaf0, Xl, GXl);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
   nl++;
   if (launches) *launches += nl;
   return cudaSuccess;
