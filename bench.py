@@ -44,29 +44,36 @@ def workload():
     return W.point_sources(m=M, p=P_ORDER, kappa=KAPPA)
 
 
-def config_dict(nrhs=1, l2="flushed between steps (256 MiB write)", gpu=True):
-    """The workload of a step; with gpu, also how the GPU path computes it
-    (the reference arm, the oracle on the host cores, has no such choices)."""
+def config_dict(nrhs=1):
+    """The workload of a step, the same for both arms (the GPU path and the
+    reference arm, the oracle on the host cores); how each arm computes it is
+    in implementation_dict."""
     wl = workload()
-    out = {
+    return {
         "workload": "helmholtz_impedance_point_sources",
         "leaves": f"{M}x{M}", "p": P_ORDER, "q": P_ORDER - 2, "kappa": KAPPA, "eta": KAPPA,
         "c": "1+0.3 sin(4 pi x) cos(6 pi y)", "s": "8 Gaussian sources, width 0.01, seed 1", "t": 0,
         "dof": M * M * (P_ORDER * P_ORDER - 4), "tensor_nodes": M * M * P_ORDER * P_ORDER,
-        "nrhs_per_step": nrhs, "l2": l2, "precision": "complex128",
+        "nrhs_per_step": nrhs, "precision": "complex128",
+        "l2": "GPU arm: L2 flushed between timed steps (256 MiB write); host-core arm: not applicable",
         "domain": list(wl.domain),
     }
-    if gpu:
-        out["leaf_form"] = ("LU factors P D B = L U (leaf kernel), two triangular sweeps a solve" if LEAF_FORM == 0
-                            else "B^-1: complex64 Gauss-Jordan inverse refined to complex128 by two steps of "
-                                 "E = I - B X (Ozaki product on tcgen05) and X += X0 E; one product a solve")
-        out["products"] = ("FP64 pipes; merge products of 2^26+ complex multiply-adds by the Ozaki scheme "
-                           "on the bf16 tensor cores (tcgen05; 9 slices of 6 bits, exact FP32 slice sums, "
-                           "complex128 totals)")
-    else:
-        out["program"] = ("the oracle (oracle/hps_oracle.c): Algorithm 1 and 2 in plain C99 complex128, "
-                          "dense LU per leaf, OpenMP over the boxes of a level")
-    return out
+
+
+def implementation_dict(gpu=True):
+    """How an arm computes the step: the GPU path's leaf form and products,
+    or the reference arm's program."""
+    if not gpu:
+        return {"program": "the oracle (oracle/hps_oracle.c): Algorithm 1 and 2 in plain C99 complex128, "
+                           "dense LU per leaf, OpenMP over the boxes of a level"}
+    return {
+        "leaf_form": ("LU factors P D B = L U (leaf kernel), two triangular sweeps a solve" if LEAF_FORM == 0
+                      else "B^-1: complex64 Gauss-Jordan inverse refined to complex128 by two steps of "
+                           "E = I - B X (Ozaki product on tcgen05) and X += X0 E; one product a solve"),
+        "products": ("FP64 pipes; merge products of 2^26+ complex multiply-adds by the Ozaki scheme "
+                     "on the bf16 tensor cores (tcgen05; 9 slices of 6 bits, exact FP32 slice sums, "
+                     "complex128 totals)"),
+    }
 
 
 class ClockSampler:
@@ -170,7 +177,7 @@ def reference_arm(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(l2="n/a (CPU)", gpu=False),
+        "config": config_dict(), "implementation": implementation_dict(gpu=False),
         "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": threads, "kind": "oracle",
                          "sample": "full 16x16-leaf build + 1-RHS solve per step"},
         "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -467,6 +474,7 @@ def ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded point sources; no dataset)", "config": config_dict(),
+        "implementation": implementation_dict(),
         "build_dof_per_s": dof / (statistics.median(build_ms) / 1e3),
         "build_ms_median": statistics.median(build_ms),
         "solve_rhs_per_s": nb / (batch_ms / 1e3), "solve_nrhs_batch": nb,
